@@ -1,0 +1,151 @@
+"""Contacts: detection and linearisation (App. A.1), Fischer-Burmeister complementarity
+functions and their derivatives (Eq. 14; App. B.2, Eqs. 52-57), split indicators (Eq. 24)
+and the conjugate-residual constraint solver (Sec. 6).
+
+TEST INFRASTRUCTURE (see the package docstring). Plain FP64.
+
+Readings of the paper used here (the paper leaves these open):
+  * detection runs once per frame on the predicted state s~; a vertex/obstacle pair is a
+    contact when the signed distance is below the scene's contact margin; the contact
+    frame is frozen for the frame (Sec. 5.3: H depends only on the detection);
+  * normal n: the obstacle's outward normal at the closest surface point p^;
+    d_n = n . p^ (Eq. 36); tangents: f1 from Gram-Schmidt of the world axis least
+    aligned with n (lowest index on ties), f2 = n x f1; d_f = f . u^ with u^ the obstacle
+    surface velocity (Eq. 37);
+  * friction is isotropic: |lambda_f| and |delta_dot_f| are Euclidean norms over (f1, f2),
+    each contact has one scalar friction compliance E_f applied to both rows;
+  * phi_f = omega_f delta_dot_f + E_f lambda_f (Eq. 55 with J_f v read as the indicator
+    times the relative tangential velocity);
+  * degenerate cases: if sqrt(delta_n^2 + r^2 lambda_n^2) is zero, omega_n = 1 and
+    E_n = 0. With lambda_n > 0: if the E_f numerator vanishes (relative to its scale) the
+    contact sticks, E_f = 0; if the denominator is not positive (the iterate lies beyond
+    |lambda_f| = 2 mu lambda_n, where Eq. 57 turns negative) E_f takes the slip value of
+    the minimum-map form (Eq. 51), (|delta_dot_f| + r (|lambda_f| - mu lambda_n)) /
+    (mu lambda_n), which has no fixed point outside the cone. A contact with mu = 0 is
+    treated like an inactive one (omega_f = 0, E_f = 1), so its friction force vanishes.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from scenegen import OBST_CYLINDER, OBST_PLANE
+
+TINY_REL = 1e-12
+
+
+def tangent_frame(n):
+    """f1 by Gram-Schmidt of the world axis least aligned with n, f2 = n x f1."""
+    n = np.asarray(n, dtype=np.float64)
+    k = int(np.argmin(np.abs(n)))
+    e = np.zeros(3)
+    e[k] = 1.0
+    f1 = e - np.dot(e, n) * n
+    f1 /= np.linalg.norm(f1)
+    f2 = np.cross(n, f1)
+    return f1, f2
+
+
+def closest_point(obst, x):
+    """(signed distance, outward unit normal, closest surface point) of x to an obstacle."""
+    p = np.asarray(obst.p, dtype=np.float64)
+    a = np.asarray(obst.axis, dtype=np.float64)
+    if obst.kind == OBST_PLANE:
+        phi = float(np.dot(a, x - p))
+        return phi, a.copy(), x - phi * a
+    if obst.kind == OBST_CYLINDER:
+        d = x - p
+        axial = np.dot(d, a)
+        radial = d - axial * a
+        rho = float(np.linalg.norm(radial))
+        if rho == 0.0:
+            n, _ = tangent_frame(a)          # on the axis: any perpendicular direction
+        else:
+            n = radial / rho
+        return rho - obst.radius, n, p + axial * a + obst.radius * n
+    raise ValueError("unknown obstacle kind")
+
+
+def detect(scene, s_tilde, free_verts):
+    """All (vertex, obstacle) pairs with signed distance below the contact margin at the
+    predicted positions, ordered by vertex id then obstacle index."""
+    out = []
+    for v in free_verts:
+        for oi, ob in enumerate(scene.obstacles):
+            phi, n, ph = closest_point(ob, s_tilde[v])
+            if phi < scene.contact_margin:
+                f1, f2 = tangent_frame(n)
+                u = np.asarray(ob.vel, dtype=np.float64)
+                out.append(dict(vertex=int(v), obstacle=oi, n=n, f1=f1, f2=f2,
+                                d_n=float(np.dot(n, ph)),
+                                d_f=np.array([np.dot(f1, u), np.dot(f2, u)]),
+                                mu=float(ob.mu), gap=phi))
+    return out
+
+
+# -- Fischer-Burmeister (App. B.2) ------------------------------------------------------
+def fb(a, b):
+    """phi_FB(a, b) = a + b - sqrt(a^2 + b^2) (Eq. 14)."""
+    return a + b - np.sqrt(a * a + b * b)
+
+
+def normal_terms(delta_n, lam_n, r_n):
+    """phi_n (Eq. 52), the split indicator omega_n (Eqs. 53, 24) and the compliance E_n
+    (Eq. 54) of one normal row."""
+    rho = np.sqrt(delta_n * delta_n + r_n * r_n * lam_n * lam_n)
+    phi = delta_n + r_n * lam_n - rho
+    if rho == 0.0:
+        return phi, 1.0, 0.0
+    omega = 1.0 - delta_n / rho
+    E = (1.0 - r_n * lam_n / rho) * r_n
+    return phi, omega, E
+
+
+def friction_terms(vel_f, lam_f, lam_n, mu, r_f):
+    """omega_f (Eqs. 56, 24), the scalar compliance E_f (Eq. 57) and phi_f (Eq. 55) of one
+    contact's two friction rows. vel_f is the tangential relative velocity delta_dot_f."""
+    if lam_n <= 0.0 or mu <= 0.0:
+        return 0.0, 1.0, np.array(lam_f, dtype=np.float64)
+    a = float(np.linalg.norm(vel_f))
+    lf = float(np.linalg.norm(lam_f))
+    s = mu * lam_n - lf
+    root = np.sqrt(a * a + r_f * r_f * s * s)
+    num = root - r_f * s
+    den = a + mu * r_f * lam_n - root
+    scale = a + mu * r_f * lam_n + r_f * abs(s)
+    if num <= TINY_REL * scale:
+        E = 0.0                                   # sticking: no tangential velocity allowed
+    elif den <= TINY_REL * scale:
+        E = (a + r_f * (lf - mu * lam_n)) / (mu * lam_n)   # far outside the cone: Eq. 51
+    else:
+        E = num / den * r_f
+    return 1.0, E, vel_f + E * np.asarray(lam_f)
+
+
+# -- conjugate residual --------------------------------------------------------------
+def conjugate_residual(apply, b, n_iter):
+    """Unpreconditioned conjugate residual for a symmetric operator, x0 = 0, exactly
+    n_iter iterations (stopping early only if the residual or search direction vanishes)."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    if not np.any(r):
+        return x
+    Ar = apply(r)
+    p = r.copy()
+    Ap = Ar.copy()
+    rAr = float(r @ Ar)
+    for _ in range(n_iter):
+        ApAp = float(Ap @ Ap)
+        if ApAp == 0.0:
+            break
+        alpha = rAr / ApAp
+        x += alpha * p
+        r -= alpha * Ap
+        if not np.any(r):
+            break
+        Ar = apply(r)
+        rAr_new = float(r @ Ar)
+        beta = rAr_new / rAr if rAr != 0.0 else 0.0
+        rAr = rAr_new
+        p = r + beta * p
+        Ap = Ar + beta * Ap
+    return x

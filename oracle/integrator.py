@@ -1,0 +1,187 @@
+"""The frame loop of Alg. 4 (Sec. 6): prediction, detection, Delassus operator and
+preconditioner, then local-global iterations constrained by the Fischer-Burmeister
+functions, and integration.
+
+TEST INFRASTRUCTURE (see the package docstring). Plain FP64.
+
+Readings of the paper used here (the paper leaves these open):
+  * q^0 = s~ (the predicted state) and lambda^0 = 0 at the start of every frame;
+  * "5 iterations" means exactly n_iters local-global iterations k = 0 .. n_iters - 1;
+  * the Schur-complement right-hand side is h^-2 (h - J A^-1 g), the sign of Algs. 3-4
+    (eliminating q from Eq. 21 gives this sign; Eq. 22 prints the opposite one);
+  * pinned vertices are eliminated (Dirichlet): they are not unknowns and move with the
+    scene's handle velocity;
+  * the residual used to count iterations (not defined by the paper) is
+    R = max_j max(|min(delta_n, r_n lambda_n)|, h |phi_f|) / L, with L the diagonal of the
+    rest bounding box.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import contact as C
+from .fem import FEM
+from .local import elastic_energy, project
+
+
+@dataclass
+class OracleOptions:
+    n_iters: int = 5
+    n_cr: int = 10
+    exact_constraint_solve: bool = False   # dense solve instead of CR (isolates CR error)
+
+
+class Oracle:
+    def __init__(self, scene):
+        self.scene = scene
+        self.fem = FEM(scene)
+        self.h = float(scene.h)
+        self.g = np.asarray(scene.gravity, dtype=np.float64)
+        self.L_ref = scene.bbox_diagonal
+
+    # -- pieces of Alg. 4 ---------------------------------------------------------------
+    def predict(self, q_t, v_t):
+        """s~ = q_t + h v_t + h^2 M^-1 f_ext (Eq. 1) with f_ext = M g."""
+        return q_t + self.h * v_t + self.h ** 2 * self.g[None, :]
+
+    def pinned_positions(self, q_t):
+        return q_t[self.scene.pinned] + self.h * np.asarray(self.scene.handle_vel)[None, :]
+
+    def local_step(self, q):
+        """p_i = project(G_i q) for every element (Eq. 5)."""
+        f = self.fem
+        F = f.deformation_gradients(q)
+        return project(F, f.model, f.w, f.V, f.emu, f.elam, f.alpha)
+
+    def contact_jacobian(self, contacts):
+        """H (3c x 3n_f): rows n_j, f1_j, f2_j at the DoFs of contact j's vertex (Eqs. 36-37)."""
+        f = self.fem
+        pos = {int(v): i for i, v in enumerate(f.free_verts)}
+        c = len(contacts)
+        H = np.zeros((3 * c, 3 * len(f.free_verts)))
+        for j, ct in enumerate(contacts):
+            k = pos[ct["vertex"]]
+            H[3 * j + 0, 3 * k:3 * k + 3] = ct["n"]
+            H[3 * j + 1, 3 * k:3 * k + 3] = ct["f1"]
+            H[3 * j + 2, 3 * k:3 * k + 3] = ct["f2"]
+        return H
+
+    def delassus(self, H):
+        """W = H A^-1 H^T (Eq. 27) from direct solves."""
+        if H.shape[0] == 0:
+            return np.zeros((0, 0))
+        X = self.fem.solve(H.T.copy())
+        return H @ X
+
+    def preconditioner(self, W, c):
+        """r_n = h^2 W_jj on normal rows, r_f = h W_jj on friction rows (Eq. 28); the two
+        friction rows share h * mean(W_f1f1, W_f2f2)."""
+        d = np.diag(W).reshape(c, 3) if c else np.zeros((0, 3))
+        return self.h ** 2 * d[:, 0], self.h * 0.5 * (d[:, 1] + d[:, 2])
+
+    def contact_state(self, q_f, q_t_f, lam, H, contacts, r_n, r_f):
+        """Gaps, indicators, compliances and NCP values at (q^k, lambda^k) (Alg. 4, "Evaluate
+        Omega, J, E, g, h"; Eq. 40 for delta_n and h delta_dot_f)."""
+        c = len(contacts)
+        h = self.h
+        Hq = (H @ q_f).reshape(c, 3)
+        Hqt = (H @ q_t_f).reshape(c, 3)
+        out = dict(omega=np.zeros((c, 3)), E=np.zeros((c, 3)), phi=np.zeros((c, 3)),
+                   delta_n=np.zeros(c), vel_f=np.zeros((c, 2)))
+        for j, ct in enumerate(contacts):
+            dn = Hq[j, 0] - ct["d_n"]
+            vf = ((Hq[j, 1:] - Hqt[j, 1:]) - h * ct["d_f"]) / h
+            phi_n, om_n, E_n = C.normal_terms(dn, lam[j, 0], r_n[j])
+            om_f, E_f, phi_f = C.friction_terms(vf, lam[j, 1:], lam[j, 0], ct["mu"], r_f[j])
+            out["omega"][j] = (om_n, om_f, om_f)
+            out["E"][j] = (E_n, E_f, E_f)
+            out["phi"][j] = (phi_n, phi_f[0], phi_f[1])
+            out["delta_n"][j] = dn
+            out["vel_f"][j] = vf
+        return out
+
+    def residual(self, cs, lam, r_n):
+        """max_j max(|min(delta_n, r_n lambda_n)|, h |phi_f|) / L_ref (dimensionless)."""
+        if len(r_n) == 0:
+            return 0.0
+        rn = np.abs(np.minimum(cs["delta_n"], r_n * lam[:, 0]))
+        rf = self.h * np.linalg.norm(cs["phi"][:, 1:], axis=1)
+        return float(np.maximum(rn, rf).max() / self.L_ref)
+
+    # -- one frame --------------------------------------------------------------------
+    def frame(self, q_t, v_t, opts: OracleOptions = OracleOptions(), lam0=None, dq0=None):
+        """Advance (q_t, v_t) by one frame. Returns (q_new, v_new, info)."""
+        f = self.fem
+        h = self.h
+        fv = f.free_verts
+        s_tilde = self.predict(q_t, v_t)
+        q_pin = self.pinned_positions(q_t)
+        contacts = C.detect(self.scene, s_tilde, fv)
+        c = len(contacts)
+        H = self.contact_jacobian(contacts)
+        W = self.delassus(H)
+        r_n, r_f = self.preconditioner(W, c)
+
+        q = s_tilde.copy()
+        q[self.scene.pinned] = q_pin
+        if dq0 is not None:
+            q[fv] += dq0[fv]
+        lam = np.zeros((c, 3)) if lam0 is None else np.array(lam0, dtype=np.float64)
+        q_t_f = q_t[fv].reshape(-1)
+        residuals = []
+        for _k in range(opts.n_iters):
+            p = self.local_step(q)                                       # local step
+            b = f.assemble_rhs(s_tilde, p, q_pin)                        # RHS (Eq. 6)
+            q_f = q[fv].reshape(-1)
+            if c:
+                cs = self.contact_state(q_f, q_t_f, lam, H, contacts, r_n, r_f)
+                residuals.append(self.residual(cs, lam, r_n))
+                Om = cs["omega"].reshape(-1)
+                J = Om[:, None] * H                                      # J = Omega H (Eq. 25)
+                g = b + h ** 2 * (J.T @ lam.reshape(-1))                 # Eq. 19
+                hv = (-np.concatenate([cs["phi"][:, :1], h * cs["phi"][:, 1:]], 1).reshape(-1)
+                      + J @ q_f)                                         # Eq. 19
+                Ecal = (cs["E"] / np.array([h ** 2, h, h])).reshape(-1)  # Eq. 20
+                K = Om[:, None] * W * Om[None, :] + np.diag(Ecal)        # Eq. 26 + E
+                rhs = (hv - J @ f.solve(g)) / h ** 2                     # Alg. 4 sign of the RHS
+                if opts.exact_constraint_solve:
+                    dlam = np.linalg.solve(K, rhs)
+                else:
+                    dlam = C.conjugate_residual(lambda x: K @ x, rhs, opts.n_cr)
+                lam = lam + dlam.reshape(c, 3)                           # Eq. 23a
+                omega_last = cs["omega"]
+                q_f = f.solve(b + h ** 2 * (J.T @ lam.reshape(-1)))      # Eq. 23b
+            else:
+                q_f = f.solve(b)                                         # Eq. 6
+            q = q.copy()
+            q[fv] = q_f.reshape(-1, 3)
+        info = dict(contacts=contacts, lam=lam, W=W, r_n=r_n, r_f=r_f, s_tilde=s_tilde, H=H)
+        if c and opts.n_iters:
+            info["omega_last"] = omega_last
+        if c:
+            cs = self.contact_state(q[fv].reshape(-1), q_t_f, lam, H, contacts, r_n, r_f)
+            residuals.append(self.residual(cs, lam, r_n))
+            info["final_state"] = cs
+        info["residuals"] = residuals
+        v_new = (q - q_t) / h
+        return q, v_new, info
+
+    # -- diagnostics --------------------------------------------------------------------
+    def energy(self, q, v):
+        """Kinetic + elastic (element's own psi) + gravitational energy."""
+        f = self.fem
+        F = f.deformation_gradients(q)
+        kin = 0.5 * float((f.mass[:, None] * v * v).sum())
+        ela = elastic_energy(F, f.model, f.V, f.emu, f.elam, f.alpha)
+        grav = -float((f.mass[:, None] * q * self.g[None, :]).sum())
+        return kin + ela + grav
+
+    def max_penetration(self, q):
+        worst = 0.0
+        for v in self.fem.free_verts:
+            for ob in self.scene.obstacles:
+                phi, _, _ = C.closest_point(ob, q[v])
+                worst = max(worst, -phi)
+        return worst

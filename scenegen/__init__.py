@@ -1,0 +1,313 @@
+"""Seeded synthetic scenes: tetrahedral lattices, material tables, obstacles, initial states.
+
+This module is shared by the FP64 oracle tests and by the CUDA path's tests and benchmark.
+It holds geometry and parameters only (vertex lattices, the Kuhn six-tetrahedron split of a
+cell, star-shaped masks, seeded rotations and obstacle layouts). None of the simulator's
+arithmetic (masses, gradients, projections, factorisations, contact laws) lives here.
+
+Scene workloads (the paper's meshes are not available, so these stand in for them):
+
+* ``cube_drop``   - an m x m x m vertex cube dropped onto a ground plane (the paper's
+  single-body drop tests; Sec. 7).
+* ``star_pull``   - an extruded five-point star pulled by a pinned cap through a seeded
+  4 x 4 array of fixed cylinders; shaped like the "crossing gingerbread man" teaser scene
+  (58.5k DoFs, up to 800 contacts; teaser caption and Tab. 3).
+* ``slope_box``   - a stiff box resting on an inclined plane (stick-slip test, Sec. 7.4,
+  Fig. 8): the analytic threshold is mu* = tan(theta).
+* ``single_tet``  - one regular tetrahedron, for closed-form checks.
+* ``batch``       - dozens of cubes of uneven size with mixed materials on tilted planes.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+MODEL_ARAP = 0      # projective-dynamics as-rigid-as-possible (SO(3) indicator)
+MODEL_COROT = 1     # co-rotational
+MODEL_SNH = 2       # stable Neo-Hookean
+
+OBST_PLANE = 0
+OBST_CYLINDER = 1
+
+GRAVITY_EARTH = (0.0, 0.0, -9.81)
+
+
+@dataclass
+class Material:
+    model: int
+    E: float
+    nu: float
+    rho: float
+
+
+@dataclass
+class Obstacle:
+    """A static analytic obstacle.
+
+    PLANE: ``p`` is a point on the plane, ``axis`` its unit outward normal.
+    CYLINDER: infinite cylinder; ``p`` a point on the axis, ``axis`` the unit axis
+    direction, ``radius`` its radius. ``mu`` is the Coulomb friction coefficient and
+    ``vel`` the obstacle's surface velocity (zero for fixed obstacles).
+    """
+    kind: int
+    p: tuple
+    axis: tuple
+    radius: float = 0.0
+    mu: float = 0.0
+    vel: tuple = (0.0, 0.0, 0.0)
+
+
+@dataclass
+class Scene:
+    """A complete simulation input. Units are SI. Arrays are float64 / int32."""
+    name: str
+    X: np.ndarray                  # (n, 3) rest positions
+    tets: np.ndarray               # (T, 4) vertex ids, positively oriented at rest
+    tet_material: np.ndarray       # (T,) index into materials
+    materials: List[Material]
+    obstacles: List[Obstacle]
+    h: float
+    gravity: tuple = GRAVITY_EARTH
+    pinned: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    handle_vel: tuple = (0.0, 0.0, 0.0)   # velocity of every pinned vertex
+    q0: Optional[np.ndarray] = None       # (n, 3) initial positions (default: X)
+    v0: Optional[np.ndarray] = None       # (n, 3) initial velocities (default: 0)
+    contact_margin: float = 0.0           # a contact exists when the gap is below this
+    n_iters: int = 5                      # local-global iterations per frame
+    n_cr: int = 10                        # conjugate-residual iterations per solve
+    n_frames: int = 1
+    spacing: float = 0.0                  # lattice spacing (informational)
+
+    def __post_init__(self):
+        self.X = np.ascontiguousarray(self.X, dtype=np.float64)
+        self.tets = np.ascontiguousarray(self.tets, dtype=np.int32)
+        self.tet_material = np.ascontiguousarray(self.tet_material, dtype=np.int32)
+        self.pinned = np.ascontiguousarray(self.pinned, dtype=np.int32)
+        if self.q0 is None:
+            self.q0 = self.X.copy()
+        if self.v0 is None:
+            self.v0 = np.zeros_like(self.X)
+        self.q0 = np.ascontiguousarray(self.q0, dtype=np.float64)
+        self.v0 = np.ascontiguousarray(self.v0, dtype=np.float64)
+
+    @property
+    def n_verts(self) -> int:
+        return int(self.X.shape[0])
+
+    @property
+    def n_tets(self) -> int:
+        return int(self.tets.shape[0])
+
+    @property
+    def bbox_diagonal(self) -> float:
+        return float(np.linalg.norm(self.X.max(0) - self.X.min(0)))
+
+
+# --------------------------------------------------------------------------------------
+# lattices
+# --------------------------------------------------------------------------------------
+# corner c of a unit cell has offsets (c & 1, (c >> 1) & 1, (c >> 2) & 1); the six Kuhn
+# tetrahedra all share the main diagonal 0 -> 7, so neighbouring cells conform.
+_CELL_OFFSETS = [(c & 1, (c >> 1) & 1, (c >> 2) & 1) for c in range(8)]
+_KUHN = [(0, 1, 3, 7), (0, 1, 5, 7), (0, 2, 3, 7), (0, 2, 6, 7), (0, 4, 5, 7), (0, 4, 6, 7)]
+
+
+def lattice_tets(nx: int, ny: int, nz: int, spacing: float, keep=None,
+                 origin=(0.0, 0.0, 0.0)):
+    """Tetrahedralise the cells of an nx x ny x nz vertex lattice.
+
+    ``keep(i, j, k)`` (cell indices) selects cells; unused vertices are dropped. Returns
+    (X, tets) with every tetrahedron positively oriented.
+    """
+    vid = -np.ones((nx, ny, nz), dtype=np.int64)
+    cells = []
+    for i in range(nx - 1):
+        for j in range(ny - 1):
+            for k in range(nz - 1):
+                if keep is None or keep(i, j, k):
+                    cells.append((i, j, k))
+    if not cells:
+        raise ValueError("empty lattice")
+    cells = np.array(cells, dtype=np.int64)
+    corner_ijk = cells[:, None, :] + np.array(_CELL_OFFSETS)[None, :, :]      # (C, 8, 3)
+    used = np.zeros((nx, ny, nz), dtype=bool)
+    used[corner_ijk[..., 0], corner_ijk[..., 1], corner_ijk[..., 2]] = True
+    ijk = np.argwhere(used)                                                   # lexicographic
+    vid[ijk[:, 0], ijk[:, 1], ijk[:, 2]] = np.arange(len(ijk))
+    X = np.asarray(origin, dtype=np.float64) + spacing * ijk.astype(np.float64)
+    corner_ids = vid[corner_ijk[..., 0], corner_ijk[..., 1], corner_ijk[..., 2]]  # (C, 8)
+    tets = corner_ids[:, np.array(_KUHN)].reshape(-1, 4)
+    # orient positively
+    d = X[tets[:, 1:]] - X[tets[:, :1]]
+    neg = np.linalg.det(d) < 0
+    tets[neg, 1], tets[neg, 2] = tets[neg, 2].copy(), tets[neg, 1].copy()
+    return X, tets.astype(np.int32)
+
+
+def random_rotation(rng: np.random.Generator) -> np.ndarray:
+    """Uniformly distributed rotation matrix from a seeded generator (unit quaternion)."""
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([
+        [1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+        [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+        [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)],
+    ])
+
+
+def _rot_y(deg: float) -> np.ndarray:
+    t = math.radians(deg)
+    return np.array([[math.cos(t), 0, math.sin(t)], [0, 1, 0], [-math.sin(t), 0, math.cos(t)]])
+
+
+def _star_polygon(r_out: float, r_in: float, points: int = 5):
+    """Vertices of a star polygon with one tip on the +x axis."""
+    ang = np.arange(2 * points) * math.pi / points
+    rad = np.where(np.arange(2 * points) % 2 == 0, r_out, r_in)
+    return np.stack([rad * np.cos(ang), rad * np.sin(ang)], 1)
+
+
+def _inside_polygon(px: float, py: float, poly: np.ndarray) -> bool:
+    inside = False
+    n = len(poly)
+    for a in range(n):
+        x1, y1 = poly[a]
+        x2, y2 = poly[(a + 1) % n]
+        if (y1 > py) != (y2 > py):
+            xc = x1 + (py - y1) * (x2 - x1) / (y2 - y1)
+            if px < xc:
+                inside = not inside
+    return inside
+
+
+# --------------------------------------------------------------------------------------
+# scenes
+# --------------------------------------------------------------------------------------
+def single_tet(edge: float = 0.1, model: int = MODEL_ARAP, E: float = 1e5, nu: float = 0.4,
+               rho: float = 1000.0, h: float = 1.0 / 60.0) -> Scene:
+    """One regular tetrahedron centred at the origin, no gravity, no obstacles."""
+    a = edge / math.sqrt(8.0)
+    X = np.array([[a, a, a], [a, -a, -a], [-a, a, -a], [-a, -a, a]], dtype=np.float64)
+    tets = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    d = X[tets[:, 1:]] - X[tets[:, :1]]
+    if np.linalg.det(d[0]) < 0:
+        tets = np.array([[0, 2, 1, 3]], dtype=np.int32)
+    return Scene("single_tet", X, tets, np.zeros(1, np.int32), [Material(model, E, nu, rho)],
+                 [], h, gravity=(0.0, 0.0, 0.0), contact_margin=0.5 * edge, spacing=edge)
+
+
+def cube_drop(m: int = 6, edge: float = 0.1, model: int = MODEL_ARAP, E: float = 1e5,
+              nu: float = 0.4, rho: float = 1000.0, height: float = 0.2, mu: float = 0.5,
+              seed: int = 0, h: float = 1.0 / 60.0, n_frames: int = 100,
+              tilt_deg: float = 0.0) -> Scene:
+    """An m^3-vertex cube (edge ``edge``) with a seeded random rotation, its lowest point
+    ``height`` above a ground plane through the origin tilted by ``tilt_deg`` about y."""
+    rng = np.random.default_rng(seed)
+    sp = edge / (m - 1)
+    X, tets = lattice_tets(m, m, m, sp, origin=(-edge / 2, -edge / 2, -edge / 2))
+    R = random_rotation(rng)
+    q0 = X @ R.T
+    n_plane = _rot_y(tilt_deg) @ np.array([0.0, 0.0, 1.0])
+    lift = height - (q0 @ n_plane).min()
+    q0 = q0 + lift * n_plane
+    obst = [Obstacle(OBST_PLANE, (0.0, 0.0, 0.0), tuple(n_plane), mu=mu)]
+    return Scene(f"cube{m}", X, tets, np.zeros(len(tets), np.int32), [Material(model, E, nu, rho)],
+                 obst, h, q0=q0, contact_margin=0.5 * sp, n_frames=n_frames, spacing=sp)
+
+
+def slope_box(mu: float, theta_deg: float = 10.0, m: int = 4, edge: float = 0.1,
+              E: float = 1e8, nu: float = 0.3, rho: float = 1000.0, model: int = MODEL_ARAP,
+              h: float = 1.0 / 60.0, n_iters: int = 10, n_cr: int = 24) -> Scene:
+    """A stiff m^3-vertex box whose bottom face rests on a plane inclined by ``theta_deg``
+    (about the y axis). Gravity is -z. The analytic stick/slip threshold is tan(theta)."""
+    sp = edge / (m - 1)
+    X, tets = lattice_tets(m, m, m, sp, origin=(-edge / 2, -edge / 2, 0.0))
+    R = _rot_y(theta_deg)
+    q0 = X @ R.T
+    n_plane = R @ np.array([0.0, 0.0, 1.0])
+    obst = [Obstacle(OBST_PLANE, (0.0, 0.0, 0.0), tuple(n_plane), mu=mu)]
+    return Scene("slope_box", X, tets, np.zeros(len(tets), np.int32),
+                 [Material(model, E, nu, rho)], obst, h, q0=q0, contact_margin=0.5 * sp,
+                 n_iters=n_iters, n_cr=n_cr, spacing=sp)
+
+
+def star_pull(n_side: int = 42, layers: int = 27, spacing: float = 0.01, seed: int = 0,
+              E: float = 1e6, nu: float = 0.45, rho: float = 1000.0, model: int = MODEL_SNH,
+              mu: float = 0.3, pull_speed: float = 0.5, cap_depth: float = 0.05,
+              h: float = 1.0 / 60.0, n_frames: int = 300, start_gap: float = 0.3,
+              inner_ratio: float = 0.5) -> Scene:
+    """Extruded five-point star pulled through a seeded 4 x 4 array of fixed cylinders.
+
+    Cross-section: a star polygon (inner/outer radius ratio ``inner_ratio``) inscribed in
+    an n_side x n_side vertex lattice; extruded along z over ``layers`` vertex layers.
+    The vertices within ``cap_depth`` of the leading (+x) tip are pinned and move at
+    ``pull_speed`` along +x. Cylinders have axes along z; four columns at an x pitch of
+    0.5 m starting ``start_gap`` ahead of the tip; y centres at -0.45, -0.15, 0.15, 0.45 m
+    plus U(-0.03, 0.03); radii U(0.02, 0.06) m. No gravity.
+    """
+    rng = np.random.default_rng(seed)
+    r_out = (n_side - 1) * spacing / 2.0
+    poly = _star_polygon(r_out, inner_ratio * r_out)
+    c0 = (n_side - 1) / 2.0
+
+    def keep(i, j, k):
+        return _inside_polygon((i + 0.5 - c0) * spacing, (j + 0.5 - c0) * spacing, poly)
+
+    X, tets = lattice_tets(n_side, n_side, layers, spacing, keep=keep,
+                           origin=(-c0 * spacing, -c0 * spacing, 0.0))
+    xmax = X[:, 0].max()
+    pinned = np.nonzero(X[:, 0] >= xmax - cap_depth - 1e-9)[0].astype(np.int32)
+    zc = 0.5 * (layers - 1) * spacing
+    obst = []
+    for col in range(4):
+        x = xmax + start_gap + 0.5 * col
+        for yc in (-0.45, -0.15, 0.15, 0.45):
+            y = yc + rng.uniform(-0.03, 0.03)
+            r = rng.uniform(0.02, 0.06)
+            obst.append(Obstacle(OBST_CYLINDER, (x, y, zc), (0.0, 0.0, 1.0), radius=r, mu=mu))
+    return Scene(f"star{n_side}x{layers}", X, tets, np.zeros(len(tets), np.int32),
+                 [Material(model, E, nu, rho)], obst, h, gravity=(0.0, 0.0, 0.0),
+                 pinned=pinned, handle_vel=(pull_speed, 0.0, 0.0),
+                 contact_margin=0.5 * spacing, n_frames=n_frames, spacing=spacing)
+
+
+def batch(n_scenes: int = 64, seed: int = 0, m_lo: int = 8, m_hi: int = 20,
+          h: float = 1.0 / 60.0) -> List[Scene]:
+    """Dozens of independent cubes of uneven size: side m ~ U{m_lo..m_hi} vertices, edge
+    U(0.1, 0.25) m, materials alternating ARAP/co-rotational versus stable Neo-Hookean, E
+    log-uniform in [1e4, 1e7] Pa, nu ~ U(0.3, 0.48), dropped onto planes tilted U(0, 30)
+    degrees with mu ~ U(0.1, 0.8)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for s in range(n_scenes):
+        m = int(rng.integers(m_lo, m_hi + 1))
+        edge = float(rng.uniform(0.1, 0.25))
+        if s % 2 == 0:
+            model = MODEL_ARAP if (s // 2) % 2 == 0 else MODEL_COROT
+        else:
+            model = MODEL_SNH
+        E = float(10 ** rng.uniform(4, 7))
+        nu = float(rng.uniform(0.3, 0.48))
+        tilt = float(rng.uniform(0, 30))
+        mu = float(rng.uniform(0.1, 0.8))
+        sc = cube_drop(m=m, edge=edge, model=model, E=E, nu=nu, height=0.05, mu=mu,
+                       seed=seed * 1000 + s, h=h, tilt_deg=tilt)
+        sc.name = f"batch{s}_m{m}"
+        out.append(sc)
+    return out
+
+
+def perturbed_state(scene: Scene, seed: int, amp: float, vel_amp: float = 0.0):
+    """Seeded random perturbation of the initial state (positions and velocities) of the
+    free vertices, for single-step comparisons from identical states."""
+    rng = np.random.default_rng(seed)
+    q = scene.q0 + amp * rng.standard_normal(scene.q0.shape)
+    v = scene.v0 + vel_amp * rng.standard_normal(scene.v0.shape)
+    if len(scene.pinned):
+        q[scene.pinned] = scene.q0[scene.pinned]
+        v[scene.pinned] = np.asarray(scene.handle_vel)
+    return q, v

@@ -1,0 +1,109 @@
+"""Pins of the oracle's contact layer: geometry, Fischer-Burmeister functions and their
+derivatives (App. B.2), the Coulomb reading of phi_f (App. A.2, Eqs. 43-44), and the
+conjugate-residual solver."""
+import numpy as np
+import pytest
+
+import scenegen as sg
+from oracle import contact as C
+
+
+def test_fb_zero_iff_complementary():
+    rng = np.random.default_rng(0)
+    a = rng.uniform(-2, 2, 4000)
+    b = rng.uniform(-2, 2, 4000)
+    assert np.all(C.fb(a, b)[(a > 0) & (b > 0)] > 0)
+    assert np.all(C.fb(a, b)[(a < 0) | (b < 0)] < 0)
+    z = rng.uniform(0, 2, 100)
+    assert np.abs(C.fb(z, 0 * z)).max() == 0 and np.abs(C.fb(0 * z, z)).max() == 0
+
+
+def test_normal_indicator_and_compliance_are_derivatives():
+    # omega_n = d phi_n / d delta_n and E_n = d phi_n / d lambda_n (Eq. 16)
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        d, lam, r = rng.normal(), rng.normal(), rng.uniform(0.1, 3)
+        phi, om, E = C.normal_terms(d, lam, r)
+        eps = 1e-7
+        dphi_dd = (C.normal_terms(d + eps, lam, r)[0] - C.normal_terms(d - eps, lam, r)[0]) / (2 * eps)
+        dphi_dl = (C.normal_terms(d, lam + eps, r)[0] - C.normal_terms(d, lam - eps, r)[0]) / (2 * eps)
+        assert abs(om - dphi_dd) < 1e-6 and abs(E - dphi_dl) < 1e-6 * max(1, r)
+        assert abs(phi - C.fb(d, r * lam)) < 1e-15
+
+
+def test_friction_reduces_to_coulomb_at_solutions():
+    rng = np.random.default_rng(2)
+    for _ in range(100):
+        lam_n = rng.uniform(0.1, 5)
+        mu = rng.uniform(0.05, 1)
+        r = rng.uniform(0.01, 2)
+        # sliding: lambda_f opposes the velocity at the cone boundary -> phi_f = 0
+        v = rng.normal(size=2)
+        lam_f = -mu * lam_n * v / np.linalg.norm(v)
+        om, E, phi = C.friction_terms(v, lam_f, lam_n, mu, r)
+        assert om == 1.0
+        assert abs(E - np.linalg.norm(v) / np.linalg.norm(lam_f)) < 1e-9 * E
+        assert np.abs(phi).max() < 1e-9 * np.linalg.norm(v)
+        # sticking: zero velocity strictly inside the cone -> E_f = 0, phi_f = 0
+        lam_f2 = rng.uniform(0, 0.9) * mu * lam_n * np.array([np.cos(1.0), np.sin(1.0)])
+        om, E, phi = C.friction_terms(np.zeros(2), lam_f2, lam_n, mu, r)
+        assert E == 0.0 and np.abs(phi).max() == 0.0
+        # inactive contact: phi_f = lambda_f drives friction to zero
+        om, E, phi = C.friction_terms(v, lam_f, -lam_n, mu, r)
+        assert om == 0.0 and E == 1.0 and np.allclose(phi, lam_f)
+
+
+def test_friction_compliance_positive_and_no_fixed_point_outside_cone():
+    rng = np.random.default_rng(3)
+    for _ in range(500):
+        lam_n, mu, r = rng.uniform(0.1, 5), rng.uniform(0.05, 1), rng.uniform(0.01, 2)
+        v = rng.normal(size=2) * rng.choice([0.0, 1e-3, 1.0])
+        lam_f = rng.normal(size=2) * mu * lam_n * rng.uniform(0, 4)
+        om, E, phi = C.friction_terms(v, lam_f, lam_n, mu, r)
+        assert E >= 0.0
+        if np.linalg.norm(lam_f) > mu * lam_n * (1 + 1e-9):
+            assert np.linalg.norm(phi) > 0.0
+
+
+def test_plane_and_cylinder_geometry():
+    pl = sg.Obstacle(sg.OBST_PLANE, (0, 0, 1.0), (0, 0, 1.0))
+    phi, n, p = C.closest_point(pl, np.array([0.3, -0.2, 0.75]))
+    assert abs(phi + 0.25) < 1e-15 and np.allclose(n, [0, 0, 1]) and np.allclose(p, [0.3, -0.2, 1.0])
+    cy = sg.Obstacle(sg.OBST_CYLINDER, (1.0, 0, 0), (0, 0, 1.0), radius=0.5)
+    phi, n, p = C.closest_point(cy, np.array([1.0, 0.3, 7.0]))
+    assert abs(phi + 0.2) < 1e-15 and np.allclose(n, [0, 1, 0]) and np.allclose(p, [1.0, 0.5, 7.0])
+    phi, n, p = C.closest_point(cy, np.array([4.0, 4.0, -1.0]))
+    assert abs(phi - (5.0 - 0.5)) < 1e-14 and np.allclose(n, [0.6, 0.8, 0])
+
+
+def test_tangent_frames_orthonormal_right_handed():
+    rng = np.random.default_rng(4)
+    for _ in range(200):
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        f1, f2 = C.tangent_frame(n)
+        D = np.stack([n, f1, f2])
+        assert np.abs(D @ D.T - np.eye(3)).max() < 1e-14
+        assert abs(np.linalg.det(D) - 1.0) < 1e-14
+
+
+def test_conjugate_residual_exact_in_n_steps_and_monotone():
+    rng = np.random.default_rng(5)
+    n = 12
+    B = rng.normal(size=(n, n))
+    K = B @ B.T + n * np.eye(n)
+    b = rng.normal(size=n)
+    x = C.conjugate_residual(lambda v: K @ v, b, n)
+    assert np.abs(x - np.linalg.solve(K, b)).max() < 1e-10 * np.abs(x).max()
+    res = [np.linalg.norm(b - K @ C.conjugate_residual(lambda v: K @ v, b, k)) for k in range(n)]
+    assert all(res[k + 1] <= res[k] * (1 + 1e-12) for k in range(n - 1))
+
+
+def test_detection_finds_exactly_the_vertices_below_margin():
+    sc = sg.cube_drop(m=4, height=0.004, seed=3)
+    pts = sc.q0
+    cts = C.detect(sc, pts, np.arange(sc.n_verts))
+    below = set(np.nonzero(pts[:, 2] < sc.contact_margin)[0].tolist())
+    assert {c["vertex"] for c in cts} == below
+    for c in cts:
+        assert abs(c["d_n"]) < 1e-15 and np.allclose(c["n"], [0, 0, 1])

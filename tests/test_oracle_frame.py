@@ -1,0 +1,205 @@
+"""Pins of the oracle's whole frame (Alg. 4) against facts that do not depend on it:
+exact invariants of the equations, closed forms, brute-force enumeration of contact
+modes, and the paper's stick-slip experiment (Sec. 7.5)."""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import scenegen as sg
+from oracle import Oracle, OracleOptions
+from oracle.fem import lame
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.mark.parametrize("model", [sg.MODEL_ARAP, sg.MODEL_COROT, sg.MODEL_SNH])
+def test_rest_state_is_a_fixed_point(model):
+    sc = sg.cube_drop(m=4, model=model)
+    sc.gravity = (0.0, 0.0, 0.0)
+    sc.obstacles = []
+    sc.q0 = sc.X.copy()
+    o = Oracle(sc)
+    q, v, _ = o.frame(sc.q0, np.zeros_like(sc.q0))
+    assert np.abs(q - sc.X).max() < 1e-14
+    assert np.abs(v).max() < 1e-12
+
+
+@pytest.mark.parametrize("model", [sg.MODEL_ARAP, sg.MODEL_COROT, sg.MODEL_SNH])
+def test_free_fall_of_a_rigidly_moving_body_is_exact(model):
+    # an undeformed body (rotated rest shape) with uniform velocity: p_i = R for every
+    # element, so q = s~ exactly and the velocity gains exactly h g
+    sc = sg.cube_drop(m=4, model=model, height=5.0, seed=4)
+    o = Oracle(sc)
+    v0 = np.tile([0.3, -0.2, 0.1], (sc.n_verts, 1))
+    q, v, info = o.frame(sc.q0, v0)
+    assert len(info["contacts"]) == 0
+    expect = sc.q0 + sc.h * v0 + sc.h ** 2 * np.asarray(sc.gravity)
+    assert np.abs(q - expect).max() < 1e-12
+    assert np.abs(v - (v0 + sc.h * np.asarray(sc.gravity))).max() < 1e-9
+
+
+@pytest.mark.parametrize("model", [sg.MODEL_ARAP, sg.MODEL_COROT, sg.MODEL_SNH])
+def test_linear_momentum_conserved_without_contact(model):
+    sc = sg.cube_drop(m=4, model=model, E=3e4)
+    sc.gravity = (0.0, 0.0, 0.0)
+    sc.obstacles = []
+    q0, v0 = sg.perturbed_state(sc, seed=1, amp=2e-3, vel_amp=0.5)
+    o = Oracle(sc)
+    q, v, _ = o.frame(q0, v0)
+    m = o.fem.mass[:, None]
+    P0 = (m * v0).sum(0)
+    P1 = (m * v).sum(0)
+    assert np.abs(P1 - P0).max() < 1e-11 * (m * np.abs(v0)).sum()
+    assert np.abs(v - v0).max() > 1e-3          # the body did deform
+
+
+def test_single_tetrahedron_closed_form():
+    # regular tet, ARAP, at rest velocity, stretched along x: F = diag(s, 1, 1) has p = I,
+    # so every iteration returns X + m / (m + h^2 w kappa) u0 with kappa = 2 / e^2 for the
+    # affine mode u0, m = rho V / 4 and w = 2 mu V.
+    e, E, nu, rho = 0.1, 1e5, 0.4, 1000.0
+    sc = sg.single_tet(edge=e, E=E, nu=nu, rho=rho)
+    o = Oracle(sc)
+    B = np.diag([0.05, 0.0, 0.0])
+    u0 = sc.X @ B.T
+    q, _, _ = o.frame(sc.X + u0, np.zeros_like(sc.X), OracleOptions(n_iters=3))
+    V = e ** 3 / (6 * math.sqrt(2))
+    mu, _ = lame(E, nu)
+    m, w, kappa = rho * V / 4, 2 * mu * V, 2 / e ** 2
+    expect = sc.X + m / (m + sc.h ** 2 * w * kappa) * u0
+    assert np.abs(q - expect).max() < 1e-14
+
+
+def test_momentum_balance_with_contact():
+    # sum_v m_v (q_v - s~_v) = h^2 sum_j D_j^T Omega_j lambda_j for the last iterate
+    sc = sg.cube_drop(m=4, height=0.001, seed=2, mu=0.4)
+    o = Oracle(sc)
+    q, v = sc.q0.copy(), sc.v0.copy()
+    for _ in range(3):
+        q_prev = q
+        q, v, info = o.frame(q, v)
+    assert len(info["contacts"]) > 0
+    m = o.fem.mass[:, None]
+    lhs = (m * (q - info["s_tilde"])).sum(0)
+    rhs = np.zeros(3)
+    for j, ct in enumerate(info["contacts"]):
+        D = np.stack([ct["n"], ct["f1"], ct["f2"]])
+        rhs += D.T @ (info["omega_last"][j] * info["lam"][j])
+    assert np.abs(lhs - sc.h ** 2 * rhs).max() < 1e-12 * (m.sum() * 1e-2)
+
+
+def _resting_cube(m=3, mu=0.5, tilt=0.0, E=1e5):
+    sc = sg.cube_drop(m=m, mu=mu, E=E, tilt_deg=tilt)
+    R = np.array([[math.cos(math.radians(tilt)), 0, math.sin(math.radians(tilt))], [0, 1, 0],
+                  [-math.sin(math.radians(tilt)), 0, math.cos(math.radians(tilt))]])
+    X = sc.X - sc.X.min(0) * np.array([0, 0, 1.0])
+    sc.q0 = X @ R.T
+    return sc
+
+
+def test_static_equilibrium_normal_forces_carry_the_weight():
+    sc = _resting_cube()
+    o = Oracle(sc)
+    q, v = sc.q0.copy(), sc.v0.copy()
+    for _ in range(40):
+        q, v, info = o.frame(q, v, OracleOptions(n_iters=20))
+    W = o.fem.mass.sum() * 9.81
+    ln = info["lam"][:, 0].sum()
+    assert abs(ln - W) < 1e-6 * W
+    assert np.abs(v).max() < 1e-6
+
+
+def test_converged_solution_satisfies_signorini_coulomb():
+    # sliding on a 20 degree incline with mu = 0.2 < tan 20: the converged frame satisfies
+    # Eq. 4 at every contact
+    sc = _resting_cube(m=3, mu=0.2, tilt=20.0)
+    o = Oracle(sc)
+    q, v = sc.q0.copy(), sc.v0.copy()
+    for _ in range(4):
+        q, v, info = o.frame(q, v, OracleOptions(n_iters=150, exact_constraint_solve=True))
+    lam, cs = info["lam"], info["final_state"]
+    scale_l = np.abs(lam[:, 0]).max()
+    eps_d = 1e-9
+    assert np.all(lam[:, 0] >= -1e-9 * scale_l)
+    assert np.all(cs["delta_n"] >= -eps_d)
+    assert np.all(np.abs(lam[:, 0] * cs["delta_n"]) <= 1e-9 * scale_l)
+    lf = np.linalg.norm(lam[:, 1:], axis=1)
+    mus = np.array([c["mu"] for c in info["contacts"]])
+    assert np.all(lf <= mus * lam[:, 0] + 1e-9 * scale_l)
+    for j in range(len(lam)):
+        vf = cs["vel_f"][j]
+        if np.linalg.norm(vf) > 1e-6:
+            cosang = -(vf @ lam[j, 1:]) / (np.linalg.norm(vf) * lf[j])
+            assert cosang > 1 - 1e-6
+            assert abs(lf[j] - mus[j] * lam[j, 0]) < 1e-7 * scale_l
+        if lam[j, 0] <= 1e-12 * scale_l:
+            assert lf[j] <= 1e-9 * scale_l
+
+
+def test_frictionless_contact_matches_brute_force_enumeration():
+    # with mu = 0 and the projections frozen at the converged state, the constrained global
+    # step is a strictly convex QP: min 1/2 q^T A q - b^T q  s.t.  H_n q >= d_n.
+    # Enumerate all active sets, keep the one meeting the KKT conditions, compare.
+    sc = sg.cube_drop(m=3, mu=0.0, height=-0.004, seed=6)
+    o = Oracle(sc)
+    opts = OracleOptions(n_iters=300, exact_constraint_solve=True)
+    q, v, info = o.frame(sc.q0, sc.v0, opts)
+    cts = info["contacts"]
+    c = len(cts)
+    assert 2 <= c <= 9
+    f = o.fem
+    fv = f.free_verts
+    p = o.local_step(q)
+    b = f.assemble_rhs(info["s_tilde"], p, o.pinned_positions(sc.q0))
+    Hn = info["H"][0::3]
+    dn = np.array([ct["d_n"] for ct in cts])
+    A = f.A_ff.toarray()
+    h2 = sc.h ** 2
+    found = []
+    for act in itertools.product([0, 1], repeat=c):
+        S = [j for j in range(c) if act[j]]
+        K = np.zeros((len(b) + len(S),) * 2)
+        K[:len(b), :len(b)] = A
+        K[:len(b), len(b):] = -h2 * Hn[S].T
+        K[len(b):, :len(b)] = Hn[S]
+        rhs = np.concatenate([b, dn[S]])
+        sol = np.linalg.solve(K, rhs)
+        qq, ll = sol[:len(b)], np.zeros(c)
+        ll[S] = sol[len(b):]
+        gap = Hn @ qq - dn
+        if np.all(ll >= -1e-12) and np.all(gap >= -1e-12):
+            found.append((qq, ll))
+    assert len(found) == 1
+    qq, ll = found[0]
+    assert np.abs(q[fv].reshape(-1) - qq).max() < 1e-8 * sc.bbox_diagonal
+    assert np.abs(info["lam"][:, 0] - ll).max() < 1e-7 * max(ll.max(), 1e-12)
+    assert np.abs(info["lam"][:, 1:]).max() == 0.0
+
+
+def test_stick_slip_threshold_matches_paper():
+    """The paper's stick-sliding test: a stiff box on a 10 degree slope sticks above
+    mu* = tan 10 deg = 0.17632698 and slides below it. We bracket mu* at +-0.005 with 30
+    local-global and 24 CR iterations per frame, and check the sliding acceleration against
+    g (sin theta - mu cos theta)."""
+    gold = json.load(open(os.path.join(GOLDEN, "stick_slip.json")))
+    th = math.radians(gold["theta_deg"])
+    assert abs(math.tan(th) - gold["mu_star"]) < 1e-8
+    down = np.array([math.cos(th), 0.0, -math.sin(th)])
+    T = 0.5
+    speeds = {}
+    for dmu in (-0.005, +0.005):
+        mu = gold["mu_star"] + dmu
+        sc = sg.slope_box(mu=mu, theta_deg=gold["theta_deg"], rho=gold["density"],
+                          E=gold["youngs_modulus"])
+        o = Oracle(sc)
+        q, v = sc.q0.copy(), sc.v0.copy()
+        for _ in range(int(round(T / sc.h))):
+            q, v, _ = o.frame(q, v, OracleOptions(n_iters=30, n_cr=gold["paper_cr_iterations"]))
+        speeds[dmu] = float(v.mean(0) @ down)
+    a_expect = 9.81 * (math.sin(th) - (gold["mu_star"] - 0.005) * math.cos(th))
+    assert abs(speeds[-0.005] / T - a_expect) < 0.02 * a_expect
+    assert abs(speeds[+0.005]) < 1e-4
