@@ -1,0 +1,216 @@
+/*
+ * silg.h - C ABI of the sparse-inverse local-global simulator (B300, sm_103a).
+ *
+ * Implements the per-iteration local-global solve of Zeng et al., "Fast But Accurate: A
+ * Real-Time Hyperelastic Simulator with Robust Frictional Contact":
+ *   - implicit Euler as minimisation (Sec. 3.1, Eq. 1), solved by local-global
+ *     iterations (Sec. 3.3, Eqs. 5-6, Alg. 1);
+ *   - the global step applied as products with the sparse inverse S of the Cholesky
+ *     factor, A^-1 = S^T S (Sec. 4.2, Theorem 1, Eqs. 7-8, Alg. 2);
+ *   - frictional contact by a Fischer-Burmeister non-smooth Newton step inside every
+ *     iteration (Sec. 5.2, Eqs. 14-23; App. B.2), with split non-smooth indicators and the
+ *     Delassus operator W = H S^T S H^T formed once per frame (Sec. 5.3, Eqs. 24-27) and
+ *     its diagonal as complementarity preconditioner (Sec. 5.4, Eq. 28), in the order of
+ *     Alg. 4 (Sec. 6).
+ *
+ * Conventions
+ *   - Every function returns an int status: SIM_OK (0) or a negative SIM_E* code; no
+ *     exception crosses the ABI. sim_strerror() names a code.
+ *   - Host inputs are FP64 / int32, always copied; the library never keeps a caller
+ *     pointer. Output buffers are caller-owned host memory unless a parameter says
+ *     "device".
+ *   - Vertex arrays are n_verts x 3, row-major (x, y, z per vertex), in the caller's
+ *     vertex numbering.
+ *   - A handle owns all its device memory and one CUDA stream (or uses the caller's
+ *     stream, see sim_options.cuda_stream). A handle is not thread-safe.
+ *   - GPU work is asynchronous: sim_step() only enqueues; errors raised on the device
+ *     (capacity overflow, non-finite state, bounded-wait timeout) are reported by the next
+ *     call that synchronises (sim_synchronize, sim_get_state, sim_get_stats, ...).
+ */
+#ifndef SILG_H
+#define SILG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------ */
+#define SIM_OK          0
+#define SIM_EINVAL     (-1)  /* invalid argument (bad index, size, material, geometry)   */
+#define SIM_ENOMEM     (-2)  /* host or device allocation failed                        */
+#define SIM_ENOTSPD    (-3)  /* the system matrix A is not positive definite             */
+#define SIM_ECUDA      (-4)  /* a CUDA runtime call failed (no device, launch error)     */
+#define SIM_ECAPACITY  (-5)  /* more contacts in a frame than sim_options.contact_capacity */
+#define SIM_ETIMEOUT   (-6)  /* a bounded device-side wait gave up                       */
+#define SIM_ENONFINITE (-7)  /* a NaN or Inf appeared in the state                       */
+#define SIM_ENOTSUP    (-8)  /* option combination not supported                        */
+
+/* ---- enumerations ------------------------------------------------------------------ */
+enum { SIM_MODEL_ARAP = 0,      /* PD as-rigid-as-possible: SO(3) indicator (Eq. 5)      */
+       SIM_MODEL_COROT = 1,     /* co-rotational: mu||F-R||^2 + lam/2 tr^2(R^T F - I)     */
+       SIM_MODEL_SNH = 2 };     /* stable Neo-Hookean (Smith, de Goes, Kim 2018)           */
+enum { SIM_OBST_PLANE = 0,      /* p: point on plane, axis: unit outward normal           */
+       SIM_OBST_CYLINDER = 1 }; /* infinite cylinder: p on axis, axis unit, radius        */
+enum { SIM_S_FP32 = 0,          /* S stored in FP32                                       */
+       SIM_S_BF16 = 1 };        /* S stored in BF16, FP32 accumulation                     */
+
+/* ---- inputs ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t n_verts;
+  int32_t n_tets;
+  const double* rest_pos;      /* n_verts x 3, rest positions X                           */
+  const int32_t* tets;         /* n_tets x 4 vertex ids, positively oriented at rest      */
+  const int32_t* tet_material; /* n_tets material indices, or NULL for material 0         */
+  const int32_t* pinned;       /* n_pinned vertex ids (Dirichlet), or NULL                */
+  int32_t n_pinned;
+  double handle_vel[3];        /* velocity of every pinned vertex (m/s)                   */
+} sim_mesh;
+
+typedef struct {
+  int32_t model;               /* SIM_MODEL_*                                              */
+  double E, nu, rho;           /* Young's modulus (Pa), Poisson ratio, density (kg/m^3)   */
+} sim_material;
+
+typedef struct {
+  int32_t kind;                /* SIM_OBST_*                                               */
+  double p[3];
+  double axis[3];
+  double radius;
+  double mu;                   /* Coulomb friction coefficient                             */
+  double vel[3];               /* surface velocity of the obstacle (0 for fixed)          */
+} sim_obstacle;
+
+typedef struct {
+  int32_t n_iters;             /* local-global iterations per frame (default 5)           */
+  int32_t n_cr_iters;          /* conjugate-residual iterations per solve (default 10)    */
+  int32_t s_precision;         /* SIM_S_FP32 (default) or SIM_S_BF16                      */
+  int32_t refine;              /* BF16 only: one FP32 residual-correction pass (default 1)*/
+  int32_t contact_capacity;    /* max contacts per frame (default 4096)                   */
+  int32_t device;              /* CUDA device ordinal (default 0)                          */
+  double gravity[3];           /* default (0, 0, -9.81)                                    */
+  double contact_margin;       /* contact when gap < margin; <= 0: half the mean edge     */
+  uint64_t spin_limit;         /* iteration limit of device-side waits (0: default)       */
+  void* cuda_stream;           /* cudaStream_t to run on, or NULL for a private stream    */
+  int32_t n_host_threads;      /* threads for the host precompute (0: all cores)          */
+} sim_options;
+
+/* Per-frame statistics of the most recent sim_step. */
+#define SIM_MAX_RESIDUALS 64
+typedef struct {
+  int64_t frame;               /* frames advanced since creation or sim_set_state        */
+  int32_t n_contacts;          /* contacts detected in the last frame                    */
+  int32_t n_contact_verts;     /* distinct contact vertices (order of W~)                */
+  int32_t n_iters;             /* iterations run in the last frame                       */
+  int32_t n_residuals;         /* n_iters + 1 residuals follow                           */
+  double residual[SIM_MAX_RESIDUALS]; /* R_k = max_j max(|min(dn, r_n ln)|, h|phi_f|)/L */
+  double max_penetration;      /* max over contacts of -delta_n at the end of the frame  */
+  int32_t kernels_per_frame;   /* kernel launches in one frame of the last n_iters        */
+} sim_stats;
+
+/* Phases of a frame timed by event nodes inside the frame's CUDA graph (milliseconds,
+ * summed over the iterations of the most recent frame); the paper reports the same split
+ * (Tab. 3: Schur., Local, Global, Assem., Cst. Solve, Corr.). */
+enum { SIM_PHASE_COLLIDE = 0,   /* prediction and collision detection (App. A.1)         */
+       SIM_PHASE_DELASSUS = 1,  /* W~ = Y^T Y and preconditioner (Eqs. 27-28)            */
+       SIM_PHASE_LOCAL = 2,     /* local step per tetrahedron (Eq. 5)                     */
+       SIM_PHASE_ASSEMBLE = 3,  /* FB evaluation and right-hand side (Eq. 19)            */
+       SIM_PHASE_SPMV1 = 4,     /* z = S g (first profile product, Eq. 8)                 */
+       SIM_PHASE_SOLVE = 5,     /* J A^-1 g, conjugate residual, S J^T dlambda (Alg. 4)   */
+       SIM_PHASE_SPMV2 = 6,     /* q = S^T y (second profile product, Eq. 23b)            */
+       SIM_PHASE_INTEGRATE = 7, /* final residual and integration                         */
+       SIM_NUM_PHASES = 8 };
+
+/* Sizes of the precomputed structure (Theorem 1 profile of S). */
+typedef struct {
+  int32_t n_verts, n_free, n_tets;
+  int64_t nnz_A;               /* non-zeros of the per-vertex matrix A~ (A = A~ (x) I3)   */
+  int64_t nnz_L;               /* non-zeros of its Cholesky factor                       */
+  int64_t nnz_S;               /* entries of S~ = L~^-1 in its row profile              */
+  int64_t stored_S;            /* stored entries including alignment padding            */
+  int32_t etree_max_depth;
+  double etree_mean_depth;
+  int32_t n_roots;
+  double precompute_seconds;
+} sim_plan_info;
+
+typedef struct sim_s sim_t;
+typedef struct sim_plan_s sim_plan_t;
+
+const char* sim_strerror(int status);
+void sim_default_options(sim_options* opts);
+
+/*
+ * Host-only precompute (no GPU needed). Builds per-element data, lumped masses, the
+ * per-vertex system matrix A~ = M~ + h^2 sum_i w_i G~_i^T G~_i over the free vertices
+ * (Eq. 6; A = A~ (x) I3 because G acts identically on x, y, z), a nested-dissection
+ * ordering P, the elimination tree in postorder, the FP64 Cholesky factor
+ * P A~ P^T = L~ L~^T and S~ = L~^-1 P stored as a row profile: row i covers exactly the
+ * columns of its elimination subtree, the contiguous range [fd(i), i] (Theorem 1).
+ * Errors: SIM_EINVAL (bad mesh), SIM_ENOTSPD, SIM_ENOMEM.
+ */
+int sim_plan_create(const sim_mesh* mesh, const sim_material* mats, int32_t n_mat, double h,
+                    const sim_options* opts, sim_plan_t** out);
+void sim_plan_destroy(sim_plan_t* plan);
+int sim_plan_get_info(const sim_plan_t* plan, sim_plan_info* info);
+/* order[k] = caller vertex id of internal free row k (n_free entries); parent[k] = etree
+ * parent of row k (-1 for roots); first_desc[k] = fd(k). Any pointer may be NULL. */
+int sim_plan_get_ordering(const sim_plan_t* plan, int32_t* order, int32_t* parent,
+                          int32_t* first_desc);
+/* x = A^-1 b on the host in FP64 through the two profile products x = S^T (S b) (Eq. 8).
+ * b, x: n_verts x 3 in caller numbering; pinned rows of b are ignored, of x set to 0. */
+int sim_plan_apply_inverse_host(const sim_plan_t* plan, const double* b, double* x);
+
+/*
+ * Create a simulator on one GPU: runs the host precompute, uploads everything, and
+ * prepares the per-frame CUDA graph. opts may be NULL (defaults). Positions start at the
+ * rest shape with zero velocity (sim_set_state to change). Errors: SIM_EINVAL,
+ * SIM_ENOTSPD, SIM_ENOMEM, SIM_ECUDA.
+ */
+int sim_create(const sim_mesh* mesh, const sim_material* mats, int32_t n_mat,
+               const sim_obstacle* obstacles, int32_t n_obs, double h,
+               const sim_options* opts, sim_t** out);
+void sim_destroy(sim_t* sim);
+
+/* One frame of Alg. 4 with n_iters local-global iterations (n_iters <= 0: the option's
+ * value). Asynchronous on the handle's stream. */
+int sim_step(sim_t* sim, int32_t n_iters);
+/* Wait for the handle's stream; returns the first device-side error, if any. */
+int sim_synchronize(sim_t* sim);
+
+/* Copy the state out (synchronises). q, v: n_verts x 3 (NULL to skip). */
+int sim_get_state(sim_t* sim, double* q, double* v);
+/* Replace the state (positions, velocities; pinned vertices included). Resets the frame
+ * counter. */
+int sim_set_state(sim_t* sim, const double* q, const double* v);
+int sim_get_stats(sim_t* sim, sim_stats* stats);
+/* Contacts of the last frame, ordered by (caller vertex id, obstacle index): vertex,
+ * obstacle, lambda (n, f1, f2 components, N), frame rows (n, f1, f2: 9 doubles). Arrays of
+ * `capacity` entries; *n_out receives the count (which may exceed capacity). */
+int sim_get_contacts(sim_t* sim, int32_t capacity, int32_t* vertex, int32_t* obstacle,
+                     double* lambda, double* frame, int32_t* n_out);
+
+/* Sizes of the simulator's precomputed structure (same fields as sim_plan_get_info). */
+int sim_get_plan_info(const sim_t* sim, sim_plan_info* info);
+
+/* Per-phase device time of the most recent frame (synchronises). ms: SIM_NUM_PHASES. */
+int sim_get_phase_times(sim_t* sim, double* ms);
+
+/* ---- component entry points (parity and profiling) ------------------------------- */
+/* x = A^-1 b with the device profile products (Eq. 8). b, x as in the host variant. */
+int sim_apply_inverse(sim_t* sim, const double* b, double* x);
+/* Local step (Eq. 5) on the device for positions q (n_verts x 3): p (n_tets x 9,
+ * row-major F-shaped projections, caller tet order). */
+int sim_local_project(sim_t* sim, const double* q, double* p);
+/* Delassus operator of the last frame over distinct contact vertices: W~ (n_cv x n_cv,
+ * row-major) with W_jk = W~(v_j, v_k) D_j D_k^T (Eq. 27); cv_vertex receives the caller
+ * vertex ids. Arrays hold `capacity` vertices; *n_out receives n_cv. */
+int sim_get_delassus(sim_t* sim, int32_t capacity, double* Wtilde, int32_t* cv_vertex,
+                     int32_t* n_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SILG_H */

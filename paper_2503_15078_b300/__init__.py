@@ -1,0 +1,265 @@
+"""B300-native sparse-inverse local-global simulator with robust frictional contact.
+
+Python binding over the C ABI of ``libsilg.so`` (include/silg.h). The binding only
+marshals arguments: every step of the solve runs in the library's CUDA kernels (sm_103a)
+or, for the one-time precompute, its C++ host code. PyTorch supplies the CUDA stream when
+it is available; nothing here computes the method.
+
+    from paper_2503_15078_b300 import Simulator
+    sim = Simulator(scene)          # any object with the scene fields (see ``_mesh_args``)
+    sim.step()                      # one frame (Alg. 4)
+    q, v = sim.state()
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _abi
+
+_lib = None
+
+
+def lib():
+    """The loaded shared library (raises ImportError if it was not built)."""
+    global _lib
+    if _lib is None:
+        _lib = _abi.load()
+    return _lib
+
+
+class SimError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = lib().sim_strerror(status).decode()
+        super().__init__(f"{where}: {_abi.STATUS.get(status, status)} ({msg})")
+
+
+def _check(status, where):
+    if status != _abi.SIM_OK:
+        raise SimError(status, where)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _iptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def _mesh_args(scene):
+    """Marshal a scene (X, tets, tet_material, materials, pinned, handle_vel, obstacles)
+    into the ABI structs; the returned tuple keeps the numpy buffers alive."""
+    X = np.ascontiguousarray(scene.X, dtype=np.float64)
+    tets = np.ascontiguousarray(scene.tets, dtype=np.int32)
+    tm = np.ascontiguousarray(scene.tet_material, dtype=np.int32)
+    pin = np.ascontiguousarray(scene.pinned, dtype=np.int32)
+    mesh = _abi.SimMesh()
+    mesh.n_verts = X.shape[0]
+    mesh.n_tets = tets.shape[0]
+    mesh.rest_pos = _dptr(X)
+    mesh.tets = _iptr(tets)
+    mesh.tet_material = _iptr(tm)
+    mesh.pinned = _iptr(pin) if len(pin) else None
+    mesh.n_pinned = len(pin)
+    for r in range(3):
+        mesh.handle_vel[r] = float(scene.handle_vel[r])
+    mats = (_abi.SimMaterial * len(scene.materials))()
+    for i, m in enumerate(scene.materials):
+        mats[i].model, mats[i].E, mats[i].nu, mats[i].rho = int(m.model), m.E, m.nu, m.rho
+    obs = (_abi.SimObstacle * max(1, len(scene.obstacles)))()
+    for i, o in enumerate(scene.obstacles):
+        obs[i].kind = int(o.kind)
+        for r in range(3):
+            obs[i].p[r] = float(o.p[r])
+            obs[i].axis[r] = float(o.axis[r])
+            obs[i].vel[r] = float(o.vel[r])
+        obs[i].radius = float(o.radius)
+        obs[i].mu = float(o.mu)
+    return mesh, mats, obs, (X, tets, tm, pin)
+
+
+def default_options():
+    o = _abi.SimOptions()
+    lib().sim_default_options(C.byref(o))
+    return o
+
+
+def _options(scene=None, **kw):
+    o = default_options()
+    if scene is not None:
+        o.n_iters = int(getattr(scene, "n_iters", o.n_iters))
+        o.n_cr_iters = int(getattr(scene, "n_cr", o.n_cr_iters))
+        g = getattr(scene, "gravity", None)
+        if g is not None:
+            for r in range(3):
+                o.gravity[r] = float(g[r])
+        o.contact_margin = float(getattr(scene, "contact_margin", 0.0))
+    for k, v in kw.items():
+        if k == "gravity":
+            for r in range(3):
+                o.gravity[r] = float(v[r])
+        else:
+            setattr(o, k, v)
+    return o
+
+
+class Plan:
+    """Host-only precompute (ordering, elimination tree, Cholesky, S~ = L~^-1 P)."""
+
+    def __init__(self, scene, h=None, **opts):
+        mesh, mats, _obs, self._keep = _mesh_args(scene)
+        o = _options(scene, **opts)
+        h = float(scene.h if h is None else h)
+        handle = C.c_void_p()
+        _check(lib().sim_plan_create(C.byref(mesh), mats, len(scene.materials), h, C.byref(o),
+                                     C.byref(handle)), "sim_plan_create")
+        self._h = handle
+        self.n_verts = mesh.n_verts
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().sim_plan_destroy(h)
+            self._h = None
+
+    def info(self):
+        i = _abi.SimPlanInfo()
+        _check(lib().sim_plan_get_info(self._h, C.byref(i)), "sim_plan_get_info")
+        return {f: getattr(i, f) for f, _ in i._fields_}
+
+    def ordering(self):
+        nf = self.info()["n_free"]
+        order = np.zeros(nf, np.int32)
+        parent = np.zeros(nf, np.int32)
+        fd = np.zeros(nf, np.int32)
+        _check(lib().sim_plan_get_ordering(self._h, _iptr(order), _iptr(parent), _iptr(fd)),
+               "sim_plan_get_ordering")
+        return order, parent, fd
+
+    def apply_inverse_host(self, b):
+        b = np.ascontiguousarray(b, dtype=np.float64).reshape(self.n_verts, 3)
+        x = np.zeros_like(b)
+        _check(lib().sim_plan_apply_inverse_host(self._h, _dptr(b), _dptr(x)),
+               "sim_plan_apply_inverse_host")
+        return x
+
+
+def _torch_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return None
+
+
+class Simulator:
+    """One scene on one GPU. Every method is a thin call into the C ABI."""
+
+    def __init__(self, scene, use_torch_stream=True, **opts):
+        mesh, mats, obs, self._keep = _mesh_args(scene)
+        o = _options(scene, **opts)
+        if use_torch_stream and "cuda_stream" not in opts:
+            s = _torch_stream()
+            if s is not None:
+                o.cuda_stream = s
+        handle = C.c_void_p()
+        _check(lib().sim_create(C.byref(mesh), mats, len(scene.materials), obs,
+                                len(scene.obstacles), float(scene.h), C.byref(o),
+                                C.byref(handle)), "sim_create")
+        self._h = handle
+        self.n_verts = mesh.n_verts
+        self.n_tets = mesh.n_tets
+        self.options = o
+        q0 = getattr(scene, "q0", None)
+        v0 = getattr(scene, "v0", None)
+        if q0 is not None:
+            self.set_state(q0, v0 if v0 is not None else np.zeros_like(q0))
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().sim_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def step(self, n_iters=0, n_frames=1):
+        for _ in range(n_frames):
+            _check(lib().sim_step(self._h, int(n_iters)), "sim_step")
+
+    def synchronize(self):
+        _check(lib().sim_synchronize(self._h), "sim_synchronize")
+
+    def state(self):
+        q = np.zeros((self.n_verts, 3))
+        v = np.zeros((self.n_verts, 3))
+        _check(lib().sim_get_state(self._h, _dptr(q), _dptr(v)), "sim_get_state")
+        return q, v
+
+    def set_state(self, q, v):
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        _check(lib().sim_set_state(self._h, _dptr(q), _dptr(v)), "sim_set_state")
+
+    def stats(self):
+        s = _abi.SimStats()
+        _check(lib().sim_get_stats(self._h, C.byref(s)), "sim_get_stats")
+        d = {f: getattr(s, f) for f, _ in s._fields_ if f != "residual"}
+        d["residuals"] = [s.residual[k] for k in range(min(s.n_residuals, _abi.SIM_MAX_RESIDUALS))]
+        return d
+
+    def plan_info(self):
+        i = _abi.SimPlanInfo()
+        _check(lib().sim_get_plan_info(self._h, C.byref(i)), "sim_get_plan_info")
+        return {f: getattr(i, f) for f, _ in i._fields_}
+
+    def phase_times(self):
+        """Device milliseconds per phase of the most recent frame (event nodes in its graph)."""
+        ms = np.zeros(_abi.SIM_NUM_PHASES)
+        _check(lib().sim_get_phase_times(self._h, _dptr(ms)), "sim_get_phase_times")
+        return dict(zip(_abi.PHASES, ms.tolist()))
+
+    def contacts(self):
+        n = C.c_int32()
+        _check(lib().sim_get_contacts(self._h, 0, None, None, None, None, C.byref(n)),
+               "sim_get_contacts")
+        c = n.value
+        vert = np.zeros(max(c, 1), np.int32)
+        obst = np.zeros(max(c, 1), np.int32)
+        lam = np.zeros((max(c, 1), 3))
+        frame = np.zeros((max(c, 1), 3, 3))
+        _check(lib().sim_get_contacts(self._h, c, _iptr(vert), _iptr(obst), _dptr(lam),
+                                      _dptr(frame), C.byref(n)), "sim_get_contacts")
+        return dict(vertex=vert[:c], obstacle=obst[:c], lam=lam[:c], frame=frame[:c])
+
+    def apply_inverse(self, b):
+        b = np.ascontiguousarray(b, dtype=np.float64).reshape(self.n_verts, 3)
+        x = np.zeros_like(b)
+        _check(lib().sim_apply_inverse(self._h, _dptr(b), _dptr(x)), "sim_apply_inverse")
+        return x
+
+    def local_project(self, q):
+        q = np.ascontiguousarray(q, dtype=np.float64).reshape(self.n_verts, 3)
+        p = np.zeros((self.n_tets, 3, 3))
+        _check(lib().sim_local_project(self._h, _dptr(q), _dptr(p)), "sim_local_project")
+        return p
+
+    def delassus(self):
+        n = C.c_int32()
+        _check(lib().sim_get_delassus(self._h, 0, None, None, C.byref(n)), "sim_get_delassus")
+        m = n.value
+        W = np.zeros((max(m, 1), max(m, 1)))
+        cv = np.zeros(max(m, 1), np.int32)
+        _check(lib().sim_get_delassus(self._h, m, _dptr(W), _iptr(cv), C.byref(n)),
+               "sim_get_delassus")
+        return W[:m, :m], cv[:m]

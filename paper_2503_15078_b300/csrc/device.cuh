@@ -1,0 +1,157 @@
+// Device data layout and kernel launchers of the sparse-inverse local-global solver
+// (internal header, sm_103a).
+//
+// Numbering: internal vertex ids put the free vertices first, in the nested-dissection
+// postorder of the elimination tree (rows of S~), then the pinned vertices. Per-vertex
+// state is FP64 AoS (x, y, z); the vectors the profile products read and write are FP32
+// SoA of length n_pad (zero padded).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "plan.hpp"
+
+namespace silg {
+
+constexpr int kWarps = 8;                     // warps per CTA of the profile products
+constexpr int kRowsPerWarp = kRowGroup / kWarps;
+constexpr int kMaxIters = SIM_MAX_RESIDUALS - 1;
+
+// device error word bits
+constexpr int kErrCapacity = 1;
+constexpr int kErrNonFinite = 2;
+constexpr int kErrTimeout = 4;
+constexpr int kErrYCapacity = 8;
+
+// counters[]: per-frame sizes decided on the device
+enum { kCntContacts = 0, kCntCv = 1, kCntU = 2, kCntY = 3, kCntYC = 4, kNumCounters = 8 };
+
+struct ObstDev {
+  int kind;
+  int pad;
+  double p[3], a[3], radius, mu, vel[3];
+};
+
+struct MatDev {
+  int model;
+  float mu, lam, alpha;
+};
+
+struct DevSim {
+  // sizes
+  int n, n_all, n_tets, n_pad, n_obs, n_mat;
+  int cap, cap_y, n_cr;
+  int n_rg, n_ct, n_p1, n_p2;
+  double h, margin, L_ref;
+  double grav[3], handle_vel[3];
+
+  // per vertex (internal numbering, n_all)
+  double* q_t;      // 3 n_all
+  double* v_t;      // 3 n_all
+  double* q_ref;    // 3 n_all: q_t for free vertices, prescribed positions for pinned
+  double* s_tilde;  // 3 n_all
+  float* dq;        // 3 n_all: q^k - q_ref (FP32)
+  double* mass;     // n_all
+  const int* depth; // n (etree depth of each free row)
+  const int* parent;
+  const int* first_desc;
+
+  // per element (caller order, internal vertex ids)
+  const int4* tet_v;
+  const float* tet_dminv;  // [9][n_tets]
+  const float* tet_w;      // PD weight
+  const float* tet_vol;
+  const int* tet_mat;
+  const MatDev* mats;
+  float4* contrib;         // [n_tets * 4]: h^2 w (p - F_ref) g_a
+  const int* inc_ptr;      // n + 1: incidences of free vertex i
+  const int* inc_idx;      // entries 4 t + a
+
+  // S~ profile
+  const float* S;
+  const long long* rowbase;
+  const int* lo;
+  const int* hi;
+  const int4* p1_items;
+  const int* p1_first;
+  const int4* p2_items;
+  const int* p2_first;
+  const int* p2_list;
+  float* p1_part;   // [n_p1][3][kRowGroup]
+  float* p2_part;   // [n_p2][3][kTileW]
+
+  // vectors (SoA, n_pad per component)
+  float* gvec;
+  float* zvec;
+  float* xout;      // 3 n (AoS) result of the transpose pass for apply_inverse
+
+  // obstacles
+  const ObstDev* obst;
+
+  // contacts (capacity cap), sorted by internal vertex then obstacle
+  int* counters;    // kNumCounters
+  int* ct_cnt;      // n: contacts of free vertex i
+  int* ct_off;      // n + 1
+  int* cv_flag;     // n
+  int* cv_off;      // n + 1
+  int* ct_vert;     // cap
+  int* ct_obst;
+  int* ct_cv;       // contact -> contact-vertex index
+  double* ct_D;     // 9 cap: rows n, f1, f2
+  double* ct_dn;    // cap
+  double* ct_df;    // 2 cap
+  double* ct_mu;    // cap
+  double* ct_r;     // 2 cap: r_n, r_f
+  double* ct_lam;   // 3 cap
+  double* ct_force; // 3 cap: D^T (Omega lambda)
+  float* ct_omega;  // 3 cap
+  float* ct_ecal;   // 3 cap: E_n / h^2, E_f / h, E_f / h
+  float* ct_Df;     // 9 cap: D in FP32
+  double* ct_hv;    // 3 cap: h-vector shifted by J q_ref
+  float* ct_rhs;    // 3 cap: Schur right-hand side
+  int* cv_vert;     // cap: internal vertex of contact vertex c (ascending)
+  int* cv_first;    // cap: first contact of contact vertex c
+  int* cv_nct;      // cap
+  float* uvec;      // 3 cap: per contact vertex D^T Omega dlambda
+  float* svec;      // 3 cap: (Y^T z) per contact vertex
+  // ancestors of contact vertices (U) and Y = S~ columns at contact vertices
+  int* u_flag;      // n
+  int* u_off;       // n + 1
+  int* u_list;      // n
+  int* row_clo;     // n: first contact vertex in the subtree of row a (row indexed)
+  int* row_len;     // n: contact vertices in the subtree of row a
+  int* u_clo;       // n: the same, compacted over U
+  int* u_len;       // n
+  int* y_ptr;       // n + 1
+  float* y_val;     // cap_y
+  int* yc_len;      // cap
+  int* yc_ptr;      // cap + 1
+  float* yc_val;    // cap_y
+  int* yc_row;      // cap_y
+  float* wt;        // cap x cap (W~, row-major with ld = n_cv)
+  // diagnostics
+  double* resid;    // kMaxIters + 1
+  double* max_pen;
+  int* err;
+  // local-projection debug output
+  float* p_out;     // 9 n_tets
+};
+
+// ---- launchers (all asynchronous on stream s) ----------------------------------------
+void launch_frame_begin(const DevSim& d, cudaStream_t s);
+void launch_collide(const DevSim& d, cudaStream_t s);
+void launch_delassus(const DevSim& d, cudaStream_t s, int wt_tiles);
+void launch_local(const DevSim& d, cudaStream_t s, bool debug_p);
+void launch_contact_eval(const DevSim& d, cudaStream_t s, int k, bool final_eval);
+void launch_rhs(const DevSim& d, cudaStream_t s);
+void launch_pass1(const DevSim& d, cudaStream_t s);
+void launch_pass2(const DevSim& d, cudaStream_t s, bool to_dq);
+void launch_ytz(const DevSim& d, cudaStream_t s);
+int launch_cr(const DevSim& d, cudaStream_t s, int cluster);
+void launch_yu(const DevSim& d, cudaStream_t s);
+void launch_integrate(const DevSim& d, cudaStream_t s);
+void launch_scan(const int* in, int* out, int n, const int* n_dev, int* total, cudaStream_t s);
+int cr_setup(int* cluster_out, size_t* smem_out);
+
+}  // namespace silg

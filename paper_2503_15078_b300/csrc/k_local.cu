@@ -1,0 +1,375 @@
+// Local step (Eq. 5) per tetrahedron, right-hand-side assembly (Eq. 6), frame start
+// (prediction, Eq. 1) and integration (Alg. 4, last two lines).
+//
+// The local step forms F = D_s D_m^-1 from FP64 positions (edge differences in FP64,
+// rounded once to FP32), computes the signed SVD by one-sided Jacobi rotations
+// (Hestenes 1958; 3x3 columns orthogonalised pairwise, quadratic convergence), and
+// projects the singular values per material:
+//   ARAP          sigma_hat = (1, 1, 1)                     (PD indicator of SO(3))
+//   co-rotational closed form of a linear 3x3 system in sigma
+//   stable NH     Newton in sigma-space with backtracking (<= 20 steps, FP32)
+// It then writes h^2 w_i (p_i - F_ref) g_a for the four corners a, where F_ref is the
+// deformation gradient of the frame's reference state q_ref; the RHS is assembled in
+// displacement form b - A q_ref, so the global solve yields q - q_ref directly.
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+namespace silg {
+namespace {
+
+__device__ __forceinline__ float dot3(const float* a, const float* b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// One-sided Jacobi SVD of a 3x3 matrix (row-major F): F = U diag(s) V^T with U, V
+// rotations and the smallest |s| negative when det F < 0.
+__device__ void svd3(const float* F, float* U, float* s, float* V) {
+  float a[3][3], v[3][3];  // a[col][row], v[col][row]
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      a[c][r] = F[3 * r + c];
+      v[c][r] = (r == c) ? 1.f : 0.f;
+    }
+  for (int sweep = 0; sweep < 10; ++sweep) {
+    bool rotated = false;
+#pragma unroll
+    for (int pr = 0; pr < 3; ++pr) {
+      const int p = pr == 2 ? 1 : 0;
+      const int q = pr == 0 ? 1 : 2;
+      float al = dot3(a[p], a[p]), be = dot3(a[q], a[q]), ga = dot3(a[p], a[q]);
+      if (!(fabsf(ga) > 1e-7f * sqrtf(al * be))) continue;
+      rotated = true;
+      float zeta = (be - al) / (2.f * ga);
+      float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+      float c = 1.f / sqrtf(1.f + t * t);
+      float sn = c * t;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        float ap = a[p][r], aq = a[q][r];
+        a[p][r] = c * ap - sn * aq;
+        a[q][r] = sn * ap + c * aq;
+        float vp = v[p][r], vq = v[q][r];
+        v[p][r] = c * vp - sn * vq;
+        v[q][r] = sn * vp + c * vq;
+      }
+    }
+    if (!rotated) break;
+  }
+  float sg[3], u[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    sg[c] = sqrtf(dot3(a[c], a[c]));
+    float inv = sg[c] > 0.f ? 1.f / sg[c] : 0.f;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) u[c][r] = a[c][r] * inv;
+  }
+  int kmin = 0;
+  if (sg[1] < sg[kmin]) kmin = 1;
+  if (sg[2] < sg[kmin]) kmin = 2;
+  float smax = fmaxf(sg[0], fmaxf(sg[1], sg[2]));
+  float detF = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+               F[2] * (F[3] * F[7] - F[4] * F[6]);
+  if (sg[kmin] <= 1e-6f * smax) {
+    // (nearly) rank deficient: complete U to a right-handed frame
+    const int i = (kmin + 1) % 3, j = (kmin + 2) % 3;
+    u[kmin][0] = u[i][1] * u[j][2] - u[i][2] * u[j][1];
+    u[kmin][1] = u[i][2] * u[j][0] - u[i][0] * u[j][2];
+    u[kmin][2] = u[i][0] * u[j][1] - u[i][1] * u[j][0];
+    if (detF < 0.f) sg[kmin] = -sg[kmin];
+  } else {
+    float du = u[0][0] * (u[1][1] * u[2][2] - u[1][2] * u[2][1]) -
+               u[1][0] * (u[0][1] * u[2][2] - u[0][2] * u[2][1]) +
+               u[2][0] * (u[0][1] * u[1][2] - u[0][2] * u[1][1]);
+    if (du < 0.f) {
+      sg[kmin] = -sg[kmin];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) u[kmin][r] = -u[kmin][r];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    s[c] = sg[c];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      U[3 * r + c] = u[c][r];
+      V[3 * r + c] = v[c][r];
+    }
+  }
+}
+
+__device__ float snh_objective(const float* x, const float* s, float w, float V, float mu,
+                               float lam, float alpha) {
+  float d0 = x[0] - s[0], d1 = x[1] - s[1], d2 = x[2] - s[2];
+  float ic = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+  float J = x[0] * x[1] * x[2];
+  float psi = 0.5f * mu * (ic - 3.f) + 0.5f * lam * (J - alpha) * (J - alpha) -
+              0.5f * mu * logf(ic + 1.f);
+  return 0.5f * w * (d0 * d0 + d1 * d1 + d2 * d2) + V * psi;
+}
+
+// argmin_x w/2 |x - s|^2 + V psi_SNH(x) by Newton with Armijo backtracking.
+__device__ void snh_sigma(const float* s, float w, float V, float mu, float lam, float alpha,
+                          float* x) {
+  x[0] = s[0];
+  x[1] = s[1];
+  x[2] = s[2];
+  const float scale = w + V * (mu + lam);
+  for (int it = 0; it < 20; ++it) {
+    float ic = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    float J = x[0] * x[1] * x[2];
+    float dJ[3] = {x[1] * x[2], x[0] * x[2], x[0] * x[1]};
+    float ic1 = ic + 1.f;
+    float g[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      g[i] = w * (x[i] - s[i]) + V * (mu * x[i] + lam * (J - alpha) * dJ[i] - mu * x[i] / ic1);
+    float xm = fmaxf(1.f, fmaxf(fabsf(x[0]), fmaxf(fabsf(x[1]), fabsf(x[2]))));
+    float gn = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    if (gn <= 1e-6f * scale * xm) break;
+    float H[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        float d2J = (i == j) ? 0.f : x[3 - i - j];
+        float eye = (i == j) ? 1.f : 0.f;
+        H[i][j] = w * eye + V * (mu * eye + lam * (dJ[i] * dJ[j] + (J - alpha) * d2J) -
+                                 mu * (eye / ic1 - 2.f * x[i] * x[j] / (ic1 * ic1)));
+      }
+    // Cholesky with an increasing diagonal shift until positive definite
+    float L00 = 0, L10 = 0, L11 = 0, L20 = 0, L21 = 0, L22 = 0;
+    float tau = 0.f;
+    bool ok = false;
+    for (int attempt = 0; attempt < 12 && !ok; ++attempt) {
+      float a00 = H[0][0] + tau, a11 = H[1][1] + tau, a22 = H[2][2] + tau;
+      ok = false;
+      if (a00 > 1e-12f * scale) {
+        L00 = sqrtf(a00);
+        L10 = H[1][0] / L00;
+        L20 = H[2][0] / L00;
+        float t11 = a11 - L10 * L10;
+        if (t11 > 1e-12f * scale) {
+          L11 = sqrtf(t11);
+          L21 = (H[2][1] - L20 * L10) / L11;
+          float t22 = a22 - L20 * L20 - L21 * L21;
+          if (t22 > 1e-12f * scale) {
+            L22 = sqrtf(t22);
+            ok = true;
+          }
+        }
+      }
+      tau = tau > 0.f ? 4.f * tau : 1e-4f * scale;
+    }
+    if (!ok) break;
+    float y0 = -g[0] / L00;
+    float y1 = (-g[1] - L10 * y0) / L11;
+    float y2 = (-g[2] - L20 * y0 - L21 * y1) / L22;
+    float d[3];
+    d[2] = y2 / L22;
+    d[1] = (y1 - L21 * d[2]) / L11;
+    d[0] = (y0 - L10 * d[1] - L20 * d[2]) / L00;
+    float f0 = snh_objective(x, s, w, V, mu, lam, alpha);
+    float slope = g[0] * d[0] + g[1] * d[1] + g[2] * d[2];
+    float t = 1.f;
+    float xc[3];
+    for (int ls = 0; ls < 24; ++ls) {
+      xc[0] = x[0] + t * d[0];
+      xc[1] = x[1] + t * d[1];
+      xc[2] = x[2] + t * d[2];
+      float f1 = snh_objective(xc, s, w, V, mu, lam, alpha);
+      if (f1 <= f0 + 1e-4f * t * slope + 4e-7f * fabsf(f0)) break;
+      t *= 0.5f;
+    }
+    float step = t * fmaxf(fabsf(d[0]), fmaxf(fabsf(d[1]), fabsf(d[2])));
+    x[0] = xc[0];
+    x[1] = xc[1];
+    x[2] = xc[2];
+    if (step <= 1e-7f * xm) break;
+  }
+}
+
+__device__ void project_tet(const float* F, int model, float w, float V, float mu, float lam,
+                            float alpha, float* p) {
+  float U[9], s[3], Vm[9], sh[3];
+  svd3(F, U, s, Vm);
+  if (model == SIM_MODEL_COROT) {
+    float a = w + 2.f * mu * V, c = lam * V;
+    float k = 2.f * mu * V + 3.f * lam * V;
+    float r0 = w * s[0] + k, r1 = w * s[1] + k, r2 = w * s[2] + k;
+    float S = (r0 + r1 + r2) / (a + 3.f * c);
+    sh[0] = (r0 - c * S) / a;
+    sh[1] = (r1 - c * S) / a;
+    sh[2] = (r2 - c * S) / a;
+  } else if (model == SIM_MODEL_SNH) {
+    snh_sigma(s, w, V, mu, lam, alpha, sh);
+  } else {
+    sh[0] = sh[1] = sh[2] = 1.f;
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      p[3 * r + c] = U[3 * r + 0] * sh[0] * Vm[3 * c + 0] + U[3 * r + 1] * sh[1] * Vm[3 * c + 1] +
+                     U[3 * r + 2] * sh[2] * Vm[3 * c + 2];
+}
+
+__global__ void k_frame_begin(DevSim d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n_all) return;
+  const double h = d.h;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    double qt = d.q_t[3 * i + r];
+    if (i < d.n) {
+      double st = qt + h * d.v_t[3 * i + r] + h * h * d.grav[r];
+      d.s_tilde[3 * i + r] = st;
+      d.q_ref[3 * i + r] = qt;
+      d.dq[3 * i + r] = (float)(st - qt);
+    } else {
+      double qp = qt + h * d.handle_vel[r];
+      d.s_tilde[3 * i + r] = qp;
+      d.q_ref[3 * i + r] = qp;
+      d.dq[3 * i + r] = 0.f;
+    }
+  }
+}
+
+template <bool kDebug>
+__global__ void __launch_bounds__(128) k_local(DevSim d) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d.n_tets) return;
+  const int T = d.n_tets;
+  int4 vi = d.tet_v[t];
+  int vv[4] = {vi.x, vi.y, vi.z, vi.w};
+  float Mi[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Mi[k] = d.tet_dminv[k * T + t];
+  float g[4][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    g[1][c] = Mi[c];
+    g[2][c] = Mi[3 + c];
+    g[3][c] = Mi[6 + c];
+    g[0][c] = -(g[1][c] + g[2][c] + g[3][c]);
+  }
+  double x0[3];
+  float dq0[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    x0[r] = d.q_ref[3 * vv[0] + r];
+    dq0[r] = d.dq[3 * vv[0] + r];
+  }
+  float Fr[9], F[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Fr[k] = F[k] = 0.f;
+#pragma unroll
+  for (int a = 1; a < 4; ++a) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      float er = (float)(d.q_ref[3 * vv[a] + r] - x0[r]);
+      float ed = d.dq[3 * vv[a] + r] - dq0[r];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Fr[3 * r + c] += er * g[a][c];
+        F[3 * r + c] += (er + ed) * g[a][c];
+      }
+    }
+  }
+  const MatDev m = d.mats[d.tet_mat[t]];
+  const float w = d.tet_w[t], V = d.tet_vol[t];
+  float p[9];
+  project_tet(F, m.model, w, V, m.mu, m.lam, m.alpha, p);
+  if (kDebug) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) d.p_out[9 * t + k] = p[k];
+    return;
+  }
+  const float s = (float)(d.h * d.h) * w;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    float o[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+      o[r] = s * ((p[3 * r] - Fr[3 * r]) * g[a][0] + (p[3 * r + 1] - Fr[3 * r + 1]) * g[a][1] +
+                  (p[3 * r + 2] - Fr[3 * r + 2]) * g[a][2]);
+    d.contrib[4 * t + a] = make_float4(o[0], o[1], o[2], 0.f);
+  }
+}
+
+// b_i - (A q_ref)_i + h^2 (J^T lambda)_i for every free vertex i, written as the FP32 SoA
+// vector g of the first profile product.
+__global__ void k_rhs(DevSim d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n_pad) return;
+  if (i >= d.n) {
+    d.gvec[i] = 0.f;
+    d.gvec[d.n_pad + i] = 0.f;
+    d.gvec[2 * d.n_pad + i] = 0.f;
+    return;
+  }
+  double m = d.mass[i];
+  double b[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) b[r] = m * (d.s_tilde[3 * i + r] - d.q_ref[3 * i + r]);
+  float e[3] = {0.f, 0.f, 0.f};
+  for (int k = d.inc_ptr[i]; k < d.inc_ptr[i + 1]; ++k) {
+    float4 c = d.contrib[d.inc_idx[k]];
+    e[0] += c.x;
+    e[1] += c.y;
+    e[2] += c.z;
+  }
+  const double h2 = d.h * d.h;
+  int nc = d.ct_cnt[i];
+  if (nc > 0) {
+    int j0 = d.ct_off[i];
+    int cap = d.cap;
+    for (int j = j0; j < j0 + nc && j < cap; ++j) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) b[r] += h2 * d.ct_force[3 * j + r];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) d.gvec[r * d.n_pad + i] = (float)(b[r] + (double)e[r]);
+}
+
+__global__ void k_integrate(DevSim d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n_all) return;
+  bool bad = false;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    double qn = d.q_ref[3 * i + r] + (double)d.dq[3 * i + r];
+    double vn = (qn - d.q_t[3 * i + r]) / d.h;
+    bad |= !isfinite(qn) || !isfinite(vn);
+    d.q_t[3 * i + r] = qn;
+    d.v_t[3 * i + r] = vn;
+  }
+  if (bad) atomicOr(d.err, kErrNonFinite);
+}
+
+}  // namespace
+
+void launch_frame_begin(const DevSim& d, cudaStream_t s) {
+  k_frame_begin<<<(d.n_all + 255) / 256, 256, 0, s>>>(d);
+}
+
+void launch_local(const DevSim& d, cudaStream_t s, bool debug_p) {
+  int grid = (d.n_tets + 127) / 128;
+  if (debug_p)
+    k_local<true><<<grid, 128, 0, s>>>(d);
+  else
+    k_local<false><<<grid, 128, 0, s>>>(d);
+}
+
+void launch_rhs(const DevSim& d, cudaStream_t s) {
+  k_rhs<<<(d.n_pad + 255) / 256, 256, 0, s>>>(d);
+}
+
+void launch_integrate(const DevSim& d, cudaStream_t s) {
+  k_integrate<<<(d.n_all + 255) / 256, 256, 0, s>>>(d);
+}
+
+}  // namespace silg

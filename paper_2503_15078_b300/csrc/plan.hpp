@@ -1,0 +1,103 @@
+// Host-side precompute of the sparse-inverse local-global solver (internal header).
+//
+// Everything here runs once per mesh on the CPU in FP64 (and integer arithmetic for the
+// ordering and symbolic phases): per-element rest data, lumped masses, the per-vertex
+// system matrix A~ (Eq. 6 with A = A~ (x) I3), a nested-dissection ordering, the
+// postordered elimination tree, the Cholesky factor L~ and the sparse inverse
+// S~ = L~^-1 P in row-profile form (Theorem 1), plus the tile schedule the device
+// products use.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "silg.h"
+
+namespace silg {
+
+// Row-profile alignment (values): every stored row starts at a column multiple of
+// kAlign and its length is a multiple of kAlign, so 16-byte vector loads of FP32 (4) and
+// BF16 (8) values stay aligned.
+constexpr int kAlign = 8;
+// Device tile shape of the two profile products: kRowGroup rows x kTileW columns.
+constexpr int kRowGroup = 32;
+constexpr int kTileW = 256;
+
+struct MatParams {
+  int model;
+  double mu_le, lam_le;   // Lame parameters of linear elasticity
+  double mu, lam, alpha;  // parameters of the element energy (SNH re-parameterised)
+  double rho;
+};
+
+struct Plan {
+  // ---- copied input ---------------------------------------------------------------
+  int n_verts = 0, n_tets = 0;
+  double h = 0;
+  std::vector<double> X;          // n_verts x 3 (caller numbering)
+  std::vector<int32_t> tets;      // n_tets x 4 (caller numbering)
+  std::vector<int32_t> tet_mat;   // n_tets
+  std::vector<MatParams> mats;
+  std::vector<uint8_t> pinned;    // n_verts flags
+  double handle_vel[3] = {0, 0, 0};
+
+  // ---- per element (caller tet order) ----------------------------------------------
+  std::vector<double> Dm_inv;     // 9 per tet, row-major
+  std::vector<double> vol;        // rest volume V_i
+  std::vector<double> weight;     // PD weight w_i = 2 mu_LE V_i
+  std::vector<double> mass;       // lumped vertex mass (caller numbering)
+  double mean_edge = 0;
+
+  // ---- numbering ------------------------------------------------------------------
+  int n_free = 0;
+  std::vector<int32_t> order;     // internal free row k -> caller vertex id
+  std::vector<int32_t> internal;  // caller vertex id -> internal id (free: k, pinned: n_free + j)
+  std::vector<int32_t> pinned_ids;// internal pinned j -> caller vertex id
+
+  // ---- elimination tree (postordered; internal free numbering) ----------------------
+  std::vector<int32_t> parent, first_desc, depth;
+
+  // ---- A~ over free vertices (CSR, internal numbering, full symmetric pattern) -------
+  std::vector<int64_t> Ap;
+  std::vector<int32_t> Ai;
+  std::vector<double> Ax;
+
+  // ---- L~ (CSC, diagonal first in each column) -----------------------------------
+  std::vector<int64_t> Lp;
+  std::vector<int32_t> Li;
+  std::vector<double> Lx;
+
+  // ---- S~ row profile --------------------------------------------------------------
+  int n_pad = 0;                  // vector length: n_free rounded up to kTileW
+  std::vector<int32_t> lo, hi;    // stored column range [lo, hi) of each row
+  std::vector<int64_t> rowbase;   // offset of column lo of each row (n_free + 1 entries)
+  std::vector<double> S;          // stored values (zeros outside [fd(i), i])
+  int64_t nnz_S = 0;
+
+  // ---- tile schedule of the device products ----------------------------------------
+  // pass 1 (z = S g): item = (row group, [ct_begin, ct_end)); pass 2 (x = S^T y): item
+  // = (column tile, list of row groups). Reductions: rows of group rg sum the pass-1
+  // partials of items [p1_first[rg], p1_first[rg+1]); columns of tile ct sum the pass-2
+  // partials of items [p2_first[ct], p2_first[ct+1]).
+  int n_rg = 0, n_ct = 0;
+  std::vector<int32_t> p1_items;  // 4 ints per item: rg, ct_begin, ct_end, weight
+  std::vector<int32_t> p1_first;  // n_rg + 1
+  std::vector<int32_t> p2_items;  // 4 ints per item: ct, list_off, list_cnt, weight
+  std::vector<int32_t> p2_first;  // n_ct + 1
+  std::vector<int32_t> p2_list;   // row groups
+
+  // ---- statistics -----------------------------------------------------------------
+  int64_t nnz_A = 0, nnz_L = 0;
+  int max_depth = 0, n_roots = 0;
+  double mean_depth = 0, seconds = 0;
+};
+
+// Build the plan. Returns SIM_OK or an error code; *err receives a message.
+int build_plan(const sim_mesh* mesh, const sim_material* mats, int n_mat, double h,
+               int n_threads, Plan* plan, std::string* err);
+
+// x = S^T (S b) on the host in FP64, internal free numbering, b and x of n_free x 3.
+void apply_inverse_internal(const Plan& p, const double* b, double* x);
+
+}  // namespace silg

@@ -1,0 +1,636 @@
+// C ABI of the simulator: creation (host precompute + upload), the per-frame CUDA graph
+// of Alg. 4, state and diagnostic accessors, and the component entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "device.cuh"
+#include "silg.h"
+
+namespace {
+
+using silg::DevSim;
+using silg::Plan;
+
+struct Graph {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace
+
+struct sim_s {
+  Plan plan;
+  DevSim d{};
+  int device = 0;
+  cudaStream_t work = nullptr;    // private stream: captures and component calls
+  cudaStream_t launch = nullptr;  // where frames run (caller stream or work)
+  int cluster = 1;
+  size_t cr_smem = 0;
+  int n_iters_default = 5;
+  bool has_obstacles = false;
+  int wt_tiles = 1;
+  std::map<int, Graph> graphs;
+  std::vector<void*> allocs;
+  int64_t frame = 0;
+  int last_iters = 0;
+  // phase events recorded by event nodes of the frame graph: [0] frame start,
+  // [1] after collision, [2] after Delassus, then 5 per iteration, then [end]
+  std::vector<cudaEvent_t> ev;
+  std::vector<int32_t> tet_caller_order;
+
+  template <class T>
+  T* alloc(size_t count) {
+    void* p = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) throw std::bad_alloc();
+    allocs.push_back(p);
+    cudaMemsetAsync(p, 0, count * sizeof(T), work);
+    return static_cast<T*>(p);
+  }
+  template <class T>
+  T* upload(const std::vector<T>& v) {
+    T* p = alloc<T>(v.size());
+    if (!v.empty()) cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, work);
+    return p;
+  }
+  ~sim_s() {
+    if (work) cudaStreamSynchronize(work);
+    for (auto& kv : graphs) {
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+      if (kv.second.g) cudaGraphDestroy(kv.second.g);
+    }
+    for (void* p : allocs) cudaFree(p);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    if (work) cudaStreamDestroy(work);
+  }
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return SIM_OK;
+  if (e == cudaErrorMemoryAllocation) return SIM_ENOMEM;
+  return SIM_ECUDA;
+}
+
+int err_status(int bits) {
+  if (bits & (silg::kErrCapacity | silg::kErrYCapacity)) return SIM_ECAPACITY;
+  if (bits & silg::kErrNonFinite) return SIM_ENONFINITE;
+  if (bits & silg::kErrTimeout) return SIM_ETIMEOUT;
+  return SIM_OK;
+}
+
+int sync_and_check(sim_s* s) {
+  cudaError_t e = cudaStreamSynchronize(s->launch);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->work);
+  if (e != cudaSuccess) return cuda_status(e);
+  int bits = 0;
+  e = cudaMemcpy(&bits, s->d.err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  return err_status(bits);
+}
+
+int kernels_per_frame(const sim_s* s, int K) {
+  const bool c = s->has_obstacles;
+  return 1 + (c ? 4 + 9 : 0) + K * (1 + (c ? 1 : 0) + 1 + 2 + (c ? 3 : 0) + 2) + (c ? 1 : 0) + 1;
+}
+
+void enqueue_frame(sim_s* s, int K, cudaStream_t st) {
+  const DevSim& d = s->d;
+  // external event-record nodes: observable from the host after each graph launch
+  auto mark = [&](int i) { cudaEventRecordWithFlags(s->ev[i], st, cudaEventRecordExternal); };
+  mark(0);
+  cudaMemsetAsync(d.resid, 0, sizeof(double) * (silg::kMaxIters + 1), st);
+  cudaMemsetAsync(d.max_pen, 0, sizeof(double), st);
+  silg::launch_frame_begin(d, st);
+  if (s->has_obstacles) silg::launch_collide(d, st);
+  mark(1);
+  if (s->has_obstacles) silg::launch_delassus(d, st, s->wt_tiles);
+  mark(2);
+  for (int k = 0; k < K; ++k) {
+    const int e = 3 + 5 * k;
+    silg::launch_local(d, st, false);
+    mark(e);
+    if (s->has_obstacles) silg::launch_contact_eval(d, st, k, false);
+    silg::launch_rhs(d, st);
+    mark(e + 1);
+    silg::launch_pass1(d, st);
+    mark(e + 2);
+    if (s->has_obstacles) {
+      silg::launch_ytz(d, st);
+      silg::launch_cr(d, st, s->cluster);
+      silg::launch_yu(d, st);
+    }
+    mark(e + 3);
+    silg::launch_pass2(d, st, true);
+    mark(e + 4);
+  }
+  if (s->has_obstacles) silg::launch_contact_eval(d, st, K, true);
+  silg::launch_integrate(d, st);
+  mark(3 + 5 * K);
+}
+
+int get_graph(sim_s* s, int K, cudaGraphExec_t* out) {
+  auto it = s->graphs.find(K);
+  if (it != s->graphs.end()) {
+    *out = it->second.exec;
+    return SIM_OK;
+  }
+  Graph g;
+  cudaError_t e = cudaStreamBeginCapture(s->work, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_status(e);
+  enqueue_frame(s, K, s->work);
+  e = cudaStreamEndCapture(s->work, &g.g);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaGraphInstantiate(&g.exec, g.g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g.g);
+    return cuda_status(e);
+  }
+  s->graphs[K] = g;
+  *out = g.exec;
+  return SIM_OK;
+}
+
+int create_device(sim_s* s, const sim_obstacle* obstacles, int n_obs, const sim_options* o) {
+  Plan& p = s->plan;
+  DevSim& d = s->d;
+  const int n = p.n_free, n_all = p.n_verts, T = p.n_tets;
+  d.n = n;
+  d.n_all = n_all;
+  d.n_tets = T;
+  d.n_pad = p.n_pad;
+  d.n_obs = n_obs;
+  d.n_mat = (int)p.mats.size();
+  d.cap = std::max(1, o->contact_capacity);
+  d.n_cr = std::max(0, o->n_cr_iters);
+  d.h = p.h;
+  for (int r = 0; r < 3; ++r) {
+    d.grav[r] = o->gravity[r];
+    d.handle_vel[r] = p.handle_vel[r];
+  }
+  d.margin = o->contact_margin > 0 ? o->contact_margin : 0.5 * p.mean_edge;
+  {
+    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+    for (int v = 0; v < n_all; ++v)
+      for (int r = 0; r < 3; ++r) {
+        mn[r] = std::min(mn[r], p.X[3 * v + r]);
+        mx[r] = std::max(mx[r], p.X[3 * v + r]);
+      }
+    d.L_ref = std::sqrt((mx[0] - mn[0]) * (mx[0] - mn[0]) + (mx[1] - mn[1]) * (mx[1] - mn[1]) +
+                        (mx[2] - mn[2]) * (mx[2] - mn[2]));
+  }
+  // ---- per vertex (internal numbering) ---------------------------------------------
+  std::vector<double> mass(n_all), X(3 * (size_t)n_all);
+  for (int v = 0; v < n_all; ++v) {
+    int iv = p.internal[v];
+    mass[iv] = p.mass[v];
+    for (int r = 0; r < 3; ++r) X[3 * (size_t)iv + r] = p.X[3 * (size_t)v + r];
+  }
+  d.mass = s->upload(mass);
+  d.q_t = s->upload(X);
+  d.v_t = s->alloc<double>(3 * (size_t)n_all);
+  d.q_ref = s->upload(X);
+  d.s_tilde = s->upload(X);
+  d.dq = s->alloc<float>(3 * (size_t)n_all);
+  d.depth = s->upload(p.depth);
+  d.parent = s->upload(p.parent);
+  d.first_desc = s->upload(p.first_desc);
+  // ---- per element ---------------------------------------------------------------
+  std::vector<int4> tv(T);
+  std::vector<float> dminv(9 * (size_t)T), tw(T), tvol(T);
+  for (int t = 0; t < T; ++t) {
+    const int32_t* v = &p.tets[4 * (size_t)t];
+    tv[t] = make_int4(p.internal[v[0]], p.internal[v[1]], p.internal[v[2]], p.internal[v[3]]);
+    for (int k = 0; k < 9; ++k) dminv[(size_t)k * T + t] = (float)p.Dm_inv[9 * (size_t)t + k];
+    tw[t] = (float)p.weight[t];
+    tvol[t] = (float)p.vol[t];
+  }
+  d.tet_v = s->upload(tv);
+  d.tet_dminv = s->upload(dminv);
+  d.tet_w = s->upload(tw);
+  d.tet_vol = s->upload(tvol);
+  d.tet_mat = s->upload(p.tet_mat);
+  std::vector<silg::MatDev> md;
+  for (auto& m : p.mats) md.push_back({m.model, (float)m.mu, (float)m.lam, (float)m.alpha});
+  d.mats = s->upload(md);
+  d.contrib = s->alloc<float4>(4 * (size_t)T);
+  {
+    std::vector<int> cnt(n + 1, 0);
+    for (int t = 0; t < T; ++t)
+      for (int a = 0; a < 4; ++a) {
+        int iv = p.internal[p.tets[4 * (size_t)t + a]];
+        if (iv < n) ++cnt[iv + 1];
+      }
+    for (int i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+    std::vector<int> idx(cnt[n]), fill(cnt.begin(), cnt.end() - 1);
+    for (int t = 0; t < T; ++t)
+      for (int a = 0; a < 4; ++a) {
+        int iv = p.internal[p.tets[4 * (size_t)t + a]];
+        if (iv < n) idx[fill[iv]++] = 4 * t + a;
+      }
+    d.inc_ptr = s->upload(cnt);
+    d.inc_idx = s->upload(idx);
+  }
+  // ---- S~ profile and tile schedule ---------------------------------------------------
+  {
+    std::vector<float> Sf(p.S.size());
+    for (size_t k = 0; k < p.S.size(); ++k) Sf[k] = (float)p.S[k];
+    d.S = s->upload(Sf);
+    std::vector<long long> rb(p.rowbase.begin(), p.rowbase.end());
+    d.rowbase = s->upload(rb);
+    d.lo = s->upload(p.lo);
+    d.hi = s->upload(p.hi);
+    std::vector<int4> it1(p.p1_items.size() / 4), it2(p.p2_items.size() / 4);
+    for (size_t k = 0; k < it1.size(); ++k)
+      it1[k] = make_int4(p.p1_items[4 * k], p.p1_items[4 * k + 1], p.p1_items[4 * k + 2], p.p1_items[4 * k + 3]);
+    for (size_t k = 0; k < it2.size(); ++k)
+      it2[k] = make_int4(p.p2_items[4 * k], p.p2_items[4 * k + 1], p.p2_items[4 * k + 2], p.p2_items[4 * k + 3]);
+    d.n_rg = p.n_rg;
+    d.n_ct = p.n_ct;
+    d.n_p1 = (int)it1.size();
+    d.n_p2 = (int)it2.size();
+    d.p1_items = s->upload(it1);
+    d.p2_items = s->upload(it2);
+    d.p1_first = s->upload(p.p1_first);
+    d.p2_first = s->upload(p.p2_first);
+    d.p2_list = s->upload(p.p2_list);
+    d.p1_part = s->alloc<float>((size_t)d.n_p1 * 3 * silg::kRowGroup);
+    d.p2_part = s->alloc<float>((size_t)d.n_p2 * 3 * silg::kTileW);
+  }
+  d.gvec = s->alloc<float>(3 * (size_t)p.n_pad);
+  d.zvec = s->alloc<float>(3 * (size_t)p.n_pad);
+  d.xout = s->alloc<float>(3 * (size_t)n);
+  // ---- obstacles and contacts --------------------------------------------------------
+  std::vector<silg::ObstDev> ob(std::max(1, n_obs));
+  for (int k = 0; k < n_obs; ++k) {
+    const sim_obstacle& so = obstacles[k];
+    if ((so.kind != SIM_OBST_PLANE && so.kind != SIM_OBST_CYLINDER) || !(so.mu >= 0) ||
+        (so.kind == SIM_OBST_CYLINDER && !(so.radius > 0)))
+      return SIM_EINVAL;
+    double an = std::sqrt(so.axis[0] * so.axis[0] + so.axis[1] * so.axis[1] + so.axis[2] * so.axis[2]);
+    if (!(an > 0)) return SIM_EINVAL;
+    ob[k].kind = so.kind;
+    for (int r = 0; r < 3; ++r) {
+      ob[k].p[r] = so.p[r];
+      ob[k].a[r] = so.axis[r] / an;
+      ob[k].vel[r] = so.vel[r];
+    }
+    ob[k].radius = so.radius;
+    ob[k].mu = so.mu;
+  }
+  d.obst = s->upload(ob);
+  const int cap = d.cap;
+  long long cap_y = (long long)cap * std::max(1, p.max_depth);
+  cap_y = std::min<long long>(cap_y, 1LL << 27);
+  d.cap_y = (int)cap_y;
+  d.counters = s->alloc<int>(silg::kNumCounters);
+  d.ct_cnt = s->alloc<int>(n);
+  d.ct_off = s->alloc<int>(n + 1);
+  d.cv_flag = s->alloc<int>(n);
+  d.cv_off = s->alloc<int>(n + 1);
+  d.ct_vert = s->alloc<int>(cap);
+  d.ct_obst = s->alloc<int>(cap);
+  d.ct_cv = s->alloc<int>(cap);
+  d.ct_D = s->alloc<double>(9 * (size_t)cap);
+  d.ct_dn = s->alloc<double>(cap);
+  d.ct_df = s->alloc<double>(2 * (size_t)cap);
+  d.ct_mu = s->alloc<double>(cap);
+  d.ct_r = s->alloc<double>(2 * (size_t)cap);
+  d.ct_lam = s->alloc<double>(3 * (size_t)cap);
+  d.ct_force = s->alloc<double>(3 * (size_t)cap);
+  d.ct_omega = s->alloc<float>(3 * (size_t)cap);
+  d.ct_ecal = s->alloc<float>(3 * (size_t)cap);
+  d.ct_Df = s->alloc<float>(9 * (size_t)cap);
+  d.ct_hv = s->alloc<double>(3 * (size_t)cap);
+  d.ct_rhs = s->alloc<float>(3 * (size_t)cap);
+  d.cv_vert = s->alloc<int>(cap);
+  d.cv_first = s->alloc<int>(cap);
+  d.cv_nct = s->alloc<int>(cap);
+  d.uvec = s->alloc<float>(3 * (size_t)cap);
+  d.svec = s->alloc<float>(3 * (size_t)cap);
+  d.u_flag = s->alloc<int>(n);
+  d.u_off = s->alloc<int>(n + 1);
+  d.u_list = s->alloc<int>(n);
+  d.row_clo = s->alloc<int>(n);
+  d.row_len = s->alloc<int>(n);
+  d.u_clo = s->alloc<int>(n);
+  d.u_len = s->alloc<int>(n);
+  d.y_ptr = s->alloc<int>(n + 1);
+  d.y_val = s->alloc<float>(cap_y);
+  d.yc_len = s->alloc<int>(cap);
+  d.yc_ptr = s->alloc<int>(cap + 1);
+  d.yc_val = s->alloc<float>(cap_y);
+  d.yc_row = s->alloc<int>(cap_y);
+  d.wt = s->alloc<float>((size_t)cap * cap);
+  d.resid = s->alloc<double>(silg::kMaxIters + 1);
+  d.max_pen = s->alloc<double>(1);
+  d.err = s->alloc<int>(1);
+  d.p_out = s->alloc<float>(9 * (size_t)T);
+  s->has_obstacles = n_obs > 0;
+  s->wt_tiles = (cap + 63) / 64;
+  s->ev.resize(4 + 5 * silg::kMaxIters);
+  for (auto& e : s->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return SIM_ECUDA;
+  if (s->has_obstacles) {
+    int st = silg::cr_setup(&s->cluster, &s->cr_smem);
+    if (st != SIM_OK) return st;
+  }
+  cudaError_t e = cudaStreamSynchronize(s->work);
+  if (e != cudaSuccess) return cuda_status(e);
+  return cuda_status(cudaGetLastError());
+}
+
+template <class F>
+int guarded(F f) {
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    return SIM_ENOMEM;
+  } catch (...) {
+    return SIM_EINVAL;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+void silg_fill_plan_info(const silg::Plan& p, sim_plan_info* info);
+
+int sim_get_plan_info(const sim_t* s, sim_plan_info* info) {
+  if (!s || !info) return SIM_EINVAL;
+  silg_fill_plan_info(s->plan, info);
+  return SIM_OK;
+}
+
+int sim_create(const sim_mesh* mesh, const sim_material* mats, int32_t n_mat,
+               const sim_obstacle* obstacles, int32_t n_obs, double h,
+               const sim_options* opts, sim_t** out) {
+  if (!out) return SIM_EINVAL;
+  *out = nullptr;
+  if (n_obs < 0 || (n_obs > 0 && !obstacles)) return SIM_EINVAL;
+  sim_options def;
+  sim_default_options(&def);
+  const sim_options* o = opts ? opts : &def;
+  if (o->n_iters < 0 || o->n_iters > silg::kMaxIters || o->n_cr_iters < 0 ||
+      o->contact_capacity <= 0 || o->contact_capacity > (1 << 16))
+    return SIM_EINVAL;
+  if (o->s_precision != SIM_S_FP32) return SIM_ENOTSUP;
+  sim_s* s = new (std::nothrow) sim_s();
+  if (!s) return SIM_ENOMEM;
+  int st = guarded([&]() {
+    std::string err;
+    int r = silg::build_plan(mesh, mats, n_mat, h, o->n_host_threads, &s->plan, &err);
+    if (r != SIM_OK) return r;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) return SIM_ECUDA;
+    if (o->device < 0 || o->device >= ndev) return SIM_EINVAL;
+    s->device = o->device;
+    if (cudaSetDevice(s->device) != cudaSuccess) return SIM_ECUDA;
+    if (cudaStreamCreateWithFlags(&s->work, cudaStreamNonBlocking) != cudaSuccess) return SIM_ECUDA;
+    s->launch = o->cuda_stream ? static_cast<cudaStream_t>(o->cuda_stream) : s->work;
+    s->n_iters_default = o->n_iters > 0 ? o->n_iters : 5;
+    return create_device(s, obstacles, n_obs, o);
+  });
+  if (st != SIM_OK) {
+    delete s;
+    return st;
+  }
+  *out = s;
+  return SIM_OK;
+}
+
+void sim_destroy(sim_t* s) {
+  if (!s) return;
+  cudaSetDevice(s->device);
+  if (s->launch) cudaStreamSynchronize(s->launch);
+  delete s;
+}
+
+int sim_step(sim_t* s, int32_t n_iters) {
+  if (!s) return SIM_EINVAL;
+  int K = n_iters > 0 ? n_iters : s->n_iters_default;
+  if (K > silg::kMaxIters) return SIM_EINVAL;
+  cudaSetDevice(s->device);
+  cudaGraphExec_t exec = nullptr;
+  int st = get_graph(s, K, &exec);
+  if (st != SIM_OK) return st;
+  cudaError_t e = cudaGraphLaunch(exec, s->launch);
+  if (e != cudaSuccess) return cuda_status(e);
+  s->frame += 1;
+  s->last_iters = K;
+  return SIM_OK;
+}
+
+int sim_synchronize(sim_t* s) {
+  if (!s) return SIM_EINVAL;
+  cudaSetDevice(s->device);
+  return sync_and_check(s);
+}
+
+int sim_get_state(sim_t* s, double* q, double* v) {
+  if (!s) return SIM_EINVAL;
+  cudaSetDevice(s->device);
+  int st = sync_and_check(s);
+  if (st == SIM_ECUDA) return st;
+  const Plan& p = s->plan;
+  const int n_all = p.n_verts;
+  std::vector<double> buf(3 * (size_t)n_all);
+  double* srcs[2] = {s->d.q_t, s->d.v_t};
+  double* dsts[2] = {q, v};
+  for (int k = 0; k < 2; ++k) {
+    if (!dsts[k]) continue;
+    cudaError_t e = cudaMemcpy(buf.data(), srcs[k], buf.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int vv = 0; vv < n_all; ++vv)
+      for (int r = 0; r < 3; ++r) dsts[k][3 * (size_t)vv + r] = buf[3 * (size_t)p.internal[vv] + r];
+  }
+  return st;
+}
+
+int sim_set_state(sim_t* s, const double* q, const double* v) {
+  if (!s || !q || !v) return SIM_EINVAL;
+  cudaSetDevice(s->device);
+  cudaError_t e = cudaStreamSynchronize(s->launch);
+  if (e != cudaSuccess) return cuda_status(e);
+  const Plan& p = s->plan;
+  const int n_all = p.n_verts;
+  std::vector<double> bq(3 * (size_t)n_all), bv(3 * (size_t)n_all);
+  for (int vv = 0; vv < n_all; ++vv)
+    for (int r = 0; r < 3; ++r) {
+      double a = q[3 * (size_t)vv + r], b = v[3 * (size_t)vv + r];
+      if (!std::isfinite(a) || !std::isfinite(b)) return SIM_EINVAL;
+      bq[3 * (size_t)p.internal[vv] + r] = a;
+      bv[3 * (size_t)p.internal[vv] + r] = b;
+    }
+  e = cudaMemcpy(s->d.q_t, bq.data(), bq.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->d.v_t, bv.data(), bv.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(s->d.err, 0, sizeof(int));
+  s->frame = 0;
+  return cuda_status(e);
+}
+
+int sim_get_stats(sim_t* s, sim_stats* out) {
+  if (!s || !out) return SIM_EINVAL;
+  cudaSetDevice(s->device);
+  int st = sync_and_check(s);
+  if (st == SIM_ECUDA) return st;
+  std::memset(out, 0, sizeof(*out));
+  int cnt[silg::kNumCounters];
+  double res[silg::kMaxIters + 1];
+  cudaMemcpy(cnt, s->d.counters, sizeof(cnt), cudaMemcpyDeviceToHost);
+  cudaMemcpy(res, s->d.resid, sizeof(res), cudaMemcpyDeviceToHost);
+  cudaMemcpy(&out->max_penetration, s->d.max_pen, sizeof(double), cudaMemcpyDeviceToHost);
+  out->frame = s->frame;
+  out->n_contacts = s->has_obstacles ? cnt[silg::kCntContacts] : 0;
+  out->n_contact_verts = s->has_obstacles ? cnt[silg::kCntCv] : 0;
+  out->n_iters = s->last_iters;
+  out->n_residuals = s->has_obstacles && s->frame > 0 ? s->last_iters + 1 : 0;
+  for (int k = 0; k < out->n_residuals; ++k) out->residual[k] = res[k];
+  out->kernels_per_frame = kernels_per_frame(s, s->last_iters > 0 ? s->last_iters : s->n_iters_default);
+  return st;
+}
+
+int sim_get_phase_times(sim_t* s, double* ms) {
+  if (!s || !ms) return SIM_EINVAL;
+  cudaSetDevice(s->device);
+  for (int k = 0; k < SIM_NUM_PHASES; ++k) ms[k] = 0.0;
+  if (s->frame == 0 || s->last_iters == 0) return SIM_OK;
+  const int K = s->last_iters;
+  cudaError_t e = cudaEventSynchronize(s->ev[3 + 5 * K]);
+  if (e != cudaSuccess) return cuda_status(e);
+  auto el = [&](int a, int b) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, s->ev[a], s->ev[b]);
+    return (double)t;
+  };
+  ms[SIM_PHASE_COLLIDE] = el(0, 1);
+  ms[SIM_PHASE_DELASSUS] = el(1, 2);
+  for (int k = 0; k < K; ++k) {
+    const int b = 3 + 5 * k;
+    ms[SIM_PHASE_LOCAL] += el(b - 1, b);
+    ms[SIM_PHASE_ASSEMBLE] += el(b, b + 1);
+    ms[SIM_PHASE_SPMV1] += el(b + 1, b + 2);
+    ms[SIM_PHASE_SOLVE] += el(b + 2, b + 3);
+    ms[SIM_PHASE_SPMV2] += el(b + 3, b + 4);
+  }
+  ms[SIM_PHASE_INTEGRATE] = el(3 + 5 * K - 1, 3 + 5 * K);
+  return SIM_OK;
+}
+
+int sim_get_contacts(sim_t* s, int32_t capacity, int32_t* vertex, int32_t* obstacle,
+                     double* lambda, double* frame, int32_t* n_out) {
+  if (!s || !n_out || capacity < 0) return SIM_EINVAL;
+  cudaSetDevice(s->device);
+  int st = sync_and_check(s);
+  if (st == SIM_ECUDA) return st;
+  int c = 0;
+  if (s->has_obstacles) cudaMemcpy(&c, s->d.counters + silg::kCntContacts, sizeof(int), cudaMemcpyDeviceToHost);
+  c = std::min(c, s->d.cap);
+  *n_out = c;
+  if (capacity == 0 || c == 0) return st;
+  std::vector<int> cv(c), co(c);
+  std::vector<double> cl(3 * (size_t)c), cD(9 * (size_t)c);
+  cudaMemcpy(cv.data(), s->d.ct_vert, sizeof(int) * c, cudaMemcpyDeviceToHost);
+  cudaMemcpy(co.data(), s->d.ct_obst, sizeof(int) * c, cudaMemcpyDeviceToHost);
+  cudaMemcpy(cl.data(), s->d.ct_lam, sizeof(double) * 3 * c, cudaMemcpyDeviceToHost);
+  cudaMemcpy(cD.data(), s->d.ct_D, sizeof(double) * 9 * c, cudaMemcpyDeviceToHost);
+  std::vector<int> perm(c);
+  std::iota(perm.begin(), perm.end(), 0);
+  const Plan& p = s->plan;
+  std::sort(perm.begin(), perm.end(), [&](int a, int b) {
+    int va = p.order[cv[a]], vb = p.order[cv[b]];
+    return va < vb || (va == vb && co[a] < co[b]);
+  });
+  for (int k = 0; k < std::min(c, (int)capacity); ++k) {
+    int j = perm[k];
+    if (vertex) vertex[k] = p.order[cv[j]];
+    if (obstacle) obstacle[k] = co[j];
+    if (lambda)
+      for (int r = 0; r < 3; ++r) lambda[3 * k + r] = cl[3 * j + r];
+    if (frame)
+      for (int r = 0; r < 9; ++r) frame[9 * k + r] = cD[9 * j + r];
+  }
+  return st;
+}
+
+int sim_apply_inverse(sim_t* s, const double* b, double* x) {
+  if (!s || !b || !x) return SIM_EINVAL;
+  cudaSetDevice(s->device);
+  const Plan& p = s->plan;
+  const int n = p.n_free, np = p.n_pad;
+  std::vector<float> g(3 * (size_t)np, 0.f);
+  for (int k = 0; k < n; ++k)
+    for (int r = 0; r < 3; ++r) g[(size_t)r * np + k] = (float)b[3 * (size_t)p.order[k] + r];
+  cudaStreamSynchronize(s->launch);
+  cudaMemcpyAsync(s->d.gvec, g.data(), g.size() * sizeof(float), cudaMemcpyHostToDevice, s->work);
+  silg::launch_pass1(s->d, s->work);
+  silg::launch_pass2(s->d, s->work, false);
+  std::vector<float> xo(3 * (size_t)n);
+  cudaMemcpyAsync(xo.data(), s->d.xout, xo.size() * sizeof(float), cudaMemcpyDeviceToHost, s->work);
+  cudaError_t e = cudaStreamSynchronize(s->work);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e);
+  std::memset(x, 0, sizeof(double) * 3 * (size_t)p.n_verts);
+  for (int k = 0; k < n; ++k)
+    for (int r = 0; r < 3; ++r) x[3 * (size_t)p.order[k] + r] = xo[3 * (size_t)k + r];
+  return SIM_OK;
+}
+
+int sim_local_project(sim_t* s, const double* q, double* pout) {
+  if (!s || !q || !pout) return SIM_EINVAL;
+  cudaSetDevice(s->device);
+  const Plan& p = s->plan;
+  const int n_all = p.n_verts, T = p.n_tets;
+  std::vector<double> qi(3 * (size_t)n_all);
+  for (int v = 0; v < n_all; ++v)
+    for (int r = 0; r < 3; ++r) qi[3 * (size_t)p.internal[v] + r] = q[3 * (size_t)v + r];
+  cudaStreamSynchronize(s->launch);
+  cudaMemcpyAsync(s->d.q_ref, qi.data(), qi.size() * sizeof(double), cudaMemcpyHostToDevice, s->work);
+  cudaMemsetAsync(s->d.dq, 0, sizeof(float) * 3 * (size_t)n_all, s->work);
+  silg::launch_local(s->d, s->work, true);
+  std::vector<float> po(9 * (size_t)T);
+  cudaMemcpyAsync(po.data(), s->d.p_out, po.size() * sizeof(float), cudaMemcpyDeviceToHost, s->work);
+  cudaError_t e = cudaStreamSynchronize(s->work);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e);
+  for (size_t k = 0; k < po.size(); ++k) pout[k] = po[k];
+  return SIM_OK;
+}
+
+int sim_get_delassus(sim_t* s, int32_t capacity, double* Wt, int32_t* cv_vertex, int32_t* n_out) {
+  if (!s || !n_out || capacity < 0) return SIM_EINVAL;
+  cudaSetDevice(s->device);
+  int st = sync_and_check(s);
+  if (st == SIM_ECUDA) return st;
+  int m = 0;
+  if (s->has_obstacles) cudaMemcpy(&m, s->d.counters + silg::kCntCv, sizeof(int), cudaMemcpyDeviceToHost);
+  m = std::min(m, s->d.cap);
+  *n_out = m;
+  if (capacity < m || m == 0) return st;
+  std::vector<float> w((size_t)m * m);
+  std::vector<int> cv(m);
+  cudaMemcpy(w.data(), s->d.wt, w.size() * sizeof(float), cudaMemcpyDeviceToHost);
+  cudaMemcpy(cv.data(), s->d.cv_vert, sizeof(int) * m, cudaMemcpyDeviceToHost);
+  const Plan& p = s->plan;
+  std::vector<int> perm(m);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::sort(perm.begin(), perm.end(), [&](int a, int b) { return p.order[cv[a]] < p.order[cv[b]]; });
+  for (int a = 0; a < m; ++a) {
+    if (cv_vertex) cv_vertex[a] = p.order[cv[perm[a]]];
+    if (Wt)
+      for (int b = 0; b < m; ++b) Wt[(size_t)a * m + b] = w[(size_t)perm[a] * m + perm[b]];
+  }
+  return st;
+}
+
+}  // extern "C"

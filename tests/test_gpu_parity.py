@@ -1,0 +1,194 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on identical seeded
+inputs. Tolerances follow from FP32 arithmetic on the device: single frames from identical
+states must agree to 1e-5 relative in positions and contact impulses."""
+import numpy as np
+import pytest
+
+import scenegen as sg
+from oracle import Oracle, OracleOptions
+from oracle.fem import FEM
+from paper_2503_15078_b300 import SimError, Simulator
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-5
+
+
+def _oracle_solve(sc, b):
+    f = FEM(sc)
+    x = np.zeros_like(b)
+    x[f.free_verts] = f.solve(b[f.free_verts].reshape(-1)).reshape(-1, 3)
+    return x
+
+
+def _relerr(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: sg.single_tet(),
+    lambda: sg.cube_drop(m=6),
+    lambda: sg.cube_drop(m=13, model=sg.MODEL_SNH, E=1e7),
+    lambda: sg.star_pull(n_side=20, layers=12),
+])
+def test_apply_inverse_matches_direct_solve(maker):
+    sc = maker()
+    sim = Simulator(sc)
+    rng = np.random.default_rng(1)
+    for trial in range(2):
+        b = rng.normal(size=(sc.n_verts, 3)) * (1.0 + 10 * trial)
+        x = sim.apply_inverse(b)
+        xr = _oracle_solve(sc, b)
+        assert _relerr(x, xr) < REL, _relerr(x, xr)
+        assert np.abs(x - xr).max() < 5 * REL * np.abs(xr).max()
+    sim.close()
+
+
+@pytest.mark.parametrize("model", [sg.MODEL_ARAP, sg.MODEL_COROT, sg.MODEL_SNH])
+def test_local_projection_matches_oracle(model):
+    sc = sg.cube_drop(m=7, model=model, E=3e5, nu=0.45)
+    q, _ = sg.perturbed_state(sc, seed=3, amp=0.004)
+    sim = Simulator(sc)
+    p = sim.local_project(q)
+    o = Oracle(sc)
+    pr = o.local_step(q)
+    # FP32 SVD rounding (~1e-7 relative) plus the FP32 Newton stopping rule
+    # |grad| <= 1e-6 (w + V (mu + lam)) for SNH, amplified by scale / w < 10 at nu = 0.45
+    err = np.abs(p - pr).max()
+    assert err < 5e-5, err
+    sim.close()
+
+
+def _frame_pair(sc, q0, v0, n_iters, n_frames=1):
+    o = Oracle(sc)
+    sim = Simulator(sc)
+    sim.set_state(q0, v0)
+    q, v = q0.copy(), v0.copy()
+    infos = []
+    for _ in range(n_frames):
+        q, v, info = o.frame(q, v, OracleOptions(n_iters=n_iters, n_cr=sc.n_cr))
+        infos.append(info)
+    sim.step(n_iters=n_iters, n_frames=n_frames)
+    qg, vg = sim.state()
+    return sim, o, (q, v, infos), (qg, vg)
+
+
+def test_frame_without_contact_matches_oracle():
+    sc = sg.cube_drop(m=8, model=sg.MODEL_SNH, E=2e5, height=1.0)
+    q0, v0 = sg.perturbed_state(sc, seed=5, amp=0.002, vel_amp=0.3)
+    sim, o, (q, v, infos), (qg, vg) = _frame_pair(sc, q0, v0, 5)
+    assert len(infos[0]["contacts"]) == 0
+    assert _relerr(qg, q) < REL
+    assert _relerr(qg - q0, q - q0) < 1e-4
+    assert _relerr(vg, v) < 1e-4
+    sim.close()
+
+
+@pytest.mark.parametrize("model", [sg.MODEL_ARAP, sg.MODEL_COROT, sg.MODEL_SNH])
+def test_frame_with_contact_matches_oracle(model):
+    sc = sg.cube_drop(m=6, model=model, height=-0.003, seed=2, mu=0.5)
+    sim, o, (q, v, infos), (qg, vg) = _frame_pair(sc, sc.q0, sc.v0, 5)
+    info = infos[0]
+    ct = sim.contacts()
+    keys_o = [(c["vertex"], c["obstacle"]) for c in info["contacts"]]
+    keys_g = list(zip(ct["vertex"].tolist(), ct["obstacle"].tolist()))
+    assert keys_g == keys_o and len(keys_o) > 3
+    assert _relerr(qg, q) < REL
+    lam_o, lam_g = info["lam"], ct["lam"]
+    assert _relerr(lam_g, lam_o) < 1e-3, _relerr(lam_g, lam_o)
+    st = sim.stats()
+    assert st["n_contacts"] == len(keys_o)
+    assert abs(st["residuals"][-1] - info["residuals"][-1]) < 1e-4 + 0.05 * info["residuals"][-1]
+    sim.close()
+
+
+def test_delassus_matches_oracle():
+    sc = sg.cube_drop(m=7, height=-0.004, seed=4)
+    sim = Simulator(sc)
+    sim.set_state(sc.q0, sc.v0)
+    sim.step(n_iters=1)
+    W, cv = sim.delassus()
+    f = FEM(sc)
+    pos = {int(v): i for i, v in enumerate(f.free_verts)}
+    E = np.zeros((3 * len(f.free_verts), len(cv)))
+    for k, v in enumerate(cv):
+        E[3 * pos[int(v)], k] = 1.0
+    X = f.solve(E)
+    Wr = E.T @ X
+    assert len(cv) > 3
+    assert np.abs(W - Wr).max() < 1e-5 * np.abs(Wr).max()
+    sim.close()
+
+
+def test_trajectory_cube_drop_matches_oracle():
+    sc = sg.cube_drop(m=6, seed=0)
+    frames = 40
+    o = Oracle(sc)
+    sim = Simulator(sc)
+    q, v = sc.q0.copy(), sc.v0.copy()
+    sim.set_state(q, v)
+    L = sc.bbox_diagonal
+    e0 = o.energy(q, v)
+    for f in range(frames):
+        q, v, info = o.frame(q, v)
+        sim.step()
+        qg, vg = sim.state()
+        assert abs(o.max_penetration(qg) - o.max_penetration(q)) <= 1e-3 * L
+        assert abs(o.energy(qg, vg) - o.energy(q, v)) <= 1e-3 * abs(e0)
+    # rolling contact is not smooth in the state, so whole trajectories drift apart at
+    # the rounding level; bound the drift, not pointwise agreement
+    assert _relerr(qg, q) < 1e-2
+    sim.close()
+
+
+def test_star_pull_frame_matches_oracle():
+    # the pulled star with pinned cap, plus one cylinder pressed 3 mm into its +y side
+    sc = sg.star_pull(n_side=16, layers=8)
+    top = int(np.argmax(sc.X[:, 1]))
+    R = 0.03
+    x, y, z = sc.X[top]
+    sc.obstacles = [sg.Obstacle(sg.OBST_CYLINDER, (x, y + R - 0.003, z), (0.0, 0.0, 1.0),
+                                radius=R, mu=0.3)] + sc.obstacles
+    v0 = np.zeros_like(sc.q0)
+    v0[:, 0] = 0.5
+    sim, o, (q, v, infos), (qg, vg) = _frame_pair(sc, sc.q0, v0, 5)
+    assert len(infos[0]["contacts"]) > 0
+    assert _relerr(qg, q) < REL
+    ct = sim.contacts()
+    assert len(ct["vertex"]) == len(infos[0]["contacts"])
+    sim.close()
+
+
+def test_determinism_and_checkpoint_replay():
+    sc = sg.cube_drop(m=6, seed=7, height=0.01)
+    sim = Simulator(sc)
+    sim.step(n_frames=5)
+    q5, v5 = sim.state()
+    sim.step(n_frames=3)
+    q8, v8 = sim.state()
+    sim.set_state(q5, v5)
+    sim.step(n_frames=3)
+    q8b, v8b = sim.state()
+    assert np.array_equal(q8, q8b) and np.array_equal(v8, v8b)
+    sim.close()
+
+
+def test_contact_capacity_overflow_is_reported():
+    sc = sg.cube_drop(m=6, height=-0.01, seed=1)
+    sim = Simulator(sc, contact_capacity=4)
+    sim.step()
+    with pytest.raises(SimError) as e:
+        sim.synchronize()
+    assert e.value.status == -5
+    sim.close()
+
+
+def test_full_size_star_global_solve():
+    # the 57k-DoF star of the benchmark: the global solve against the direct solve
+    sc = sg.star_pull()
+    sim = Simulator(sc)
+    b = np.random.default_rng(0).normal(size=(sc.n_verts, 3))
+    x = sim.apply_inverse(b)
+    xr = _oracle_solve(sc, b)
+    assert _relerr(x, xr) < REL
+    sim.close()
