@@ -122,6 +122,18 @@ class ClockSampler:
 # ----------------------------------------------------------------------------------------
 # CPU oracle timing (bounded sample): shared by cpu_baseline and the reference arm
 # ----------------------------------------------------------------------------------------
+try:
+    from threadpoolctl import threadpool_limits as _single_thread
+    _HAVE_TPC = True
+except ImportError:          # BLAS threads stay at their default; reported in "cores"
+    import contextlib
+
+    _HAVE_TPC = False
+
+    def _single_thread(_n):
+        return contextlib.nullcontext()
+
+
 class OracleTimer:
     """Times the FP64 oracle on a benchmark state: the per-frame work (detection, and W
     from a subsample of its 3c direct solves scaled to all of them) once, then full
@@ -131,12 +143,12 @@ class OracleTimer:
 
     def __init__(self, scene, q, v, n_iters, w_cols=60):
         import numpy as np
-        from threadpoolctl import threadpool_limits
         from oracle import Oracle
         from oracle import contact as C
-        self.np, self.C, self.limits = np, C, threadpool_limits
+        self.np, self.C, self.limits = np, C, _single_thread
+        self.cores = 1 if _HAVE_TPC else (os.cpu_count() or 1)
         self.scene, self.q, self.v, self.n_iters = scene, q, v, n_iters
-        with threadpool_limits(1):
+        with _single_thread(1):
             o = self.o = Oracle(scene)
             f = o.fem
             f.solve(np.zeros(len(f.free_dofs)))
@@ -187,7 +199,8 @@ class OracleTimer:
         return 1e3 * (t_iter + (self.t_detect + self.t_w) / self.n_iters)
 
     def description(self, n_timed):
-        return (f"FP64 oracle, 1 thread, star_pull state with {self.c} contacts: detection "
+        threads = "1 thread" if _HAVE_TPC else f"numpy/BLAS default threads (<= {self.cores})"
+        return (f"FP64 oracle, {threads}, star_pull state with {self.c} contacts: detection "
                 f"once, W from {self.ncols} of its {3 * self.c} direct solves scaled to all, "
                 f"{n_timed} full local-global iteration(s); per-frame work divided by "
                 f"{self.n_iters} iterations")
@@ -281,7 +294,7 @@ def run_ours(args):
         ot = OracleTimer(scene, q0, v0, n_iters)
         ts = [ot.iteration_seconds() for _ in range(2)]
         cpu = {"value": round(ot.ms_per_iteration(statistics.mean(ts)), 3), "unit": UNIT,
-               "cores": 1, "kind": "oracle", "sample": ot.description(len(ts))}
+               "cores": ot.cores, "kind": "oracle", "sample": ot.description(len(ts))}
     out = {
         "metric": METRIC,
         "value": round(mean_frame / n_iters, 5),
@@ -357,7 +370,7 @@ def run_reference(args):
     for _ in range(max(1, args.warmup)):
         ot.iteration_seconds()
     vals = [ot.ms_per_iteration(ot.iteration_seconds()) for _ in range(max(1, args.steps))]
-    desc, cores = ot.description(len(vals)), 1
+    desc, cores = ot.description(len(vals)), ot.cores
     value = statistics.mean(vals)
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT,
            "n_gpus": world, "steps": len(vals), "warmup": max(1, args.warmup),

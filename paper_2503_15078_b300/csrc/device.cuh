@@ -78,6 +78,10 @@ struct DevSim {
   const int4* p2_items;
   const int* p2_first;
   const int* p2_list;
+  const int* p1_order;
+  const int* p2_order;
+  int n_sm;         // persistent-kernel grid size
+  const float* zero;  // kTileW zeros: the load target of lanes outside a row's range
   float* p1_part;   // [n_p1][3][kRowGroup]
   float* p2_part;   // [n_p2][3][kTileW]
 
@@ -153,5 +157,6 @@ void launch_yu(const DevSim& d, cudaStream_t s);
 void launch_integrate(const DevSim& d, cudaStream_t s);
 void launch_scan(const int* in, int* out, int n, const int* n_dev, int* total, cudaStream_t s);
 int cr_setup(int* cluster_out, size_t* smem_out);
+int sinv_setup();
 
 }  // namespace silg

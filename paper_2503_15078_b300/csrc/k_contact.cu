@@ -230,8 +230,12 @@ __global__ void k_y_gather(DevSim d) {
   }
 }
 
-// W~ = Y^T Y, 64 x 64 output tiles of the lower triangle (mirrored), FP32.
+// W~ = Y^T Y, 64 x 64 output tiles of the lower triangle (mirrored), FP32. A row of Y
+// touches the tile only if its contact-vertex range meets both column blocks; the CTA
+// first compacts those rows (ranges are nested subtree intervals, so most rows below
+// the top separators drop out for off-diagonal tiles), then accumulates 16 rows at a time.
 constexpr int kWT = 64;
+constexpr int kWTRows = 4096;   // compacted rows per chunk
 __global__ void __launch_bounds__(256) k_wtilde(DevSim d) {
   const int ncv = min(d.counters[kCntCv], d.cap);
   const int ta = blockIdx.x, tb = blockIdx.y;
@@ -239,37 +243,71 @@ __global__ void __launch_bounds__(256) k_wtilde(DevSim d) {
   const int nU = d.counters[kCntU];
   if (d.y_ptr[nU] > d.cap_y) return;
   __shared__ float As[16][kWT + 4], Bs[16][kWT + 4];
+  __shared__ int rows[kWTRows];
+  __shared__ int nrows;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   float acc[4][4] = {};
   const int a0 = ta * kWT, b0 = tb * kWT;
-  for (int u0 = 0; u0 < nU; u0 += 16) {
+  const int a1 = min(a0 + kWT, ncv), b1 = min(b0 + kWT, ncv);
+  for (int chunk0 = 0; chunk0 < nU; chunk0 += kWTRows) {
     __syncthreads();
-    for (int e = threadIdx.x; e < 16 * kWT; e += 256) {
-      const int rl = e / kWT, cl = e % kWT;
-      const int u = u0 + rl;
-      float va = 0.f, vb = 0.f;
-      if (u < nU) {
-        const int clo = d.u_clo[u], len = d.u_len[u], base = d.y_ptr[u];
-        int ca = a0 + cl - clo, cb = b0 + cl - clo;
-        if (ca >= 0 && ca < len) va = d.y_val[base + ca];
-        if (cb >= 0 && cb < len) vb = d.y_val[base + cb];
+    if (threadIdx.x == 0) nrows = 0;
+    __syncthreads();
+    // deterministic compaction: ballot within warps, then warps in order
+    const int chunk1 = min(nU, chunk0 + kWTRows);
+    for (int base = chunk0; base < chunk1; base += blockDim.x) {
+      const int u = base + threadIdx.x;
+      bool keep = false;
+      if (u < chunk1) {
+        const int clo = d.u_clo[u], chi = clo + d.u_len[u];
+        keep = clo < a1 && chi > a0 && clo < b1 && chi > b0;
       }
-      As[rl][cl] = va;
-      Bs[rl][cl] = vb;
+      const unsigned ball = __ballot_sync(0xffffffffu, keep);
+      __shared__ int wcount[8];
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+      if (lane == 0) wcount[wid] = __popc(ball);
+      __syncthreads();
+      int off = nrows;
+      for (int w = 0; w < wid; ++w) off += wcount[w];
+      if (keep) rows[off + __popc(ball & ((1u << lane) - 1))] = u;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < 8; ++w) t += wcount[w];
+        nrows += t;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      float av[4], bv[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        av[q] = As[k][ty * 4 + q];
-        bv[q] = Bs[k][tx * 4 + q];
+    const int nr = nrows;
+    for (int r0 = 0; r0 < nr; r0 += 16) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < 16 * kWT; e += 256) {
+        const int rl = e / kWT, cl = e % kWT;
+        float va = 0.f, vb = 0.f;
+        if (r0 + rl < nr) {
+          const int u = rows[r0 + rl];
+          const int clo = d.u_clo[u], len = d.u_len[u], base = d.y_ptr[u];
+          const int ca = a0 + cl - clo, cb = b0 + cl - clo;
+          if (ca >= 0 && ca < len) va = d.y_val[base + ca];
+          if (cb >= 0 && cb < len) vb = d.y_val[base + cb];
+        }
+        As[rl][cl] = va;
+        Bs[rl][cl] = vb;
       }
+      __syncthreads();
 #pragma unroll
-      for (int p = 0; p < 4; ++p)
+      for (int k = 0; k < 16; ++k) {
+        float av[4], bv[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[p][q] += av[p] * bv[q];
+        for (int q = 0; q < 4; ++q) {
+          av[q] = As[k][ty * 4 + q];
+          bv[q] = Bs[k][tx * 4 + q];
+        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[p][q] += av[p] * bv[q];
+      }
     }
   }
 #pragma unroll
@@ -387,6 +425,7 @@ __global__ void k_ytz(DevSim d) {
   if (c >= ncv) return;
   if (d.yc_ptr[ncv] > d.cap_y) return;
   float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll 4
   for (int k = d.yc_ptr[c] + lane; k < d.yc_ptr[c + 1]; k += 32) {
     const float y = d.yc_val[k];
     const int a = d.yc_row[k];
@@ -480,21 +519,26 @@ __global__ void __launch_bounds__(kCrThreads) k_cr(DevSim d, int smem_bytes) {
   L.ncv = min(d.counters[kCntCv], d.cap);
   // every CTA reads the same counters, so this exit is taken by all or by none
   if (L.c == 0 || L.ncv == 0) return;
-  L.cv0 = cv_split(d, L.rank, L.R, L.c, L.ncv);
-  L.cv1 = cv_split(d, L.rank + 1, L.R, L.c, L.ncv);
-  L.j0 = L.cv0 < L.ncv ? min(d.cv_first[L.cv0], L.c) : L.c;
-  L.j1 = L.cv1 < L.ncv ? min(d.cv_first[L.cv1], L.c) : L.c;
-  if (L.j1 < L.j0) L.j1 = L.j0;
+  // split of the contact vertices over the cluster ranks, computed once per CTA
+  __shared__ int split_cv[17], split_j[17];
+  if (threadIdx.x <= L.R) {
+    const int r = threadIdx.x;
+    const int cv = cv_split(d, r, L.R, L.c, L.ncv);
+    split_cv[r] = cv;
+    split_j[r] = cv < L.ncv ? min(d.cv_first[cv], L.c) : L.c;
+  }
+  __syncthreads();
+  L.cv0 = split_cv[L.rank];
+  L.cv1 = split_cv[L.rank + 1];
+  L.j0 = split_j[L.rank];
+  L.j1 = max(split_j[L.rank + 1], L.j0);
   const int nj = L.j1 - L.j0, nv = L.cv1 - L.cv0;
   // the largest owned slice over the cluster decides, identically in every CTA, whether
   // the per-contact vectors fit in shared memory
   int nj_max = 0, nv_max = 0;
   for (int r = 0; r < L.R; ++r) {
-    const int a0 = cv_split(d, r, L.R, L.c, L.ncv), a1 = cv_split(d, r + 1, L.R, L.c, L.ncv);
-    const int b0 = a0 < L.ncv ? min(d.cv_first[a0], L.c) : L.c;
-    const int b1 = a1 < L.ncv ? min(d.cv_first[a1], L.c) : L.c;
-    nj_max = max(nj_max, max(0, b1 - b0));
-    nv_max = max(nv_max, a1 - a0);
+    nj_max = max(nj_max, max(0, split_j[r + 1] - split_j[r]));
+    nv_max = max(nv_max, split_cv[r + 1] - split_cv[r]);
   }
   // shared layout (same offsets in every CTA for the exchanged parts)
   float* dots = sm;                   // 8 floats, exchanged
@@ -563,7 +607,7 @@ __global__ void __launch_bounds__(kCrThreads) k_cr(DevSim d, int smem_bytes) {
     cl.sync();
     for (int r = 0; r < L.R; ++r) {
       if (r == L.rank) continue;
-      const int a0 = cv_split(d, r, L.R, L.c, L.ncv), a1 = cv_split(d, r + 1, L.R, L.c, L.ncv);
+      const int a0 = split_cv[r], a1 = split_cv[r + 1];
       const float* src = cl.map_shared_rank(uall, r);
       for (int e = 3 * a0 + threadIdx.x; e < 3 * a1; e += blockDim.x) uall[e] = src[e];
     }

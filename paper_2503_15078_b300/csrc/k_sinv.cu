@@ -4,11 +4,22 @@
 // on the per-vertex factor (A = A~ (x) I3, so each S~ value multiplies an x, y, z triple).
 //
 // Storage: row i holds columns [lo_i, hi_i), a superset of its elimination subtree
-// [fd(i), i] aligned to 8 values; rows are concatenated. Work is tiled into
-// kRowGroup x kTileW tiles; each lane owns fixed 4-column chunks of a tile and reads them
-// with aligned 16-byte loads. Pass-1 work items walk a row group across column tiles,
-// pass-2 items walk a column tile down a list of row groups; both emit partial sums that
-// a second kernel adds in a fixed order, so the result is deterministic.
+// [fd(i), i] aligned to 8 values; rows are concatenated. The work is cut into tiles of
+// kRowGroup rows x kTileW columns; a tile's part of a row is one contiguous, 32-byte
+// aligned run of at most 1 KB. Each warp owns kRowsPerWarp rows of a tile and each lane
+// two fixed 4-column chunks, read with 16-byte loads.
+//
+// The products are HBM-bound: every S~ value is read once per product. Throughput comes
+// from memory-level parallelism, so the inner loops issue all loads of two tiles
+// (16 x 16 bytes per lane) before any arithmetic, without branches: a lane whose chunk lies
+// outside its row's stored range loads from a small zero buffer instead, which also makes
+// masking unnecessary.
+//
+// Pass-1 work items walk one row group across up to kMaxTilesP1 column tiles (the item's
+// slice of g is staged in shared memory); pass-2 items walk one column tile down a list
+// of row groups (their row metadata and y values are staged in shared memory). Both
+// write per-item partial sums that a second kernel adds in a fixed order, so results are
+// deterministic. Items are launched largest first.
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -19,14 +30,7 @@ namespace {
 constexpr int RG = kRowGroup;
 constexpr int TW = kTileW;
 constexpr int kChunks = TW / 128;  // float4 chunks per lane per row
-
-__device__ __forceinline__ float4 ld_stream(const float* p) {
-  float4 v;
-  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "l"(p));
-  return v;
-}
+constexpr int kUnroll = 2;         // tiles in flight per warp
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -34,71 +38,82 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-struct RowRef {
-  const float* base;  // address of column 0 of the row (may point before the row)
-  int lo, hi;
-};
+__device__ __forceinline__ float dot4(const float4& a, const float4& b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+}
 
-__device__ __forceinline__ RowRef row_ref(const DevSim& d, int r) {
-  RowRef rr;
-  if (r < d.n) {
-    rr.lo = d.lo[r];
-    rr.hi = d.hi[r];
-    rr.base = d.S + (d.rowbase[r] - rr.lo);
-  } else {
-    rr.lo = rr.hi = 0;
-    rr.base = d.S;
-  }
-  return rr;
+__device__ __forceinline__ float4 ld4(const float* p) {
+  return __ldg(reinterpret_cast<const float4*>(p));
 }
 
 // z partials: item (rg, [ct0, ct1)) -> p1_part[item][comp][row in group]
-__global__ void __launch_bounds__(256) k_pass1(DevSim d) {
-  __shared__ float4 gs[3][TW / 4];
-  const int4 it = d.p1_items[blockIdx.x];
+__global__ void __launch_bounds__(256, 2) k_pass1(DevSim d) {
+  extern __shared__ __align__(16) float4 gsm[];  // [3][q4]
+  const int item = d.p1_order[blockIdx.x];
+  const int4 it = d.p1_items[item];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c_begin = it.y * TW;
+  const int q4 = (it.z - it.y) * (TW / 4);
+  for (int e = threadIdx.x; e < 3 * q4; e += blockDim.x) {
+    const int comp = e / q4, q = e % q4;
+    gsm[e] = *reinterpret_cast<const float4*>(d.gvec + comp * d.n_pad + c_begin + 4 * q);
+  }
   const int r_first = it.x * RG + warp * kRowsPerWarp;
-  RowRef rows[kRowsPerWarp];
+  const float* base[kRowsPerWarp];
+  int lo[kRowsPerWarp], hi[kRowsPerWarp];
 #pragma unroll
-  for (int k = 0; k < kRowsPerWarp; ++k) rows[k] = row_ref(d, r_first + k);
+  for (int k = 0; k < kRowsPerWarp; ++k) {
+    const int r = r_first + k;
+    if (r < d.n) {
+      lo[k] = d.lo[r];
+      hi[k] = d.hi[r];
+      base[k] = d.S + (d.rowbase[r] - lo[k]);
+    } else {
+      lo[k] = hi[k] = 0;
+      base[k] = d.S;
+    }
+  }
+  __syncthreads();
   float acc[kRowsPerWarp][3];
 #pragma unroll
   for (int k = 0; k < kRowsPerWarp; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0.f;
-  for (int ct = it.y; ct < it.z; ++ct) {
-    const int c0 = ct * TW;
-    __syncthreads();
-    if (threadIdx.x < 3 * (TW / 4)) {
-      int comp = threadIdx.x / (TW / 4), q = threadIdx.x % (TW / 4);
-      gs[comp][q] = *reinterpret_cast<const float4*>(d.gvec + comp * d.n_pad + c0 + 4 * q);
-    }
-    __syncthreads();
-    float4 g[3][kChunks];
+  for (int ct = it.y; ct < it.z; ct += kUnroll) {
+    float4 v[kUnroll][kRowsPerWarp][kChunks];
 #pragma unroll
-    for (int m = 0; m < kChunks; ++m)
-#pragma unroll
-      for (int comp = 0; comp < 3; ++comp) g[comp][m] = gs[comp][lane + 32 * m];
-#pragma unroll
-    for (int k = 0; k < kRowsPerWarp; ++k) {
+    for (int u = 0; u < kUnroll; ++u)
 #pragma unroll
       for (int m = 0; m < kChunks; ++m) {
-        const int c = c0 + 4 * lane + 128 * m;
-        if (c >= rows[k].lo && c < rows[k].hi) {
-          float4 s = ld_stream(rows[k].base + c);
+        const int c = (ct + u) * TW + 4 * lane + 128 * m;
+        const bool tile_ok = ct + u < it.z;
 #pragma unroll
-          for (int comp = 0; comp < 3; ++comp)
-            acc[k][comp] += s.x * g[comp][m].x + s.y * g[comp][m].y + s.z * g[comp][m].z +
-                            s.w * g[comp][m].w;
+        for (int k = 0; k < kRowsPerWarp; ++k) {
+          const bool ok = tile_ok && c >= lo[k] && c < hi[k];
+          v[u][k][m] = ld4(ok ? base[k] + c : d.zero + 4 * lane);
+        }
+      }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      if (ct + u >= it.z) break;
+#pragma unroll
+      for (int m = 0; m < kChunks; ++m) {
+        const int q = (ct + u - it.y) * (TW / 4) + lane + 32 * m;
+        const float4 g0 = gsm[q], g1 = gsm[q4 + q], g2 = gsm[2 * q4 + q];
+#pragma unroll
+        for (int k = 0; k < kRowsPerWarp; ++k) {
+          acc[k][0] += dot4(v[u][k][m], g0);
+          acc[k][1] += dot4(v[u][k][m], g1);
+          acc[k][2] += dot4(v[u][k][m], g2);
         }
       }
     }
   }
-  float* out = d.p1_part + (size_t)blockIdx.x * 3 * RG;
+  float* out = d.p1_part + (size_t)item * 3 * RG;
 #pragma unroll
   for (int k = 0; k < kRowsPerWarp; ++k)
 #pragma unroll
     for (int comp = 0; comp < 3; ++comp) {
-      float v = warp_sum(acc[k][comp]);
-      if (lane == 0) out[comp * RG + warp * kRowsPerWarp + k] = v;
+      const float s = warp_sum(acc[k][comp]);
+      if (lane == 0) out[comp * RG + warp * kRowsPerWarp + k] = s;
     }
 }
 
@@ -123,12 +138,44 @@ __global__ void k_reduce1(DevSim d) {
   d.zvec[2 * d.n_pad + r] = s2;
 }
 
+struct RowMeta {
+  long long base;   // offset of column 0 of the row in S~ (may precede the row)
+  int lo, hi;
+  float y0, y1, y2, pad;
+};
+
+constexpr size_t kP2Meta = sizeof(RowMeta) * kMaxGroupsP2 * RG;
+constexpr size_t kP2Smem = kP2Meta + sizeof(float) * kWarps * 3 * TW;
+
 // x partials: item (ct, row-group list) -> p2_part[item][comp][column in tile]
-__global__ void __launch_bounds__(256) k_pass2(DevSim d) {
-  __shared__ float red[kWarps][3][TW];
-  const int4 it = d.p2_items[blockIdx.x];
+__global__ void __launch_bounds__(256, 2) k_pass2(DevSim d) {
+  extern __shared__ __align__(16) unsigned char smem2[];
+  RowMeta* meta = reinterpret_cast<RowMeta*>(smem2);
+  float* red = reinterpret_cast<float*>(smem2 + kP2Meta);
+  const int item = d.p2_order[blockIdx.x];
+  const int4 it = d.p2_items[item];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c0 = it.x * TW;
+  const int nrg = it.z;
+  for (int e = threadIdx.x; e < nrg * RG; e += blockDim.x) {
+    const int r = d.p2_list[it.y + e / RG] * RG + e % RG;
+    RowMeta m;
+    if (r < d.n) {
+      m.lo = d.lo[r];
+      m.hi = d.hi[r];
+      m.base = d.rowbase[r] - m.lo;
+      m.y0 = d.zvec[r];
+      m.y1 = d.zvec[d.n_pad + r];
+      m.y2 = d.zvec[2 * d.n_pad + r];
+    } else {
+      m.lo = m.hi = 0;
+      m.base = 0;
+      m.y0 = m.y1 = m.y2 = 0.f;
+    }
+    m.pad = 0.f;
+    meta[e] = m;
+  }
+  __syncthreads();
   float acc[kChunks][3][4];
 #pragma unroll
   for (int m = 0; m < kChunks; ++m)
@@ -136,20 +183,34 @@ __global__ void __launch_bounds__(256) k_pass2(DevSim d) {
     for (int comp = 0; comp < 3; ++comp)
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[m][comp][e] = 0.f;
-  for (int li = 0; li < it.z; ++li) {
-    const int rg = d.p2_list[it.y + li];
-    const int r_first = rg * RG + warp * kRowsPerWarp;
+  for (int li = 0; li < nrg; li += kUnroll) {
+    float4 v[kUnroll][kRowsPerWarp][kChunks];
 #pragma unroll
-    for (int k = 0; k < kRowsPerWarp; ++k) {
-      const int r = r_first + k;
-      RowRef rr = row_ref(d, r);
-      if (r >= d.n) continue;
-      float y0 = d.zvec[r], y1 = d.zvec[d.n_pad + r], y2 = d.zvec[2 * d.n_pad + r];
+    for (int u = 0; u < kUnroll; ++u) {
+      const bool grp_ok = li + u < nrg;
+      const RowMeta* rm = meta + (grp_ok ? li + u : li) * RG + warp * kRowsPerWarp;
 #pragma unroll
-      for (int m = 0; m < kChunks; ++m) {
-        const int c = c0 + 4 * lane + 128 * m;
-        if (c >= rr.lo && c < rr.hi) {
-          float4 s = ld_stream(rr.base + c);
+      for (int k = 0; k < kRowsPerWarp; ++k) {
+        const int lo = rm[k].lo, hi = rm[k].hi;
+        const float* base = d.S + rm[k].base;
+#pragma unroll
+        for (int m = 0; m < kChunks; ++m) {
+          const int c = c0 + 4 * lane + 128 * m;
+          const bool ok = grp_ok && c >= lo && c < hi;
+          v[u][k][m] = ld4(ok ? base + c : d.zero + 4 * lane);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      if (li + u >= nrg) break;
+      const RowMeta* rm = meta + (li + u) * RG + warp * kRowsPerWarp;
+#pragma unroll
+      for (int k = 0; k < kRowsPerWarp; ++k) {
+        const float y0 = rm[k].y0, y1 = rm[k].y1, y2 = rm[k].y2;
+#pragma unroll
+        for (int m = 0; m < kChunks; ++m) {
+          const float4 s = v[u][k][m];
           acc[m][0][0] += s.x * y0; acc[m][0][1] += s.y * y0;
           acc[m][0][2] += s.z * y0; acc[m][0][3] += s.w * y0;
           acc[m][1][0] += s.x * y1; acc[m][1][1] += s.y * y1;
@@ -164,15 +225,15 @@ __global__ void __launch_bounds__(256) k_pass2(DevSim d) {
   for (int m = 0; m < kChunks; ++m)
 #pragma unroll
     for (int comp = 0; comp < 3; ++comp)
-      *reinterpret_cast<float4*>(&red[warp][comp][4 * lane + 128 * m]) =
+      *reinterpret_cast<float4*>(&red[(warp * 3 + comp) * TW + 4 * lane + 128 * m]) =
           make_float4(acc[m][comp][0], acc[m][comp][1], acc[m][comp][2], acc[m][comp][3]);
   __syncthreads();
-  float* out = d.p2_part + (size_t)blockIdx.x * 3 * TW;
+  float* out = d.p2_part + (size_t)item * 3 * TW;
   for (int idx = threadIdx.x; idx < 3 * TW; idx += blockDim.x) {
     const int comp = idx / TW, c = idx % TW;
     float s = 0.f;
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) s += red[w][comp][c];
+    for (int w = 0; w < kWarps; ++w) s += red[(w * 3 + comp) * TW + c];
     out[comp * TW + c] = s;
   }
 }
@@ -197,15 +258,26 @@ __global__ void k_reduce2(DevSim d) {
   out[3 * c + 2] = s2;
 }
 
+constexpr size_t kP1Smem = 3 * kMaxTilesP1 * TW * sizeof(float);
+
 }  // namespace
 
+int sinv_setup() {
+  if (cudaFuncSetAttribute(k_pass2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kP2Smem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kP1Smem) !=
+          cudaSuccess)
+    return SIM_ECUDA;
+  return SIM_OK;
+}
+
 void launch_pass1(const DevSim& d, cudaStream_t s) {
-  k_pass1<<<d.n_p1, 256, 0, s>>>(d);
+  k_pass1<<<d.n_p1, 256, kP1Smem, s>>>(d);
   k_reduce1<<<(d.n_pad + 255) / 256, 256, 0, s>>>(d);
 }
 
 void launch_pass2(const DevSim& d, cudaStream_t s, bool to_dq) {
-  k_pass2<<<d.n_p2, 256, 0, s>>>(d);
+  k_pass2<<<d.n_p2, 256, kP2Smem, s>>>(d);
   if (to_dq)
     k_reduce2<true><<<(d.n + 255) / 256, 256, 0, s>>>(d);
   else

@@ -485,7 +485,7 @@ int build_plan(const sim_mesh* mesh, const sim_material* mats, int n_mat, double
       }
       if (w == 0) continue;
       tiles_of_ct[ct].push_back({rg, (int32_t)w});
-      if (acc > 0 && acc + w > budget) {
+      if (acc > 0 && (acc + w > budget || ct - start >= kMaxTilesP1)) {
         p.p1_items.insert(p.p1_items.end(), {rg, start, ct, (int32_t)acc});
         start = ct;
         acc = 0;
@@ -504,7 +504,8 @@ int build_plan(const sim_mesh* mesh, const sim_material* mats, int n_mat, double
     int64_t acc = 0;
     int off = (int)p.p2_list.size();
     for (auto& e : L) {
-      if (acc > 0 && acc + e.second > budget) {
+      const int in_item = (int)p.p2_list.size() - off;
+      if (acc > 0 && (acc + e.second > budget || in_item >= kMaxGroupsP2)) {
         int cnt = (int)p.p2_list.size() - off;
         p.p2_items.insert(p.p2_items.end(), {ct, off, cnt, (int32_t)acc});
         off = (int)p.p2_list.size();
@@ -519,6 +520,25 @@ int build_plan(const sim_mesh* mesh, const sim_material* mats, int n_mat, double
     }
     p.p2_first[ct + 1] = (int32_t)(p.p2_items.size() / 4);
   }
+  auto by_weight = [](const std::vector<int32_t>& items, std::vector<int32_t>& order) {
+    const int m = (int)items.size() / 4;
+    order.resize(m);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return items[4 * a + 3] > items[4 * b + 3]; });
+  };
+  for (size_t k = 0; k < p.p1_items.size(); k += 4)
+    if (p.p1_items[k + 2] - p.p1_items[k + 1] > kMaxTilesP1 || p.p1_items[k + 2] <= p.p1_items[k + 1]) {
+      *err = "internal: pass-1 item spans too many column tiles";
+      return SIM_EINVAL;
+    }
+  for (size_t k = 0; k < p.p2_items.size(); k += 4)
+    if (p.p2_items[k + 2] <= 0) {
+      *err = "internal: empty pass-2 item";
+      return SIM_EINVAL;
+    }
+  by_weight(p.p1_items, p.p1_order);
+  by_weight(p.p2_items, p.p2_order);
   p.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return SIM_OK;
 }

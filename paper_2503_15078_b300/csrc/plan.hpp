@@ -23,6 +23,11 @@ constexpr int kAlign = 8;
 // Device tile shape of the two profile products: kRowGroup rows x kTileW columns.
 constexpr int kRowGroup = 32;
 constexpr int kTileW = 256;
+// Work-item limits (the kernels stage an item's vector slice and row metadata in shared
+// memory): a pass-1 item spans at most kMaxTilesP1 column tiles, a pass-2 item at most
+// kMaxGroupsP2 row groups.
+constexpr int kMaxTilesP1 = 8;
+constexpr int kMaxGroupsP2 = 32;
 
 struct MatParams {
   int model;
@@ -86,6 +91,9 @@ struct Plan {
   std::vector<int32_t> p2_items;  // 4 ints per item: ct, list_off, list_cnt, weight
   std::vector<int32_t> p2_first;  // n_ct + 1
   std::vector<int32_t> p2_list;   // row groups
+  // processing orders: items by decreasing weight (the persistent kernels deal them out
+  // round-robin, largest first)
+  std::vector<int32_t> p1_order, p2_order;
 
   // ---- statistics -----------------------------------------------------------------
   int64_t nnz_A = 0, nnz_L = 0;

@@ -263,6 +263,13 @@ int create_device(sim_s* s, const sim_obstacle* obstacles, int n_obs, const sim_
     d.p1_first = s->upload(p.p1_first);
     d.p2_first = s->upload(p.p2_first);
     d.p2_list = s->upload(p.p2_list);
+    d.p1_order = s->upload(p.p1_order);
+    d.p2_order = s->upload(p.p2_order);
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    d.n_sm = std::max(1, nsm);
+    d.zero = s->alloc<float>(silg::kTileW);
     d.p1_part = s->alloc<float>((size_t)d.n_p1 * 3 * silg::kRowGroup);
     d.p2_part = s->alloc<float>((size_t)d.n_p2 * 3 * silg::kTileW);
   }
@@ -337,6 +344,7 @@ int create_device(sim_s* s, const sim_obstacle* obstacles, int n_obs, const sim_
   d.p_out = s->alloc<float>(9 * (size_t)T);
   s->has_obstacles = n_obs > 0;
   s->wt_tiles = (cap + 63) / 64;
+  if (silg::sinv_setup() != SIM_OK) return SIM_ECUDA;
   s->ev.resize(4 + 5 * silg::kMaxIters);
   for (auto& e : s->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return SIM_ECUDA;
