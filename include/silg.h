@@ -210,6 +210,28 @@ int sim_local_project(sim_t* sim, const double* q, double* p);
 int sim_get_delassus(sim_t* sim, int32_t capacity, double* Wtilde, int32_t* cv_vertex,
                      int32_t* n_out);
 
+/*
+ * x = A^-1 g through the two profile products, for callers that cannot allocate device
+ * memory at the time of the call: real-time loops that forbid cudaMalloc (it may
+ * synchronise the device and its latency is unbounded), code running while another
+ * component captures the stream into a CUDA graph, or embedders whose device memory is
+ * all handed out by their own pool. The paper has no counterpart; it is a packaging of
+ * the global step (the same kernels as sim_apply_inverse).
+ *
+ * g, x: device pointers to n_free x 3 FP32 row-major arrays in the solver's internal row
+ * order (row k is caller vertex order[k] of sim_plan_get_ordering for the same mesh;
+ * pinned vertices have no row). stream: a cudaStream_t, or NULL for the legacy stream.
+ * The call only enqueues work and returns; it calls no allocator. Its scratch (at most
+ * 16 MiB: the padded copy of g, z = S g and the partial sums of both products) is one
+ * static device array that every GPU loading the library holds until the process exits;
+ * meshes whose scratch would exceed it get SIM_ECAPACITY. The first call on a device
+ * looks up that array's device address, so make the first call before any stream
+ * capture. Every call shares the array and overwrites all of it that it reads; calls that
+ * overlap on the GPU (for example on two streams, or from two handles on one device) race.
+ * Errors: SIM_EINVAL (null argument), SIM_ECAPACITY, SIM_ECUDA (launch failure).
+ */
+int sim_apply_inverse_noalloc(const sim_t* sim, const float* g, float* x, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

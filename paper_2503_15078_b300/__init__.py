@@ -248,6 +248,14 @@ class Simulator:
         _check(lib().sim_apply_inverse(self._h, _dptr(b), _dptr(x)), "sim_apply_inverse")
         return x
 
+    def apply_inverse_noalloc(self, g_ptr, x_ptr, stream_ptr=None):
+        """x = A^-1 g on device buffers without allocating (see sim_apply_inverse_noalloc):
+        g_ptr and x_ptr are device addresses of n_free x 3 FP32 arrays in the solver's row
+        order; the call is asynchronous on the given stream."""
+        _check(lib().sim_apply_inverse_noalloc(self._h, C.c_void_p(g_ptr), C.c_void_p(x_ptr),
+                                               C.c_void_p(stream_ptr or 0)),
+               "sim_apply_inverse_noalloc")
+
     def local_project(self, q):
         q = np.ascontiguousarray(q, dtype=np.float64).reshape(self.n_verts, 3)
         p = np.zeros((self.n_tets, 3, 3))

@@ -81,6 +81,7 @@ PROTOTYPES = {
     "sim_apply_inverse": (C.c_int, [C.c_void_p, _dp, _dp]),
     "sim_local_project": (C.c_int, [C.c_void_p, _dp, _dp]),
     "sim_get_delassus": (C.c_int, [C.c_void_p, C.c_int32, _dp, _ip, _ip]),
+    "sim_apply_inverse_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 

@@ -370,6 +370,13 @@ int guarded(F f) {
 
 }  // namespace
 
+// Device view of a simulator (for entry points compiled in other files).
+const silg::DevSim* silg_sim_devsim(const sim_t* s, int* device) {
+  if (!s) return nullptr;
+  if (device) *device = s->device;
+  return &s->d;
+}
+
 extern "C" {
 
 void silg_fill_plan_info(const silg::Plan& p, sim_plan_info* info);
