@@ -44,6 +44,7 @@ struct DevSim {
   int cap, cap_y, n_cr;
   int n_rg, n_ct, n_p1, n_p2;
   double h, margin, L_ref;
+  float h2f;        // h^2 in FP32
   double grav[3], handle_vel[3];
 
   // per vertex (internal numbering, n_all)
@@ -52,6 +53,8 @@ struct DevSim {
   double* q_ref;    // 3 n_all: q_t for free vertices, prescribed positions for pinned
   double* s_tilde;  // 3 n_all
   float* dq;        // 3 n_all: q^k - q_ref (FP32)
+  float* qr_hi;     // 3 n_all: q_ref as an unevaluated FP32 sum hi + lo (edge vectors
+  float* qr_lo;     //          of the local step are formed from it in FP32)
   double* mass;     // n_all
   const int* depth; // n (etree depth of each free row)
   const int* parent;

@@ -20,7 +20,11 @@ namespace cg = cooperative_groups;
 namespace silg {
 namespace {
 
-constexpr int kCrThreads = 512;
+constexpr int kCrThreads = 256;
+
+// W~ is stored row-major with its leading dimension padded to a multiple of 4 floats
+// (zero padding), so rows can be read with 16-byte vector loads.
+__host__ __device__ __forceinline__ int wt_ld(int ncv) { return (ncv + 3) & ~3; }
 constexpr double kTinyRel = 1e-12;
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -75,12 +79,32 @@ __device__ double obst_query(const ObstDev& o, const double* x, double* n, doubl
   return rho - o.radius;
 }
 
+// Signed distance in FP32 as a conservative filter: pairs clearly farther than the margin
+// are rejected without FP64 work; every pair within kPrefilterSlack of the margin is
+// decided by the FP64 query, exactly as in FP64 arithmetic throughout.
+constexpr float kPrefilterSlack = 1e-3f;
+__device__ __forceinline__ bool maybe_contact(const ObstDev& o, const double* x, double margin) {
+  const float px = (float)(x[0] - o.p[0]), py = (float)(x[1] - o.p[1]), pz = (float)(x[2] - o.p[2]);
+  const float ax = (float)o.a[0], ay = (float)o.a[1], az = (float)o.a[2];
+  float phi;
+  if (o.kind == SIM_OBST_PLANE) {
+    phi = ax * px + ay * py + az * pz;
+  } else {
+    const float axial = ax * px + ay * py + az * pz;
+    const float rx = px - axial * ax, ry = py - axial * ay, rz = pz - axial * az;
+    phi = sqrtf(rx * rx + ry * ry + rz * rz) - (float)o.radius;
+  }
+  const float scale = fabsf(px) + fabsf(py) + fabsf(pz) + (float)o.radius + (float)fabs(margin);
+  return phi < (float)margin + kPrefilterSlack * scale;
+}
+
 __global__ void k_collide_count(DevSim d) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n) return;
   double x[3] = {d.s_tilde[3 * i], d.s_tilde[3 * i + 1], d.s_tilde[3 * i + 2]};
   int cnt = 0;
   for (int o = 0; o < d.n_obs; ++o) {
+    if (!maybe_contact(d.obst[o], x, d.margin)) continue;
     double nn[3], ph[3];
     if (obst_query(d.obst[o], x, nn, ph) < d.margin) ++cnt;
   }
@@ -102,6 +126,7 @@ __global__ void k_collide_write(DevSim d) {
   }
   for (int o = 0; o < d.n_obs; ++o) {
     const ObstDev& ob = d.obst[o];
+    if (!maybe_contact(ob, x, d.margin)) continue;
     double n[3], ph[3];
     if (!(obst_query(ob, x, n, ph) < d.margin)) continue;
     if (j < d.cap) {
@@ -124,46 +149,54 @@ __global__ void k_collide_write(DevSim d) {
   }
 }
 
-// single-CTA exclusive scan: out[k] = sum in[0..k), out[len] = total; *total = total
+// single-CTA exclusive scan: out[k] = sum in[0..k), out[len] = total; *total = total.
+// The array is walked in coalesced tiles of 4 x blockDim elements (each thread scans four
+// consecutive values), with the running total carried from tile to tile.
 __global__ void __launch_bounds__(1024) k_scan(const int* in, int* out, int n_static,
                                                const int* n_dev, int* total) {
   __shared__ int wsum[32];
   int n = n_dev ? *n_dev : n_static;
   if (n < 0) n = 0;
-  const int T = blockDim.x, tid = threadIdx.x;
-  const int per = (n + T - 1) / T;
-  const int start = min(n, tid * per), end = min(n, start + per);
-  int local = 0;
-  for (int k = start; k < end; ++k) local += in[k];
-  const int lane = tid & 31, wid = tid >> 5;
-  int incl = local;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) wsum[wid] = incl;
-  __syncthreads();
-  if (wid == 0) {
-    int v = (lane < T / 32) ? wsum[lane] : 0;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int tile = 4 * blockDim.x;
+  int carry = 0;
+  for (int base = 0; base < n; base += tile) {
+    const int idx = base + 4 * tid;
+    int v0 = idx < n ? in[idx] : 0, v1 = idx + 1 < n ? in[idx + 1] : 0;
+    int v2 = idx + 2 < n ? in[idx + 2] : 0, v3 = idx + 3 < n ? in[idx + 3] : 0;
+    const int sum4 = v0 + v1 + v2 + v3;
+    int incl = sum4;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      int t = __shfl_up_sync(0xffffffffu, v, o);
-      if (lane >= o) v += t;
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
     }
-    wsum[lane] = v;
-  }
-  __syncthreads();
-  int run = incl - local + (wid > 0 ? wsum[wid - 1] : 0);
-  for (int k = start; k < end; ++k) {
-    int v = in[k];
-    out[k] = run;
-    run += v;
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      int w = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += t;
+      }
+      wsum[lane] = w;
+    }
+    __syncthreads();
+    int run = carry + (wid > 0 ? wsum[wid - 1] : 0) + incl - sum4;
+    if (idx < n) out[idx] = run;
+    run += v0;
+    if (idx + 1 < n) out[idx + 1] = run;
+    run += v1;
+    if (idx + 2 < n) out[idx + 2] = run;
+    run += v2;
+    if (idx + 3 < n) out[idx + 3] = run;
+    carry += wsum[31];
+    __syncthreads();
   }
   if (tid == 0) {
-    int tot = wsum[31];
-    out[n] = tot;
-    if (total) *total = tot;
+    out[n] = carry;
+    if (total) *total = carry;
   }
 }
 
@@ -233,19 +266,24 @@ __global__ void k_y_gather(DevSim d) {
 // W~ = Y^T Y, 64 x 64 output tiles of the lower triangle (mirrored), FP32. A row of Y
 // touches the tile only if its contact-vertex range meets both column blocks; the CTA
 // first compacts those rows (ranges are nested subtree intervals, so most rows below
-// the top separators drop out for off-diagonal tiles), then accumulates 16 rows at a time.
+// the top separators drop out for off-diagonal tiles), then accumulates 32 rows at a
+// time: the rows' metadata is staged once per batch, each thread owns a 4 x 4 block.
 constexpr int kWT = 64;
 constexpr int kWTRows = 4096;   // compacted rows per chunk
+constexpr int kWTBatch = 32;
 __global__ void __launch_bounds__(256) k_wtilde(DevSim d) {
   const int ncv = min(d.counters[kCntCv], d.cap);
   const int ta = blockIdx.x, tb = blockIdx.y;
   if (tb > ta || ta * kWT >= ncv) return;
   const int nU = d.counters[kCntU];
   if (d.y_ptr[nU] > d.cap_y) return;
-  __shared__ float As[16][kWT + 4], Bs[16][kWT + 4];
+  __shared__ __align__(16) float As[kWTBatch][kWT], Bs[kWTBatch][kWT];
   __shared__ int rows[kWTRows];
+  __shared__ int meta_lo[kWTBatch], meta_len[kWTBatch], meta_base[kWTBatch];
+  __shared__ int wcount[8];
   __shared__ int nrows;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   float acc[4][4] = {};
   const int a0 = ta * kWT, b0 = tb * kWT;
   const int a1 = min(a0 + kWT, ncv), b1 = min(b0 + kWT, ncv);
@@ -263,8 +301,6 @@ __global__ void __launch_bounds__(256) k_wtilde(DevSim d) {
         keep = clo < a1 && chi > a0 && clo < b1 && chi > b0;
       }
       const unsigned ball = __ballot_sync(0xffffffffu, keep);
-      __shared__ int wcount[8];
-      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
       if (lane == 0) wcount[wid] = __popc(ball);
       __syncthreads();
       int off = nrows;
@@ -279,34 +315,40 @@ __global__ void __launch_bounds__(256) k_wtilde(DevSim d) {
       __syncthreads();
     }
     const int nr = nrows;
-    for (int r0 = 0; r0 < nr; r0 += 16) {
+    for (int r0 = 0; r0 < nr; r0 += kWTBatch) {
       __syncthreads();
-      for (int e = threadIdx.x; e < 16 * kWT; e += 256) {
-        const int rl = e / kWT, cl = e % kWT;
-        float va = 0.f, vb = 0.f;
+      if (threadIdx.x < kWTBatch) {
+        const int rl = threadIdx.x;
         if (r0 + rl < nr) {
           const int u = rows[r0 + rl];
-          const int clo = d.u_clo[u], len = d.u_len[u], base = d.y_ptr[u];
-          const int ca = a0 + cl - clo, cb = b0 + cl - clo;
-          if (ca >= 0 && ca < len) va = d.y_val[base + ca];
-          if (cb >= 0 && cb < len) vb = d.y_val[base + cb];
+          meta_lo[rl] = d.u_clo[u];
+          meta_len[rl] = d.u_len[u];
+          meta_base[rl] = d.y_ptr[u];
+        } else {
+          meta_lo[rl] = 0;
+          meta_len[rl] = 0;
+          meta_base[rl] = 0;
         }
-        As[rl][cl] = va;
-        Bs[rl][cl] = vb;
       }
       __syncthreads();
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        float av[4], bv[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          av[q] = As[k][ty * 4 + q];
-          bv[q] = Bs[k][tx * 4 + q];
-        }
+#pragma unroll 4
+      for (int e = threadIdx.x; e < kWTBatch * kWT; e += 256) {
+        const int rl = e / kWT, cl = e % kWT;
+        const int clo = meta_lo[rl], len = meta_len[rl], base = meta_base[rl];
+        const int ca = a0 + cl - clo, cb = b0 + cl - clo;
+        As[rl][cl] = (ca >= 0 && ca < len) ? d.y_val[base + ca] : 0.f;
+        Bs[rl][cl] = (cb >= 0 && cb < len) ? d.y_val[base + cb] : 0.f;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int k = 0; k < kWTBatch; ++k) {
+        const float4 av = *reinterpret_cast<const float4*>(&As[k][ty * 4]);
+        const float4 bv = *reinterpret_cast<const float4*>(&Bs[k][tx * 4]);
+        const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
         for (int p = 0; p < 4; ++p)
 #pragma unroll
-          for (int q = 0; q < 4; ++q) acc[p][q] += av[p] * bv[q];
+          for (int q = 0; q < 4; ++q) acc[p][q] += a4[p] * b4[q];
       }
     }
   }
@@ -315,9 +357,12 @@ __global__ void __launch_bounds__(256) k_wtilde(DevSim d) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       int ra = a0 + ty * 4 + p, cb = b0 + tx * 4 + q;
+      const int ld = wt_ld(ncv);
       if (ra < ncv && cb < ncv) {
-        d.wt[(size_t)ra * ncv + cb] = acc[p][q];
-        d.wt[(size_t)cb * ncv + ra] = acc[p][q];
+        d.wt[(size_t)ra * ld + cb] = acc[p][q];
+        d.wt[(size_t)cb * ld + ra] = acc[p][q];
+      } else if (ta == tb && ra < ncv && cb >= ncv && cb < ld) {
+        d.wt[(size_t)ra * ld + cb] = 0.f;   // zero padding of the last column group
       }
     }
 }
@@ -328,7 +373,7 @@ __global__ void k_precond(DevSim d) {
   if (j >= c) return;
   int ncv = min(d.counters[kCntCv], d.cap);
   int cv = d.ct_cv[j];
-  double w = (cv < ncv) ? (double)d.wt[(size_t)cv * ncv + cv] : 0.0;
+  double w = (cv < ncv) ? (double)d.wt[(size_t)cv * wt_ld(ncv) + cv] : 0.0;
   d.ct_r[2 * j] = d.h * d.h * w;
   d.ct_r[2 * j + 1] = d.h * w;
   for (int r = 0; r < 3; ++r) d.ct_lam[3 * j + r] = 0.0;
@@ -418,15 +463,20 @@ __global__ void k_contact_eval(DevSim d, int k, int final_eval) {
   }
 }
 
-// (Y^T z) per contact vertex, then the Schur right-hand side h^-2 (h - J A^-1 g) per contact
-__global__ void k_ytz(DevSim d) {
-  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+// (Y^T z) per contact vertex, then the Schur right-hand side h^-2 (h - J A^-1 g) per
+// contact. One 128-thread CTA per contact vertex strides along its ancestor path and the
+// partial sums are combined in a fixed order.
+constexpr int kYtzThreads = 128;
+__global__ void __launch_bounds__(kYtzThreads) k_ytz(DevSim d) {
+  const int c = blockIdx.x;
   const int ncv = min(d.counters[kCntCv], d.cap);
   if (c >= ncv) return;
   if (d.yc_ptr[ncv] > d.cap_y) return;
+  __shared__ float part[3][kYtzThreads / 32];
   float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  const int k1 = d.yc_ptr[c + 1];
 #pragma unroll 4
-  for (int k = d.yc_ptr[c] + lane; k < d.yc_ptr[c + 1]; k += 32) {
+  for (int k = d.yc_ptr[c] + threadIdx.x; k < k1; k += kYtzThreads) {
     const float y = d.yc_val[k];
     const int a = d.yc_row[k];
     s0 += y * d.zvec[a];
@@ -436,6 +486,20 @@ __global__ void k_ytz(DevSim d) {
   s0 = warp_sum(s0);
   s1 = warp_sum(s1);
   s2 = warp_sum(s2);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    part[0][wid] = s0;
+    part[1][wid] = s1;
+    part[2][wid] = s2;
+  }
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  s0 = s1 = s2 = 0.f;
+  for (int w = 0; w < kYtzThreads / 32; ++w) {
+    s0 += part[0][w];
+    s1 += part[1][w];
+    s2 += part[2][w];
+  }
   const double ih2 = 1.0 / (d.h * d.h);
   const int j0 = d.cv_first[c], j1 = min(j0 + d.cv_nct[c], d.cap);
   for (int j = j0 + lane; j < j1; j += 32) {
@@ -454,6 +518,7 @@ __global__ void k_yu(DevSim d) {
   if (idx >= nU || d.y_ptr[nU] > d.cap_y) return;
   const int clo = d.u_clo[idx], len = d.u_len[idx], base = d.y_ptr[idx];
   float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+#pragma unroll 4
   for (int k = lane; k < len; k += 32) {
     const float y = d.y_val[base + k];
     const float* u = d.uvec + 3 * (clo + k);
@@ -495,21 +560,7 @@ __device__ int cv_split(const DevSim& d, int r, int R, int c, int ncv) {
   return lo;
 }
 
-__device__ float block_sum(float v, float* scratch) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  v = warp_sum(v);
-  __syncthreads();
-  if (lane == 0) scratch[wid] = v;
-  __syncthreads();
-  float t = 0.f;
-  if (wid == 0) {
-    t = lane < (int)(blockDim.x >> 5) ? scratch[lane] : 0.f;
-    t = warp_sum(t);
-  }
-  return t;  // valid in warp 0
-}
-
-__global__ void __launch_bounds__(kCrThreads) k_cr(DevSim d, int smem_bytes) {
+__global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) {
   extern __shared__ __align__(16) float sm[];
   cg::cluster_group cl = cg::this_cluster();
   CrLayout L;
@@ -533,32 +584,36 @@ __global__ void __launch_bounds__(kCrThreads) k_cr(DevSim d, int smem_bytes) {
   L.j0 = split_j[L.rank];
   L.j1 = max(split_j[L.rank + 1], L.j0);
   const int nj = L.j1 - L.j0, nv = L.cv1 - L.cv0;
-  // the largest owned slice over the cluster decides, identically in every CTA, whether
-  // the per-contact vectors fit in shared memory
   int nj_max = 0, nv_max = 0;
   for (int r = 0; r < L.R; ++r) {
     nj_max = max(nj_max, max(0, split_j[r + 1] - split_j[r]));
     nv_max = max(nv_max, split_cv[r + 1] - split_cv[r]);
   }
-  // shared layout (same offsets in every CTA for the exchanged parts)
-  float* dots = sm;                   // 8 floats, exchanged
-  float* scratch = sm + 8;            // 32 floats
-  float* uall = sm + 64;              // 3 ncv, own range exchanged
-  float* wloc = uall + 3 * L.ncv;     // 3 nv
-  float* vx = wloc + 3 * nv;          // per owned contact: x, r, p, Ar, Ap, rhs (3 each)
-  float* vr = vx + 3 * nj;
-  float* vp = vr + 3 * nj;
-  float* vAr = vp + 3 * nj;
-  float* vAp = vAr + 3 * nj;
-  float* Df = vAp + 3 * nj;           // 9 nj
-  float* om = Df + 9 * nj;            // 3 nj
-  float* ec = om + 3 * nj;            // 3 nj
-  float* wrows = ec + 3 * nj;         // nv x ncv if it fits
+  // shared layout (identical offsets in every CTA for the parts written remotely):
+  //   dots[16] float4  per-rank partial dot products (written by every rank)
+  //   uall[ldw] float4 u for all contact vertices (each rank writes its own range everywhere)
+  const int ldw = wt_ld(L.ncv);
+  float4* dots = reinterpret_cast<float4*>(sm);          // 16 float4
+  float4* uall = dots + 16;                              // ldw float4
+  float4* uloc = uall + ldw;                             // nv_max float4 (own slice)
+  float* wloc = reinterpret_cast<float*>(uloc + nv_max); // 3 nv
+  float* vx = wloc + 3 * nv_max;      // per owned contact: x, r, p, Ar, Ap (3 each)
+  float* vr = vx + 3 * nj_max;
+  float* vp = vr + 3 * nj_max;
+  float* vAr = vp + 3 * nj_max;
+  float* vAp = vAr + 3 * nj_max;
+  float* Df = vAp + 3 * nj_max;       // 9 nj
+  float* om = Df + 9 * nj_max;        // 3 nj
+  float* ec = om + 3 * nj_max;        // 3 nj
+  int* cvf = reinterpret_cast<int*>(ec + 3 * nj_max);   // owned cv: first local contact
+  int* cvn = cvf + nv_max;                              // owned cv: contact count
+  int* ctl = cvn + nv_max;                              // owned contact: local cv index
+  // nv x ldw rows of W~ if they fit, 16-byte aligned for vector loads
+  float* wrows = sm + ((((reinterpret_cast<float*>(ctl + nj_max)) - sm) + 3) & ~size_t(3));
   const size_t used = (size_t)(wrows - sm) * sizeof(float);
-  const size_t used_max = (size_t)(64 + 3 * L.ncv + 3 * nv_max + 30 * nj_max) * sizeof(float);
-  const bool w_in_smem = used + (size_t)nv * L.ncv * sizeof(float) <= (size_t)smem_bytes;
-  const float* wsrc = w_in_smem ? wrows : d.wt + (size_t)L.cv0 * L.ncv;
-  if (used_max > (size_t)smem_bytes) {
+  const bool w_in_smem = used + (size_t)nv * ldw * sizeof(float) <= (size_t)smem_bytes;
+  const float* wsrc = w_in_smem ? wrows : d.wt + (size_t)L.cv0 * ldw;
+  if (used > (size_t)smem_bytes) {   // uniform: depends only on cluster-wide maxima
     if (threadIdx.x == 0 && L.rank == 0) atomicOr(d.err, kErrCapacity);
     cl.sync();
     return;
@@ -571,116 +626,139 @@ __global__ void __launch_bounds__(kCrThreads) k_cr(DevSim d, int smem_bytes) {
     ec[e] = d.ct_ecal[3 * j + e % 3];
   }
   for (int e = threadIdx.x; e < 9 * nj; e += blockDim.x) Df[e] = d.ct_Df[9 * L.j0 + e];
-  if (w_in_smem) {
-    const float4* src = reinterpret_cast<const float4*>(d.wt + (size_t)L.cv0 * L.ncv);
-    const size_t total = (size_t)nv * L.ncv;
-    if ((((size_t)L.cv0 * L.ncv) & 3) == 0 && (reinterpret_cast<size_t>(wrows) & 15) == 0) {
-      for (size_t e = threadIdx.x; e < total / 4; e += blockDim.x)
-        reinterpret_cast<float4*>(wrows)[e] = src[e];
-      for (size_t e = (total / 4) * 4 + threadIdx.x; e < total; e += blockDim.x)
-        wrows[e] = d.wt[(size_t)L.cv0 * L.ncv + e];
-    } else {
-      for (size_t e = threadIdx.x; e < total; e += blockDim.x)
-        wrows[e] = d.wt[(size_t)L.cv0 * L.ncv + e];
-    }
+  for (int cvl = threadIdx.x; cvl < nv; cvl += blockDim.x) {
+    const int jb = max(0, d.cv_first[L.cv0 + cvl] - L.j0);
+    cvf[cvl] = jb;
+    cvn[cvl] = max(0, min(nj, jb + d.cv_nct[L.cv0 + cvl]) - jb);
   }
-  __syncthreads();
+  for (int jl = threadIdx.x; jl < nj; jl += blockDim.x)
+    ctl[jl] = min(max(d.ct_cv[L.j0 + jl] - L.cv0, 0), max(nv - 1, 0));
+  for (int e = L.ncv + threadIdx.x; e < ldw; e += blockDim.x) uall[e] = make_float4(0, 0, 0, 0);
+  if (w_in_smem) {
+    const float4* src = reinterpret_cast<const float4*>(d.wt + (size_t)L.cv0 * ldw);
+    float4* dst = reinterpret_cast<float4*>(wrows);
+    const size_t total4 = (size_t)nv * ldw / 4;
+    for (size_t e = threadIdx.x; e < total4; e += blockDim.x) dst[e] = src[e];
+  }
+  // every CTA of the cluster must be running before shared memory is written remotely
+  cl.sync();
 
-  // K v -> Kv for the owned contacts
+  // Kv = K v for the owned contacts; v must be complete in shared memory on entry
   auto apply = [&](const float* v, float* Kv) {
     for (int cvl = threadIdx.x; cvl < nv; cvl += blockDim.x) {
-      const int cv = L.cv0 + cvl;
       float u0 = 0.f, u1 = 0.f, u2 = 0.f;
-      const int jb = max(0, d.cv_first[cv] - L.j0), je = min(nj, jb + d.cv_nct[cv]);
+      const int jb = cvf[cvl], je = jb + cvn[cvl];
       for (int jl = jb; jl < je; ++jl) {
         const float* D = Df + 9 * jl;
-        float a0 = om[3 * jl] * v[3 * jl], a1 = om[3 * jl + 1] * v[3 * jl + 1],
-              a2 = om[3 * jl + 2] * v[3 * jl + 2];
+        const float a0 = om[3 * jl] * v[3 * jl], a1 = om[3 * jl + 1] * v[3 * jl + 1],
+                    a2 = om[3 * jl + 2] * v[3 * jl + 2];
         u0 += D[0] * a0 + D[3] * a1 + D[6] * a2;
         u1 += D[1] * a0 + D[4] * a1 + D[7] * a2;
         u2 += D[2] * a0 + D[5] * a1 + D[8] * a2;
       }
-      uall[3 * cv] = u0;
-      uall[3 * cv + 1] = u1;
-      uall[3 * cv + 2] = u2;
-    }
-    cl.sync();
-    for (int r = 0; r < L.R; ++r) {
-      if (r == L.rank) continue;
-      const int a0 = split_cv[r], a1 = split_cv[r + 1];
-      const float* src = cl.map_shared_rank(uall, r);
-      for (int e = 3 * a0 + threadIdx.x; e < 3 * a1; e += blockDim.x) uall[e] = src[e];
+      uloc[cvl] = make_float4(u0, u1, u2, 0.f);
     }
     __syncthreads();
+    // one 16-byte remote store per (rank, owned vertex), spread over all threads
+    for (int e = threadIdx.x; e < L.R * nv; e += blockDim.x) {
+      const int r = e / nv, cvl = e - r * nv;
+      cl.map_shared_rank(uall, r)[L.cv0 + cvl] = uloc[cvl];
+    }
+    cl.sync();   // every rank's slice of u is now in every CTA
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int cvl = warp; cvl < nv; cvl += nw) {
-      const float* wr = wsrc + (size_t)cvl * L.ncv;
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-      for (int k = lane; k < L.ncv; k += 32) {
-        const float w = wr[k];
-        s0 += w * uall[3 * k];
-        s1 += w * uall[3 * k + 1];
-        s2 += w * uall[3 * k + 2];
+    const int ng = ldw / 4;
+    // four rows per warp at a time, so the shuffle reductions of the rows overlap
+    for (int row0 = 4 * warp; row0 < nv; row0 += 4 * nw) {
+      float acc[4][3] = {};
+      const int nrow = min(4, nv - row0);
+      for (int g4 = lane; g4 < ng; g4 += 32) {
+        const float4 a = uall[4 * g4], b = uall[4 * g4 + 1], c = uall[4 * g4 + 2],
+                     e = uall[4 * g4 + 3];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (k < nrow) {
+            const float4 w = reinterpret_cast<const float4*>(wsrc + (size_t)(row0 + k) * ldw)[g4];
+            acc[k][0] += w.x * a.x + w.y * b.x + w.z * c.x + w.w * e.x;
+            acc[k][1] += w.x * a.y + w.y * b.y + w.z * c.y + w.w * e.y;
+            acc[k][2] += w.x * a.z + w.y * b.z + w.z * c.z + w.w * e.z;
+          }
+        }
       }
-      s0 = warp_sum(s0);
-      s1 = warp_sum(s1);
-      s2 = warp_sum(s2);
-      if (lane == 0) {
-        wloc[3 * cvl] = s0;
-        wloc[3 * cvl + 1] = s1;
-        wloc[3 * cvl + 2] = s2;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) acc[k][q] = warp_sum(acc[k][q]);
+      if (lane < 3 * nrow) {
+        const int k = lane / 3, q = lane % 3;
+        float val = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+          for (int qq = 0; qq < 3; ++qq)
+            if (kk == k && qq == q) val = acc[kk][qq];
+        wloc[3 * (row0 + k) + q] = val;
       }
     }
     __syncthreads();
     for (int e = threadIdx.x; e < 3 * nj; e += blockDim.x) {
       const int jl = e / 3, r = e % 3;
-      const int cvl = min(max(d.ct_cv[L.j0 + jl] - L.cv0, 0), max(nv - 1, 0));
+      const int cvl = ctl[jl];
       const float* D = Df + 9 * jl + 3 * r;
       const float dw = D[0] * wloc[3 * cvl] + D[1] * wloc[3 * cvl + 1] + D[2] * wloc[3 * cvl + 2];
       Kv[e] = om[e] * dw + ec[e] * v[e];
     }
-    __syncthreads();
   };
-  // cluster-wide sums of up to 3 values, identical in every CTA
-  __shared__ float red_out[4];
-  auto exchange = [&](float a, float b, float c3, int nvals) {
-    float sa = block_sum(a, scratch);
-    float sb = nvals > 1 ? block_sum(b, scratch) : 0.f;
-    float sc = nvals > 2 ? block_sum(c3, scratch) : 0.f;
-    if (threadIdx.x == 0) {
-      dots[0] = sa;
-      dots[1] = sb;
-      dots[2] = sc;
+  // cluster-wide sums of three values. Per warp, then per CTA in warp 0, then over the
+  // ranks in warp 0 of every CTA: the same shuffle tree on the same values everywhere, so
+  // every CTA holds identical scalars (deterministic).
+  __shared__ float wpart[3][32];
+  __shared__ float red3[3];
+  auto exchange = [&](float& a, float& b, float& c) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_sum(c);
+    if (lane == 0) {
+      wpart[0][wid] = a;
+      wpart[1][wid] = b;
+      wpart[2][wid] = c;
+    }
+    __syncthreads();
+    if (wid == 0) {
+      a = warp_sum(lane < nw ? wpart[0][lane] : 0.f);
+      b = warp_sum(lane < nw ? wpart[1][lane] : 0.f);
+      c = warp_sum(lane < nw ? wpart[2][lane] : 0.f);
+      if (lane < L.R) cl.map_shared_rank(dots, lane)[L.rank] = make_float4(a, b, c, 0.f);
     }
     cl.sync();
-    if (threadIdx.x < 32) {
-      const int lane = threadIdx.x;
-      float t[3] = {0.f, 0.f, 0.f};
-      if (lane < L.R) {
-        const float* src = cl.map_shared_rank(dots, lane);
-        t[0] = src[0];
-        t[1] = src[1];
-        t[2] = src[2];
-      }
-      for (int q = 0; q < 3; ++q) {
-        float v = warp_sum(t[q]);
-        if (lane == 0) red_out[q] = v;
+    if (wid == 0) {
+      const float4 t = lane < L.R ? dots[lane] : make_float4(0, 0, 0, 0);
+      a = warp_sum(t.x);
+      b = warp_sum(t.y);
+      c = warp_sum(t.z);
+      if (lane == 0) {
+        red3[0] = a;
+        red3[1] = b;
+        red3[2] = c;
       }
     }
     __syncthreads();
+    a = red3[0];
+    b = red3[1];
+    c = red3[2];
   };
 
   // r = rhs, x = 0, p = r, Ap = Ar
   apply(vr, vAr);
-  float pa = 0.f, pb = 0.f;
+  float s1 = 0.f, s2 = 0.f, s3 = 0.f;
   for (int e = threadIdx.x; e < 3 * nj; e += blockDim.x) {
     vp[e] = vr[e];
     vAp[e] = vAr[e];
-    pa += vr[e] * vAr[e];
-    pb += vAr[e] * vAr[e];
+    s1 += vr[e] * vAr[e];
+    s2 += vAr[e] * vAr[e];
   }
-  exchange(pa, pb, 0.f, 2);
-  float rAr = red_out[0], ApAp = red_out[1];
+  exchange(s1, s2, s3);
+  float rAr = s1, ApAp = s2;
   for (int it = 0; it < d.n_cr; ++it) {
     if (!(ApAp > 0.f)) break;
     const float alpha = rAr / ApAp;
@@ -690,14 +768,14 @@ __global__ void __launch_bounds__(kCrThreads) k_cr(DevSim d, int smem_bytes) {
     }
     __syncthreads();
     apply(vr, vAr);
-    float s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    s1 = s2 = s3 = 0.f;
     for (int e = threadIdx.x; e < 3 * nj; e += blockDim.x) {
       s1 += vr[e] * vAr[e];
       s2 += vAr[e] * vAr[e];
       s3 += vAr[e] * vAp[e];
     }
-    exchange(s1, s2, s3, 3);
-    const float rAr_new = red_out[0], ArAr = red_out[1], ArAp = red_out[2];
+    exchange(s1, s2, s3);
+    const float rAr_new = s1, ArAr = s2, ArAp = s3;
     const float beta = rAr != 0.f ? rAr_new / rAr : 0.f;
     ApAp = ArAr + 2.f * beta * ArAp + beta * beta * ApAp;
     rAr = rAr_new;
@@ -705,18 +783,18 @@ __global__ void __launch_bounds__(kCrThreads) k_cr(DevSim d, int smem_bytes) {
       vp[e] = vr[e] + beta * vp[e];
       vAp[e] = vAr[e] + beta * vAp[e];
     }
-    __syncthreads();
   }
+  __syncthreads();
   // lambda += dlambda; u = D^T (omega * dlambda) per owned contact vertex
   for (int e = threadIdx.x; e < 3 * nj; e += blockDim.x) d.ct_lam[3 * L.j0 + e] += (double)vx[e];
   for (int cvl = threadIdx.x; cvl < nv; cvl += blockDim.x) {
     const int cv = L.cv0 + cvl;
     float u0 = 0.f, u1 = 0.f, u2 = 0.f;
-    const int jb = max(0, d.cv_first[cv] - L.j0), je = min(nj, jb + d.cv_nct[cv]);
+    const int jb = cvf[cvl], je = jb + cvn[cvl];
     for (int jl = jb; jl < je; ++jl) {
       const float* D = Df + 9 * jl;
-      float a0 = om[3 * jl] * vx[3 * jl], a1 = om[3 * jl + 1] * vx[3 * jl + 1],
-            a2 = om[3 * jl + 2] * vx[3 * jl + 2];
+      const float a0 = om[3 * jl] * vx[3 * jl], a1 = om[3 * jl + 1] * vx[3 * jl + 1],
+                  a2 = om[3 * jl + 2] * vx[3 * jl + 2];
       u0 += D[0] * a0 + D[3] * a1 + D[6] * a2;
       u1 += D[1] * a0 + D[4] * a1 + D[7] * a2;
       u2 += D[2] * a0 + D[5] * a1 + D[8] * a2;
@@ -725,7 +803,7 @@ __global__ void __launch_bounds__(kCrThreads) k_cr(DevSim d, int smem_bytes) {
     d.uvec[3 * cv + 1] = u1;
     d.uvec[3 * cv + 2] = u2;
   }
-  cl.sync();  // no CTA leaves while another may still read its shared memory
+  cl.sync();  // no CTA leaves while another may still write into its shared memory
 }
 
 }  // namespace
@@ -735,11 +813,11 @@ void launch_scan(const int* in, int* out, int n, const int* n_dev, int* total, c
 }
 
 void launch_collide(const DevSim& d, cudaStream_t s) {
-  const int g = (d.n + 255) / 256;
-  k_collide_count<<<g, 256, 0, s>>>(d);
+  const int g = (d.n + 63) / 64;
+  k_collide_count<<<g, 64, 0, s>>>(d);
   launch_scan(d.ct_cnt, d.ct_off, d.n, nullptr, d.counters + kCntContacts, s);
   launch_scan(d.cv_flag, d.cv_off, d.n, nullptr, d.counters + kCntCv, s);
-  k_collide_write<<<g, 256, 0, s>>>(d);
+  k_collide_write<<<g, 64, 0, s>>>(d);
 }
 
 void launch_delassus(const DevSim& d, cudaStream_t s, int wt_tiles) {
@@ -757,11 +835,12 @@ void launch_delassus(const DevSim& d, cudaStream_t s, int wt_tiles) {
 }
 
 void launch_contact_eval(const DevSim& d, cudaStream_t s, int k, bool final_eval) {
-  k_contact_eval<<<(d.cap + 127) / 128, 128, 0, s>>>(d, k, final_eval ? 1 : 0);
+  // FP64-heavy and short: small CTAs spread the contacts over many SMs
+  k_contact_eval<<<(d.cap + 31) / 32, 32, 0, s>>>(d, k, final_eval ? 1 : 0);
 }
 
 void launch_ytz(const DevSim& d, cudaStream_t s) {
-  k_ytz<<<(d.cap * 32 + 255) / 256, 256, 0, s>>>(d);
+  k_ytz<<<d.cap, kYtzThreads, 0, s>>>(d);
 }
 
 void launch_yu(const DevSim& d, cudaStream_t s) {

@@ -1,13 +1,15 @@
 // Local step (Eq. 5) per tetrahedron, right-hand-side assembly (Eq. 6), frame start
 // (prediction, Eq. 1) and integration (Alg. 4, last two lines).
 //
-// The local step forms F = D_s D_m^-1 from FP64 positions (edge differences in FP64,
-// rounded once to FP32), computes the signed SVD by one-sided Jacobi rotations
+// The local step forms F = D_s D_m^-1 from the frame's reference positions plus the
+// iterate's FP32 displacement, computes the signed SVD by one-sided Jacobi rotations
 // (Hestenes 1958; 3x3 columns orthogonalised pairwise, quadratic convergence), and
 // projects the singular values per material:
 //   ARAP          sigma_hat = (1, 1, 1)                     (PD indicator of SO(3))
 //   co-rotational closed form of a linear 3x3 system in sigma
 //   stable NH     Newton in sigma-space with backtracking (<= 20 steps, FP32)
+// The frame's reference positions are kept as two FP32 words (hi + lo), so edge vectors
+// x_a - x_0 are formed in FP32 as (hi_a - hi_0) + (lo_a - lo_0) without FP64 arithmetic.
 // It then writes h^2 w_i (p_i - F_ref) g_a for the four corners a, where F_ref is the
 // deformation gradient of the frame's reference state q_ref; the RHS is assembled in
 // displacement form b - A q_ref, so the global solve yields q - q_ref directly.
@@ -216,6 +218,12 @@ __device__ void project_tet(const float* F, int model, float w, float V, float m
                      U[3 * r + 2] * sh[2] * Vm[3 * c + 2];
 }
 
+__device__ __forceinline__ void split_ref(const DevSim& d, int i, int r, double q) {
+  const float hi = (float)q;
+  d.qr_hi[3 * i + r] = hi;
+  d.qr_lo[3 * i + r] = (float)(q - (double)hi);
+}
+
 __global__ void k_frame_begin(DevSim d) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n_all) return;
@@ -228,13 +236,23 @@ __global__ void k_frame_begin(DevSim d) {
       d.s_tilde[3 * i + r] = st;
       d.q_ref[3 * i + r] = qt;
       d.dq[3 * i + r] = (float)(st - qt);
+      split_ref(d, i, r, qt);
     } else {
       double qp = qt + h * d.handle_vel[r];
       d.s_tilde[3 * i + r] = qp;
       d.q_ref[3 * i + r] = qp;
       d.dq[3 * i + r] = 0.f;
+      split_ref(d, i, r, qp);
     }
   }
+}
+
+// q_ref -> (hi, lo) for callers that set q_ref directly (component entry points)
+__global__ void k_split_ref(DevSim d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n_all) return;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) split_ref(d, i, r, d.q_ref[3 * i + r]);
 }
 
 template <bool kDebug>
@@ -255,11 +273,11 @@ __global__ void __launch_bounds__(128) k_local(DevSim d) {
     g[3][c] = Mi[6 + c];
     g[0][c] = -(g[1][c] + g[2][c] + g[3][c]);
   }
-  double x0[3];
-  float dq0[3];
+  float h0[3], l0[3], dq0[3];
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    x0[r] = d.q_ref[3 * vv[0] + r];
+    h0[r] = d.qr_hi[3 * vv[0] + r];
+    l0[r] = d.qr_lo[3 * vv[0] + r];
     dq0[r] = d.dq[3 * vv[0] + r];
   }
   float Fr[9], F[9];
@@ -269,7 +287,7 @@ __global__ void __launch_bounds__(128) k_local(DevSim d) {
   for (int a = 1; a < 4; ++a) {
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-      float er = (float)(d.q_ref[3 * vv[a] + r] - x0[r]);
+      float er = (d.qr_hi[3 * vv[a] + r] - h0[r]) + (d.qr_lo[3 * vv[a] + r] - l0[r]);
       float ed = d.dq[3 * vv[a] + r] - dq0[r];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -287,7 +305,7 @@ __global__ void __launch_bounds__(128) k_local(DevSim d) {
     for (int k = 0; k < 9; ++k) d.p_out[9 * t + k] = p[k];
     return;
   }
-  const float s = (float)(d.h * d.h) * w;
+  const float s = d.h2f * w;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     float o[3];
@@ -358,10 +376,12 @@ void launch_frame_begin(const DevSim& d, cudaStream_t s) {
 
 void launch_local(const DevSim& d, cudaStream_t s, bool debug_p) {
   int grid = (d.n_tets + 127) / 128;
-  if (debug_p)
+  if (debug_p) {
+    k_split_ref<<<(d.n_all + 255) / 256, 256, 0, s>>>(d);
     k_local<true><<<grid, 128, 0, s>>>(d);
-  else
+  } else {
     k_local<false><<<grid, 128, 0, s>>>(d);
+  }
 }
 
 void launch_rhs(const DevSim& d, cudaStream_t s) {

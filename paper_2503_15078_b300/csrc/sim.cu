@@ -173,6 +173,7 @@ int create_device(sim_s* s, const sim_obstacle* obstacles, int n_obs, const sim_
   d.cap = std::max(1, o->contact_capacity);
   d.n_cr = std::max(0, o->n_cr_iters);
   d.h = p.h;
+  d.h2f = (float)(p.h * p.h);
   for (int r = 0; r < 3; ++r) {
     d.grav[r] = o->gravity[r];
     d.handle_vel[r] = p.handle_vel[r];
@@ -201,6 +202,8 @@ int create_device(sim_s* s, const sim_obstacle* obstacles, int n_obs, const sim_
   d.q_ref = s->upload(X);
   d.s_tilde = s->upload(X);
   d.dq = s->alloc<float>(3 * (size_t)n_all);
+  d.qr_hi = s->alloc<float>(3 * (size_t)n_all);
+  d.qr_lo = s->alloc<float>(3 * (size_t)n_all);
   d.depth = s->upload(p.depth);
   d.parent = s->upload(p.parent);
   d.first_desc = s->upload(p.first_desc);
@@ -337,7 +340,7 @@ int create_device(sim_s* s, const sim_obstacle* obstacles, int n_obs, const sim_
   d.yc_ptr = s->alloc<int>(cap + 1);
   d.yc_val = s->alloc<float>(cap_y);
   d.yc_row = s->alloc<int>(cap_y);
-  d.wt = s->alloc<float>((size_t)cap * cap);
+  d.wt = s->alloc<float>((size_t)cap * ((cap + 3) & ~3));
   d.resid = s->alloc<double>(silg::kMaxIters + 1);
   d.max_pen = s->alloc<double>(1);
   d.err = s->alloc<int>(1);
@@ -632,7 +635,8 @@ int sim_get_delassus(sim_t* s, int32_t capacity, double* Wt, int32_t* cv_vertex,
   m = std::min(m, s->d.cap);
   *n_out = m;
   if (capacity < m || m == 0) return st;
-  std::vector<float> w((size_t)m * m);
+  const int ld = (m + 3) & ~3;   // padded leading dimension of the device copy
+  std::vector<float> w((size_t)m * ld);
   std::vector<int> cv(m);
   cudaMemcpy(w.data(), s->d.wt, w.size() * sizeof(float), cudaMemcpyDeviceToHost);
   cudaMemcpy(cv.data(), s->d.cv_vert, sizeof(int) * m, cudaMemcpyDeviceToHost);
@@ -643,7 +647,7 @@ int sim_get_delassus(sim_t* s, int32_t capacity, double* Wt, int32_t* cv_vertex,
   for (int a = 0; a < m; ++a) {
     if (cv_vertex) cv_vertex[a] = p.order[cv[perm[a]]];
     if (Wt)
-      for (int b = 0; b < m; ++b) Wt[(size_t)a * m + b] = w[(size_t)perm[a] * m + perm[b]];
+      for (int b = 0; b < m; ++b) Wt[(size_t)a * m + b] = w[(size_t)perm[a] * ld + perm[b]];
   }
   return st;
 }
