@@ -87,7 +87,12 @@ typedef struct {
   int32_t n_iters;             /* local-global iterations per frame (default 5)           */
   int32_t n_cr_iters;          /* conjugate-residual iterations per solve (default 10)    */
   int32_t s_precision;         /* SIM_S_FP32 (default) or SIM_S_BF16                      */
-  int32_t refine;              /* BF16 only: one FP32 residual-correction pass (default 1)*/
+  int32_t refine;              /* BF16 only: residual correction x += S~^T S~ (b - A~ x),
+                                  the residual summed in FP64 from the FP32 iterate, after
+                                  the global step of the last iteration of
+                                  each frame (1, default), of every iteration (2), or never
+                                  (0). Each correction costs one A~ product and two more
+                                  profile products. Other values: SIM_EINVAL.            */
   int32_t contact_capacity;    /* max contacts per frame (default 4096)                   */
   int32_t device;              /* CUDA device ordinal (default 0)                          */
   double gravity[3];           /* default (0, 0, -9.81)                                    */
@@ -199,7 +204,8 @@ int sim_get_plan_info(const sim_t* sim, sim_plan_info* info);
 int sim_get_phase_times(sim_t* sim, double* ms);
 
 /* ---- component entry points (parity and profiling) ------------------------------- */
-/* x = A^-1 b with the device profile products (Eq. 8). b, x as in the host variant. */
+/* x = A^-1 b with the device profile products (Eq. 8). b, x as in the host variant. With
+ * a BF16 profile and refine > 0, one residual correction follows (see sim_options). */
 int sim_apply_inverse(sim_t* sim, const double* b, double* x);
 /* Local step (Eq. 5) on the device for positions q (n_verts x 3): p (n_tets x 9,
  * row-major F-shaped projections, caller tet order). */
@@ -216,7 +222,8 @@ int sim_get_delassus(sim_t* sim, int32_t capacity, double* Wtilde, int32_t* cv_v
  * synchronise the device and its latency is unbounded), code running while another
  * component captures the stream into a CUDA graph, or embedders whose device memory is
  * all handed out by their own pool. The paper has no counterpart; it is a packaging of
- * the global step (the same kernels as sim_apply_inverse).
+ * the global step (the same kernels as sim_apply_inverse). It always reads the FP32
+ * profile, which the device holds in either s_precision mode, and applies no correction.
  *
  * g, x: device pointers to n_free x 3 FP32 row-major arrays in the solver's internal row
  * order (row k is caller vertex order[k] of sim_plan_get_ordering for the same mesh;

@@ -71,8 +71,16 @@ struct DevSim {
   const int* inc_ptr;      // n + 1: incidences of free vertex i
   const int* inc_idx;      // entries 4 t + a
 
-  // S~ profile
+  // S~ profile (FP32 values, or BF16 bit patterns when s_bf16 is set)
   const float* S;
+  const unsigned short* Sb;
+  int s_bf16;
+  int refine;       // BF16 residual correction: 0 none, 1 last iteration, 2 every iteration
+  // A~ over the free vertices (CSR, internal numbering, FP64): the residual of a solve
+  const int* A_ptr;
+  const int* A_idx;
+  const double* A_val;
+  float* gsave;     // 3 n_pad SoA: right-hand side of the residual-correction solve
   const long long* rowbase;
   const int* lo;
   const int* hi;
@@ -153,7 +161,13 @@ void launch_local(const DevSim& d, cudaStream_t s, bool debug_p);
 void launch_contact_eval(const DevSim& d, cudaStream_t s, int k, bool final_eval);
 void launch_rhs(const DevSim& d, cudaStream_t s);
 void launch_pass1(const DevSim& d, cudaStream_t s);
-void launch_pass2(const DevSim& d, cudaStream_t s, bool to_dq);
+// pass-2 output: write dq or xout, or add into them (residual correction)
+enum { kOutDq = 0, kOutX = 1, kOutAddDq = 2, kOutAddX = 3 };
+void launch_pass2(const DevSim& d, cudaStream_t s, int out_mode);
+// residual of a global solve into gsave: gsave - A xout (kResApply), g - A dq (kResFrame),
+// g + h^2 J^T dlambda - A dq (kResFrameContact)
+enum { kResApply = 0, kResFrame = 1, kResFrameContact = 2 };
+void launch_residual(const DevSim& d, cudaStream_t s, int mode);
 void launch_ytz(const DevSim& d, cudaStream_t s);
 int launch_cr(const DevSim& d, cudaStream_t s, int cluster);
 void launch_yu(const DevSim& d, cudaStream_t s);

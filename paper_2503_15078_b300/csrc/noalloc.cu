@@ -44,6 +44,7 @@ extern "C" int sim_apply_inverse_noalloc(const sim_t* sim, const float* g, float
   const silg::DevSim* src = silg_sim_devsim(sim, &dev);
   if (!src || dev < 0 || dev >= kMaxDevices) return SIM_EINVAL;
   silg::DevSim d = *src;
+  d.s_bf16 = 0;  // always the FP32 profile (kept on the device in either precision mode)
   const size_t n_vec = align_up(3 * (size_t)d.n_pad, 64);
   const size_t n_p1 = align_up((size_t)d.n_p1 * 3 * silg::kRowGroup, 64);
   const size_t n_p2 = align_up((size_t)d.n_p2 * 3 * silg::kTileW, 64);
@@ -63,6 +64,6 @@ extern "C" int sim_apply_inverse_noalloc(const sim_t* sim, const float* g, float
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   k_rows_to_soa<<<(d.n_pad + 255) / 256, 256, 0, s>>>(g, d.gvec, d.n, d.n_pad);
   silg::launch_pass1(d, s);
-  silg::launch_pass2(d, s, false);
+  silg::launch_pass2(d, s, silg::kOutX);
   return cudaGetLastError() == cudaSuccess ? SIM_OK : SIM_ECUDA;
 }

@@ -98,9 +98,16 @@ int sync_and_check(sim_s* s) {
   return err_status(bits);
 }
 
+// iterations of a K-iteration frame that end with a residual correction (BF16 profile)
+int refined_iters(const sim_s* s, int K) {
+  if (!s->d.s_bf16 || s->d.refine <= 0) return 0;
+  return s->d.refine >= 2 ? K : 1;
+}
+
 int kernels_per_frame(const sim_s* s, int K) {
   const bool c = s->has_obstacles;
-  return 1 + (c ? 4 + 9 : 0) + K * (1 + (c ? 1 : 0) + 1 + 2 + (c ? 3 : 0) + 2) + (c ? 1 : 0) + 1;
+  return 1 + (c ? 4 + 9 : 0) + K * (1 + (c ? 1 : 0) + 1 + 2 + (c ? 3 : 0) + 2) + (c ? 1 : 0) + 1 +
+         5 * refined_iters(s, K);
 }
 
 void enqueue_frame(sim_s* s, int K, cudaStream_t st) {
@@ -130,7 +137,16 @@ void enqueue_frame(sim_s* s, int K, cudaStream_t st) {
       silg::launch_yu(d, st);
     }
     mark(e + 3);
-    silg::launch_pass2(d, st, true);
+    silg::launch_pass2(d, st, silg::kOutDq);
+    if (k >= K - refined_iters(s, K)) {
+      // BF16 profile: dq += S~^T S~ (rhs - A~ dq), the residual summed in FP64 and the
+      // iteration's contact impulses held fixed
+      silg::launch_residual(d, st, s->has_obstacles ? silg::kResFrameContact : silg::kResFrame);
+      DevSim dr = d;
+      dr.gvec = d.gsave;
+      silg::launch_pass1(dr, st);
+      silg::launch_pass2(dr, st, silg::kOutAddDq);
+    }
     mark(e + 4);
   }
   if (s->has_obstacles) silg::launch_contact_eval(d, st, K, true);
@@ -248,6 +264,26 @@ int create_device(sim_s* s, const sim_obstacle* obstacles, int n_obs, const sim_
     std::vector<float> Sf(p.S.size());
     for (size_t k = 0; k < p.S.size(); ++k) Sf[k] = (float)p.S[k];
     d.S = s->upload(Sf);
+    d.s_bf16 = o->s_precision == SIM_S_BF16;
+    d.refine = std::max(0, std::min(2, o->refine));
+    d.Sb = nullptr;
+    if (d.s_bf16) {
+      // round to nearest even from the FP32 value (finite inputs)
+      std::vector<uint16_t> Sb(Sf.size());
+      for (size_t k = 0; k < Sf.size(); ++k) {
+        uint32_t u;
+        std::memcpy(&u, &Sf[k], 4);
+        u += 0x7fffu + ((u >> 16) & 1u);
+        Sb[k] = (uint16_t)(u >> 16);
+      }
+      d.Sb = reinterpret_cast<const unsigned short*>(s->upload(Sb));
+    }
+    // A~ over the free vertices (FP64) for residuals of the global solve
+    std::vector<int> ap(p.Ap.begin(), p.Ap.end());
+    d.A_ptr = s->upload(ap);
+    d.A_idx = s->upload(p.Ai);
+    d.A_val = s->upload(p.Ax);
+    d.gsave = s->alloc<float>(3 * (size_t)p.n_pad);
     std::vector<long long> rb(p.rowbase.begin(), p.rowbase.end());
     d.rowbase = s->upload(rb);
     d.lo = s->upload(p.lo);
@@ -402,7 +438,8 @@ int sim_create(const sim_mesh* mesh, const sim_material* mats, int32_t n_mat,
   if (o->n_iters < 0 || o->n_iters > silg::kMaxIters || o->n_cr_iters < 0 ||
       o->contact_capacity <= 0 || o->contact_capacity > (1 << 16))
     return SIM_EINVAL;
-  if (o->s_precision != SIM_S_FP32) return SIM_ENOTSUP;
+  if (o->s_precision != SIM_S_FP32 && o->s_precision != SIM_S_BF16) return SIM_EINVAL;
+  if (o->refine < 0 || o->refine > 2) return SIM_EINVAL;
   sim_s* s = new (std::nothrow) sim_s();
   if (!s) return SIM_ENOMEM;
   int st = guarded([&]() {
@@ -592,7 +629,16 @@ int sim_apply_inverse(sim_t* s, const double* b, double* x) {
   cudaStreamSynchronize(s->launch);
   cudaMemcpyAsync(s->d.gvec, g.data(), g.size() * sizeof(float), cudaMemcpyHostToDevice, s->work);
   silg::launch_pass1(s->d, s->work);
-  silg::launch_pass2(s->d, s->work, false);
+  silg::launch_pass2(s->d, s->work, silg::kOutX);
+  if (s->d.s_bf16 && s->d.refine > 0) {
+    // x += S~^T S~ (b - A~ x), the residual summed in FP64
+    cudaMemcpyAsync(s->d.gsave, g.data(), g.size() * sizeof(float), cudaMemcpyHostToDevice, s->work);
+    silg::launch_residual(s->d, s->work, silg::kResApply);
+    DevSim dr = s->d;
+    dr.gvec = s->d.gsave;
+    silg::launch_pass1(dr, s->work);
+    silg::launch_pass2(dr, s->work, silg::kOutAddX);
+  }
   std::vector<float> xo(3 * (size_t)n);
   cudaMemcpyAsync(xo.data(), s->d.xout, xo.size() * sizeof(float), cudaMemcpyDeviceToHost, s->work);
   cudaError_t e = cudaStreamSynchronize(s->work);

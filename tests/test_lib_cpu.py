@@ -112,3 +112,11 @@ def test_create_without_a_gpu_fails_loudly():
     with pytest.raises(SimError) as e:
         Simulator(sg.cube_drop(m=3))
     assert e.value.status == -4
+
+
+@pytest.mark.parametrize("opts", [{"s_precision": 2}, {"s_precision": -1}, {"refine": 3},
+                                  {"refine": -1}, {"n_iters": 65}, {"contact_capacity": 0}])
+def test_invalid_options_are_rejected_before_any_device_work(opts):
+    with pytest.raises(SimError) as e:
+        Simulator(sg.cube_drop(m=3), **opts)
+    assert e.value.status == -1
