@@ -97,7 +97,10 @@ typedef struct {
   int32_t device;              /* CUDA device ordinal (default 0)                          */
   double gravity[3];           /* default (0, 0, -9.81)                                    */
   double contact_margin;       /* contact when gap < margin; <= 0: half the mean edge     */
-  uint64_t spin_limit;         /* iteration limit of device-side waits (0: default)       */
+  uint64_t spin_limit;         /* polls of a device-side wait (the CR kernel's bulk copy of
+                                  its Delassus rows into shared memory) before it gives up,
+                                  falls back to global memory and reports SIM_ETIMEOUT at
+                                  the next synchronisation (0: 2^22)                      */
   void* cuda_stream;           /* cudaStream_t to run on, or NULL for a private stream    */
   int32_t n_host_threads;      /* threads for the host precompute (0: all cores)          */
 } sim_options;

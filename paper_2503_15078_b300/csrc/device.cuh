@@ -145,6 +145,13 @@ struct DevSim {
   float* yc_val;    // cap_y
   int* yc_row;      // cap_y
   float* wt;        // cap x cap (W~, row-major with ld = n_cv)
+  int* kb_lo;       // n / 32 + 1: union of the contact-vertex intervals of 32 rows of U
+  int* kb_hi;
+  float* wt_part;   // partial 64 x 64 tiles of W~
+  int wt_grid;      // CTAs of the W~ product
+  int cr_R;         // CTAs in the CR cluster
+  int* cr_split;    // 2 (kCrMaxRanks + 1): first contact vertex, first contact per rank
+  unsigned long long spin_limit;  // polls of a device-side wait before it reports a timeout
   // diagnostics
   double* resid;    // kMaxIters + 1
   double* max_pen;
@@ -156,7 +163,22 @@ struct DevSim {
 // ---- launchers (all asynchronous on stream s) ----------------------------------------
 void launch_frame_begin(const DevSim& d, cudaStream_t s);
 void launch_collide(const DevSim& d, cudaStream_t s);
-void launch_delassus(const DevSim& d, cudaStream_t s, int wt_tiles);
+void launch_delassus(const DevSim& d, cudaStream_t s);
+// W~ work items: at most kWtMaxSplit K-splits per 64 x 64 tile; partial tiles for
+// wt_items_max(cap, grid) items
+constexpr int kWtMaxSplit = 16;
+constexpr int kCrMaxRanks = 16;
+inline long long wt_items_max(int cap, int grid) {
+  long long best = 0;
+  for (int nb = 1; nb <= (cap + 63) / 64; ++nb) {
+    long long nt = (long long)nb * (nb + 1) / 2;
+    long long S = (grid + nt - 1) / nt;
+    if (S < 1) S = 1;
+    if (S > kWtMaxSplit) S = kWtMaxSplit;
+    if (nt * S > best) best = nt * S;
+  }
+  return best;
+}
 void launch_local(const DevSim& d, cudaStream_t s, bool debug_p);
 void launch_contact_eval(const DevSim& d, cudaStream_t s, int k, bool final_eval);
 void launch_rhs(const DevSim& d, cudaStream_t s);

@@ -263,113 +263,210 @@ __global__ void k_y_gather(DevSim d) {
   }
 }
 
-// W~ = Y^T Y, 64 x 64 output tiles of the lower triangle (mirrored), FP32. A row of Y
-// touches the tile only if its contact-vertex range meets both column blocks; the CTA
-// first compacts those rows (ranges are nested subtree intervals, so most rows below
-// the top separators drop out for off-diagonal tiles), then accumulates 32 rows at a
-// time: the rows' metadata is staged once per batch, each thread owns a 4 x 4 block.
-constexpr int kWT = 64;
-constexpr int kWTRows = 4096;   // compacted rows per chunk
-constexpr int kWTBatch = 32;
-__global__ void __launch_bounds__(256) k_wtilde(DevSim d) {
-  const int ncv = min(d.counters[kCntCv], d.cap);
-  const int ta = blockIdx.x, tb = blockIdx.y;
-  if (tb > ta || ta * kWT >= ncv) return;
+// W~ = Y^T Y (FP32) as a block-sparse product. Y has one row per ancestor row a of a
+// contact vertex (the set U, in elimination-tree postorder) and is non-zero only on the
+// contact vertices of a's subtree, a contiguous interval [clo_a, clo_a + len_a). Rows are
+// taken in blocks of kWtKB; a block contributes to the output tile (I, J) only if the
+// union of its rows' intervals meets both column blocks, so the lower-level blocks of the
+// tree drop out of every off-diagonal tile. Work items are (lower-triangle tile, K split):
+// the split count S is chosen on the device from the contact-vertex count so that there
+// are about as many items as resident CTAs; each item sums its share of the tile's
+// contributing row blocks into a partial tile, and k_wt_reduce adds the S partials in a
+// fixed order (deterministic) and writes both triangles and the zero padding.
+constexpr int kWtT = 64;         // output tile
+constexpr int kWtKB = 32;        // rows of Y per block
+constexpr int kWtThreads = 128;  // 8 x 4 outputs per thread
+constexpr int kWtList = 1024;    // row blocks staged per round
+
+__device__ __forceinline__ void wt_layout(int ncv, int target, int& nb, int& ntiles, int& S) {
+  nb = (ncv + kWtT - 1) / kWtT;
+  ntiles = nb * (nb + 1) / 2;
+  S = ntiles > 0 ? min(kWtMaxSplit, max(1, (target + ntiles - 1) / ntiles)) : 1;
+}
+
+__device__ __forceinline__ void tri_decode(int t, int& I, int& J) {
+  int i = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+  while ((i + 1) * (i + 2) / 2 <= t) ++i;
+  while (i * (i + 1) / 2 > t) --i;
+  I = i;
+  J = t - i * (i + 1) / 2;
+}
+
+// union of the contact-vertex intervals of each block of kWtKB rows of U
+__global__ void k_wt_blocks(DevSim d) {
+  const int kb = blockIdx.x * blockDim.x + threadIdx.x;
   const int nU = d.counters[kCntU];
-  if (d.y_ptr[nU] > d.cap_y) return;
-  __shared__ __align__(16) float As[kWTBatch][kWT], Bs[kWTBatch][kWT];
-  __shared__ int rows[kWTRows];
-  __shared__ int meta_lo[kWTBatch], meta_len[kWTBatch], meta_base[kWTBatch];
-  __shared__ int wcount[8];
-  __shared__ int nrows;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  float acc[4][4] = {};
-  const int a0 = ta * kWT, b0 = tb * kWT;
-  const int a1 = min(a0 + kWT, ncv), b1 = min(b0 + kWT, ncv);
-  for (int chunk0 = 0; chunk0 < nU; chunk0 += kWTRows) {
-    __syncthreads();
-    if (threadIdx.x == 0) nrows = 0;
-    __syncthreads();
-    // deterministic compaction: ballot within warps, then warps in order
-    const int chunk1 = min(nU, chunk0 + kWTRows);
-    for (int base = chunk0; base < chunk1; base += blockDim.x) {
-      const int u = base + threadIdx.x;
-      bool keep = false;
-      if (u < chunk1) {
-        const int clo = d.u_clo[u], chi = clo + d.u_len[u];
-        keep = clo < a1 && chi > a0 && clo < b1 && chi > b0;
-      }
-      const unsigned ball = __ballot_sync(0xffffffffu, keep);
-      if (lane == 0) wcount[wid] = __popc(ball);
-      __syncthreads();
-      int off = nrows;
-      for (int w = 0; w < wid; ++w) off += wcount[w];
-      if (keep) rows[off + __popc(ball & ((1u << lane) - 1))] = u;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        int t = 0;
-        for (int w = 0; w < 8; ++w) t += wcount[w];
-        nrows += t;
-      }
-      __syncthreads();
+  if (kb * kWtKB >= nU) return;
+  int lo = 1 << 30, hi = -1;
+  for (int u = kb * kWtKB; u < min(nU, (kb + 1) * kWtKB); ++u) {
+    lo = min(lo, d.u_clo[u]);
+    hi = max(hi, d.u_clo[u] + d.u_len[u]);
+  }
+  d.kb_lo[kb] = lo;
+  d.kb_hi[kb] = hi;
+}
+
+__global__ void __launch_bounds__(kWtThreads) k_wt_items(DevSim d) {
+  const int ncv = min(d.counters[kCntCv], d.cap);
+  const int nU = d.counters[kCntU];
+  if (ncv == 0 || nU == 0 || d.y_ptr[nU] > d.cap_y) return;
+  int nb, ntiles, S;
+  wt_layout(ncv, d.wt_grid, nb, ntiles, S);
+  const int nitems = ntiles * S;
+  const int nkb = (nU + kWtKB - 1) / kWtKB;
+  __shared__ __align__(16) float As[kWtKB][kWtT];
+  __shared__ __align__(16) float Bs[kWtKB][kWtT];
+  __shared__ int kbl[kWtList];
+  __shared__ int list_n;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int ty = t >> 4, tx = t & 15;  // outputs rows 8 ty .. +7, columns 4 tx .. +3
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int tile = item / S, sp = item - tile * S;
+    int I, J;
+    tri_decode(tile, I, J);
+    const int a0 = I * kWtT, b0 = J * kWtT;
+    const int a1 = min(a0 + kWtT, ncv), b1 = min(b0 + kWtT, ncv);
+    const bool diag = I == J;
+    // contributing row blocks, counted by every warp alike (uniform across the CTA)
+    int cnt = 0;
+    for (int g0 = 0; g0 < nkb; g0 += 32) {
+      const int kb = g0 + lane;
+      const bool v = kb < nkb && d.kb_lo[kb] < a1 && d.kb_hi[kb] > a0 && d.kb_lo[kb] < b1 &&
+                     d.kb_hi[kb] > b0;
+      cnt += __popc(__ballot_sync(0xffffffffu, v));
     }
-    const int nr = nrows;
-    for (int r0 = 0; r0 < nr; r0 += kWTBatch) {
+    const int r_begin = (int)((long long)sp * cnt / S), r_end = (int)((long long)(sp + 1) * cnt / S);
+    float acc[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    int scan_g0 = 0, rank = 0;  // scan state, meaningful in warp 0
+    while (true) {
       __syncthreads();
-      if (threadIdx.x < kWTBatch) {
-        const int rl = threadIdx.x;
-        if (r0 + rl < nr) {
-          const int u = rows[r0 + rl];
-          meta_lo[rl] = d.u_clo[u];
-          meta_len[rl] = d.u_len[u];
-          meta_base[rl] = d.y_ptr[u];
-        } else {
-          meta_lo[rl] = 0;
-          meta_len[rl] = 0;
-          meta_base[rl] = 0;
+      if (warp == 0) {
+        int m = 0;
+        while (scan_g0 < nkb && m <= kWtList - 32 && rank < r_end) {
+          const int kb = scan_g0 + lane;
+          const bool v = kb < nkb && d.kb_lo[kb] < a1 && d.kb_hi[kb] > a0 && d.kb_lo[kb] < b1 &&
+                         d.kb_hi[kb] > b0;
+          const unsigned mask = __ballot_sync(0xffffffffu, v);
+          const int myrank = rank + __popc(mask & ((1u << lane) - 1u));
+          const bool take = v && myrank >= r_begin && myrank < r_end;
+          const unsigned tmask = __ballot_sync(0xffffffffu, take);
+          if (take) kbl[m + __popc(tmask & ((1u << lane) - 1u))] = kb;
+          m += __popc(tmask);
+          rank += __popc(mask);
+          scan_g0 += 32;
+        }
+        if (lane == 0) list_n = m;
+      }
+      __syncthreads();
+      const int m = list_n;
+      if (m == 0) break;
+      for (int li = 0; li < m; ++li) {
+        const int r0 = kbl[li] * kWtKB;
+        // stage the block: warp w loads rows 8w .. 8w+7, lanes cover 64 columns
+        float pa[8][2], pb[8][2];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int u = r0 + 8 * warp + k;
+          int clo = 0, len = 0, base = 0;
+          if (u < nU) {
+            clo = d.u_clo[u];
+            len = d.u_len[u];
+            base = d.y_ptr[u];
+          }
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h;
+            const int ca = a0 + c - clo, cb = b0 + c - clo;
+            pa[k][h] = (ca >= 0 && ca < len) ? d.y_val[base + ca] : 0.f;
+            pb[k][h] = (!diag && cb >= 0 && cb < len) ? d.y_val[base + cb] : 0.f;
+          }
+        }
+        __syncthreads();  // previous block's products are done
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            As[8 * warp + k][lane + 32 * h] = pa[k][h];
+            Bs[8 * warp + k][lane + 32 * h] = pb[k][h];
+          }
+        __syncthreads();
+        const float(*Bsrc)[kWtT] = diag ? As : Bs;
+#pragma unroll 8
+        for (int k = 0; k < kWtKB; ++k) {
+          const float4 x0 = *reinterpret_cast<const float4*>(&As[k][8 * ty]);
+          const float4 x1 = *reinterpret_cast<const float4*>(&As[k][8 * ty + 4]);
+          const float4 y = *reinterpret_cast<const float4*>(&Bsrc[k][4 * tx]);
+          const float av[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+          const float bv[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
         }
       }
-      __syncthreads();
-#pragma unroll 4
-      for (int e = threadIdx.x; e < kWTBatch * kWT; e += 256) {
-        const int rl = e / kWT, cl = e % kWT;
-        const int clo = meta_lo[rl], len = meta_len[rl], base = meta_base[rl];
-        const int ca = a0 + cl - clo, cb = b0 + cl - clo;
-        As[rl][cl] = (ca >= 0 && ca < len) ? d.y_val[base + ca] : 0.f;
-        Bs[rl][cl] = (cb >= 0 && cb < len) ? d.y_val[base + cb] : 0.f;
-      }
-      __syncthreads();
-#pragma unroll 8
-      for (int k = 0; k < kWTBatch; ++k) {
-        const float4 av = *reinterpret_cast<const float4*>(&As[k][ty * 4]);
-        const float4 bv = *reinterpret_cast<const float4*>(&Bs[k][tx * 4]);
-        const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
+    }
+    float* out = d.wt_part + (size_t)item * kWtT * kWtT;
 #pragma unroll
-        for (int p = 0; p < 4; ++p)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) acc[p][q] += a4[p] * b4[q];
-      }
+    for (int i = 0; i < 8; ++i)
+      *reinterpret_cast<float4*>(out + (8 * ty + i) * kWtT + 4 * tx) =
+          make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+  }
+}
+
+__global__ void k_wt_reduce(DevSim d) {
+  const int ncv = min(d.counters[kCntCv], d.cap);
+  const int nU = d.counters[kCntU];
+  if (ncv == 0 || nU == 0 || d.y_ptr[nU] > d.cap_y) return;
+  int nb, ntiles, S;
+  wt_layout(ncv, d.wt_grid, nb, ntiles, S);
+  const int ld = wt_ld(ncv);
+  const long long total = (long long)ntiles * kWtT * kWtT;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int tile = (int)(e / (kWtT * kWtT)), el = (int)(e % (kWtT * kWtT));
+    int I, J;
+    tri_decode(tile, I, J);
+    const int ra = I * kWtT + el / kWtT, cb = J * kWtT + el % kWtT;
+    if (ra < ncv && cb < ncv) {
+      float sum = 0.f;
+      const float* p = d.wt_part + (size_t)tile * S * kWtT * kWtT + el;
+      for (int sp = 0; sp < S; ++sp) sum += p[(size_t)sp * kWtT * kWtT];
+      d.wt[(size_t)ra * ld + cb] = sum;
+      d.wt[(size_t)cb * ld + ra] = sum;
+    } else if (ra >= ncv && ra < ld && cb < ncv) {
+      d.wt[(size_t)cb * ld + ra] = 0.f;   // zero padding of the last column group
+    } else if (cb >= ncv && cb < ld && ra < ncv) {
+      d.wt[(size_t)ra * ld + cb] = 0.f;
     }
   }
-#pragma unroll
-  for (int p = 0; p < 4; ++p)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      int ra = a0 + ty * 4 + p, cb = b0 + tx * 4 + q;
-      const int ld = wt_ld(ncv);
-      if (ra < ncv && cb < ncv) {
-        d.wt[(size_t)ra * ld + cb] = acc[p][q];
-        d.wt[(size_t)cb * ld + ra] = acc[p][q];
-      } else if (ta == tb && ra < ncv && cb >= ncv && cb < ld) {
-        d.wt[(size_t)ra * ld + cb] = 0.f;   // zero padding of the last column group
-      }
-    }
+}
+
+// Split of the contact vertices over the CR cluster's ranks, balanced by contacts: rank r
+// owns contact vertices [cv_split(r), cv_split(r + 1)).
+__device__ int cv_split(const DevSim& d, int r, int R, int c, int ncv) {
+  if (r >= R) return ncv;
+  long long target = (long long)r * c / R;
+  int lo = 0, hi = ncv;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (d.cv_first[mid] < target) lo = mid + 1; else hi = mid;
+  }
+  return lo;
 }
 
 __global__ void k_precond(DevSim d) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   int c = min(d.counters[kCntContacts], d.cap);
+  if (blockIdx.x == 0 && threadIdx.x <= d.cr_R) {
+    const int ncv = min(d.counters[kCntCv], d.cap), r = threadIdx.x;
+    const int cv = cv_split(d, r, d.cr_R, c, ncv);
+    d.cr_split[r] = cv;
+    d.cr_split[kCrMaxRanks + 1 + r] = cv < ncv ? min(d.cv_first[cv], c) : c;
+  }
   if (j >= c) return;
   int ncv = min(d.counters[kCntCv], d.cap);
   int cv = d.ct_cv[j];
@@ -545,20 +642,32 @@ __global__ void k_yu(DevSim d) {
 // through distributed shared memory; dot products are reduced per CTA and then over the
 // cluster in rank order, so every CTA holds the same scalars and the result is
 // deterministic.
+constexpr unsigned kBulkChunk = 32768;  // bytes per bulk-copy instruction
+constexpr int kCrG = 8;  // register-held column groups per lane: W~ rows up to 1024 wide
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// wait for phase `parity` of an mbarrier, at most `limit` polls (0: a default of 2^22);
+// false on timeout
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, unsigned long long limit) {
+  if (limit == 0) limit = 1ull << 22;
+  for (unsigned long long i = 0; i < limit; ++i) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
 struct CrLayout {
   int R, rank, c, ncv, cv0, cv1, j0, j1;
 };
-
-__device__ int cv_split(const DevSim& d, int r, int R, int c, int ncv) {
-  if (r >= R) return ncv;
-  long long target = (long long)r * c / R;
-  int lo = 0, hi = ncv;
-  while (lo < hi) {
-    int mid = (lo + hi) >> 1;
-    if (d.cv_first[mid] < target) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
 
 __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) {
   extern __shared__ __align__(16) float sm[];
@@ -571,12 +680,10 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
   // every CTA reads the same counters, so this exit is taken by all or by none
   if (L.c == 0 || L.ncv == 0) return;
   // split of the contact vertices over the cluster ranks, computed once per CTA
-  __shared__ int split_cv[17], split_j[17];
+  __shared__ int split_cv[kCrMaxRanks + 1], split_j[kCrMaxRanks + 1];
   if (threadIdx.x <= L.R) {
-    const int r = threadIdx.x;
-    const int cv = cv_split(d, r, L.R, L.c, L.ncv);
-    split_cv[r] = cv;
-    split_j[r] = cv < L.ncv ? min(d.cv_first[cv], L.c) : L.c;
+    split_cv[threadIdx.x] = d.cr_split[threadIdx.x];
+    split_j[threadIdx.x] = d.cr_split[kCrMaxRanks + 1 + threadIdx.x];
   }
   __syncthreads();
   L.cv0 = split_cv[L.rank];
@@ -608,15 +715,34 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
   int* cvf = reinterpret_cast<int*>(ec + 3 * nj_max);   // owned cv: first local contact
   int* cvn = cvf + nv_max;                              // owned cv: contact count
   int* ctl = cvn + nv_max;                              // owned contact: local cv index
-  // nv x ldw rows of W~ if they fit, 16-byte aligned for vector loads
+  // the owned rows of W~ that fit (16-byte aligned, one bulk copy); the rest are read from
+  // global memory
   float* wrows = sm + ((((reinterpret_cast<float*>(ctl + nj_max)) - sm) + 3) & ~size_t(3));
   const size_t used = (size_t)(wrows - sm) * sizeof(float);
-  const bool w_in_smem = used + (size_t)nv * ldw * sizeof(float) <= (size_t)smem_bytes;
-  const float* wsrc = w_in_smem ? wrows : d.wt + (size_t)L.cv0 * ldw;
+  __shared__ __align__(8) unsigned long long wbar;
   if (used > (size_t)smem_bytes) {   // uniform: depends only on cluster-wide maxima
     if (threadIdx.x == 0 && L.rank == 0) atomicOr(d.err, kErrCapacity);
     cl.sync();
     return;
+  }
+  int rows_sm = (int)min((size_t)nv, ((size_t)smem_bytes - used) / ((size_t)ldw * sizeof(float)));
+  if (threadIdx.x == 0 && rows_sm > 0) {
+    // rows are contiguous in W~ (row-major, ld a multiple of 4 floats): 16-byte aligned
+    // source and destination, sizes multiples of 16 bytes
+    const unsigned bar = smem_u32(&wbar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const unsigned long long bytes = (unsigned long long)rows_sm * ldw * sizeof(float);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"((unsigned)bytes) : "memory");
+    const char* src = reinterpret_cast<const char*>(d.wt + (size_t)L.cv0 * ldw);
+    const unsigned dst = smem_u32(wrows);
+    for (unsigned long long off = 0; off < bytes; off += kBulkChunk) {
+      const unsigned sz = (unsigned)min((unsigned long long)kBulkChunk, bytes - off);
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+              "r"(dst + (unsigned)off), "l"(src + off), "r"(sz), "r"(bar) : "memory");
+    }
   }
   for (int e = threadIdx.x; e < 3 * nj; e += blockDim.x) {
     const int j = L.j0 + e / 3;
@@ -634,12 +760,16 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
   for (int jl = threadIdx.x; jl < nj; jl += blockDim.x)
     ctl[jl] = min(max(d.ct_cv[L.j0 + jl] - L.cv0, 0), max(nv - 1, 0));
   for (int e = L.ncv + threadIdx.x; e < ldw; e += blockDim.x) uall[e] = make_float4(0, 0, 0, 0);
-  if (w_in_smem) {
-    const float4* src = reinterpret_cast<const float4*>(d.wt + (size_t)L.cv0 * ldw);
-    float4* dst = reinterpret_cast<float4*>(wrows);
-    const size_t total4 = (size_t)nv * ldw / 4;
-    for (size_t e = threadIdx.x; e < total4; e += blockDim.x) dst[e] = src[e];
+  __syncthreads();
+  const bool w_copy = rows_sm > 0;
+  bool w_late = false;
+  if (w_copy && !mbar_wait(smem_u32(&wbar), 0, d.spin_limit)) {
+    // the copy did not complete in time: report it and read every row from global memory
+    if (threadIdx.x == 0) atomicOr(d.err, kErrTimeout);
+    rows_sm = 0;
+    w_late = true;
   }
+  __syncthreads();
   // every CTA of the cluster must be running before shared memory is written remotely
   cl.sync();
 
@@ -667,17 +797,74 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
     cl.sync();   // every rank's slice of u is now in every CTA
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int ng = ldw / 4;
+    auto wrow_ptr = [&](int row) {
+      return reinterpret_cast<const float4*>(
+          row < rows_sm ? wrows + (size_t)row * ldw : d.wt + (size_t)(L.cv0 + row) * ldw);
+    };
+    if (ldw <= 32 * 4 * kCrG) {
+      // lane l owns the columns l + 32 m (m < 4 kCrG): its u values live in registers
+      // (loaded conflict-free: consecutive lanes read consecutive 16-byte entries), and
+      // each warp streams whole rows of W~, two at a time, with consecutive lanes on
+      // consecutive words (no bank conflicts)
+      constexpr int M = 4 * kCrG;
+      float ux[M], uy[M], uz[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const int col = lane + 32 * m;
+        const float4 t = col < ldw ? uall[col] : make_float4(0.f, 0.f, 0.f, 0.f);
+        ux[m] = t.x;
+        uy[m] = t.y;
+        uz[m] = t.z;
+      }
+      // rows held in shared memory are read through a shared-memory pointer (so the loads
+      // are shared-memory loads, not generic ones); the rest through a global one
+      auto rows = [&](int r_begin, int r_end, auto row_ptr) {
+      for (int row = r_begin + 2 * warp; row < r_end; row += 2 * nw) {
+        const bool two = row + 1 < r_end;
+        const float* w0 = row_ptr(row);
+        const float* w1 = row_ptr(two ? row + 1 : row);
+        float a[2][3] = {};
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const int col = lane + 32 * m;
+          if (col < ldw) {
+            const float p = w0[col], q = w1[col];
+            a[0][0] += p * ux[m];
+            a[0][1] += p * uy[m];
+            a[0][2] += p * uz[m];
+            a[1][0] += q * ux[m];
+            a[1][1] += q * uy[m];
+            a[1][2] += q * uz[m];
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) a[k][c] = warp_sum(a[k][c]);
+        if (lane < 3) wloc[3 * row + lane] = lane == 0 ? a[0][0] : (lane == 1 ? a[0][1] : a[0][2]);
+        if (two && lane >= 3 && lane < 6)
+          wloc[3 * row + lane] = lane == 3 ? a[1][0] : (lane == 4 ? a[1][1] : a[1][2]);
+      }
+      };
+      const int n_sm_rows = min(rows_sm, nv);
+      rows(0, n_sm_rows, [&](int r) { return wrows + (size_t)r * ldw; });
+      rows(n_sm_rows, nv, [&](int r) { return d.wt + (size_t)(L.cv0 + r) * ldw; });
+    } else {
     // four rows per warp at a time, so the shuffle reductions of the rows overlap
     for (int row0 = 4 * warp; row0 < nv; row0 += 4 * nw) {
       float acc[4][3] = {};
       const int nrow = min(4, nv - row0);
+      const float4* wrow[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) wrow[k] = wrow_ptr(min(row0 + k, nv - 1));
+#pragma unroll 2
       for (int g4 = lane; g4 < ng; g4 += 32) {
         const float4 a = uall[4 * g4], b = uall[4 * g4 + 1], c = uall[4 * g4 + 2],
                      e = uall[4 * g4 + 3];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           if (k < nrow) {
-            const float4 w = reinterpret_cast<const float4*>(wsrc + (size_t)(row0 + k) * ldw)[g4];
+            const float4 w = wrow[k][g4];
             acc[k][0] += w.x * a.x + w.y * b.x + w.z * c.x + w.w * e.x;
             acc[k][1] += w.x * a.y + w.y * b.y + w.z * c.y + w.w * e.y;
             acc[k][2] += w.x * a.z + w.y * b.z + w.z * c.z + w.w * e.z;
@@ -698,6 +885,7 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
             if (kk == k && qq == q) val = acc[kk][qq];
         wloc[3 * (row0 + k) + q] = val;
       }
+    }
     }
     __syncthreads();
     for (int e = threadIdx.x; e < 3 * nj; e += blockDim.x) {
@@ -803,6 +991,9 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
     d.uvec[3 * cv + 1] = u1;
     d.uvec[3 * cv + 2] = u2;
   }
+  // a copy that timed out may still be in flight: give it another bounded wait before the
+  // shared memory is released
+  if (w_late) mbar_wait(smem_u32(&wbar), 0, d.spin_limit);
   cl.sync();  // no CTA leaves while another may still write into its shared memory
 }
 
@@ -820,7 +1011,7 @@ void launch_collide(const DevSim& d, cudaStream_t s) {
   k_collide_write<<<g, 64, 0, s>>>(d);
 }
 
-void launch_delassus(const DevSim& d, cudaStream_t s, int wt_tiles) {
+void launch_delassus(const DevSim& d, cudaStream_t s) {
   const int g = (d.n + 255) / 256;
   k_u_flag<<<g, 256, 0, s>>>(d);
   launch_scan(d.u_flag, d.u_off, d.n, nullptr, d.counters + kCntU, s);
@@ -829,8 +1020,9 @@ void launch_delassus(const DevSim& d, cudaStream_t s, int wt_tiles) {
   k_yc_len<<<(d.cap + 255) / 256, 256, 0, s>>>(d);
   launch_scan(d.yc_len, d.yc_ptr, 0, d.counters + kCntCv, d.counters + kCntYC, s);
   k_y_gather<<<(d.n * 32 + 255) / 256, 256, 0, s>>>(d);
-  dim3 grid(wt_tiles, wt_tiles);
-  k_wtilde<<<grid, 256, 0, s>>>(d);
+  k_wt_blocks<<<(d.n / kWtKB + 1 + 127) / 128, 128, 0, s>>>(d);
+  k_wt_items<<<d.wt_grid, kWtThreads, 0, s>>>(d);
+  k_wt_reduce<<<2 * d.n_sm, 256, 0, s>>>(d);
   k_precond<<<(d.cap + 255) / 256, 256, 0, s>>>(d);
 }
 

@@ -36,7 +36,6 @@ struct sim_s {
   size_t cr_smem = 0;
   int n_iters_default = 5;
   bool has_obstacles = false;
-  int wt_tiles = 1;
   std::map<int, Graph> graphs;
   std::vector<void*> allocs;
   int64_t frame = 0;
@@ -106,7 +105,7 @@ int refined_iters(const sim_s* s, int K) {
 
 int kernels_per_frame(const sim_s* s, int K) {
   const bool c = s->has_obstacles;
-  return 1 + (c ? 4 + 9 : 0) + K * (1 + (c ? 1 : 0) + 1 + 2 + (c ? 3 : 0) + 2) + (c ? 1 : 0) + 1 +
+  return 1 + (c ? 4 + 11 : 0) + K * (1 + (c ? 1 : 0) + 1 + 2 + (c ? 3 : 0) + 2) + (c ? 1 : 0) + 1 +
          5 * refined_iters(s, K);
 }
 
@@ -120,7 +119,7 @@ void enqueue_frame(sim_s* s, int K, cudaStream_t st) {
   silg::launch_frame_begin(d, st);
   if (s->has_obstacles) silg::launch_collide(d, st);
   mark(1);
-  if (s->has_obstacles) silg::launch_delassus(d, st, s->wt_tiles);
+  if (s->has_obstacles) silg::launch_delassus(d, st);
   mark(2);
   for (int k = 0; k < K; ++k) {
     const int e = 3 + 5 * k;
@@ -382,15 +381,21 @@ int create_device(sim_s* s, const sim_obstacle* obstacles, int n_obs, const sim_
   d.err = s->alloc<int>(1);
   d.p_out = s->alloc<float>(9 * (size_t)T);
   s->has_obstacles = n_obs > 0;
-  s->wt_tiles = (cap + 63) / 64;
+  d.wt_grid = 4 * d.n_sm;
+  d.spin_limit = o->spin_limit;
+  d.kb_lo = s->alloc<int>(n / 32 + 1);
+  d.kb_hi = s->alloc<int>(n / 32 + 1);
+  d.wt_part = s->alloc<float>((size_t)silg::wt_items_max(cap, d.wt_grid) * 64 * 64);
   if (silg::sinv_setup() != SIM_OK) return SIM_ECUDA;
   s->ev.resize(4 + 5 * silg::kMaxIters);
   for (auto& e : s->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return SIM_ECUDA;
+  d.cr_split = s->alloc<int>(2 * (silg::kCrMaxRanks + 1));
   if (s->has_obstacles) {
     int st = silg::cr_setup(&s->cluster, &s->cr_smem);
     if (st != SIM_OK) return st;
   }
+  d.cr_R = s->cluster;
   cudaError_t e = cudaStreamSynchronize(s->work);
   if (e != cudaSuccess) return cuda_status(e);
   return cuda_status(cudaGetLastError());
