@@ -125,11 +125,13 @@ enum { SIM_PHASE_COLLIDE = 0,   /* prediction and collision detection (App. A.1)
        SIM_PHASE_DELASSUS = 1,  /* W~ = Y^T Y and preconditioner (Eqs. 27-28)            */
        SIM_PHASE_LOCAL = 2,     /* local step per tetrahedron (Eq. 5)                     */
        SIM_PHASE_ASSEMBLE = 3,  /* FB evaluation and right-hand side (Eq. 19)            */
-       SIM_PHASE_SPMV1 = 4,     /* z = S g (first profile product, Eq. 8)                 */
+       SIM_PHASE_SPMV1 = 4,     /* z = S g (first profile product, Eq. 8): the product     */
        SIM_PHASE_SOLVE = 5,     /* J A^-1 g, conjugate residual, S J^T dlambda (Alg. 4)   */
-       SIM_PHASE_SPMV2 = 6,     /* q = S^T y (second profile product, Eq. 23b)            */
+       SIM_PHASE_SPMV2 = 6,     /* q = S^T y (second profile product): the product         */
        SIM_PHASE_INTEGRATE = 7, /* final residual and integration                         */
-       SIM_NUM_PHASES = 8 };
+       SIM_PHASE_REDUCE = 8,    /* fixed-order sums of both products' partial sums (and a
+                                   BF16 residual correction)                              */
+       SIM_NUM_PHASES = 9 };
 
 /* Sizes of the precomputed structure (Theorem 1 profile of S). */
 typedef struct {

@@ -11,8 +11,9 @@ SIM_OK = 0
 STATUS = {0: "SIM_OK", -1: "SIM_EINVAL", -2: "SIM_ENOMEM", -3: "SIM_ENOTSPD", -4: "SIM_ECUDA",
           -5: "SIM_ECAPACITY", -6: "SIM_ETIMEOUT", -7: "SIM_ENONFINITE", -8: "SIM_ENOTSUP"}
 SIM_MAX_RESIDUALS = 64
-SIM_NUM_PHASES = 8
-PHASES = ["collide", "delassus", "local", "assemble", "spmv1", "solve", "spmv2", "integrate"]
+SIM_NUM_PHASES = 9
+PHASES = ["collide", "delassus", "local", "assemble", "spmv1", "solve", "spmv2", "integrate",
+          "reduce"]
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)

@@ -42,7 +42,7 @@ struct DevSim {
   // sizes
   int n, n_all, n_tets, n_pad, n_obs, n_mat;
   int cap, cap_y, n_cr;
-  int n_rg, n_ct, n_p1, n_p2;
+  int n_rg, n_ct;
   double h, margin, L_ref;
   float h2f;        // h^2 in FP32
   double grav[3], handle_vel[3];
@@ -84,17 +84,24 @@ struct DevSim {
   const long long* rowbase;
   const int* lo;
   const int* hi;
-  const int4* p1_items;
-  const int* p1_first;
-  const int4* p2_items;
-  const int* p2_first;
-  const int* p2_list;
-  const int* p1_order;
-  const int* p2_order;
+  // balanced tile streams of the two products (StreamSchedule on the host)
+  const int2* s1_tiles;   // (row group, column tile)
+  const int* s1_cta;      // s1_grid + 1
+  const int* s1_seg_base; // s1_grid
+  const int* s1_seg_first;// n_rg + 1
+  const int2* s2_tiles;   // (column tile, row group)
+  const int* s2_cta;
+  const int* s2_seg_base;
+  const int* s2_seg_first;// n_ct + 1
+  const int* s1_col_first;  // s1_grid + 1: the CTA's distinct column tiles in s1_cols
+  const int* s1_cols;
+  const int* s1_col_slot;   // per pass-1 tile: position of its column tile in that list
+  int s1_max_cols;
+  int s1_grid, s2_grid, n_seg1, n_seg2;
   int n_sm;         // persistent-kernel grid size
   const float* zero;  // kTileW zeros: the load target of lanes outside a row's range
-  float* p1_part;   // [n_p1][3][kRowGroup]
-  float* p2_part;   // [n_p2][3][kTileW]
+  float* p1_part;   // [n_seg1][3][kRowGroup]
+  float* p2_part;   // [n_seg2][3][kTileW]
 
   // vectors (SoA, n_pad per component)
   float* gvec;
@@ -168,6 +175,7 @@ void launch_delassus(const DevSim& d, cudaStream_t s);
 // wt_items_max(cap, grid) items
 constexpr int kWtMaxSplit = 16;
 constexpr int kCrMaxRanks = 16;
+constexpr int kMaxStagedCols = 32;  // column tiles of g staged per pass-1 CTA (96 KB)
 inline long long wt_items_max(int cap, int grid) {
   long long best = 0;
   for (int nb = 1; nb <= (cap + 63) / 64; ++nb) {
@@ -182,10 +190,19 @@ inline long long wt_items_max(int cap, int grid) {
 void launch_local(const DevSim& d, cudaStream_t s, bool debug_p);
 void launch_contact_eval(const DevSim& d, cudaStream_t s, int k, bool final_eval);
 void launch_rhs(const DevSim& d, cudaStream_t s);
+// z = S~ g: the product (partial sums) and the fixed-order reduction into zvec
 void launch_pass1(const DevSim& d, cudaStream_t s);
-// pass-2 output: write dq or xout, or add into them (residual correction)
+void launch_reduce1(const DevSim& d, cudaStream_t s);
+// x = S~^T y: the product and the reduction, which writes dq or xout or adds into them
 enum { kOutDq = 0, kOutX = 1, kOutAddDq = 2, kOutAddX = 3 };
-void launch_pass2(const DevSim& d, cudaStream_t s, int out_mode);
+void launch_pass2(const DevSim& d, cudaStream_t s);
+void launch_reduce2(const DevSim& d, cudaStream_t s, int out_mode);
+inline void launch_solve(const DevSim& d, cudaStream_t s, int out_mode) {
+  launch_pass1(d, s);
+  launch_reduce1(d, s);
+  launch_pass2(d, s);
+  launch_reduce2(d, s, out_mode);
+}
 // residual of a global solve into gsave: gsave - A xout (kResApply), g - A dq (kResFrame),
 // g + h^2 J^T dlambda - A dq (kResFrameContact)
 enum { kResApply = 0, kResFrame = 1, kResFrameContact = 2 };

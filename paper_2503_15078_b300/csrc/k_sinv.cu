@@ -5,21 +5,20 @@
 //
 // Storage: row i holds columns [lo_i, hi_i), a superset of its elimination subtree
 // [fd(i), i] aligned to 8 values; rows are concatenated. The work is cut into tiles of
-// kRowGroup rows x kTileW columns; a tile's part of a row is one contiguous, 32-byte
-// aligned run of at most 1 KB. Each warp owns kRowsPerWarp rows of a tile and each lane
-// two fixed 4-column chunks, read with 16-byte loads.
+// kRowGroup rows x kTileW columns; a tile's part of a row is one contiguous, aligned run
+// of at most 1 KB (FP32). Each warp owns kRowsPerWarp rows of a tile and each lane two
+// fixed 4-column chunks, read with one 16-byte (FP32) or 8-byte (BF16) load each.
 //
-// The products are HBM-bound: every S~ value is read once per product. Throughput comes
-// from memory-level parallelism, so the inner loops issue all loads of two tiles
-// (16 x 16 bytes per lane) before any arithmetic, without branches: a lane whose chunk lies
-// outside its row's stored range loads from a small zero buffer instead, which also makes
-// masking unnecessary.
-//
-// Pass-1 work items walk one row group across up to kMaxTilesP1 column tiles (the item's
-// slice of g is staged in shared memory); pass-2 items walk one column tile down a list
-// of row groups (their row metadata and y values are staged in shared memory). Both
-// write per-item partial sums that a second kernel adds in a fixed order, so results are
-// deterministic. Items are launched largest first.
+// The products are HBM-bound: every S~ value is read once per product. Each CTA streams
+// a contiguous range of the pass's tile order, the ranges cut so that every CTA has about
+// the same number of bytes to read (one wave, no tail of large items). Throughput comes
+// from memory-level parallelism: a warp issues the loads of kUnroll tiles before any
+// arithmetic, without branches (a lane whose chunk lies outside its row's range loads
+// from a small zero buffer instead), and the row metadata of the next tiles is fetched
+// by the lanes while those loads are in flight. A run of tiles with the same row group
+// (pass 1) or column tile (pass 2) accumulates in registers and ends in one partial-sum
+// slot; a second kernel adds each row's (column's) slots in a fixed order, so results are
+// deterministic.
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -29,7 +28,7 @@ namespace {
 
 constexpr int RG = kRowGroup;
 constexpr int TW = kTileW;
-constexpr int kChunks = TW / 128;  // float4 chunks per lane per row
+constexpr int kChunks = TW / 128;  // 4-column chunks per lane per row
 
 // Value formats of the profile. A lane's 4-column chunk is one 16-byte load in FP32 and
 // one 8-byte load in BF16; the raw registers are widened to FP32 at the arithmetic.
@@ -40,8 +39,14 @@ template <> struct Fmt<float> {
   using Raw = float4;
   static constexpr int kUnroll = 2;  // tiles in flight per warp
   static __device__ __forceinline__ const float* vals(const DevSim& d) { return d.S; }
+  // streamed once: first in line for eviction from L1, so the vector slices read by
+  // every warp stay cached
   static __device__ __forceinline__ Raw load(const float* p) {
-    return __ldg(reinterpret_cast<const float4*>(p));
+    Raw r;
+    asm volatile("ld.global.nc.L1::evict_first.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                 : "l"(p));
+    return r;
   }
   static __device__ __forceinline__ float4 widen(const Raw& r) { return r; }
 };
@@ -50,7 +55,11 @@ template <> struct Fmt<unsigned short> {
   static constexpr int kUnroll = 4;
   static __device__ __forceinline__ const unsigned short* vals(const DevSim& d) { return d.Sb; }
   static __device__ __forceinline__ Raw load(const unsigned short* p) {
-    return __ldg(reinterpret_cast<const uint2*>(p));
+    Raw r;
+    asm volatile("ld.global.nc.L1::evict_first.v2.u32 {%0, %1}, [%2];"
+                 : "=r"(r.x), "=r"(r.y)
+                 : "l"(p));
+    return r;
   }
   // a BF16 value is the upper half of the FP32 with the same bits
   static __device__ __forceinline__ float4 widen(const Raw& r) {
@@ -69,64 +78,129 @@ __device__ __forceinline__ float dot4(const float4& a, const float4& b) {
   return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
 }
 
+// Row metadata of the tiles of one batch, held one entry per lane: lane u * 4 + k has
+// row k (of the warp's kRowsPerWarp) of tile t + u. base is the offset of column 0 of the
+// row (so that S + base + c addresses column c).
+struct LaneMeta {
+  int key, other;  // the tile's coordinates in the pass's order
+  int lo, hi;
+  long long base;
+  float y0, y1, y2;  // pass 2: the row's values of y
+};
 
-// z partials: item (rg, [ct0, ct1)) -> p1_part[item][comp][row in group]
+template <bool kWithY>
+__device__ __forceinline__ LaneMeta fetch_meta(const DevSim& d, const int2* tiles, int t_end,
+                                               int t, int lane, int warp, bool pass2) {
+  LaneMeta m;
+  m.key = m.other = -1;
+  m.lo = m.hi = 0;
+  m.base = 0;
+  m.y0 = m.y1 = m.y2 = 0.f;
+  const int u = lane >> 2, k = lane & 3;
+  if (t + u < t_end) {
+    const int2 tl = tiles[t + u];
+    m.key = tl.x;
+    m.other = tl.y;
+    const int rg = pass2 ? tl.y : tl.x;
+    const int r = rg * RG + warp * kRowsPerWarp + k;
+    if (r < d.n) {
+      m.lo = d.lo[r];
+      m.hi = d.hi[r];
+      m.base = d.rowbase[r] - m.lo;
+      if (kWithY) {
+        m.y0 = d.zvec[r];
+        m.y1 = d.zvec[d.n_pad + r];
+        m.y2 = d.zvec[2 * d.n_pad + r];
+      }
+    }
+  }
+  return m;
+}
+
+// z partials: one slot per run of tiles of one row group -> p1_part[slot][comp][row]
 template <class T>
 __global__ void __launch_bounds__(256, 2) k_pass1(DevSim d) {
   using F = Fmt<T>;
-  constexpr int kUnroll = F::kUnroll;
+  constexpr int U = F::kUnroll;
+  static_assert(U * kRowsPerWarp <= 32, "one metadata entry per lane");
   const T* S = F::vals(d);
   const T* zero = reinterpret_cast<const T*>(d.zero);
-  extern __shared__ __align__(16) float4 gsm[];  // [3][q4]
-  const int item = d.p1_order[blockIdx.x];
-  const int4 it = d.p1_items[item];
+  extern __shared__ __align__(16) float4 gsm[];  // [column slot][comp][kTileW / 4]
+  const int t0 = d.s1_cta[blockIdx.x], t1 = d.s1_cta[blockIdx.x + 1];
+  if (t0 >= t1) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c_begin = it.y * TW;
-  const int q4 = (it.z - it.y) * (TW / 4);
-  for (int e = threadIdx.x; e < 3 * q4; e += blockDim.x) {
-    const int comp = e / q4, q = e % q4;
-    gsm[e] = *reinterpret_cast<const float4*>(d.gvec + comp * d.n_pad + c_begin + 4 * q);
-  }
-  const int r_first = it.x * RG + warp * kRowsPerWarp;
-  const T* base[kRowsPerWarp];
-  int lo[kRowsPerWarp], hi[kRowsPerWarp];
-#pragma unroll
-  for (int k = 0; k < kRowsPerWarp; ++k) {
-    const int r = r_first + k;
-    if (r < d.n) {
-      lo[k] = d.lo[r];
-      hi[k] = d.hi[r];
-      base[k] = S + (d.rowbase[r] - lo[k]);
-    } else {
-      lo[k] = hi[k] = 0;
-      base[k] = S;
+  int slot = d.s1_seg_base[blockIdx.x];
+  LaneMeta mt = fetch_meta<false>(d, d.s1_tiles, t1, t0, lane, warp, false);
+  {
+    // the g slices of the CTA's column tiles, copied asynchronously while the first
+    // tiles' loads are issued below
+    const int c0 = d.s1_col_first[blockIdx.x], nc = d.s1_col_first[blockIdx.x + 1] - c0;
+    for (int e = threadIdx.x; e < nc * 3 * (TW / 4); e += blockDim.x) {
+      const int k = e / (3 * (TW / 4)), rem = e % (3 * (TW / 4));
+      const int comp = rem / (TW / 4), q = rem % (TW / 4);
+      const float* src = d.gvec + comp * d.n_pad + d.s1_cols[c0 + k] * TW + 4 * q;
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(gsm + e);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
   }
-  __syncthreads();
+  bool g_ready = false;
+  int cur = __shfl_sync(0xffffffffu, mt.key, 0);
   float acc[kRowsPerWarp][3];
 #pragma unroll
   for (int k = 0; k < kRowsPerWarp; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0.f;
-  for (int ct = it.y; ct < it.z; ct += kUnroll) {
-    typename F::Raw v[kUnroll][kRowsPerWarp][kChunks];
+  auto flush = [&]() {
+    float* out = d.p1_part + (size_t)slot * 3 * RG;
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u)
+    for (int k = 0; k < kRowsPerWarp; ++k)
 #pragma unroll
-      for (int m = 0; m < kChunks; ++m) {
-        const int c = (ct + u) * TW + 4 * lane + 128 * m;
-        const bool tile_ok = ct + u < it.z;
+      for (int comp = 0; comp < 3; ++comp) {
+        const float v = warp_sum(acc[k][comp]);
+        if (lane == 0) out[comp * RG + warp * kRowsPerWarp + k] = v;
+        acc[k][comp] = 0.f;
+      }
+    ++slot;
+  };
+  for (int t = t0; t < t1; t += U) {
+    typename F::Raw v[U][kRowsPerWarp][kChunks];
 #pragma unroll
-        for (int k = 0; k < kRowsPerWarp; ++k) {
-          const bool ok = tile_ok && c >= lo[k] && c < hi[k];
-          v[u][k][m] = F::load(ok ? base[k] + c : zero + 4 * lane);
+    for (int u = 0; u < U; ++u) {
+      const int ct = __shfl_sync(0xffffffffu, mt.other, u * 4);
+#pragma unroll
+      for (int k = 0; k < kRowsPerWarp; ++k) {
+        const int src = u * 4 + k;
+        const int lo = __shfl_sync(0xffffffffu, mt.lo, src);
+        const int hi = __shfl_sync(0xffffffffu, mt.hi, src);
+        const long long base = __shfl_sync(0xffffffffu, mt.base, src);
+#pragma unroll
+        for (int m = 0; m < kChunks; ++m) {
+          const int c = ct * TW + 4 * lane + 128 * m;
+          const bool ok = c >= lo && c < hi;   // empty for tiles past the range (lo = hi)
+          v[u][k][m] = F::load(ok ? S + base + c : zero + 4 * lane);
         }
       }
+    }
+    const int lkey = mt.key;  // this batch's tiles (lanes 4u)
+    const int lslot = (lane & 3) == 0 && t + (lane >> 2) < t1 ? d.s1_col_slot[t + (lane >> 2)] : 0;
+    mt = fetch_meta<false>(d, d.s1_tiles, t1, t + U, lane, warp, false);
+    if (!g_ready) {
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      __syncthreads();
+      g_ready = true;
+    }
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      if (ct + u >= it.z) break;
+    for (int u = 0; u < U; ++u) {
+      if (t + u >= t1) break;
+      const int rg = __shfl_sync(0xffffffffu, lkey, u * 4);
+      const int gs = __shfl_sync(0xffffffffu, lslot, u * 4);
+      if (rg != cur) {
+        flush();
+        cur = rg;
+      }
 #pragma unroll
       for (int m = 0; m < kChunks; ++m) {
-        const int q = (ct + u - it.y) * (TW / 4) + lane + 32 * m;
-        const float4 g0 = gsm[q], g1 = gsm[q4 + q], g2 = gsm[2 * q4 + q];
+        const float4* gp = gsm + gs * 3 * (TW / 4) + lane + 32 * m;
+        const float4 g0 = gp[0], g1 = gp[TW / 4], g2 = gp[2 * (TW / 4)];
 #pragma unroll
         for (int k = 0; k < kRowsPerWarp; ++k) {
           const float4 sv = F::widen(v[u][k][m]);
@@ -137,17 +211,10 @@ __global__ void __launch_bounds__(256, 2) k_pass1(DevSim d) {
       }
     }
   }
-  float* out = d.p1_part + (size_t)item * 3 * RG;
-#pragma unroll
-  for (int k = 0; k < kRowsPerWarp; ++k)
-#pragma unroll
-    for (int comp = 0; comp < 3; ++comp) {
-      const float s = warp_sum(acc[k][comp]);
-      if (lane == 0) out[comp * RG + warp * kRowsPerWarp + k] = s;
-    }
+  flush();
 }
 
-// z_r = sum of its row group's partials, in item order; zero padding beyond n.
+// z_r = sum of its row group's slots, in slot order; zero padding beyond n.
 __global__ void k_reduce1(DevSim d) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= d.n_pad) return;
@@ -157,7 +224,7 @@ __global__ void k_reduce1(DevSim d) {
   }
   const int rg = r / RG, lr = r % RG;
   float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-  for (int i = d.p1_first[rg]; i < d.p1_first[rg + 1]; ++i) {
+  for (int i = d.s1_seg_first[rg]; i < d.s1_seg_first[rg + 1]; ++i) {
     const float* p = d.p1_part + (size_t)i * 3 * RG;
     s0 += p[lr];
     s1 += p[RG + lr];
@@ -168,49 +235,24 @@ __global__ void k_reduce1(DevSim d) {
   d.zvec[2 * d.n_pad + r] = s2;
 }
 
-struct RowMeta {
-  long long base;   // offset of column 0 of the row in S~ (may precede the row)
-  int lo, hi;
-  float y0, y1, y2, pad;
-};
 
-constexpr size_t kP2Meta = sizeof(RowMeta) * kMaxGroupsP2 * RG;
-constexpr size_t kP2Smem = kP2Meta + sizeof(float) * kWarps * 3 * TW;
+constexpr size_t kP2Smem = sizeof(float) * kWarps * 3 * TW;
 
-// x partials: item (ct, row-group list) -> p2_part[item][comp][column in tile]
+// x partials: one slot per run of tiles of one column tile -> p2_part[slot][comp][column]
 template <class T>
 __global__ void __launch_bounds__(256, 2) k_pass2(DevSim d) {
   using F = Fmt<T>;
-  constexpr int kUnroll = F::kUnroll;
+  constexpr int U = F::kUnroll;
+  static_assert(U * kRowsPerWarp <= 32, "one metadata entry per lane");
   const T* S = F::vals(d);
   const T* zero = reinterpret_cast<const T*>(d.zero);
-  extern __shared__ __align__(16) unsigned char smem2[];
-  RowMeta* meta = reinterpret_cast<RowMeta*>(smem2);
-  float* red = reinterpret_cast<float*>(smem2 + kP2Meta);
-  const int item = d.p2_order[blockIdx.x];
-  const int4 it = d.p2_items[item];
+  extern __shared__ __align__(16) float red[];  // [warp][comp][column]
+  const int t0 = d.s2_cta[blockIdx.x], t1 = d.s2_cta[blockIdx.x + 1];
+  if (t0 >= t1) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c0 = it.x * TW;
-  const int nrg = it.z;
-  for (int e = threadIdx.x; e < nrg * RG; e += blockDim.x) {
-    const int r = d.p2_list[it.y + e / RG] * RG + e % RG;
-    RowMeta m;
-    if (r < d.n) {
-      m.lo = d.lo[r];
-      m.hi = d.hi[r];
-      m.base = d.rowbase[r] - m.lo;
-      m.y0 = d.zvec[r];
-      m.y1 = d.zvec[d.n_pad + r];
-      m.y2 = d.zvec[2 * d.n_pad + r];
-    } else {
-      m.lo = m.hi = 0;
-      m.base = 0;
-      m.y0 = m.y1 = m.y2 = 0.f;
-    }
-    m.pad = 0.f;
-    meta[e] = m;
-  }
-  __syncthreads();
+  int slot = d.s2_seg_base[blockIdx.x];
+  LaneMeta mt = fetch_meta<true>(d, d.s2_tiles, t1, t0, lane, warp, true);
+  int cur = __shfl_sync(0xffffffffu, mt.key, 0);
   float acc[kChunks][3][4];
 #pragma unroll
   for (int m = 0; m < kChunks; ++m)
@@ -218,70 +260,89 @@ __global__ void __launch_bounds__(256, 2) k_pass2(DevSim d) {
     for (int comp = 0; comp < 3; ++comp)
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[m][comp][e] = 0.f;
-  for (int li = 0; li < nrg; li += kUnroll) {
-    typename F::Raw v[kUnroll][kRowsPerWarp][kChunks];
+  // every warp reaches a flush at the same tile, so the barriers are uniform
+  auto flush = [&]() {
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const bool grp_ok = li + u < nrg;
-      const RowMeta* rm = meta + (grp_ok ? li + u : li) * RG + warp * kRowsPerWarp;
+    for (int m = 0; m < kChunks; ++m)
+#pragma unroll
+      for (int comp = 0; comp < 3; ++comp) {
+        *reinterpret_cast<float4*>(&red[(warp * 3 + comp) * TW + 4 * lane + 128 * m]) =
+            make_float4(acc[m][comp][0], acc[m][comp][1], acc[m][comp][2], acc[m][comp][3]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[m][comp][e] = 0.f;
+      }
+    __syncthreads();
+    float* out = d.p2_part + (size_t)slot * 3 * TW;
+    for (int idx = threadIdx.x; idx < 3 * TW; idx += blockDim.x) {
+      const int comp = idx / TW, c = idx % TW;
+      float s = 0.f;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) s += red[(w * 3 + comp) * TW + c];
+      out[comp * TW + c] = s;
+    }
+    __syncthreads();
+    ++slot;
+  };
+  for (int t = t0; t < t1; t += U) {
+    typename F::Raw v[U][kRowsPerWarp][kChunks];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int ctu = __shfl_sync(0xffffffffu, mt.key, u * 4);
 #pragma unroll
       for (int k = 0; k < kRowsPerWarp; ++k) {
-        const int lo = rm[k].lo, hi = rm[k].hi;
-        const T* base = S + rm[k].base;
+        const int src = u * 4 + k;
+        const int lo = __shfl_sync(0xffffffffu, mt.lo, src);
+        const int hi = __shfl_sync(0xffffffffu, mt.hi, src);
+        const long long base = __shfl_sync(0xffffffffu, mt.base, src);
 #pragma unroll
         for (int m = 0; m < kChunks; ++m) {
-          const int c = c0 + 4 * lane + 128 * m;
-          const bool ok = grp_ok && c >= lo && c < hi;
-          v[u][k][m] = F::load(ok ? base + c : zero + 4 * lane);
+          const int c = ctu * TW + 4 * lane + 128 * m;
+          const bool ok = c >= lo && c < hi;
+          v[u][k][m] = F::load(ok ? S + base + c : zero + 4 * lane);
         }
       }
     }
+    const float ly0 = mt.y0, ly1 = mt.y1, ly2 = mt.y2;  // this batch's y, one row per lane
+    const int lkey = mt.key;
+    mt = fetch_meta<true>(d, d.s2_tiles, t1, t + U, lane, warp, true);
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      if (li + u >= nrg) break;
-      const RowMeta* rm = meta + (li + u) * RG + warp * kRowsPerWarp;
+    for (int u = 0; u < U; ++u) {
+      if (t + u >= t1) break;
+      const int ct = __shfl_sync(0xffffffffu, lkey, u * 4);
+      if (ct != cur) {
+        flush();
+        cur = ct;
+      }
 #pragma unroll
       for (int k = 0; k < kRowsPerWarp; ++k) {
-        const float y0 = rm[k].y0, y1 = rm[k].y1, y2 = rm[k].y2;
+        const float y0 = __shfl_sync(0xffffffffu, ly0, u * 4 + k);
+        const float y1 = __shfl_sync(0xffffffffu, ly1, u * 4 + k);
+        const float y2 = __shfl_sync(0xffffffffu, ly2, u * 4 + k);
 #pragma unroll
         for (int m = 0; m < kChunks; ++m) {
-          const float4 s = F::widen(v[u][k][m]);
-          acc[m][0][0] += s.x * y0; acc[m][0][1] += s.y * y0;
-          acc[m][0][2] += s.z * y0; acc[m][0][3] += s.w * y0;
-          acc[m][1][0] += s.x * y1; acc[m][1][1] += s.y * y1;
-          acc[m][1][2] += s.z * y1; acc[m][1][3] += s.w * y1;
-          acc[m][2][0] += s.x * y2; acc[m][2][1] += s.y * y2;
-          acc[m][2][2] += s.z * y2; acc[m][2][3] += s.w * y2;
+          const float4 sv = F::widen(v[u][k][m]);
+          acc[m][0][0] += sv.x * y0; acc[m][0][1] += sv.y * y0;
+          acc[m][0][2] += sv.z * y0; acc[m][0][3] += sv.w * y0;
+          acc[m][1][0] += sv.x * y1; acc[m][1][1] += sv.y * y1;
+          acc[m][1][2] += sv.z * y1; acc[m][1][3] += sv.w * y1;
+          acc[m][2][0] += sv.x * y2; acc[m][2][1] += sv.y * y2;
+          acc[m][2][2] += sv.z * y2; acc[m][2][3] += sv.w * y2;
         }
       }
     }
   }
-#pragma unroll
-  for (int m = 0; m < kChunks; ++m)
-#pragma unroll
-    for (int comp = 0; comp < 3; ++comp)
-      *reinterpret_cast<float4*>(&red[(warp * 3 + comp) * TW + 4 * lane + 128 * m]) =
-          make_float4(acc[m][comp][0], acc[m][comp][1], acc[m][comp][2], acc[m][comp][3]);
-  __syncthreads();
-  float* out = d.p2_part + (size_t)item * 3 * TW;
-  for (int idx = threadIdx.x; idx < 3 * TW; idx += blockDim.x) {
-    const int comp = idx / TW, c = idx % TW;
-    float s = 0.f;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) s += red[(w * 3 + comp) * TW + c];
-    out[comp * TW + c] = s;
-  }
+  flush();
 }
 
-// x_c = sum of its column tile's partials, in item order, written to the iterate's
-// displacement dq (AoS, FP32), to xout (AoS), or added into dq.
+// x_c = sum of its column tile's slots, in slot order, written to the iterate's
+// displacement dq (AoS, FP32), to xout (AoS), or added into one of them.
 template <int kMode>
 __global__ void k_reduce2(DevSim d) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= d.n) return;
   const int ct = c / TW, lc = c % TW;
   float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-  for (int i = d.p2_first[ct]; i < d.p2_first[ct + 1]; ++i) {
+  for (int i = d.s2_seg_first[ct]; i < d.s2_seg_first[ct + 1]; ++i) {
     const float* p = d.p2_part + (size_t)i * 3 * TW;
     s0 += p[lc];
     s1 += p[TW + lc];
@@ -298,6 +359,7 @@ __global__ void k_reduce2(DevSim d) {
     out[3 * c + 2] = s2;
   }
 }
+
 
 // Residual of a global solve, rho = rhs - A~ x per component, into gsave (SoA).
 //   kResApply:        rhs = gsave (the saved right-hand side), x = xout
@@ -341,34 +403,37 @@ __global__ void k_residual(DevSim d) {
 
 }  // namespace
 
-constexpr size_t kP1Smem = 3 * kMaxTilesP1 * TW * sizeof(float);
-
 int sinv_setup() {
-  if (cudaFuncSetAttribute(k_pass2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kP2Smem) !=
+  // pass 1 stages the g slices of a CTA's column tiles: up to 3 KB per tile of its range
+  const int most = kMaxStagedCols * 3 * TW * (int)sizeof(float);
+  if (cudaFuncSetAttribute(k_pass1<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, most) !=
           cudaSuccess ||
-      cudaFuncSetAttribute(k_pass1<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kP1Smem) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k_pass2<unsigned short>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kP2Smem) != cudaSuccess ||
       cudaFuncSetAttribute(k_pass1<unsigned short>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kP1Smem) != cudaSuccess)
+                           most) != cudaSuccess)
     return SIM_ECUDA;
   return SIM_OK;
 }
 
 void launch_pass1(const DevSim& d, cudaStream_t s) {
+  const size_t smem = (size_t)d.s1_max_cols * 3 * TW * sizeof(float);
   if (d.s_bf16)
-    k_pass1<unsigned short><<<d.n_p1, 256, kP1Smem, s>>>(d);
+    k_pass1<unsigned short><<<d.s1_grid, 256, smem, s>>>(d);
   else
-    k_pass1<float><<<d.n_p1, 256, kP1Smem, s>>>(d);
+    k_pass1<float><<<d.s1_grid, 256, smem, s>>>(d);
+}
+
+void launch_reduce1(const DevSim& d, cudaStream_t s) {
   k_reduce1<<<(d.n_pad + 255) / 256, 256, 0, s>>>(d);
 }
 
-void launch_pass2(const DevSim& d, cudaStream_t s, int out_mode) {
+void launch_pass2(const DevSim& d, cudaStream_t s) {
   if (d.s_bf16)
-    k_pass2<unsigned short><<<d.n_p2, 256, kP2Smem, s>>>(d);
+    k_pass2<unsigned short><<<d.s2_grid, 256, kP2Smem, s>>>(d);
   else
-    k_pass2<float><<<d.n_p2, 256, kP2Smem, s>>>(d);
+    k_pass2<float><<<d.s2_grid, 256, kP2Smem, s>>>(d);
+}
+
+void launch_reduce2(const DevSim& d, cudaStream_t s, int out_mode) {
   const int g = (d.n + 255) / 256;
   switch (out_mode) {
     case kOutDq: k_reduce2<kOutDq><<<g, 256, 0, s>>>(d); break;

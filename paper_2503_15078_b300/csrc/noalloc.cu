@@ -46,8 +46,8 @@ extern "C" int sim_apply_inverse_noalloc(const sim_t* sim, const float* g, float
   silg::DevSim d = *src;
   d.s_bf16 = 0;  // always the FP32 profile (kept on the device in either precision mode)
   const size_t n_vec = align_up(3 * (size_t)d.n_pad, 64);
-  const size_t n_p1 = align_up((size_t)d.n_p1 * 3 * silg::kRowGroup, 64);
-  const size_t n_p2 = align_up((size_t)d.n_p2 * 3 * silg::kTileW, 64);
+  const size_t n_p1 = align_up((size_t)d.n_seg1 * 3 * silg::kRowGroup, 64);
+  const size_t n_p2 = align_up((size_t)d.n_seg2 * 3 * silg::kTileW, 64);
   if (2 * n_vec + n_p1 + n_p2 > kNoAllocFloats) return SIM_ECAPACITY;
   if (cudaSetDevice(dev) != cudaSuccess) return SIM_ECUDA;
   if (!g_scratch_addr[dev]) {
@@ -63,7 +63,6 @@ extern "C" int sim_apply_inverse_noalloc(const sim_t* sim, const float* g, float
   d.xout = x;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   k_rows_to_soa<<<(d.n_pad + 255) / 256, 256, 0, s>>>(g, d.gvec, d.n, d.n_pad);
-  silg::launch_pass1(d, s);
-  silg::launch_pass2(d, s, silg::kOutX);
+  silg::launch_solve(d, s, silg::kOutX);
   return cudaGetLastError() == cudaSuccess ? SIM_OK : SIM_ECUDA;
 }

@@ -459,86 +459,33 @@ int build_plan(const sim_mesh* mesh, const sim_material* mats, int n_mat, double
     for (int t = 0; t < nt; ++t) th.emplace_back(worker);
     for (auto& t : th) t.join();
   }
-  // ---- tile schedule ----------------------------------------------------------------
+  // ---- tiles of the device products ------------------------------------------------
   const int RG = kRowGroup, TW = kTileW;
-  const int64_t budget = 64 * 1024;  // values per work item
   p.n_rg = (nf + RG - 1) / RG;
   p.n_ct = p.n_pad / TW;
-  std::vector<std::vector<std::pair<int32_t, int32_t>>> tiles_of_ct(p.n_ct);  // (rg, weight)
-  p.p1_items.clear();
-  p.p1_first.assign(p.n_rg + 1, 0);
+  std::vector<std::vector<std::pair<int32_t, int32_t>>> tiles_of_ct(p.n_ct);  // (rg, values)
+  p.tiles1.clear();
   for (int rg = 0; rg < p.n_rg; ++rg) {
-    int r0 = rg * RG, r1 = std::min(nf, r0 + RG);
+    const int r0 = rg * RG, r1 = std::min(nf, r0 + RG);
     int cmin = p.n_pad, cmax = 0;
     for (int r = r0; r < r1; ++r) {
       cmin = std::min(cmin, p.lo[r]);
       cmax = std::max(cmax, p.hi[r]);
     }
-    int ct0 = cmin / TW, ct1 = (cmax + TW - 1) / TW;
-    int64_t acc = 0;
-    int start = ct0;
-    for (int ct = ct0; ct < ct1; ++ct) {
-      int64_t w = 0;
+    for (int ct = cmin / TW; ct < (cmax + TW - 1) / TW; ++ct) {
+      int32_t w = 0;
       for (int r = r0; r < r1; ++r) {
-        int a = std::max(p.lo[r], ct * TW), b = std::min(p.hi[r], (ct + 1) * TW);
+        const int a = std::max(p.lo[r], ct * TW), b = std::min(p.hi[r], (ct + 1) * TW);
         if (b > a) w += b - a;
       }
       if (w == 0) continue;
-      tiles_of_ct[ct].push_back({rg, (int32_t)w});
-      if (acc > 0 && (acc + w > budget || ct - start >= kMaxTilesP1)) {
-        p.p1_items.insert(p.p1_items.end(), {rg, start, ct, (int32_t)acc});
-        start = ct;
-        acc = 0;
-      }
-      if (acc == 0) start = ct;
-      acc += w;
+      p.tiles1.insert(p.tiles1.end(), {rg, ct, w});
+      tiles_of_ct[ct].push_back({rg, w});
     }
-    if (acc > 0) p.p1_items.insert(p.p1_items.end(), {rg, start, ct1, (int32_t)acc});
-    p.p1_first[rg + 1] = (int32_t)(p.p1_items.size() / 4);
   }
-  p.p2_items.clear();
-  p.p2_list.clear();
-  p.p2_first.assign(p.n_ct + 1, 0);
-  for (int ct = 0; ct < p.n_ct; ++ct) {
-    auto& L = tiles_of_ct[ct];
-    int64_t acc = 0;
-    int off = (int)p.p2_list.size();
-    for (auto& e : L) {
-      const int in_item = (int)p.p2_list.size() - off;
-      if (acc > 0 && (acc + e.second > budget || in_item >= kMaxGroupsP2)) {
-        int cnt = (int)p.p2_list.size() - off;
-        p.p2_items.insert(p.p2_items.end(), {ct, off, cnt, (int32_t)acc});
-        off = (int)p.p2_list.size();
-        acc = 0;
-      }
-      p.p2_list.push_back(e.first);
-      acc += e.second;
-    }
-    if (acc > 0) {
-      int cnt = (int)p.p2_list.size() - off;
-      p.p2_items.insert(p.p2_items.end(), {ct, off, cnt, (int32_t)acc});
-    }
-    p.p2_first[ct + 1] = (int32_t)(p.p2_items.size() / 4);
-  }
-  auto by_weight = [](const std::vector<int32_t>& items, std::vector<int32_t>& order) {
-    const int m = (int)items.size() / 4;
-    order.resize(m);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int b) { return items[4 * a + 3] > items[4 * b + 3]; });
-  };
-  for (size_t k = 0; k < p.p1_items.size(); k += 4)
-    if (p.p1_items[k + 2] - p.p1_items[k + 1] > kMaxTilesP1 || p.p1_items[k + 2] <= p.p1_items[k + 1]) {
-      *err = "internal: pass-1 item spans too many column tiles";
-      return SIM_EINVAL;
-    }
-  for (size_t k = 0; k < p.p2_items.size(); k += 4)
-    if (p.p2_items[k + 2] <= 0) {
-      *err = "internal: empty pass-2 item";
-      return SIM_EINVAL;
-    }
-  by_weight(p.p1_items, p.p1_order);
-  by_weight(p.p2_items, p.p2_order);
+  p.tiles2.clear();
+  for (int ct = 0; ct < p.n_ct; ++ct)
+    for (auto& e : tiles_of_ct[ct]) p.tiles2.insert(p.tiles2.end(), {ct, e.first, e.second});
   p.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return SIM_OK;
 }
@@ -571,6 +518,76 @@ void apply_inverse_internal(const Plan& p, const double* b, double* x) {
       x[3 * c + 2] += s * z[3 * i + 2];
     }
   }
+}
+
+void build_stream_schedule(const Plan& p, bool pass2, int grid, double zero_cost,
+                           StreamSchedule* out) {
+  const std::vector<int32_t>& T = pass2 ? p.tiles2 : p.tiles1;
+  const int nt = (int)T.size() / 3;
+  const int n_keys = pass2 ? p.n_ct : p.n_rg;
+  grid = std::max(1, grid);
+  // cost of a tile: its stored values plus a share of the loads issued for its empty
+  // positions (those are served from the zero page in L1, not from memory)
+  std::vector<double> pre(nt + 1, 0.0);
+  for (int t = 0; t < nt; ++t)
+    pre[t + 1] = pre[t] + T[3 * t + 2] + zero_cost * (kRowGroup * kTileW - T[3 * t + 2]);
+  out->tiles.resize(2 * (size_t)nt);
+  for (int t = 0; t < nt; ++t) {
+    out->tiles[2 * t] = T[3 * t];
+    out->tiles[2 * t + 1] = T[3 * t + 1];
+  }
+  out->cta_first.assign(grid + 1, nt);
+  int t = 0;
+  for (int c = 0; c < grid; ++c) {
+    const double target = pre[nt] * c / grid;
+    while (t < nt && pre[t + 1] <= target) ++t;
+    out->cta_first[c] = t;
+  }
+  out->cta_first[grid] = nt;
+  for (int c = 1; c <= grid; ++c) out->cta_first[c] = std::max(out->cta_first[c], out->cta_first[c - 1]);
+  // distinct second coordinates (pass 1: column tiles) of each CTA's range
+  out->cta_col_first.assign(grid + 1, 0);
+  out->cta_cols.clear();
+  out->tile_col_slot.assign(nt, 0);
+  out->max_cols = 0;
+  for (int c = 0; c < grid; ++c) {
+    out->cta_col_first[c] = (int)out->cta_cols.size();
+    const int first = (int)out->cta_cols.size();
+    for (int u = out->cta_first[c]; u < out->cta_first[c + 1]; ++u) {
+      const int col = T[3 * u + 1];
+      int pos = -1;
+      for (int k = first; k < (int)out->cta_cols.size(); ++k)
+        if (out->cta_cols[k] == col) pos = k - first;
+      if (pos < 0) {
+        pos = (int)out->cta_cols.size() - first;
+        out->cta_cols.push_back(col);
+      }
+      out->tile_col_slot[u] = pos;
+    }
+    out->max_cols = std::max(out->max_cols, (int)out->cta_cols.size() - first);
+  }
+  out->cta_col_first[grid] = (int)out->cta_cols.size();
+  // partial-sum slots: one per run of equal keys inside a CTA's range, numbered CTA by
+  // CTA, so the slots of each key are contiguous and in a fixed order
+  out->seg_base.assign(grid, 0);
+  out->seg_first.assign(n_keys + 1, -1);
+  int slot = 0;
+  for (int c = 0; c < grid; ++c) {
+    out->seg_base[c] = slot;
+    int prev = -1;
+    for (int u = out->cta_first[c]; u < out->cta_first[c + 1]; ++u) {
+      const int key = T[3 * u];
+      if (key != prev) {
+        if (out->seg_first[key] < 0) out->seg_first[key] = slot;
+        ++slot;
+        prev = key;
+      }
+    }
+  }
+  out->n_seg = slot;
+  out->seg_first[n_keys] = slot;
+  for (int k = n_keys - 1; k >= 0; --k)
+    if (out->seg_first[k] < 0) out->seg_first[k] = out->seg_first[k + 1];
 }
 
 }  // namespace silg

@@ -23,11 +23,6 @@ constexpr int kAlign = 8;
 // Device tile shape of the two profile products: kRowGroup rows x kTileW columns.
 constexpr int kRowGroup = 32;
 constexpr int kTileW = 256;
-// Work-item limits (the kernels stage an item's vector slice and row metadata in shared
-// memory): a pass-1 item spans at most kMaxTilesP1 column tiles, a pass-2 item at most
-// kMaxGroupsP2 row groups.
-constexpr int kMaxTilesP1 = 8;
-constexpr int kMaxGroupsP2 = 32;
 
 struct MatParams {
   int model;
@@ -80,20 +75,13 @@ struct Plan {
   std::vector<double> S;          // stored values (zeros outside [fd(i), i])
   int64_t nnz_S = 0;
 
-  // ---- tile schedule of the device products ----------------------------------------
-  // pass 1 (z = S g): item = (row group, [ct_begin, ct_end)); pass 2 (x = S^T y): item
-  // = (column tile, list of row groups). Reductions: rows of group rg sum the pass-1
-  // partials of items [p1_first[rg], p1_first[rg+1]); columns of tile ct sum the pass-2
-  // partials of items [p2_first[ct], p2_first[ct+1]).
+  // ---- tiles of the device products ------------------------------------------------
+  // Tiles of kRowGroup rows x kTileW columns that hold stored values. tiles1: (row group,
+  // column tile, values) ordered by row group, then column tile (pass 1, z = S g);
+  // tiles2: (column tile, row group, values) ordered by column tile, then row group
+  // (pass 2, x = S^T y).
   int n_rg = 0, n_ct = 0;
-  std::vector<int32_t> p1_items;  // 4 ints per item: rg, ct_begin, ct_end, weight
-  std::vector<int32_t> p1_first;  // n_rg + 1
-  std::vector<int32_t> p2_items;  // 4 ints per item: ct, list_off, list_cnt, weight
-  std::vector<int32_t> p2_first;  // n_ct + 1
-  std::vector<int32_t> p2_list;   // row groups
-  // processing orders: items by decreasing weight (the persistent kernels deal them out
-  // round-robin, largest first)
-  std::vector<int32_t> p1_order, p2_order;
+  std::vector<int32_t> tiles1, tiles2;
 
   // ---- statistics -----------------------------------------------------------------
   int64_t nnz_A = 0, nnz_L = 0;
@@ -104,6 +92,26 @@ struct Plan {
 // Build the plan. Returns SIM_OK or an error code; *err receives a message.
 int build_plan(const sim_mesh* mesh, const sim_material* mats, int n_mat, double h,
                int n_threads, Plan* plan, std::string* err);
+
+// Device work split of one product: CTA c streams tiles [cta_first[c], cta_first[c+1])
+// of the pass's tile order, split so that every CTA has about the same cost; each run of
+// tiles with the same key (row group in pass 1, column tile in pass 2) inside a CTA writes
+// one partial-sum slot, seg_base[c] being the CTA's first; the slots of key k are
+// [seg_first[k], seg_first[k+1]).
+struct StreamSchedule {
+  std::vector<int32_t> tiles;      // 2 per tile: key, other coordinate
+  // pass 1: the distinct column tiles of each CTA's range (cta_cols[cta_col_first[c] ..
+  // cta_col_first[c+1])), the position of each tile's column tile in that list, and the
+  // longest list
+  std::vector<int32_t> cta_col_first, cta_cols, tile_col_slot;
+  int max_cols = 0;
+  std::vector<int32_t> cta_first;  // grid + 1
+  std::vector<int32_t> seg_base;   // grid
+  std::vector<int32_t> seg_first;  // keys + 1
+  int n_seg = 0;
+};
+void build_stream_schedule(const Plan& p, bool pass2, int grid, double zero_cost,
+                           StreamSchedule* out);
 
 // x = S^T (S b) on the host in FP64, internal free numbering, b and x of n_free x 3.
 void apply_inverse_internal(const Plan& p, const double* b, double* x);

@@ -19,6 +19,10 @@ namespace {
 using silg::DevSim;
 using silg::Plan;
 
+// event marks per iteration in the frame graph: after the local step, the assembly, the
+// first product, its reduction, the constraint solve, the second product and its reduction
+constexpr int kMarksPerIter = 7;
+
 struct Graph {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -41,7 +45,7 @@ struct sim_s {
   int64_t frame = 0;
   int last_iters = 0;
   // phase events recorded by event nodes of the frame graph: [0] frame start,
-  // [1] after collision, [2] after Delassus, then 5 per iteration, then [end]
+  // [1] after collision, [2] after Delassus, then kMarksPerIter per iteration, then [end]
   std::vector<cudaEvent_t> ev;
   std::vector<int32_t> tet_caller_order;
 
@@ -105,6 +109,8 @@ int refined_iters(const sim_s* s, int K) {
 
 int kernels_per_frame(const sim_s* s, int K) {
   const bool c = s->has_obstacles;
+  // per iteration: local, [contact eval], rhs, pass 1 + reduction, [Y^T z, CR, Y u],
+  // pass 2 + reduction; a residual correction adds the residual and both passes
   return 1 + (c ? 4 + 11 : 0) + K * (1 + (c ? 1 : 0) + 1 + 2 + (c ? 3 : 0) + 2) + (c ? 1 : 0) + 1 +
          5 * refined_iters(s, K);
 }
@@ -122,7 +128,7 @@ void enqueue_frame(sim_s* s, int K, cudaStream_t st) {
   if (s->has_obstacles) silg::launch_delassus(d, st);
   mark(2);
   for (int k = 0; k < K; ++k) {
-    const int e = 3 + 5 * k;
+    const int e = 3 + kMarksPerIter * k;
     silg::launch_local(d, st, false);
     mark(e);
     if (s->has_obstacles) silg::launch_contact_eval(d, st, k, false);
@@ -130,27 +136,30 @@ void enqueue_frame(sim_s* s, int K, cudaStream_t st) {
     mark(e + 1);
     silg::launch_pass1(d, st);
     mark(e + 2);
+    silg::launch_reduce1(d, st);
+    mark(e + 3);
     if (s->has_obstacles) {
       silg::launch_ytz(d, st);
       silg::launch_cr(d, st, s->cluster);
       silg::launch_yu(d, st);
     }
-    mark(e + 3);
-    silg::launch_pass2(d, st, silg::kOutDq);
+    mark(e + 4);
+    silg::launch_pass2(d, st);
+    mark(e + 5);
+    silg::launch_reduce2(d, st, silg::kOutDq);
     if (k >= K - refined_iters(s, K)) {
       // BF16 profile: dq += S~^T S~ (rhs - A~ dq), the residual summed in FP64 and the
       // iteration's contact impulses held fixed
       silg::launch_residual(d, st, s->has_obstacles ? silg::kResFrameContact : silg::kResFrame);
       DevSim dr = d;
       dr.gvec = d.gsave;
-      silg::launch_pass1(dr, st);
-      silg::launch_pass2(dr, st, silg::kOutAddDq);
+      silg::launch_solve(dr, st, silg::kOutAddDq);
     }
-    mark(e + 4);
+    mark(e + 6);
   }
   if (s->has_obstacles) silg::launch_contact_eval(d, st, K, true);
   silg::launch_integrate(d, st);
-  mark(3 + 5 * K);
+  mark(3 + kMarksPerIter * K);
 }
 
 int get_graph(sim_s* s, int K, cudaGraphExec_t* out) {
@@ -172,6 +181,46 @@ int get_graph(sim_s* s, int K, cudaGraphExec_t* out) {
   }
   s->graphs[K] = g;
   *out = g.exec;
+  return SIM_OK;
+}
+
+// Build and upload the balanced tile streams of the two profile products for the given
+// grid sizes and zero-load cost; (re)allocates the partial-sum slots.
+int upload_schedules(sim_s* s, int grid1, int grid2, double zero_cost) {
+  const Plan& p = s->plan;
+  DevSim& d = s->d;
+  silg::StreamSchedule s1, s2;
+  silg::build_stream_schedule(p, false, grid1, zero_cost, &s1);
+  // pass 1 stages the g slices of a CTA's column tiles in shared memory (3 KB each, at
+  // most silg::kMaxStagedCols): more CTAs when a range has too many
+  while (s1.max_cols > silg::kMaxStagedCols && grid1 < (1 << 20)) {
+    grid1 *= 2;
+    silg::build_stream_schedule(p, false, grid1, zero_cost, &s1);
+  }
+  silg::build_stream_schedule(p, true, grid2, zero_cost, &s2);
+  auto pairs = [](const std::vector<int32_t>& v) {
+    std::vector<int2> o(v.size() / 2);
+    for (size_t k = 0; k < o.size(); ++k) o[k] = make_int2(v[2 * k], v[2 * k + 1]);
+    return o;
+  };
+  d.s1_tiles = s->upload(pairs(s1.tiles));
+  d.s1_cta = s->upload(s1.cta_first);
+  d.s1_seg_base = s->upload(s1.seg_base);
+  d.s1_seg_first = s->upload(s1.seg_first);
+  d.s2_tiles = s->upload(pairs(s2.tiles));
+  d.s2_cta = s->upload(s2.cta_first);
+  d.s2_seg_base = s->upload(s2.seg_base);
+  d.s2_seg_first = s->upload(s2.seg_first);
+  d.s1_col_first = s->upload(s1.cta_col_first);
+  d.s1_cols = s->upload(s1.cta_cols);
+  d.s1_col_slot = s->upload(s1.tile_col_slot);
+  d.s1_max_cols = s1.max_cols;
+  d.s1_grid = grid1;
+  d.s2_grid = grid2;
+  d.n_seg1 = s1.n_seg;
+  d.n_seg2 = s2.n_seg;
+  d.p1_part = s->alloc<float>((size_t)std::max(1, s1.n_seg) * 3 * silg::kRowGroup);
+  d.p2_part = s->alloc<float>((size_t)std::max(1, s2.n_seg) * 3 * silg::kTileW);
   return SIM_OK;
 }
 
@@ -287,29 +336,14 @@ int create_device(sim_s* s, const sim_obstacle* obstacles, int n_obs, const sim_
     d.rowbase = s->upload(rb);
     d.lo = s->upload(p.lo);
     d.hi = s->upload(p.hi);
-    std::vector<int4> it1(p.p1_items.size() / 4), it2(p.p2_items.size() / 4);
-    for (size_t k = 0; k < it1.size(); ++k)
-      it1[k] = make_int4(p.p1_items[4 * k], p.p1_items[4 * k + 1], p.p1_items[4 * k + 2], p.p1_items[4 * k + 3]);
-    for (size_t k = 0; k < it2.size(); ++k)
-      it2[k] = make_int4(p.p2_items[4 * k], p.p2_items[4 * k + 1], p.p2_items[4 * k + 2], p.p2_items[4 * k + 3]);
     d.n_rg = p.n_rg;
     d.n_ct = p.n_ct;
-    d.n_p1 = (int)it1.size();
-    d.n_p2 = (int)it2.size();
-    d.p1_items = s->upload(it1);
-    d.p2_items = s->upload(it2);
-    d.p1_first = s->upload(p.p1_first);
-    d.p2_first = s->upload(p.p2_first);
-    d.p2_list = s->upload(p.p2_list);
-    d.p1_order = s->upload(p.p1_order);
-    d.p2_order = s->upload(p.p2_order);
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     d.n_sm = std::max(1, nsm);
     d.zero = s->alloc<float>(silg::kTileW);
-    d.p1_part = s->alloc<float>((size_t)d.n_p1 * 3 * silg::kRowGroup);
-    d.p2_part = s->alloc<float>((size_t)d.n_p2 * 3 * silg::kTileW);
+    if (int st = upload_schedules(s, 2 * d.n_sm, 2 * d.n_sm, 1.0); st != SIM_OK) return st;
   }
   d.gvec = s->alloc<float>(3 * (size_t)p.n_pad);
   d.zvec = s->alloc<float>(3 * (size_t)p.n_pad);
@@ -387,7 +421,7 @@ int create_device(sim_s* s, const sim_obstacle* obstacles, int n_obs, const sim_
   d.kb_hi = s->alloc<int>(n / 32 + 1);
   d.wt_part = s->alloc<float>((size_t)silg::wt_items_max(cap, d.wt_grid) * 64 * 64);
   if (silg::sinv_setup() != SIM_OK) return SIM_ECUDA;
-  s->ev.resize(4 + 5 * silg::kMaxIters);
+  s->ev.resize(4 + kMarksPerIter * silg::kMaxIters);
   for (auto& e : s->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return SIM_ECUDA;
   d.cr_split = s->alloc<int>(2 * (silg::kCrMaxRanks + 1));
@@ -566,7 +600,7 @@ int sim_get_phase_times(sim_t* s, double* ms) {
   for (int k = 0; k < SIM_NUM_PHASES; ++k) ms[k] = 0.0;
   if (s->frame == 0 || s->last_iters == 0) return SIM_OK;
   const int K = s->last_iters;
-  cudaError_t e = cudaEventSynchronize(s->ev[3 + 5 * K]);
+  cudaError_t e = cudaEventSynchronize(s->ev[3 + kMarksPerIter * K]);
   if (e != cudaSuccess) return cuda_status(e);
   auto el = [&](int a, int b) {
     float t = 0.f;
@@ -576,14 +610,15 @@ int sim_get_phase_times(sim_t* s, double* ms) {
   ms[SIM_PHASE_COLLIDE] = el(0, 1);
   ms[SIM_PHASE_DELASSUS] = el(1, 2);
   for (int k = 0; k < K; ++k) {
-    const int b = 3 + 5 * k;
+    const int b = 3 + kMarksPerIter * k;
     ms[SIM_PHASE_LOCAL] += el(b - 1, b);
     ms[SIM_PHASE_ASSEMBLE] += el(b, b + 1);
     ms[SIM_PHASE_SPMV1] += el(b + 1, b + 2);
-    ms[SIM_PHASE_SOLVE] += el(b + 2, b + 3);
-    ms[SIM_PHASE_SPMV2] += el(b + 3, b + 4);
+    ms[SIM_PHASE_REDUCE] += el(b + 2, b + 3) + el(b + 5, b + 6);
+    ms[SIM_PHASE_SOLVE] += el(b + 3, b + 4);
+    ms[SIM_PHASE_SPMV2] += el(b + 4, b + 5);
   }
-  ms[SIM_PHASE_INTEGRATE] = el(3 + 5 * K - 1, 3 + 5 * K);
+  ms[SIM_PHASE_INTEGRATE] = el(3 + kMarksPerIter * K - 1, 3 + kMarksPerIter * K);
   return SIM_OK;
 }
 
@@ -633,16 +668,14 @@ int sim_apply_inverse(sim_t* s, const double* b, double* x) {
     for (int r = 0; r < 3; ++r) g[(size_t)r * np + k] = (float)b[3 * (size_t)p.order[k] + r];
   cudaStreamSynchronize(s->launch);
   cudaMemcpyAsync(s->d.gvec, g.data(), g.size() * sizeof(float), cudaMemcpyHostToDevice, s->work);
-  silg::launch_pass1(s->d, s->work);
-  silg::launch_pass2(s->d, s->work, silg::kOutX);
+  silg::launch_solve(s->d, s->work, silg::kOutX);
   if (s->d.s_bf16 && s->d.refine > 0) {
     // x += S~^T S~ (b - A~ x), the residual summed in FP64
     cudaMemcpyAsync(s->d.gsave, g.data(), g.size() * sizeof(float), cudaMemcpyHostToDevice, s->work);
     silg::launch_residual(s->d, s->work, silg::kResApply);
     DevSim dr = s->d;
     dr.gvec = s->d.gsave;
-    silg::launch_pass1(dr, s->work);
-    silg::launch_pass2(dr, s->work, silg::kOutAddX);
+    silg::launch_solve(dr, s->work, silg::kOutAddX);
   }
   std::vector<float> xo(3 * (size_t)n);
   cudaMemcpyAsync(xo.data(), s->d.xout, xo.size() * sizeof(float), cudaMemcpyDeviceToHost, s->work);
