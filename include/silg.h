@@ -182,6 +182,35 @@ int sim_plan_apply_inverse_host(const sim_plan_t* plan, const double* b, double*
 int sim_create(const sim_mesh* mesh, const sim_material* mats, int32_t n_mat,
                const sim_obstacle* obstacles, int32_t n_obs, double h,
                const sim_options* opts, sim_t** out);
+
+/* One independent scene of a batch: its mesh, its materials (tet_material indexes this
+ * list), its obstacles (they act on this scene's vertices only) and its contact margin
+ * (<= 0: half the scene's mean edge; opts->contact_margin is not used by a batch). */
+typedef struct {
+  sim_mesh mesh;
+  const sim_material* materials;
+  int32_t n_materials;
+  const sim_obstacle* obstacles;
+  int32_t n_obstacles;
+  double contact_margin;
+} sim_scene;
+
+/*
+ * Many independent scenes of uneven size in one simulator: every kernel of a frame runs
+ * once over all scenes (no per-scene launches). Vertices (and tets) are numbered scene
+ * after scene: scene s's vertex v is vertex sum_{s'<s} n_verts(s') + v of every state,
+ * contact and Delassus accessor. The system matrix is block diagonal (one elimination
+ * forest, ordered scene by scene), the Delassus operator is stored as one block per scene
+ * and each scene's constraint solve runs in its own thread-block cluster with its own
+ * scalars, so a scene's frame is the frame it would have alone (up to the rounding of its
+ * reordered sums). Errors as sim_create; n_scenes < 1 or a NULL list: SIM_EINVAL.
+ */
+int sim_create_batch(const sim_scene* scenes, int32_t n_scenes, double h,
+                     const sim_options* opts, sim_t** out);
+/* Per-scene residuals of the last frame: out[s * (n_iters + 1) + k] for scene s, iteration
+ * k (the same measure as sim_stats.residual, over the scene's contacts; 0 without contacts).
+ * capacity: doubles available in out. */
+int sim_get_scene_residuals(sim_t* sim, int32_t capacity, double* out);
 void sim_destroy(sim_t* sim);
 
 /* One frame of Alg. 4 with n_iters local-global iterations (n_iters <= 0: the option's

@@ -158,27 +158,64 @@ def _torch_stream():
 
 
 class Simulator:
-    """One scene on one GPU. Every method is a thin call into the C ABI."""
+    """One scene, or a batch of independent scenes (a list), on one GPU. Every method is a
+    thin call into the C ABI. A batch numbers vertices scene after scene; scene_offsets
+    gives each scene's first vertex."""
 
     def __init__(self, scene, use_torch_stream=True, **opts):
-        mesh, mats, obs, self._keep = _mesh_args(scene)
-        o = _options(scene, **opts)
+        batch = isinstance(scene, (list, tuple))
+        first = scene[0] if batch else scene
+        o = _options(first, **opts)
         if use_torch_stream and "cuda_stream" not in opts:
             s = _torch_stream()
             if s is not None:
                 o.cuda_stream = s
         handle = C.c_void_p()
-        _check(lib().sim_create(C.byref(mesh), mats, len(scene.materials), obs,
-                                len(scene.obstacles), float(scene.h), C.byref(o),
-                                C.byref(handle)), "sim_create")
+        if batch:
+            scs = (_abi.SimScene * len(scene))()
+            self._keep = []
+            for k, sc in enumerate(scene):
+                mesh, mats, obs, keep = _mesh_args(sc)
+                self._keep.append((mats, obs, keep))
+                scs[k].mesh = mesh
+                scs[k].materials = C.cast(mats, C.POINTER(_abi.SimMaterial))
+                scs[k].n_materials = len(sc.materials)
+                scs[k].obstacles = C.cast(obs, C.POINTER(_abi.SimObstacle))
+                scs[k].n_obstacles = len(sc.obstacles)
+                scs[k].contact_margin = float(getattr(sc, "contact_margin", 0.0))
+            self._keep.append(scs)
+            _check(lib().sim_create_batch(scs, len(scene), float(first.h), C.byref(o),
+                                          C.byref(handle)), "sim_create_batch")
+            sizes = [sc.n_verts for sc in scene]
+            self.scene_offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+            self.n_verts = int(self.scene_offsets[-1])
+            self.n_tets = int(sum(len(sc.tets) for sc in scene))
+            self.n_scenes = len(scene)
+            q0 = np.concatenate([sc.q0 for sc in scene])
+            v0 = np.concatenate([sc.v0 for sc in scene])
+        else:
+            mesh, mats, obs, self._keep = _mesh_args(scene)
+            _check(lib().sim_create(C.byref(mesh), mats, len(scene.materials), obs,
+                                    len(scene.obstacles), float(scene.h), C.byref(o),
+                                    C.byref(handle)), "sim_create")
+            self.n_verts = mesh.n_verts
+            self.n_tets = mesh.n_tets
+            self.n_scenes = 1
+            self.scene_offsets = np.array([0, mesh.n_verts], dtype=np.int64)
+            q0 = getattr(scene, "q0", None)
+            v0 = getattr(scene, "v0", None)
         self._h = handle
-        self.n_verts = mesh.n_verts
-        self.n_tets = mesh.n_tets
         self.options = o
-        q0 = getattr(scene, "q0", None)
-        v0 = getattr(scene, "v0", None)
         if q0 is not None:
             self.set_state(q0, v0 if v0 is not None else np.zeros_like(q0))
+
+    def scene_residuals(self):
+        """(n_scenes, n_iters + 1) residuals of the last frame, per scene."""
+        K = self.stats()["n_iters"]
+        out = np.zeros((self.n_scenes, K + 1))
+        _check(lib().sim_get_scene_residuals(self._h, out.size, _dptr(out)),
+               "sim_get_scene_residuals")
+        return out
 
     def close(self):
         h = getattr(self, "_h", None)

@@ -34,6 +34,12 @@ class SimObstacle(C.Structure):
                 ("radius", C.c_double), ("mu", C.c_double), ("vel", C.c_double * 3)]
 
 
+class SimScene(C.Structure):
+    _fields_ = [("mesh", SimMesh), ("materials", C.POINTER(SimMaterial)),
+                ("n_materials", C.c_int32), ("obstacles", C.POINTER(SimObstacle)),
+                ("n_obstacles", C.c_int32), ("contact_margin", C.c_double)]
+
+
 class SimOptions(C.Structure):
     _fields_ = [("n_iters", C.c_int32), ("n_cr_iters", C.c_int32), ("s_precision", C.c_int32),
                 ("refine", C.c_int32), ("contact_capacity", C.c_int32), ("device", C.c_int32),
@@ -59,6 +65,9 @@ class SimPlanInfo(C.Structure):
 
 # name -> (restype, argtypes); every entry must be exported by libsilg.so
 PROTOTYPES = {
+    "sim_create_batch": (C.c_int, [C.POINTER(SimScene), C.c_int32, C.c_double,
+                                   C.POINTER(SimOptions), C.POINTER(C.c_void_p)]),
+    "sim_get_scene_residuals": (C.c_int, [C.c_void_p, C.c_int32, _dp]),
     "sim_strerror": (C.c_char_p, [C.c_int]),
     "sim_default_options": (None, [C.POINTER(SimOptions)]),
     "sim_plan_create": (C.c_int, [C.POINTER(SimMesh), C.POINTER(SimMaterial), C.c_int32,

@@ -43,9 +43,26 @@ struct DevSim {
   int n, n_all, n_tets, n_pad, n_obs, n_mat;
   int cap, cap_y, n_cr;
   int n_rg, n_ct;
-  double h, margin, L_ref;
+  double h;
   float h2f;        // h^2 in FP32
-  double grav[3], handle_vel[3];
+  double grav[3];
+  // scenes (one for sim_create): vertices are ordered scene by scene
+  int n_scenes;
+  const int* vert_scene;      // n_all (internal numbering)
+  const int* scene_vfirst;    // n_scenes + 1: first internal free vertex of each scene
+  const int* obst_scene;      // n_obs: the scene an obstacle acts on
+  const double* scene_margin; // contact margin
+  const double* scene_Lref;   // rest bounding-box diagonal (residual scale)
+  const double* scene_hvel;   // 3 per scene: velocity of the scene's pinned vertices
+  // per frame, from the contact lists (k_scene_ranges): contact vertices [sc_cvb[s],
+  // sc_cvb[s+1]) and contacts [sc_jb[s], sc_jb[s+1]) of scene s; its W~ block (row-major,
+  // ld sc_ld[s]) at sc_wtoff[s]; its first 64 x 64 W~ tile in the tile list
+  int* sc_cvb;
+  int* sc_jb;
+  int* sc_ld;
+  long long* sc_wtoff;
+  int* sc_tileoff;
+  double* resid_scene;        // n_scenes x (kMaxIters + 1)
 
   // per vertex (internal numbering, n_all)
   double* q_t;      // 3 n_all
@@ -156,8 +173,9 @@ struct DevSim {
   int* kb_hi;
   float* wt_part;   // partial 64 x 64 tiles of W~
   int wt_grid;      // CTAs of the W~ product
-  int cr_R;         // CTAs in the CR cluster
-  int* cr_split;    // 2 (kCrMaxRanks + 1): first contact vertex, first contact per rank
+  int cr_R;         // CTAs per CR cluster (one cluster per scene)
+  int* cr_split;    // per scene 2 (kCrMaxRanks + 1): first contact vertex (scene-local) and
+                    // first contact (global) of each rank
   unsigned long long spin_limit;  // polls of a device-side wait before it reports a timeout
   // diagnostics
   double* resid;    // kMaxIters + 1
@@ -212,7 +230,7 @@ int launch_cr(const DevSim& d, cudaStream_t s, int cluster);
 void launch_yu(const DevSim& d, cudaStream_t s);
 void launch_integrate(const DevSim& d, cudaStream_t s);
 void launch_scan(const int* in, int* out, int n, const int* n_dev, int* total, cudaStream_t s);
-int cr_setup(int* cluster_out, size_t* smem_out);
+int cr_setup(int n_scenes, int* cluster_out, size_t* smem_out);
 int sinv_setup();
 
 }  // namespace silg

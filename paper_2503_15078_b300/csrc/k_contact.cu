@@ -102,11 +102,13 @@ __global__ void k_collide_count(DevSim d) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n) return;
   double x[3] = {d.s_tilde[3 * i], d.s_tilde[3 * i + 1], d.s_tilde[3 * i + 2]};
+  const int sc = d.vert_scene[i];
+  const double margin = d.scene_margin[sc];
   int cnt = 0;
   for (int o = 0; o < d.n_obs; ++o) {
-    if (!maybe_contact(d.obst[o], x, d.margin)) continue;
+    if (d.obst_scene[o] != sc || !maybe_contact(d.obst[o], x, margin)) continue;
     double nn[3], ph[3];
-    if (obst_query(d.obst[o], x, nn, ph) < d.margin) ++cnt;
+    if (obst_query(d.obst[o], x, nn, ph) < margin) ++cnt;
   }
   d.ct_cnt[i] = cnt;
   d.cv_flag[i] = cnt > 0;
@@ -124,11 +126,13 @@ __global__ void k_collide_write(DevSim d) {
     d.cv_first[cv] = j;
     d.cv_nct[cv] = d.ct_cnt[i];
   }
+  const int sc = d.vert_scene[i];
+  const double margin = d.scene_margin[sc];
   for (int o = 0; o < d.n_obs; ++o) {
     const ObstDev& ob = d.obst[o];
-    if (!maybe_contact(ob, x, d.margin)) continue;
+    if (d.obst_scene[o] != sc || !maybe_contact(ob, x, margin)) continue;
     double n[3], ph[3];
-    if (!(obst_query(ob, x, n, ph) < d.margin)) continue;
+    if (!(obst_query(ob, x, n, ph) < margin)) continue;
     if (j < d.cap) {
       double f1[3], f2[3];
       tangent_frame(n, f1, f2);
@@ -278,10 +282,19 @@ constexpr int kWtKB = 32;        // rows of Y per block
 constexpr int kWtThreads = 128;  // 8 x 4 outputs per thread
 constexpr int kWtList = 1024;    // row blocks staged per round
 
-__device__ __forceinline__ void wt_layout(int ncv, int target, int& nb, int& ntiles, int& S) {
-  nb = (ncv + kWtT - 1) / kWtT;
-  ntiles = nb * (nb + 1) / 2;
-  S = ntiles > 0 ? min(kWtMaxSplit, max(1, (target + ntiles - 1) / ntiles)) : 1;
+// K splits for ntiles tiles so that there are about `target` work items
+__device__ __forceinline__ int wt_splits(int ntiles, int target) {
+  return ntiles > 0 ? min(kWtMaxSplit, max(1, (target + ntiles - 1) / ntiles)) : 1;
+}
+
+// tile t of the list of every scene's lower-triangle tiles -> scene, block row I, column J
+__device__ __forceinline__ int tile_scene(const DevSim& d, int t) {
+  int lo = 0, hi = d.n_scenes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (d.sc_tileoff[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
 }
 
 __device__ __forceinline__ void tri_decode(int t, int& I, int& J) {
@@ -290,6 +303,33 @@ __device__ __forceinline__ void tri_decode(int t, int& I, int& J) {
   while (i * (i + 1) / 2 > t) --i;
   I = i;
   J = t - i * (i + 1) / 2;
+}
+
+// Per-scene ranges of the contact lists (contacts and contact vertices are sorted by
+// internal vertex, and vertices are ordered scene by scene), the scenes' W~ blocks and
+// their tiles. One CTA; the scans over scenes are serial.
+__global__ void k_scene_ranges(DevSim d) {
+  const int ncv = min(d.counters[kCntCv], d.cap), c = min(d.counters[kCntContacts], d.cap);
+  for (int sc = threadIdx.x; sc <= d.n_scenes; sc += blockDim.x) {
+    const int cvb = lower_bound_i(d.cv_vert, ncv, d.scene_vfirst[sc]);
+    d.sc_cvb[sc] = cvb;
+    d.sc_jb[sc] = cvb < ncv ? min(d.cv_first[cvb], c) : c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long off = 0;
+    int toff = 0;
+    for (int sc = 0; sc < d.n_scenes; ++sc) {
+      const int nv = d.sc_cvb[sc + 1] - d.sc_cvb[sc], ld = wt_ld(nv), nb = (nv + kWtT - 1) / kWtT;
+      d.sc_ld[sc] = ld;
+      d.sc_wtoff[sc] = off;
+      d.sc_tileoff[sc] = toff;
+      off += (long long)nv * ld;
+      toff += nb * (nb + 1) / 2;
+    }
+    d.sc_wtoff[d.n_scenes] = off;
+    d.sc_tileoff[d.n_scenes] = toff;
+  }
 }
 
 // union of the contact-vertex intervals of each block of kWtKB rows of U
@@ -310,8 +350,7 @@ __global__ void __launch_bounds__(kWtThreads) k_wt_items(DevSim d) {
   const int ncv = min(d.counters[kCntCv], d.cap);
   const int nU = d.counters[kCntU];
   if (ncv == 0 || nU == 0 || d.y_ptr[nU] > d.cap_y) return;
-  int nb, ntiles, S;
-  wt_layout(ncv, d.wt_grid, nb, ntiles, S);
+  const int ntiles = d.sc_tileoff[d.n_scenes], S = wt_splits(ntiles, d.wt_grid);
   const int nitems = ntiles * S;
   const int nkb = (nU + kWtKB - 1) / kWtKB;
   __shared__ __align__(16) float As[kWtKB][kWtT];
@@ -322,10 +361,13 @@ __global__ void __launch_bounds__(kWtThreads) k_wt_items(DevSim d) {
   const int ty = t >> 4, tx = t & 15;  // outputs rows 8 ty .. +7, columns 4 tx .. +3
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
     const int tile = item / S, sp = item - tile * S;
+    const int sc = tile_scene(d, tile);
     int I, J;
-    tri_decode(tile, I, J);
-    const int a0 = I * kWtT, b0 = J * kWtT;
-    const int a1 = min(a0 + kWtT, ncv), b1 = min(b0 + kWtT, ncv);
+    tri_decode(tile - d.sc_tileoff[sc], I, J);
+    // global contact-vertex ranges of the tile's rows and columns
+    const int cvb = d.sc_cvb[sc], cve = d.sc_cvb[sc + 1];
+    const int a0 = cvb + I * kWtT, b0 = cvb + J * kWtT;
+    const int a1 = min(a0 + kWtT, cve), b1 = min(b0 + kWtT, cve);
     const bool diag = I == J;
     // contributing row blocks, counted by every warp alike (uniform across the CTA)
     int cnt = 0;
@@ -421,38 +463,40 @@ __global__ void k_wt_reduce(DevSim d) {
   const int ncv = min(d.counters[kCntCv], d.cap);
   const int nU = d.counters[kCntU];
   if (ncv == 0 || nU == 0 || d.y_ptr[nU] > d.cap_y) return;
-  int nb, ntiles, S;
-  wt_layout(ncv, d.wt_grid, nb, ntiles, S);
-  const int ld = wt_ld(ncv);
+  const int ntiles = d.sc_tileoff[d.n_scenes], S = wt_splits(ntiles, d.wt_grid);
   const long long total = (long long)ntiles * kWtT * kWtT;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const int tile = (int)(e / (kWtT * kWtT)), el = (int)(e % (kWtT * kWtT));
+    const int sc = tile_scene(d, tile);
     int I, J;
-    tri_decode(tile, I, J);
+    tri_decode(tile - d.sc_tileoff[sc], I, J);
+    // scene-local row and column of the scene's block
+    const int nv = d.sc_cvb[sc + 1] - d.sc_cvb[sc], ld = d.sc_ld[sc];
+    float* W = d.wt + d.sc_wtoff[sc];
     const int ra = I * kWtT + el / kWtT, cb = J * kWtT + el % kWtT;
-    if (ra < ncv && cb < ncv) {
+    if (ra < nv && cb < nv) {
       float sum = 0.f;
       const float* p = d.wt_part + (size_t)tile * S * kWtT * kWtT + el;
       for (int sp = 0; sp < S; ++sp) sum += p[(size_t)sp * kWtT * kWtT];
-      d.wt[(size_t)ra * ld + cb] = sum;
-      d.wt[(size_t)cb * ld + ra] = sum;
-    } else if (ra >= ncv && ra < ld && cb < ncv) {
-      d.wt[(size_t)cb * ld + ra] = 0.f;   // zero padding of the last column group
-    } else if (cb >= ncv && cb < ld && ra < ncv) {
-      d.wt[(size_t)ra * ld + cb] = 0.f;
+      W[(size_t)ra * ld + cb] = sum;
+      W[(size_t)cb * ld + ra] = sum;
+    } else if (ra >= nv && ra < ld && cb < nv) {
+      W[(size_t)cb * ld + ra] = 0.f;   // zero padding of the last column group
+    } else if (cb >= nv && cb < ld && ra < nv) {
+      W[(size_t)ra * ld + cb] = 0.f;
     }
   }
 }
 
-// Split of the contact vertices over the CR cluster's ranks, balanced by contacts: rank r
-// owns contact vertices [cv_split(r), cv_split(r + 1)).
-__device__ int cv_split(const DevSim& d, int r, int R, int c, int ncv) {
-  if (r >= R) return ncv;
-  long long target = (long long)r * c / R;
-  int lo = 0, hi = ncv;
+// Split of a scene's contact vertices over its CR cluster's ranks, balanced by contacts:
+// rank r owns the scene's contact vertices [cv_split(r), cv_split(r + 1)) (global ids).
+__device__ int cv_split(const DevSim& d, int r, int R, int cvb, int cve, int jb, int je) {
+  if (r >= R) return cve;
+  const long long target = jb + (long long)r * (je - jb) / R;
+  int lo = cvb, hi = cve;
   while (lo < hi) {
-    int mid = (lo + hi) >> 1;
+    const int mid = (lo + hi) >> 1;
     if (d.cv_first[mid] < target) lo = mid + 1; else hi = mid;
   }
   return lo;
@@ -461,16 +505,25 @@ __device__ int cv_split(const DevSim& d, int r, int R, int c, int ncv) {
 __global__ void k_precond(DevSim d) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   int c = min(d.counters[kCntContacts], d.cap);
-  if (blockIdx.x == 0 && threadIdx.x <= d.cr_R) {
-    const int ncv = min(d.counters[kCntCv], d.cap), r = threadIdx.x;
-    const int cv = cv_split(d, r, d.cr_R, c, ncv);
-    d.cr_split[r] = cv;
-    d.cr_split[kCrMaxRanks + 1 + r] = cv < ncv ? min(d.cv_first[cv], c) : c;
+  if (blockIdx.x == 0) {
+    const int R = d.cr_R, per = 2 * (kCrMaxRanks + 1);
+    for (int e = threadIdx.x; e < d.n_scenes * (R + 1); e += blockDim.x) {
+      const int sc = e / (R + 1), r = e % (R + 1);
+      const int cvb = d.sc_cvb[sc], cve = d.sc_cvb[sc + 1];
+      const int jb = d.sc_jb[sc], je = d.sc_jb[sc + 1];
+      const int cv = cv_split(d, r, R, cvb, cve, jb, je);
+      d.cr_split[sc * per + r] = cv - cvb;
+      d.cr_split[sc * per + kCrMaxRanks + 1 + r] = cv < cve ? min(d.cv_first[cv], je) : je;
+    }
   }
   if (j >= c) return;
-  int ncv = min(d.counters[kCntCv], d.cap);
-  int cv = d.ct_cv[j];
-  double w = (cv < ncv) ? (double)d.wt[(size_t)cv * wt_ld(ncv) + cv] : 0.0;
+  const int ncv = min(d.counters[kCntCv], d.cap);
+  const int cv = d.ct_cv[j];
+  double w = 0.0;
+  if (cv < ncv) {
+    const int sc = d.vert_scene[d.ct_vert[j]], l = cv - d.sc_cvb[sc];
+    w = (double)d.wt[d.sc_wtoff[sc] + (size_t)l * d.sc_ld[sc] + l];
+  }
   d.ct_r[2 * j] = d.h * d.h * w;
   d.ct_r[2 * j + 1] = d.h * w;
   for (int r = 0; r < 3; ++r) d.ct_lam[3 * j + r] = 0.0;
@@ -537,8 +590,11 @@ __global__ void k_contact_eval(DevSim d, int k, int final_eval) {
     phif0 = vf[0] + Ef * lf0;
     phif1 = vf[1] + Ef * lf1;
   }
-  const double res = fmax(fabs(fmin(dn, rn * ln)), h * sqrt(phif0 * phif0 + phif1 * phif1)) / d.L_ref;
+  const int sc = d.vert_scene[v];
+  const double res =
+      fmax(fabs(fmin(dn, rn * ln)), h * sqrt(phif0 * phif0 + phif1 * phif1)) / d.scene_Lref[sc];
   atomic_max_nonneg(&d.resid[k], res);
+  atomic_max_nonneg(&d.resid_scene[sc * (kMaxIters + 1) + k], res);
   if (final_eval) {
     if (-dn > 0.0) atomic_max_nonneg(d.max_pen, -dn);
     return;
@@ -675,15 +731,19 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
   CrLayout L;
   L.R = (int)cl.num_blocks();
   L.rank = (int)cl.block_rank();
-  L.c = min(d.counters[kCntContacts], d.cap);
-  L.ncv = min(d.counters[kCntCv], d.cap);
+  // this cluster's scene: its contacts and contact vertices (global ids cvb.., jb..)
+  const int scene = blockIdx.x / L.R;
+  const int cvb = d.sc_cvb[scene], jb = d.sc_jb[scene];
+  L.c = d.sc_jb[scene + 1] - jb;
+  L.ncv = d.sc_cvb[scene + 1] - cvb;
   // every CTA reads the same counters, so this exit is taken by all or by none
   if (L.c == 0 || L.ncv == 0) return;
   // split of the contact vertices over the cluster ranks, computed once per CTA
   __shared__ int split_cv[kCrMaxRanks + 1], split_j[kCrMaxRanks + 1];
   if (threadIdx.x <= L.R) {
-    split_cv[threadIdx.x] = d.cr_split[threadIdx.x];
-    split_j[threadIdx.x] = d.cr_split[kCrMaxRanks + 1 + threadIdx.x];
+    const int* sp = d.cr_split + scene * 2 * (kCrMaxRanks + 1);
+    split_cv[threadIdx.x] = sp[threadIdx.x];
+    split_j[threadIdx.x] = sp[kCrMaxRanks + 1 + threadIdx.x];
   }
   __syncthreads();
   L.cv0 = split_cv[L.rank];
@@ -699,7 +759,8 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
   // shared layout (identical offsets in every CTA for the parts written remotely):
   //   dots[16] float4  per-rank partial dot products (written by every rank)
   //   uall[ldw] float4 u for all contact vertices (each rank writes its own range everywhere)
-  const int ldw = wt_ld(L.ncv);
+  const int ldw = d.sc_ld[scene];
+  const float* wblk = d.wt + d.sc_wtoff[scene];  // the scene's W~ block, row-major
   float4* dots = reinterpret_cast<float4*>(sm);          // 16 float4
   float4* uall = dots + 16;                              // ldw float4
   float4* uloc = uall + ldw;                             // nv_max float4 (own slice)
@@ -735,7 +796,7 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
     const unsigned long long bytes = (unsigned long long)rows_sm * ldw * sizeof(float);
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
                  "r"((unsigned)bytes) : "memory");
-    const char* src = reinterpret_cast<const char*>(d.wt + (size_t)L.cv0 * ldw);
+    const char* src = reinterpret_cast<const char*>(wblk + (size_t)L.cv0 * ldw);
     const unsigned dst = smem_u32(wrows);
     for (unsigned long long off = 0; off < bytes; off += kBulkChunk) {
       const unsigned sz = (unsigned)min((unsigned long long)kBulkChunk, bytes - off);
@@ -753,12 +814,12 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
   }
   for (int e = threadIdx.x; e < 9 * nj; e += blockDim.x) Df[e] = d.ct_Df[9 * L.j0 + e];
   for (int cvl = threadIdx.x; cvl < nv; cvl += blockDim.x) {
-    const int jb = max(0, d.cv_first[L.cv0 + cvl] - L.j0);
-    cvf[cvl] = jb;
-    cvn[cvl] = max(0, min(nj, jb + d.cv_nct[L.cv0 + cvl]) - jb);
+    const int jf = max(0, d.cv_first[cvb + L.cv0 + cvl] - L.j0);
+    cvf[cvl] = jf;
+    cvn[cvl] = max(0, min(nj, jf + d.cv_nct[cvb + L.cv0 + cvl]) - jf);
   }
   for (int jl = threadIdx.x; jl < nj; jl += blockDim.x)
-    ctl[jl] = min(max(d.ct_cv[L.j0 + jl] - L.cv0, 0), max(nv - 1, 0));
+    ctl[jl] = min(max(d.ct_cv[L.j0 + jl] - cvb - L.cv0, 0), max(nv - 1, 0));
   for (int e = L.ncv + threadIdx.x; e < ldw; e += blockDim.x) uall[e] = make_float4(0, 0, 0, 0);
   __syncthreads();
   const bool w_copy = rows_sm > 0;
@@ -799,7 +860,7 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
     const int ng = ldw / 4;
     auto wrow_ptr = [&](int row) {
       return reinterpret_cast<const float4*>(
-          row < rows_sm ? wrows + (size_t)row * ldw : d.wt + (size_t)(L.cv0 + row) * ldw);
+          row < rows_sm ? wrows + (size_t)row * ldw : wblk + (size_t)(L.cv0 + row) * ldw);
     };
     if (ldw <= 32 * 4 * kCrG) {
       // lane l owns the columns l + 32 m (m < 4 kCrG): its u values live in registers
@@ -848,7 +909,7 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
       };
       const int n_sm_rows = min(rows_sm, nv);
       rows(0, n_sm_rows, [&](int r) { return wrows + (size_t)r * ldw; });
-      rows(n_sm_rows, nv, [&](int r) { return d.wt + (size_t)(L.cv0 + r) * ldw; });
+      rows(n_sm_rows, nv, [&](int r) { return wblk + (size_t)(L.cv0 + r) * ldw; });
     } else {
     // four rows per warp at a time, so the shuffle reductions of the rows overlap
     for (int row0 = 4 * warp; row0 < nv; row0 += 4 * nw) {
@@ -976,7 +1037,7 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
   // lambda += dlambda; u = D^T (omega * dlambda) per owned contact vertex
   for (int e = threadIdx.x; e < 3 * nj; e += blockDim.x) d.ct_lam[3 * L.j0 + e] += (double)vx[e];
   for (int cvl = threadIdx.x; cvl < nv; cvl += blockDim.x) {
-    const int cv = L.cv0 + cvl;
+    const int cv = cvb + L.cv0 + cvl;
     float u0 = 0.f, u1 = 0.f, u2 = 0.f;
     const int jb = cvf[cvl], je = jb + cvn[cvl];
     for (int jl = jb; jl < je; ++jl) {
@@ -1020,6 +1081,7 @@ void launch_delassus(const DevSim& d, cudaStream_t s) {
   k_yc_len<<<(d.cap + 255) / 256, 256, 0, s>>>(d);
   launch_scan(d.yc_len, d.yc_ptr, 0, d.counters + kCntCv, d.counters + kCntYC, s);
   k_y_gather<<<(d.n * 32 + 255) / 256, 256, 0, s>>>(d);
+  k_scene_ranges<<<1, 256, 0, s>>>(d);
   k_wt_blocks<<<(d.n / kWtKB + 1 + 127) / 128, 128, 0, s>>>(d);
   k_wt_items<<<d.wt_grid, kWtThreads, 0, s>>>(d);
   k_wt_reduce<<<2 * d.n_sm, 256, 0, s>>>(d);
@@ -1041,7 +1103,9 @@ void launch_yu(const DevSim& d, cudaStream_t s) {
 
 static size_t g_cr_smem = 0;
 
-int cr_setup(int* cluster_out, size_t* smem_out) {
+// Cluster size of the CR kernel: the largest R (16, 8, 4, 2, 1) such that one cluster per
+// scene can be resident at once; R = 1 when not even that fits in one wave.
+int cr_setup(int n_scenes, int* cluster_out, size_t* smem_out) {
   int dev = 0;
   cudaGetDevice(&dev);
   int optin = 0;
@@ -1064,7 +1128,8 @@ int cr_setup(int* cluster_out, size_t* smem_out) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, k_cr, &cfg) == cudaSuccess && nclusters > 0) {
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_cr, &cfg) == cudaSuccess &&
+        (nclusters >= n_scenes || (R == 1 && nclusters > 0))) {
       chosen = R;
       break;
     }
@@ -1079,7 +1144,7 @@ int cr_setup(int* cluster_out, size_t* smem_out) {
 
 int launch_cr(const DevSim& d, cudaStream_t s, int cluster) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(cluster);
+  cfg.gridDim = dim3(cluster * d.n_scenes);
   cfg.blockDim = dim3(kCrThreads);
   cfg.dynamicSmemBytes = g_cr_smem;
   cfg.stream = s;

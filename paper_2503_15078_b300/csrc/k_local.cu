@@ -238,7 +238,7 @@ __global__ void k_frame_begin(DevSim d) {
       d.dq[3 * i + r] = (float)(st - qt);
       split_ref(d, i, r, qt);
     } else {
-      double qp = qt + h * d.handle_vel[r];
+      double qp = qt + h * d.scene_hvel[3 * d.vert_scene[i] + r];
       d.s_tilde[3 * i + r] = qp;
       d.q_ref[3 * i + r] = qp;
       d.dq[3 * i + r] = 0.f;

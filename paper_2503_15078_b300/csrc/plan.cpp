@@ -90,7 +90,8 @@ struct Dissector {
 }  // namespace
 
 int build_plan(const sim_mesh* mesh, const sim_material* mats, int n_mat, double h,
-               int n_threads, Plan* P, std::string* err) {
+               int n_threads, Plan* P, std::string* err, const int32_t* vertex_scene,
+               int n_scenes) {
   auto t0 = std::chrono::steady_clock::now();
   Plan& p = *P;
   if (!mesh || !mesh->rest_pos || !mesh->tets || mesh->n_verts <= 0 || mesh->n_tets <= 0 ||
@@ -107,6 +108,18 @@ int build_plan(const sim_mesh* mesh, const sim_material* mats, int n_mat, double
   p.tet_mat.assign(T, 0);
   if (mesh->tet_material) p.tet_mat.assign(mesh->tet_material, mesh->tet_material + T);
   for (int r = 0; r < 3; ++r) p.handle_vel[r] = mesh->handle_vel[r];
+  p.n_scenes = std::max(1, n_scenes);
+  p.vertex_scene.assign(n, 0);
+  if (vertex_scene) {
+    for (int v = 0; v < n; ++v) {
+      if (vertex_scene[v] < 0 || vertex_scene[v] >= p.n_scenes ||
+          (v > 0 && vertex_scene[v] < vertex_scene[v - 1])) {
+        *err = "vertex scene ids must be non-decreasing and below the scene count";
+        return SIM_EINVAL;
+      }
+      p.vertex_scene[v] = vertex_scene[v];
+    }
+  }
   for (double x : p.X)
     if (!std::isfinite(x)) {
       *err = "non-finite rest position";
@@ -224,9 +237,12 @@ int build_plan(const sim_mesh* mesh, const sim_material* mats, int n_mat, double
     for (int r = 0; r < 3; ++r) fxyz[3 * f + r] = p.X[3 * free_ids[f] + r];
   Dissector D(gp, gi, fxyz.data(), nf);
   {
-    std::vector<int32_t> all(nf);
-    std::iota(all.begin(), all.end(), 0);
-    D.run(std::move(all));
+    // scene by scene (scenes share no element, so each is ordered on its own and the
+    // elimination forest keeps them apart and in scene order)
+    std::vector<std::vector<int32_t>> by_scene(p.n_scenes);
+    for (int f = 0; f < nf; ++f) by_scene[p.vertex_scene[free_ids[f]]].push_back(f);
+    for (auto& S : by_scene)
+      if (!S.empty()) D.run(std::move(S));
   }
   std::vector<int32_t>& nd = D.out;  // nd[k] = free index at position k
   std::vector<int32_t> nd_inv(nf);
@@ -283,6 +299,16 @@ int build_plan(const sim_mesh* mesh, const sim_material* mats, int n_mat, double
   }
   p.internal.assign(n, -1);
   for (int k = 0; k < nf; ++k) p.internal[p.order[k]] = k;
+  // scene boundaries in the internal free numbering
+  p.scene_vfirst.assign(p.n_scenes + 1, nf);
+  for (int k = nf - 1; k >= 0; --k) p.scene_vfirst[p.vertex_scene[p.order[k]]] = k;
+  for (int sc = p.n_scenes - 1; sc >= 0; --sc)
+    p.scene_vfirst[sc] = std::min(p.scene_vfirst[sc], p.scene_vfirst[sc + 1]);
+  for (int k = 1; k < nf; ++k)
+    if (p.vertex_scene[p.order[k]] < p.vertex_scene[p.order[k - 1]]) {
+      *err = "internal: scenes are not contiguous in the elimination order";
+      return SIM_EINVAL;
+    }
   for (int v = 0; v < n; ++v)
     if (p.pinned[v]) {
       p.internal[v] = nf + (int)p.pinned_ids.size();

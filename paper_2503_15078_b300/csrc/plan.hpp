@@ -41,6 +41,9 @@ struct Plan {
   std::vector<MatParams> mats;
   std::vector<uint8_t> pinned;    // n_verts flags
   double handle_vel[3] = {0, 0, 0};
+  int n_scenes = 1;
+  std::vector<int32_t> vertex_scene;  // scene of each vertex (caller numbering)
+  std::vector<int32_t> scene_vfirst;  // n_scenes + 1: scene boundaries, internal free ids
 
   // ---- per element (caller tet order) ----------------------------------------------
   std::vector<double> Dm_inv;     // 9 per tet, row-major
@@ -90,8 +93,11 @@ struct Plan {
 };
 
 // Build the plan. Returns SIM_OK or an error code; *err receives a message.
+// vertex_scene (optional): scene of each vertex, non-decreasing; the ordering is computed
+// scene by scene so that every scene's free vertices are contiguous.
 int build_plan(const sim_mesh* mesh, const sim_material* mats, int n_mat, double h,
-               int n_threads, Plan* plan, std::string* err);
+               int n_threads, Plan* plan, std::string* err,
+               const int32_t* vertex_scene = nullptr, int n_scenes = 1);
 
 // Device work split of one product: CTA c streams tiles [cta_first[c], cta_first[c+1])
 // of the pass's tile order, split so that every CTA has about the same cost; each run of

@@ -111,7 +111,7 @@ int kernels_per_frame(const sim_s* s, int K) {
   const bool c = s->has_obstacles;
   // per iteration: local, [contact eval], rhs, pass 1 + reduction, [Y^T z, CR, Y u],
   // pass 2 + reduction; a residual correction adds the residual and both passes
-  return 1 + (c ? 4 + 11 : 0) + K * (1 + (c ? 1 : 0) + 1 + 2 + (c ? 3 : 0) + 2) + (c ? 1 : 0) + 1 +
+  return 1 + (c ? 4 + 12 : 0) + K * (1 + (c ? 1 : 0) + 1 + 2 + (c ? 3 : 0) + 2) + (c ? 1 : 0) + 1 +
          5 * refined_iters(s, K);
 }
 
@@ -121,6 +121,7 @@ void enqueue_frame(sim_s* s, int K, cudaStream_t st) {
   auto mark = [&](int i) { cudaEventRecordWithFlags(s->ev[i], st, cudaEventRecordExternal); };
   mark(0);
   cudaMemsetAsync(d.resid, 0, sizeof(double) * (silg::kMaxIters + 1), st);
+  cudaMemsetAsync(d.resid_scene, 0, sizeof(double) * (silg::kMaxIters + 1) * d.n_scenes, st);
   cudaMemsetAsync(d.max_pen, 0, sizeof(double), st);
   silg::launch_frame_begin(d, st);
   if (s->has_obstacles) silg::launch_collide(d, st);
@@ -224,7 +225,16 @@ int upload_schedules(sim_s* s, int grid1, int grid2, double zero_cost) {
   return SIM_OK;
 }
 
-int create_device(sim_s* s, const sim_obstacle* obstacles, int n_obs, const sim_options* o) {
+// Per-scene inputs of the device arrays (one entry for sim_create).
+struct SceneData {
+  std::vector<sim_obstacle> obstacles;
+  std::vector<int32_t> obstacle_scene;
+  std::vector<double> margin, L_ref, hvel;  // hvel: 3 per scene
+};
+
+int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
+  const sim_obstacle* obstacles = sd.obstacles.data();
+  const int n_obs = (int)sd.obstacles.size();
   Plan& p = s->plan;
   DevSim& d = s->d;
   const int n = p.n_free, n_all = p.n_verts, T = p.n_tets;
@@ -238,21 +248,25 @@ int create_device(sim_s* s, const sim_obstacle* obstacles, int n_obs, const sim_
   d.n_cr = std::max(0, o->n_cr_iters);
   d.h = p.h;
   d.h2f = (float)(p.h * p.h);
-  for (int r = 0; r < 3; ++r) {
-    d.grav[r] = o->gravity[r];
-    d.handle_vel[r] = p.handle_vel[r];
-  }
-  d.margin = o->contact_margin > 0 ? o->contact_margin : 0.5 * p.mean_edge;
+  for (int r = 0; r < 3; ++r) d.grav[r] = o->gravity[r];
+  // ---- scenes -------------------------------------------------------------------------
+  d.n_scenes = p.n_scenes;
   {
-    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
-    for (int v = 0; v < n_all; ++v)
-      for (int r = 0; r < 3; ++r) {
-        mn[r] = std::min(mn[r], p.X[3 * v + r]);
-        mx[r] = std::max(mx[r], p.X[3 * v + r]);
-      }
-    d.L_ref = std::sqrt((mx[0] - mn[0]) * (mx[0] - mn[0]) + (mx[1] - mn[1]) * (mx[1] - mn[1]) +
-                        (mx[2] - mn[2]) * (mx[2] - mn[2]));
+    std::vector<int> vs(n_all);
+    for (int v = 0; v < n_all; ++v) vs[p.internal[v]] = p.vertex_scene[v];
+    d.vert_scene = s->upload(vs);
   }
+  d.scene_vfirst = s->upload(p.scene_vfirst);
+  d.obst_scene = s->upload(sd.obstacle_scene);
+  d.scene_margin = s->upload(sd.margin);
+  d.scene_Lref = s->upload(sd.L_ref);
+  d.scene_hvel = s->upload(sd.hvel);
+  d.sc_cvb = s->alloc<int>(p.n_scenes + 1);
+  d.sc_jb = s->alloc<int>(p.n_scenes + 1);
+  d.sc_ld = s->alloc<int>(p.n_scenes);
+  d.sc_wtoff = s->alloc<long long>(p.n_scenes + 1);
+  d.sc_tileoff = s->alloc<int>(p.n_scenes + 1);
+  d.resid_scene = s->alloc<double>((size_t)p.n_scenes * (silg::kMaxIters + 1));
   // ---- per vertex (internal numbering) ---------------------------------------------
   std::vector<double> mass(n_all), X(3 * (size_t)n_all);
   for (int v = 0; v < n_all; ++v) {
@@ -419,14 +433,16 @@ int create_device(sim_s* s, const sim_obstacle* obstacles, int n_obs, const sim_
   d.spin_limit = o->spin_limit;
   d.kb_lo = s->alloc<int>(n / 32 + 1);
   d.kb_hi = s->alloc<int>(n / 32 + 1);
-  d.wt_part = s->alloc<float>((size_t)silg::wt_items_max(cap, d.wt_grid) * 64 * 64);
+  // every scene may add one partly filled block row of W~ tiles
+  d.wt_part = s->alloc<float>(
+      (size_t)silg::wt_items_max(cap + 64 * p.n_scenes, d.wt_grid) * 64 * 64);
   if (silg::sinv_setup() != SIM_OK) return SIM_ECUDA;
   s->ev.resize(4 + kMarksPerIter * silg::kMaxIters);
   for (auto& e : s->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return SIM_ECUDA;
-  d.cr_split = s->alloc<int>(2 * (silg::kCrMaxRanks + 1));
+  d.cr_split = s->alloc<int>((size_t)p.n_scenes * 2 * (silg::kCrMaxRanks + 1));
   if (s->has_obstacles) {
-    int st = silg::cr_setup(&s->cluster, &s->cr_smem);
+    int st = silg::cr_setup(p.n_scenes, &s->cluster, &s->cr_smem);
     if (st != SIM_OK) return st;
   }
   d.cr_R = s->cluster;
@@ -465,25 +481,125 @@ int sim_get_plan_info(const sim_t* s, sim_plan_info* info) {
   return SIM_OK;
 }
 
-int sim_create(const sim_mesh* mesh, const sim_material* mats, int32_t n_mat,
-               const sim_obstacle* obstacles, int32_t n_obs, double h,
-               const sim_options* opts, sim_t** out) {
-  if (!out) return SIM_EINVAL;
-  *out = nullptr;
-  if (n_obs < 0 || (n_obs > 0 && !obstacles)) return SIM_EINVAL;
-  sim_options def;
-  sim_default_options(&def);
-  const sim_options* o = opts ? opts : &def;
+namespace {
+
+double mean_edge(const sim_mesh& m) {
+  double sum = 0;
+  long long cnt = 0;
+  for (int t = 0; t < m.n_tets; ++t) {
+    const int32_t* v = m.tets + 4 * (size_t)t;
+    if (v[0] < 0 || v[0] >= m.n_verts) continue;
+    for (int a = 1; a < 4; ++a) {
+      if (v[a] < 0 || v[a] >= m.n_verts) continue;
+      double e2 = 0;
+      for (int r = 0; r < 3; ++r) {
+        const double dx = m.rest_pos[3 * (size_t)v[a] + r] - m.rest_pos[3 * (size_t)v[0] + r];
+        e2 += dx * dx;
+      }
+      sum += std::sqrt(e2);
+      ++cnt;
+    }
+  }
+  return cnt ? sum / cnt : 0.0;
+}
+
+double bbox_diagonal(const sim_mesh& m) {
+  double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+  for (int v = 0; v < m.n_verts; ++v)
+    for (int r = 0; r < 3; ++r) {
+      mn[r] = std::min(mn[r], m.rest_pos[3 * (size_t)v + r]);
+      mx[r] = std::max(mx[r], m.rest_pos[3 * (size_t)v + r]);
+    }
+  double s2 = 0;
+  for (int r = 0; r < 3; ++r) s2 += (mx[r] - mn[r]) * (mx[r] - mn[r]);
+  return std::sqrt(s2);
+}
+
+int check_options(const sim_options* o) {
   if (o->n_iters < 0 || o->n_iters > silg::kMaxIters || o->n_cr_iters < 0 ||
       o->contact_capacity <= 0 || o->contact_capacity > (1 << 16))
     return SIM_EINVAL;
   if (o->s_precision != SIM_S_FP32 && o->s_precision != SIM_S_BF16) return SIM_EINVAL;
   if (o->refine < 0 || o->refine > 2) return SIM_EINVAL;
+  return SIM_OK;
+}
+
+// The union of the scenes: vertices, tets, materials and obstacles concatenated scene by
+// scene; each scene keeps its margin, scale and handle velocity. margin_override > 0
+// replaces every scene's margin (sim_create's option).
+int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_options* opts,
+                  double margin_override, sim_t** out) {
+  if (!out) return SIM_EINVAL;
+  *out = nullptr;
+  if (!scenes || n_scenes < 1) return SIM_EINVAL;
+  sim_options def;
+  sim_default_options(&def);
+  const sim_options* o = opts ? opts : &def;
+  if (check_options(o) != SIM_OK) return SIM_EINVAL;
+  long long nv_tot = 0, nt_tot = 0, np_tot = 0;
+  for (int k = 0; k < n_scenes; ++k) {
+    const sim_scene& sc = scenes[k];
+    if (sc.mesh.n_verts <= 0 || sc.mesh.n_tets <= 0 || !sc.mesh.rest_pos || !sc.mesh.tets ||
+        !sc.materials || sc.n_materials <= 0 || sc.n_obstacles < 0 ||
+        (sc.n_obstacles > 0 && !sc.obstacles) || sc.mesh.n_pinned < 0 ||
+        (sc.mesh.n_pinned > 0 && !sc.mesh.pinned))
+      return SIM_EINVAL;
+    nv_tot += sc.mesh.n_verts;
+    nt_tot += sc.mesh.n_tets;
+    np_tot += sc.mesh.n_pinned;
+  }
+  if (nv_tot >= (1LL << 31) || nt_tot >= (1LL << 29)) return SIM_EINVAL;
   sim_s* s = new (std::nothrow) sim_s();
   if (!s) return SIM_ENOMEM;
   int st = guarded([&]() {
+    std::vector<double> X;
+    std::vector<int32_t> tets, tmat, pinned, vscene;
+    std::vector<sim_material> mats;
+    SceneData sd;
+    X.reserve(3 * nv_tot);
+    tets.reserve(4 * nt_tot);
+    int voff = 0;
+    for (int k = 0; k < n_scenes; ++k) {
+      const sim_scene& sc = scenes[k];
+      const sim_mesh& m = sc.mesh;
+      const int moff = (int)mats.size();
+      X.insert(X.end(), m.rest_pos, m.rest_pos + 3 * (size_t)m.n_verts);
+      for (int t = 0; t < m.n_tets; ++t) {
+        for (int a = 0; a < 4; ++a) {
+          const int v = m.tets[4 * (size_t)t + a];
+          tets.push_back(v >= 0 && v < m.n_verts ? v + voff : -1);
+        }
+        const int mt = m.tet_material ? m.tet_material[t] : 0;
+        tmat.push_back(mt >= 0 && mt < sc.n_materials ? mt + moff : -1);
+      }
+      for (int q = 0; q < m.n_pinned; ++q)
+        pinned.push_back(m.pinned[q] >= 0 && m.pinned[q] < m.n_verts ? m.pinned[q] + voff : -1);
+      mats.insert(mats.end(), sc.materials, sc.materials + sc.n_materials);
+      vscene.insert(vscene.end(), m.n_verts, k);
+      for (int q = 0; q < sc.n_obstacles; ++q) {
+        sd.obstacles.push_back(sc.obstacles[q]);
+        sd.obstacle_scene.push_back(k);
+      }
+      const double me = mean_edge(m);
+      sd.margin.push_back(margin_override > 0 ? margin_override
+                                              : (sc.contact_margin > 0 ? sc.contact_margin : 0.5 * me));
+      sd.L_ref.push_back(bbox_diagonal(m));
+      for (int r = 0; r < 3; ++r) sd.hvel.push_back(m.handle_vel[r]);
+      voff += m.n_verts;
+    }
+    if (sd.obstacle_scene.empty()) sd.obstacle_scene.push_back(0);
+    sim_mesh um{};
+    um.n_verts = (int32_t)nv_tot;
+    um.n_tets = (int32_t)nt_tot;
+    um.rest_pos = X.data();
+    um.tets = tets.data();
+    um.tet_material = tmat.data();
+    um.pinned = pinned.empty() ? nullptr : pinned.data();
+    um.n_pinned = (int32_t)np_tot;
+    for (int r = 0; r < 3; ++r) um.handle_vel[r] = scenes[0].mesh.handle_vel[r];
     std::string err;
-    int r = silg::build_plan(mesh, mats, n_mat, h, o->n_host_threads, &s->plan, &err);
+    int r = silg::build_plan(&um, mats.data(), (int)mats.size(), h, o->n_host_threads, &s->plan,
+                             &err, vscene.data(), n_scenes);
     if (r != SIM_OK) return r;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) return SIM_ECUDA;
@@ -493,7 +609,7 @@ int sim_create(const sim_mesh* mesh, const sim_material* mats, int32_t n_mat,
     if (cudaStreamCreateWithFlags(&s->work, cudaStreamNonBlocking) != cudaSuccess) return SIM_ECUDA;
     s->launch = o->cuda_stream ? static_cast<cudaStream_t>(o->cuda_stream) : s->work;
     s->n_iters_default = o->n_iters > 0 ? o->n_iters : 5;
-    return create_device(s, obstacles, n_obs, o);
+    return create_device(s, sd, o);
   });
   if (st != SIM_OK) {
     delete s;
@@ -501,6 +617,50 @@ int sim_create(const sim_mesh* mesh, const sim_material* mats, int32_t n_mat,
   }
   *out = s;
   return SIM_OK;
+}
+
+}  // namespace
+
+int sim_create(const sim_mesh* mesh, const sim_material* mats, int32_t n_mat,
+               const sim_obstacle* obstacles, int32_t n_obs, double h,
+               const sim_options* opts, sim_t** out) {
+  if (!out) return SIM_EINVAL;
+  *out = nullptr;
+  if (!mesh || n_obs < 0 || (n_obs > 0 && !obstacles)) return SIM_EINVAL;
+  sim_options def;
+  sim_default_options(&def);
+  const sim_options* o = opts ? opts : &def;
+  sim_scene sc{};
+  sc.mesh = *mesh;
+  sc.materials = mats;
+  sc.n_materials = n_mat;
+  sc.obstacles = obstacles;
+  sc.n_obstacles = n_obs;
+  sc.contact_margin = o->contact_margin;
+  return create_common(&sc, 1, h, o, o->contact_margin, out);
+}
+
+int sim_create_batch(const sim_scene* scenes, int32_t n_scenes, double h,
+                     const sim_options* opts, sim_t** out) {
+  return create_common(scenes, n_scenes, h, opts, 0.0, out);
+}
+
+int sim_get_scene_residuals(sim_t* s, int32_t capacity, double* out) {
+  if (!s || !out || capacity < 0) return SIM_EINVAL;
+  cudaSetDevice(s->device);
+  int st = sync_and_check(s);
+  if (st == SIM_ECUDA) return st;
+  const int K = s->last_iters, S = s->plan.n_scenes;
+  std::vector<double> r((size_t)S * (silg::kMaxIters + 1));
+  cudaError_t e = cudaMemcpy(r.data(), s->d.resid_scene, r.size() * sizeof(double),
+                             cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  for (int sc = 0; sc < S; ++sc)
+    for (int k = 0; k <= K; ++k) {
+      const long long idx = (long long)sc * (K + 1) + k;
+      if (idx < capacity) out[idx] = s->has_obstacles ? r[(size_t)sc * (silg::kMaxIters + 1) + k] : 0.0;
+    }
+  return st;
 }
 
 void sim_destroy(sim_t* s) {
@@ -719,11 +879,24 @@ int sim_get_delassus(sim_t* s, int32_t capacity, double* Wt, int32_t* cv_vertex,
   m = std::min(m, s->d.cap);
   *n_out = m;
   if (capacity < m || m == 0) return st;
-  const int ld = (m + 3) & ~3;   // padded leading dimension of the device copy
-  std::vector<float> w((size_t)m * ld);
-  std::vector<int> cv(m);
-  cudaMemcpy(w.data(), s->d.wt, w.size() * sizeof(float), cudaMemcpyDeviceToHost);
+  // one block per scene (block-diagonal W~): blocks at sc_wtoff with leading dimension sc_ld
+  const int S = s->plan.n_scenes;
+  std::vector<int> cvb(S + 1), ldv(S);
+  std::vector<long long> off(S + 1);
+  cudaMemcpy(cvb.data(), s->d.sc_cvb, sizeof(int) * (S + 1), cudaMemcpyDeviceToHost);
+  cudaMemcpy(ldv.data(), s->d.sc_ld, sizeof(int) * S, cudaMemcpyDeviceToHost);
+  cudaMemcpy(off.data(), s->d.sc_wtoff, sizeof(long long) * (S + 1), cudaMemcpyDeviceToHost);
+  std::vector<float> w((size_t)std::max(0LL, off[S]));
+  std::vector<int> cv(m), scene_of(m, 0);
+  if (!w.empty()) cudaMemcpy(w.data(), s->d.wt, w.size() * sizeof(float), cudaMemcpyDeviceToHost);
   cudaMemcpy(cv.data(), s->d.cv_vert, sizeof(int) * m, cudaMemcpyDeviceToHost);
+  for (int sc = 0; sc < S; ++sc)
+    for (int a = cvb[sc]; a < std::min(cvb[sc + 1], m); ++a) scene_of[a] = sc;
+  auto entry = [&](int a, int b) -> double {
+    const int sa = scene_of[a];
+    if (scene_of[b] != sa) return 0.0;
+    return w[off[sa] + (size_t)(a - cvb[sa]) * ldv[sa] + (b - cvb[sa])];
+  };
   const Plan& p = s->plan;
   std::vector<int> perm(m);
   std::iota(perm.begin(), perm.end(), 0);
@@ -731,7 +904,7 @@ int sim_get_delassus(sim_t* s, int32_t capacity, double* Wt, int32_t* cv_vertex,
   for (int a = 0; a < m; ++a) {
     if (cv_vertex) cv_vertex[a] = p.order[cv[perm[a]]];
     if (Wt)
-      for (int b = 0; b < m; ++b) Wt[(size_t)a * m + b] = w[(size_t)perm[a] * ld + perm[b]];
+      for (int b = 0; b < m; ++b) Wt[(size_t)a * m + b] = entry(perm[a], perm[b]);
   }
   return st;
 }
