@@ -51,6 +51,11 @@ def parse():
     ap.add_argument("--n-side", type=int, default=42)
     ap.add_argument("--s-precision", choices=["fp32", "bf16"], default="fp32",
                     help="storage of the S~ values (bf16: FP32 accumulation)")
+    ap.add_argument("--workload", choices=["star", "batch64"], default="star",
+                    help="star: the 57k-DoF pulled star (the headline); batch64: 64 uneven "
+                         "cubes on tilted planes in one simulator")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="1: let the library time the products' launch configurations")
     ap.add_argument("--refine", type=int, default=1,
                     help="bf16 only: residual corrections, 0 none, 1 last iteration, 2 every")
     return ap.parse_args()
@@ -270,6 +275,21 @@ def contact_state(scene, placement):
     return q, v
 
 
+def batch_state(scenes):
+    """Every cube moved along its plane's normal until its lowest vertex is a quarter of
+    its lattice spacing inside the plane (pure geometry), at rest."""
+    import numpy as np
+    qs, vs = [], []
+    for sc in scenes:
+        pl = sc.obstacles[0]
+        n = np.asarray(pl.axis, dtype=np.float64)
+        n = n / np.linalg.norm(n)
+        dist = (sc.q0 - np.asarray(pl.p)) @ n
+        qs.append(sc.q0 - (dist.min() + 0.25 * sc.spacing) * n)
+        vs.append(np.zeros_like(sc.q0))
+    return np.concatenate(qs), np.concatenate(vs)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -281,11 +301,21 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    scene = sg.star_pull(n_side=args.n_side, seed=rank)
+    batch = args.workload == "batch64"
+    if batch:
+        scenes = sg.batch(n_scenes=64, seed=rank)
+        scene = scenes[0]
+        if args.s_precision == "fp32" and "--s-precision" not in sys.argv:
+            args.s_precision = "bf16"   # the batch workload stores S~ in BF16 by definition
+        q0, v0 = batch_state(scenes)
+    else:
+        scene = sg.star_pull(n_side=args.n_side, seed=rank)
+        q0, v0 = contact_state(scene, args.placement)
     bf16 = args.s_precision == "bf16"
-    sim = Simulator(scene, s_precision=1 if bf16 else 0, refine=args.refine)
+    sim = Simulator(scenes if batch else scene, s_precision=1 if bf16 else 0,
+                    refine=args.refine, autotune=args.autotune,
+                    contact_capacity=16384 if batch else 4096)
     n_iters = scene.n_iters
-    q0, v0 = contact_state(scene, args.placement)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def one_step():
@@ -347,9 +377,9 @@ def run_ours(args):
         qh, vh = sim.state()
         e2e.append(time.perf_counter() - t0)
     e2e_ms = 1e3 * statistics.mean(e2e) / n_iters
-    h2d = 2 * scene.n_verts * 3 * 8
+    h2d = 2 * sim.n_verts * 3 * 8
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not batch:
         ot = OracleTimer(scene, q0, v0, n_iters)
         ts = [ot.iteration_seconds() for _ in range(2)]
         cpu = {"value": round(ot.ms_per_iteration(statistics.mean(ts)), 3), "unit": UNIT,
@@ -368,19 +398,29 @@ def run_ours(args):
         "dtype": "bf16/f32" if bf16 else "f32",
         "data": "synthetic",
         "config": {
-            "workload": "star_pull: extruded 5-point star 42x42x27 lattice, 19008 verts / "
-                        "57024 DoFs / 96252 tets, SNH E=1e6 nu=0.45, pinned cap pulled at "
-                        "0.5 m/s through 4x4 seeded cylinders mu=0.3, h=1/60, 5 L-G + 10 CR "
-                        "iterations per frame; every step replays one frame from the star placed "
-                        "10.25 cm into the first cylinder row (810 contacts)",
-            "dofs": 3 * scene.n_verts,
+            "workload": (
+                "batch64: 64 cubes of 8^3..20^3 vertices (seeded), ARAP/co-rot vs SNH, E "
+                "log-uniform 1e4..1e7, nu 0.3..0.48, planes tilted 0..30 deg, mu 0.1..0.8, "
+                "each placed a quarter lattice spacing into its plane; one simulator, "
+                "S~ in BF16 + FP32 correction, 5 L-G + 10 CR iterations per frame"
+                if batch else
+                "star_pull: extruded 5-point star 42x42x27 lattice, 19008 verts / "
+                "57024 DoFs / 96252 tets, SNH E=1e6 nu=0.45, pinned cap pulled at "
+                "0.5 m/s through 4x4 seeded cylinders mu=0.3, h=1/60, 5 L-G + 10 CR "
+                "iterations per frame; every step replays one frame from the star placed "
+                "10.25 cm into the first cylinder row (810 contacts)"),
+            "dofs": 3 * sim.n_verts,
+            "scenes": sim.n_scenes,
             "free_dofs": 3 * n_free,
-            "tets": scene.n_tets,
+            "tets": sim.n_tets,
             "contacts_mean": round(statistics.mean(contacts), 1),
             "placement_m": args.placement,
             "n_iters": n_iters,
             "nnz_S": nnz,
             "s_precision": args.s_precision,
+            "products_launch": {k: v for k, v in sim.tuning().items()
+                                if k in ("tuned", "pass1_ctas", "pass2_ctas", "pass1_unroll",
+                                         "pass2_unroll", "pass1_balance", "pass2_balance")},
             "refine": args.refine if bf16 else None,
             "l2": "flushed (256 MB write) before every timed step",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",

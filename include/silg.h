@@ -103,7 +103,23 @@ typedef struct {
                                   the next synchronisation (0: 2^22)                      */
   void* cuda_stream;           /* cudaStream_t to run on, or NULL for a private stream    */
   int32_t n_host_threads;      /* threads for the host precompute (0: all cores)          */
+  int32_t autotune;            /* 1: time the profile products' launch configurations at
+                                  creation and keep the fastest (sim_get_tuning); 0
+                                  (default): the fixed configuration                     */
 } sim_options;
+
+/* Launch configuration of the two profile products (z = S g, x = S^T y), chosen by the
+ * autotuner or fixed. */
+typedef struct {
+  int32_t tuned;               /* 1 if the autotuner ran                                   */
+  int32_t candidates;          /* configurations timed per product                        */
+  int32_t pass1_ctas, pass2_ctas;       /* CTAs of each product's launch                  */
+  int32_t pass1_unroll, pass2_unroll;   /* 1: the format's tiles in flight per warp, 0: half */
+  double pass1_balance, pass2_balance;  /* cost of an empty tile position relative to a
+                                           stored value when the tiles are split over CTAs */
+  double pass1_us, pass2_us;            /* median launch time of the choice (tuned only)   */
+  double pass1_default_us, pass2_default_us; /* ... of the fixed configuration           */
+} sim_tuning;
 
 /* Per-frame statistics of the most recent sim_step. */
 #define SIM_MAX_RESIDUALS 64
@@ -211,6 +227,8 @@ int sim_create_batch(const sim_scene* scenes, int32_t n_scenes, double h,
  * k (the same measure as sim_stats.residual, over the scene's contacts; 0 without contacts).
  * capacity: doubles available in out. */
 int sim_get_scene_residuals(sim_t* sim, int32_t capacity, double* out);
+/* The products' launch configuration (tuned or fixed). */
+int sim_get_tuning(const sim_t* sim, sim_tuning* out);
 void sim_destroy(sim_t* sim);
 
 /* One frame of Alg. 4 with n_iters local-global iterations (n_iters <= 0: the option's

@@ -209,6 +209,12 @@ class Simulator:
         if q0 is not None:
             self.set_state(q0, v0 if v0 is not None else np.zeros_like(q0))
 
+    def tuning(self):
+        """Launch configuration of the profile products (autotuned or fixed)."""
+        t = _abi.SimTuning()
+        _check(lib().sim_get_tuning(self._h, C.byref(t)), "sim_get_tuning")
+        return {f: getattr(t, f) for f, _ in t._fields_}
+
     def scene_residuals(self):
         """(n_scenes, n_iters + 1) residuals of the last frame, per scene."""
         K = self.stats()["n_iters"]

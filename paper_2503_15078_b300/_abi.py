@@ -45,7 +45,15 @@ class SimOptions(C.Structure):
                 ("refine", C.c_int32), ("contact_capacity", C.c_int32), ("device", C.c_int32),
                 ("gravity", C.c_double * 3), ("contact_margin", C.c_double),
                 ("spin_limit", C.c_uint64), ("cuda_stream", C.c_void_p),
-                ("n_host_threads", C.c_int32)]
+                ("n_host_threads", C.c_int32), ("autotune", C.c_int32)]
+
+
+class SimTuning(C.Structure):
+    _fields_ = [("tuned", C.c_int32), ("candidates", C.c_int32), ("pass1_ctas", C.c_int32),
+                ("pass2_ctas", C.c_int32), ("pass1_unroll", C.c_int32),
+                ("pass2_unroll", C.c_int32), ("pass1_balance", C.c_double),
+                ("pass2_balance", C.c_double), ("pass1_us", C.c_double), ("pass2_us", C.c_double),
+                ("pass1_default_us", C.c_double), ("pass2_default_us", C.c_double)]
 
 
 class SimStats(C.Structure):
@@ -68,6 +76,7 @@ PROTOTYPES = {
     "sim_create_batch": (C.c_int, [C.POINTER(SimScene), C.c_int32, C.c_double,
                                    C.POINTER(SimOptions), C.POINTER(C.c_void_p)]),
     "sim_get_scene_residuals": (C.c_int, [C.c_void_p, C.c_int32, _dp]),
+    "sim_get_tuning": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sim_strerror": (C.c_char_p, [C.c_int]),
     "sim_default_options": (None, [C.POINTER(SimOptions)]),
     "sim_plan_create": (C.c_int, [C.POINTER(SimMesh), C.POINTER(SimMaterial), C.c_int32,

@@ -41,6 +41,7 @@ void sim_default_options(sim_options* o) {
   o->spin_limit = 0;
   o->cuda_stream = nullptr;
   o->n_host_threads = 0;
+  o->autotune = 0;
 }
 
 int sim_plan_create(const sim_mesh* mesh, const sim_material* mats, int32_t n_mat, double h,

@@ -117,11 +117,11 @@ __device__ __forceinline__ LaneMeta fetch_meta(const DevSim& d, const int2* tile
   return m;
 }
 
-// z partials: one slot per run of tiles of one row group -> p1_part[slot][comp][row]
-template <class T>
+// z partials: one slot per run of tiles of one row group -> p1_part[slot][comp][row].
+// U: tiles in flight per warp (the format's default, or half of it).
+template <class T, int U>
 __global__ void __launch_bounds__(256, 2) k_pass1(DevSim d) {
   using F = Fmt<T>;
-  constexpr int U = F::kUnroll;
   static_assert(U * kRowsPerWarp <= 32, "one metadata entry per lane");
   const T* S = F::vals(d);
   const T* zero = reinterpret_cast<const T*>(d.zero);
@@ -239,10 +239,9 @@ __global__ void k_reduce1(DevSim d) {
 constexpr size_t kP2Smem = sizeof(float) * kWarps * 3 * TW;
 
 // x partials: one slot per run of tiles of one column tile -> p2_part[slot][comp][column]
-template <class T>
+template <class T, int U>
 __global__ void __launch_bounds__(256, 2) k_pass2(DevSim d) {
   using F = Fmt<T>;
-  constexpr int U = F::kUnroll;
   static_assert(U * kRowsPerWarp <= 32, "one metadata entry per lane");
   const T* S = F::vals(d);
   const T* zero = reinterpret_cast<const T*>(d.zero);
@@ -406,20 +405,26 @@ __global__ void k_residual(DevSim d) {
 int sinv_setup() {
   // pass 1 stages the g slices of a CTA's column tiles: up to 3 KB per tile of its range
   const int most = kMaxStagedCols * 3 * TW * (int)sizeof(float);
-  if (cudaFuncSetAttribute(k_pass1<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, most) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k_pass1<unsigned short>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           most) != cudaSuccess)
-    return SIM_ECUDA;
+  const void* fns[] = {(const void*)k_pass1<float, 2>, (const void*)k_pass1<float, 1>,
+                       (const void*)k_pass1<unsigned short, 4>,
+                       (const void*)k_pass1<unsigned short, 2>};
+  for (const void* f : fns)
+    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, most) != cudaSuccess)
+      return SIM_ECUDA;
   return SIM_OK;
 }
 
+// unroll: 1 = the format's default tiles in flight, 0 = half of it
 void launch_pass1(const DevSim& d, cudaStream_t s) {
   const size_t smem = (size_t)d.s1_max_cols * 3 * TW * sizeof(float);
-  if (d.s_bf16)
-    k_pass1<unsigned short><<<d.s1_grid, 256, smem, s>>>(d);
-  else
-    k_pass1<float><<<d.s1_grid, 256, smem, s>>>(d);
+  const int g = d.s1_grid;
+  if (d.s_bf16) {
+    if (d.s1_unroll) k_pass1<unsigned short, 4><<<g, 256, smem, s>>>(d);
+    else k_pass1<unsigned short, 2><<<g, 256, smem, s>>>(d);
+  } else {
+    if (d.s1_unroll) k_pass1<float, 2><<<g, 256, smem, s>>>(d);
+    else k_pass1<float, 1><<<g, 256, smem, s>>>(d);
+  }
 }
 
 void launch_reduce1(const DevSim& d, cudaStream_t s) {
@@ -427,10 +432,14 @@ void launch_reduce1(const DevSim& d, cudaStream_t s) {
 }
 
 void launch_pass2(const DevSim& d, cudaStream_t s) {
-  if (d.s_bf16)
-    k_pass2<unsigned short><<<d.s2_grid, 256, kP2Smem, s>>>(d);
-  else
-    k_pass2<float><<<d.s2_grid, 256, kP2Smem, s>>>(d);
+  const int g = d.s2_grid;
+  if (d.s_bf16) {
+    if (d.s2_unroll) k_pass2<unsigned short, 4><<<g, 256, kP2Smem, s>>>(d);
+    else k_pass2<unsigned short, 2><<<g, 256, kP2Smem, s>>>(d);
+  } else {
+    if (d.s2_unroll) k_pass2<float, 2><<<g, 256, kP2Smem, s>>>(d);
+    else k_pass2<float, 1><<<g, 256, kP2Smem, s>>>(d);
+  }
 }
 
 void launch_reduce2(const DevSim& d, cudaStream_t s, int out_mode) {

@@ -48,6 +48,7 @@ struct sim_s {
   // [1] after collision, [2] after Delassus, then kMarksPerIter per iteration, then [end]
   std::vector<cudaEvent_t> ev;
   std::vector<int32_t> tet_caller_order;
+  sim_tuning tuning{};
 
   template <class T>
   T* alloc(size_t count) {
@@ -187,42 +188,136 @@ int get_graph(sim_s* s, int K, cudaGraphExec_t* out) {
 
 // Build and upload the balanced tile streams of the two profile products for the given
 // grid sizes and zero-load cost; (re)allocates the partial-sum slots.
-int upload_schedules(sim_s* s, int grid1, int grid2, double zero_cost) {
+std::vector<int2> pairs(const std::vector<int32_t>& v) {
+  std::vector<int2> o(v.size() / 2);
+  for (size_t k = 0; k < o.size(); ++k) o[k] = make_int2(v[2 * k], v[2 * k + 1]);
+  return o;
+}
+
+// Build and upload the balanced tile stream of one profile product for a grid size and a
+// zero-load cost; (re)allocates its partial-sum slots.
+int upload_schedule(sim_s* s, bool pass2, int grid, double zero_cost) {
   const Plan& p = s->plan;
   DevSim& d = s->d;
-  silg::StreamSchedule s1, s2;
-  silg::build_stream_schedule(p, false, grid1, zero_cost, &s1);
-  // pass 1 stages the g slices of a CTA's column tiles in shared memory (3 KB each, at
-  // most silg::kMaxStagedCols): more CTAs when a range has too many
-  while (s1.max_cols > silg::kMaxStagedCols && grid1 < (1 << 20)) {
-    grid1 *= 2;
-    silg::build_stream_schedule(p, false, grid1, zero_cost, &s1);
+  silg::StreamSchedule sc;
+  silg::build_stream_schedule(p, pass2, grid, zero_cost, &sc);
+  if (!pass2) {
+    // pass 1 stages the g slices of a CTA's column tiles in shared memory (3 KB each, at
+    // most silg::kMaxStagedCols): more CTAs when a range has too many
+    while (sc.max_cols > silg::kMaxStagedCols && grid < (1 << 20)) {
+      grid *= 2;
+      silg::build_stream_schedule(p, false, grid, zero_cost, &sc);
+    }
+    d.s1_tiles = s->upload(pairs(sc.tiles));
+    d.s1_cta = s->upload(sc.cta_first);
+    d.s1_seg_base = s->upload(sc.seg_base);
+    d.s1_seg_first = s->upload(sc.seg_first);
+    d.s1_col_first = s->upload(sc.cta_col_first);
+    d.s1_cols = s->upload(sc.cta_cols);
+    d.s1_col_slot = s->upload(sc.tile_col_slot);
+    d.s1_max_cols = sc.max_cols;
+    d.s1_grid = grid;
+    d.n_seg1 = sc.n_seg;
+    d.p1_part = s->alloc<float>((size_t)std::max(1, sc.n_seg) * 3 * silg::kRowGroup);
+  } else {
+    d.s2_tiles = s->upload(pairs(sc.tiles));
+    d.s2_cta = s->upload(sc.cta_first);
+    d.s2_seg_base = s->upload(sc.seg_base);
+    d.s2_seg_first = s->upload(sc.seg_first);
+    d.s2_grid = grid;
+    d.n_seg2 = sc.n_seg;
+    d.p2_part = s->alloc<float>((size_t)std::max(1, sc.n_seg) * 3 * silg::kTileW);
   }
-  silg::build_stream_schedule(p, true, grid2, zero_cost, &s2);
-  auto pairs = [](const std::vector<int32_t>& v) {
-    std::vector<int2> o(v.size() / 2);
-    for (size_t k = 0; k < o.size(); ++k) o[k] = make_int2(v[2 * k], v[2 * k + 1]);
-    return o;
-  };
-  d.s1_tiles = s->upload(pairs(s1.tiles));
-  d.s1_cta = s->upload(s1.cta_first);
-  d.s1_seg_base = s->upload(s1.seg_base);
-  d.s1_seg_first = s->upload(s1.seg_first);
-  d.s2_tiles = s->upload(pairs(s2.tiles));
-  d.s2_cta = s->upload(s2.cta_first);
-  d.s2_seg_base = s->upload(s2.seg_base);
-  d.s2_seg_first = s->upload(s2.seg_first);
-  d.s1_col_first = s->upload(s1.cta_col_first);
-  d.s1_cols = s->upload(s1.cta_cols);
-  d.s1_col_slot = s->upload(s1.tile_col_slot);
-  d.s1_max_cols = s1.max_cols;
-  d.s1_grid = grid1;
-  d.s2_grid = grid2;
-  d.n_seg1 = s1.n_seg;
-  d.n_seg2 = s2.n_seg;
-  d.p1_part = s->alloc<float>((size_t)std::max(1, s1.n_seg) * 3 * silg::kRowGroup);
-  d.p2_part = s->alloc<float>((size_t)std::max(1, s2.n_seg) * 3 * silg::kTileW);
   return SIM_OK;
+}
+
+// Launch configuration of the profile products before tuning: two CTAs per SM (the
+// register limit of the kernels), tiles balanced by count, the format's tiles in flight.
+constexpr int kDefaultCtasPerSm = 2;
+constexpr double kDefaultBalance = 1.0;
+
+// The autotuner of the two profile products. For each product it times every candidate
+// launch configuration -- CTAs per SM (1 to 4; above 2 the grid runs in waves), the cost
+// of an empty tile position relative to a stored value in the balanced split (1: equal
+// tiles per CTA; 0.25: nearer equal bytes), and the tiles in flight per warp (the format's
+// default or half) -- on the simulator's own matrix with CUDA events (median of 5 launches
+// after 2 warm-up launches), and keeps the fastest.
+int autotune_products(sim_s* s) {
+  DevSim& d = s->d;
+  cudaStream_t st = s->work;
+  {
+    // any right-hand side: the products' time does not depend on the values
+    std::vector<float> g(3 * (size_t)d.n_pad, 0.f);
+    uint32_t x = 12345u;
+    for (int k = 0; k < d.n; ++k)
+      for (int r = 0; r < 3; ++r) {
+        x = x * 1664525u + 1013904223u;
+        g[(size_t)r * d.n_pad + k] = (float)((x >> 8) * (1.0 / 16777216.0) - 0.5);
+      }
+    cudaMemcpyAsync(d.gvec, g.data(), g.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+    silg::launch_solve(d, st, silg::kOutX);   // zvec holds a valid z for pass 2
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SIM_ECUDA;
+  const int ctas[] = {1, 2, 3, 4};
+  const double balance[] = {1.0, 0.25};
+  const int unroll[] = {1, 0};
+  sim_tuning& T = s->tuning;
+  T = sim_tuning{};
+  int status = SIM_OK;
+  for (int pass = 0; pass < 2 && status == SIM_OK; ++pass) {
+    double best = 1e300;
+    int best_c = kDefaultCtasPerSm, best_u = 1;
+    double best_b = kDefaultBalance, dflt = 0;
+    int n_cand = 0;
+    for (int c : ctas)
+      for (double b : balance)
+        for (int u : unroll) {
+          upload_schedule(s, pass == 1, c * d.n_sm, b);
+          (pass ? d.s2_unroll : d.s1_unroll) = u;
+          auto launch = [&]() { pass ? silg::launch_pass2(d, st) : silg::launch_pass1(d, st); };
+          for (int w = 0; w < 2; ++w) launch();
+          std::vector<float> t(5);
+          for (float& ms : t) {
+            cudaEventRecord(e0, st);
+            launch();
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) status = SIM_ECUDA;
+            cudaEventElapsedTime(&ms, e0, e1);
+          }
+          if (cudaGetLastError() != cudaSuccess) status = SIM_ECUDA;
+          std::sort(t.begin(), t.end());
+          const double us = 1e3 * t[2];
+          ++n_cand;
+          if (c == kDefaultCtasPerSm && b == kDefaultBalance && u == 1) dflt = us;
+          if (us < best) {
+            best = us;
+            best_c = c;
+            best_b = b;
+            best_u = u;
+          }
+        }
+    upload_schedule(s, pass == 1, best_c * d.n_sm, best_b);
+    (pass ? d.s2_unroll : d.s1_unroll) = best_u;
+    if (pass == 0) {
+      T.pass1_ctas = d.s1_grid;
+      T.pass1_unroll = best_u;
+      T.pass1_balance = best_b;
+      T.pass1_us = best;
+      T.pass1_default_us = dflt;
+    } else {
+      T.pass2_ctas = d.s2_grid;
+      T.pass2_unroll = best_u;
+      T.pass2_balance = best_b;
+      T.pass2_us = best;
+      T.pass2_default_us = dflt;
+    }
+    T.candidates = n_cand;
+  }
+  T.tuned = status == SIM_OK;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return status;
 }
 
 // Per-scene inputs of the device arrays (one entry for sim_create).
@@ -357,7 +452,9 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     d.n_sm = std::max(1, nsm);
     d.zero = s->alloc<float>(silg::kTileW);
-    if (int st = upload_schedules(s, 2 * d.n_sm, 2 * d.n_sm, 1.0); st != SIM_OK) return st;
+    d.s1_unroll = d.s2_unroll = 1;
+    upload_schedule(s, false, kDefaultCtasPerSm * d.n_sm, kDefaultBalance);
+    upload_schedule(s, true, kDefaultCtasPerSm * d.n_sm, kDefaultBalance);
   }
   d.gvec = s->alloc<float>(3 * (size_t)p.n_pad);
   d.zvec = s->alloc<float>(3 * (size_t)p.n_pad);
@@ -446,6 +543,10 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
     if (st != SIM_OK) return st;
   }
   d.cr_R = s->cluster;
+  if (o->autotune) {
+    int st = autotune_products(s);
+    if (st != SIM_OK) return st;
+  }
   cudaError_t e = cudaStreamSynchronize(s->work);
   if (e != cudaSuccess) return cuda_status(e);
   return cuda_status(cudaGetLastError());
@@ -643,6 +744,19 @@ int sim_create(const sim_mesh* mesh, const sim_material* mats, int32_t n_mat,
 int sim_create_batch(const sim_scene* scenes, int32_t n_scenes, double h,
                      const sim_options* opts, sim_t** out) {
   return create_common(scenes, n_scenes, h, opts, 0.0, out);
+}
+
+int sim_get_tuning(const sim_t* s, sim_tuning* out) {
+  if (!s || !out) return SIM_EINVAL;
+  *out = s->tuning;
+  if (!out->tuned) {
+    out->pass1_ctas = s->d.s1_grid;
+    out->pass2_ctas = s->d.s2_grid;
+    out->pass1_unroll = s->d.s1_unroll;
+    out->pass2_unroll = s->d.s2_unroll;
+    out->pass1_balance = out->pass2_balance = kDefaultBalance;
+  }
+  return SIM_OK;
 }
 
 int sim_get_scene_residuals(sim_t* s, int32_t capacity, double* out) {
