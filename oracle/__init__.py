@@ -26,5 +26,8 @@ Modules:
                   functions and their derivatives (App. B.2), conjugate residual
   sparse_inverse  elimination tree, Cholesky factor and its inverse (Theorem 1, Alg. 2)
   integrator      the frame loop of Alg. 4, residual and energy diagnostics
+  precision       BF16 storage of S and one residual correction (not from the paper)
+  mlp             the learned warm start's network: forward, backward, loss (not from the
+                  paper: a predictor of the initial contact impulses)
 """
 from .integrator import Oracle, OracleOptions  # noqa: F401
