@@ -268,6 +268,37 @@ int sim_local_project(sim_t* sim, const double* q, double* p);
 int sim_get_delassus(sim_t* sim, int32_t capacity, double* Wtilde, int32_t* cv_vertex,
                      int32_t* n_out);
 
+/* ---- learned warm start (not from the paper) ----------------------------------------
+ * A small network predicts, per contact, the initial impulse lambda^0 and a normal
+ * displacement guess from SIM_MLP_FEATURES features. The paper starts every frame from
+ * lambda = 0; the network is an addition, trained on frames the plain method solved, with
+ * the cold start kept as the fallback. Layout of the flat FP32 parameter vector
+ * (SIM_MLP_PARAMS values): W1 (16 x 128, row = input; rows 11..15 multiply zero padding),
+ * b1 (128), W2 (128 x 128), b2, W3 (128 x 128), b3, W4 (128 x 8, columns 4..7 unused), b4 (8);
+ * hidden units use GELU(x) = x Phi(x). The device computes with BF16 weights and
+ * activations and FP32 accumulation (tensor cores). */
+#define SIM_MLP_FEATURES 11
+#define SIM_MLP_OUTPUTS 4
+#define SIM_MLP_PARAMS 36232
+typedef struct sim_mlp_s sim_mlp_t;
+/* A network on `device` with zero parameters; max_batch bounds the rows of one gradient. */
+int sim_mlp_create(int32_t device, int32_t max_batch, sim_mlp_t** out);
+void sim_mlp_destroy(sim_mlp_t* net);
+/* Weights uniform in +-sqrt(6 / (fan_in + fan_out)) from a splitmix64 stream, biases 0. */
+int sim_mlp_init(sim_mlp_t* net, uint64_t seed);
+int sim_mlp_set_params(sim_mlp_t* net, const float* theta);   /* also resets Adam's moments */
+int sim_mlp_get_params(const sim_mlp_t* net, float* theta);
+/* Y (rows x SIM_MLP_OUTPUTS) = net(X (rows x SIM_MLP_FEATURES)); host arrays. */
+int sim_mlp_forward(sim_mlp_t* net, const float* X, int32_t rows, float* Y);
+/* Gradient (SIM_MLP_PARAMS) and value of L = 1/(2 rows) sum (Y - T)^2 over the outputs;
+ * rows <= max_batch (else SIM_ECAPACITY). grad or loss may be NULL. */
+int sim_mlp_gradient(sim_mlp_t* net, const float* X, const float* T, int32_t rows, float* grad,
+                     float* loss);
+/* Adam (beta 0.9 / 0.999, eps 1e-8) on minibatches of `batch` rows of a fresh seeded
+ * permutation each epoch; epoch_loss (epochs values, or NULL) receives the mean batch loss. */
+int sim_mlp_train(sim_mlp_t* net, const float* X, const float* T, int32_t rows, int32_t epochs,
+                  int32_t batch, float lr, uint64_t seed, float* epoch_loss);
+
 /*
  * x = A^-1 g through the two profile products, for callers that cannot allocate device
  * memory at the time of the call: real-time loops that forbid cudaMalloc (it may

@@ -157,6 +157,68 @@ def _torch_stream():
     return None
 
 
+def _fptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+class WarmStartNet:
+    """The warm-start network on one GPU (thin wrapper over the sim_mlp_* C ABI)."""
+
+    FEATURES, OUTPUTS, PARAMS = _abi.MLP_FEATURES, _abi.MLP_OUTPUTS, _abi.MLP_PARAMS
+
+    def __init__(self, device=0, max_batch=65536, seed=None):
+        h = C.c_void_p()
+        _check(lib().sim_mlp_create(int(device), int(max_batch), C.byref(h)), "sim_mlp_create")
+        self._h = h
+        if seed is not None:
+            _check(lib().sim_mlp_init(self._h, int(seed)), "sim_mlp_init")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().sim_mlp_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_params(self, theta):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        assert t.size == self.PARAMS
+        _check(lib().sim_mlp_set_params(self._h, _fptr(t)), "sim_mlp_set_params")
+
+    def params(self):
+        t = np.zeros(self.PARAMS, np.float32)
+        _check(lib().sim_mlp_get_params(self._h, _fptr(t)), "sim_mlp_get_params")
+        return t
+
+    def forward(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, self.FEATURES)
+        Y = np.zeros((X.shape[0], self.OUTPUTS), np.float32)
+        _check(lib().sim_mlp_forward(self._h, _fptr(X), X.shape[0], _fptr(Y)), "sim_mlp_forward")
+        return Y
+
+    def gradient(self, X, T):
+        X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, self.FEATURES)
+        T = np.ascontiguousarray(T, dtype=np.float32).reshape(-1, self.OUTPUTS)
+        g = np.zeros(self.PARAMS, np.float32)
+        loss = np.zeros(1, np.float32)
+        _check(lib().sim_mlp_gradient(self._h, _fptr(X), _fptr(T), X.shape[0], _fptr(g),
+                                      _fptr(loss)), "sim_mlp_gradient")
+        return g, float(loss[0])
+
+    def train(self, X, T, epochs, batch=512, lr=1e-3, seed=0):
+        X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, self.FEATURES)
+        T = np.ascontiguousarray(T, dtype=np.float32).reshape(-1, self.OUTPUTS)
+        el = np.zeros(max(1, epochs), np.float32)
+        _check(lib().sim_mlp_train(self._h, _fptr(X), _fptr(T), X.shape[0], int(epochs),
+                                   int(batch), float(lr), int(seed), _fptr(el)), "sim_mlp_train")
+        return el[:epochs]
+
+
 class Simulator:
     """One scene, or a batch of independent scenes (a list), on one GPU. Every method is a
     thin call into the C ABI. A batch numbers vertices scene after scene; scene_offsets

@@ -17,6 +17,8 @@ PHASES = ["collide", "delassus", "local", "assemble", "spmv1", "solve", "spmv2",
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
+_fp = C.POINTER(C.c_float)
+MLP_FEATURES, MLP_OUTPUTS, MLP_PARAMS = 11, 4, 36232
 
 
 class SimMesh(C.Structure):
@@ -77,6 +79,15 @@ PROTOTYPES = {
                                    C.POINTER(SimOptions), C.POINTER(C.c_void_p)]),
     "sim_get_scene_residuals": (C.c_int, [C.c_void_p, C.c_int32, _dp]),
     "sim_get_tuning": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sim_mlp_create": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_void_p)]),
+    "sim_mlp_destroy": (None, [C.c_void_p]),
+    "sim_mlp_init": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "sim_mlp_set_params": (C.c_int, [C.c_void_p, _fp]),
+    "sim_mlp_get_params": (C.c_int, [C.c_void_p, _fp]),
+    "sim_mlp_forward": (C.c_int, [C.c_void_p, _fp, C.c_int32, _fp]),
+    "sim_mlp_gradient": (C.c_int, [C.c_void_p, _fp, _fp, C.c_int32, _fp, _fp]),
+    "sim_mlp_train": (C.c_int, [C.c_void_p, _fp, _fp, C.c_int32, C.c_int32, C.c_int32, C.c_float,
+                                C.c_uint64, _fp]),
     "sim_strerror": (C.c_char_p, [C.c_int]),
     "sim_default_options": (None, [C.POINTER(SimOptions)]),
     "sim_plan_create": (C.c_int, [C.POINTER(SimMesh), C.POINTER(SimMaterial), C.c_int32,
