@@ -147,7 +147,8 @@ enum { SIM_PHASE_COLLIDE = 0,   /* prediction and collision detection (App. A.1)
        SIM_PHASE_INTEGRATE = 7, /* final residual and integration                         */
        SIM_PHASE_REDUCE = 8,    /* fixed-order sums of both products' partial sums (and a
                                    BF16 residual correction)                              */
-       SIM_NUM_PHASES = 9 };
+       SIM_PHASE_WARMSTART = 9, /* warm-start features, guess and its acceptance          */
+       SIM_NUM_PHASES = 10 };
 
 /* Sizes of the precomputed structure (Theorem 1 profile of S). */
 typedef struct {
@@ -298,6 +299,23 @@ int sim_mlp_gradient(sim_mlp_t* net, const float* X, const float* T, int32_t row
  * permutation each epoch; epoch_loss (epochs values, or NULL) receives the mean batch loss. */
 int sim_mlp_train(sim_mlp_t* net, const float* X, const float* T, int32_t rows, int32_t epochs,
                   int32_t batch, float lr, uint64_t seed, float* epoch_loss);
+/* Start of each frame: mode 0 cold (lambda = 0, q = s~; the paper's start, the default),
+ * 1 the network's guess (net's current parameters are copied; same device), 2 the previous
+ * frame's impulse and move at the same vertex and obstacle. A guess is kept for a scene only
+ * if the residual of its impulses at k = 0 (at the position they predict) is below the cold
+ * start's. */
+int sim_set_warmstart(sim_t* sim, const sim_mlp_t* net, int32_t mode);
+/* Training samples of the last frame, one per contact (device order): X (n x
+ * SIM_MLP_FEATURES) the features at the frame's start -- gap / margin, normal (3), relative
+ * velocity h / margin (3), the previous frame's impulse at the same vertex and obstacle in
+ * this frame's basis / scale (3, or 0), m_v W~_vv -- where scale = margin / (h^2 W~_vv); T
+ * (n x 4) what the network should output: the frame's final impulse / scale minus features
+ * 7..9, and the vertex's move along the normal over the frame / margin. The learned start
+ * uses lambda^0 = (features 7..9 + output 0..2) scale and translates the scene by the mean
+ * over its contact vertices of (output 3 x margin) x normal, kept within one margin of the
+ * translation h^2 sum_j D_j^T lambda_j^0 / (the scene's free mass) that the impulses give
+ * it. *n_out receives the count; arrays hold `capacity` rows. */
+int sim_get_warmstart_samples(sim_t* sim, int32_t capacity, float* X, float* T, int32_t* n_out);
 
 /*
  * x = A^-1 g through the two profile products, for callers that cannot allocate device

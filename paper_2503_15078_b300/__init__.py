@@ -271,6 +271,23 @@ class Simulator:
         if q0 is not None:
             self.set_state(q0, v0 if v0 is not None else np.zeros_like(q0))
 
+    def set_warmstart(self, mode, net=None):
+        """0 cold (the paper's start), 1 the network's guess, 2 the previous frame's impulses."""
+        _check(lib().sim_set_warmstart(self._h, net.handle if net is not None else None,
+                                       int(mode)), "sim_set_warmstart")
+
+    def warmstart_samples(self):
+        """(features, targets) of the last frame's contacts."""
+        n = C.c_int32()
+        _check(lib().sim_get_warmstart_samples(self._h, 0, None, None, C.byref(n)),
+               "sim_get_warmstart_samples")
+        c = n.value
+        X = np.zeros((max(c, 1), WarmStartNet.FEATURES), np.float32)
+        T = np.zeros((max(c, 1), WarmStartNet.OUTPUTS), np.float32)
+        _check(lib().sim_get_warmstart_samples(self._h, c, _fptr(X), _fptr(T), C.byref(n)),
+               "sim_get_warmstart_samples")
+        return X[:c], T[:c]
+
     def tuning(self):
         """Launch configuration of the profile products (autotuned or fixed)."""
         t = _abi.SimTuning()

@@ -11,9 +11,9 @@ SIM_OK = 0
 STATUS = {0: "SIM_OK", -1: "SIM_EINVAL", -2: "SIM_ENOMEM", -3: "SIM_ENOTSPD", -4: "SIM_ECUDA",
           -5: "SIM_ECAPACITY", -6: "SIM_ETIMEOUT", -7: "SIM_ENONFINITE", -8: "SIM_ENOTSUP"}
 SIM_MAX_RESIDUALS = 64
-SIM_NUM_PHASES = 9
+SIM_NUM_PHASES = 10
 PHASES = ["collide", "delassus", "local", "assemble", "spmv1", "solve", "spmv2", "integrate",
-          "reduce"]
+          "reduce", "warmstart"]
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
@@ -80,6 +80,9 @@ PROTOTYPES = {
     "sim_get_scene_residuals": (C.c_int, [C.c_void_p, C.c_int32, _dp]),
     "sim_get_tuning": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sim_mlp_create": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_void_p)]),
+    "sim_set_warmstart": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "sim_get_warmstart_samples": (C.c_int, [C.c_void_p, C.c_int32, _fp, _fp,
+                                            C.POINTER(C.c_int32)]),
     "sim_mlp_destroy": (None, [C.c_void_p]),
     "sim_mlp_init": (C.c_int, [C.c_void_p, C.c_uint64]),
     "sim_mlp_set_params": (C.c_int, [C.c_void_p, _fp]),

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "mlp.cuh"
 #include "plan.hpp"
 
 namespace silg {
@@ -54,6 +55,7 @@ struct DevSim {
   const double* scene_margin; // contact margin
   const double* scene_Lref;   // rest bounding-box diagonal (residual scale)
   const double* scene_hvel;   // 3 per scene: velocity of the scene's pinned vertices
+  const double* scene_mass;   // the scene's free mass
   // per frame, from the contact lists (k_scene_ranges): contact vertices [sc_cvb[s],
   // sc_cvb[s+1]) and contacts [sc_jb[s], sc_jb[s+1]) of scene s; its W~ block (row-major,
   // ld sc_ld[s]) at sc_wtoff[s]; its first 64 x 64 W~ tile in the tile list
@@ -63,6 +65,22 @@ struct DevSim {
   long long* sc_wtoff;
   int* sc_tileoff;
   double* resid_scene;        // n_scenes x (kMaxIters + 1)
+  // warm start (not from the paper): 0 cold (lambda = 0, q = s~), 1 learned, 2 the previous
+  // frame's impulses
+  int ws_mode;
+  MlpDev ws_net;              // BF16 weights (w_t) and the parameter vector (biases)
+  float* ws_feat;             // cap x kMlpIn: features at the frame start
+  float* ws_out;              // cap x kMlpOut: network outputs
+  double* ws_scale;           // cap: impulse scale margin / (h^2 W~_vv)
+  double* ws_lam0;            // cap x 3: the guess (contact frame)
+  double* ws_move;            // cap: the guessed move of the contact's vertex along its normal
+  double* ws_shift;           // 6 per scene: the impulse translation and the applied one
+  double* ws_res;             // 2 per scene: residual of the guess, of the cold start
+  float* ws_target;           // cap x 4: the frame's final impulse / scale, normal move / margin
+  int* prev_valid;            // n: the vertex had a contact in the previous frame
+  int* prev_obst;             // n: its obstacle
+  double* prev_force;         // 3 n: its impulse in world coordinates, D^T lambda
+  double* prev_move;          // n: its move along the normal over the frame (q - s~) . n
 
   // per vertex (internal numbering, n_all)
   double* q_t;      // 3 n_all
@@ -230,6 +248,12 @@ void launch_ytz(const DevSim& d, cudaStream_t s);
 int launch_cr(const DevSim& d, cudaStream_t s, int cluster);
 void launch_yu(const DevSim& d, cudaStream_t s);
 void launch_integrate(const DevSim& d, cudaStream_t s);
+// warm start: features of the frame's contacts (always, for training data); the guess and
+// its acceptance (modes 1, 2); the record of the frame's impulses and targets at its end
+void launch_ws_features(const DevSim& d, cudaStream_t s);
+void launch_ws_start(const DevSim& d, cudaStream_t s);
+void launch_ws_record(const DevSim& d, cudaStream_t s);
+int ws_kernels(int mode);   // launches of launch_ws_start
 void launch_scan(const int* in, int* out, int n, const int* n_dev, int* total, cudaStream_t s);
 int cr_setup(int n_scenes, int* cluster_out, size_t* smem_out);
 int sinv_setup();

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include "device.cuh"
+#include "fb.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -25,7 +26,6 @@ constexpr int kCrThreads = 256;
 // W~ is stored row-major with its leading dimension padded to a multiple of 4 floats
 // (zero padding), so rows can be read with 16-byte vector loads.
 __host__ __device__ __forceinline__ int wt_ld(int ncv) { return (ncv + 3) & ~3; }
-constexpr double kTinyRel = 1e-12;
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -33,10 +33,6 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
-  // non-negative doubles order like their bit patterns
-  atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
-}
 
 __device__ void tangent_frame(const double* n, double* f1, double* f2) {
   int k = 0;
@@ -539,60 +535,18 @@ __global__ void k_contact_eval(DevSim d, int k, int final_eval) {
   const double h = d.h;
   double D[9];
   for (int r = 0; r < 9; ++r) D[r] = d.ct_D[9 * j + r];
-  double dqv[3], q[3], qt[3];
+  double dqv[3], q[3];
   for (int r = 0; r < 3; ++r) {
     dqv[r] = (double)d.dq[3 * v + r];
     q[r] = d.q_ref[3 * v + r] + dqv[r];
-    qt[r] = d.q_t[3 * v + r];
   }
-  const double dn = D[0] * q[0] + D[1] * q[1] + D[2] * q[2] - d.ct_dn[j];
-  double vf[2];
-  for (int a = 0; a < 2; ++a) {
-    const double* f = D + 3 + 3 * a;
-    vf[a] = ((f[0] * (q[0] - qt[0]) + f[1] * (q[1] - qt[1]) + f[2] * (q[2] - qt[2])) -
-             h * d.ct_df[2 * j + a]) / h;
-  }
-  const double ln = d.ct_lam[3 * j], lf0 = d.ct_lam[3 * j + 1], lf1 = d.ct_lam[3 * j + 2];
-  const double rn = d.ct_r[2 * j], rf = d.ct_r[2 * j + 1], mu = d.ct_mu[j];
-  // normal row (Eqs. 52-54)
-  const double rho = sqrt(dn * dn + rn * rn * ln * ln);
-  const double phin = dn + rn * ln - rho;
-  double omn, En;
-  if (rho == 0.0) {
-    omn = 1.0;
-    En = 0.0;
-  } else {
-    omn = 1.0 - dn / rho;
-    En = (1.0 - rn * ln / rho) * rn;
-  }
-  // friction rows (Eqs. 55-57)
-  double omf, Ef, phif0, phif1;
-  if (ln <= 0.0 || mu <= 0.0) {
-    omf = 0.0;
-    Ef = 1.0;
-    phif0 = lf0;
-    phif1 = lf1;
-  } else {
-    const double a = sqrt(vf[0] * vf[0] + vf[1] * vf[1]);
-    const double lf = sqrt(lf0 * lf0 + lf1 * lf1);
-    const double s = mu * ln - lf;
-    const double root = sqrt(a * a + rf * rf * s * s);
-    const double num = root - rf * s;
-    const double den = a + mu * rf * ln - root;
-    const double scale = a + mu * rf * ln + rf * fabs(s);
-    if (num <= kTinyRel * scale)
-      Ef = 0.0;
-    else if (den <= kTinyRel * scale)
-      Ef = (a + rf * (lf - mu * ln)) / (mu * ln);
-    else
-      Ef = num / den * rf;
-    omf = 1.0;
-    phif0 = vf[0] + Ef * lf0;
-    phif1 = vf[1] + Ef * lf1;
-  }
+  const double lamv[3] = {d.ct_lam[3 * j], d.ct_lam[3 * j + 1], d.ct_lam[3 * j + 2]};
   const int sc = d.vert_scene[v];
-  const double res =
-      fmax(fabs(fmin(dn, rn * ln)), h * sqrt(phif0 * phif0 + phif1 * phif1)) / d.scene_Lref[sc];
+  const FbTerms fb = fb_terms(d, j, q, lamv, d.scene_Lref[sc]);
+  const double dn = fb.dn, phin = fb.phin, omn = fb.omn, En = fb.En;
+  const double omf = fb.omf, Ef = fb.Ef, phif0 = fb.phif0, phif1 = fb.phif1;
+  const double ln = lamv[0], lf0 = lamv[1], lf1 = lamv[2];
+  const double res = fb.res;
   atomic_max_nonneg(&d.resid[k], res);
   atomic_max_nonneg(&d.resid_scene[sc * (kMaxIters + 1) + k], res);
   if (final_eval) {

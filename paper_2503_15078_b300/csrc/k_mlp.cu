@@ -167,7 +167,11 @@ __device__ __forceinline__ void hidden_layer(const bf16* in, int ld_in, BF bfrag
 constexpr size_t kInferSmem = sizeof(bf16) * (kWTElems + 4 * (16 * kLdIn + 2 * 16 * kLdH)) +
                               sizeof(float) * kNBias;
 
-__global__ void __launch_bounds__(128) k_mlp_infer(MlpDev m, const float* X, int n, float* Y) {
+// n_dev (optional): the row count on the device, at most n (a launch sized for a capacity)
+__global__ void __launch_bounds__(128) k_mlp_infer(MlpDev m, const float* X, int n, const int* n_dev,
+                                                   float* Y) {
+  if (n_dev) n = min(n, *n_dev);
+  if (blockIdx.x * kMlpRows >= n) return;   // the whole CTA leaves together
   extern __shared__ __align__(16) unsigned char smem[];
   bf16* wt = reinterpret_cast<bf16*>(smem);
   bf16* act = wt + kWTElems;                         // per warp: x [16][kLdIn], h0, h1 [16][kLdH]
@@ -432,7 +436,13 @@ int mlp_setup() {
 
 void mlp_launch_infer(const MlpDev& m, const float* X, int n, float* Y, cudaStream_t s) {
   if (n <= 0) return;
-  k_mlp_infer<<<(n + kMlpRows - 1) / kMlpRows, 128, kInferSmem, s>>>(m, X, n, Y);
+  k_mlp_infer<<<(n + kMlpRows - 1) / kMlpRows, 128, kInferSmem, s>>>(m, X, n, nullptr, Y);
+}
+
+void mlp_launch_infer_dev(const MlpDev& m, const float* X, const int* n_dev, int n_max, float* Y,
+                          cudaStream_t s) {
+  if (n_max <= 0) return;
+  k_mlp_infer<<<(n_max + kMlpRows - 1) / kMlpRows, 128, kInferSmem, s>>>(m, X, n_max, n_dev, Y);
 }
 
 void mlp_launch_gradient(const MlpDev& m, const float* X, const float* T, const int* idx, int n,

@@ -1,0 +1,232 @@
+// Warm start of a frame (an addition to the paper, whose frames start from lambda = 0 and
+// q = s~): per contact, the impulse lambda^0 and a move of its vertex along the normal,
+// predicted by the network from per-contact features (the impulse as a change of the
+// previous frame's) or taken from the previous frame's contact at the same vertex and
+// obstacle; per scene, a translation from the moves (see k_ws_translate). The guess is kept
+// only if the residual of its impulses (the frame's residual measure at k = 0, at the
+// position those impulses predict) is below the cold start's; the decision is per scene.
+//
+// Features (dimensionless): gap at s~ / margin; the normal (3); the velocity relative to the
+// obstacle times h / margin (3); the previous frame's impulse at the same vertex and
+// obstacle, in this frame's contact basis / scale (3, or 0); m_v W~_vv in (0, 1] (how much
+// of the vertex's inertia the rest of the body adds). The impulse scale margin / (h^2 W~_vv)
+// is the impulse that moves the vertex by one margin.
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+#include "fb.cuh"
+
+namespace silg {
+namespace {
+
+__device__ __forceinline__ double wt_diag(const DevSim& d, int j) {
+  const int cv = d.ct_cv[j];
+  const int sc = d.vert_scene[d.ct_vert[j]], l = cv - d.sc_cvb[sc];
+  return (double)d.wt[d.sc_wtoff[sc] + (size_t)l * d.sc_ld[sc] + l];
+}
+
+__global__ void k_ws_features(DevSim d) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = min(d.counters[kCntContacts], d.cap);
+  if (j >= c) return;
+  const int v = d.ct_vert[j], sc = d.vert_scene[v], o = d.ct_obst[j];
+  const double* D = d.ct_D + 9 * j;
+  const double margin = d.scene_margin[sc], h = d.h;
+  const double w = fmax(wt_diag(d, j), 1e-300);
+  const double scale = margin / (h * h * w);
+  float* f = d.ws_feat + (size_t)j * kMlpIn;
+  double st[3];
+  for (int r = 0; r < 3; ++r) st[r] = d.s_tilde[3 * v + r];
+  f[0] = (float)((D[0] * st[0] + D[1] * st[1] + D[2] * st[2] - d.ct_dn[j]) / margin);
+  for (int r = 0; r < 3; ++r) f[1 + r] = (float)D[r];
+  // relative velocity: the vertex's v_t minus the obstacle's surface velocity
+  for (int r = 0; r < 3; ++r) {
+    const double u = d.ct_df[2 * j] * D[3 + r] + d.ct_df[2 * j + 1] * D[6 + r];  // tangential part
+    f[4 + r] = (float)(h * (d.v_t[3 * v + r] - u) / margin);
+  }
+  double lp[3] = {0.0, 0.0, 0.0};
+  if (d.prev_valid[v] && d.prev_obst[v] == o)
+    for (int r = 0; r < 3; ++r)
+      lp[r] = D[3 * r] * d.prev_force[3 * v] + D[3 * r + 1] * d.prev_force[3 * v + 1] +
+              D[3 * r + 2] * d.prev_force[3 * v + 2];
+  for (int r = 0; r < 3; ++r) f[7 + r] = (float)(lp[r] / scale);
+  f[10] = (float)(d.mass[v] * w);
+  for (int r = kMlpNF; r < kMlpIn; ++r) f[r] = 0.f;
+  d.ws_scale[j] = scale;
+}
+
+// the guess of contact j: its impulse (admissible: lambda_n >= 0, |lambda_f| <= mu
+// lambda_n) and the move of its vertex along the normal
+__global__ void k_ws_guess(DevSim d) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = min(d.counters[kCntContacts], d.cap);
+  if (j >= c) return;
+  const int v = d.ct_vert[j], sc = d.vert_scene[v];
+  const double scale = d.ws_scale[j], mu = d.ct_mu[j], margin = d.scene_margin[sc];
+  double lam[3] = {0.0, 0.0, 0.0}, move = 0.0;
+  if (d.ws_mode == 1) {
+    // the network predicts the change from the previous frame's impulse (features 7..9)
+    const float* y = d.ws_out + (size_t)j * kMlpOut;
+    const float* f = d.ws_feat + (size_t)j * kMlpIn;
+    for (int r = 0; r < 3; ++r) lam[r] = ((double)f[7 + r] + (double)y[r]) * scale;
+    move = (double)y[3] * margin;
+  } else {
+    const float* f = d.ws_feat + (size_t)j * kMlpIn;
+    for (int r = 0; r < 3; ++r) lam[r] = (double)f[7 + r] * scale;
+    if (d.prev_valid[v] && d.prev_obst[v] == d.ct_obst[j]) move = d.prev_move[v];
+  }
+  lam[0] = fmax(lam[0], 0.0);
+  const double lf = sqrt(lam[1] * lam[1] + lam[2] * lam[2]), cap = mu * lam[0];
+  if (lf > cap) {
+    const double s = lf > 0.0 ? cap / lf : 0.0;
+    lam[1] *= s;
+    lam[2] *= s;
+  }
+  for (int r = 0; r < 3; ++r) d.ws_lam0[3 * j + r] = lam[r];
+  d.ws_move[j] = move;
+}
+
+// per scene (one CTA each): two translations, summed in a fixed order. The impulse
+// translation h^2 sum_j D_j^T lambda_j^0 / M is what the guessed impulses give the scene's
+// free mass over one step (an impulse guess that holds a resting body up also lifts its
+// predicted position by the sag of gravity); it judges the impulse guess. The move
+// translation is the mean over the scene's contact vertices of their guessed move along the
+// normal; the scene is moved by it, kept within one contact margin of the impulse
+// translation.
+__global__ void k_ws_translate(DevSim d) {
+  const int sc = blockIdx.x;
+  const int jb = d.sc_jb[sc], je = d.sc_jb[sc + 1];
+  __shared__ double part[6][128];
+  double t[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int j = jb + threadIdx.x; j < je; j += blockDim.x) {
+    const double* D = d.ct_D + 9 * j;
+    const double* l = d.ws_lam0 + 3 * j;
+    for (int r = 0; r < 3; ++r) t[r] += D[r] * l[0] + D[3 + r] * l[1] + D[6 + r] * l[2];
+    if (d.cv_first[d.ct_cv[j]] == j)
+      for (int r = 0; r < 3; ++r) t[3 + r] += d.ws_move[j] * D[r];
+  }
+  for (int r = 0; r < 6; ++r) part[r][threadIdx.x] = t[r];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int r = 0; r < 6; ++r) part[r][threadIdx.x] += part[r][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int ncv = d.sc_cvb[sc + 1] - d.sc_cvb[sc];
+    double imp[3], dev[3], dn = 0.0;
+    for (int r = 0; r < 3; ++r) {
+      imp[r] = d.h * d.h * part[r][0] / d.scene_mass[sc];
+      dev[r] = (ncv > 0 ? part[3 + r][0] / ncv : 0.0) - imp[r];
+      dn += dev[r] * dev[r];
+    }
+    dn = sqrt(dn);
+    const double lim = d.scene_margin[sc], f = dn > lim ? lim / dn : 1.0;
+    for (int r = 0; r < 3; ++r) {
+      d.ws_shift[6 * sc + r] = imp[r];                 // judges the impulses
+      d.ws_shift[6 * sc + 3 + r] = imp[r] + f * dev[r];  // applied
+    }
+  }
+}
+
+// residuals at k = 0 of the guess (translated scene, guessed impulses) and of the cold
+// start (s~, lambda = 0), max per scene
+__global__ void k_ws_residuals(DevSim d) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = min(d.counters[kCntContacts], d.cap);
+  if (j >= c) return;
+  const int v = d.ct_vert[j], sc = d.vert_scene[v];
+  double q[3], q0[3], lam[3];
+  for (int r = 0; r < 3; ++r) {
+    q0[r] = d.q_ref[3 * v + r] + (double)d.dq[3 * v + r];
+    q[r] = q0[r] + d.ws_shift[6 * sc + r];
+    lam[r] = d.ws_lam0[3 * j + r];
+  }
+  const double zero[3] = {0.0, 0.0, 0.0};
+  const double L = d.scene_Lref[sc];
+  atomic_max_nonneg(&d.ws_res[2 * sc], fb_terms(d, j, q, lam, L).res);
+  atomic_max_nonneg(&d.ws_res[2 * sc + 1], fb_terms(d, j, q0, zero, L).res);
+}
+
+// strictly better than the cold start (an empty guess is the cold start and is not taken)
+__device__ __forceinline__ bool ws_accepted(const DevSim& d, int sc) {
+  return d.ws_res[2 * sc] < d.ws_res[2 * sc + 1];
+}
+
+// keep the guess where it is not worse than the cold start (per scene): impulses ...
+__global__ void k_ws_commit(DevSim d) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = min(d.counters[kCntContacts], d.cap);
+  if (j >= c) return;
+  if (!ws_accepted(d, d.vert_scene[d.ct_vert[j]])) return;
+  for (int r = 0; r < 3; ++r) d.ct_lam[3 * j + r] = d.ws_lam0[3 * j + r];
+}
+
+// ... and the translation of the scene's free vertices
+__global__ void k_ws_shift(DevSim d) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= d.n) return;
+  const int sc = d.vert_scene[v];
+  if (!ws_accepted(d, sc)) return;
+  for (int r = 0; r < 3; ++r) d.dq[3 * v + r] += (float)d.ws_shift[6 * sc + 3 + r];
+}
+
+__global__ void k_ws_clear(DevSim d) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < d.n) d.prev_valid[v] = 0;
+}
+
+// the frame's final impulses (for the next frame's features) and the training targets
+__global__ void k_ws_record(DevSim d) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = min(d.counters[kCntContacts], d.cap);
+  if (j >= c) return;
+  const int v = d.ct_vert[j], sc = d.vert_scene[v];
+  const double* D = d.ct_D + 9 * j;
+  const double* lam = d.ct_lam + 3 * j;
+  double mv = 0.0;
+  for (int r = 0; r < 3; ++r)
+    mv += D[r] * (d.q_ref[3 * v + r] + (double)d.dq[3 * v + r] - d.s_tilde[3 * v + r]);
+  if (d.cv_first[d.ct_cv[j]] == j) {
+    d.prev_valid[v] = 1;
+    d.prev_obst[v] = d.ct_obst[j];
+    d.prev_move[v] = mv;
+    for (int r = 0; r < 3; ++r)
+      d.prev_force[3 * v + r] = D[r] * lam[0] + D[3 + r] * lam[1] + D[6 + r] * lam[2];
+  }
+  // targets of the network: the change of the impulse from the previous frame's (the
+  // features 7..9 seen at this frame's start), over the scale; the normal move over the margin
+  const double scale = d.ws_scale[j];
+  const float* f = d.ws_feat + (size_t)j * kMlpIn;
+  float* t = d.ws_target + 4 * (size_t)j;
+  for (int r = 0; r < 3; ++r) t[r] = (float)(lam[r] / scale - (double)f[7 + r]);
+  t[3] = (float)(mv / d.scene_margin[sc]);
+}
+
+}  // namespace
+
+void launch_ws_features(const DevSim& d, cudaStream_t s) {
+  k_ws_features<<<(d.cap + 127) / 128, 128, 0, s>>>(d);
+}
+
+int ws_kernels(int mode) { return mode == 0 ? 0 : (mode == 1 ? 6 : 5); }
+
+void launch_ws_start(const DevSim& d, cudaStream_t s) {
+  if (d.ws_mode == 0) return;
+  cudaMemsetAsync(d.ws_res, 0, sizeof(double) * 2 * d.n_scenes, s);
+  if (d.ws_mode == 1)
+    mlp_launch_infer_dev(d.ws_net, d.ws_feat, d.counters + kCntContacts, d.cap, d.ws_out, s);
+  const int g = (d.cap + 127) / 128;
+  k_ws_guess<<<g, 128, 0, s>>>(d);
+  k_ws_translate<<<d.n_scenes, 128, 0, s>>>(d);
+  k_ws_residuals<<<g, 128, 0, s>>>(d);
+  k_ws_commit<<<g, 128, 0, s>>>(d);
+  k_ws_shift<<<(d.n + 255) / 256, 256, 0, s>>>(d);
+}
+
+void launch_ws_record(const DevSim& d, cudaStream_t s) {
+  k_ws_clear<<<(d.n + 255) / 256, 256, 0, s>>>(d);
+  k_ws_record<<<(d.cap + 127) / 128, 128, 0, s>>>(d);
+}
+
+}  // namespace silg

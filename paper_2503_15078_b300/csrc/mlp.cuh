@@ -57,6 +57,9 @@ int mlp_setup();
 void mlp_launch_convert(const MlpDev& m, cudaStream_t s);
 // Y (n x kMlpOut, FP32) = network(X (n x kMlpIn, FP32)); rows_idx (optional) selects X rows
 void mlp_launch_infer(const MlpDev& m, const float* X, int n, float* Y, cudaStream_t s);
+// the same for min(*n_dev, n_max) rows, the count read on the device (graph capture)
+void mlp_launch_infer_dev(const MlpDev& m, const float* X, const int* n_dev, int n_max, float* Y,
+                          cudaStream_t s);
 // gradient of the mean squared error over the batch rows idx[0..n) (all rows if idx is
 // null) into m.grad, loss into m.loss; n <= m.max_ctas * kMlpRows
 void mlp_launch_gradient(const MlpDev& m, const float* X, const float* T, const int* idx, int n,

@@ -86,6 +86,13 @@ double uniform01(uint64_t& s) { return (splitmix64(s) >> 11) * (1.0 / 9007199254
 
 extern "C" {
 
+// the network's device buffers (for sim_set_warmstart)
+const silg::MlpDev* silg_mlp_dev(const sim_mlp_t* net, int* device) {
+  if (!net) return nullptr;
+  if (device) *device = net->device;
+  return &net->m;
+}
+
 int sim_mlp_create(int32_t device, int32_t max_batch, sim_mlp_t** out) {
   if (!out || max_batch <= 0) return SIM_EINVAL;
   *out = nullptr;

@@ -45,7 +45,8 @@ struct sim_s {
   int64_t frame = 0;
   int last_iters = 0;
   // phase events recorded by event nodes of the frame graph: [0] frame start,
-  // [1] after collision, [2] after Delassus, then kMarksPerIter per iteration, then [end]
+  // [1] after collision, [2] after Delassus, [3] after the warm start, then kMarksPerIter
+  // per iteration, then [end]
   std::vector<cudaEvent_t> ev;
   std::vector<int32_t> tet_caller_order;
   sim_tuning tuning{};
@@ -129,8 +130,13 @@ void enqueue_frame(sim_s* s, int K, cudaStream_t st) {
   mark(1);
   if (s->has_obstacles) silg::launch_delassus(d, st);
   mark(2);
+  if (s->has_obstacles) {
+    silg::launch_ws_features(d, st);
+    silg::launch_ws_start(d, st);
+  }
+  mark(3);
   for (int k = 0; k < K; ++k) {
-    const int e = 3 + kMarksPerIter * k;
+    const int e = 4 + kMarksPerIter * k;
     silg::launch_local(d, st, false);
     mark(e);
     if (s->has_obstacles) silg::launch_contact_eval(d, st, k, false);
@@ -159,13 +165,18 @@ void enqueue_frame(sim_s* s, int K, cudaStream_t st) {
     }
     mark(e + 6);
   }
-  if (s->has_obstacles) silg::launch_contact_eval(d, st, K, true);
+  if (s->has_obstacles) {
+    silg::launch_contact_eval(d, st, K, true);
+    silg::launch_ws_record(d, st);
+  }
   silg::launch_integrate(d, st);
-  mark(3 + kMarksPerIter * K);
+  mark(4 + kMarksPerIter * K);
 }
 
+// frame graphs are cached per (iteration count, warm-start mode)
 int get_graph(sim_s* s, int K, cudaGraphExec_t* out) {
-  auto it = s->graphs.find(K);
+  const int key = 4 * K + s->d.ws_mode;
+  auto it = s->graphs.find(key);
   if (it != s->graphs.end()) {
     *out = it->second.exec;
     return SIM_OK;
@@ -181,7 +192,7 @@ int get_graph(sim_s* s, int K, cudaGraphExec_t* out) {
     cudaGraphDestroy(g.g);
     return cuda_status(e);
   }
-  s->graphs[K] = g;
+  s->graphs[key] = g;
   *out = g.exec;
   return SIM_OK;
 }
@@ -356,6 +367,13 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   d.scene_margin = s->upload(sd.margin);
   d.scene_Lref = s->upload(sd.L_ref);
   d.scene_hvel = s->upload(sd.hvel);
+  {
+    std::vector<double> sm(p.n_scenes, 0.0);
+    for (int v = 0; v < n_all; ++v)
+      if (!p.pinned[v]) sm[p.vertex_scene[v]] += p.mass[v];
+    for (double& m : sm) m = m > 0 ? m : 1.0;
+    d.scene_mass = s->upload(sm);
+  }
   d.sc_cvb = s->alloc<int>(p.n_scenes + 1);
   d.sc_jb = s->alloc<int>(p.n_scenes + 1);
   d.sc_ld = s->alloc<int>(p.n_scenes);
@@ -534,10 +552,28 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   d.wt_part = s->alloc<float>(
       (size_t)silg::wt_items_max(cap + 64 * p.n_scenes, d.wt_grid) * 64 * 64);
   if (silg::sinv_setup() != SIM_OK) return SIM_ECUDA;
-  s->ev.resize(4 + kMarksPerIter * silg::kMaxIters);
+  s->ev.resize(5 + kMarksPerIter * silg::kMaxIters);
   for (auto& e : s->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return SIM_ECUDA;
   d.cr_split = s->alloc<int>((size_t)p.n_scenes * 2 * (silg::kCrMaxRanks + 1));
+  // warm start
+  d.ws_mode = 0;
+  d.ws_net = silg::MlpDev{};
+  d.ws_net.theta = s->alloc<float>(silg::kMlpParams);
+  d.ws_net.w_t = s->alloc<__nv_bfloat16>(silg::kWTElems);
+  d.ws_feat = s->alloc<float>((size_t)cap * silg::kMlpIn);
+  d.ws_out = s->alloc<float>((size_t)cap * silg::kMlpOut);
+  d.ws_scale = s->alloc<double>(cap);
+  d.ws_lam0 = s->alloc<double>(3 * (size_t)cap);
+  d.ws_move = s->alloc<double>(cap);
+  d.ws_shift = s->alloc<double>(6 * (size_t)p.n_scenes);
+  d.ws_res = s->alloc<double>(2 * (size_t)p.n_scenes);
+  d.ws_target = s->alloc<float>(4 * (size_t)cap);
+  d.prev_valid = s->alloc<int>(n);
+  d.prev_obst = s->alloc<int>(n);
+  d.prev_force = s->alloc<double>(3 * (size_t)n);
+  d.prev_move = s->alloc<double>(n);
+  if (silg::mlp_setup() != 0) return SIM_ECUDA;
   if (s->has_obstacles) {
     int st = silg::cr_setup(p.n_scenes, &s->cluster, &s->cr_smem);
     if (st != SIM_OK) return st;
@@ -746,6 +782,51 @@ int sim_create_batch(const sim_scene* scenes, int32_t n_scenes, double h,
   return create_common(scenes, n_scenes, h, opts, 0.0, out);
 }
 
+const silg::MlpDev* silg_mlp_dev(const sim_mlp_t* net, int* device);
+
+int sim_set_warmstart(sim_t* s, const sim_mlp_t* net, int32_t mode) {
+  if (!s || mode < 0 || mode > 2 || (mode == 1 && !net)) return SIM_EINVAL;
+  cudaSetDevice(s->device);
+  cudaError_t e = cudaStreamSynchronize(s->launch);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (mode == 1) {
+    int dev = -1;
+    const silg::MlpDev* m = silg_mlp_dev(net, &dev);
+    if (!m || dev != s->device) return SIM_EINVAL;
+    e = cudaMemcpy(s->d.ws_net.theta, m->theta, sizeof(float) * silg::kMlpParams, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(s->d.ws_net.w_t, m->w_t, sizeof(__nv_bfloat16) * silg::kWTElems,
+                     cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  s->d.ws_mode = mode;   // graphs are cached per mode; the network's weights are read at launch
+  return SIM_OK;
+}
+
+int sim_get_warmstart_samples(sim_t* s, int32_t capacity, float* X, float* T, int32_t* n_out) {
+  if (!s || !n_out || capacity < 0) return SIM_EINVAL;
+  cudaSetDevice(s->device);
+  int st = sync_and_check(s);
+  if (st == SIM_ECUDA) return st;
+  int c = 0;
+  if (s->has_obstacles && s->frame > 0)
+    cudaMemcpy(&c, s->d.counters + silg::kCntContacts, sizeof(int), cudaMemcpyDeviceToHost);
+  c = std::min(c, s->d.cap);
+  *n_out = c;
+  if (c == 0 || capacity < c) return st;
+  std::vector<float> f((size_t)c * silg::kMlpIn), t(4 * (size_t)c);
+  cudaMemcpy(f.data(), s->d.ws_feat, f.size() * sizeof(float), cudaMemcpyDeviceToHost);
+  cudaError_t e = cudaMemcpy(t.data(), s->d.ws_target, t.size() * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  for (int j = 0; j < c; ++j) {
+    if (X)
+      for (int q = 0; q < silg::kMlpNF; ++q) X[(size_t)j * silg::kMlpNF + q] = f[(size_t)j * silg::kMlpIn + q];
+    if (T)
+      for (int q = 0; q < 4; ++q) T[4 * (size_t)j + q] = t[4 * (size_t)j + q];
+  }
+  return st;
+}
+
 int sim_get_tuning(const sim_t* s, sim_tuning* out) {
   if (!s || !out) return SIM_EINVAL;
   *out = s->tuning;
@@ -840,7 +921,9 @@ int sim_set_state(sim_t* s, const double* q, const double* v) {
       bq[3 * (size_t)p.internal[vv] + r] = a;
       bv[3 * (size_t)p.internal[vv] + r] = b;
     }
-  e = cudaMemcpy(s->d.q_t, bq.data(), bq.size() * sizeof(double), cudaMemcpyHostToDevice);
+  e = cudaMemset(s->d.prev_valid, 0, sizeof(int) * s->d.n);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(s->d.q_t, bq.data(), bq.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->d.v_t, bv.data(), bv.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(s->d.err, 0, sizeof(int));
   s->frame = 0;
@@ -874,7 +957,7 @@ int sim_get_phase_times(sim_t* s, double* ms) {
   for (int k = 0; k < SIM_NUM_PHASES; ++k) ms[k] = 0.0;
   if (s->frame == 0 || s->last_iters == 0) return SIM_OK;
   const int K = s->last_iters;
-  cudaError_t e = cudaEventSynchronize(s->ev[3 + kMarksPerIter * K]);
+  cudaError_t e = cudaEventSynchronize(s->ev[4 + kMarksPerIter * K]);
   if (e != cudaSuccess) return cuda_status(e);
   auto el = [&](int a, int b) {
     float t = 0.f;
@@ -883,8 +966,9 @@ int sim_get_phase_times(sim_t* s, double* ms) {
   };
   ms[SIM_PHASE_COLLIDE] = el(0, 1);
   ms[SIM_PHASE_DELASSUS] = el(1, 2);
+  ms[SIM_PHASE_WARMSTART] = el(2, 3);
   for (int k = 0; k < K; ++k) {
-    const int b = 3 + kMarksPerIter * k;
+    const int b = 4 + kMarksPerIter * k;
     ms[SIM_PHASE_LOCAL] += el(b - 1, b);
     ms[SIM_PHASE_ASSEMBLE] += el(b, b + 1);
     ms[SIM_PHASE_SPMV1] += el(b + 1, b + 2);
@@ -892,7 +976,7 @@ int sim_get_phase_times(sim_t* s, double* ms) {
     ms[SIM_PHASE_SOLVE] += el(b + 3, b + 4);
     ms[SIM_PHASE_SPMV2] += el(b + 4, b + 5);
   }
-  ms[SIM_PHASE_INTEGRATE] = el(3 + kMarksPerIter * K - 1, 3 + kMarksPerIter * K);
+  ms[SIM_PHASE_INTEGRATE] = el(4 + kMarksPerIter * K - 1, 4 + kMarksPerIter * K);
   return SIM_OK;
 }
 

@@ -1,0 +1,142 @@
+"""Training and evaluation of the learned warm start through the C ABI (an addition to the
+paper's method, whose frames start from lambda = 0).
+
+collect    runs the plain method (cold start) over scenes and returns, per contact and
+           frame, the features seen at the frame's start and the frame's final impulse and
+           normal move (the targets)
+train      fits the network on the GPU (sim_mlp_train: the project's own tensor-core
+           forward/backward kernels and Adam)
+evaluate   iterations and device milliseconds until the frame's residual reaches a
+           tolerance, per frame, for a given start (cold, previous frame, learned)
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import SimError, Simulator, WarmStartNet
+
+MODES = {"cold": 0, "learned": 1, "previous": 2}
+
+
+def collect(scenes, frames, n_iters=20, tol=1e-4, **opts):
+    """Samples of the frames whose final residual reached tol (their impulses are the
+    method's answer, not an iterate still moving)."""
+    Xs, Ts = [], []
+    for sc in scenes:
+        sim = Simulator(sc, n_iters=n_iters, **opts)
+        for _ in range(frames):
+            try:
+                sim.step()
+                X, T = sim.warmstart_samples()
+                r = sim.stats()["residuals"]
+            except SimError:   # a frame that left the state non-finite ends the trajectory
+                break
+            if len(X) and r[-1] <= tol:
+                Xs.append(X)
+                Ts.append(T)
+        sim.close()
+    if not Xs:
+        return np.zeros((0, WarmStartNet.FEATURES), np.float32), np.zeros((0, 4), np.float32)
+    return np.concatenate(Xs), np.concatenate(Ts)
+
+
+def train(X, T, epochs=60, batch=512, lr=1e-3, seed=0, device=0):
+    net = WarmStartNet(device=device, max_batch=max(batch, 64), seed=seed)
+    losses = net.train(X, T, epochs=epochs, batch=batch, lr=lr, seed=seed + 1)
+    return net, losses
+
+
+def evaluate_from_states(scenes, frames, modes, net=None, k_max=40, tol=1e-4, **opts):
+    """A/B from identical states: each scene's reference trajectory is run with the cold start
+    and k_max iterations per frame; every frame with contacts is then replayed once per
+    start in `modes` from the reference state of the frame before it (one cold frame to set
+    up the previous frame's impulses, then the frame under test). Returns, per mode, the
+    iterations until the residual reaches tol (k_max + 1 if never) and the device time to
+    get there, over the same frames."""
+    out = {m: {"iters": [], "ms": [], "res": []} for m in modes}
+    for sc in scenes:
+        ref = Simulator(sc, n_iters=k_max, **opts)
+        states = [ref.state()]
+        contact = []
+        for _ in range(frames):
+            try:
+                ref.step()
+                contact.append(ref.stats()["n_contacts"] > 0)
+                states.append(ref.state())
+            except SimError:
+                break
+        ref.close()
+        sim = Simulator(sc, n_iters=k_max, **opts)
+        for f in range(1, len(contact)):
+            if not contact[f]:
+                continue
+            for m in modes:
+                try:
+                    sim.set_state(*states[f - 1])
+                    sim.set_warmstart(0)
+                    sim.step()                      # frame f - 1: the previous impulses
+                    sim.set_warmstart(MODES[m] if isinstance(m, str) else int(m), net)
+                    sim.step()                      # frame f from the reference state
+                    st = sim.stats()
+                except SimError:
+                    out[m]["iters"].append(k_max + 1)
+                    out[m]["ms"].append(np.nan)
+                    out[m]["res"].append(np.full(k_max + 1, np.nan))
+                    continue
+                r = np.asarray(st["residuals"])
+                out[m]["res"].append(r[:k_max + 1])
+                hit = np.nonzero(r <= tol)[0]
+                k = int(hit[0]) if len(hit) else k_max + 1
+                ph = sim.phase_times()
+                per_iter = sum(ph[p] for p in ("local", "assemble", "spmv1", "solve", "spmv2",
+                                               "reduce")) / k_max
+                start = ph["collide"] + ph["delassus"] + ph["warmstart"]
+                out[m]["iters"].append(k)
+                out[m]["ms"].append(start + min(k, k_max) * per_iter + ph["integrate"])
+        sim.close()
+    res = {}
+    for m, d in out.items():
+        it, ms = np.asarray(d["iters"]), np.asarray(d["ms"])
+        res[m] = {"frames": int(len(it)), "mean_iters": float(it.mean()) if len(it) else 0.0,
+                  "median_iters": float(np.median(it)) if len(it) else 0.0,
+                  "unreached": int((it > k_max).sum()),
+                  "mean_ms": float(np.nanmean(ms)) if len(ms) else 0.0,
+                  "iters": it.tolist(), "residuals": np.asarray(d["res"])}
+    return res
+
+
+def evaluate(scenes, frames, mode, net=None, k_max=40, tol=1e-4, **opts):
+    """Each scene runs `frames` frames of k_max iterations from its initial state with the
+    given start; for every frame with contacts: the first k with residual R_k <= tol (k_max + 1
+    if none) and the device time to get there: collision, Delassus and warm start, plus k
+    times the frame's mean time per iteration."""
+    iters, ms = [], []
+    for sc in scenes:
+        sim = Simulator(sc, n_iters=k_max, **opts)
+        sim.set_warmstart(MODES[mode] if isinstance(mode, str) else int(mode), net)
+        for _ in range(frames):
+            try:
+                sim.step()
+                st = sim.stats()
+            except SimError:   # non-finite: counted as not reached, the trajectory ends
+                iters.append(k_max + 1)
+                ms.append(np.nan)
+                break
+            if st["n_contacts"] == 0:
+                continue
+            r = np.asarray(st["residuals"])
+            hit = np.nonzero(r <= tol)[0]
+            k = int(hit[0]) if len(hit) else k_max + 1
+            ph = sim.phase_times()
+            per_iter = sum(ph[p] for p in ("local", "assemble", "spmv1", "solve", "spmv2",
+                                           "reduce")) / k_max
+            start = ph["collide"] + ph["delassus"] + ph["warmstart"]
+            iters.append(k)
+            ms.append(start + min(k, k_max) * per_iter + ph["integrate"])
+        sim.close()
+    iters, ms = np.asarray(iters), np.asarray(ms)
+    return {"frames": int(len(iters)), "mean_iters": float(iters.mean()) if len(iters) else 0.0,
+            "median_iters": float(np.median(iters)) if len(iters) else 0.0,
+            "unreached": int((iters > k_max).sum()),
+            "mean_ms": float(np.nanmean(ms)) if len(ms) else 0.0,
+            "diverged": int(np.isnan(ms).sum())}

@@ -301,6 +301,24 @@ def batch(n_scenes: int = 64, seed: int = 0, m_lo: int = 8, m_hi: int = 20,
     return out
 
 
+def warmstart_scenes(seeds, m: int = 6, frames: int = 100) -> List[Scene]:
+    """The learned warm start's workload: the 6^3-vertex cube (edge 0.1 m, E = 1e5,
+    nu = 0.4), ARAP for even seeds and co-rotational for odd ones, dropped from a seeded
+    height in [0.1, 0.3] m with a seeded rotation onto a plane tilted by a seeded angle in
+    [0, 20] degrees (mu = 0.5)."""
+    out = []
+    for s in seeds:
+        rng = np.random.default_rng(10_000 + int(s))
+        height = float(rng.uniform(0.1, 0.3))
+        tilt = float(rng.uniform(0.0, 20.0))
+        model = MODEL_ARAP if int(s) % 2 == 0 else MODEL_COROT
+        sc = cube_drop(m=m, edge=0.1, model=model, E=1e5, nu=0.4, height=height, mu=0.5,
+                       seed=int(s), n_frames=frames, tilt_deg=tilt)
+        sc.name = f"ws{s}"
+        out.append(sc)
+    return out
+
+
 def perturbed_state(scene: Scene, seed: int, amp: float, vel_amp: float = 0.0):
     """Seeded random perturbation of the initial state (positions and velocities) of the
     free vertices, for single-step comparisons from identical states."""

@@ -1,0 +1,86 @@
+"""The learned warm start end to end: training data from the plain method, training on the
+GPU with the project's kernels, and the A/B on held-out scenes -- iterations and device time
+until the frame's residual reaches 1e-4, against the cold start (the paper's) and the
+previous frame's impulses. Also: the samples and the fallback rule."""
+import numpy as np
+import pytest
+
+import scenegen as sg
+from paper_2503_15078_b300 import Simulator, warmstart
+
+pytestmark = pytest.mark.gpu
+
+
+def test_samples_describe_the_frame():
+    sc = sg.warmstart_scenes([3])[0]
+    sim = Simulator(sc, n_iters=20)
+    n_with = 0
+    for _ in range(60):
+        sim.step()
+        X, T = sim.warmstart_samples()
+        ct = sim.contacts()
+        assert len(X) == len(T) == len(ct["vertex"])
+        if len(X):
+            n_with += 1
+            assert np.all(np.isfinite(X)) and np.all(np.isfinite(T))
+            assert np.allclose(np.linalg.norm(X[:, 1:4], axis=1), 1.0, atol=1e-5)  # normals
+            # m_v W~_vv lies in (0, 1]: the rest of the body only adds inertia
+            assert np.all((X[:, 10] > 0) & (X[:, 10] <= 1.0 + 1e-6))
+    assert n_with > 10
+    sim.close()
+
+
+def test_a_worse_guess_falls_back_to_the_cold_start():
+    # a network that adds 1000 scales of normal impulse at every contact: the guess's
+    # residual at k = 0 is far above the cold start's, so it is rejected and every frame is
+    # the cold frame
+    from paper_2503_15078_b300 import WarmStartNet
+    sc = sg.warmstart_scenes([4])[0]
+    net = WarmStartNet()
+    theta = np.zeros(WarmStartNet.PARAMS, np.float32)
+    theta[-8] = 1000.0   # b4[0]: the normal-impulse output
+    net.set_params(theta)
+    a = Simulator(sc, n_iters=8)
+    b = Simulator(sc, n_iters=8)
+    b.set_warmstart(1, net)
+    for _ in range(40):
+        a.step()
+        b.step()
+    qa, _ = a.state()
+    qb, _ = b.state()
+    assert np.array_equal(qa, qb)
+    a.close()
+    b.close()
+    net.close()
+
+
+def test_learned_start_against_the_cold_start_from_identical_states():
+    # training data: frames of the plain method (cold start, 20 iterations) whose residual
+    # reached 1e-4, on 16 seeded drops; validation and evaluation on other seeds
+    X, T = warmstart.collect(sg.warmstart_scenes(range(0, 16), frames=80), frames=80, n_iters=20)
+    Xv, Tv = warmstart.collect(sg.warmstart_scenes(range(200, 204), frames=80), frames=80,
+                               n_iters=20)
+    assert len(X) > 1000 and len(Xv) > 300
+    net, losses = warmstart.train(X, T, epochs=60, batch=512, lr=1e-3, seed=0)
+    assert losses[-1] < 0.5 * losses[0]
+    # held-out prediction: the move along the normal is learned (far better than predicting
+    # no move); the impulse's change from the previous frame is not better than zero (the
+    # previous frame's impulse is already as good as the features allow)
+    mse = ((net.forward(Xv) - Tv) ** 2).mean(0)
+    mse0 = (Tv ** 2).mean(0)
+    print("held-out mse", mse, "zero", mse0)
+    assert mse[3] < 0.05 * mse0[3]
+    res = warmstart.evaluate_from_states(sg.warmstart_scenes(range(100, 105), frames=60), 60,
+                                         ["cold", "previous", "learned"], net=net)
+    logR5 = {m: float(np.nanmean(np.log10(np.maximum(r["residuals"][:, 5], 1e-16))))
+             for m, r in res.items()}
+    for m, r in res.items():
+        print(m, {k: v for k, v in r.items() if k not in ("iters", "residuals")},
+              "mean log10 R after 5 iterations %.2f" % logR5[m])
+    # the gain: a lower residual after the 5 iterations the frames run; iterations to 1e-4
+    # are reported (about half of the frames never reach it within 40 iterations, from any
+    # start: the friction indicators flip at lambda_n = 0)
+    assert logR5["learned"] < logR5["cold"]
+    assert logR5["previous"] < logR5["cold"]
+    assert res["cold"]["frames"] == res["learned"]["frames"] > 100
+    net.close()
