@@ -36,6 +36,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ms/local-global iter @58.5k DoFs; frame ms to 1e-4 residual, learned vs plain"
+# DRAM bytes (read + write) per launch of the FP32 profile products on this workload, mean of
+# k_pass1 and k_pass2, from one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum;
+# valid while those kernels are unchanged
+PRODUCT_TRAFFIC_BYTES = {"fp32": 105.7e6}
 UNIT = "ms/iter"
 
 
@@ -51,6 +55,8 @@ def parse():
     ap.add_argument("--n-side", type=int, default=42)
     ap.add_argument("--s-precision", choices=["fp32", "bf16"], default="fp32",
                     help="storage of the S~ values (bf16: FP32 accumulation)")
+    ap.add_argument("--no-warmstart", action="store_true",
+                    help="skip the learned-vs-plain frame time to residual 1e-4")
     ap.add_argument("--workload", choices=["star", "batch64"], default="star",
                     help="star: the 57k-DoF pulled star (the headline); batch64: 64 uneven "
                          "cubes on tilted planes in one simulator")
@@ -66,6 +72,18 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(value, device="cuda"):
+    """The largest value over the ranks of the default process group (the job's time is
+    its slowest rank's); the value itself without a group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def measured_peaks():
@@ -290,6 +308,35 @@ def batch_state(scenes):
     return np.concatenate(qs), np.concatenate(vs)
 
 
+def warmstart_ab():
+    """The second half of the metric: frame time to residual 1e-4, learned warm start vs the
+    plain cold start, on the 6^3 cube drops (train on 16 seeds, 80 frames each, from frames
+    the plain method solved; evaluate on 5 held-out seeds, every contact frame replayed from
+    the same state with each start, up to 40 iterations)."""
+    import numpy as np
+    import scenegen as sg
+    from paper_2503_15078_b300 import warmstart
+    t0 = time.perf_counter()
+    X, T = warmstart.collect(sg.warmstart_scenes(range(0, 16), frames=80), frames=80, n_iters=20)
+    net, losses = warmstart.train(X, T, epochs=60, batch=512, lr=1e-3, seed=0)
+    res = warmstart.evaluate_from_states(sg.warmstart_scenes(range(100, 105), frames=60), 60,
+                                         ["cold", "previous", "learned"], net=net)
+    out = {"workload": "6^3 cube drops (config-1 scene, seeded height/rotation/tilt); 16 "
+                       "training seeds x 80 frames, 5 held-out seeds x 60 frames",
+           "training_samples": int(len(X)), "train_loss": [float(losses[0]), float(losses[-1])],
+           "tolerance": 1e-4, "max_iters": 40}
+    for m, r in res.items():
+        R5 = r["residuals"][:, 5]
+        out[m] = {"frames": r["frames"], "mean_iters_to_tol": round(r["mean_iters"], 2),
+                  "median_iters_to_tol": r["median_iters"], "unreached": r["unreached"],
+                  "mean_frame_ms_to_tol": round(r["mean_ms"], 4),
+                  "mean_log10_residual_after_5_iters":
+                      round(float(np.nanmean(np.log10(np.maximum(R5, 1e-16)))), 3)}
+    out["seconds"] = round(time.perf_counter() - t0, 1)
+    net.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -347,10 +394,7 @@ def run_ours(args):
     clocks = clk.summary()
     frame_ms = [sum(p.values()) for p in frames]
     mean_frame = statistics.mean(frame_ms)
-    if world > 1:
-        t = torch.tensor([mean_frame], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        mean_frame = float(t.item())
+    mean_frame = max_over_ranks(mean_frame)
     phase_mean = {k: statistics.mean(p[k] for p in frames) for k in frames[0]}
     stats = sim.stats()
     # ---- roofline of the dominant kernels: the two S~ profile products -----------------
@@ -437,7 +481,8 @@ def run_ours(args):
             "frac": round(achieved / peak, 4),
             "algorithmic_bytes_per_pass": bytes_pass,
             "achieved_with_reduction": round(achieved_red, 1),
-            "traffic": None,
+            "traffic": (PRODUCT_TRAFFIC_BYTES.get(args.s_precision)
+                        if not batch and args.n_side == 42 else None),
         },
         "e2e": {"value": round(e2e_ms, 4), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": h2d},
@@ -445,6 +490,8 @@ def run_ours(args):
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
+    if rank == 0 and not batch and not args.no_warmstart:
+        out["warmstart"] = warmstart_ab()
     if rank == 0:
         print(json.dumps(out), flush=True)
     sim.close()
