@@ -318,11 +318,14 @@ def warmstart_ab():
     from paper_2503_15078_b300 import warmstart
     t0 = time.perf_counter()
     X, T = warmstart.collect(sg.warmstart_scenes(range(0, 16), frames=80), frames=80, n_iters=20)
-    net, losses = warmstart.train(X, T, epochs=60, batch=512, lr=1e-3, seed=0)
+    Xv, Tv = warmstart.collect(sg.warmstart_scenes(range(200, 204), frames=80), frames=80,
+                               n_iters=20)
+    net, losses = warmstart.train(X, T, epochs=60, batch=512, lr=1e-3, seed=0, X_val=Xv, T_val=Tv)
     res = warmstart.evaluate_from_states(sg.warmstart_scenes(range(100, 105), frames=60), 60,
                                          ["cold", "previous", "learned"], net=net)
     out = {"workload": "6^3 cube drops (config-1 scene, seeded height/rotation/tilt); 16 "
-                       "training seeds x 80 frames, 5 held-out seeds x 60 frames",
+                       "training seeds x 80 frames, 4 validation seeds (output shrinkage), "
+                       "5 held-out seeds x 60 frames",
            "training_samples": int(len(X)), "train_loss": [float(losses[0]), float(losses[-1])],
            "tolerance": 1e-4, "max_iters": 40}
     for m, r in res.items():

@@ -13,6 +13,8 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "device.cuh"
 #include "fb.cuh"
 
@@ -240,26 +242,28 @@ __global__ void k_yc_len(DevSim d) {
 // Y rows (row-major over U) and Y columns (contact vertex major, bottom-up along the
 // ancestor path) gathered from the S~ profile.
 __global__ void k_y_gather(DevSim d) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, nwarps = (gridDim.x * blockDim.x) >> 5;
   const int nU = d.counters[kCntU];
-  if (warp >= nU) return;
   if (d.y_ptr[nU] > d.cap_y || d.yc_ptr[min(d.counters[kCntCv], d.cap)] > d.cap_y) {
-    if (warp == 0 && lane == 0) atomicOr(d.err, kErrYCapacity);
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(d.err, kErrYCapacity);
     return;
   }
-  const int a = d.u_list[warp];
-  const int clo = d.u_clo[warp], len = d.u_len[warp];
-  const float* srow = d.S + (d.rowbase[a] - d.lo[a]);
-  const int base = d.y_ptr[warp];
-  const int da = d.depth[a];
-  for (int k = lane; k < len; k += 32) {
-    const int c = clo + k;
-    const int v = d.cv_vert[c];
-    float val = srow[v];
-    d.y_val[base + k] = val;
-    const int pos = d.yc_ptr[c] + d.depth[v] - da;
-    d.yc_val[pos] = val;
-    d.yc_row[pos] = a;
+  // warps walk the rows of U with a grid stride (the grid is sized for the SMs)
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nU; w += nwarps) {
+    const int a = d.u_list[w];
+    const int clo = d.u_clo[w], len = d.u_len[w];
+    const float* srow = d.S + (d.rowbase[a] - d.lo[a]);
+    const int base = d.y_ptr[w];
+    const int da = d.depth[a];
+    for (int k = lane; k < len; k += 32) {
+      const int c = clo + k;
+      const int v = d.cv_vert[c];
+      const float val = srow[v];
+      d.y_val[base + k] = val;
+      const int pos = d.yc_ptr[c] + d.depth[v] - da;
+      d.yc_val[pos] = val;
+      d.yc_row[pos] = a;
+    }
   }
 }
 
@@ -575,73 +579,80 @@ __global__ void k_contact_eval(DevSim d, int k, int final_eval) {
 // partial sums are combined in a fixed order.
 constexpr int kYtzThreads = 128;
 __global__ void __launch_bounds__(kYtzThreads) k_ytz(DevSim d) {
-  const int c = blockIdx.x;
   const int ncv = min(d.counters[kCntCv], d.cap);
-  if (c >= ncv) return;
-  if (d.yc_ptr[ncv] > d.cap_y) return;
+  if (d.yc_ptr[ncv] > d.cap_y) return;   // uniform over the grid
   __shared__ float part[3][kYtzThreads / 32];
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-  const int k1 = d.yc_ptr[c + 1];
-#pragma unroll 4
-  for (int k = d.yc_ptr[c] + threadIdx.x; k < k1; k += kYtzThreads) {
-    const float y = d.yc_val[k];
-    const int a = d.yc_row[k];
-    s0 += y * d.zvec[a];
-    s1 += y * d.zvec[d.n_pad + a];
-    s2 += y * d.zvec[2 * d.n_pad + a];
-  }
-  s0 = warp_sum(s0);
-  s1 = warp_sum(s1);
-  s2 = warp_sum(s2);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) {
-    part[0][wid] = s0;
-    part[1][wid] = s1;
-    part[2][wid] = s2;
-  }
-  __syncthreads();
-  if (threadIdx.x >= 32) return;
-  s0 = s1 = s2 = 0.f;
-  for (int w = 0; w < kYtzThreads / 32; ++w) {
-    s0 += part[0][w];
-    s1 += part[1][w];
-    s2 += part[2][w];
-  }
   const double ih2 = 1.0 / (d.h * d.h);
-  const int j0 = d.cv_first[c], j1 = min(j0 + d.cv_nct[c], d.cap);
-  for (int j = j0 + lane; j < j1; j += 32) {
-    for (int r = 0; r < 3; ++r) {
-      const float* Dr = d.ct_Df + 9 * j + 3 * r;
-      float jag = d.ct_omega[3 * j + r] * (Dr[0] * s0 + Dr[1] * s1 + Dr[2] * s2);
-      d.ct_rhs[3 * j + r] = (float)((d.ct_hv[3 * j + r] - (double)jag) * ih2);
+  // CTAs walk the contact vertices with a grid stride (the grid is sized for the SMs, not
+  // for the capacity); every thread of a CTA runs the same iterations
+  for (int c = blockIdx.x; c < ncv; c += gridDim.x) {
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    const int k1 = d.yc_ptr[c + 1];
+#pragma unroll 4
+    for (int k = d.yc_ptr[c] + threadIdx.x; k < k1; k += kYtzThreads) {
+      const float y = d.yc_val[k];
+      const int a = d.yc_row[k];
+      s0 += y * d.zvec[a];
+      s1 += y * d.zvec[d.n_pad + a];
+      s2 += y * d.zvec[2 * d.n_pad + a];
     }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if (lane == 0) {
+      part[0][wid] = s0;
+      part[1][wid] = s1;
+      part[2][wid] = s2;
+    }
+    __syncthreads();
+    if (wid == 0) {
+      s0 = s1 = s2 = 0.f;
+      for (int w = 0; w < kYtzThreads / 32; ++w) {
+        s0 += part[0][w];
+        s1 += part[1][w];
+        s2 += part[2][w];
+      }
+      const int j0 = d.cv_first[c], j1 = min(j0 + d.cv_nct[c], d.cap);
+      for (int j = j0 + lane; j < j1; j += 32) {
+        for (int r = 0; r < 3; ++r) {
+          const float* Dr = d.ct_Df + 9 * j + 3 * r;
+          const float jag = d.ct_omega[3 * j + r] * (Dr[0] * s0 + Dr[1] * s1 + Dr[2] * s2);
+          d.ct_rhs[3 * j + r] = (float)((d.ct_hv[3 * j + r] - (double)jag) * ih2);
+        }
+      }
+    }
+    __syncthreads();   // part[] is reused by the next contact vertex
   }
 }
 
 // y = z + h^2 Y u, in place on z (rows of U only)
 __global__ void k_yu(DevSim d) {
-  const int idx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, nwarps = (gridDim.x * blockDim.x) >> 5;
   const int nU = d.counters[kCntU];
-  if (idx >= nU || d.y_ptr[nU] > d.cap_y) return;
-  const int clo = d.u_clo[idx], len = d.u_len[idx], base = d.y_ptr[idx];
-  float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+  if (d.y_ptr[nU] > d.cap_y) return;
+  const float h2 = (float)(d.h * d.h);
+  // warps walk the rows of U with a grid stride (the grid is sized for the SMs)
+  for (int idx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; idx < nU; idx += nwarps) {
+    const int clo = d.u_clo[idx], len = d.u_len[idx], base = d.y_ptr[idx];
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f;
 #pragma unroll 4
-  for (int k = lane; k < len; k += 32) {
-    const float y = d.y_val[base + k];
-    const float* u = d.uvec + 3 * (clo + k);
-    t0 += y * u[0];
-    t1 += y * u[1];
-    t2 += y * u[2];
-  }
-  t0 = warp_sum(t0);
-  t1 = warp_sum(t1);
-  t2 = warp_sum(t2);
-  if (lane == 0) {
-    const int a = d.u_list[idx];
-    const float h2 = (float)(d.h * d.h);
-    d.zvec[a] += h2 * t0;
-    d.zvec[d.n_pad + a] += h2 * t1;
-    d.zvec[2 * d.n_pad + a] += h2 * t2;
+    for (int k = lane; k < len; k += 32) {
+      const float y = d.y_val[base + k];
+      const float* u = d.uvec + 3 * (clo + k);
+      t0 += y * u[0];
+      t1 += y * u[1];
+      t2 += y * u[2];
+    }
+    t0 = warp_sum(t0);
+    t1 = warp_sum(t1);
+    t2 = warp_sum(t2);
+    if (lane == 0) {
+      const int a = d.u_list[idx];
+      d.zvec[a] += h2 * t0;
+      d.zvec[d.n_pad + a] += h2 * t1;
+      d.zvec[2 * d.n_pad + a] += h2 * t2;
+    }
   }
 }
 
@@ -1034,7 +1045,7 @@ void launch_delassus(const DevSim& d, cudaStream_t s) {
   launch_scan(d.u_len, d.y_ptr, 0, d.counters + kCntU, d.counters + kCntY, s);
   k_yc_len<<<(d.cap + 255) / 256, 256, 0, s>>>(d);
   launch_scan(d.yc_len, d.yc_ptr, 0, d.counters + kCntCv, d.counters + kCntYC, s);
-  k_y_gather<<<(d.n * 32 + 255) / 256, 256, 0, s>>>(d);
+  k_y_gather<<<std::min((d.n * 32 + 255) / 256, 8 * d.n_sm), 256, 0, s>>>(d);
   k_scene_ranges<<<1, 256, 0, s>>>(d);
   k_wt_blocks<<<(d.n / kWtKB + 1 + 127) / 128, 128, 0, s>>>(d);
   k_wt_items<<<d.wt_grid, kWtThreads, 0, s>>>(d);
@@ -1048,11 +1059,11 @@ void launch_contact_eval(const DevSim& d, cudaStream_t s, int k, bool final_eval
 }
 
 void launch_ytz(const DevSim& d, cudaStream_t s) {
-  k_ytz<<<d.cap, kYtzThreads, 0, s>>>(d);
+  k_ytz<<<std::min(d.cap, 8 * d.n_sm), kYtzThreads, 0, s>>>(d);
 }
 
 void launch_yu(const DevSim& d, cudaStream_t s) {
-  k_yu<<<(d.n * 32 + 255) / 256, 256, 0, s>>>(d);
+  k_yu<<<std::min((d.n * 32 + 255) / 256, 8 * d.n_sm), 256, 0, s>>>(d);
 }
 
 static size_t g_cr_smem = 0;

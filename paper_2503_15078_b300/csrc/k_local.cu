@@ -319,35 +319,45 @@ __global__ void __launch_bounds__(128) k_local(DevSim d) {
 
 // b_i - (A q_ref)_i + h^2 (J^T lambda)_i for every free vertex i, written as the FP32 SoA
 // vector g of the first profile product.
+// b_i = M_i (s~_i - q_ref_i) + sum of the vertex's element contributions + h^2 (contact
+// forces), for the free vertex i. kRhsLanes lanes share a vertex: each sums a strided part of
+// its incidence list, the parts meet in a fixed shuffle tree (deterministic), so the
+// dependent gathers of one thread shrink by that factor.
+constexpr int kRhsLanes = 8;
 __global__ void k_rhs(DevSim d) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= d.n_pad) return;
-  if (i >= d.n) {
-    d.gvec[i] = 0.f;
-    d.gvec[d.n_pad + i] = 0.f;
-    d.gvec[2 * d.n_pad + i] = 0.f;
-    return;
-  }
-  double m = d.mass[i];
-  double b[3];
-#pragma unroll
-  for (int r = 0; r < 3; ++r) b[r] = m * (d.s_tilde[3 * i + r] - d.q_ref[3 * i + r]);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = t / kRhsLanes, sub = t % kRhsLanes;
+  // the grid is exactly n_pad * kRhsLanes threads (n_pad is a multiple of 256), so every
+  // lane of a warp reaches the shuffles below
   float e[3] = {0.f, 0.f, 0.f};
-  for (int k = d.inc_ptr[i]; k < d.inc_ptr[i + 1]; ++k) {
-    float4 c = d.contrib[d.inc_idx[k]];
+  const int k0 = i < d.n ? d.inc_ptr[i] : 0, k1 = i < d.n ? d.inc_ptr[i + 1] : 0;
+  for (int k = k0 + sub; k < k1; k += kRhsLanes) {
+    const float4 c = d.contrib[d.inc_idx[k]];
     e[0] += c.x;
     e[1] += c.y;
     e[2] += c.z;
   }
+  const unsigned mask = 0xffffffffu;
+#pragma unroll
+  for (int o = kRhsLanes / 2; o > 0; o >>= 1)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) e[r] += __shfl_xor_sync(mask, e[r], o, kRhsLanes);
+  if (sub != 0) return;
+  if (i >= d.n) {
+    d.gvec[i] = d.gvec[d.n_pad + i] = d.gvec[2 * d.n_pad + i] = 0.f;
+    return;
+  }
+  const double m = d.mass[i];
+  double b[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) b[r] = m * (d.s_tilde[3 * i + r] - d.q_ref[3 * i + r]);
   const double h2 = d.h * d.h;
-  int nc = d.ct_cnt[i];
+  const int nc = d.ct_cnt[i];
   if (nc > 0) {
-    int j0 = d.ct_off[i];
-    int cap = d.cap;
-    for (int j = j0; j < j0 + nc && j < cap; ++j) {
+    const int j0 = d.ct_off[i];
+    for (int j = j0; j < j0 + nc && j < d.cap; ++j)
 #pragma unroll
       for (int r = 0; r < 3; ++r) b[r] += h2 * d.ct_force[3 * j + r];
-    }
   }
 #pragma unroll
   for (int r = 0; r < 3; ++r) d.gvec[r * d.n_pad + i] = (float)(b[r] + (double)e[r]);
@@ -385,7 +395,7 @@ void launch_local(const DevSim& d, cudaStream_t s, bool debug_p) {
 }
 
 void launch_rhs(const DevSim& d, cudaStream_t s) {
-  k_rhs<<<(d.n_pad + 255) / 256, 256, 0, s>>>(d);
+  k_rhs<<<(d.n_pad * kRhsLanes + 255) / 256, 256, 0, s>>>(d);
 }
 
 void launch_integrate(const DevSim& d, cudaStream_t s) {

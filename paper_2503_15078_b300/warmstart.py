@@ -40,9 +40,28 @@ def collect(scenes, frames, n_iters=20, tol=1e-4, **opts):
     return np.concatenate(Xs), np.concatenate(Ts)
 
 
-def train(X, T, epochs=60, batch=512, lr=1e-3, seed=0, device=0):
+SHRINK = (0.0, 0.25, 0.5, 0.75, 1.0)
+
+
+def train(X, T, epochs=60, batch=512, lr=1e-3, seed=0, device=0, X_val=None, T_val=None):
+    """Fit the network; with a validation set, then scale each output (its row of the last
+    layer) by the factor in SHRINK with the lowest validation error, so that an output with
+    no skill on held-out frames (better left at zero: no change from the previous frame's
+    impulse) is switched off. Returns the network and the per-epoch losses."""
     net = WarmStartNet(device=device, max_batch=max(batch, 64), seed=seed)
     losses = net.train(X, T, epochs=epochs, batch=batch, lr=lr, seed=seed + 1)
+    if X_val is not None and len(X_val):
+        Y = net.forward(X_val)
+        theta = net.params()
+        H, OUT = 128, 8
+        w4 = theta[-OUT - H * OUT:-OUT].reshape(H, OUT)
+        b4 = theta[-OUT:]
+        for c in range(Y.shape[1]):
+            err = [float(np.mean((a * Y[:, c] - T_val[:, c]) ** 2)) for a in SHRINK]
+            a = SHRINK[int(np.argmin(err))]
+            w4[:, c] *= a
+            b4[c] *= a
+        net.set_params(theta)
     return net, losses
 
 
