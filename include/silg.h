@@ -139,8 +139,11 @@ typedef struct {
  * (Tab. 3: Schur., Local, Global, Assem., Cst. Solve, Corr.). */
 enum { SIM_PHASE_COLLIDE = 0,   /* prediction and collision detection (App. A.1)         */
        SIM_PHASE_DELASSUS = 1,  /* W~ = Y^T Y and preconditioner (Eqs. 27-28)            */
-       SIM_PHASE_LOCAL = 2,     /* local step per tetrahedron (Eq. 5)                     */
-       SIM_PHASE_ASSEMBLE = 3,  /* FB evaluation and right-hand side (Eq. 19)            */
+       SIM_PHASE_LOCAL = 2,     /* local step per tetrahedron (Eq. 5), beside the FB
+                                   evaluation of the contacts (two graph branches; with a
+                                   cold start the first local step runs beside collision
+                                   and Delassus work)                                     */
+       SIM_PHASE_ASSEMBLE = 3,  /* right-hand side (Eq. 19)                                */
        SIM_PHASE_SPMV1 = 4,     /* z = S g (first profile product, Eq. 8): the product     */
        SIM_PHASE_SOLVE = 5,     /* J A^-1 g, conjugate residual, S J^T dlambda (Alg. 4)   */
        SIM_PHASE_SPMV2 = 6,     /* q = S^T y (second profile product): the product         */

@@ -35,6 +35,8 @@ struct sim_s {
   DevSim d{};
   int device = 0;
   cudaStream_t work = nullptr;    // private stream: captures and component calls
+  cudaStream_t aux = nullptr;     // second branch of the frame graph (captured from work)
+  std::vector<cudaEvent_t> fj;    // fork/join events of the frame graph's branches
   cudaStream_t launch = nullptr;  // where frames run (caller stream or work)
   int cluster = 1;
   size_t cr_smem = 0;
@@ -74,6 +76,8 @@ struct sim_s {
     }
     for (void* p : allocs) cudaFree(p);
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : fj) cudaEventDestroy(e);
+    if (aux) cudaStreamDestroy(aux);
     if (work) cudaStreamDestroy(work);
   }
 };
@@ -121,11 +125,30 @@ void enqueue_frame(sim_s* s, int K, cudaStream_t st) {
   const DevSim& d = s->d;
   // external event-record nodes: observable from the host after each graph launch
   auto mark = [&](int i) { cudaEventRecordWithFlags(s->ev[i], st, cudaEventRecordExternal); };
+  // two branches of the graph: work forked onto the aux stream and joined back
+  int n_fj = 0;
+  auto fork = [&]() {
+    cudaEventRecord(s->fj[n_fj], st);
+    cudaStreamWaitEvent(s->aux, s->fj[n_fj], 0);
+    ++n_fj;
+  };
+  auto join = [&]() {
+    cudaEventRecord(s->fj[n_fj], s->aux);
+    cudaStreamWaitEvent(st, s->fj[n_fj], 0);
+    ++n_fj;
+  };
   mark(0);
   cudaMemsetAsync(d.resid, 0, sizeof(double) * (silg::kMaxIters + 1), st);
   cudaMemsetAsync(d.resid_scene, 0, sizeof(double) * (silg::kMaxIters + 1) * d.n_scenes, st);
   cudaMemsetAsync(d.max_pen, 0, sizeof(double), st);
   silg::launch_frame_begin(d, st);
+  // the first local step needs only the prediction: with a cold start it runs beside the
+  // collision and Delassus work (a warm start moves q^0, so then it waits)
+  const bool early_local = s->has_obstacles && d.ws_mode == 0;
+  if (early_local) {
+    fork();
+    silg::launch_local(d, s->aux, false);
+  }
   if (s->has_obstacles) silg::launch_collide(d, st);
   mark(1);
   if (s->has_obstacles) silg::launch_delassus(d, st);
@@ -137,9 +160,20 @@ void enqueue_frame(sim_s* s, int K, cudaStream_t st) {
   mark(3);
   for (int k = 0; k < K; ++k) {
     const int e = 4 + kMarksPerIter * k;
-    silg::launch_local(d, st, false);
+    // the local step and the contact evaluation depend on the same iterate only: two
+    // branches, joined before the right-hand side that needs both
+    if (k == 0 && early_local) {
+      silg::launch_contact_eval(d, st, k, false);
+      join();
+    } else if (s->has_obstacles) {
+      fork();
+      silg::launch_contact_eval(d, s->aux, k, false);
+      silg::launch_local(d, st, false);
+      join();
+    } else {
+      silg::launch_local(d, st, false);
+    }
     mark(e);
-    if (s->has_obstacles) silg::launch_contact_eval(d, st, k, false);
     silg::launch_rhs(d, st);
     mark(e + 1);
     silg::launch_pass1(d, st);
@@ -743,7 +777,12 @@ int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_opt
     if (o->device < 0 || o->device >= ndev) return SIM_EINVAL;
     s->device = o->device;
     if (cudaSetDevice(s->device) != cudaSuccess) return SIM_ECUDA;
-    if (cudaStreamCreateWithFlags(&s->work, cudaStreamNonBlocking) != cudaSuccess) return SIM_ECUDA;
+    if (cudaStreamCreateWithFlags(&s->work, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking) != cudaSuccess)
+      return SIM_ECUDA;
+    s->fj.resize(2 * silg::kMaxIters + 4);
+    for (auto& e : s->fj)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return SIM_ECUDA;
     s->launch = o->cuda_stream ? static_cast<cudaStream_t>(o->cuda_stream) : s->work;
     s->n_iters_default = o->n_iters > 0 ? o->n_iters : 5;
     return create_device(s, sd, o);
