@@ -114,7 +114,8 @@ typedef struct {
   int32_t tuned;               /* 1 if the autotuner ran                                   */
   int32_t candidates;          /* configurations timed per product                        */
   int32_t pass1_ctas, pass2_ctas;       /* CTAs of each product's launch                  */
-  int32_t pass1_unroll, pass2_unroll;   /* 1: the format's tiles in flight per warp, 0: half */
+  int32_t pass1_unroll, pass2_unroll;   /* tiles in flight per warp: 1 the format's default,
+                                           0 half, 2 twice (one resident CTA per SM)      */
   double pass1_balance, pass2_balance;  /* cost of an empty tile position relative to a
                                            stored value when the tiles are split over CTAs */
   double pass1_us, pass2_us;            /* median launch time of the choice (tuned only)   */

@@ -133,7 +133,7 @@ struct DevSim {
   const int* s1_col_slot;   // per pass-1 tile: position of its column tile in that list
   int s1_max_cols;
   int s1_grid, s2_grid, n_seg1, n_seg2;
-  int s1_unroll, s2_unroll;  // 1: the value format's tiles in flight per warp, 0: half
+  int s1_unroll, s2_unroll;  // tiles in flight per warp: 1 the format's, 0 half, 2 twice
   int n_sm;         // persistent-kernel grid size
   const float* zero;  // kTileW zeros: the load target of lanes outside a row's range
   float* p1_part;   // [n_seg1][3][kRowGroup]

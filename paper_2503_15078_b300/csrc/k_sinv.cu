@@ -68,6 +68,12 @@ template <> struct Fmt<unsigned short> {
   }
 };
 
+// CTAs per SM the products are built for: two with the format's tiles in flight (or half),
+// one with twice as many (their registers hold twice the loads in flight)
+template <class T, int U> struct PassOcc {
+  static constexpr int kMinBlocks = U > Fmt<T>::kUnroll ? 1 : 2;
+};
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -120,7 +126,7 @@ __device__ __forceinline__ LaneMeta fetch_meta(const DevSim& d, const int2* tile
 // z partials: one slot per run of tiles of one row group -> p1_part[slot][comp][row].
 // U: tiles in flight per warp (the format's default, or half of it).
 template <class T, int U>
-__global__ void __launch_bounds__(256, 2) k_pass1(DevSim d) {
+__global__ void __launch_bounds__(256, PassOcc<T, U>::kMinBlocks) k_pass1(DevSim d) {
   using F = Fmt<T>;
   static_assert(U * kRowsPerWarp <= 32, "one metadata entry per lane");
   const T* S = F::vals(d);
@@ -240,7 +246,7 @@ constexpr size_t kP2Smem = sizeof(float) * kWarps * 3 * TW;
 
 // x partials: one slot per run of tiles of one column tile -> p2_part[slot][comp][column]
 template <class T, int U>
-__global__ void __launch_bounds__(256, 2) k_pass2(DevSim d) {
+__global__ void __launch_bounds__(256, PassOcc<T, U>::kMinBlocks) k_pass2(DevSim d) {
   using F = Fmt<T>;
   static_assert(U * kRowsPerWarp <= 32, "one metadata entry per lane");
   const T* S = F::vals(d);
@@ -406,23 +412,26 @@ int sinv_setup() {
   // pass 1 stages the g slices of a CTA's column tiles: up to 3 KB per tile of its range
   const int most = kMaxStagedCols * 3 * TW * (int)sizeof(float);
   const void* fns[] = {(const void*)k_pass1<float, 2>, (const void*)k_pass1<float, 1>,
-                       (const void*)k_pass1<unsigned short, 4>,
-                       (const void*)k_pass1<unsigned short, 2>};
+                       (const void*)k_pass1<float, 4>, (const void*)k_pass1<unsigned short, 4>,
+                       (const void*)k_pass1<unsigned short, 2>,
+                       (const void*)k_pass1<unsigned short, 8>};
   for (const void* f : fns)
     if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, most) != cudaSuccess)
       return SIM_ECUDA;
   return SIM_OK;
 }
 
-// unroll: 1 = the format's default tiles in flight, 0 = half of it
+// unroll: 1 = the format's default tiles in flight, 0 = half of it, 2 = twice
 void launch_pass1(const DevSim& d, cudaStream_t s) {
   const size_t smem = (size_t)d.s1_max_cols * 3 * TW * sizeof(float);
   const int g = d.s1_grid;
   if (d.s_bf16) {
-    if (d.s1_unroll) k_pass1<unsigned short, 4><<<g, 256, smem, s>>>(d);
+    if (d.s1_unroll == 2) k_pass1<unsigned short, 8><<<g, 256, smem, s>>>(d);
+    else if (d.s1_unroll == 1) k_pass1<unsigned short, 4><<<g, 256, smem, s>>>(d);
     else k_pass1<unsigned short, 2><<<g, 256, smem, s>>>(d);
   } else {
-    if (d.s1_unroll) k_pass1<float, 2><<<g, 256, smem, s>>>(d);
+    if (d.s1_unroll == 2) k_pass1<float, 4><<<g, 256, smem, s>>>(d);
+    else if (d.s1_unroll == 1) k_pass1<float, 2><<<g, 256, smem, s>>>(d);
     else k_pass1<float, 1><<<g, 256, smem, s>>>(d);
   }
 }
@@ -434,10 +443,12 @@ void launch_reduce1(const DevSim& d, cudaStream_t s) {
 void launch_pass2(const DevSim& d, cudaStream_t s) {
   const int g = d.s2_grid;
   if (d.s_bf16) {
-    if (d.s2_unroll) k_pass2<unsigned short, 4><<<g, 256, kP2Smem, s>>>(d);
+    if (d.s2_unroll == 2) k_pass2<unsigned short, 8><<<g, 256, kP2Smem, s>>>(d);
+    else if (d.s2_unroll == 1) k_pass2<unsigned short, 4><<<g, 256, kP2Smem, s>>>(d);
     else k_pass2<unsigned short, 2><<<g, 256, kP2Smem, s>>>(d);
   } else {
-    if (d.s2_unroll) k_pass2<float, 2><<<g, 256, kP2Smem, s>>>(d);
+    if (d.s2_unroll == 2) k_pass2<float, 4><<<g, 256, kP2Smem, s>>>(d);
+    else if (d.s2_unroll == 1) k_pass2<float, 2><<<g, 256, kP2Smem, s>>>(d);
     else k_pass2<float, 1><<<g, 256, kP2Smem, s>>>(d);
   }
 }

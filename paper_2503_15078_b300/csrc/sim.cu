@@ -282,11 +282,12 @@ constexpr int kDefaultCtasPerSm = 2;
 constexpr double kDefaultBalance = 1.0;
 
 // The autotuner of the two profile products. For each product it times every candidate
-// launch configuration -- CTAs per SM (1 to 4; above 2 the grid runs in waves), the cost
-// of an empty tile position relative to a stored value in the balanced split (1: equal
-// tiles per CTA; 0.25: nearer equal bytes), and the tiles in flight per warp (the format's
-// default or half) -- on the simulator's own matrix with CUDA events (median of 5 launches
-// after 2 warm-up launches), and keeps the fastest.
+// launch configuration -- CTAs per SM (1 to 4; above the kernel's residency the grid runs
+// in waves), the cost of an empty tile position relative to a stored value in the balanced
+// split (1: equal tiles per CTA; 0.25: nearer equal bytes), and the tiles in flight per warp
+// (the format's default, half, or twice with one resident CTA per SM) -- on the simulator's
+// own matrix with CUDA events (median of 5 launches after 2 warm-up launches), and keeps
+// the fastest.
 int autotune_products(sim_s* s) {
   DevSim& d = s->d;
   cudaStream_t st = s->work;
@@ -306,7 +307,7 @@ int autotune_products(sim_s* s) {
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SIM_ECUDA;
   const int ctas[] = {1, 2, 3, 4};
   const double balance[] = {1.0, 0.25};
-  const int unroll[] = {1, 0};
+  const int unroll[] = {1, 0, 2};
   sim_tuning& T = s->tuning;
   T = sim_tuning{};
   int status = SIM_OK;

@@ -21,10 +21,10 @@ def test_autotuned_products_keep_parity_and_beat_or_match_the_default():
     sim = Simulator(sc, autotune=1)
     t = sim.tuning()
     print("tuning:", t)
-    assert t["tuned"] == 1 and t["candidates"] == 16
+    assert t["tuned"] == 1 and t["candidates"] == 24
     # the fixed configuration is one of the candidates, so the choice is never slower
     assert t["pass1_us"] <= t["pass1_default_us"] and t["pass2_us"] <= t["pass2_default_us"]
-    assert t["pass1_unroll"] in (0, 1) and t["pass2_unroll"] in (0, 1)
+    assert t["pass1_unroll"] in (0, 1, 2) and t["pass2_unroll"] in (0, 1, 2)
     b = np.random.default_rng(3).normal(size=(sc.n_verts, 3))
     f = FEM(sc)
     xr = np.zeros_like(b)
