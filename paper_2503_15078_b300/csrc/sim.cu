@@ -37,6 +37,8 @@ struct sim_s {
   cudaStream_t work = nullptr;    // private stream: captures and component calls
   cudaStream_t aux = nullptr;     // second branch of the frame graph (captured from work)
   std::vector<cudaEvent_t> fj;    // fork/join events of the frame graph's branches
+  double* pinned = nullptr;       // page-locked staging of q and v (2 x 3 n_verts) for the
+                                  // state accessors
   cudaStream_t launch = nullptr;  // where frames run (caller stream or work)
   int cluster = 1;
   size_t cr_smem = 0;
@@ -77,6 +79,7 @@ struct sim_s {
     for (void* p : allocs) cudaFree(p);
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     for (cudaEvent_t e : fj) cudaEventDestroy(e);
+    if (pinned) cudaFreeHost(pinned);
     if (aux) cudaStreamDestroy(aux);
     if (work) cudaStreamDestroy(work);
   }
@@ -781,6 +784,9 @@ int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_opt
     if (cudaStreamCreateWithFlags(&s->work, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking) != cudaSuccess)
       return SIM_ECUDA;
+    if (cudaMallocHost(&s->pinned, sizeof(double) * 6 * (size_t)std::max<long long>(1, nv_tot)) !=
+        cudaSuccess)
+      return SIM_ENOMEM;
     s->fj.resize(2 * silg::kMaxIters + 4);
     for (auto& e : s->fj)
       if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return SIM_ECUDA;
@@ -929,19 +935,21 @@ int sim_synchronize(sim_t* s) {
 int sim_get_state(sim_t* s, double* q, double* v) {
   if (!s) return SIM_EINVAL;
   cudaSetDevice(s->device);
+  const Plan& p = s->plan;
+  const size_t m = 3 * (size_t)p.n_verts;
+  // both copies on the frame's stream into page-locked staging, then one wait
+  if (q) cudaMemcpyAsync(s->pinned, s->d.q_t, m * sizeof(double), cudaMemcpyDeviceToHost, s->launch);
+  if (v) cudaMemcpyAsync(s->pinned + m, s->d.v_t, m * sizeof(double), cudaMemcpyDeviceToHost, s->launch);
   int st = sync_and_check(s);
   if (st == SIM_ECUDA) return st;
-  const Plan& p = s->plan;
-  const int n_all = p.n_verts;
-  std::vector<double> buf(3 * (size_t)n_all);
-  double* srcs[2] = {s->d.q_t, s->d.v_t};
+  const double* srcs[2] = {s->pinned, s->pinned + m};
   double* dsts[2] = {q, v};
   for (int k = 0; k < 2; ++k) {
     if (!dsts[k]) continue;
-    cudaError_t e = cudaMemcpy(buf.data(), srcs[k], buf.size() * sizeof(double), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_status(e);
-    for (int vv = 0; vv < n_all; ++vv)
-      for (int r = 0; r < 3; ++r) dsts[k][3 * (size_t)vv + r] = buf[3 * (size_t)p.internal[vv] + r];
+    for (int vv = 0; vv < p.n_verts; ++vv) {
+      const size_t iv = 3 * (size_t)p.internal[vv];
+      for (int r = 0; r < 3; ++r) dsts[k][3 * (size_t)vv + r] = srcs[k][iv + r];
+    }
   }
   return st;
 }
@@ -949,23 +957,28 @@ int sim_get_state(sim_t* s, double* q, double* v) {
 int sim_set_state(sim_t* s, const double* q, const double* v) {
   if (!s || !q || !v) return SIM_EINVAL;
   cudaSetDevice(s->device);
+  // the staging may still feed an earlier copy: wait for the frame's stream first
   cudaError_t e = cudaStreamSynchronize(s->launch);
   if (e != cudaSuccess) return cuda_status(e);
   const Plan& p = s->plan;
-  const int n_all = p.n_verts;
-  std::vector<double> bq(3 * (size_t)n_all), bv(3 * (size_t)n_all);
-  for (int vv = 0; vv < n_all; ++vv)
+  const size_t m = 3 * (size_t)p.n_verts;
+  double* bq = s->pinned;
+  double* bv = s->pinned + m;
+  for (int vv = 0; vv < p.n_verts; ++vv) {
+    const size_t iv = 3 * (size_t)p.internal[vv];
     for (int r = 0; r < 3; ++r) {
-      double a = q[3 * (size_t)vv + r], b = v[3 * (size_t)vv + r];
+      const double a = q[3 * (size_t)vv + r], b = v[3 * (size_t)vv + r];
       if (!std::isfinite(a) || !std::isfinite(b)) return SIM_EINVAL;
-      bq[3 * (size_t)p.internal[vv] + r] = a;
-      bv[3 * (size_t)p.internal[vv] + r] = b;
+      bq[iv + r] = a;
+      bv[iv + r] = b;
     }
-  e = cudaMemset(s->d.prev_valid, 0, sizeof(int) * s->d.n);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(s->d.q_t, bq.data(), bq.size() * sizeof(double), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(s->d.v_t, bv.data(), bv.size() * sizeof(double), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(s->d.err, 0, sizeof(int));
+  }
+  // in stream order before the next frame; the copies read the staging asynchronously
+  cudaMemsetAsync(s->d.prev_valid, 0, sizeof(int) * s->d.n, s->launch);
+  cudaMemcpyAsync(s->d.q_t, bq, m * sizeof(double), cudaMemcpyHostToDevice, s->launch);
+  cudaMemcpyAsync(s->d.v_t, bv, m * sizeof(double), cudaMemcpyHostToDevice, s->launch);
+  cudaMemsetAsync(s->d.err, 0, sizeof(int), s->launch);
+  e = cudaGetLastError();
   s->frame = 0;
   return cuda_status(e);
 }
