@@ -1,6 +1,7 @@
 """Contacts: detection and linearisation (App. A.1), Fischer-Burmeister complementarity
-functions and their derivatives (Eq. 14; App. B.2, Eqs. 52-57), split indicators (Eq. 24)
-and the conjugate-residual constraint solver (Sec. 6).
+functions and their derivatives (Eq. 14; App. B.2, Eqs. 52-57), the minimum-map
+alternative the paper compares against (App. B.1), split indicators (Eq. 24) and the
+conjugate-residual constraint solver (Sec. 6).
 
 TEST INFRASTRUCTURE (see the package docstring). Plain FP64.
 
@@ -119,6 +120,37 @@ def friction_terms(vel_f, lam_f, lam_n, mu, r_f):
     else:
         E = num / den * r_f
     return 1.0, E, vel_f + E * np.asarray(lam_f)
+
+
+# -- minimum map (App. B.1) ---------------------------------------------------------
+def minmap_normal_terms(delta_n, lam_n, r_n):
+    """phi_n = min(delta_n, r_n lambda_n) with its indicator and compliance (App. B.1): on
+    the gap branch (delta_n <= r_n lambda_n, ties included) phi_n = delta_n, omega_n = 1,
+    E_n = 0; on the impulse branch phi_n = r_n lambda_n, omega_n = 0, E_n = r_n."""
+    if delta_n <= r_n * lam_n:
+        return delta_n, 1.0, 0.0
+    return r_n * lam_n, 0.0, r_n
+
+
+def minmap_friction_terms(vel_f, lam_f, lam_n, mu, r_f):
+    """omega_f, the scalar compliance E_f and phi_f = omega_f delta_dot_f + E_f lambda_f of
+    the minimum-map friction rows (App. B.1). Inactive contacts (lambda_n <= 0, or mu = 0)
+    as in the Fischer-Burmeister form. Active ones, with s = mu lambda_n - |lambda_f|: stick
+    (E_f = 0) while |delta_dot_f| <= r_f s, else the slip compliance
+    (|delta_dot_f| - r_f s) / (mu lambda_n)."""
+    if lam_n <= 0.0 or mu <= 0.0:
+        return 0.0, 1.0, np.array(lam_f, dtype=np.float64)
+    a = float(np.linalg.norm(vel_f))
+    s = mu * lam_n - float(np.linalg.norm(lam_f))
+    if a <= r_f * s:
+        E = 0.0
+    else:
+        E = (a - r_f * s) / (mu * lam_n)
+    return 1.0, E, vel_f + E * np.asarray(lam_f)
+
+
+NCP_TERMS = {"fb": (normal_terms, friction_terms),
+             "minmap": (minmap_normal_terms, minmap_friction_terms)}
 
 
 # -- conjugate residual --------------------------------------------------------------

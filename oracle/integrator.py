@@ -1,6 +1,8 @@
 """The frame loop of Alg. 4 (Sec. 6): prediction, detection, Delassus operator and
 preconditioner, then local-global iterations constrained by the Fischer-Burmeister
-functions, and integration.
+functions, and integration. Two comparison variants of the paper are options: the
+minimum-map complementarity functions (App. B.1) and the mass-inverse complementarity
+preconditioner r_n = h^2 [H M^-1 H^T]_jj, r_f = h [H M^-1 H^T]_jj (Sec. 5.4).
 
 TEST INFRASTRUCTURE (see the package docstring). Plain FP64.
 
@@ -13,7 +15,12 @@ Readings of the paper used here (the paper leaves these open):
     scene's handle velocity;
   * the residual used to count iterations (not defined by the paper) is
     R = max_j max(|min(delta_n, r_n lambda_n)|, h |phi_f|) / L, with L the diagonal of the
-    rest bounding box.
+    rest bounding box. It is one measure for every variant: r from the Delassus diagonal
+    and phi_f with the Fischer-Burmeister E_f, whichever complementarity function and
+    preconditioner drive the iteration;
+  * the mass-inverse preconditioner, like the Delassus one, uses H (not J = Omega H, which
+    depends on r) and gives the two friction rows h times the mean of their diagonal
+    entries.
 """
 from __future__ import annotations
 
@@ -31,6 +38,8 @@ class OracleOptions:
     n_iters: int = 5
     n_cr: int = 10
     exact_constraint_solve: bool = False   # dense solve instead of CR (isolates CR error)
+    ncp: str = "fb"                        # "fb" (App. B.2) or "minmap" (App. B.1)
+    precond: str = "delassus"              # "delassus" (Eq. 28) or "mass" (Sec. 5.4)
 
 
 class Oracle:
@@ -81,9 +90,20 @@ class Oracle:
         d = np.diag(W).reshape(c, 3) if c else np.zeros((0, 3))
         return self.h ** 2 * d[:, 0], self.h * 0.5 * (d[:, 1] + d[:, 2])
 
-    def contact_state(self, q_f, q_t_f, lam, H, contacts, r_n, r_f):
+    def mass_preconditioner(self, H, c):
+        """r_n = h^2 [H M^-1 H^T]_jj on normal rows, r_f = h [H M^-1 H^T]_jj on friction rows
+        (the mass-inverse alternative of Sec. 5.4); M is the lumped mass of the free DoFs."""
+        if c == 0:
+            return np.zeros(0), np.zeros(0)
+        minv = 1.0 / np.repeat(self.fem.mass[self.fem.free_verts], 3)
+        d = ((H * H) @ minv).reshape(c, 3)
+        return self.h ** 2 * d[:, 0], self.h * 0.5 * (d[:, 1] + d[:, 2])
+
+    def contact_state(self, q_f, q_t_f, lam, H, contacts, r_n, r_f, ncp="fb"):
         """Gaps, indicators, compliances and NCP values at (q^k, lambda^k) (Alg. 4, "Evaluate
-        Omega, J, E, g, h"; Eq. 40 for delta_n and h delta_dot_f)."""
+        Omega, J, E, g, h"; Eq. 40 for delta_n and h delta_dot_f) with the Fischer-Burmeister
+        (App. B.2) or minimum-map (App. B.1) functions."""
+        normal_terms, friction_terms = C.NCP_TERMS[ncp]
         c = len(contacts)
         h = self.h
         Hq = (H @ q_f).reshape(c, 3)
@@ -93,8 +113,8 @@ class Oracle:
         for j, ct in enumerate(contacts):
             dn = Hq[j, 0] - ct["d_n"]
             vf = ((Hq[j, 1:] - Hqt[j, 1:]) - h * ct["d_f"]) / h
-            phi_n, om_n, E_n = C.normal_terms(dn, lam[j, 0], r_n[j])
-            om_f, E_f, phi_f = C.friction_terms(vf, lam[j, 1:], lam[j, 0], ct["mu"], r_f[j])
+            phi_n, om_n, E_n = normal_terms(dn, lam[j, 0], r_n[j])
+            om_f, E_f, phi_f = friction_terms(vf, lam[j, 1:], lam[j, 0], ct["mu"], r_f[j])
             out["omega"][j] = (om_n, om_f, om_f)
             out["E"][j] = (E_n, E_f, E_f)
             out["phi"][j] = (phi_n, phi_f[0], phi_f[1])
@@ -122,7 +142,21 @@ class Oracle:
         c = len(contacts)
         H = self.contact_jacobian(contacts)
         W = self.delassus(H)
-        r_n, r_f = self.preconditioner(W, c)
+        r_n, r_f = self.preconditioner(W, c)                 # also the residual's scale
+        if opts.precond == "delassus":
+            rp_n, rp_f = r_n, r_f
+        elif opts.precond == "mass":
+            rp_n, rp_f = self.mass_preconditioner(H, c)
+        else:
+            raise ValueError("precond must be 'delassus' or 'mass'")
+        if opts.ncp not in C.NCP_TERMS:
+            raise ValueError("ncp must be 'fb' or 'minmap'")
+        plain = opts.ncp == "fb" and opts.precond == "delassus"
+
+        def measure(q_f, cs, lam):
+            if not plain:
+                cs = self.contact_state(q_f, q_t_f, lam, H, contacts, r_n, r_f)
+            return self.residual(cs, lam, r_n), cs
 
         q = s_tilde.copy()
         q[self.scene.pinned] = q_pin
@@ -136,8 +170,8 @@ class Oracle:
             b = f.assemble_rhs(s_tilde, p, q_pin)                        # RHS (Eq. 6)
             q_f = q[fv].reshape(-1)
             if c:
-                cs = self.contact_state(q_f, q_t_f, lam, H, contacts, r_n, r_f)
-                residuals.append(self.residual(cs, lam, r_n))
+                cs = self.contact_state(q_f, q_t_f, lam, H, contacts, rp_n, rp_f, opts.ncp)
+                residuals.append(measure(q_f, cs, lam)[0])
                 Om = cs["omega"].reshape(-1)
                 J = Om[:, None] * H                                      # J = Omega H (Eq. 25)
                 g = b + h ** 2 * (J.T @ lam.reshape(-1))                 # Eq. 19
@@ -157,12 +191,15 @@ class Oracle:
                 q_f = f.solve(b)                                         # Eq. 6
             q = q.copy()
             q[fv] = q_f.reshape(-1, 3)
-        info = dict(contacts=contacts, lam=lam, W=W, r_n=r_n, r_f=r_f, s_tilde=s_tilde, H=H)
+        info = dict(contacts=contacts, lam=lam, W=W, r_n=r_n, r_f=r_f, rp_n=rp_n, rp_f=rp_f,
+                    s_tilde=s_tilde, H=H)
         if c and opts.n_iters:
             info["omega_last"] = omega_last
         if c:
-            cs = self.contact_state(q[fv].reshape(-1), q_t_f, lam, H, contacts, r_n, r_f)
-            residuals.append(self.residual(cs, lam, r_n))
+            q_f = q[fv].reshape(-1)
+            cs = self.contact_state(q_f, q_t_f, lam, H, contacts, rp_n, rp_f, opts.ncp)
+            res, cs = measure(q_f, cs, lam)
+            residuals.append(res)
             info["final_state"] = cs
         info["residuals"] = residuals
         v_new = (q - q_t) / h

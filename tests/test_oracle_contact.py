@@ -107,3 +107,68 @@ def test_detection_finds_exactly_the_vertices_below_margin():
     assert {c["vertex"] for c in cts} == below
     for c in cts:
         assert abs(c["d_n"]) < 1e-15 and np.allclose(c["n"], [0, 0, 1])
+
+
+def test_minmap_normal_zero_iff_complementary_and_branch_derivatives():
+    # min(delta, r lambda) vanishes exactly on 0 <= delta _|_ lambda >= 0 (App. B.1), and on
+    # each branch omega_n and E_n are the derivatives in delta_n and lambda_n
+    rng = np.random.default_rng(11)
+    for _ in range(400):
+        d, lam, r = rng.normal(), rng.normal(), rng.uniform(0.1, 3)
+        phi, om, E = C.minmap_normal_terms(d, lam, r)
+        if d > 0 and lam > 0:
+            assert phi > 0
+        if d < 0 or lam < 0:
+            assert phi < 0
+        eps = 1e-7 * min(1.0, abs(d - r * lam))
+        dphi_dd = (C.minmap_normal_terms(d + eps, lam, r)[0] -
+                   C.minmap_normal_terms(d - eps, lam, r)[0]) / (2 * eps)
+        dphi_dl = (C.minmap_normal_terms(d, lam + eps / r, r)[0] -
+                   C.minmap_normal_terms(d, lam - eps / r, r)[0]) / (2 * eps / r)
+        assert abs(om - dphi_dd) < 1e-6 and abs(E - dphi_dl) < 1e-6 * max(1, r)
+        assert om in (0.0, 1.0) and E in (0.0, r) and (om == 1.0) == (E == 0.0)
+    z = rng.uniform(0, 2, 50)
+    for x in z:
+        assert C.minmap_normal_terms(x, 0.0, 1.3)[0] == 0.0
+        assert C.minmap_normal_terms(0.0, x, 1.3)[0] == 0.0
+
+
+def test_minmap_friction_vanishes_exactly_on_coulomb_states():
+    rng = np.random.default_rng(12)
+    for _ in range(200):
+        lam_n = rng.uniform(0.1, 5)
+        mu = rng.uniform(0.05, 1)
+        r = rng.uniform(0.01, 2)
+        v = rng.normal(size=2)
+        # slip: lambda_f on the cone boundary, opposite to the velocity
+        lam_f = -mu * lam_n * v / np.linalg.norm(v)
+        om, E, phi = C.minmap_friction_terms(v, lam_f, lam_n, mu, r)
+        assert om == 1.0
+        assert abs(E - np.linalg.norm(v) / (mu * lam_n)) < 1e-12 * E
+        assert np.abs(phi).max() < 1e-12 * np.linalg.norm(v)
+        # stick: zero velocity inside the cone
+        lam_f2 = rng.uniform(0, 0.99) * mu * lam_n * np.array([np.cos(0.3), np.sin(0.3)])
+        om, E, phi = C.minmap_friction_terms(np.zeros(2), lam_f2, lam_n, mu, r)
+        assert E == 0.0 and np.abs(phi).max() == 0.0
+        # not solutions: slip along the velocity, or a moving contact inside the cone with
+        # the velocity above r (mu lambda_n - |lambda_f|)
+        om, E, phi = C.minmap_friction_terms(v, -lam_f, lam_n, mu, r)
+        assert np.linalg.norm(phi) > 1.9 * np.linalg.norm(v)
+        s = mu * lam_n - np.linalg.norm(lam_f2)
+        v2 = v / np.linalg.norm(v) * (r * s * rng.uniform(1.5, 3.0))
+        om, E, phi = C.minmap_friction_terms(v2, lam_f2, lam_n, mu, r)
+        assert E > 0 and np.linalg.norm(phi) > 0
+        # inactive contact: phi_f = lambda_f, the same as the Fischer-Burmeister form
+        om, E, phi = C.minmap_friction_terms(v, lam_f, -lam_n, mu, r)
+        assert om == 0.0 and E == 1.0 and np.allclose(phi, lam_f)
+
+
+def test_minmap_and_fb_share_indicators_away_from_the_kink():
+    # on the two arms of the complementarity set (an active contact with delta_n -> 0, a
+    # separated one with lambda_n -> 0) the FB indicator and compliance tend to the
+    # minimum map's branch values
+    for d, lam in ((1e-9, 1.0), (1.0, 1e-9), (1e-12, 3.0), (2.0, 1e-12)):
+        r = 0.7
+        _, om_fb, E_fb = C.normal_terms(d, lam, r)
+        _, om_mm, E_mm = C.minmap_normal_terms(d, lam, r)
+        assert abs(om_fb - om_mm) < 1e-6 and abs(E_fb - E_mm) < 1e-6
