@@ -23,7 +23,15 @@ Readings of the paper used here (the paper leaves these open):
     |lambda_f| = 2 mu lambda_n, where Eq. 57 turns negative) E_f takes the slip value of
     the minimum-map form (Eq. 51), (|delta_dot_f| + r (|lambda_f| - mu lambda_n)) /
     (mu lambda_n), which has no fixed point outside the cone. A contact with mu = 0 is
-    treated like an inactive one (omega_f = 0, E_f = 1), so its friction force vanishes.
+    treated like an inactive one (omega_f = 0, E_f = 1), so its friction force vanishes;
+  * friction is active (App. B.1-B.2: lambda_n > 0) when the normal impulse is resolvable:
+    r_n lambda_n > ACTIVE_REL * L, with r_n the Delassus-diagonal scale (Eq. 28) and L the
+    residual's length scale. When the Newton step drives a separating contact's lambda_n
+    to zero it lands on rounding noise of either sign (1e-40 in FP64, 1e-7 of the cancelled
+    impulse in FP32); read literally, a positive residue switches on friction with a
+    compliance E_f ~ |delta_dot_f| / (mu lambda_n) that swamps the constraint solve and
+    makes the residual jump. The tolerance (1e-6 of the scene's length) lies far above both
+    noise levels and far below the residual targets (1e-4).
 """
 from __future__ import annotations
 
@@ -32,6 +40,7 @@ import numpy as np
 from scenegen import OBST_CYLINDER, OBST_PLANE
 
 TINY_REL = 1e-12
+ACTIVE_REL = 1e-6
 
 
 def tangent_frame(n):
@@ -101,10 +110,18 @@ def normal_terms(delta_n, lam_n, r_n):
     return phi, omega, E
 
 
-def friction_terms(vel_f, lam_f, lam_n, mu, r_f):
+def friction_active(lam_n, r_n, L):
+    """Whether a contact's friction rows are active: r_n lambda_n > ACTIVE_REL * L."""
+    return r_n * lam_n > ACTIVE_REL * L
+
+
+def friction_terms(vel_f, lam_f, lam_n, mu, r_f, active=None):
     """omega_f (Eqs. 56, 24), the scalar compliance E_f (Eq. 57) and phi_f (Eq. 55) of one
-    contact's two friction rows. vel_f is the tangential relative velocity delta_dot_f."""
-    if lam_n <= 0.0 or mu <= 0.0:
+    contact's two friction rows. vel_f is the tangential relative velocity delta_dot_f;
+    active: the friction_active decision (default lambda_n > 0)."""
+    if active is None:
+        active = lam_n > 0.0
+    if not active or mu <= 0.0:
         return 0.0, 1.0, np.array(lam_f, dtype=np.float64)
     a = float(np.linalg.norm(vel_f))
     lf = float(np.linalg.norm(lam_f))
@@ -132,13 +149,15 @@ def minmap_normal_terms(delta_n, lam_n, r_n):
     return r_n * lam_n, 0.0, r_n
 
 
-def minmap_friction_terms(vel_f, lam_f, lam_n, mu, r_f):
+def minmap_friction_terms(vel_f, lam_f, lam_n, mu, r_f, active=None):
     """omega_f, the scalar compliance E_f and phi_f = omega_f delta_dot_f + E_f lambda_f of
     the minimum-map friction rows (App. B.1). Inactive contacts (lambda_n <= 0, or mu = 0)
     as in the Fischer-Burmeister form. Active ones, with s = mu lambda_n - |lambda_f|: stick
     (E_f = 0) while |delta_dot_f| <= r_f s, else the slip compliance
-    (|delta_dot_f| - r_f s) / (mu lambda_n)."""
-    if lam_n <= 0.0 or mu <= 0.0:
+    (|delta_dot_f| - r_f s) / (mu lambda_n). active: as in friction_terms."""
+    if active is None:
+        active = lam_n > 0.0
+    if not active or mu <= 0.0:
         return 0.0, 1.0, np.array(lam_f, dtype=np.float64)
     a = float(np.linalg.norm(vel_f))
     s = mu * lam_n - float(np.linalg.norm(lam_f))

@@ -18,6 +18,8 @@ Readings of the paper used here (the paper leaves these open):
     rest bounding box. It is one measure for every variant: r from the Delassus diagonal
     and phi_f with the Fischer-Burmeister E_f, whichever complementarity function and
     preconditioner drive the iteration;
+  * friction is active when r_n lambda_n > ACTIVE_REL * L (``contact.friction_active``;
+    App. B.1-B.2 write lambda_n > 0), decided with the Delassus r_n for every variant;
   * the mass-inverse preconditioner, like the Delassus one, uses H (not J = Omega H, which
     depends on r) and gives the two friction rows h times the mean of their diagonal
     entries.
@@ -99,10 +101,13 @@ class Oracle:
         d = ((H * H) @ minv).reshape(c, 3)
         return self.h ** 2 * d[:, 0], self.h * 0.5 * (d[:, 1] + d[:, 2])
 
-    def contact_state(self, q_f, q_t_f, lam, H, contacts, r_n, r_f, ncp="fb"):
+    def contact_state(self, q_f, q_t_f, lam, H, contacts, r_n, r_f, ncp="fb", r_act=None):
         """Gaps, indicators, compliances and NCP values at (q^k, lambda^k) (Alg. 4, "Evaluate
         Omega, J, E, g, h"; Eq. 40 for delta_n and h delta_dot_f) with the Fischer-Burmeister
-        (App. B.2) or minimum-map (App. B.1) functions."""
+        (App. B.2) or minimum-map (App. B.1) functions. r_act: the Delassus-diagonal r_n of
+        the friction activity test (default r_n)."""
+        if r_act is None:
+            r_act = r_n
         normal_terms, friction_terms = C.NCP_TERMS[ncp]
         c = len(contacts)
         h = self.h
@@ -114,7 +119,8 @@ class Oracle:
             dn = Hq[j, 0] - ct["d_n"]
             vf = ((Hq[j, 1:] - Hqt[j, 1:]) - h * ct["d_f"]) / h
             phi_n, om_n, E_n = normal_terms(dn, lam[j, 0], r_n[j])
-            om_f, E_f, phi_f = friction_terms(vf, lam[j, 1:], lam[j, 0], ct["mu"], r_f[j])
+            act = C.friction_active(lam[j, 0], r_act[j], self.L_ref)
+            om_f, E_f, phi_f = friction_terms(vf, lam[j, 1:], lam[j, 0], ct["mu"], r_f[j], act)
             out["omega"][j] = (om_n, om_f, om_f)
             out["E"][j] = (E_n, E_f, E_f)
             out["phi"][j] = (phi_n, phi_f[0], phi_f[1])
@@ -165,13 +171,15 @@ class Oracle:
         lam = np.zeros((c, 3)) if lam0 is None else np.array(lam0, dtype=np.float64)
         q_t_f = q_t[fv].reshape(-1)
         residuals = []
+        lam_iters = []                     # lambda at each residual's iterate
         for _k in range(opts.n_iters):
             p = self.local_step(q)                                       # local step
             b = f.assemble_rhs(s_tilde, p, q_pin)                        # RHS (Eq. 6)
             q_f = q[fv].reshape(-1)
             if c:
-                cs = self.contact_state(q_f, q_t_f, lam, H, contacts, rp_n, rp_f, opts.ncp)
+                cs = self.contact_state(q_f, q_t_f, lam, H, contacts, rp_n, rp_f, opts.ncp, r_n)
                 residuals.append(measure(q_f, cs, lam)[0])
+                lam_iters.append(lam.copy())
                 Om = cs["omega"].reshape(-1)
                 J = Om[:, None] * H                                      # J = Omega H (Eq. 25)
                 g = b + h ** 2 * (J.T @ lam.reshape(-1))                 # Eq. 19
@@ -197,11 +205,13 @@ class Oracle:
             info["omega_last"] = omega_last
         if c:
             q_f = q[fv].reshape(-1)
-            cs = self.contact_state(q_f, q_t_f, lam, H, contacts, rp_n, rp_f, opts.ncp)
+            cs = self.contact_state(q_f, q_t_f, lam, H, contacts, rp_n, rp_f, opts.ncp, r_n)
             res, cs = measure(q_f, cs, lam)
             residuals.append(res)
+            lam_iters.append(lam.copy())
             info["final_state"] = cs
         info["residuals"] = residuals
+        info["lam_iters"] = lam_iters
         v_new = (q - q_t) / h
         return q, v_new, info
 

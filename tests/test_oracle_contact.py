@@ -172,3 +172,20 @@ def test_minmap_and_fb_share_indicators_away_from_the_kink():
         _, om_fb, E_fb = C.normal_terms(d, lam, r)
         _, om_mm, E_mm = C.minmap_normal_terms(d, lam, r)
         assert abs(om_fb - om_mm) < 1e-6 and abs(E_fb - E_mm) < 1e-6
+
+
+def test_friction_activity_needs_a_resolvable_normal_impulse():
+    # App. B.1-B.2 switch friction on for lambda_n > 0; the reading takes that decision with
+    # a tolerance r_n lambda_n > ACTIVE_REL L, so a rounding residue of a cancelled impulse
+    # is inactive, while any impulse that displaces the contact by more than that is active
+    r, L, mu = 2e-3, 0.2, 0.5
+    v = np.array([3e-3, -1e-3])
+    for lam_n, expect in ((1e-52, False), (4.8e-7 * 1e-3, False), (-1.0, False),
+                          (2.0 * C.ACTIVE_REL * L / r, True), (1.0, True)):
+        act = C.friction_active(lam_n, r, L)
+        assert act == expect
+        for terms in (C.friction_terms, C.minmap_friction_terms):
+            om, E, phi = terms(v, np.zeros(2), lam_n, mu, 0.01, act)
+            assert om == (1.0 if expect else 0.0)
+            if not expect:
+                assert E == 1.0 and np.all(phi == 0.0)

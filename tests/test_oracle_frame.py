@@ -295,3 +295,18 @@ def test_mass_preconditioner_blurs_the_stick_slip_threshold():
     a, a_exp = _slope_acceleration(gold, -gold["paper_mass_preconditioner_accuracy"],
                                    precond="mass")
     assert abs(a - a_exp) < 0.03 * a_exp
+
+
+def test_cancelled_normal_impulse_does_not_switch_on_friction():
+    # cube pressed into the plane, minimum map with the mass-inverse preconditioner: one
+    # contact's normal impulse turns negative and the impulse branch cancels it; in FP64
+    # it lands on residues of 1e-41 .. 1e-52 of either sign. With friction decided on
+    # lambda_n > 0 literally, the last iterate then showed a residual of 2.4e-3 although the
+    # frame was solved to 1e-16; the activity tolerance keeps it solved.
+    sc = sg.cube_drop(m=6, model=sg.MODEL_ARAP, height=-0.003, seed=2, mu=0.5)
+    o = Oracle(sc)
+    _, _, info = o.frame(sc.q0, sc.v0, OracleOptions(n_iters=5, n_cr=sc.n_cr, ncp="minmap",
+                                                     precond="mass"))
+    assert max(info["residuals"][2:]) < 1e-12
+    lam_n = info["lam"][:, 0]
+    assert np.any((lam_n != 0) & (np.abs(lam_n) < 1e-30))
