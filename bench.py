@@ -312,7 +312,9 @@ def warmstart_ab():
     """The second half of the metric: frame time to residual 1e-4, learned warm start vs the
     plain cold start, on the 6^3 cube drops (train on 16 seeds, 80 frames each, from frames
     the plain method solved; evaluate on 5 held-out seeds, every contact frame replayed from
-    the same state with each start, up to 40 iterations)."""
+    the same state with each start, up to 40 iterations). "portfolio" runs the learned start
+    beside the cold one as a two-copy batch and takes whichever reaches the tolerance first
+    (its time is the batch's)."""
     import numpy as np
     import scenegen as sg
     from paper_2503_15078_b300 import warmstart
@@ -322,7 +324,7 @@ def warmstart_ab():
                                n_iters=20)
     net, losses = warmstart.train(X, T, epochs=60, batch=512, lr=1e-3, seed=0, X_val=Xv, T_val=Tv)
     res = warmstart.evaluate_from_states(sg.warmstart_scenes(range(100, 105), frames=60), 60,
-                                         ["cold", "previous", "learned"], net=net)
+                                         ["cold", "previous", "learned", "portfolio"], net=net)
     out = {"workload": "6^3 cube drops (config-1 scene, seeded height/rotation/tilt); 16 "
                        "training seeds x 80 frames, 4 validation seeds (output shrinkage), "
                        "5 held-out seeds x 60 frames",

@@ -56,6 +56,12 @@ enum { SIM_OBST_PLANE = 0,      /* p: point on plane, axis: unit outward normal 
        SIM_OBST_CYLINDER = 1 }; /* infinite cylinder: p on axis, axis unit, radius        */
 enum { SIM_S_FP32 = 0,          /* S stored in FP32                                       */
        SIM_S_BF16 = 1 };        /* S stored in BF16, FP32 accumulation                     */
+enum { SIM_NCP_FB = 0,          /* Fischer-Burmeister complementarity functions (App. B.2) */
+       SIM_NCP_MINMAP = 1 };    /* minimum-map functions (App. B.1)                       */
+enum { SIM_PRECOND_DELASSUS = 0,/* r_n = h^2 W_jj, r_f = h W_jj from the Delassus operator
+                                   (Eq. 28)                                               */
+       SIM_PRECOND_MASS = 1 };  /* r_n = h^2 [H M^-1 H^T]_jj, r_f = h [H M^-1 H^T]_jj: the
+                                   mass-inverse alternative of Sec. 5.4 (h^2/m_v, h/m_v)   */
 
 /* ---- inputs ------------------------------------------------------------------------- */
 typedef struct {
@@ -106,6 +112,11 @@ typedef struct {
   int32_t autotune;            /* 1: time the profile products' launch configurations at
                                   creation and keep the fastest (sim_get_tuning); 0
                                   (default): the fixed configuration                     */
+  int32_t ncp;                 /* SIM_NCP_FB (default) or SIM_NCP_MINMAP: the functions
+                                  that drive the iteration. The residual (sim_stats) is one
+                                  measure for every choice: min(delta_n, r_n lambda_n) and
+                                  h phi_f with the FB E_f, r from the Delassus diagonal. */
+  int32_t precond;             /* SIM_PRECOND_DELASSUS (default) or SIM_PRECOND_MASS      */
 } sim_options;
 
 /* Launch configuration of the two profile products (z = S g, x = S^T y), chosen by the
@@ -309,6 +320,17 @@ int sim_mlp_train(sim_mlp_t* net, const float* X, const float* T, int32_t rows, 
  * if the residual of its impulses at k = 0 (at the position they predict) is below the cold
  * start's. */
 int sim_set_warmstart(sim_t* sim, const sim_mlp_t* net, int32_t mode);
+/* Portfolio start (not from the paper): the simulator's scenes (sim_create_batch) are groups
+ * of `copies` identical copies of a scene, consecutive (scenes g * copies .. g * copies +
+ * copies - 1 form group g). Copy 0 of each group always runs the cold start; the other
+ * copies take the start set with sim_set_warmstart. After each frame every copy of a group
+ * continues from the copy whose final residual is the lowest (ties: the lowest copy):
+ * positions, velocities and the previous-frame contact data the features read. The copies
+ * run side by side in the same launches, so a group costs about one scene's latency.
+ * copies = 1 turns it off (the default). Synchronises the handle's stream; frame graphs are
+ * rebuilt. Errors: SIM_EINVAL (copies < 1, a scene count that is not a multiple of copies,
+ * copies that differ in any input: mesh, materials, pins, handle, obstacles, margin). */
+int sim_set_portfolio(sim_t* sim, int32_t copies);
 /* Training samples of the last frame, one per contact (device order): X (n x
  * SIM_MLP_FEATURES) the features at the frame's start -- gap / margin, normal (3), relative
  * velocity h / margin (3), the previous frame's impulse at the same vertex and obstacle in

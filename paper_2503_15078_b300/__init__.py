@@ -101,9 +101,18 @@ def _options(scene=None, **kw):
         if k == "gravity":
             for r in range(3):
                 o.gravity[r] = float(v[r])
+        elif k in _NAMED and isinstance(v, str):
+            if v not in _NAMED[k]:
+                raise ValueError(f"{k} must be one of {sorted(_NAMED[k])}")
+            setattr(o, k, _NAMED[k][v])
         else:
             setattr(o, k, v)
     return o
+
+
+# options that also take names: the complementarity functions (App. B.1-B.2) and the
+# complementarity preconditioner (Sec. 5.4)
+_NAMED = {"ncp": {"fb": 0, "minmap": 1}, "precond": {"delassus": 0, "mass": 1}}
 
 
 class Plan:
@@ -275,6 +284,11 @@ class Simulator:
         """0 cold (the paper's start), 1 the network's guess, 2 the previous frame's impulses."""
         _check(lib().sim_set_warmstart(self._h, net.handle if net is not None else None,
                                        int(mode)), "sim_set_warmstart")
+
+    def set_portfolio(self, copies):
+        """Scenes are groups of `copies` identical copies: copy 0 runs cold, the others the
+        warm start, and each frame every copy continues from the best one (1: off)."""
+        _check(lib().sim_set_portfolio(self._h, int(copies)), "sim_set_portfolio")
 
     def warmstart_samples(self):
         """(features, targets) of the last frame's contacts."""

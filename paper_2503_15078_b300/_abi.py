@@ -47,7 +47,8 @@ class SimOptions(C.Structure):
                 ("refine", C.c_int32), ("contact_capacity", C.c_int32), ("device", C.c_int32),
                 ("gravity", C.c_double * 3), ("contact_margin", C.c_double),
                 ("spin_limit", C.c_uint64), ("cuda_stream", C.c_void_p),
-                ("n_host_threads", C.c_int32), ("autotune", C.c_int32)]
+                ("n_host_threads", C.c_int32), ("autotune", C.c_int32),
+                ("ncp", C.c_int32), ("precond", C.c_int32)]
 
 
 class SimTuning(C.Structure):
@@ -81,6 +82,7 @@ PROTOTYPES = {
     "sim_get_tuning": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sim_mlp_create": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_void_p)]),
     "sim_set_warmstart": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "sim_set_portfolio": (C.c_int, [C.c_void_p, C.c_int32]),
     "sim_get_warmstart_samples": (C.c_int, [C.c_void_p, C.c_int32, _fp, _fp,
                                             C.POINTER(C.c_int32)]),
     "sim_mlp_destroy": (None, [C.c_void_p]),

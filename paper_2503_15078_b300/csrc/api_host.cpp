@@ -42,6 +42,8 @@ void sim_default_options(sim_options* o) {
   o->cuda_stream = nullptr;
   o->n_host_threads = 0;
   o->autotune = 0;
+  o->ncp = SIM_NCP_FB;
+  o->precond = SIM_PRECOND_DELASSUS;
 }
 
 int sim_plan_create(const sim_mesh* mesh, const sim_material* mats, int32_t n_mat, double h,

@@ -43,6 +43,7 @@ struct DevSim {
   // sizes
   int n, n_all, n_tets, n_pad, n_obs, n_mat;
   int cap, cap_y, n_cr;
+  int ncp, precond;  // SIM_NCP_*, SIM_PRECOND_*
   int n_rg, n_ct;
   double h;
   float h2f;        // h^2 in FP32
@@ -68,6 +69,10 @@ struct DevSim {
   // warm start (not from the paper): 0 cold (lambda = 0, q = s~), 1 learned, 2 the previous
   // frame's impulses
   int ws_mode;
+  // portfolio (not from the paper): scenes form groups of pf_copies identical copies; copy 0
+  // of a group runs the cold start, the others the warm start, and at the frame's end every
+  // copy continues from the copy with the lowest final residual (1: off)
+  int pf_copies;
   MlpDev ws_net;              // BF16 weights (w_t) and the parameter vector (biases)
   float* ws_feat;             // cap x kMlpIn: features at the frame start
   float* ws_out;              // cap x kMlpOut: network outputs
@@ -160,7 +165,8 @@ struct DevSim {
   double* ct_dn;    // cap
   double* ct_df;    // 2 cap
   double* ct_mu;    // cap
-  double* ct_r;     // 2 cap: r_n, r_f
+  double* ct_r;     // 4 cap: r_n, r_f of the iteration, then r_n, r_f of the Delassus
+                    // diagonal (the residual's; the same unless SIM_PRECOND_MASS)
   double* ct_lam;   // 3 cap
   double* ct_force; // 3 cap: D^T (Omega lambda)
   float* ct_omega;  // 3 cap
@@ -254,6 +260,9 @@ void launch_ws_features(const DevSim& d, cudaStream_t s);
 void launch_ws_start(const DevSim& d, cudaStream_t s);
 void launch_ws_record(const DevSim& d, cudaStream_t s);
 int ws_kernels(int mode);   // launches of launch_ws_start
+// portfolio: every copy of a group takes the state of the copy with the lowest final
+// residual after a K-iteration frame (one launch)
+void launch_pf_sync(const DevSim& d, cudaStream_t s, int K);
 void launch_scan(const int* in, int* out, int n, const int* n_dev, int* total, cudaStream_t s);
 int cr_setup(int n_scenes, int* cluster_out, size_t* smem_out);
 int sinv_setup();

@@ -1,5 +1,7 @@
-// Fischer-Burmeister terms of one contact (App. B.2), shared by the per-iteration contact
-// evaluation and the warm start's choice between its guess and the cold start (FP64).
+// Complementarity terms of one contact, shared by the per-iteration contact evaluation and
+// the warm start's choice between its guess and the cold start (FP64): the
+// Fischer-Burmeister functions (App. B.2) or the minimum map (App. B.1), and the residual
+// measure, which is the same for both.
 #pragma once
 
 #include "device.cuh"
@@ -7,14 +9,79 @@
 namespace silg {
 
 constexpr double kFbTinyRel = 1e-12;
+// Friction rows are active when the normal impulse is resolvable, r_n lambda_n > kActiveRel L
+// (r_n from the Delassus diagonal, L the scene's length): App. B.1-B.2 write lambda_n > 0,
+// but a normal impulse cancelled by the Newton step lands on rounding residues of either
+// sign (about 1e-7 of the cancelled value in FP32), and a positive residue would switch on
+// a friction compliance ~ |v_f| / (mu lambda_n) that swamps the constraint solve.
+constexpr double kActiveRel = 1e-6;
 
 struct FbTerms {
   double dn;            // delta_n = n . q - d_n
   double vf[2];         // tangential velocity relative to the obstacle
-  double phin, omn, En; // normal row (Eqs. 52-54)
-  double phif0, phif1, omf, Ef;  // friction rows (Eqs. 55-57)
+  double phin, omn, En; // normal row (Eqs. 52-54, or App. B.1)
+  double phif0, phif1, omf, Ef;  // friction rows (Eqs. 55-57, or App. B.1)
   double res;           // the residual measure max(|min(dn, r_n lambda_n)|, h |phi_f|) / L
 };
+
+// Normal and friction rows at gap dn, tangential velocity vf, impulses (ln, lf0, lf1) with
+// preconditioner (rn, rf): Fischer-Burmeister (minmap = false) or minimum map; active: the
+// friction activity decision.
+__device__ inline void ncp_rows(bool minmap, double dn, const double vf[2], double ln,
+                                double lf0, double lf1, double rn, double rf, double mu,
+                                bool active, FbTerms& o) {
+  if (minmap) {
+    // min(delta_n, r_n lambda_n): the gap branch (ties included) or the impulse branch
+    if (dn <= rn * ln) {
+      o.phin = dn;
+      o.omn = 1.0;
+      o.En = 0.0;
+    } else {
+      o.phin = rn * ln;
+      o.omn = 0.0;
+      o.En = rn;
+    }
+  } else {
+    const double rho = sqrt(dn * dn + rn * rn * ln * ln);
+    o.phin = dn + rn * ln - rho;
+    if (rho == 0.0) {
+      o.omn = 1.0;
+      o.En = 0.0;
+    } else {
+      o.omn = 1.0 - dn / rho;
+      o.En = (1.0 - rn * ln / rho) * rn;
+    }
+  }
+  if (!active || mu <= 0.0) {
+    // inactive friction in both forms: phi_f = lambda_f drives the impulse to zero
+    o.omf = 0.0;
+    o.Ef = 1.0;
+    o.phif0 = lf0;
+    o.phif1 = lf1;
+    return;
+  }
+  const double a = sqrt(vf[0] * vf[0] + vf[1] * vf[1]);
+  const double lf = sqrt(lf0 * lf0 + lf1 * lf1);
+  const double s = mu * ln - lf;
+  if (minmap) {
+    // stick while |v_f| <= r_f s, else the slip compliance (|v_f| - r_f s) / (mu lambda_n)
+    o.Ef = a <= rf * s ? 0.0 : (a - rf * s) / (mu * ln);
+  } else {
+    const double root = sqrt(a * a + rf * rf * s * s);
+    const double num = root - rf * s;
+    const double den = a + mu * rf * ln - root;
+    const double scale = a + mu * rf * ln + rf * fabs(s);
+    if (num <= kFbTinyRel * scale)
+      o.Ef = 0.0;
+    else if (den <= kFbTinyRel * scale)
+      o.Ef = (a + rf * (lf - mu * ln)) / (mu * ln);
+    else
+      o.Ef = num / den * rf;
+  }
+  o.omf = 1.0;
+  o.phif0 = vf[0] + o.Ef * lf0;
+  o.phif1 = vf[1] + o.Ef * lf1;
+}
 
 // contact j at vertex position q (world) with impulses lam (n, f1, f2); L: residual scale
 __device__ inline FbTerms fb_terms(const DevSim& d, int j, const double q[3], const double lam[3],
@@ -32,41 +99,21 @@ __device__ inline FbTerms fb_terms(const DevSim& d, int j, const double q[3], co
                h * d.ct_df[2 * j + a]) / h;
   }
   const double ln = lam[0], lf0 = lam[1], lf1 = lam[2];
-  const double rn = d.ct_r[2 * j], rf = d.ct_r[2 * j + 1], mu = d.ct_mu[j];
-  const double dn = o.dn;
-  const double rho = sqrt(dn * dn + rn * rn * ln * ln);
-  o.phin = dn + rn * ln - rho;
-  if (rho == 0.0) {
-    o.omn = 1.0;
-    o.En = 0.0;
-  } else {
-    o.omn = 1.0 - dn / rho;
-    o.En = (1.0 - rn * ln / rho) * rn;
+  const double mu = d.ct_mu[j];
+  const double rn_m = d.ct_r[4 * j + 2];
+  const bool active = rn_m * ln > kActiveRel * L;
+  ncp_rows(d.ncp == SIM_NCP_MINMAP, o.dn, o.vf, ln, lf0, lf1, d.ct_r[4 * j], d.ct_r[4 * j + 1],
+           mu, active, o);
+  // the residual: min(delta_n, r_n lambda_n) and h phi_f with the Fischer-Burmeister E_f, r
+  // from the Delassus diagonal, whichever functions and preconditioner drive the iteration
+  double pf0 = o.phif0, pf1 = o.phif1;
+  if (d.ncp != SIM_NCP_FB || d.precond != SIM_PRECOND_DELASSUS) {
+    FbTerms m;
+    ncp_rows(false, o.dn, o.vf, ln, lf0, lf1, rn_m, d.ct_r[4 * j + 3], mu, active, m);
+    pf0 = m.phif0;
+    pf1 = m.phif1;
   }
-  if (ln <= 0.0 || mu <= 0.0) {
-    o.omf = 0.0;
-    o.Ef = 1.0;
-    o.phif0 = lf0;
-    o.phif1 = lf1;
-  } else {
-    const double a = sqrt(o.vf[0] * o.vf[0] + o.vf[1] * o.vf[1]);
-    const double lf = sqrt(lf0 * lf0 + lf1 * lf1);
-    const double s = mu * ln - lf;
-    const double root = sqrt(a * a + rf * rf * s * s);
-    const double num = root - rf * s;
-    const double den = a + mu * rf * ln - root;
-    const double scale = a + mu * rf * ln + rf * fabs(s);
-    if (num <= kFbTinyRel * scale)
-      o.Ef = 0.0;
-    else if (den <= kFbTinyRel * scale)
-      o.Ef = (a + rf * (lf - mu * ln)) / (mu * ln);
-    else
-      o.Ef = num / den * rf;
-    o.omf = 1.0;
-    o.phif0 = o.vf[0] + o.Ef * lf0;
-    o.phif1 = o.vf[1] + o.Ef * lf1;
-  }
-  o.res = fmax(fabs(fmin(dn, rn * ln)), h * sqrt(o.phif0 * o.phif0 + o.phif1 * o.phif1)) / L;
+  o.res = fmax(fabs(fmin(o.dn, rn_m * ln)), h * sqrt(pf0 * pf0 + pf1 * pf1)) / L;
   return o;
 }
 

@@ -524,8 +524,14 @@ __global__ void k_precond(DevSim d) {
     const int sc = d.vert_scene[d.ct_vert[j]], l = cv - d.sc_cvb[sc];
     w = (double)d.wt[d.sc_wtoff[sc] + (size_t)l * d.sc_ld[sc] + l];
   }
-  d.ct_r[2 * j] = d.h * d.h * w;
-  d.ct_r[2 * j + 1] = d.h * w;
+  // the residual's scale is always the Delassus diagonal (Eq. 28); the iteration's is that
+  // or, with the mass-inverse preconditioner (Sec. 5.4), [H M^-1 H^T]_jj = 1 / m_v for a
+  // one-vertex contact with unit frame rows
+  const double wi = d.precond == SIM_PRECOND_MASS ? 1.0 / d.mass[d.ct_vert[j]] : w;
+  d.ct_r[4 * j] = d.h * d.h * wi;
+  d.ct_r[4 * j + 1] = d.h * wi;
+  d.ct_r[4 * j + 2] = d.h * d.h * w;
+  d.ct_r[4 * j + 3] = d.h * w;
   for (int r = 0; r < 3; ++r) d.ct_lam[3 * j + r] = 0.0;
   for (int r = 0; r < 9; ++r) d.ct_Df[9 * j + r] = (float)d.ct_D[9 * j + r];
 }

@@ -148,8 +148,10 @@ __global__ void k_ws_residuals(DevSim d) {
   atomic_max_nonneg(&d.ws_res[2 * sc + 1], fb_terms(d, j, q0, zero, L).res);
 }
 
-// strictly better than the cold start (an empty guess is the cold start and is not taken)
+// strictly better than the cold start (an empty guess is the cold start and is not taken);
+// copy 0 of a portfolio group always runs cold
 __device__ __forceinline__ bool ws_accepted(const DevSim& d, int sc) {
+  if (d.pf_copies > 1 && sc % d.pf_copies == 0) return false;
   return d.ws_res[2 * sc] < d.ws_res[2 * sc + 1];
 }
 
@@ -203,7 +205,40 @@ __global__ void k_ws_record(DevSim d) {
   t[3] = (float)(mv / d.scene_margin[sc]);
 }
 
+// Portfolio: a free vertex of a copy that did not win takes its counterpart's state in the
+// winning copy (lowest final residual, non-finite counted as infinite, ties to the lowest
+// copy): positions, velocities and the previous-frame contact data of the features. The
+// winner's vertices are only read.
+__global__ void k_pf_sync(DevSim d, int K) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= d.n) return;
+  const int sc = d.vert_scene[v], C = d.pf_copies, g0 = sc - sc % C;
+  int best = g0;
+  double rb = INFINITY;
+  for (int c = 0; c < C; ++c) {
+    const double r = d.resid_scene[(size_t)(g0 + c) * (kMaxIters + 1) + K];
+    if (isfinite(r) && r < rb) {
+      rb = r;
+      best = g0 + c;
+    }
+  }
+  if (best == sc) return;
+  const int w = v - d.scene_vfirst[sc] + d.scene_vfirst[best];
+  for (int r = 0; r < 3; ++r) {
+    d.q_t[3 * v + r] = d.q_t[3 * w + r];
+    d.v_t[3 * v + r] = d.v_t[3 * w + r];
+    d.prev_force[3 * v + r] = d.prev_force[3 * w + r];
+  }
+  d.prev_valid[v] = d.prev_valid[w];
+  d.prev_obst[v] = d.prev_obst[w];
+  d.prev_move[v] = d.prev_move[w];
+}
+
 }  // namespace
+
+void launch_pf_sync(const DevSim& d, cudaStream_t s, int K) {
+  k_pf_sync<<<(d.n + 255) / 256, 256, 0, s>>>(d, K);
+}
 
 void launch_ws_features(const DevSim& d, cudaStream_t s) {
   k_ws_features<<<(d.cap + 127) / 128, 128, 0, s>>>(d);

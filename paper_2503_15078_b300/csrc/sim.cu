@@ -52,6 +52,7 @@ struct sim_s {
   // [1] after collision, [2] after Delassus, [3] after the warm start, then kMarksPerIter
   // per iteration, then [end]
   std::vector<cudaEvent_t> ev;
+  std::vector<uint64_t> scene_sig;  // per scene: hash of its inputs (portfolio copies check)
   std::vector<int32_t> tet_caller_order;
   sim_tuning tuning{};
 
@@ -121,7 +122,8 @@ int kernels_per_frame(const sim_s* s, int K) {
   // per iteration: local, [contact eval], rhs, pass 1 + reduction, [Y^T z, CR, Y u],
   // pass 2 + reduction; a residual correction adds the residual and both passes
   return 1 + (c ? 4 + 12 : 0) + K * (1 + (c ? 1 : 0) + 1 + 2 + (c ? 3 : 0) + 2) + (c ? 1 : 0) + 1 +
-         5 * refined_iters(s, K);
+         5 * refined_iters(s, K) + (c ? silg::ws_kernels(s->d.ws_mode) : 0) +
+         (c && s->d.pf_copies > 1 ? 1 : 0);
 }
 
 void enqueue_frame(sim_s* s, int K, cudaStream_t st) {
@@ -207,6 +209,7 @@ void enqueue_frame(sim_s* s, int K, cudaStream_t st) {
     silg::launch_ws_record(d, st);
   }
   silg::launch_integrate(d, st);
+  if (s->has_obstacles && d.pf_copies > 1) silg::launch_pf_sync(d, st, K);
   mark(4 + kMarksPerIter * K);
 }
 
@@ -390,6 +393,9 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   d.n_mat = (int)p.mats.size();
   d.cap = std::max(1, o->contact_capacity);
   d.n_cr = std::max(0, o->n_cr_iters);
+  d.ncp = o->ncp;
+  d.precond = o->precond;
+  d.pf_copies = 1;
   d.h = p.h;
   d.h2f = (float)(p.h * p.h);
   for (int r = 0; r < 3; ++r) d.grav[r] = o->gravity[r];
@@ -550,7 +556,7 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   d.ct_dn = s->alloc<double>(cap);
   d.ct_df = s->alloc<double>(2 * (size_t)cap);
   d.ct_mu = s->alloc<double>(cap);
-  d.ct_r = s->alloc<double>(2 * (size_t)cap);
+  d.ct_r = s->alloc<double>(4 * (size_t)cap);
   d.ct_lam = s->alloc<double>(3 * (size_t)cap);
   d.ct_force = s->alloc<double>(3 * (size_t)cap);
   d.ct_omega = s->alloc<float>(3 * (size_t)cap);
@@ -696,6 +702,8 @@ int check_options(const sim_options* o) {
     return SIM_EINVAL;
   if (o->s_precision != SIM_S_FP32 && o->s_precision != SIM_S_BF16) return SIM_EINVAL;
   if (o->refine < 0 || o->refine > 2) return SIM_EINVAL;
+  if (o->ncp != SIM_NCP_FB && o->ncp != SIM_NCP_MINMAP) return SIM_EINVAL;
+  if (o->precond != SIM_PRECOND_DELASSUS && o->precond != SIM_PRECOND_MASS) return SIM_EINVAL;
   return SIM_OK;
 }
 
@@ -760,6 +768,40 @@ int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_opt
                                               : (sc.contact_margin > 0 ? sc.contact_margin : 0.5 * me));
       sd.L_ref.push_back(bbox_diagonal(m));
       for (int r = 0; r < 3; ++r) sd.hvel.push_back(m.handle_vel[r]);
+      {
+        // FNV-1a over everything that defines the scene (local numbering)
+        uint64_t hsh = 1469598103934665603ull;
+        auto mix = [&](const void* ptr, size_t bytes) {
+          const unsigned char* c = static_cast<const unsigned char*>(ptr);
+          for (size_t i = 0; i < bytes; ++i) hsh = (hsh ^ c[i]) * 1099511628211ull;
+        };
+        mix(&m.n_verts, sizeof(m.n_verts));
+        mix(m.rest_pos, sizeof(double) * 3 * (size_t)m.n_verts);
+        mix(m.tets, sizeof(int32_t) * 4 * (size_t)m.n_tets);
+        for (int t = 0; t < m.n_tets; ++t) {
+          const int mt = m.tet_material ? m.tet_material[t] : 0;
+          if (mt >= 0 && mt < sc.n_materials) {
+            const sim_material& ma = sc.materials[mt];
+            mix(&ma.model, sizeof(ma.model));
+            mix(&ma.E, sizeof(double));
+            mix(&ma.nu, sizeof(double));
+            mix(&ma.rho, sizeof(double));
+          }
+        }
+        if (m.n_pinned > 0) mix(m.pinned, sizeof(int32_t) * m.n_pinned);
+        mix(m.handle_vel, sizeof(m.handle_vel));
+        for (int q = 0; q < sc.n_obstacles; ++q) {
+          const sim_obstacle& ob = sc.obstacles[q];
+          mix(&ob.kind, sizeof(ob.kind));
+          mix(ob.p, sizeof(ob.p));
+          mix(ob.axis, sizeof(ob.axis));
+          mix(&ob.radius, sizeof(double));
+          mix(&ob.mu, sizeof(double));
+          mix(ob.vel, sizeof(ob.vel));
+        }
+        mix(&sd.margin.back(), sizeof(double));
+        s->scene_sig.push_back(hsh);
+      }
       voff += m.n_verts;
     }
     if (sd.obstacle_scene.empty()) sd.obstacle_scene.push_back(0);
@@ -846,6 +888,47 @@ int sim_set_warmstart(sim_t* s, const sim_mlp_t* net, int32_t mode) {
     if (e != cudaSuccess) return cuda_status(e);
   }
   s->d.ws_mode = mode;   // graphs are cached per mode; the network's weights are read at launch
+  return SIM_OK;
+}
+
+int sim_set_portfolio(sim_t* s, int32_t copies) {
+  if (!s || copies < 1) return SIM_EINVAL;
+  const Plan& p = s->plan;
+  if (p.n_scenes % copies) return SIM_EINVAL;
+  if (copies > 1) {
+    // the copies of a group must be the same scene: same vertex count, rest positions and
+    // pins, and the same internal numbering relative to the scene's first free vertex
+    std::vector<int> voff(p.n_scenes + 1, p.n_verts);
+    for (int v = p.n_verts - 1; v >= 0; --v) voff[p.vertex_scene[v]] = v;
+    for (int sc = p.n_scenes - 1; sc >= 0; --sc) voff[sc] = std::min(voff[sc], voff[sc + 1]);
+    for (int a = 0; a < p.n_scenes; a += copies)
+      for (int b = a + 1; b < a + copies; ++b) {
+        if (s->scene_sig[a] != s->scene_sig[b]) return SIM_EINVAL;
+        const int nv = voff[a + 1] - voff[a];
+        if (voff[b + 1] - voff[b] != nv) return SIM_EINVAL;
+        for (int i = 0; i < nv; ++i) {
+          const int va = voff[a] + i, vb = voff[b] + i;
+          if (p.pinned[va] != p.pinned[vb]) return SIM_EINVAL;
+          for (int r = 0; r < 3; ++r)
+            if (p.X[3 * (size_t)va + r] != p.X[3 * (size_t)vb + r]) return SIM_EINVAL;
+          if (!p.pinned[va] &&
+              p.internal[vb] - p.scene_vfirst[b] != p.internal[va] - p.scene_vfirst[a])
+            return SIM_EINVAL;
+        }
+      }
+  }
+  cudaSetDevice(s->device);
+  cudaError_t e = cudaStreamSynchronize(s->launch);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (s->d.pf_copies != copies) {
+    // kernels capture the device view by value: rebuild the frame graphs
+    for (auto& kv : s->graphs) {
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+      if (kv.second.g) cudaGraphDestroy(kv.second.g);
+    }
+    s->graphs.clear();
+    s->d.pf_copies = copies;
+  }
   return SIM_OK;
 }
 

@@ -7,7 +7,8 @@ collect    runs the plain method (cold start) over scenes and returns, per conta
 train      fits the network on the GPU (sim_mlp_train: the project's own tensor-core
            forward/backward kernels and Adam)
 evaluate   iterations and device milliseconds until the frame's residual reaches a
-           tolerance, per frame, for a given start (cold, previous frame, learned)
+           tolerance, per frame, for a given start (cold, previous frame, learned, or a
+           portfolio: the cold start and a warm start side by side, best of the two)
 """
 from __future__ import annotations
 
@@ -16,6 +17,8 @@ import numpy as np
 from . import SimError, Simulator, WarmStartNet
 
 MODES = {"cold": 0, "learned": 1, "previous": 2}
+# portfolio starts: two copies of the scene in one batch, copy 0 cold, copy 1 this start
+PORTFOLIO = {"portfolio": 1, "portfolio_previous": 2}
 
 
 def collect(scenes, frames, n_iters=20, tol=1e-4, **opts):
@@ -71,8 +74,11 @@ def evaluate_from_states(scenes, frames, modes, net=None, k_max=40, tol=1e-4, **
     start in `modes` from the reference state of the frame before it (one cold frame to set
     up the previous frame's impulses, then the frame under test). Returns, per mode, the
     iterations until the residual reaches tol (k_max + 1 if never) and the device time to
-    get there, over the same frames."""
+    get there, over the same frames. A portfolio mode runs the frame as a two-copy batch
+    (sim_set_portfolio) and reaches tol at the first iteration where either copy does; its
+    time is the batch's."""
     out = {m: {"iters": [], "ms": [], "res": []} for m in modes}
+    pf_modes = [m for m in modes if m in PORTFOLIO]
     for sc in scenes:
         ref = Simulator(sc, n_iters=k_max, **opts)
         states = [ref.state()]
@@ -86,33 +92,46 @@ def evaluate_from_states(scenes, frames, modes, net=None, k_max=40, tol=1e-4, **
                 break
         ref.close()
         sim = Simulator(sc, n_iters=k_max, **opts)
+        pf = None
+        if pf_modes:
+            pf = Simulator([sc, sc], n_iters=k_max, **opts)
+            pf.set_portfolio(2)
         for f in range(1, len(contact)):
             if not contact[f]:
                 continue
             for m in modes:
+                s_m = pf if m in PORTFOLIO else sim
+                state = states[f - 1]
+                if s_m is pf:
+                    state = tuple(np.concatenate([a, a]) for a in state)
                 try:
-                    sim.set_state(*states[f - 1])
-                    sim.set_warmstart(0)
-                    sim.step()                      # frame f - 1: the previous impulses
-                    sim.set_warmstart(MODES[m] if isinstance(m, str) else int(m), net)
-                    sim.step()                      # frame f from the reference state
-                    st = sim.stats()
+                    s_m.set_state(*state)
+                    s_m.set_warmstart(0)
+                    s_m.step()                      # frame f - 1: the previous impulses
+                    mode = PORTFOLIO[m] if s_m is pf else MODES[m] if isinstance(m, str) else int(m)
+                    s_m.set_warmstart(mode, net)
+                    s_m.step()                      # frame f from the reference state
+                    st = s_m.stats()
+                    # a portfolio reaches the tolerance when either copy does
+                    r = (s_m.scene_residuals().min(axis=0) if s_m is pf
+                         else np.asarray(st["residuals"]))
                 except SimError:
                     out[m]["iters"].append(k_max + 1)
                     out[m]["ms"].append(np.nan)
                     out[m]["res"].append(np.full(k_max + 1, np.nan))
                     continue
-                r = np.asarray(st["residuals"])
                 out[m]["res"].append(r[:k_max + 1])
                 hit = np.nonzero(r <= tol)[0]
                 k = int(hit[0]) if len(hit) else k_max + 1
-                ph = sim.phase_times()
+                ph = s_m.phase_times()
                 per_iter = sum(ph[p] for p in ("local", "assemble", "spmv1", "solve", "spmv2",
                                                "reduce")) / k_max
                 start = ph["collide"] + ph["delassus"] + ph["warmstart"]
                 out[m]["iters"].append(k)
                 out[m]["ms"].append(start + min(k, k_max) * per_iter + ph["integrate"])
         sim.close()
+        if pf is not None:
+            pf.close()
     res = {}
     for m, d in out.items():
         it, ms = np.asarray(d["iters"]), np.asarray(d["ms"])

@@ -115,8 +115,19 @@ def test_create_without_a_gpu_fails_loudly():
 
 
 @pytest.mark.parametrize("opts", [{"s_precision": 2}, {"s_precision": -1}, {"refine": 3},
-                                  {"refine": -1}, {"n_iters": 65}, {"contact_capacity": 0}])
+                                  {"refine": -1}, {"n_iters": 65}, {"contact_capacity": 0},
+                                  {"ncp": 2}, {"ncp": -1}, {"precond": 2}])
 def test_invalid_options_are_rejected_before_any_device_work(opts):
     with pytest.raises(SimError) as e:
         Simulator(sg.cube_drop(m=3), **opts)
     assert e.value.status == -1
+
+
+def test_named_options_map_to_the_abi_values():
+    from paper_2503_15078_b300 import _options
+    o = _options(sg.cube_drop(m=3), ncp="minmap", precond="mass")
+    assert (o.ncp, o.precond) == (1, 1)
+    o = _options(sg.cube_drop(m=3))
+    assert (o.ncp, o.precond) == (0, 0)
+    with pytest.raises(ValueError):
+        _options(None, ncp="newton")
