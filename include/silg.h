@@ -117,6 +117,12 @@ typedef struct {
                                   measure for every choice: min(delta_n, r_n lambda_n) and
                                   h phi_f with the FB E_f, r from the Delassus diagonal. */
   int32_t precond;             /* SIM_PRECOND_DELASSUS (default) or SIM_PRECOND_MASS      */
+  double residual_tol;         /* > 0: sim_step with n_iters <= 0 iterates until the
+                                  residual R_k (sim_stats) is <= residual_tol, at least one
+                                  update and at most max_iters, decided on the device (a
+                                  CUDA graph while-node); 0 (default): n_iters <= 0 means
+                                  the option's n_iters. Negative or NaN: SIM_EINVAL.     */
+  int32_t max_iters;           /* cap of those iterations, 1..63 (default 40)             */
 } sim_options;
 
 /* Launch configuration of the two profile products (z = S g, x = S^T y), chosen by the
@@ -163,7 +169,11 @@ enum { SIM_PHASE_COLLIDE = 0,   /* prediction and collision detection (App. A.1)
        SIM_PHASE_REDUCE = 8,    /* fixed-order sums of both products' partial sums (and a
                                    BF16 residual correction)                              */
        SIM_PHASE_WARMSTART = 9, /* warm-start features, guess and its acceptance          */
-       SIM_NUM_PHASES = 10 };
+       SIM_PHASE_ITERATIONS = 10, /* a frame to a tolerance: all its iterations (the loop's
+                                  body has no phase marks; phases 2-6 and 8 are then 0;
+                                  integration includes the final evaluation). 0 in frames
+                                  of a fixed iteration count.                            */
+       SIM_NUM_PHASES = 11 };
 
 /* Sizes of the precomputed structure (Theorem 1 profile of S). */
 typedef struct {
@@ -248,7 +258,9 @@ int sim_get_tuning(const sim_t* sim, sim_tuning* out);
 void sim_destroy(sim_t* sim);
 
 /* One frame of Alg. 4 with n_iters local-global iterations (n_iters <= 0: the option's
- * value). Asynchronous on the handle's stream. */
+ * n_iters, or, if sim_options.residual_tol > 0, iterations until R_k <= residual_tol: at
+ * least 1 and at most max_iters, the stopping decision taken on the device; sim_stats
+ * reports the count). Asynchronous on the handle's stream. */
 int sim_step(sim_t* sim, int32_t n_iters);
 /* Wait for the handle's stream; returns the first device-side error, if any. */
 int sim_synchronize(sim_t* sim);

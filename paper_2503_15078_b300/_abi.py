@@ -11,9 +11,9 @@ SIM_OK = 0
 STATUS = {0: "SIM_OK", -1: "SIM_EINVAL", -2: "SIM_ENOMEM", -3: "SIM_ENOTSPD", -4: "SIM_ECUDA",
           -5: "SIM_ECAPACITY", -6: "SIM_ETIMEOUT", -7: "SIM_ENONFINITE", -8: "SIM_ENOTSUP"}
 SIM_MAX_RESIDUALS = 64
-SIM_NUM_PHASES = 10
+SIM_NUM_PHASES = 11
 PHASES = ["collide", "delassus", "local", "assemble", "spmv1", "solve", "spmv2", "integrate",
-          "reduce", "warmstart"]
+          "reduce", "warmstart", "iterations"]
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
@@ -48,7 +48,8 @@ class SimOptions(C.Structure):
                 ("gravity", C.c_double * 3), ("contact_margin", C.c_double),
                 ("spin_limit", C.c_uint64), ("cuda_stream", C.c_void_p),
                 ("n_host_threads", C.c_int32), ("autotune", C.c_int32),
-                ("ncp", C.c_int32), ("precond", C.c_int32)]
+                ("ncp", C.c_int32), ("precond", C.c_int32),
+                ("residual_tol", C.c_double), ("max_iters", C.c_int32)]
 
 
 class SimTuning(C.Structure):

@@ -44,6 +44,8 @@ void sim_default_options(sim_options* o) {
   o->autotune = 0;
   o->ncp = SIM_NCP_FB;
   o->precond = SIM_PRECOND_DELASSUS;
+  o->residual_tol = 0.0;
+  o->max_iters = 40;
 }
 
 int sim_plan_create(const sim_mesh* mesh, const sim_material* mats, int32_t n_mat, double h,

@@ -44,6 +44,12 @@ struct DevSim {
   int n, n_all, n_tets, n_pad, n_obs, n_mat;
   int cap, cap_y, n_cr;
   int ncp, precond;  // SIM_NCP_*, SIM_PRECOND_*
+  // iterating to a tolerance (sim_options.residual_tol > 0, sim_step with n_iters <= 0): the
+  // device counts the finished global updates and a CUDA graph while-node repeats the
+  // iteration until R_k <= res_tol or max_iters updates
+  int* iter_k;
+  double res_tol;
+  int max_iters;
   int n_rg, n_ct;
   double h;
   float h2f;        // h^2 in FP32
@@ -231,7 +237,14 @@ inline long long wt_items_max(int cap, int grid) {
   return best;
 }
 void launch_local(const DevSim& d, cudaStream_t s, bool debug_p);
+// k < 0: the iteration index is read from d.iter_k (frames that iterate to a tolerance)
 void launch_contact_eval(const DevSim& d, cudaStream_t s, int k, bool final_eval);
+// frames that iterate to a tolerance: count one more finished update; set the while-node's
+// condition (continue while k < max_iters, R_k > res_tol and no device error); clear the
+// residual entries of the current k (before a final correction re-evaluates them)
+void launch_iter_advance(const DevSim& d, cudaStream_t s);
+void launch_iter_decide(const DevSim& d, cudaStream_t s, cudaGraphConditionalHandle h);
+void launch_iter_clear(const DevSim& d, cudaStream_t s);
 void launch_rhs(const DevSim& d, cudaStream_t s);
 // z = S~ g: the product (partial sums) and the fixed-order reduction into zvec
 void launch_pass1(const DevSim& d, cudaStream_t s);
@@ -262,6 +275,7 @@ void launch_ws_record(const DevSim& d, cudaStream_t s);
 int ws_kernels(int mode);   // launches of launch_ws_start
 // portfolio: every copy of a group takes the state of the copy with the lowest final
 // residual after a K-iteration frame (one launch)
+// (K < 0: read from d.iter_k)
 void launch_pf_sync(const DevSim& d, cudaStream_t s, int K);
 void launch_scan(const int* in, int* out, int n, const int* n_dev, int* total, cudaStream_t s);
 int cr_setup(int n_scenes, int* cluster_out, size_t* smem_out);

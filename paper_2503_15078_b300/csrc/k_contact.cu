@@ -541,6 +541,7 @@ __global__ void k_contact_eval(DevSim d, int k, int final_eval) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   int c = min(d.counters[kCntContacts], d.cap);
   if (j >= c) return;
+  if (k < 0) k = *d.iter_k;
   const int v = d.ct_vert[j];
   const double h = d.h;
   double D[9];
@@ -1063,6 +1064,49 @@ void launch_contact_eval(const DevSim& d, cudaStream_t s, int k, bool final_eval
   // FP64-heavy and short: small CTAs spread the contacts over many SMs
   k_contact_eval<<<(d.cap + 31) / 32, 32, 0, s>>>(d, k, final_eval ? 1 : 0);
 }
+
+namespace {
+
+__global__ void k_iter_advance(DevSim d) {
+  if (threadIdx.x == 0) *d.iter_k += 1;
+}
+
+// one thread: whether the while-node runs another iteration. It always terminates the loop
+// at max_iters (<= kMaxIters) finished updates, whatever the residuals hold. The residual
+// is the worst scene's; with a portfolio, a group counts with its best copy.
+__global__ void k_iter_decide(DevSim d, cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0) return;
+  const int k = *d.iter_k;
+  double r = d.resid[k];
+  if (d.pf_copies > 1) {
+    r = 0.0;
+    for (int g0 = 0; g0 < d.n_scenes; g0 += d.pf_copies) {
+      double best = INFINITY;
+      for (int c = 0; c < d.pf_copies; ++c)
+        best = fmin(best, d.resid_scene[(g0 + c) * (kMaxIters + 1) + k]);
+      r = fmax(r, best);
+    }
+  }
+  const bool more = k < d.max_iters && !(r <= d.res_tol) && *d.err == 0;
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+__global__ void k_iter_clear(DevSim d) {
+  const int k = *d.iter_k;
+  if (blockIdx.x == 0 && threadIdx.x == 0) d.resid[k] = 0.0;
+  for (int sc = threadIdx.x; sc < d.n_scenes; sc += blockDim.x)
+    d.resid_scene[sc * (kMaxIters + 1) + k] = 0.0;
+}
+
+}  // namespace
+
+void launch_iter_advance(const DevSim& d, cudaStream_t s) { k_iter_advance<<<1, 32, 0, s>>>(d); }
+
+void launch_iter_decide(const DevSim& d, cudaStream_t s, cudaGraphConditionalHandle h) {
+  k_iter_decide<<<1, 32, 0, s>>>(d, h);
+}
+
+void launch_iter_clear(const DevSim& d, cudaStream_t s) { k_iter_clear<<<1, 256, 0, s>>>(d); }
 
 void launch_ytz(const DevSim& d, cudaStream_t s) {
   k_ytz<<<std::min(d.cap, 8 * d.n_sm), kYtzThreads, 0, s>>>(d);

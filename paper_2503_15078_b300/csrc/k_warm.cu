@@ -212,6 +212,7 @@ __global__ void k_ws_record(DevSim d) {
 __global__ void k_pf_sync(DevSim d, int K) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= d.n) return;
+  if (K < 0) K = *d.iter_k;
   const int sc = d.vert_scene[v], C = d.pf_copies, g0 = sc - sc % C;
   int best = g0;
   double rb = INFINITY;

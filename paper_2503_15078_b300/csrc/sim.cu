@@ -36,6 +36,8 @@ struct sim_s {
   int device = 0;
   cudaStream_t work = nullptr;    // private stream: captures and component calls
   cudaStream_t aux = nullptr;     // second branch of the frame graph (captured from work)
+  cudaStream_t body = nullptr;    // capture of a while-node's body (frames to a tolerance)
+  cudaStream_t body_aux = nullptr;// and its second branch
   std::vector<cudaEvent_t> fj;    // fork/join events of the frame graph's branches
   double* pinned = nullptr;       // page-locked staging of q and v (2 x 3 n_verts) for the
                                   // state accessors
@@ -47,7 +49,8 @@ struct sim_s {
   std::map<int, Graph> graphs;
   std::vector<void*> allocs;
   int64_t frame = 0;
-  int last_iters = 0;
+  int last_iters = 0;             // -1: a frame to a tolerance whose count is on the device
+  bool last_to_tol = false;       // the most recent frame iterated to a tolerance
   // phase events recorded by event nodes of the frame graph: [0] frame start,
   // [1] after collision, [2] after Delassus, [3] after the warm start, then kMarksPerIter
   // per iteration, then [end]
@@ -82,6 +85,8 @@ struct sim_s {
     for (cudaEvent_t e : fj) cudaEventDestroy(e);
     if (pinned) cudaFreeHost(pinned);
     if (aux) cudaStreamDestroy(aux);
+    if (body) cudaStreamDestroy(body);
+    if (body_aux) cudaStreamDestroy(body_aux);
     if (work) cudaStreamDestroy(work);
   }
 };
@@ -115,6 +120,29 @@ int sync_and_check(sim_s* s) {
 int refined_iters(const sim_s* s, int K) {
   if (!s->d.s_bf16 || s->d.refine <= 0) return 0;
   return s->d.refine >= 2 ? K : 1;
+}
+
+// finished updates of the most recent frame (read from the device after a frame to a
+// tolerance); -1 on a CUDA error
+int frame_iters(sim_s* s) {
+  if (s->last_iters >= 0) return s->last_iters;
+  int k = 0;
+  if (cudaStreamSynchronize(s->launch) != cudaSuccess ||
+      cudaMemcpy(&k, s->d.iter_k, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return -1;
+  s->last_iters = k;
+  return k;
+}
+
+// launches of a frame to a tolerance that made K updates (enqueue_frame_to_tolerance)
+int kernels_per_frame_to_tolerance(const sim_s* s, int K) {
+  const bool c = s->has_obstacles;
+  const int refine_body = s->d.s_bf16 && s->d.refine >= 2 ? 5 : 0;
+  const int refine_end = s->d.s_bf16 && s->d.refine == 1 ? 6 : 0;
+  const int before = 1 + (c ? 4 + 12 + silg::ws_kernels(s->d.ws_mode) : 0) + 1 + (c ? 1 : 0);
+  const int body = 1 + 2 + (c ? 3 : 0) + 2 + refine_body + 1 + (c ? 1 : 0) + 1 + 1;
+  const int after = refine_end + (c ? 1 : 0) + 1 + (c && s->d.pf_copies > 1 ? 1 : 0);
+  return before + K * body + after;
 }
 
 int kernels_per_frame(const sim_s* s, int K) {
@@ -213,7 +241,130 @@ void enqueue_frame(sim_s* s, int K, cudaStream_t st) {
   mark(4 + kMarksPerIter * K);
 }
 
-// frame graphs are cached per (iteration count, warm-start mode)
+// A frame that iterates until the residual reaches sim_options.residual_tol (at least one
+// update, at most max_iters): the same kernels as enqueue_frame, with the iterations in the
+// body of a CUDA graph while-node. The body runs the rest of iteration k (right-hand side,
+// products, constraint solve), counts the update on the device, evaluates the next iterate
+// (contact terms beside the local step) and lets a one-thread kernel set the node's
+// condition from R_{k+1}. Event nodes are not allowed in a conditional body, so phase
+// marks stand only around the loop. Returns a CUDA error, or cudaSuccess.
+cudaError_t enqueue_frame_to_tolerance(sim_s* s, cudaStream_t st) {
+  const DevSim& d = s->d;
+  auto mark = [&](int i) { cudaEventRecordWithFlags(s->ev[i], st, cudaEventRecordExternal); };
+  int n_fj = 0;
+  auto fork = [&](cudaStream_t from, cudaStream_t to) {
+    cudaEventRecord(s->fj[n_fj], from);
+    cudaStreamWaitEvent(to, s->fj[n_fj], 0);
+    ++n_fj;
+  };
+  auto join = [&](cudaStream_t from, cudaStream_t to) { fork(from, to); };
+  mark(0);
+  cudaMemsetAsync(d.resid, 0, sizeof(double) * (silg::kMaxIters + 1), st);
+  cudaMemsetAsync(d.resid_scene, 0, sizeof(double) * (silg::kMaxIters + 1) * d.n_scenes, st);
+  cudaMemsetAsync(d.max_pen, 0, sizeof(double), st);
+  cudaMemsetAsync(d.iter_k, 0, sizeof(int), st);
+  silg::launch_frame_begin(d, st);
+  const bool early_local = s->has_obstacles && d.ws_mode == 0;
+  if (early_local) {
+    fork(st, s->aux);
+    silg::launch_local(d, s->aux, false);
+  }
+  if (s->has_obstacles) silg::launch_collide(d, st);
+  mark(1);
+  if (s->has_obstacles) silg::launch_delassus(d, st);
+  mark(2);
+  if (s->has_obstacles) {
+    silg::launch_ws_features(d, st);
+    silg::launch_ws_start(d, st);
+  }
+  mark(3);
+  // the top of iteration 0
+  if (early_local) {
+    silg::launch_contact_eval(d, st, 0, false);
+    join(s->aux, st);
+  } else if (s->has_obstacles) {
+    fork(st, s->aux);
+    silg::launch_contact_eval(d, s->aux, 0, false);
+    silg::launch_local(d, st, false);
+    join(s->aux, st);
+  } else {
+    silg::launch_local(d, st, false);
+  }
+  // the while-node, its condition 1 at every launch (at least one update)
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t n_deps = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &n_deps);
+  if (e != cudaSuccess) return e;
+  cudaGraphConditionalHandle h;
+  e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t loop;
+  e = cudaGraphAddNode(&loop, g, deps, nullptr, n_deps, &cp);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  e = cudaStreamUpdateCaptureDependencies(st, &loop, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e != cudaSuccess) return e;
+  {
+    cudaStream_t b = s->body, ba = s->body_aux;
+    e = cudaStreamBeginCaptureToGraph(b, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    silg::launch_rhs(d, b);
+    silg::launch_pass1(d, b);
+    silg::launch_reduce1(d, b);
+    if (s->has_obstacles) {
+      silg::launch_ytz(d, b);
+      silg::launch_cr(d, b, s->cluster);
+      silg::launch_yu(d, b);
+    }
+    silg::launch_pass2(d, b);
+    silg::launch_reduce2(d, b, silg::kOutDq);
+    if (d.s_bf16 && d.refine >= 2) {
+      silg::launch_residual(d, b, s->has_obstacles ? silg::kResFrameContact : silg::kResFrame);
+      DevSim dr = d;
+      dr.gvec = d.gsave;
+      silg::launch_solve(dr, b, silg::kOutAddDq);
+    }
+    silg::launch_iter_advance(d, b);
+    if (s->has_obstacles) {
+      fork(b, ba);
+      silg::launch_contact_eval(d, ba, -1, false);
+      silg::launch_local(d, b, false);
+      join(ba, b);
+    } else {
+      silg::launch_local(d, b, false);
+    }
+    silg::launch_iter_decide(d, b, h);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(b, &captured);
+    if (e != cudaSuccess) return e;
+  }
+  mark(4);
+  if (d.s_bf16 && d.refine == 1) {
+    // the correction after the last update; its residual entries are evaluated again
+    silg::launch_iter_clear(d, st);
+    silg::launch_residual(d, st, s->has_obstacles ? silg::kResFrameContact : silg::kResFrame);
+    DevSim dr = d;
+    dr.gvec = d.gsave;
+    silg::launch_solve(dr, st, silg::kOutAddDq);
+  }
+  if (s->has_obstacles) {
+    silg::launch_contact_eval(d, st, -1, true);
+    silg::launch_ws_record(d, st);
+  }
+  silg::launch_integrate(d, st);
+  if (s->has_obstacles && d.pf_copies > 1) silg::launch_pf_sync(d, st, -1);
+  mark(5);
+  return cudaGetLastError();
+}
+
+// frame graphs are cached per (iteration count, warm-start mode); K = 0: to a tolerance
 int get_graph(sim_s* s, int K, cudaGraphExec_t* out) {
   const int key = 4 * K + s->d.ws_mode;
   auto it = s->graphs.find(key);
@@ -224,8 +375,16 @@ int get_graph(sim_s* s, int K, cudaGraphExec_t* out) {
   Graph g;
   cudaError_t e = cudaStreamBeginCapture(s->work, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_status(e);
-  enqueue_frame(s, K, s->work);
+  cudaError_t eq = cudaSuccess;
+  if (K > 0)
+    enqueue_frame(s, K, s->work);
+  else
+    eq = enqueue_frame_to_tolerance(s, s->work);
   e = cudaStreamEndCapture(s->work, &g.g);
+  if (eq != cudaSuccess) {
+    if (e == cudaSuccess) cudaGraphDestroy(g.g);
+    return cuda_status(eq);
+  }
   if (e != cudaSuccess) return cuda_status(e);
   e = cudaGraphInstantiate(&g.exec, g.g, 0);
   if (e != cudaSuccess) {
@@ -396,6 +555,8 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   d.ncp = o->ncp;
   d.precond = o->precond;
   d.pf_copies = 1;
+  d.res_tol = o->residual_tol;
+  d.max_iters = o->max_iters;
   d.h = p.h;
   d.h2f = (float)(p.h * p.h);
   for (int r = 0; r < 3; ++r) d.grav[r] = o->gravity[r];
@@ -585,6 +746,7 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   d.wt = s->alloc<float>((size_t)cap * ((cap + 3) & ~3));
   d.resid = s->alloc<double>(silg::kMaxIters + 1);
   d.max_pen = s->alloc<double>(1);
+  d.iter_k = s->alloc<int>(1);
   d.err = s->alloc<int>(1);
   d.p_out = s->alloc<float>(9 * (size_t)T);
   s->has_obstacles = n_obs > 0;
@@ -703,6 +865,8 @@ int check_options(const sim_options* o) {
   if (o->s_precision != SIM_S_FP32 && o->s_precision != SIM_S_BF16) return SIM_EINVAL;
   if (o->refine < 0 || o->refine > 2) return SIM_EINVAL;
   if (o->ncp != SIM_NCP_FB && o->ncp != SIM_NCP_MINMAP) return SIM_EINVAL;
+  if (!(o->residual_tol >= 0.0) || o->max_iters < 1 || o->max_iters > silg::kMaxIters)
+    return SIM_EINVAL;
   if (o->precond != SIM_PRECOND_DELASSUS && o->precond != SIM_PRECOND_MASS) return SIM_EINVAL;
   return SIM_OK;
 }
@@ -824,7 +988,9 @@ int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_opt
     s->device = o->device;
     if (cudaSetDevice(s->device) != cudaSuccess) return SIM_ECUDA;
     if (cudaStreamCreateWithFlags(&s->work, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking) != cudaSuccess)
+        cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->body, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->body_aux, cudaStreamNonBlocking) != cudaSuccess)
       return SIM_ECUDA;
     if (cudaMallocHost(&s->pinned, sizeof(double) * 6 * (size_t)std::max<long long>(1, nv_tot)) !=
         cudaSuccess)
@@ -974,7 +1140,8 @@ int sim_get_scene_residuals(sim_t* s, int32_t capacity, double* out) {
   cudaSetDevice(s->device);
   int st = sync_and_check(s);
   if (st == SIM_ECUDA) return st;
-  const int K = s->last_iters, S = s->plan.n_scenes;
+  const int K = frame_iters(s), S = s->plan.n_scenes;
+  if (K < 0) return SIM_ECUDA;
   std::vector<double> r((size_t)S * (silg::kMaxIters + 1));
   cudaError_t e = cudaMemcpy(r.data(), s->d.resid_scene, r.size() * sizeof(double),
                              cudaMemcpyDeviceToHost);
@@ -996,7 +1163,9 @@ void sim_destroy(sim_t* s) {
 
 int sim_step(sim_t* s, int32_t n_iters) {
   if (!s) return SIM_EINVAL;
-  int K = n_iters > 0 ? n_iters : s->n_iters_default;
+  // n_iters <= 0 with a residual tolerance: iterate to it (K = 0 selects that graph)
+  const bool to_tol = n_iters <= 0 && s->d.res_tol > 0.0;
+  int K = to_tol ? 0 : (n_iters > 0 ? n_iters : s->n_iters_default);
   if (K > silg::kMaxIters) return SIM_EINVAL;
   cudaSetDevice(s->device);
   cudaGraphExec_t exec = nullptr;
@@ -1005,7 +1174,8 @@ int sim_step(sim_t* s, int32_t n_iters) {
   cudaError_t e = cudaGraphLaunch(exec, s->launch);
   if (e != cudaSuccess) return cuda_status(e);
   s->frame += 1;
-  s->last_iters = K;
+  s->last_iters = to_tol ? -1 : K;
+  s->last_to_tol = to_tol;
   return SIM_OK;
 }
 
@@ -1071,6 +1241,7 @@ int sim_get_stats(sim_t* s, sim_stats* out) {
   cudaSetDevice(s->device);
   int st = sync_and_check(s);
   if (st == SIM_ECUDA) return st;
+  if (frame_iters(s) < 0) return SIM_ECUDA;
   std::memset(out, 0, sizeof(*out));
   int cnt[silg::kNumCounters];
   double res[silg::kMaxIters + 1];
@@ -1083,7 +1254,9 @@ int sim_get_stats(sim_t* s, sim_stats* out) {
   out->n_iters = s->last_iters;
   out->n_residuals = s->has_obstacles && s->frame > 0 ? s->last_iters + 1 : 0;
   for (int k = 0; k < out->n_residuals; ++k) out->residual[k] = res[k];
-  out->kernels_per_frame = kernels_per_frame(s, s->last_iters > 0 ? s->last_iters : s->n_iters_default);
+  out->kernels_per_frame = s->last_to_tol ? kernels_per_frame_to_tolerance(s, s->last_iters)
+                                          : kernels_per_frame(s, s->last_iters > 0 ? s->last_iters
+                                                                                   : s->n_iters_default);
   return st;
 }
 
@@ -1092,14 +1265,24 @@ int sim_get_phase_times(sim_t* s, double* ms) {
   cudaSetDevice(s->device);
   for (int k = 0; k < SIM_NUM_PHASES; ++k) ms[k] = 0.0;
   if (s->frame == 0 || s->last_iters == 0) return SIM_OK;
-  const int K = s->last_iters;
-  cudaError_t e = cudaEventSynchronize(s->ev[4 + kMarksPerIter * K]);
-  if (e != cudaSuccess) return cuda_status(e);
   auto el = [&](int a, int b) {
     float t = 0.f;
     cudaEventElapsedTime(&t, s->ev[a], s->ev[b]);
     return (double)t;
   };
+  if (s->last_to_tol) {
+    cudaError_t e = cudaEventSynchronize(s->ev[5]);
+    if (e != cudaSuccess) return cuda_status(e);
+    ms[SIM_PHASE_COLLIDE] = el(0, 1);
+    ms[SIM_PHASE_DELASSUS] = el(1, 2);
+    ms[SIM_PHASE_WARMSTART] = el(2, 3);
+    ms[SIM_PHASE_ITERATIONS] = el(3, 4);
+    ms[SIM_PHASE_INTEGRATE] = el(4, 5);
+    return SIM_OK;
+  }
+  const int K = s->last_iters;
+  cudaError_t e = cudaEventSynchronize(s->ev[4 + kMarksPerIter * K]);
+  if (e != cudaSuccess) return cuda_status(e);
   ms[SIM_PHASE_COLLIDE] = el(0, 1);
   ms[SIM_PHASE_DELASSUS] = el(1, 2);
   ms[SIM_PHASE_WARMSTART] = el(2, 3);

@@ -8,7 +8,8 @@ train      fits the network on the GPU (sim_mlp_train: the project's own tensor-
            forward/backward kernels and Adam)
 evaluate   iterations and device milliseconds until the frame's residual reaches a
            tolerance, per frame, for a given start (cold, previous frame, learned, or a
-           portfolio: the cold start and a warm start side by side, best of the two)
+           portfolio: the cold start and a warm start side by side, best of the two);
+           evaluate_to_tolerance measures the same with frames that stop on the device
 """
 from __future__ import annotations
 
@@ -140,6 +141,65 @@ def evaluate_from_states(scenes, frames, modes, net=None, k_max=40, tol=1e-4, **
                   "unreached": int((it > k_max).sum()),
                   "mean_ms": float(np.nanmean(ms)) if len(ms) else 0.0,
                   "iters": it.tolist(), "residuals": np.asarray(d["res"])}
+    return res
+
+
+def evaluate_to_tolerance(scenes, frames, modes, net=None, k_max=40, tol=1e-4, **opts):
+    """The A/B of evaluate_from_states with frames that stop on the device when the residual
+    reaches tol (sim_options.residual_tol; at least one update, at most k_max): per mode the
+    updates each contact frame took and its measured device time (the whole frame: collision,
+    Delassus, start, iterations, integration). A portfolio stops when either copy is done."""
+    out = {m: {"iters": [], "ms": []} for m in modes}
+    for sc in scenes:
+        ref = Simulator(sc, n_iters=k_max, **opts)
+        states = [ref.state()]
+        contact = []
+        for _ in range(frames):
+            try:
+                ref.step()
+                contact.append(ref.stats()["n_contacts"] > 0)
+                states.append(ref.state())
+            except SimError:
+                break
+        ref.close()
+        sims = {}
+        for m in modes:
+            pf = m in PORTFOLIO
+            sim = Simulator([sc, sc] if pf else sc, n_iters=k_max, residual_tol=tol,
+                            max_iters=k_max, **opts)
+            if pf:
+                sim.set_portfolio(2)
+            sims[m] = sim
+        for f in range(1, len(contact)):
+            if not contact[f]:
+                continue
+            for m in modes:
+                sim = sims[m]
+                state = states[f - 1]
+                if m in PORTFOLIO:
+                    state = tuple(np.concatenate([a, a]) for a in state)
+                try:
+                    sim.set_state(*state)
+                    sim.set_warmstart(0)
+                    sim.step(n_iters=k_max)         # frame f - 1: the previous impulses
+                    sim.set_warmstart(PORTFOLIO.get(m, MODES.get(m, 0)), net)
+                    sim.step()                      # frame f, to the tolerance
+                    k = sim.stats()["n_iters"]
+                    ms = sum(sim.phase_times().values())
+                except SimError:
+                    k, ms = k_max + 1, np.nan
+                out[m]["iters"].append(k)
+                out[m]["ms"].append(ms)
+        for sim in sims.values():
+            sim.close()
+    res = {}
+    for m, d in out.items():
+        it, ms = np.asarray(d["iters"]), np.asarray(d["ms"])
+        res[m] = {"frames": int(len(it)), "mean_iters": float(it.mean()) if len(it) else 0.0,
+                  "median_iters": float(np.median(it)) if len(it) else 0.0,
+                  "at_cap": int((it >= k_max).sum()),
+                  "mean_ms": float(np.nanmean(ms)) if len(ms) else 0.0,
+                  "median_ms": float(np.nanmedian(ms)) if len(ms) else 0.0}
     return res
 
 
