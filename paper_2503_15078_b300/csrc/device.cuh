@@ -59,6 +59,7 @@ struct DevSim {
   const int* vert_scene;      // n_all (internal numbering)
   const int* scene_vfirst;    // n_scenes + 1: first internal free vertex of each scene
   const int* obst_scene;      // n_obs: the scene an obstacle acts on
+  const int* scene_ofirst;    // n_scenes + 1: each scene's obstacles are [first, next first)
   const double* scene_margin; // contact margin
   const double* scene_Lref;   // rest bounding-box diagonal (residual scale)
   const double* scene_hvel;   // 3 per scene: velocity of the scene's pinned vertices

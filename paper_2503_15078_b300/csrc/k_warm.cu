@@ -231,7 +231,8 @@ __global__ void k_pf_sync(DevSim d, int K) {
     d.prev_force[3 * v + r] = d.prev_force[3 * w + r];
   }
   d.prev_valid[v] = d.prev_valid[w];
-  d.prev_obst[v] = d.prev_obst[w];
+  // the same obstacle of this copy (copies list their obstacles in the same order)
+  d.prev_obst[v] = d.prev_obst[w] - d.scene_ofirst[best] + d.scene_ofirst[sc];
   d.prev_move[v] = d.prev_move[w];
 }
 

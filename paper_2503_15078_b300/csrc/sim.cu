@@ -569,6 +569,13 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   }
   d.scene_vfirst = s->upload(p.scene_vfirst);
   d.obst_scene = s->upload(sd.obstacle_scene);
+  {
+    // obstacles are listed scene by scene
+    std::vector<int> of(p.n_scenes + 1, n_obs);
+    for (int q = n_obs - 1; q >= 0; --q) of[sd.obstacle_scene[q]] = q;
+    for (int sc = p.n_scenes - 1; sc >= 0; --sc) of[sc] = std::min(of[sc], of[sc + 1]);
+    d.scene_ofirst = s->upload(of);
+  }
   d.scene_margin = s->upload(sd.margin);
   d.scene_Lref = s->upload(sd.L_ref);
   d.scene_hvel = s->upload(sd.hvel);

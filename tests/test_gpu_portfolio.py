@@ -89,3 +89,28 @@ def test_portfolio_continues_from_the_better_copy():
     winner = q_cold[:n] if r_pf[0, -1] <= r_pf[1, -1] else q_prev[n:]
     assert np.array_equal(q_pf[:n], winner)
     assert r_pf[0, -1] != r_pf[1, -1]
+
+
+def test_warm_copy_starts_like_a_single_scene():
+    # after a synchronised frame the warm copy must see the previous frame's impulses at its
+    # own obstacles: its start (residual at k = 0) matches a single scene's warm start, not
+    # the cold start
+    sc = sg.warmstart_scenes([100], frames=60)[0]
+    q, v = _contact_state(sc)
+    one = Simulator(sc, n_iters=6)
+    one.set_state(q, v)
+    one.step()
+    one.set_warmstart(2)
+    one.step()
+    r_one = one.scene_residuals()[0]
+    pf = Simulator([sc, sc], n_iters=6)
+    pf.set_portfolio(2)
+    pf.set_state(np.concatenate([q, q]), np.concatenate([v, v]))
+    pf.step()
+    pf.set_warmstart(2)
+    pf.step()
+    r_pf = pf.scene_residuals()
+    assert abs(r_pf[1, 0] - r_one[0]) <= 1e-3 * r_one[0]
+    assert abs(r_pf[1, 0] - r_pf[0, 0]) > 1e-2 * r_pf[0, 0]
+    one.close()
+    pf.close()
