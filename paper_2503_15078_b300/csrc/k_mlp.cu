@@ -123,10 +123,16 @@ __device__ __forceinline__ void load_bias(const float* th, float* bias) {
   }
 }
 
+// global -> shared, 16-byte aligned, bytes a multiple of 16: asynchronous copies, all in
+// flight at once, then one wait (the callers synchronise the CTA before reading)
 __device__ __forceinline__ void copy16(void* dst, const void* src, int bytes) {
-  uint4* d = reinterpret_cast<uint4*>(dst);
-  const uint4* s = reinterpret_cast<const uint4*>(src);
-  for (int e = threadIdx.x; e < bytes / 16; e += blockDim.x) d[e] = s[e];
+  const char* s = static_cast<const char*>(src);
+  const unsigned d0 = (unsigned)__cvta_generic_to_shared(dst);
+  for (int e = threadIdx.x; e < bytes / 16; e += blockDim.x)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d0 + 16u * (unsigned)e),
+                 "l"(s + 16 * (size_t)e) : "memory");
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // One hidden layer for the warp's 16 rows: out = GELU(in W + b), in[16][ld_in] with K

@@ -2,7 +2,7 @@
 // q = s~): per contact, the impulse lambda^0 and a move of its vertex along the normal,
 // predicted by the network from per-contact features (the impulse as a change of the
 // previous frame's) or taken from the previous frame's contact at the same vertex and
-// obstacle; per scene, a translation from the moves (see k_ws_translate). The guess is kept
+// obstacle; per scene, a translation from the moves (see k_ws_scene). The guess is kept
 // only if the residual of its impulses (the frame's residual measure at k = 0, at the
 // position those impulses predict) is below the cold start's; the decision is per scene.
 //
@@ -57,10 +57,7 @@ __global__ void k_ws_features(DevSim d) {
 
 // the guess of contact j: its impulse (admissible: lambda_n >= 0, |lambda_f| <= mu
 // lambda_n) and the move of its vertex along the normal
-__global__ void k_ws_guess(DevSim d) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int c = min(d.counters[kCntContacts], d.cap);
-  if (j >= c) return;
+__device__ void ws_guess(const DevSim& d, int j) {
   const int v = d.ct_vert[j], sc = d.vert_scene[v];
   const double scale = d.ws_scale[j], mu = d.ct_mu[j], margin = d.scene_margin[sc];
   double lam[3] = {0.0, 0.0, 0.0}, move = 0.0;
@@ -86,17 +83,35 @@ __global__ void k_ws_guess(DevSim d) {
   d.ws_move[j] = move;
 }
 
-// per scene (one CTA each): two translations, summed in a fixed order. The impulse
-// translation h^2 sum_j D_j^T lambda_j^0 / M is what the guessed impulses give the scene's
-// free mass over one step (an impulse guess that holds a resting body up also lifts its
-// predicted position by the sag of gravity); it judges the impulse guess. The move
-// translation is the mean over the scene's contact vertices of their guessed move along the
-// normal; the scene is moved by it, kept within one contact margin of the impulse
-// translation.
-__global__ void k_ws_translate(DevSim d) {
+// strictly better than the cold start (an empty guess is the cold start and is not taken);
+// copy 0 of a portfolio group always runs cold
+__device__ __forceinline__ bool ws_accepted(const DevSim& d, int sc, double r_guess,
+                                            double r_cold) {
+  if (d.pf_copies > 1 && sc % d.pf_copies == 0) return false;
+  return r_guess < r_cold;
+}
+
+constexpr int kWsThreads = 256;
+
+// The warm start of one scene per CTA, in the order of its steps:
+//  1. the guess of every contact of the scene (ws_guess);
+//  2. two translations, summed in a fixed order. The impulse translation
+//     h^2 sum_j D_j^T lambda_j^0 / M is what the guessed impulses give the scene's free mass
+//     over one step (an impulse guess that holds a resting body up also lifts its predicted
+//     position by the sag of gravity); it judges the impulse guess. The move translation is
+//     the mean over the scene's contact vertices of their guessed move along the normal; the
+//     scene is moved by it, kept within one contact margin of the impulse translation;
+//  3. the residuals at k = 0 of the guess (translated scene, guessed impulses) and of the
+//     cold start (s~, lambda = 0), max over the scene's contacts;
+//  4. if the guess is kept: its impulses, and the translation of the scene's free vertices.
+__global__ void __launch_bounds__(kWsThreads) k_ws_scene(DevSim d) {
   const int sc = blockIdx.x;
   const int jb = d.sc_jb[sc], je = d.sc_jb[sc + 1];
-  __shared__ double part[6][128];
+  __shared__ double part[6][kWsThreads];
+  __shared__ double shift[6];
+  __shared__ int keep;
+  for (int j = jb + threadIdx.x; j < je; j += blockDim.x) ws_guess(d, j);
+  __syncthreads();
   double t[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   for (int j = jb + threadIdx.x; j < je; j += blockDim.x) {
     const double* D = d.ct_D + 9 * j;
@@ -123,54 +138,51 @@ __global__ void k_ws_translate(DevSim d) {
     dn = sqrt(dn);
     const double lim = d.scene_margin[sc], f = dn > lim ? lim / dn : 1.0;
     for (int r = 0; r < 3; ++r) {
-      d.ws_shift[6 * sc + r] = imp[r];                 // judges the impulses
-      d.ws_shift[6 * sc + 3 + r] = imp[r] + f * dev[r];  // applied
+      shift[r] = imp[r];                 // judges the impulses
+      shift[3 + r] = imp[r] + f * dev[r];  // applied
     }
+    for (int r = 0; r < 6; ++r) d.ws_shift[6 * sc + r] = shift[r];
   }
-}
-
-// residuals at k = 0 of the guess (translated scene, guessed impulses) and of the cold
-// start (s~, lambda = 0), max per scene
-__global__ void k_ws_residuals(DevSim d) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int c = min(d.counters[kCntContacts], d.cap);
-  if (j >= c) return;
-  const int v = d.ct_vert[j], sc = d.vert_scene[v];
-  double q[3], q0[3], lam[3];
-  for (int r = 0; r < 3; ++r) {
-    q0[r] = d.q_ref[3 * v + r] + (double)d.dq[3 * v + r];
-    q[r] = q0[r] + d.ws_shift[6 * sc + r];
-    lam[r] = d.ws_lam0[3 * j + r];
-  }
-  const double zero[3] = {0.0, 0.0, 0.0};
+  __syncthreads();
+  double rg = 0.0, rc = 0.0;
   const double L = d.scene_Lref[sc];
-  atomic_max_nonneg(&d.ws_res[2 * sc], fb_terms(d, j, q, lam, L).res);
-  atomic_max_nonneg(&d.ws_res[2 * sc + 1], fb_terms(d, j, q0, zero, L).res);
-}
-
-// strictly better than the cold start (an empty guess is the cold start and is not taken);
-// copy 0 of a portfolio group always runs cold
-__device__ __forceinline__ bool ws_accepted(const DevSim& d, int sc) {
-  if (d.pf_copies > 1 && sc % d.pf_copies == 0) return false;
-  return d.ws_res[2 * sc] < d.ws_res[2 * sc + 1];
-}
-
-// keep the guess where it is not worse than the cold start (per scene): impulses ...
-__global__ void k_ws_commit(DevSim d) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int c = min(d.counters[kCntContacts], d.cap);
-  if (j >= c) return;
-  if (!ws_accepted(d, d.vert_scene[d.ct_vert[j]])) return;
-  for (int r = 0; r < 3; ++r) d.ct_lam[3 * j + r] = d.ws_lam0[3 * j + r];
-}
-
-// ... and the translation of the scene's free vertices
-__global__ void k_ws_shift(DevSim d) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= d.n) return;
-  const int sc = d.vert_scene[v];
-  if (!ws_accepted(d, sc)) return;
-  for (int r = 0; r < 3; ++r) d.dq[3 * v + r] += (float)d.ws_shift[6 * sc + 3 + r];
+  const double zero[3] = {0.0, 0.0, 0.0};
+  for (int j = jb + threadIdx.x; j < je; j += blockDim.x) {
+    const int v = d.ct_vert[j];
+    double q[3], q0[3], lam[3];
+    for (int r = 0; r < 3; ++r) {
+      q0[r] = d.q_ref[3 * v + r] + (double)d.dq[3 * v + r];
+      q[r] = q0[r] + shift[r];
+      lam[r] = d.ws_lam0[3 * j + r];
+    }
+    rg = fmax(rg, fb_terms(d, j, q, lam, L).res);
+    rc = fmax(rc, fb_terms(d, j, q0, zero, L).res);
+  }
+  part[0][threadIdx.x] = rg;
+  part[1][threadIdx.x] = rc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      part[0][threadIdx.x] = fmax(part[0][threadIdx.x], part[0][threadIdx.x + w]);
+      part[1][threadIdx.x] = fmax(part[1][threadIdx.x], part[1][threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    d.ws_res[2 * sc] = part[0][0];
+    d.ws_res[2 * sc + 1] = part[1][0];
+    keep = ws_accepted(d, sc, part[0][0], part[1][0]) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!keep) return;
+  for (int j = jb + threadIdx.x; j < je; j += blockDim.x)
+    for (int r = 0; r < 3; ++r) d.ct_lam[3 * j + r] = d.ws_lam0[3 * j + r];
+  const float s0 = (float)shift[3], s1 = (float)shift[4], s2 = (float)shift[5];
+  for (int v = d.scene_vfirst[sc] + threadIdx.x; v < d.scene_vfirst[sc + 1]; v += blockDim.x) {
+    d.dq[3 * v] += s0;
+    d.dq[3 * v + 1] += s1;
+    d.dq[3 * v + 2] += s2;
+  }
 }
 
 __global__ void k_ws_clear(DevSim d) {
@@ -246,19 +258,13 @@ void launch_ws_features(const DevSim& d, cudaStream_t s) {
   k_ws_features<<<(d.cap + 127) / 128, 128, 0, s>>>(d);
 }
 
-int ws_kernels(int mode) { return mode == 0 ? 0 : (mode == 1 ? 6 : 5); }
+int ws_kernels(int mode) { return mode == 0 ? 0 : (mode == 1 ? 2 : 1); }
 
 void launch_ws_start(const DevSim& d, cudaStream_t s) {
   if (d.ws_mode == 0) return;
-  cudaMemsetAsync(d.ws_res, 0, sizeof(double) * 2 * d.n_scenes, s);
   if (d.ws_mode == 1)
     mlp_launch_infer_dev(d.ws_net, d.ws_feat, d.counters + kCntContacts, d.cap, d.ws_out, s);
-  const int g = (d.cap + 127) / 128;
-  k_ws_guess<<<g, 128, 0, s>>>(d);
-  k_ws_translate<<<d.n_scenes, 128, 0, s>>>(d);
-  k_ws_residuals<<<g, 128, 0, s>>>(d);
-  k_ws_commit<<<g, 128, 0, s>>>(d);
-  k_ws_shift<<<(d.n + 255) / 256, 256, 0, s>>>(d);
+  k_ws_scene<<<d.n_scenes, kWsThreads, 0, s>>>(d);
 }
 
 void launch_ws_record(const DevSim& d, cudaStream_t s) {
