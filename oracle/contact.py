@@ -75,10 +75,14 @@ def closest_point(obst, x):
     raise ValueError("unknown obstacle kind")
 
 
-def detect(scene, s_tilde, free_verts):
+def detect(scene, s_tilde, free_verts, t_end=0.0):
     """All (vertex, obstacle) pairs with signed distance below the contact margin at the
-    predicted positions, ordered by vertex id then obstacle index."""
+    predicted positions, ordered by vertex id then obstacle index; then, at its vertex, each
+    anchor (a bilateral constraint, App. A.1's b rows) with the id n_obstacles + its index,
+    its target at time t_end (the end of the frame) and the world axes as its three rows."""
     out = []
+    anchor_of = {int(a.vertex): i for i, a in enumerate(getattr(scene, "anchors", []))}
+    n_obs = len(scene.obstacles)
     for v in free_verts:
         for oi, ob in enumerate(scene.obstacles):
             phi, n, ph = closest_point(ob, s_tilde[v])
@@ -89,7 +93,22 @@ def detect(scene, s_tilde, free_verts):
                                 d_n=float(np.dot(n, ph)),
                                 d_f=np.array([np.dot(f1, u), np.dot(f2, u)]),
                                 mu=float(ob.mu), gap=phi))
+        a = anchor_of.get(int(v))
+        if a is not None:
+            an = scene.anchors[a]
+            target = np.asarray(an.target, float) + t_end * np.asarray(an.vel, float)
+            eye = np.eye(3)
+            out.append(dict(vertex=int(v), obstacle=n_obs + a, n=eye[0], f1=eye[1], f2=eye[2],
+                            anchor=True, target=target, compliance=float(an.compliance),
+                            d_n=float(target[0]), d_f=np.zeros(2), mu=0.0, gap=0.0))
     return out
+
+
+def bilateral_terms(delta, lam, e):
+    """The three rows of an anchor (App. B, bilateral constraints: J_b q - d_b + E_b lambda_b
+    = 0): phi = delta + e lambda, indicator 1 and compliance e on every row."""
+    phi = np.asarray(delta, float) + e * np.asarray(lam, float)
+    return phi, np.ones(3), np.full(3, float(e))
 
 
 # -- Fischer-Burmeister (App. B.2) ------------------------------------------------------

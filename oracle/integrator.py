@@ -20,6 +20,12 @@ Readings of the paper used here (the paper leaves these open):
     preconditioner drive the iteration;
   * friction is active when r_n lambda_n > ACTIVE_REL * L (``contact.friction_active``;
     App. B.1-B.2 write lambda_n > 0), decided with the Delassus r_n for every variant;
+  * anchors (bilateral constraints, App. A.1-B): each ties a free vertex to a target moving
+    at constant velocity (its position at the frame's end time) by the three rows
+    e_x, e_y, e_z of phi_b = H_b q - d_b + e lambda_b, always active (Omega = 1), with
+    compliance E_b = e entering the Schur system as E_b / h^2 and right-hand side
+    -phi_b + J_b q^k like a normal row (Eqs. 19-21); they count in the residual with
+    max |phi_b| / L;
   * the mass-inverse preconditioner, like the Delassus one, uses H (not J = Omega H, which
     depends on r) and gives the two friction rows h times the mean of their diagonal
     entries.
@@ -114,8 +120,14 @@ class Oracle:
         Hq = (H @ q_f).reshape(c, 3)
         Hqt = (H @ q_t_f).reshape(c, 3)
         out = dict(omega=np.zeros((c, 3)), E=np.zeros((c, 3)), phi=np.zeros((c, 3)),
-                   delta_n=np.zeros(c), vel_f=np.zeros((c, 2)))
+                   delta_n=np.zeros(c), vel_f=np.zeros((c, 2)),
+                   bilateral=np.array([bool(ct.get("anchor")) for ct in contacts], dtype=bool))
         for j, ct in enumerate(contacts):
+            if ct.get("anchor"):
+                phi, om, E = C.bilateral_terms(Hq[j] - ct["target"], lam[j], ct["compliance"])
+                out["omega"][j], out["E"][j], out["phi"][j] = om, E, phi
+                out["delta_n"][j] = Hq[j, 0] - ct["target"][0]
+                continue
             dn = Hq[j, 0] - ct["d_n"]
             vf = ((Hq[j, 1:] - Hqt[j, 1:]) - h * ct["d_f"]) / h
             phi_n, om_n, E_n = normal_terms(dn, lam[j, 0], r_n[j])
@@ -129,22 +141,28 @@ class Oracle:
         return out
 
     def residual(self, cs, lam, r_n):
-        """max_j max(|min(delta_n, r_n lambda_n)|, h |phi_f|) / L_ref (dimensionless)."""
+        """max_j max(|min(delta_n, r_n lambda_n)|, h |phi_f|) / L_ref (dimensionless); an
+        anchor counts with max_r |phi_r| / L_ref."""
         if len(r_n) == 0:
             return 0.0
         rn = np.abs(np.minimum(cs["delta_n"], r_n * lam[:, 0]))
         rf = self.h * np.linalg.norm(cs["phi"][:, 1:], axis=1)
-        return float(np.maximum(rn, rf).max() / self.L_ref)
+        res = np.maximum(rn, rf)
+        b = cs["bilateral"]
+        res[b] = np.abs(cs["phi"][b]).max(axis=1)
+        return float(res.max() / self.L_ref)
 
     # -- one frame --------------------------------------------------------------------
-    def frame(self, q_t, v_t, opts: OracleOptions = OracleOptions(), lam0=None, dq0=None):
-        """Advance (q_t, v_t) by one frame. Returns (q_new, v_new, info)."""
+    def frame(self, q_t, v_t, opts: OracleOptions = OracleOptions(), lam0=None, dq0=None,
+              t=0.0):
+        """Advance (q_t, v_t) by one frame starting at time t (the anchors' targets move with
+        time). Returns (q_new, v_new, info)."""
         f = self.fem
         h = self.h
         fv = f.free_verts
         s_tilde = self.predict(q_t, v_t)
         q_pin = self.pinned_positions(q_t)
-        contacts = C.detect(self.scene, s_tilde, fv)
+        contacts = C.detect(self.scene, s_tilde, fv, t + h)
         c = len(contacts)
         H = self.contact_jacobian(contacts)
         W = self.delassus(H)
@@ -183,9 +201,12 @@ class Oracle:
                 Om = cs["omega"].reshape(-1)
                 J = Om[:, None] * H                                      # J = Omega H (Eq. 25)
                 g = b + h ** 2 * (J.T @ lam.reshape(-1))                 # Eq. 19
-                hv = (-np.concatenate([cs["phi"][:, :1], h * cs["phi"][:, 1:]], 1).reshape(-1)
-                      + J @ q_f)                                         # Eq. 19
-                Ecal = (cs["E"] / np.array([h ** 2, h, h])).reshape(-1)  # Eq. 20
+                # friction rows are velocity-level (h phi_f, E_f / h); an anchor's three
+                # rows are position-level like a normal row (App. B, bilateral items)
+                lev = np.where(cs["bilateral"][:, None], 1.0, np.array([1.0, h, h])[None, :])
+                hv = -(lev * cs["phi"]).reshape(-1) + J @ q_f            # Eq. 19
+                Ecal = (cs["E"] / (h * np.where(cs["bilateral"][:, None], h,
+                                                np.array([h, 1.0, 1.0])[None, :]))).reshape(-1)
                 K = Om[:, None] * W * Om[None, :] + np.diag(Ecal)        # Eq. 26 + E
                 rhs = (hv - J @ f.solve(g)) / h ** 2                     # Alg. 4 sign of the RHS
                 if opts.exact_constraint_solve:

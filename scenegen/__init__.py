@@ -44,6 +44,17 @@ class Material:
 
 
 @dataclass
+class Anchor:
+    """A bilateral constraint tying a free vertex to a target point: the three rows
+    e_x, e_y, e_z of (q_v - target) + compliance * lambda = 0. The target starts at
+    ``target`` and moves at ``vel``; compliance (m/N) 0 makes the constraint hard."""
+    vertex: int
+    target: tuple
+    vel: tuple = (0.0, 0.0, 0.0)
+    compliance: float = 0.0
+
+
+@dataclass
 class Obstacle:
     """A static analytic obstacle.
 
@@ -73,6 +84,7 @@ class Scene:
     gravity: tuple = GRAVITY_EARTH
     pinned: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
     handle_vel: tuple = (0.0, 0.0, 0.0)   # velocity of every pinned vertex
+    anchors: List["Anchor"] = field(default_factory=list)   # bilateral vertex targets
     q0: Optional[np.ndarray] = None       # (n, 3) initial positions (default: X)
     v0: Optional[np.ndarray] = None       # (n, 3) initial velocities (default: 0)
     contact_margin: float = 0.0           # a contact exists when the gap is below this
@@ -273,6 +285,39 @@ def star_pull(n_side: int = 42, layers: int = 27, spacing: float = 0.01, seed: i
                  [Material(model, E, nu, rho)], obst, h, gravity=(0.0, 0.0, 0.0),
                  pinned=pinned, handle_vel=(pull_speed, 0.0, 0.0),
                  contact_margin=0.5 * spacing, n_frames=n_frames, spacing=spacing)
+
+
+def anchored_handle(scene: Scene, compliance: float = 0.0) -> Scene:
+    """The same scene with its pinned handle replaced by anchors: every pinned vertex
+    becomes a free vertex tied to a target that starts at its initial position and moves
+    with the handle velocity (the bilateral form of the moving positional constraint)."""
+    import copy
+    sc = copy.deepcopy(scene)
+    sc.anchors = [Anchor(int(v), tuple(float(x) for x in scene.q0[v]), tuple(scene.handle_vel),
+                         compliance) for v in scene.pinned]
+    sc.pinned = np.zeros(0, np.int32)
+    sc.name = scene.name + "_anchored"
+    return sc
+
+
+def hanging_cube(m: int = 5, edge: float = 0.1, model: int = MODEL_ARAP, E: float = 1e5,
+                 nu: float = 0.4, rho: float = 1000.0, compliance: float = 0.0,
+                 target_vel=(0.0, 0.0, 0.0), h: float = 1.0 / 60.0, floor: bool = False,
+                 mu: float = 0.5) -> Scene:
+    """An m^3-vertex cube hanging under gravity from one anchor at the vertex nearest the
+    centre of its top face (for odd m right above the centre of mass), optionally above a
+    floor plane two edges below the cube."""
+    X, tets = lattice_tets(m, m, m, edge / (m - 1))
+    c = X.mean(0)
+    d = np.abs(X[:, 0] - c[0]) + np.abs(X[:, 1] - c[1]) - 1e3 * X[:, 2]
+    top = int(np.argmin(d))
+    obst = []
+    if floor:
+        obst.append(Obstacle(OBST_PLANE, (0.0, 0.0, -2.0 * edge), (0.0, 0.0, 1.0), mu=mu))
+    sc = Scene(f"hang{m}", X, tets, np.zeros(len(tets), np.int32), [Material(model, E, nu, rho)],
+               obst, h, contact_margin=0.5 * edge / (m - 1), spacing=edge / (m - 1))
+    sc.anchors = [Anchor(top, tuple(float(x) for x in X[top]), tuple(target_vel), compliance)]
+    return sc
 
 
 def batch(n_scenes: int = 64, seed: int = 0, m_lo: int = 8, m_hi: int = 20,

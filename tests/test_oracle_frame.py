@@ -310,3 +310,87 @@ def test_cancelled_normal_impulse_does_not_switch_on_friction():
     assert max(info["residuals"][2:]) < 1e-12
     lam_n = info["lam"][:, 0]
     assert np.any((lam_n != 0) & (np.abs(lam_n) < 1e-30))
+
+
+def _settle(o, sc, frames, opts):
+    q, v = sc.q0.copy(), sc.v0.copy()
+    for f in range(frames):
+        q, v, info = o.frame(q, v, opts, t=f * sc.h)
+    return q, v, info
+
+
+@pytest.mark.parametrize("compliance", [0.0, 2e-4])
+def test_anchor_holds_the_weight_at_rest(compliance):
+    # a cube hanging from one anchor above its centre of mass settles with the anchor's
+    # vertical force equal to the weight, and the anchored vertex where the bilateral row
+    # puts it: on the target (hard) or below it by e times the force (a spring of stiffness
+    # 1/e). A slow rocking mode of the lattice (its tets are not mirror-symmetric) is still
+    # decaying: the sideways force and the velocities are small, not zero.
+    sc = sg.hanging_cube(m=5, compliance=compliance)
+    o = Oracle(sc)
+    q, v, info = _settle(o, sc, 200, OracleOptions(n_iters=20, exact_constraint_solve=True))
+    a = sc.anchors[0]
+    (j,) = [k for k, ct in enumerate(info["contacts"]) if ct.get("anchor")]
+    lam = info["lam"][j]
+    weight = o.fem.mass.sum() * 9.81
+    assert abs(lam[2] - weight) < 1e-6 * weight
+    assert np.abs(lam[:2]).max() < 2e-4 * weight
+    gap = q[a.vertex] - np.asarray(a.target)
+    assert np.abs(gap + compliance * lam).max() < 1e-12 * sc.bbox_diagonal
+    if compliance:
+        assert abs(gap[2] + compliance * weight) < 1e-6 * compliance * weight
+    assert np.abs(v).max() < 1e-3
+
+
+def test_anchored_handle_equals_the_dirichlet_handle():
+    # the bilateral form of the moving positional constraint (hard anchors at the handle's
+    # vertices, those vertices free): with an exact constraint solve every global step is
+    # the KKT solution whose free part is the Dirichlet solve, so from the same q^0 (the
+    # handle moving from the start) every iterate equals the Dirichlet elimination's
+    base = sg.star_pull(n_side=8, layers=4, spacing=0.02, cap_depth=0.03)
+    base.obstacles = []
+    base.v0[base.pinned] = np.asarray(base.handle_vel)
+    anch = sg.anchored_handle(base)
+    o_d, o_a = Oracle(base), Oracle(anch)
+    opts = OracleOptions(n_iters=12, exact_constraint_solve=True)
+    qd, vd = base.q0.copy(), base.v0.copy()
+    qa, va = qd.copy(), vd.copy()
+    for f in range(3):
+        qd, vd, _ = o_d.frame(qd, vd, opts, t=f * base.h)
+        qa, va, info = o_a.frame(qa, va, opts, t=f * base.h)
+        assert info["residuals"][-1] < 1e-12
+        assert np.abs(qa - qd).max() < 1e-10 * base.bbox_diagonal
+    assert len(anch.anchors) == len(base.pinned) > 4
+
+
+def test_momentum_balance_with_anchor_and_contact():
+    # sum_v m_v (q_v - s~_v) = h^2 sum_j D_j^T Omega_j lambda_j, anchors included
+    sc = sg.hanging_cube(m=4, compliance=1e-4, floor=True, target_vel=(0.0, 0.0, -1.0))
+    o = Oracle(sc)
+    q, v = sc.q0.copy(), sc.v0.copy()
+    for f in range(12):
+        q, v, info = o.frame(q, v, t=f * sc.h)
+    kinds = {bool(ct.get("anchor")) for ct in info["contacts"]}
+    assert kinds == {True, False}
+    m = o.fem.mass[:, None]
+    lhs = (m * (q - info["s_tilde"])).sum(0)
+    rhs = np.zeros(3)
+    for j, ct in enumerate(info["contacts"]):
+        D = np.stack([ct["n"], ct["f1"], ct["f2"]])
+        rhs += D.T @ (info["omega_last"][j] * info["lam"][j])
+    assert np.abs(lhs - sc.h ** 2 * rhs).max() < 1e-12 * (m.sum() * 1e-2)
+
+
+def test_anchor_row_is_solved_in_one_newton_step():
+    # an anchor's rows are linear in q and lambda, so one constrained global step with an
+    # exact constraint solve (the compliance entering as E_b / h^2 in the Schur system, the
+    # row's right-hand side d_b - E_b lambda^k) leaves phi_b = 0 at the new iterate
+    sc = sg.hanging_cube(m=4, compliance=3e-4, target_vel=(0.2, 0.0, 0.1))
+    o = Oracle(sc)
+    q, v = sc.q0.copy(), sc.v0.copy()
+    for f in range(4):
+        q, v, info = o.frame(q, v, OracleOptions(n_iters=1, exact_constraint_solve=True),
+                             t=f * sc.h)
+        (j,) = [k for k, ct in enumerate(info["contacts"]) if ct.get("anchor")]
+        assert np.abs(info["final_state"]["phi"][j]).max() < 1e-14
+        assert np.abs(info["lam"][j]).max() > 0.1
