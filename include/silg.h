@@ -225,9 +225,27 @@ int sim_create(const sim_mesh* mesh, const sim_material* mats, int32_t n_mat,
                const sim_obstacle* obstacles, int32_t n_obs, double h,
                const sim_options* opts, sim_t** out);
 
+/* An anchor: a bilateral constraint (the b rows of J with compliance E_b, App. A.1 and
+ * App. B) tying a free vertex to a moving target by the three rows e_x, e_y, e_z of
+ *   phi_b = q_v - p(t) + compliance * lambda_b = 0,
+ * always active. p(t) = target + vel * t is the target at the end of the frame, t counted
+ * from the simulator's creation or the last sim_set_state. Rows enter the constraint solve
+ * like normal rows (compliance / h^2 in the Schur system); they count in the residual with
+ * max |phi_b| / L, appear among the contacts (sim_get_contacts) with obstacle id = the
+ * simulator's obstacle count + the anchor's index over all scenes, and in n_contacts.
+ * vertex: a free (not pinned) vertex of its scene, at most one anchor per vertex;
+ * compliance >= 0 (m/N; 0: a hard constraint). Anything else: SIM_EINVAL at creation. */
+typedef struct {
+  int32_t vertex;
+  double target[3];
+  double vel[3];
+  double compliance;
+} sim_anchor;
+
 /* One independent scene of a batch: its mesh, its materials (tet_material indexes this
- * list), its obstacles (they act on this scene's vertices only) and its contact margin
- * (<= 0: half the scene's mean edge; opts->contact_margin is not used by a batch). */
+ * list), its obstacles (they act on this scene's vertices only), its contact margin
+ * (<= 0: half the scene's mean edge; opts->contact_margin is not used by a batch) and its
+ * anchors (may be NULL with n_anchors = 0). */
 typedef struct {
   sim_mesh mesh;
   const sim_material* materials;
@@ -235,6 +253,8 @@ typedef struct {
   const sim_obstacle* obstacles;
   int32_t n_obstacles;
   double contact_margin;
+  const sim_anchor* anchors;
+  int32_t n_anchors;
 } sim_scene;
 
 /*

@@ -235,6 +235,8 @@ class Simulator:
 
     def __init__(self, scene, use_torch_stream=True, **opts):
         batch = isinstance(scene, (list, tuple))
+        if not batch and getattr(scene, "anchors", None):
+            scene, batch = [scene], True     # anchors travel in sim_scene (sim_create_batch)
         first = scene[0] if batch else scene
         o = _options(first, **opts)
         if use_torch_stream and "cuda_stream" not in opts:
@@ -254,6 +256,18 @@ class Simulator:
                 scs[k].obstacles = C.cast(obs, C.POINTER(_abi.SimObstacle))
                 scs[k].n_obstacles = len(sc.obstacles)
                 scs[k].contact_margin = float(getattr(sc, "contact_margin", 0.0))
+                anchors = getattr(sc, "anchors", None) or []
+                if anchors:
+                    an = (_abi.SimAnchor * len(anchors))()
+                    for i, a in enumerate(anchors):
+                        an[i].vertex = int(a.vertex)
+                        for r in range(3):
+                            an[i].target[r] = float(a.target[r])
+                            an[i].vel[r] = float(a.vel[r])
+                        an[i].compliance = float(a.compliance)
+                    self._keep.append(an)
+                    scs[k].anchors = C.cast(an, C.POINTER(_abi.SimAnchor))
+                    scs[k].n_anchors = len(anchors)
             self._keep.append(scs)
             _check(lib().sim_create_batch(scs, len(scene), float(first.h), C.byref(o),
                                           C.byref(handle)), "sim_create_batch")

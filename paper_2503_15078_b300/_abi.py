@@ -36,10 +36,16 @@ class SimObstacle(C.Structure):
                 ("radius", C.c_double), ("mu", C.c_double), ("vel", C.c_double * 3)]
 
 
+class SimAnchor(C.Structure):
+    _fields_ = [("vertex", C.c_int32), ("target", C.c_double * 3), ("vel", C.c_double * 3),
+                ("compliance", C.c_double)]
+
+
 class SimScene(C.Structure):
     _fields_ = [("mesh", SimMesh), ("materials", C.POINTER(SimMaterial)),
                 ("n_materials", C.c_int32), ("obstacles", C.POINTER(SimObstacle)),
-                ("n_obstacles", C.c_int32), ("contact_margin", C.c_double)]
+                ("n_obstacles", C.c_int32), ("contact_margin", C.c_double),
+                ("anchors", C.POINTER(SimAnchor)), ("n_anchors", C.c_int32)]
 
 
 class SimOptions(C.Structure):

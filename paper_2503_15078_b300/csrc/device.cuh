@@ -60,6 +60,15 @@ struct DevSim {
   const int* scene_vfirst;    // n_scenes + 1: first internal free vertex of each scene
   const int* obst_scene;      // n_obs: the scene an obstacle acts on
   const int* scene_ofirst;    // n_scenes + 1: each scene's obstacles are [first, next first)
+  // anchors (bilateral constraints): contact slots with obstacle id n_obs + a, rows e_x,
+  // e_y, e_z; the slot keeps the target in ct_dn (x) and ct_df (y, z), the compliance in
+  // ct_mu
+  int n_anc;
+  int* anc_of;                // n: the anchor of a free vertex, or -1
+  double* anc_pos;            // 3 n_anc: the target at the end of the current frame
+  const double* anc_pos0;     // 3 n_anc: the target at time 0
+  const double* anc_vel;      // 3 n_anc
+  const double* anc_e;        // n_anc: compliance
   const double* scene_margin; // contact margin
   const double* scene_Lref;   // rest bounding-box diagonal (residual scale)
   const double* scene_hvel;   // 3 per scene: velocity of the scene's pinned vertices

@@ -22,6 +22,9 @@ struct FbTerms {
   double phin, omn, En; // normal row (Eqs. 52-54, or App. B.1)
   double phif0, phif1, omf, Ef;  // friction rows (Eqs. 55-57, or App. B.1)
   double res;           // the residual measure max(|min(dn, r_n lambda_n)|, h |phi_f|) / L
+  bool bilateral;       // an anchor: phin, phif0, phif1 are its three position-level rows
+                        // phi_b = q - p + e lambda, En = Ef = e, omn = omf = 1, res =
+                        // max |phi_b| / L
 };
 
 // Normal and friction rows at gap dn, tangential velocity vf, impulses (ln, lf0, lf1) with
@@ -90,6 +93,24 @@ __device__ inline FbTerms fb_terms(const DevSim& d, int j, const double q[3], co
   const int v = d.ct_vert[j];
   const double h = d.h;
   const double* D = d.ct_D + 9 * j;
+  o.bilateral = d.ct_obst[j] >= d.n_obs;
+  if (o.bilateral) {
+    // rows e_x, e_y, e_z (D = I): phi_b = q - p + e lambda with the target p in ct_dn, ct_df
+    const double e = d.ct_mu[j];
+    const double p[3] = {d.ct_dn[j], d.ct_df[2 * j], d.ct_df[2 * j + 1]};
+    double ph[3];
+    for (int r = 0; r < 3; ++r)
+      ph[r] = D[3 * r] * q[0] + D[3 * r + 1] * q[1] + D[3 * r + 2] * q[2] - p[r] + e * lam[r];
+    o.dn = ph[0] - e * lam[0];
+    o.vf[0] = o.vf[1] = 0.0;
+    o.phin = ph[0];
+    o.phif0 = ph[1];
+    o.phif1 = ph[2];
+    o.omn = o.omf = 1.0;
+    o.En = o.Ef = e;
+    o.res = fmax(fabs(ph[0]), fmax(fabs(ph[1]), fabs(ph[2]))) / L;
+    return o;
+  }
   double qt[3];
   for (int r = 0; r < 3; ++r) qt[r] = d.q_t[3 * v + r];
   o.dn = D[0] * q[0] + D[1] * q[1] + D[2] * q[2] - d.ct_dn[j];

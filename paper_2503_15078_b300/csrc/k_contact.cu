@@ -108,6 +108,7 @@ __global__ void k_collide_count(DevSim d) {
     double nn[3], ph[3];
     if (obst_query(d.obst[o], x, nn, ph) < margin) ++cnt;
   }
+  if (d.n_anc > 0 && d.anc_of[i] >= 0) ++cnt;   // its anchor: one more slot, after the obstacles
   d.ct_cnt[i] = cnt;
   d.cv_flag[i] = cnt > 0;
 }
@@ -148,6 +149,19 @@ __global__ void k_collide_write(DevSim d) {
       d.ct_mu[j] = ob.mu;
     }
     ++j;
+  }
+  const int a = d.n_anc > 0 ? d.anc_of[i] : -1;
+  if (a >= 0 && j < d.cap) {
+    // the anchor's slot: rows e_x, e_y, e_z; the target (at the frame's end) in ct_dn and
+    // ct_df; the compliance in ct_mu
+    for (int r = 0; r < 9; ++r) d.ct_D[9 * j + r] = (r % 4 == 0) ? 1.0 : 0.0;
+    d.ct_vert[j] = i;
+    d.ct_obst[j] = d.n_obs + a;
+    d.ct_cv[j] = cv;
+    d.ct_dn[j] = d.anc_pos[3 * a];
+    d.ct_df[2 * j] = d.anc_pos[3 * a + 1];
+    d.ct_df[2 * j + 1] = d.anc_pos[3 * a + 2];
+    d.ct_mu[j] = d.anc_e[a];
   }
 }
 
@@ -554,6 +568,21 @@ __global__ void k_contact_eval(DevSim d, int k, int final_eval) {
   const double lamv[3] = {d.ct_lam[3 * j], d.ct_lam[3 * j + 1], d.ct_lam[3 * j + 2]};
   const int sc = d.vert_scene[v];
   const FbTerms fb = fb_terms(d, j, q, lamv, d.scene_Lref[sc]);
+  if (fb.bilateral) {
+    // an anchor: three position-level rows, always active (App. B, bilateral items)
+    atomic_max_nonneg(&d.resid[k], fb.res);
+    atomic_max_nonneg(&d.resid_scene[sc * (kMaxIters + 1) + k], fb.res);
+    if (final_eval) return;
+    const double phb[3] = {fb.phin, fb.phif0, fb.phif1};
+    for (int r = 0; r < 3; ++r) {
+      d.ct_force[3 * j + r] = D[r] * lamv[0] + D[3 + r] * lamv[1] + D[6 + r] * lamv[2];
+      d.ct_omega[3 * j + r] = 1.f;
+      d.ct_ecal[3 * j + r] = (float)(fb.En / (h * h));
+      const double Ddq = D[3 * r] * dqv[0] + D[3 * r + 1] * dqv[1] + D[3 * r + 2] * dqv[2];
+      d.ct_hv[3 * j + r] = -phb[r] + Ddq;
+    }
+    return;
+  }
   const double dn = fb.dn, phin = fb.phin, omn = fb.omn, En = fb.En;
   const double omf = fb.omf, Ef = fb.Ef, phif0 = fb.phif0, phif1 = fb.phif1;
   const double ln = lamv[0], lf0 = lamv[1], lf1 = lamv[2];

@@ -228,6 +228,12 @@ __global__ void k_frame_begin(DevSim d) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n_all) return;
   const double h = d.h;
+  if (i < d.n && d.n_anc > 0) {
+    // the vertex's anchor target moves to the end of this frame
+    const int a = d.anc_of[i];
+    if (a >= 0)
+      for (int r = 0; r < 3; ++r) d.anc_pos[3 * a + r] += h * d.anc_vel[3 * a + r];
+  }
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     double qt = d.q_t[3 * i + r];

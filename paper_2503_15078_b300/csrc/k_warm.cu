@@ -35,6 +35,12 @@ __global__ void k_ws_features(DevSim d) {
   const double w = fmax(wt_diag(d, j), 1e-300);
   const double scale = margin / (h * h * w);
   float* f = d.ws_feat + (size_t)j * kMlpIn;
+  if (o >= d.n_obs) {
+    // an anchor: not guessed (its impulse starts at 0); no features
+    for (int r = 0; r < kMlpIn; ++r) f[r] = 0.f;
+    d.ws_scale[j] = scale;
+    return;
+  }
   double st[3];
   for (int r = 0; r < 3; ++r) st[r] = d.s_tilde[3 * v + r];
   f[0] = (float)((D[0] * st[0] + D[1] * st[1] + D[2] * st[2] - d.ct_dn[j]) / margin);
@@ -59,6 +65,11 @@ __global__ void k_ws_features(DevSim d) {
 // lambda_n) and the move of its vertex along the normal
 __device__ void ws_guess(const DevSim& d, int j) {
   const int v = d.ct_vert[j], sc = d.vert_scene[v];
+  if (d.ct_obst[j] >= d.n_obs) {   // anchors start from lambda = 0
+    for (int r = 0; r < 3; ++r) d.ws_lam0[3 * j + r] = 0.0;
+    d.ws_move[j] = 0.0;
+    return;
+  }
   const double scale = d.ws_scale[j], mu = d.ct_mu[j], margin = d.scene_margin[sc];
   double lam[3] = {0.0, 0.0, 0.0}, move = 0.0;
   if (d.ws_mode == 1) {
@@ -201,7 +212,7 @@ __global__ void k_ws_record(DevSim d) {
   double mv = 0.0;
   for (int r = 0; r < 3; ++r)
     mv += D[r] * (d.q_ref[3 * v + r] + (double)d.dq[3 * v + r] - d.s_tilde[3 * v + r]);
-  if (d.cv_first[d.ct_cv[j]] == j) {
+  if (d.cv_first[d.ct_cv[j]] == j && d.ct_obst[j] < d.n_obs) {
     d.prev_valid[v] = 1;
     d.prev_obst[v] = d.ct_obst[j];
     d.prev_move[v] = mv;

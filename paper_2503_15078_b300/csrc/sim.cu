@@ -536,6 +536,7 @@ struct SceneData {
   std::vector<sim_obstacle> obstacles;
   std::vector<int32_t> obstacle_scene;
   std::vector<double> margin, L_ref, hvel;  // hvel: 3 per scene
+  std::vector<sim_anchor> anchors;          // vertex ids in the union's numbering
 };
 
 int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
@@ -569,6 +570,27 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   }
   d.scene_vfirst = s->upload(p.scene_vfirst);
   d.obst_scene = s->upload(sd.obstacle_scene);
+  {
+    // anchors: per free internal vertex, its anchor (targets reset to time 0)
+    const int na = (int)sd.anchors.size();
+    d.n_anc = na;
+    std::vector<int> of(std::max(1, n), -1);
+    std::vector<double> pos(3 * (size_t)std::max(1, na)), vel(pos.size()), e(std::max(1, na));
+    for (int a = 0; a < na; ++a) {
+      const sim_anchor& an = sd.anchors[a];
+      of[p.internal[an.vertex]] = a;
+      for (int r = 0; r < 3; ++r) {
+        pos[3 * a + r] = an.target[r];
+        vel[3 * a + r] = an.vel[r];
+      }
+      e[a] = an.compliance;
+    }
+    d.anc_of = s->upload(of);
+    d.anc_pos0 = s->upload(pos);
+    d.anc_pos = s->upload(pos);
+    d.anc_vel = s->upload(vel);
+    d.anc_e = s->upload(e);
+  }
   {
     // obstacles are listed scene by scene
     std::vector<int> of(p.n_scenes + 1, n_obs);
@@ -756,7 +778,7 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   d.iter_k = s->alloc<int>(1);
   d.err = s->alloc<int>(1);
   d.p_out = s->alloc<float>(9 * (size_t)T);
-  s->has_obstacles = n_obs > 0;
+  s->has_obstacles = n_obs > 0 || !sd.anchors.empty();
   d.wt_grid = 4 * d.n_sm;
   d.spin_limit = o->spin_limit;
   d.kb_lo = s->alloc<int>(n / 32 + 1);
@@ -934,6 +956,22 @@ int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_opt
         sd.obstacles.push_back(sc.obstacles[q]);
         sd.obstacle_scene.push_back(k);
       }
+      if (sc.n_anchors < 0 || (sc.n_anchors > 0 && !sc.anchors)) return SIM_EINVAL;
+      {
+        std::vector<char> used(m.n_verts, 0);
+        for (int q = 0; q < m.n_pinned; ++q)
+          if (m.pinned[q] >= 0 && m.pinned[q] < m.n_verts) used[m.pinned[q]] = 1;
+        for (int q = 0; q < sc.n_anchors; ++q) {
+          sim_anchor a = sc.anchors[q];
+          bool ok = a.vertex >= 0 && a.vertex < m.n_verts && used[a.vertex] == 0 &&
+                    std::isfinite(a.compliance) && a.compliance >= 0.0;
+          for (int r = 0; r < 3; ++r) ok = ok && std::isfinite(a.target[r]) && std::isfinite(a.vel[r]);
+          if (!ok) return SIM_EINVAL;
+          used[a.vertex] = 2;
+          a.vertex += voff;
+          sd.anchors.push_back(a);
+        }
+      }
       const double me = mean_edge(m);
       sd.margin.push_back(margin_override > 0 ? margin_override
                                               : (sc.contact_margin > 0 ? sc.contact_margin : 0.5 * me));
@@ -971,6 +1009,13 @@ int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_opt
           mix(ob.vel, sizeof(ob.vel));
         }
         mix(&sd.margin.back(), sizeof(double));
+        for (int q = 0; q < sc.n_anchors; ++q) {
+          const sim_anchor& a = sc.anchors[q];
+          mix(&a.vertex, sizeof(a.vertex));
+          mix(a.target, sizeof(a.target));
+          mix(a.vel, sizeof(a.vel));
+          mix(&a.compliance, sizeof(double));
+        }
         s->scene_sig.push_back(hsh);
       }
       voff += m.n_verts;
@@ -1114,17 +1159,25 @@ int sim_get_warmstart_samples(sim_t* s, int32_t capacity, float* X, float* T, in
   if (s->has_obstacles && s->frame > 0)
     cudaMemcpy(&c, s->d.counters + silg::kCntContacts, sizeof(int), cudaMemcpyDeviceToHost);
   c = std::min(c, s->d.cap);
-  *n_out = c;
-  if (c == 0 || capacity < c) return st;
+  // anchors are not samples (the warm start does not guess them)
+  std::vector<int> obst(std::max(1, c));
+  if (c > 0) cudaMemcpy(obst.data(), s->d.ct_obst, sizeof(int) * c, cudaMemcpyDeviceToHost);
+  int ns = 0;
+  for (int j = 0; j < c; ++j) ns += obst[j] < s->d.n_obs;
+  *n_out = ns;
+  if (ns == 0 || capacity < ns) return st;
   std::vector<float> f((size_t)c * silg::kMlpIn), t(4 * (size_t)c);
   cudaMemcpy(f.data(), s->d.ws_feat, f.size() * sizeof(float), cudaMemcpyDeviceToHost);
   cudaError_t e = cudaMemcpy(t.data(), s->d.ws_target, t.size() * sizeof(float), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_status(e);
+  int row = 0;
   for (int j = 0; j < c; ++j) {
+    if (obst[j] >= s->d.n_obs) continue;
     if (X)
-      for (int q = 0; q < silg::kMlpNF; ++q) X[(size_t)j * silg::kMlpNF + q] = f[(size_t)j * silg::kMlpIn + q];
+      for (int q = 0; q < silg::kMlpNF; ++q) X[(size_t)row * silg::kMlpNF + q] = f[(size_t)j * silg::kMlpIn + q];
     if (T)
-      for (int q = 0; q < 4; ++q) T[4 * (size_t)j + q] = t[4 * (size_t)j + q];
+      for (int q = 0; q < 4; ++q) T[4 * (size_t)row + q] = t[4 * (size_t)j + q];
+    ++row;
   }
   return st;
 }
@@ -1235,6 +1288,9 @@ int sim_set_state(sim_t* s, const double* q, const double* v) {
   }
   // in stream order before the next frame; the copies read the staging asynchronously
   cudaMemsetAsync(s->d.prev_valid, 0, sizeof(int) * s->d.n, s->launch);
+  if (s->d.n_anc > 0)   // time restarts at 0: so do the anchors' targets
+    cudaMemcpyAsync(s->d.anc_pos, s->d.anc_pos0, 3 * sizeof(double) * s->d.n_anc,
+                    cudaMemcpyDeviceToDevice, s->launch);
   cudaMemcpyAsync(s->d.q_t, bq, m * sizeof(double), cudaMemcpyHostToDevice, s->launch);
   cudaMemcpyAsync(s->d.v_t, bv, m * sizeof(double), cudaMemcpyHostToDevice, s->launch);
   cudaMemsetAsync(s->d.err, 0, sizeof(int), s->launch);

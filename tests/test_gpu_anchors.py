@@ -1,0 +1,139 @@
+"""Anchors (bilateral constraints tying a free vertex to a moving target, App. A.1 and App. B)
+on the GPU against the FP64 oracle: single frames, trajectories, anchors beside frictional
+contacts, and the anchored form of the pulled star's handle."""
+import numpy as np
+import pytest
+
+import scenegen as sg
+from oracle import Oracle, OracleOptions
+from paper_2503_15078_b300 import Simulator
+
+pytestmark = pytest.mark.gpu
+
+
+def _relerr(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _anchor_rows(info):
+    return [j for j, ct in enumerate(info["contacts"]) if ct.get("anchor")]
+
+
+@pytest.mark.parametrize("compliance,vel", [(0.0, (0.0, 0.0, 0.0)), (2e-4, (0.3, 0.0, 0.2)),
+                                            (0.0, (0.0, -0.5, 0.0))])
+def test_anchor_frame_matches_oracle(compliance, vel):
+    sc = sg.hanging_cube(m=5, compliance=compliance, target_vel=vel)
+    q0, v0 = sg.perturbed_state(sc, seed=4, amp=0.002, vel_amp=0.1)
+    o = Oracle(sc)
+    q, v, info = o.frame(q0, v0, OracleOptions(n_iters=5, n_cr=sc.n_cr), t=0.0)
+    sim = Simulator(sc)
+    sim.set_state(q0, v0)
+    sim.step(n_iters=5)
+    qg, vg = sim.state()
+    assert _relerr(qg - q0, q - q0) < 1e-4
+    ct = sim.contacts()
+    assert len(ct["vertex"]) == len(info["contacts"]) == 1
+    assert ct["obstacle"][0] == len(sc.obstacles) + 0
+    assert _relerr(ct["lam"], info["lam"]) < 1e-4
+    res = sim.stats()["residuals"]
+    for rg, ro in zip(res, info["residuals"]):
+        assert abs(rg - ro) < 1e-6 + 1e-3 * ro
+    sim.close()
+
+
+def test_anchor_trajectory_free_running():
+    # 18 frames with a target moving down into a floor: the anchor drags the cube into
+    # contact. Free-running, so FP32 rounding accumulates (and the impacts amplify it): held
+    # to the trajectory gates, positions within 1e-3 L and energy within 1e-2, and the
+    # anchor's impulse within 5e-2 (it is -(q_v - p) / e, with e = 1e-4 m/N)
+    sc = sg.hanging_cube(m=4, compliance=1e-4, floor=True, target_vel=(0.0, 0.0, -1.0))
+    o = Oracle(sc)
+    sim = Simulator(sc)
+    q, v = sc.q0.copy(), sc.v0.copy()
+    n_contact = 0
+    for f in range(18):
+        q, v, info = o.frame(q, v, OracleOptions(n_iters=5, n_cr=sc.n_cr), t=f * sc.h)
+        sim.step(n_iters=5)
+        qg, vg = sim.state()
+        assert np.abs(qg - q).max() < 1e-3 * sc.bbox_diagonal
+        e_o, e_g = o.energy(q, v), o.energy(qg, vg)
+        assert abs(e_g - e_o) < 1e-2 * abs(e_o)
+        ct = sim.contacts()
+        ja = [k for k, ob in enumerate(ct["obstacle"]) if ob >= len(sc.obstacles)]
+        j = _anchor_rows(info)[0]
+        assert len(ja) == 1 and _relerr(ct["lam"][ja[0]], info["lam"][j]) < 5e-2
+        n_contact += len(info["contacts"]) > 1
+    assert n_contact >= 3
+    sim.close()
+
+
+def test_static_anchor_resynchronised_frames():
+    # a static target (time-independent), so every GPU frame can start from the oracle's
+    # state: 30 frames of a cube swinging from an off-centre anchor
+    sc = sg.hanging_cube(m=5, compliance=0.0)
+    sc.anchors[0].target = tuple(np.asarray(sc.anchors[0].target) + np.array([0.02, 0.0, 0.0]))
+    o = Oracle(sc)
+    sim = Simulator(sc)
+    q, v = sc.q0.copy(), sc.v0.copy()
+    for f in range(30):
+        sim.set_state(q, v)
+        qn, vn, info = o.frame(q, v, OracleOptions(n_iters=5, n_cr=sc.n_cr), t=0.0)
+        sim.step(n_iters=5)
+        qg, _ = sim.state()
+        assert _relerr(qg - q, qn - q) < 1e-4
+        q, v = qn, vn
+    sim.close()
+
+
+def _cr32(cr64):
+    def cr(apply, b, n_iter):
+        x = cr64(lambda v: apply(v.astype(np.float64)).astype(np.float32),
+                 b.astype(np.float32), n_iter)
+        return x.astype(np.float64)
+    return cr
+
+
+def test_anchored_star_handle_matches_oracle():
+    # the pulled star with its handle as hard anchors, pressed against a cylinder. The
+    # 256 hard anchor rows make the constraint operator ill-conditioned: the oracle's own
+    # frame moves by 5e-4 of its displacement when its conjugate residual runs in float32,
+    # so the GPU frame is held to 10x that deviation (the rule of the resynchronised drop)
+    base = sg.star_pull(n_side=16, layers=8)
+    top = int(np.argmax(base.X[:, 1]))
+    R = 0.03
+    x, y, z = base.X[top]
+    base.obstacles = [sg.Obstacle(sg.OBST_CYLINDER, (x, y + R - 0.003, z), (0.0, 0.0, 1.0),
+                                  radius=R, mu=0.3)] + base.obstacles
+    sc = sg.anchored_handle(base)
+    v0 = np.zeros_like(sc.q0)
+    v0[:, 0] = 0.5
+    import oracle.contact as OC
+    o = Oracle(sc)
+    opts = OracleOptions(n_iters=5, n_cr=sc.n_cr)
+    q, v, info = o.frame(sc.q0, v0, opts, t=0.0)
+    cr64 = OC.conjugate_residual
+    OC.conjugate_residual = _cr32(cr64)
+    try:
+        q32, _, _ = o.frame(sc.q0, v0, opts, t=0.0)
+    finally:
+        OC.conjugate_residual = cr64
+    dev32 = _relerr(q32 - sc.q0, q - sc.q0)
+    sim = Simulator(sc)
+    sim.set_state(sc.q0, v0)
+    sim.step(n_iters=5)
+    qg, _ = sim.state()
+    assert _relerr(qg - sc.q0, q - sc.q0) < max(1e-4, 10 * dev32)
+    ct = sim.contacts()
+    assert len(ct["vertex"]) == len(info["contacts"]) > len(sc.anchors)
+    sim.close()
+
+
+def test_anchor_frames_to_tolerance():
+    # the residual counts the anchor rows: a frame to 1e-6 ends with them satisfied
+    sc = sg.hanging_cube(m=4, compliance=5e-5, target_vel=(0.1, 0.0, 0.0))
+    sim = Simulator(sc, residual_tol=1e-6, max_iters=40)
+    for _ in range(5):
+        sim.step()
+        st = sim.stats()
+        assert st["residuals"][-1] <= 1e-6 or st["n_iters"] == 40
+    sim.close()

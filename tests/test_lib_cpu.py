@@ -133,3 +133,20 @@ def test_named_options_map_to_the_abi_values():
     assert (o.ncp, o.precond) == (0, 0)
     with pytest.raises(ValueError):
         _options(None, ncp="newton")
+
+
+@pytest.mark.parametrize("bad", ["pinned", "range", "twice", "compliance"])
+def test_invalid_anchors_are_rejected(bad):
+    sc = sg.hanging_cube(m=3)
+    a = sc.anchors[0]
+    if bad == "pinned":
+        sc.pinned = np.array([a.vertex], np.int32)
+    elif bad == "range":
+        a.vertex = sc.n_verts
+    elif bad == "twice":
+        sc.anchors.append(sg.Anchor(a.vertex, a.target))
+    else:
+        a.compliance = -1.0
+    with pytest.raises(SimError) as e:
+        Simulator(sc)
+    assert e.value.status == -1
