@@ -26,6 +26,12 @@ Readings of the paper used here (the paper leaves these open):
     compliance E_b = e entering the Schur system as E_b / h^2 and right-hand side
     -phi_b + J_b q^k like a normal row (Eqs. 19-21); they count in the residual with
     max |phi_b| / L;
+  * ADMM-PD (the paper's implementation follows Overby et al. 2017; Sec. 7): the scaled
+    dual variables u_i start at 0 every frame; per iteration z_i = prox of V_i psi_i with
+    weight w_i at G_i q + u_i, u_i += G_i q - z_i, and the global step reads z_i - u_i.
+    Its fixed point is stationary for the true incremental potential
+    |q - s~|_M^2 / (2 h^2) + sum_i V_i psi_i(G_i q), where the plain local step's is
+    stationary for the relaxed one (equal for ARAP);
   * the mass-inverse preconditioner, like the Delassus one, uses H (not J = Omega H, which
     depends on r) and gives the two friction rows h times the mean of their diagonal
     entries.
@@ -38,6 +44,8 @@ import numpy as np
 
 from . import contact as C
 from .fem import FEM
+from scenegen import MODEL_ARAP, MODEL_COROT
+
 from .local import elastic_energy, project
 
 
@@ -47,6 +55,7 @@ class OracleOptions:
     n_cr: int = 10
     exact_constraint_solve: bool = False   # dense solve instead of CR (isolates CR error)
     ncp: str = "fb"                        # "fb" (App. B.2) or "minmap" (App. B.1)
+    local: str = "pd"                      # "pd" (Eq. 5) or "admm" (ADMM-PD, Sec. 7)
     precond: str = "delassus"              # "delassus" (Eq. 28) or "mass" (Sec. 5.4)
 
 
@@ -71,6 +80,21 @@ class Oracle:
         f = self.fem
         F = f.deformation_gradients(q)
         return project(F, f.model, f.w, f.V, f.emu, f.elam, f.alpha)
+
+    def admm_local_step(self, q, u):
+        """ADMM-PD's local step with scaled dual variables u (one 3x3 per element): z_i the
+        proximal point of V_i psi_i with weight w_i at G_i q + u_i, then
+        u_i <- u_i + G_i q - z_i; the global step reads p_i = z_i - u_i. Returns (p, u).
+        ARAP elements use their energy mu ||F - R||^2 (co-rotational with lambda = 0), not
+        the SO(3) indicator of the plain local step."""
+        f = self.fem
+        F = f.deformation_gradients(q)
+        arap = f.model == MODEL_ARAP
+        model = np.where(arap, MODEL_COROT, f.model)
+        lam = np.where(arap, 0.0, f.elam)
+        z = project(F + u, model, f.w, f.V, f.emu, lam, f.alpha)
+        u = u + F - z
+        return z - u, u
 
     def contact_jacobian(self, contacts):
         """H (3c x 3n_f): rows n_j, f1_j, f2_j at the DoFs of contact j's vertex (Eqs. 36-37)."""
@@ -190,8 +214,14 @@ class Oracle:
         q_t_f = q_t[fv].reshape(-1)
         residuals = []
         lam_iters = []                     # lambda at each residual's iterate
+        if opts.local not in ("pd", "admm"):
+            raise ValueError("local must be 'pd' or 'admm'")
+        u = np.zeros((f.T, 3, 3))          # ADMM-PD duals, zero at every frame start
         for _k in range(opts.n_iters):
-            p = self.local_step(q)                                       # local step
+            if opts.local == "admm":
+                p, u = self.admm_local_step(q, u)                        # ADMM-PD
+            else:
+                p = self.local_step(q)                                   # local step
             b = f.assemble_rhs(s_tilde, p, q_pin)                        # RHS (Eq. 6)
             q_f = q[fv].reshape(-1)
             if c:

@@ -12,6 +12,7 @@ import pytest
 import scenegen as sg
 from oracle import Oracle, OracleOptions
 from oracle.fem import lame
+from oracle.local import elastic_energy
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -394,3 +395,51 @@ def test_anchor_row_is_solved_in_one_newton_step():
         (j,) = [k for k, ct in enumerate(info["contacts"]) if ct.get("anchor")]
         assert np.abs(info["final_state"]["phi"][j]).max() < 1e-14
         assert np.abs(info["lam"][j]).max() > 0.1
+
+
+def _incremental_potential(o, s_tilde, q):
+    """|q - s~|_M^2 / (2 h^2) + sum_i V_i psi_i(G_i q): the implicit-Euler objective (Eq. 1)
+    with each element's true energy."""
+    f = o.fem
+    kin = 0.5 / o.h ** 2 * float((f.mass[:, None] * (q - s_tilde) ** 2).sum())
+    return kin + elastic_energy(f.deformation_gradients(q), f.model, f.V, f.emu, f.elam, f.alpha)
+
+
+def _potential_gradient(o, s_tilde, q, eps=1e-7):
+    g = np.zeros_like(q)
+    for v in o.fem.free_verts:
+        for r in range(3):
+            qp, qm = q.copy(), q.copy()
+            qp[v, r] += eps
+            qm[v, r] -= eps
+            g[v, r] = (_incremental_potential(o, s_tilde, qp) -
+                       _incremental_potential(o, s_tilde, qm)) / (2 * eps)
+    return g
+
+
+@pytest.mark.parametrize("model", [sg.MODEL_COROT, sg.MODEL_SNH])
+def test_admm_pd_reaches_the_true_energy_minimiser(model):
+    # ADMM-PD's fixed point is stationary for the true incremental potential; the plain
+    # local-global iteration's is stationary for the relaxed one, not for this
+    sc = sg.cube_drop(m=3, model=model, E=2e5, nu=0.4, height=1.0)
+    q0, v0 = sg.perturbed_state(sc, seed=8, amp=0.004, vel_amp=0.2)
+    o = Oracle(sc)
+    s_tilde = o.predict(q0, v0)
+    scale = np.abs(o.fem.mass[:, None] * (q0 - s_tilde)).max() / sc.h ** 2
+    q_admm, _, _ = o.frame(q0, v0, OracleOptions(n_iters=400, local="admm"))
+    q_pd, _, _ = o.frame(q0, v0, OracleOptions(n_iters=400))
+    g_admm = np.abs(_potential_gradient(o, s_tilde, q_admm)).max()
+    g_pd = np.abs(_potential_gradient(o, s_tilde, q_pd)).max()
+    assert g_admm < 1e-6 * scale
+    assert g_pd > 1e-3 * scale
+
+
+def test_admm_pd_equals_pd_for_arap():
+    # for ARAP the relaxed energy w/2 |F - R|^2 is the element's energy, so both iterations
+    # reach the same frame
+    sc = sg.cube_drop(m=3, model=sg.MODEL_ARAP, E=2e5, nu=0.4, height=1.0)
+    q0, v0 = sg.perturbed_state(sc, seed=9, amp=0.004, vel_amp=0.2)
+    o = Oracle(sc)
+    q_admm, _, _ = o.frame(q0, v0, OracleOptions(n_iters=1200, local="admm"))
+    q_pd, _, _ = o.frame(q0, v0, OracleOptions(n_iters=1200))
+    assert np.abs(q_admm - q_pd).max() < 1e-12 * sc.bbox_diagonal
