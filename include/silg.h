@@ -58,6 +58,10 @@ enum { SIM_S_FP32 = 0,          /* S stored in FP32                             
        SIM_S_BF16 = 1 };        /* S stored in BF16, FP32 accumulation                     */
 enum { SIM_NCP_FB = 0,          /* Fischer-Burmeister complementarity functions (App. B.2) */
        SIM_NCP_MINMAP = 1 };    /* minimum-map functions (App. B.1)                       */
+enum { SIM_LOCAL_PD = 0,        /* the local step of Eq. 5 (projective dynamics)          */
+       SIM_LOCAL_ADMM = 1 };    /* ADMM-PD: scaled dual variables per element, zero at each
+                                   frame start; the local step projects G q + u, the global
+                                   step reads z - u; ARAP elements use mu |F - R|^2        */
 enum { SIM_PRECOND_DELASSUS = 0,/* r_n = h^2 W_jj, r_f = h W_jj from the Delassus operator
                                    (Eq. 28)                                               */
        SIM_PRECOND_MASS = 1 };  /* r_n = h^2 [H M^-1 H^T]_jj, r_f = h [H M^-1 H^T]_jj: the
@@ -123,6 +127,7 @@ typedef struct {
                                   CUDA graph while-node); 0 (default): n_iters <= 0 means
                                   the option's n_iters. Negative or NaN: SIM_EINVAL.     */
   int32_t max_iters;           /* cap of those iterations, 1..63 (default 40)             */
+  int32_t local_solver;        /* SIM_LOCAL_PD (default) or SIM_LOCAL_ADMM                */
 } sim_options;
 
 /* Launch configuration of the two profile products (z = S g, x = S^T y), chosen by the

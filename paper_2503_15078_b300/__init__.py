@@ -110,9 +110,10 @@ def _options(scene=None, **kw):
     return o
 
 
-# options that also take names: the complementarity functions (App. B.1-B.2) and the
-# complementarity preconditioner (Sec. 5.4)
-_NAMED = {"ncp": {"fb": 0, "minmap": 1}, "precond": {"delassus": 0, "mass": 1}}
+# options that also take names: the complementarity functions (App. B.1-B.2), the
+# complementarity preconditioner (Sec. 5.4) and the local step (PD or ADMM-PD)
+_NAMED = {"ncp": {"fb": 0, "minmap": 1}, "precond": {"delassus": 0, "mass": 1},
+          "local_solver": {"pd": 0, "admm": 1}}
 
 
 class Plan:

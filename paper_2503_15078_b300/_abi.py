@@ -55,7 +55,8 @@ class SimOptions(C.Structure):
                 ("spin_limit", C.c_uint64), ("cuda_stream", C.c_void_p),
                 ("n_host_threads", C.c_int32), ("autotune", C.c_int32),
                 ("ncp", C.c_int32), ("precond", C.c_int32),
-                ("residual_tol", C.c_double), ("max_iters", C.c_int32)]
+                ("residual_tol", C.c_double), ("max_iters", C.c_int32),
+                ("local_solver", C.c_int32)]
 
 
 class SimTuning(C.Structure):

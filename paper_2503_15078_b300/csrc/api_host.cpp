@@ -46,6 +46,7 @@ void sim_default_options(sim_options* o) {
   o->precond = SIM_PRECOND_DELASSUS;
   o->residual_tol = 0.0;
   o->max_iters = 40;
+  o->local_solver = SIM_LOCAL_PD;
 }
 
 int sim_plan_create(const sim_mesh* mesh, const sim_material* mats, int32_t n_mat, double h,

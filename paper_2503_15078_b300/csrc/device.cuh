@@ -44,6 +44,10 @@ struct DevSim {
   int n, n_all, n_tets, n_pad, n_obs, n_mat;
   int cap, cap_y, n_cr;
   int ncp, precond;  // SIM_NCP_*, SIM_PRECOND_*
+  // ADMM-PD (SIM_LOCAL_ADMM): scaled duals per element, 9 FP32 values stored k * n_tets + t,
+  // zeroed at every frame start (null with the plain local step)
+  int admm;
+  float* tet_u;
   // iterating to a tolerance (sim_options.residual_tol > 0, sim_step with n_iters <= 0): the
   // device counts the finished global updates and a CUDA graph while-node repeats the
   // iteration until R_k <= res_tol or max_iters updates

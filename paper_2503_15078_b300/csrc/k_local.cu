@@ -305,7 +305,26 @@ __global__ void __launch_bounds__(128) k_local(DevSim d) {
   const MatDev m = d.mats[d.tet_mat[t]];
   const float w = d.tet_w[t], V = d.tet_vol[t];
   float p[9];
-  project_tet(F, m.model, w, V, m.mu, m.lam, m.alpha, p);
+  if (d.admm && !kDebug) {
+    // ADMM-PD: z = prox at F + u (ARAP as mu |F - R|^2: co-rotational with lambda = 0),
+    // u += F - z, and the global step reads z - u
+    float y[9], u[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      u[k] = d.tet_u[(size_t)k * T + t];
+      y[k] = F[k] + u[k];
+    }
+    const bool arap = m.model == SIM_MODEL_ARAP;
+    project_tet(y, arap ? SIM_MODEL_COROT : m.model, w, V, m.mu, arap ? 0.f : m.lam, m.alpha, p);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float un = u[k] + F[k] - p[k];
+      d.tet_u[(size_t)k * T + t] = un;
+      p[k] -= un;
+    }
+  } else {
+    project_tet(F, m.model, w, V, m.mu, m.lam, m.alpha, p);
+  }
   if (kDebug) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) d.p_out[9 * t + k] = p[k];

@@ -174,6 +174,7 @@ void enqueue_frame(sim_s* s, int K, cudaStream_t st) {
   cudaMemsetAsync(d.resid, 0, sizeof(double) * (silg::kMaxIters + 1), st);
   cudaMemsetAsync(d.resid_scene, 0, sizeof(double) * (silg::kMaxIters + 1) * d.n_scenes, st);
   cudaMemsetAsync(d.max_pen, 0, sizeof(double), st);
+  if (d.admm) cudaMemsetAsync(d.tet_u, 0, sizeof(float) * 9 * (size_t)d.n_tets, st);
   silg::launch_frame_begin(d, st);
   // the first local step needs only the prediction: with a cold start it runs beside the
   // collision and Delassus work (a warm start moves q^0, so then it waits)
@@ -263,6 +264,7 @@ cudaError_t enqueue_frame_to_tolerance(sim_s* s, cudaStream_t st) {
   cudaMemsetAsync(d.resid_scene, 0, sizeof(double) * (silg::kMaxIters + 1) * d.n_scenes, st);
   cudaMemsetAsync(d.max_pen, 0, sizeof(double), st);
   cudaMemsetAsync(d.iter_k, 0, sizeof(int), st);
+  if (d.admm) cudaMemsetAsync(d.tet_u, 0, sizeof(float) * 9 * (size_t)d.n_tets, st);
   silg::launch_frame_begin(d, st);
   const bool early_local = s->has_obstacles && d.ws_mode == 0;
   if (early_local) {
@@ -558,6 +560,8 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   d.pf_copies = 1;
   d.res_tol = o->residual_tol;
   d.max_iters = o->max_iters;
+  d.admm = o->local_solver == SIM_LOCAL_ADMM;
+  d.tet_u = d.admm ? s->alloc<float>(9 * (size_t)T) : nullptr;
   d.h = p.h;
   d.h2f = (float)(p.h * p.h);
   for (int r = 0; r < 3; ++r) d.grav[r] = o->gravity[r];
@@ -894,6 +898,7 @@ int check_options(const sim_options* o) {
   if (o->s_precision != SIM_S_FP32 && o->s_precision != SIM_S_BF16) return SIM_EINVAL;
   if (o->refine < 0 || o->refine > 2) return SIM_EINVAL;
   if (o->ncp != SIM_NCP_FB && o->ncp != SIM_NCP_MINMAP) return SIM_EINVAL;
+  if (o->local_solver != SIM_LOCAL_PD && o->local_solver != SIM_LOCAL_ADMM) return SIM_EINVAL;
   if (!(o->residual_tol >= 0.0) || o->max_iters < 1 || o->max_iters > silg::kMaxIters)
     return SIM_EINVAL;
   if (o->precond != SIM_PRECOND_DELASSUS && o->precond != SIM_PRECOND_MASS) return SIM_EINVAL;

@@ -118,7 +118,8 @@ def test_create_without_a_gpu_fails_loudly():
                                   {"refine": -1}, {"n_iters": 65}, {"contact_capacity": 0},
                                   {"ncp": 2}, {"ncp": -1}, {"precond": 2},
                                   {"residual_tol": -1.0}, {"residual_tol": float("nan")},
-                                  {"max_iters": 0}, {"max_iters": 64}])
+                                  {"max_iters": 0}, {"max_iters": 64},
+                                  {"local_solver": 2}])
 def test_invalid_options_are_rejected_before_any_device_work(opts):
     with pytest.raises(SimError) as e:
         Simulator(sg.cube_drop(m=3), **opts)
