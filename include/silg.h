@@ -128,6 +128,15 @@ typedef struct {
                                   the option's n_iters. Negative or NaN: SIM_EINVAL.     */
   int32_t max_iters;           /* cap of those iterations, 1..63 (default 40)             */
   int32_t local_solver;        /* SIM_LOCAL_PD (default) or SIM_LOCAL_ADMM                */
+  /* Device memory of the simulator's buffers (all of them; not the page-locked host
+   * staging, not a network's or the allocation-free solve's): dev_alloc(bytes, alloc_ctx)
+   * must return memory on opts->device aligned to 256 bytes, or NULL (sim_create then
+   * returns SIM_ENOMEM); dev_free(ptr, alloc_ctx) releases it, in sim_destroy or when
+   * creation fails. Both NULL (default): cudaMalloc / cudaFree. Only one of them set:
+   * SIM_EINVAL. The calls happen inside sim_create / sim_create_batch and sim_destroy. */
+  void* (*dev_alloc)(size_t bytes, void* ctx);
+  void (*dev_free)(void* ptr, void* ctx);
+  void* alloc_ctx;
 } sim_options;
 
 /* Launch configuration of the two profile products (z = S g, x = S^T y), chosen by the

@@ -101,6 +101,10 @@ def _options(scene=None, **kw):
         if k == "gravity":
             for r in range(3):
                 o.gravity[r] = float(v[r])
+        elif k in ("dev_alloc", "dev_free") and v is not None and callable(v) \
+                and not isinstance(v, (_abi.DEV_ALLOC, _abi.DEV_FREE)):
+            # a Python callable: wrapped (the options struct keeps the wrapper alive)
+            setattr(o, k, (_abi.DEV_ALLOC if k == "dev_alloc" else _abi.DEV_FREE)(v))
         elif k in _NAMED and isinstance(v, str):
             if v not in _NAMED[k]:
                 raise ValueError(f"{k} must be one of {sorted(_NAMED[k])}")

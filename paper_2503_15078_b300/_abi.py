@@ -48,6 +48,11 @@ class SimScene(C.Structure):
                 ("anchors", C.POINTER(SimAnchor)), ("n_anchors", C.c_int32)]
 
 
+# device allocator hooks of sim_options
+DEV_ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+DEV_FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
 class SimOptions(C.Structure):
     _fields_ = [("n_iters", C.c_int32), ("n_cr_iters", C.c_int32), ("s_precision", C.c_int32),
                 ("refine", C.c_int32), ("contact_capacity", C.c_int32), ("device", C.c_int32),
@@ -56,7 +61,8 @@ class SimOptions(C.Structure):
                 ("n_host_threads", C.c_int32), ("autotune", C.c_int32),
                 ("ncp", C.c_int32), ("precond", C.c_int32),
                 ("residual_tol", C.c_double), ("max_iters", C.c_int32),
-                ("local_solver", C.c_int32)]
+                ("local_solver", C.c_int32),
+                ("dev_alloc", DEV_ALLOC), ("dev_free", DEV_FREE), ("alloc_ctx", C.c_void_p)]
 
 
 class SimTuning(C.Structure):

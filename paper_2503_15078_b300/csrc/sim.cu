@@ -48,6 +48,9 @@ struct sim_s {
   bool has_obstacles = false;
   std::map<int, Graph> graphs;
   std::vector<void*> allocs;
+  void* (*dev_alloc)(size_t, void*) = nullptr;   // the caller's device allocator, if any
+  void (*dev_free)(void*, void*) = nullptr;
+  void* alloc_ctx = nullptr;
   int64_t frame = 0;
   int last_iters = 0;             // -1: a frame to a tolerance whose count is on the device
   bool last_to_tol = false;       // the most recent frame iterated to a tolerance
@@ -63,7 +66,12 @@ struct sim_s {
   T* alloc(size_t count) {
     void* p = nullptr;
     if (count == 0) count = 1;
-    if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) throw std::bad_alloc();
+    if (dev_alloc) {
+      p = dev_alloc(count * sizeof(T), alloc_ctx);
+      if (!p) throw std::bad_alloc();
+    } else if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+      throw std::bad_alloc();
+    }
     allocs.push_back(p);
     cudaMemsetAsync(p, 0, count * sizeof(T), work);
     return static_cast<T*>(p);
@@ -80,7 +88,12 @@ struct sim_s {
       if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
       if (kv.second.g) cudaGraphDestroy(kv.second.g);
     }
-    for (void* p : allocs) cudaFree(p);
+    for (void* p : allocs) {
+      if (dev_free)
+        dev_free(p, alloc_ctx);
+      else
+        cudaFree(p);
+    }
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     for (cudaEvent_t e : fj) cudaEventDestroy(e);
     if (pinned) cudaFreeHost(pinned);
@@ -901,6 +914,7 @@ int check_options(const sim_options* o) {
   if (o->local_solver != SIM_LOCAL_PD && o->local_solver != SIM_LOCAL_ADMM) return SIM_EINVAL;
   if (!(o->residual_tol >= 0.0) || o->max_iters < 1 || o->max_iters > silg::kMaxIters)
     return SIM_EINVAL;
+  if ((o->dev_alloc == nullptr) != (o->dev_free == nullptr)) return SIM_EINVAL;
   if (o->precond != SIM_PRECOND_DELASSUS && o->precond != SIM_PRECOND_MASS) return SIM_EINVAL;
   return SIM_OK;
 }
@@ -932,6 +946,9 @@ int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_opt
   if (nv_tot >= (1LL << 31) || nt_tot >= (1LL << 29)) return SIM_EINVAL;
   sim_s* s = new (std::nothrow) sim_s();
   if (!s) return SIM_ENOMEM;
+  s->dev_alloc = o->dev_alloc;
+  s->dev_free = o->dev_free;
+  s->alloc_ctx = o->alloc_ctx;
   int st = guarded([&]() {
     std::vector<double> X;
     std::vector<int32_t> tets, tmat, pinned, vscene;

@@ -151,3 +151,9 @@ def test_invalid_anchors_are_rejected(bad):
     with pytest.raises(SimError) as e:
         Simulator(sc)
     assert e.value.status == -1
+
+
+def test_allocator_hooks_must_come_in_pairs():
+    with pytest.raises(SimError) as e:
+        Simulator(sg.cube_drop(m=3), dev_alloc=lambda n, c: None)
+    assert e.value.status == -1
