@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--n-side", type=int, default=42)
     ap.add_argument("--s-precision", choices=["fp32", "bf16"], default="fp32",
                     help="storage of the S~ values (bf16: FP32 accumulation)")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the timing of the paper's variants on the star frame")
     ap.add_argument("--no-warmstart", action="store_true",
                     help="skip the learned-vs-plain frame time to residual 1e-4")
     ap.add_argument("--workload", choices=["star", "batch64"], default="star",
@@ -348,6 +350,44 @@ def warmstart_ab():
     return out
 
 
+def variants_timing(scene, q0, v0, steps, flush):
+    """The placed star frame with each of the paper's variants (and ADMM-PD and the anchored
+    handle): device ms per local-global iteration, mean over `steps` replays after 3
+    warm-ups, L2 flushed before each; the variant's final residual is reported with it."""
+    import numpy as np
+    import torch
+    import scenegen as sg
+    from paper_2503_15078_b300 import Simulator
+    cases = {"minmap": dict(ncp="minmap"), "mass_precond": dict(precond="mass"),
+             "admm_pd": dict(local_solver="admm"), "anchored_handle": {}}
+    out = {}
+    for name, kw in cases.items():
+        sc, v = scene, v0.copy()
+        if name == "anchored_handle":
+            # the handle's vertices free, tied by hard anchors to targets that start where
+            # the placed state has them and move with the handle
+            sc = sg.anchored_handle(scene)
+            sc.anchors = [sg.Anchor(a.vertex, tuple(q0[a.vertex]), a.vel, 0.0)
+                          for a in sc.anchors]
+            v[scene.pinned] = np.asarray(scene.handle_vel)
+        sim = Simulator(sc, autotune=0, **kw)
+        times, res = [], []
+        for k in range(3 + steps):
+            sim.set_state(q0, v)
+            flush.zero_()
+            torch.cuda.synchronize()
+            sim.step()
+            ph = sim.phase_times()
+            if k >= 3:
+                times.append(sum(ph.values()) / sc.n_iters)
+                res.append(sim.stats()["residuals"][-1])
+        out[name] = {"ms_per_iter": round(statistics.mean(times), 5),
+                     "contacts": sim.stats()["n_contacts"],
+                     "final_residual": float(f"{statistics.mean(res):.3e}")}
+        sim.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -504,6 +544,8 @@ def run_ours(args):
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
+    if rank == 0 and not batch and not args.no_variants:
+        out["variants"] = variants_timing(scene, q0, v0, min(args.steps, 10), flush)
     if rank == 0 and not batch and not args.no_warmstart:
         out["warmstart"] = warmstart_ab()
     if rank == 0:
