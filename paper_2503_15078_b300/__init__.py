@@ -304,6 +304,11 @@ class Simulator:
         _check(lib().sim_set_warmstart(self._h, net.handle if net is not None else None,
                                        int(mode)), "sim_set_warmstart")
 
+    def set_phase_marks(self, on):
+        """Event nodes around every phase of every iteration (True) or only around the
+        once-per-frame phases, the iterations timed as one phase (False)."""
+        _check(lib().sim_set_phase_marks(self._h, int(bool(on))), "sim_set_phase_marks")
+
     def set_portfolio(self, copies):
         """Scenes are groups of `copies` identical copies: copy 0 runs cold, the others the
         warm start, and each frame every copy continues from the best one (1: off)."""

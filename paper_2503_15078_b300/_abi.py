@@ -61,7 +61,7 @@ class SimOptions(C.Structure):
                 ("n_host_threads", C.c_int32), ("autotune", C.c_int32),
                 ("ncp", C.c_int32), ("precond", C.c_int32),
                 ("residual_tol", C.c_double), ("max_iters", C.c_int32),
-                ("local_solver", C.c_int32),
+                ("local_solver", C.c_int32), ("phase_marks", C.c_int32),
                 ("dev_alloc", DEV_ALLOC), ("dev_free", DEV_FREE), ("alloc_ctx", C.c_void_p)]
 
 
@@ -97,6 +97,7 @@ PROTOTYPES = {
     "sim_mlp_create": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_void_p)]),
     "sim_set_warmstart": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "sim_set_portfolio": (C.c_int, [C.c_void_p, C.c_int32]),
+    "sim_set_phase_marks": (C.c_int, [C.c_void_p, C.c_int32]),
     "sim_get_warmstart_samples": (C.c_int, [C.c_void_p, C.c_int32, _fp, _fp,
                                             C.POINTER(C.c_int32)]),
     "sim_mlp_destroy": (None, [C.c_void_p]),

@@ -47,6 +47,7 @@ void sim_default_options(sim_options* o) {
   o->residual_tol = 0.0;
   o->max_iters = 40;
   o->local_solver = SIM_LOCAL_PD;
+  o->phase_marks = 1;
 }
 
 int sim_plan_create(const sim_mesh* mesh, const sim_material* mats, int32_t n_mat, double h,

@@ -54,6 +54,8 @@ struct sim_s {
   int64_t frame = 0;
   int last_iters = 0;             // -1: a frame to a tolerance whose count is on the device
   bool last_to_tol = false;       // the most recent frame iterated to a tolerance
+  bool phase_marks = true;        // event nodes around every phase of every iteration
+  bool last_marks = true;         // ... in the most recent frame
   // phase events recorded by event nodes of the frame graph: [0] frame start,
   // [1] after collision, [2] after Delassus, [3] after the warm start, then kMarksPerIter
   // per iteration, then [end]
@@ -171,6 +173,10 @@ void enqueue_frame(sim_s* s, int K, cudaStream_t st) {
   const DevSim& d = s->d;
   // external event-record nodes: observable from the host after each graph launch
   auto mark = [&](int i) { cudaEventRecordWithFlags(s->ev[i], st, cudaEventRecordExternal); };
+  // per-iteration marks only with phase_marks (each event node costs a few microseconds)
+  auto imark = [&](int i) {
+    if (s->phase_marks) mark(i);
+  };
   // two branches of the graph: work forked onto the aux stream and joined back
   int n_fj = 0;
   auto fork = [&]() {
@@ -220,21 +226,21 @@ void enqueue_frame(sim_s* s, int K, cudaStream_t st) {
     } else {
       silg::launch_local(d, st, false);
     }
-    mark(e);
+    imark(e);
     silg::launch_rhs(d, st);
-    mark(e + 1);
+    imark(e + 1);
     silg::launch_pass1(d, st);
-    mark(e + 2);
+    imark(e + 2);
     silg::launch_reduce1(d, st);
-    mark(e + 3);
+    imark(e + 3);
     if (s->has_obstacles) {
       silg::launch_ytz(d, st);
       silg::launch_cr(d, st, s->cluster);
       silg::launch_yu(d, st);
     }
-    mark(e + 4);
+    imark(e + 4);
     silg::launch_pass2(d, st);
-    mark(e + 5);
+    imark(e + 5);
     silg::launch_reduce2(d, st, silg::kOutDq);
     if (k >= K - refined_iters(s, K)) {
       // BF16 profile: dq += S~^T S~ (rhs - A~ dq), the residual summed in FP64 and the
@@ -244,15 +250,16 @@ void enqueue_frame(sim_s* s, int K, cudaStream_t st) {
       dr.gvec = d.gsave;
       silg::launch_solve(dr, st, silg::kOutAddDq);
     }
-    mark(e + 6);
+    imark(e + 6);
   }
+  if (!s->phase_marks) mark(4);   // the iterations as one phase
   if (s->has_obstacles) {
     silg::launch_contact_eval(d, st, K, true);
     silg::launch_ws_record(d, st);
   }
   silg::launch_integrate(d, st);
   if (s->has_obstacles && d.pf_copies > 1) silg::launch_pf_sync(d, st, K);
-  mark(4 + kMarksPerIter * K);
+  mark(s->phase_marks ? 4 + kMarksPerIter * K : 5);
 }
 
 // A frame that iterates until the residual reaches sim_options.residual_tol (at least one
@@ -379,9 +386,10 @@ cudaError_t enqueue_frame_to_tolerance(sim_s* s, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// frame graphs are cached per (iteration count, warm-start mode); K = 0: to a tolerance
+// frame graphs are cached per (iteration count, phase marks, warm-start mode); K = 0: to a
+// tolerance
 int get_graph(sim_s* s, int K, cudaGraphExec_t* out) {
-  const int key = 4 * K + s->d.ws_mode;
+  const int key = 8 * K + (K > 0 && s->phase_marks ? 4 : 0) + s->d.ws_mode;
   auto it = s->graphs.find(key);
   if (it != s->graphs.end()) {
     *out = it->second.exec;
@@ -946,6 +954,7 @@ int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_opt
   if (nv_tot >= (1LL << 31) || nt_tot >= (1LL << 29)) return SIM_EINVAL;
   sim_s* s = new (std::nothrow) sim_s();
   if (!s) return SIM_ENOMEM;
+  s->phase_marks = o->phase_marks != 0;
   s->dev_alloc = o->dev_alloc;
   s->dev_free = o->dev_free;
   s->alloc_ctx = o->alloc_ctx;
@@ -1131,6 +1140,12 @@ int sim_set_warmstart(sim_t* s, const sim_mlp_t* net, int32_t mode) {
   return SIM_OK;
 }
 
+int sim_set_phase_marks(sim_t* s, int32_t on) {
+  if (!s || (on != 0 && on != 1)) return SIM_EINVAL;
+  s->phase_marks = on != 0;   // graphs are cached per setting
+  return SIM_OK;
+}
+
 int sim_set_portfolio(sim_t* s, int32_t copies) {
   if (!s || copies < 1) return SIM_EINVAL;
   const Plan& p = s->plan;
@@ -1258,6 +1273,7 @@ int sim_step(sim_t* s, int32_t n_iters) {
   s->frame += 1;
   s->last_iters = to_tol ? -1 : K;
   s->last_to_tol = to_tol;
+  s->last_marks = s->phase_marks;
   return SIM_OK;
 }
 
@@ -1355,7 +1371,7 @@ int sim_get_phase_times(sim_t* s, double* ms) {
     cudaEventElapsedTime(&t, s->ev[a], s->ev[b]);
     return (double)t;
   };
-  if (s->last_to_tol) {
+  if (s->last_to_tol || !s->last_marks) {
     cudaError_t e = cudaEventSynchronize(s->ev[5]);
     if (e != cudaSuccess) return cuda_status(e);
     ms[SIM_PHASE_COLLIDE] = el(0, 1);

@@ -98,3 +98,28 @@ def test_tolerance_frames_in_a_batch_and_a_trajectory():
             assert all(x > 1e-4 for x in r[1:-1])
     assert max(counts) > 1
     sim.close()
+
+
+def test_frames_without_phase_marks_are_the_same_frames():
+    # the production graph (event nodes only around the once-per-frame phases) computes
+    # the instrumented graph's frame bit for bit, reports the iterations as one phase, and
+    # is faster (each event node costs a few microseconds)
+    sc = sg.warmstart_scenes([101], frames=60)[0]
+    q, v = _contact_state(sc)
+    sim = Simulator(sc)
+    out = {}
+    for marks in (True, False, True, False):
+        sim.set_phase_marks(marks)
+        times = []
+        for _ in range(6):
+            sim.set_state(q, v)
+            sim.step(n_iters=8)
+            ph = sim.phase_times()
+            times.append(sum(ph.values()))
+        out[marks] = (sim.state()[0], sim.stats()["residuals"], ph, min(times))
+    assert np.array_equal(out[True][0], out[False][0])
+    assert out[True][1] == out[False][1]
+    assert out[False][2]["iterations"] > 0 and out[False][2]["local"] == 0.0
+    assert out[True][2]["iterations"] == 0.0 and out[True][2]["local"] > 0
+    assert out[False][3] < out[True][3]
+    sim.close()
