@@ -15,6 +15,38 @@
 
 namespace silg {
 
+// First instruction of a kernel that may be launched with programmatic dependent launch:
+// blocks until the grids it depends on have completed and their writes are visible (a
+// no-op for a kernel launched without it), then allows its own dependent grid to launch.
+__device__ __forceinline__ void pdl_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  // and let the next grid be launched now: its blocks are scheduled as this grid's leave
+  // and wait (above) until this grid has completed
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// kernel<<<grid, block, smem, s>>>(args...), with programmatic stream serialisation when
+// pdl is set
+template <class Kernel, class... Args>
+inline cudaError_t launch_k(bool pdl, Kernel kernel, unsigned grid, unsigned block, size_t smem,
+                            cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+}  // namespace silg
+
+namespace silg {
+
 constexpr int kWarps = 8;                     // warps per CTA of the profile products
 constexpr int kRowsPerWarp = kRowGroup / kWarps;
 constexpr int kMaxIters = SIM_MAX_RESIDUALS - 1;
@@ -222,6 +254,11 @@ struct DevSim {
   int* cr_split;    // per scene 2 (kCrMaxRanks + 1): first contact vertex (scene-local) and
                     // first contact (global) of each rank
   unsigned long long spin_limit;  // polls of a device-side wait before it reports a timeout
+  // launch the straight-line kernels of an iteration with programmatic dependent launch
+  // (the next kernel's launch overlaps the tail of the one before; it waits for that one's
+  // completion at its first instruction). Host-side switch, set while capturing a
+  // production frame graph, whose kernels are not separated by event nodes.
+  int pdl;
   // diagnostics
   double* resid;    // kMaxIters + 1
   double* max_pen;

@@ -615,6 +615,7 @@ __global__ void k_contact_eval(DevSim d, int k, int final_eval) {
 // partial sums are combined in a fixed order.
 constexpr int kYtzThreads = 128;
 __global__ void __launch_bounds__(kYtzThreads) k_ytz(DevSim d) {
+  pdl_wait();
   const int ncv = min(d.counters[kCntCv], d.cap);
   if (d.yc_ptr[ncv] > d.cap_y) return;   // uniform over the grid
   __shared__ float part[3][kYtzThreads / 32];
@@ -664,6 +665,7 @@ __global__ void __launch_bounds__(kYtzThreads) k_ytz(DevSim d) {
 
 // y = z + h^2 Y u, in place on z (rows of U only)
 __global__ void k_yu(DevSim d) {
+  pdl_wait();
   const int lane = threadIdx.x & 31, nwarps = (gridDim.x * blockDim.x) >> 5;
   const int nU = d.counters[kCntU];
   if (d.y_ptr[nU] > d.cap_y) return;
@@ -727,6 +729,7 @@ struct CrLayout {
 };
 
 __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) {
+  pdl_wait();
   extern __shared__ __align__(16) float sm[];
   cg::cluster_group cl = cg::this_cluster();
   CrLayout L;
@@ -1138,11 +1141,11 @@ void launch_iter_decide(const DevSim& d, cudaStream_t s, cudaGraphConditionalHan
 void launch_iter_clear(const DevSim& d, cudaStream_t s) { k_iter_clear<<<1, 256, 0, s>>>(d); }
 
 void launch_ytz(const DevSim& d, cudaStream_t s) {
-  k_ytz<<<std::min(d.cap, 8 * d.n_sm), kYtzThreads, 0, s>>>(d);
+  launch_k(d.pdl, k_ytz, std::min(d.cap, 8 * d.n_sm), kYtzThreads, 0, s, d);
 }
 
 void launch_yu(const DevSim& d, cudaStream_t s) {
-  k_yu<<<std::min((d.n * 32 + 255) / 256, 8 * d.n_sm), 256, 0, s>>>(d);
+  launch_k(d.pdl, k_yu, std::min((d.n * 32 + 255) / 256, 8 * d.n_sm), 256, 0, s, d);
 }
 
 static size_t g_cr_smem = 0;
@@ -1192,13 +1195,15 @@ int launch_cr(const DevSim& d, cudaStream_t s, int cluster) {
   cfg.blockDim = dim3(kCrThreads);
   cfg.dynamicSmemBytes = g_cr_smem;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = cluster;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = d.pdl ? 2 : 1;
   return cudaLaunchKernelEx(&cfg, k_cr, d, (int)g_cr_smem) == cudaSuccess ? SIM_OK : SIM_ECUDA;
 }
 

@@ -263,6 +263,7 @@ __global__ void k_split_ref(DevSim d) {
 
 template <bool kDebug>
 __global__ void __launch_bounds__(128) k_local(DevSim d) {
+  pdl_wait();
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= d.n_tets) return;
   const int T = d.n_tets;
@@ -415,7 +416,7 @@ void launch_local(const DevSim& d, cudaStream_t s, bool debug_p) {
     k_split_ref<<<(d.n_all + 255) / 256, 256, 0, s>>>(d);
     k_local<true><<<grid, 128, 0, s>>>(d);
   } else {
-    k_local<false><<<grid, 128, 0, s>>>(d);
+    launch_k(d.pdl, k_local<false>, grid, 128, 0, s, d);
   }
 }
 

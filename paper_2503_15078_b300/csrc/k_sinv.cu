@@ -127,6 +127,7 @@ __device__ __forceinline__ LaneMeta fetch_meta(const DevSim& d, const int2* tile
 // U: tiles in flight per warp (the format's default, or half of it).
 template <class T, int U>
 __global__ void __launch_bounds__(256, PassOcc<T, U>::kMinBlocks) k_pass1(DevSim d) {
+  pdl_wait();
   using F = Fmt<T>;
   static_assert(U * kRowsPerWarp <= 32, "one metadata entry per lane");
   const T* S = F::vals(d);
@@ -222,6 +223,7 @@ __global__ void __launch_bounds__(256, PassOcc<T, U>::kMinBlocks) k_pass1(DevSim
 
 // z_r = sum of its row group's slots, in slot order; zero padding beyond n.
 __global__ void k_reduce1(DevSim d) {
+  pdl_wait();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= d.n_pad) return;
   if (r >= d.n) {
@@ -247,6 +249,7 @@ constexpr size_t kP2Smem = sizeof(float) * kWarps * 3 * TW;
 // x partials: one slot per run of tiles of one column tile -> p2_part[slot][comp][column]
 template <class T, int U>
 __global__ void __launch_bounds__(256, PassOcc<T, U>::kMinBlocks) k_pass2(DevSim d) {
+  pdl_wait();
   using F = Fmt<T>;
   static_assert(U * kRowsPerWarp <= 32, "one metadata entry per lane");
   const T* S = F::vals(d);
@@ -343,6 +346,7 @@ __global__ void __launch_bounds__(256, PassOcc<T, U>::kMinBlocks) k_pass2(DevSim
 // displacement dq (AoS, FP32), to xout (AoS), or added into one of them.
 template <int kMode>
 __global__ void k_reduce2(DevSim d) {
+  pdl_wait();
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= d.n) return;
   const int ct = c / TW, lc = c % TW;
@@ -426,40 +430,40 @@ void launch_pass1(const DevSim& d, cudaStream_t s) {
   const size_t smem = (size_t)d.s1_max_cols * 3 * TW * sizeof(float);
   const int g = d.s1_grid;
   if (d.s_bf16) {
-    if (d.s1_unroll == 2) k_pass1<unsigned short, 8><<<g, 256, smem, s>>>(d);
-    else if (d.s1_unroll == 1) k_pass1<unsigned short, 4><<<g, 256, smem, s>>>(d);
-    else k_pass1<unsigned short, 2><<<g, 256, smem, s>>>(d);
+    if (d.s1_unroll == 2) launch_k(d.pdl, k_pass1<unsigned short, 8>, g, 256, smem, s, d);
+    else if (d.s1_unroll == 1) launch_k(d.pdl, k_pass1<unsigned short, 4>, g, 256, smem, s, d);
+    else launch_k(d.pdl, k_pass1<unsigned short, 2>, g, 256, smem, s, d);
   } else {
-    if (d.s1_unroll == 2) k_pass1<float, 4><<<g, 256, smem, s>>>(d);
-    else if (d.s1_unroll == 1) k_pass1<float, 2><<<g, 256, smem, s>>>(d);
-    else k_pass1<float, 1><<<g, 256, smem, s>>>(d);
+    if (d.s1_unroll == 2) launch_k(d.pdl, k_pass1<float, 4>, g, 256, smem, s, d);
+    else if (d.s1_unroll == 1) launch_k(d.pdl, k_pass1<float, 2>, g, 256, smem, s, d);
+    else launch_k(d.pdl, k_pass1<float, 1>, g, 256, smem, s, d);
   }
 }
 
 void launch_reduce1(const DevSim& d, cudaStream_t s) {
-  k_reduce1<<<(d.n_pad + 255) / 256, 256, 0, s>>>(d);
+  launch_k(d.pdl, k_reduce1, (d.n_pad + 255) / 256, 256, 0, s, d);
 }
 
 void launch_pass2(const DevSim& d, cudaStream_t s) {
   const int g = d.s2_grid;
   if (d.s_bf16) {
-    if (d.s2_unroll == 2) k_pass2<unsigned short, 8><<<g, 256, kP2Smem, s>>>(d);
-    else if (d.s2_unroll == 1) k_pass2<unsigned short, 4><<<g, 256, kP2Smem, s>>>(d);
-    else k_pass2<unsigned short, 2><<<g, 256, kP2Smem, s>>>(d);
+    if (d.s2_unroll == 2) launch_k(d.pdl, k_pass2<unsigned short, 8>, g, 256, kP2Smem, s, d);
+    else if (d.s2_unroll == 1) launch_k(d.pdl, k_pass2<unsigned short, 4>, g, 256, kP2Smem, s, d);
+    else launch_k(d.pdl, k_pass2<unsigned short, 2>, g, 256, kP2Smem, s, d);
   } else {
-    if (d.s2_unroll == 2) k_pass2<float, 4><<<g, 256, kP2Smem, s>>>(d);
-    else if (d.s2_unroll == 1) k_pass2<float, 2><<<g, 256, kP2Smem, s>>>(d);
-    else k_pass2<float, 1><<<g, 256, kP2Smem, s>>>(d);
+    if (d.s2_unroll == 2) launch_k(d.pdl, k_pass2<float, 4>, g, 256, kP2Smem, s, d);
+    else if (d.s2_unroll == 1) launch_k(d.pdl, k_pass2<float, 2>, g, 256, kP2Smem, s, d);
+    else launch_k(d.pdl, k_pass2<float, 1>, g, 256, kP2Smem, s, d);
   }
 }
 
 void launch_reduce2(const DevSim& d, cudaStream_t s, int out_mode) {
   const int g = (d.n + 255) / 256;
   switch (out_mode) {
-    case kOutDq: k_reduce2<kOutDq><<<g, 256, 0, s>>>(d); break;
-    case kOutX: k_reduce2<kOutX><<<g, 256, 0, s>>>(d); break;
-    case kOutAddDq: k_reduce2<kOutAddDq><<<g, 256, 0, s>>>(d); break;
-    default: k_reduce2<kOutAddX><<<g, 256, 0, s>>>(d); break;
+    case kOutDq: launch_k(d.pdl, k_reduce2<kOutDq>, g, 256, 0, s, d); break;
+    case kOutX: launch_k(d.pdl, k_reduce2<kOutX>, g, 256, 0, s, d); break;
+    case kOutAddDq: launch_k(d.pdl, k_reduce2<kOutAddDq>, g, 256, 0, s, d); break;
+    default: launch_k(d.pdl, k_reduce2<kOutAddX>, g, 256, 0, s, d); break;
   }
 }
 

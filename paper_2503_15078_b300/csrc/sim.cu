@@ -170,7 +170,11 @@ int kernels_per_frame(const sim_s* s, int K) {
 }
 
 void enqueue_frame(sim_s* s, int K, cudaStream_t st) {
-  const DevSim& d = s->d;
+  // the production graph (no event nodes between the kernels of an iteration) launches
+  // the iteration's straight-line kernels with programmatic dependent launch
+  DevSim dv = s->d;
+  dv.pdl = s->phase_marks ? 0 : 1;
+  const DevSim& d = dv;
   // external event-record nodes: observable from the host after each graph launch
   auto mark = [&](int i) { cudaEventRecordWithFlags(s->ev[i], st, cudaEventRecordExternal); };
   // per-iteration marks only with phase_marks (each event node costs a few microseconds)
@@ -270,7 +274,9 @@ void enqueue_frame(sim_s* s, int K, cudaStream_t st) {
 // condition from R_{k+1}. Event nodes are not allowed in a conditional body, so phase
 // marks stand only around the loop. Returns a CUDA error, or cudaSuccess.
 cudaError_t enqueue_frame_to_tolerance(sim_s* s, cudaStream_t st) {
-  const DevSim& d = s->d;
+  DevSim dv = s->d;
+  dv.pdl = 1;   // no event nodes inside the loop (see enqueue_frame)
+  const DevSim& d = dv;
   auto mark = [&](int i) { cudaEventRecordWithFlags(s->ev[i], st, cudaEventRecordExternal); };
   int n_fj = 0;
   auto fork = [&](cudaStream_t from, cudaStream_t to) {
