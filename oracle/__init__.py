@@ -19,9 +19,10 @@ matrices and pinned against the ancestor-closure theorem and dense inversion.
 
 Modules:
   fem             rest-shape data, the deformation-gradient operator G, lumped masses,
-                  weights and the system matrix A (Eq. 6)
+                  weights and the system matrix A (Eq. 6), for tetrahedra and triangle
+                  (membrane) elements, and the Laplace-Beltrami bending term
   local           per-element projections (Eq. 5) for ARAP, co-rotational and stable
-                  Neo-Hookean energies
+                  Neo-Hookean energies; ARAP and co-rotational membranes
   contact         collision detection and linearisation (App. A.1), Fischer-Burmeister
                   functions and their derivatives (App. B.2), the minimum map (App. B.1),
                   anchors (bilateral constraints), conjugate residual

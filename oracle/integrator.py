@@ -46,7 +46,7 @@ from . import contact as C
 from .fem import FEM
 from scenegen import MODEL_ARAP, MODEL_COROT
 
-from .local import elastic_energy, project
+from .local import elastic_energy, membrane_energy, project, project_membrane
 
 
 @dataclass
@@ -76,10 +76,16 @@ class Oracle:
         return q_t[self.scene.pinned] + self.h * np.asarray(self.scene.handle_vel)[None, :]
 
     def local_step(self, q):
-        """p_i = project(G_i q) for every element (Eq. 5)."""
+        """p_i = project(G_i q) for every element (Eq. 5): the tetrahedra's (T, 3, 3), then,
+        with a triangle sheet, the membranes' 3 x 2 values after them (one flat vector)."""
         f = self.fem
-        F = f.deformation_gradients(q)
-        return project(F, f.model, f.w, f.V, f.emu, f.elam, f.alpha)
+        p = (project(f.deformation_gradients(q), f.model, f.w, f.V, f.emu, f.elam, f.alpha)
+             if f.T else np.zeros((0, 3, 3)))
+        if not f.Nt:
+            return p
+        pt = project_membrane(f.triangle_gradients(q), f.t_model, f.t_w, f.t_V, f.t_mu,
+                              f.t_lam)
+        return np.concatenate([p.reshape(-1), pt.reshape(-1)])
 
     def admm_local_step(self, q, u):
         """ADMM-PD's local step with scaled dual variables u (one 3x3 per element): z_i the
@@ -216,6 +222,8 @@ class Oracle:
         lam_iters = []                     # lambda at each residual's iterate
         if opts.local not in ("pd", "admm"):
             raise ValueError("local must be 'pd' or 'admm'")
+        if opts.local == "admm" and f.Nt:
+            raise ValueError("ADMM-PD is for tetrahedra only")
         u = np.zeros((f.T, 3, 3))          # ADMM-PD duals, zero at every frame start
         for _k in range(opts.n_iters):
             if opts.local == "admm":
@@ -272,7 +280,10 @@ class Oracle:
         f = self.fem
         F = f.deformation_gradients(q)
         kin = 0.5 * float((f.mass[:, None] * v * v).sum())
-        ela = elastic_energy(F, f.model, f.V, f.emu, f.elam, f.alpha)
+        ela = elastic_energy(F, f.model, f.V, f.emu, f.elam, f.alpha) if f.T else 0.0
+        if f.Nt:
+            ela += membrane_energy(f.triangle_gradients(q), f.t_model, f.t_V, f.t_mu, f.t_lam)
+            ela += 0.5 * float((q * (f.K_bend @ q)).sum())
         grav = -float((f.mass[:, None] * q * self.g[None, :]).sum())
         return kin + ela + grav
 

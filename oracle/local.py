@@ -160,3 +160,45 @@ def elastic_energy(F, model, V, mu, lam, alpha):
     k = model == MODEL_SNH
     e[k] = psi_snh(s[k], mu[k], lam[k], alpha[k])
     return float((V * e).sum())
+
+
+# -- membranes (triangle elements, 3 x 2 deformation gradients) -------------------------
+def svd_membrane(F):
+    """Thin SVD of 3 x 2 deformation gradients: F = U diag(s) V^T with U (3 x 2, orthonormal
+    columns), s >= 0, V a 2 x 2 rotation or reflection (a membrane in 3D cannot invert)."""
+    U, s, Vt = np.linalg.svd(F, full_matrices=False)
+    return U, s, Vt
+
+
+def sigma_corot2(s, w, V, mu, lam):
+    """Closed-form minimiser of w/2 ||x - s||^2 + V (mu ||x - 1||^2 + lam/2 (sum x - 2)^2)
+    over the two singular values: (w + 2 mu V) x_i + lam V sum(x) = w s_i + 2 mu V + 2 lam V,
+    summed for sum(x), substituted back for each x_i."""
+    a = w + 2.0 * mu * V
+    c = lam * V
+    rhs = w[:, None] * s + (2.0 * mu * V + 2.0 * lam * V)[:, None]
+    S = rhs.sum(-1) / (a + 2.0 * c)
+    return (rhs - (c * S)[:, None]) / a[:, None]
+
+
+def project_membrane(F, model, w, V, mu, lam):
+    """p_i = argmin w_i/2 ||p - F_i||^2 + V_i psi_i(p) for 3 x 2 membrane gradients (Eq. 5):
+    ARAP the closest matrix with orthonormal columns (U V^T), co-rotational the closed form
+    above; the stable Neo-Hookean energy is not defined for membranes here."""
+    if np.any(model == MODEL_SNH):
+        raise ValueError("membranes are ARAP or co-rotational")
+    U, s, Vt = svd_membrane(F)
+    sh = np.ones_like(s)
+    c = model == MODEL_COROT
+    if c.any():
+        sh[c] = sigma_corot2(s[c], w[c], V[c], mu[c], lam[c])
+    return np.einsum("tij,tj,tjk->tik", U, sh, Vt)
+
+
+def membrane_energy(F, model, V, mu, lam):
+    """sum_i V_i psi_i(F_i): mu ||s - 1||^2 (+ lam/2 (sum s - 2)^2 co-rotational)."""
+    _, s, _ = svd_membrane(F)
+    e = mu * ((s - 1.0) ** 2).sum(-1)
+    c = model == MODEL_COROT
+    e[c] += 0.5 * lam[c] * (s[c].sum(-1) - 2.0) ** 2
+    return float((V * e).sum())

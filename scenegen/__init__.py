@@ -85,6 +85,12 @@ class Scene:
     pinned: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
     handle_vel: tuple = (0.0, 0.0, 0.0)   # velocity of every pinned vertex
     anchors: List["Anchor"] = field(default_factory=list)   # bilateral vertex targets
+    # triangle (membrane) elements: (Nt, 3) vertex ids, their materials, the sheet's
+    # thickness (m) and its bending stiffness k_b (N m, Laplace-Beltrami, flat rest)
+    tris: Optional[np.ndarray] = None
+    tri_material: Optional[np.ndarray] = None
+    thickness: float = 0.0
+    bending: float = 0.0
     q0: Optional[np.ndarray] = None       # (n, 3) initial positions (default: X)
     v0: Optional[np.ndarray] = None       # (n, 3) initial velocities (default: 0)
     contact_margin: float = 0.0           # a contact exists when the gap is below this
@@ -95,8 +101,13 @@ class Scene:
 
     def __post_init__(self):
         self.X = np.ascontiguousarray(self.X, dtype=np.float64)
-        self.tets = np.ascontiguousarray(self.tets, dtype=np.int32)
+        self.tets = np.ascontiguousarray(self.tets, dtype=np.int32).reshape(-1, 4)
         self.tet_material = np.ascontiguousarray(self.tet_material, dtype=np.int32)
+        self.tris = np.ascontiguousarray(np.zeros((0, 3)) if self.tris is None else self.tris,
+                                         dtype=np.int32).reshape(-1, 3)
+        if self.tri_material is None:
+            self.tri_material = np.zeros(len(self.tris), np.int32)
+        self.tri_material = np.ascontiguousarray(self.tri_material, dtype=np.int32)
         self.pinned = np.ascontiguousarray(self.pinned, dtype=np.int32)
         if self.q0 is None:
             self.q0 = self.X.copy()
@@ -298,6 +309,45 @@ def anchored_handle(scene: Scene, compliance: float = 0.0) -> Scene:
     sc.pinned = np.zeros(0, np.int32)
     sc.name = scene.name + "_anchored"
     return sc
+
+
+def cloth(n: int = 12, size: float = 0.5, model: int = MODEL_ARAP, E: float = 1e5,
+          nu: float = 0.3, rho: float = 200.0, thickness: float = 1e-3, bending: float = 1e-4,
+          height: float = 0.3, pin: str = "corners", h: float = 1.0 / 60.0,
+          obstacles: Optional[List[Obstacle]] = None, seed: int = 0,
+          tilt_deg: float = 0.0) -> Scene:
+    """A flat square sheet of n x n vertices (side ``size``, triangles alternating their
+    diagonal) in the plane z = height, rotated about the x axis by ``tilt_deg``; ARAP or
+    co-rotational membrane with thickness and a Laplace-Beltrami bending stiffness.
+    pin: "corners" (the two corners at y = max), "edge" (the row y = max) or "none"."""
+    g = np.linspace(-0.5 * size, 0.5 * size, n)
+    xx, yy = np.meshgrid(g, g, indexing="ij")
+    X = np.stack([xx.ravel(), yy.ravel(), np.zeros(n * n)], axis=1)
+    c = math.cos(math.radians(tilt_deg)); sn = math.sin(math.radians(tilt_deg))
+    X = X @ np.array([[1, 0, 0], [0, c, sn], [0, -sn, c]]).T
+    X[:, 2] += height
+    tris = []
+    for i in range(n - 1):
+        for j in range(n - 1):
+            a, b, cc, d = i * n + j, (i + 1) * n + j, (i + 1) * n + j + 1, i * n + j + 1
+            if (i + j) % 2 == 0:
+                tris += [(a, b, cc), (a, cc, d)]
+            else:
+                tris += [(a, b, d), (b, cc, d)]
+    tris = np.array(tris, np.int32)
+    if pin == "corners":
+        pinned = np.array([n - 1, n * n - 1], np.int32)
+    elif pin == "edge":
+        pinned = np.array([i * n + n - 1 for i in range(n)], np.int32)
+    else:
+        pinned = np.zeros(0, np.int32)
+    obst = [] if obstacles is None else list(obstacles)
+    spacing = size / (n - 1)
+    return Scene(f"cloth{n}", X, np.zeros((0, 4), np.int32), np.zeros(0, np.int32),
+                 [Material(model, E, nu, rho)], obst, h, pinned=pinned,
+                 contact_margin=0.5 * spacing, spacing=spacing, tris=tris,
+                 tri_material=np.zeros(len(tris), np.int32), thickness=thickness,
+                 bending=bending)
 
 
 def hanging_cube(m: int = 5, edge: float = 0.1, model: int = MODEL_ARAP, E: float = 1e5,
