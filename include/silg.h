@@ -77,6 +77,18 @@ typedef struct {
   const int32_t* pinned;       /* n_pinned vertex ids (Dirichlet), or NULL                */
   int32_t n_pinned;
   double handle_vel[3];        /* velocity of every pinned vertex (m/s)                   */
+  /* Triangle (membrane) elements of a sheet: F = [x1 - x0, x2 - x0] D_m^-1 (3 x 2) with D_m
+   * the rest edges in the triangle's plane, volume = area x thickness, weight 2 mu V; ARAP
+   * (closest orthonormal columns) or co-rotational (SIM_MODEL_SNH: SIM_EINVAL), the plain
+   * local step only (SIM_LOCAL_ADMM with triangles: SIM_EINVAL). n_tets may be 0 when
+   * n_tris > 0. Bending: k_b/2 sum over interior vertices of |L x|^2 / A (L the rest
+   * cotangent Laplacian, A the mixed Voronoi area), a constant term of the system matrix;
+   * the rest sheet is taken as flat (zero rest curvature). */
+  const int32_t* tris;         /* n_tris x 3 vertex ids, or NULL                           */
+  const int32_t* tri_material; /* n_tris material indices, or NULL for material 0         */
+  int32_t n_tris;
+  double thickness;            /* of the sheet (m); > 0 when n_tris > 0                    */
+  double bending;              /* k_b (N m) >= 0                                          */
 } sim_mesh;
 
 typedef struct {

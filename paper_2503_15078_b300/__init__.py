@@ -66,6 +66,16 @@ def _mesh_args(scene):
     mesh.n_pinned = len(pin)
     for r in range(3):
         mesh.handle_vel[r] = float(scene.handle_vel[r])
+    tris = np.ascontiguousarray(getattr(scene, "tris", None) if getattr(scene, "tris", None)
+                                is not None else np.zeros((0, 3)), dtype=np.int32).reshape(-1, 3)
+    trm = np.ascontiguousarray(getattr(scene, "tri_material", None)
+                               if getattr(scene, "tri_material", None) is not None
+                               else np.zeros(len(tris)), dtype=np.int32)
+    mesh.tris = _iptr(tris) if len(tris) else None
+    mesh.tri_material = _iptr(trm) if len(tris) else None
+    mesh.n_tris = len(tris)
+    mesh.thickness = float(getattr(scene, "thickness", 0.0))
+    mesh.bending = float(getattr(scene, "bending", 0.0))
     mats = (_abi.SimMaterial * len(scene.materials))()
     for i, m in enumerate(scene.materials):
         mats[i].model, mats[i].E, mats[i].nu, mats[i].rho = int(m.model), m.E, m.nu, m.rho
@@ -78,7 +88,7 @@ def _mesh_args(scene):
             obs[i].vel[r] = float(o.vel[r])
         obs[i].radius = float(o.radius)
         obs[i].mu = float(o.mu)
-    return mesh, mats, obs, (X, tets, tm, pin)
+    return mesh, mats, obs, (X, tets, tm, pin, tris, trm)
 
 
 def default_options():

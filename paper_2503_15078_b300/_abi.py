@@ -24,7 +24,8 @@ MLP_FEATURES, MLP_OUTPUTS, MLP_PARAMS = 11, 4, 36232
 class SimMesh(C.Structure):
     _fields_ = [("n_verts", C.c_int32), ("n_tets", C.c_int32), ("rest_pos", _dp),
                 ("tets", _ip), ("tet_material", _ip), ("pinned", _ip), ("n_pinned", C.c_int32),
-                ("handle_vel", C.c_double * 3)]
+                ("handle_vel", C.c_double * 3), ("tris", _ip), ("tri_material", _ip),
+                ("n_tris", C.c_int32), ("thickness", C.c_double), ("bending", C.c_double)]
 
 
 class SimMaterial(C.Structure):

@@ -159,7 +159,20 @@ struct DevSim {
   const float* tet_vol;
   const int* tet_mat;
   const MatDev* mats;
-  float4* contrib;         // [n_tets * 4]: h^2 w (p - F_ref) g_a
+  float4* contrib;         // [n_tets * 4 + n_tris * 3]: h^2 w (p - F_ref) g_a per corner
+  // triangle (membrane) elements
+  int n_tris;
+  const int4* tri_v;       // internal vertex ids (w unused)
+  const float* tri_dminv;  // 4 x n_tris (k * n_tris + t): D_m^-1 row-major 2 x 2
+  const float* tri_w;
+  const float* tri_vol;
+  const int* tri_mat;
+  // bending: rows of K = sum k_b L^T diag(interior / A) L for the free vertices (internal
+  // numbering, columns over all vertices), and the per-frame force -h^2 K q_ref
+  const int* bend_ptr;     // n + 1, or null without bending
+  const int* bend_idx;
+  const double* bend_val;
+  float* bend_f;           // 3 n
   const int* inc_ptr;      // n + 1: incidences of free vertex i
   const int* inc_idx;      // entries 4 t + a
 

@@ -343,6 +343,110 @@ __global__ void __launch_bounds__(128) k_local(DevSim d) {
   }
 }
 
+// The local step of a triangle (membrane) element: F = [x1 - x0, x2 - x0] D_m^-1 (3 x 2),
+// p = U diag(sigma_hat) V^T over the thin SVD, written as p = F V diag(sigma_hat / sigma) V^T
+// with V and sigma^2 the eigenpairs of the 2 x 2 F^T F (a Jacobi rotation). ARAP:
+// sigma_hat = 1 (the closest matrix with orthonormal columns); co-rotational: the closed-form
+// minimiser of w/2 |x - sigma|^2 + V (mu |x - 1|^2 + lam/2 (sum x - 2)^2). Corner a's
+// contribution h^2 w (p - F_ref) g_a goes to contrib[4 n_tets + 3 t + a].
+__global__ void __launch_bounds__(128) k_local_tri(DevSim d) {
+  pdl_wait();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d.n_tris) return;
+  const int Nt = d.n_tris;
+  const int4 vi = d.tri_v[t];
+  const int vv[3] = {vi.x, vi.y, vi.z};
+  const float M0 = d.tri_dminv[t], M1 = d.tri_dminv[Nt + t], M2 = d.tri_dminv[2 * Nt + t],
+              M3 = d.tri_dminv[3 * Nt + t];
+  float g[3][2];
+  g[1][0] = M0;
+  g[1][1] = M1;
+  g[2][0] = M2;
+  g[2][1] = M3;
+  g[0][0] = -(M0 + M2);
+  g[0][1] = -(M1 + M3);
+  float h0[3], l0[3], dq0[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    h0[r] = d.qr_hi[3 * vv[0] + r];
+    l0[r] = d.qr_lo[3 * vv[0] + r];
+    dq0[r] = d.dq[3 * vv[0] + r];
+  }
+  float Fr[6], F[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) Fr[k] = F[k] = 0.f;
+#pragma unroll
+  for (int a = 1; a < 3; ++a) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float er = (d.qr_hi[3 * vv[a] + r] - h0[r]) + (d.qr_lo[3 * vv[a] + r] - l0[r]);
+      const float ed = d.dq[3 * vv[a] + r] - dq0[r];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        Fr[2 * r + c] += er * g[a][c];
+        F[2 * r + c] += (er + ed) * g[a][c];
+      }
+    }
+  }
+  // C = F^T F and its eigenpairs
+  const float c00 = F[0] * F[0] + F[2] * F[2] + F[4] * F[4];
+  const float c01 = F[0] * F[1] + F[2] * F[3] + F[4] * F[5];
+  const float c11 = F[1] * F[1] + F[3] * F[3] + F[5] * F[5];
+  const float th = 0.5f * atan2f(2.f * c01, c00 - c11);
+  const float cs = cosf(th), sn = sinf(th);
+  const float mid = 0.5f * (c00 + c11), rad = sqrtf(0.25f * (c00 - c11) * (c00 - c11) + c01 * c01);
+  const float s0 = sqrtf(fmaxf(mid + rad, 0.f)), s1 = sqrtf(fmaxf(mid - rad, 0.f));
+  const MatDev m = d.mats[d.tri_mat[t]];
+  const float w = d.tri_w[t], V = d.tri_vol[t];
+  float x0 = 1.f, x1 = 1.f;
+  if (m.model == SIM_MODEL_COROT) {
+    const float a = w + 2.f * m.mu * V, c = m.lam * V;
+    const float k = 2.f * m.mu * V + 2.f * m.lam * V;
+    const float r0 = w * s0 + k, r1 = w * s1 + k;
+    const float S = (r0 + r1) / (a + 2.f * c);
+    x0 = (r0 - c * S) / a;
+    x1 = (r1 - c * S) / a;
+  }
+  // p = F M with M = V diag(x / s) V^T (the eigenvectors (cs, sn) and (-sn, cs)); a
+  // collapsed direction keeps its ratio finite
+  const float k0 = x0 / fmaxf(s0, 1e-12f), k1 = x1 / fmaxf(s1, 1e-12f);
+  const float m00 = k0 * cs * cs + k1 * sn * sn, m11 = k0 * sn * sn + k1 * cs * cs;
+  const float m01 = (k0 - k1) * cs * sn;
+  float p[6];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    p[2 * r] = F[2 * r] * m00 + F[2 * r + 1] * m01;
+    p[2 * r + 1] = F[2 * r] * m01 + F[2 * r + 1] * m11;
+  }
+  const float sc = d.h2f * w;
+  const size_t base = 4 * (size_t)d.n_tets + 3 * (size_t)t;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float o[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+      o[r] = sc * ((p[2 * r] - Fr[2 * r]) * g[a][0] + (p[2 * r + 1] - Fr[2 * r + 1]) * g[a][1]);
+    d.contrib[base + a] = make_float4(o[0], o[1], o[2], 0.f);
+  }
+}
+
+// The bending term's part of b - A q_ref, -h^2 K q_ref for every free vertex (the rest
+// curvature is zero, so the term has no projection); once per frame, after q_ref is set.
+__global__ void k_bend_force(DevSim d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n) return;
+  double f[3] = {0.0, 0.0, 0.0};
+  for (int e = d.bend_ptr[i]; e < d.bend_ptr[i + 1]; ++e) {
+    const double k = d.bend_val[e];
+    const int j = d.bend_idx[e];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) f[r] += k * d.q_ref[3 * j + r];
+  }
+  const double h2 = d.h * d.h;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) d.bend_f[3 * i + r] = (float)(-h2 * f[r]);
+}
+
 // b_i - (A q_ref)_i + h^2 (J^T lambda)_i for every free vertex i, written as the FP32 SoA
 // vector g of the first profile product.
 // b_i = M_i (s~_i - q_ref_i) + sum of the vertex's element contributions + h^2 (contact
@@ -385,6 +489,9 @@ __global__ void k_rhs(DevSim d) {
 #pragma unroll
       for (int r = 0; r < 3; ++r) b[r] += h2 * d.ct_force[3 * j + r];
   }
+  if (d.bend_f)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) e[r] += d.bend_f[3 * i + r];
 #pragma unroll
   for (int r = 0; r < 3; ++r) d.gvec[r * d.n_pad + i] = (float)(b[r] + (double)e[r]);
 }
@@ -408,15 +515,17 @@ __global__ void k_integrate(DevSim d) {
 
 void launch_frame_begin(const DevSim& d, cudaStream_t s) {
   k_frame_begin<<<(d.n_all + 255) / 256, 256, 0, s>>>(d);
+  if (d.bend_ptr) k_bend_force<<<(d.n + 255) / 256, 256, 0, s>>>(d);
 }
 
 void launch_local(const DevSim& d, cudaStream_t s, bool debug_p) {
   int grid = (d.n_tets + 127) / 128;
   if (debug_p) {
     k_split_ref<<<(d.n_all + 255) / 256, 256, 0, s>>>(d);
-    k_local<true><<<grid, 128, 0, s>>>(d);
+    if (grid > 0) k_local<true><<<grid, 128, 0, s>>>(d);
   } else {
-    launch_k(d.pdl, k_local<false>, grid, 128, 0, s, d);
+    if (grid > 0) launch_k(d.pdl, k_local<false>, grid, 128, 0, s, d);
+    if (d.n_tris > 0) launch_k(d.pdl, k_local_tri, (d.n_tris + 127) / 128, 128, 0, s, d);
   }
 }
 

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <map>
 #include <cmath>
 #include <numeric>
 #include <thread>
@@ -91,20 +92,26 @@ struct Dissector {
 
 int build_plan(const sim_mesh* mesh, const sim_material* mats, int n_mat, double h,
                int n_threads, Plan* P, std::string* err, const int32_t* vertex_scene,
-               int n_scenes) {
+               int n_scenes, const double* tri_thickness, const double* vert_bending) {
   auto t0 = std::chrono::steady_clock::now();
   Plan& p = *P;
-  if (!mesh || !mesh->rest_pos || !mesh->tets || mesh->n_verts <= 0 || mesh->n_tets <= 0 ||
-      !mats || n_mat <= 0 || !(h > 0) || !std::isfinite(h)) {
+  if (!mesh || !mesh->rest_pos || mesh->n_verts <= 0 || mesh->n_tets < 0 || mesh->n_tris < 0 ||
+      mesh->n_tets + mesh->n_tris <= 0 || (mesh->n_tets > 0 && !mesh->tets) ||
+      (mesh->n_tris > 0 && !mesh->tris) || !mats || n_mat <= 0 || !(h > 0) ||
+      !std::isfinite(h)) {
     *err = "null or empty mesh / materials, or non-positive h";
     return SIM_EINVAL;
   }
-  const int n = mesh->n_verts, T = mesh->n_tets;
+  const int n = mesh->n_verts, T = mesh->n_tets, Nt = mesh->n_tris;
   p.n_verts = n;
   p.n_tets = T;
+  p.n_tris = Nt;
   p.h = h;
   p.X.assign(mesh->rest_pos, mesh->rest_pos + 3 * (size_t)n);
-  p.tets.assign(mesh->tets, mesh->tets + 4 * (size_t)T);
+  if (T > 0) p.tets.assign(mesh->tets, mesh->tets + 4 * (size_t)T);
+  if (Nt > 0) p.tris.assign(mesh->tris, mesh->tris + 3 * (size_t)Nt);
+  p.tri_mat.assign(Nt, 0);
+  if (Nt > 0 && mesh->tri_material) p.tri_mat.assign(mesh->tri_material, mesh->tri_material + Nt);
   p.tet_mat.assign(T, 0);
   if (mesh->tet_material) p.tet_mat.assign(mesh->tet_material, mesh->tet_material + T);
   for (int r = 0; r < 3; ++r) p.handle_vel[r] = mesh->handle_vel[r];
@@ -195,7 +202,148 @@ int build_plan(const sim_mesh* mesh, const sim_material* mats, int n_mat, double
       edge_sum += std::sqrt(Dm[a - 1] * Dm[a - 1] + Dm[3 + a - 1] * Dm[3 + a - 1] +
                             Dm[6 + a - 1] * Dm[6 + a - 1]);
   }
-  p.mean_edge = edge_sum / (3.0 * T);
+  // ---- triangles: in-plane rest edges, area x thickness, mass -----------------------
+  p.tri_dminv.resize(4 * (size_t)Nt);
+  p.tri_vol.resize(Nt);
+  p.tri_weight.resize(Nt);
+  for (int t = 0; t < Nt; ++t) {
+    const int32_t* v = &p.tris[3 * (size_t)t];
+    for (int a = 0; a < 3; ++a)
+      if (v[a] < 0 || v[a] >= n) {
+        *err = "triangle index out of range";
+        return SIM_EINVAL;
+      }
+    if (p.tri_mat[t] < 0 || p.tri_mat[t] >= n_mat ||
+        p.mats[p.tri_mat[t]].model == SIM_MODEL_SNH) {
+      *err = "triangle material out of range, or stable Neo-Hookean (membranes: ARAP or "
+             "co-rotational)";
+      return SIM_EINVAL;
+    }
+    const double th = tri_thickness ? tri_thickness[t] : mesh->thickness;
+    if (!(th > 0) || !std::isfinite(th)) {
+      *err = "a triangle sheet needs a positive thickness";
+      return SIM_EINVAL;
+    }
+    double e1[3], e2[3], nr[3];
+    for (int r = 0; r < 3; ++r) {
+      e1[r] = p.X[3 * v[1] + r] - p.X[3 * v[0] + r];
+      e2[r] = p.X[3 * v[2] + r] - p.X[3 * v[0] + r];
+    }
+    nr[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    nr[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    nr[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    const double l1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    const double nn = std::sqrt(nr[0] * nr[0] + nr[1] * nr[1] + nr[2] * nr[2]);
+    if (!(l1 > 0) || !(nn > 0)) {
+      *err = "degenerate rest triangle " + std::to_string(t);
+      return SIM_EINVAL;
+    }
+    // rest frame: a1 along e1, a2 = n x a1; D_m = [[l1, e2.a1], [0, e2.a2]]
+    double a1[3], a2[3];
+    for (int r = 0; r < 3; ++r) a1[r] = e1[r] / l1;
+    a2[0] = (nr[1] * a1[2] - nr[2] * a1[1]) / nn;
+    a2[1] = (nr[2] * a1[0] - nr[0] * a1[2]) / nn;
+    a2[2] = (nr[0] * a1[1] - nr[1] * a1[0]) / nn;
+    const double d00 = l1, d01 = e2[0] * a1[0] + e2[1] * a1[1] + e2[2] * a1[2];
+    const double d11 = e2[0] * a2[0] + e2[1] * a2[1] + e2[2] * a2[2];
+    double* Mi = &p.tri_dminv[4 * (size_t)t];
+    Mi[0] = 1.0 / d00;
+    Mi[1] = -d01 / (d00 * d11);
+    Mi[2] = 0.0;
+    Mi[3] = 1.0 / d11;
+    p.tri_vol[t] = 0.5 * nn * th;
+    const MatParams& mp = p.mats[p.tri_mat[t]];
+    p.tri_weight[t] = 2.0 * mp.mu_le * p.tri_vol[t];
+    for (int a = 0; a < 3; ++a) p.mass[v[a]] += mp.rho * p.tri_vol[t] / 3.0;
+    edge_sum += l1 + std::sqrt(e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2]);
+  }
+  p.mean_edge = edge_sum / (3.0 * T + 2.0 * Nt);
+  // ---- bending: K = sum k_b L^T diag(interior / A) L ----------------------------------
+  {
+    // cotangent weights per edge, mixed Voronoi areas, boundary edges (one triangle)
+    std::map<std::pair<int, int>, std::pair<double, int>> edge;   // (w_ij, triangles)
+    std::vector<double> area(n, 0.0);
+    bool any = false;
+    for (int t = 0; t < Nt; ++t) {
+      const int32_t* v = &p.tris[3 * (size_t)t];
+      double P[3][3], cot[3];
+      for (int a = 0; a < 3; ++a)
+        for (int r = 0; r < 3; ++r) P[a][r] = p.X[3 * v[a] + r];
+      for (int k = 0; k < 3; ++k) {
+        // the angle at corner k, between the edges to the two others
+        const int a = (k + 1) % 3, b = (k + 2) % 3;
+        double u[3], w[3], c[3];
+        for (int r = 0; r < 3; ++r) {
+          u[r] = P[a][r] - P[k][r];
+          w[r] = P[b][r] - P[k][r];
+        }
+        c[0] = u[1] * w[2] - u[2] * w[1];
+        c[1] = u[2] * w[0] - u[0] * w[2];
+        c[2] = u[0] * w[1] - u[1] * w[0];
+        cot[k] = (u[0] * w[0] + u[1] * w[1] + u[2] * w[2]) /
+                 std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        auto key = std::make_pair(std::min(v[a], v[b]), std::max(v[a], v[b]));
+        auto& e = edge[key];
+        e.first += 0.5 * cot[k];
+        e.second += 1;
+      }
+      const double ar = p.tri_vol[t] / (tri_thickness ? tri_thickness[t] : mesh->thickness);
+      const bool obtuse = cot[0] < 0 || cot[1] < 0 || cot[2] < 0;
+      for (int k = 0; k < 3; ++k) {
+        if (obtuse) {
+          area[v[k]] += cot[k] < 0 ? ar / 2 : ar / 4;
+        } else {
+          const int a = (k + 1) % 3, b = (k + 2) % 3;
+          double lb = 0, la = 0;
+          for (int r = 0; r < 3; ++r) {
+            lb += (P[b][r] - P[k][r]) * (P[b][r] - P[k][r]);
+            la += (P[a][r] - P[k][r]) * (P[a][r] - P[k][r]);
+          }
+          area[v[k]] += (lb * cot[a] + la * cot[b]) / 8.0;
+        }
+      }
+    }
+    std::vector<char> boundary(n, 0);
+    for (auto& e : edge)
+      if (e.second.second == 1) boundary[e.first.first] = boundary[e.first.second] = 1;
+    // rows of L (L_ii = sum w, L_ij = -w), then K = L^T diag(c) L with c = k_b / A at
+    // interior sheet vertices
+    std::vector<std::vector<std::pair<int32_t, double>>> Lr(n);
+    for (auto& e : edge) {
+      const int i = e.first.first, j = e.first.second;
+      const double w = e.second.first;
+      Lr[i].push_back({i, w});
+      Lr[i].push_back({j, -w});
+      Lr[j].push_back({j, w});
+      Lr[j].push_back({i, -w});
+    }
+    std::vector<std::map<int32_t, double>> K(n);
+    for (int i = 0; i < n; ++i) {
+      const double kb = vert_bending ? vert_bending[i] : mesh->bending;
+      if (!(kb >= 0) || !std::isfinite(kb)) {
+        *err = "bending stiffness must be finite and non-negative";
+        return SIM_EINVAL;
+      }
+      if (kb == 0 || boundary[i] || !(area[i] > 0) || Lr[i].empty()) continue;
+      std::map<int32_t, double> row;   // row i of L, merged
+      for (auto& e : Lr[i]) row[e.first] += e.second;
+      const double c = kb / area[i];
+      for (auto& a : row)
+        for (auto& b : row) K[a.first][b.first] += c * a.second * b.second;
+      any = true;
+    }
+    p.Kp.assign(n + 1, 0);
+    p.Ki.clear();
+    p.Kx.clear();
+    if (any)
+      for (int i = 0; i < n; ++i) {
+        for (auto& e : K[i]) {
+          p.Ki.push_back(e.first);
+          p.Kx.push_back(e.second);
+        }
+        p.Kp[i + 1] = (int64_t)p.Ki.size();
+      }
+  }
   for (int v = 0; v < n; ++v)
     if (!(p.mass[v] > 0)) {
       *err = "vertex " + std::to_string(v) + " belongs to no element";
@@ -222,6 +370,19 @@ int build_plan(const sim_mesh* mesh, const sim_material* mats, int n_mat, double
         if (a != b && free_of[v[a]] >= 0 && free_of[v[b]] >= 0)
           nb[free_of[v[a]]].push_back(free_of[v[b]]);
   }
+  for (int t = 0; t < Nt; ++t) {
+    const int32_t* v = &p.tris[3 * (size_t)t];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b)
+        if (a != b && free_of[v[a]] >= 0 && free_of[v[b]] >= 0)
+          nb[free_of[v[a]]].push_back(free_of[v[b]]);
+  }
+  if (!p.Kx.empty())
+    for (int i = 0; i < n; ++i)
+      for (int64_t e = p.Kp[i]; e < p.Kp[i + 1]; ++e) {
+        const int j = p.Ki[e];
+        if (i != j && free_of[i] >= 0 && free_of[j] >= 0) nb[free_of[i]].push_back(free_of[j]);
+      }
   std::vector<int64_t> gp(nf + 1, 0);
   std::vector<int32_t> gi;
   for (int f = 0; f < nf; ++f) {
@@ -358,6 +519,35 @@ int build_plan(const sim_mesh* mesh, const sim_material* mats, int n_mat, double
         }
       }
     }
+    for (int t = 0; t < Nt; ++t) {
+      const int32_t* v = &p.tris[3 * (size_t)t];
+      const double* Mi = &p.tri_dminv[4 * (size_t)t];
+      double g[3][2];
+      for (int c = 0; c < 2; ++c) {
+        g[1][c] = Mi[c];
+        g[2][c] = Mi[2 + c];
+        g[0][c] = -(g[1][c] + g[2][c]);
+      }
+      const double s = h * h * p.tri_weight[t];
+      for (int a = 0; a < 3; ++a) {
+        const int ia = p.internal[v[a]];
+        if (ia >= nf) continue;
+        for (int b = 0; b < 3; ++b) {
+          const int ib = p.internal[v[b]];
+          if (ib >= nf) continue;
+          rows[ia].push_back({ib, s * (g[a][0] * g[b][0] + g[a][1] * g[b][1])});
+        }
+      }
+    }
+    if (!p.Kx.empty())
+      for (int i = 0; i < n; ++i) {
+        const int ii = p.internal[i];
+        if (ii >= nf) continue;
+        for (int64_t e = p.Kp[i]; e < p.Kp[i + 1]; ++e) {
+          const int jj = p.internal[p.Ki[e]];
+          if (jj < nf) rows[ii].push_back({jj, h * h * p.Kx[e]});
+        }
+      }
     p.Ap.assign(nf + 1, 0);
     p.Ai.clear();
     p.Ax.clear();

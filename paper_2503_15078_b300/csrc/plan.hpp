@@ -45,6 +45,18 @@ struct Plan {
   std::vector<int32_t> vertex_scene;  // scene of each vertex (caller numbering)
   std::vector<int32_t> scene_vfirst;  // n_scenes + 1: scene boundaries, internal free ids
 
+  // ---- triangle (membrane) elements and bending ------------------------------------
+  int n_tris = 0;
+  std::vector<int32_t> tris;      // n_tris x 3 (caller numbering)
+  std::vector<int32_t> tri_mat;
+  std::vector<double> tri_dminv;  // 4 per triangle: D_m^-1, row-major 2 x 2
+  std::vector<double> tri_vol;    // area x thickness
+  std::vector<double> tri_weight; // 2 mu_LE V
+  // K = sum k_b L^T diag(interior / A) L (caller numbering, CSR over all vertices, symmetric)
+  std::vector<int64_t> Kp;
+  std::vector<int32_t> Ki;
+  std::vector<double> Kx;
+
   // ---- per element (caller tet order) ----------------------------------------------
   std::vector<double> Dm_inv;     // 9 per tet, row-major
   std::vector<double> vol;        // rest volume V_i
@@ -95,9 +107,12 @@ struct Plan {
 // Build the plan. Returns SIM_OK or an error code; *err receives a message.
 // vertex_scene (optional): scene of each vertex, non-decreasing; the ordering is computed
 // scene by scene so that every scene's free vertices are contiguous.
+// tri_thickness (per triangle) and vert_bending (per vertex) override the mesh's single
+// thickness and bending (a batch's scenes each have their own)
 int build_plan(const sim_mesh* mesh, const sim_material* mats, int n_mat, double h,
                int n_threads, Plan* plan, std::string* err,
-               const int32_t* vertex_scene = nullptr, int n_scenes = 1);
+               const int32_t* vertex_scene = nullptr, int n_scenes = 1,
+               const double* tri_thickness = nullptr, const double* vert_bending = nullptr);
 
 // Device work split of one product: CTA c streams tiles [cta_first[c], cta_first[c+1])
 // of the pass's tile order, split so that every CTA has about the same cost; each run of

@@ -149,13 +149,18 @@ int frame_iters(sim_s* s) {
   return k;
 }
 
+// local-step launches per iteration (tetrahedra, triangles) and per-frame extras (bending)
+int local_kernels(const sim_s* s) { return (s->d.n_tets > 0) + (s->d.n_tris > 0); }
+
 // launches of a frame to a tolerance that made K updates (enqueue_frame_to_tolerance)
 int kernels_per_frame_to_tolerance(const sim_s* s, int K) {
   const bool c = s->has_obstacles;
   const int refine_body = s->d.s_bf16 && s->d.refine >= 2 ? 5 : 0;
   const int refine_end = s->d.s_bf16 && s->d.refine == 1 ? 6 : 0;
-  const int before = 1 + (c ? 4 + 12 + silg::ws_kernels(s->d.ws_mode) : 0) + 1 + (c ? 1 : 0);
-  const int body = 1 + 2 + (c ? 3 : 0) + 2 + refine_body + 1 + (c ? 1 : 0) + 1 + 1;
+  const int before = 1 + (s->d.bend_ptr != nullptr) +
+                     (c ? 4 + 12 + silg::ws_kernels(s->d.ws_mode) : 0) + local_kernels(s) +
+                     (c ? 1 : 0);
+  const int body = 1 + 2 + (c ? 3 : 0) + 2 + refine_body + 1 + (c ? 1 : 0) + local_kernels(s) + 1;
   const int after = refine_end + (c ? 1 : 0) + 1 + (c && s->d.pf_copies > 1 ? 1 : 0);
   return before + K * body + after;
 }
@@ -164,7 +169,8 @@ int kernels_per_frame(const sim_s* s, int K) {
   const bool c = s->has_obstacles;
   // per iteration: local, [contact eval], rhs, pass 1 + reduction, [Y^T z, CR, Y u],
   // pass 2 + reduction; a residual correction adds the residual and both passes
-  return 1 + (c ? 4 + 12 : 0) + K * (1 + (c ? 1 : 0) + 1 + 2 + (c ? 3 : 0) + 2) + (c ? 1 : 0) + 1 +
+  return 1 + (s->d.bend_ptr != nullptr) + (c ? 4 + 12 : 0) +
+         K * (local_kernels(s) + (c ? 1 : 0) + 1 + 2 + (c ? 3 : 0) + 2) + (c ? 1 : 0) + 1 +
          5 * refined_iters(s, K) + (c ? silg::ws_kernels(s->d.ws_mode) : 0) +
          (c && s->d.pf_copies > 1 ? 1 : 0);
 }
@@ -681,7 +687,27 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   std::vector<silg::MatDev> md;
   for (auto& m : p.mats) md.push_back({m.model, (float)m.mu, (float)m.lam, (float)m.alpha});
   d.mats = s->upload(md);
-  d.contrib = s->alloc<float4>(4 * (size_t)T);
+  // triangles: corner contributions follow the tetrahedra's in contrib
+  const int Nt = p.n_tris;
+  d.n_tris = Nt;
+  {
+    std::vector<int4> trv(std::max(1, Nt));
+    std::vector<float> tdm(4 * (size_t)std::max(1, Nt)), trw(std::max(1, Nt)),
+        trvol(std::max(1, Nt));
+    for (int t = 0; t < Nt; ++t) {
+      const int32_t* v = &p.tris[3 * (size_t)t];
+      trv[t] = make_int4(p.internal[v[0]], p.internal[v[1]], p.internal[v[2]], 0);
+      for (int k = 0; k < 4; ++k) tdm[(size_t)k * Nt + t] = (float)p.tri_dminv[4 * (size_t)t + k];
+      trw[t] = (float)p.tri_weight[t];
+      trvol[t] = (float)p.tri_vol[t];
+    }
+    d.tri_v = s->upload(trv);
+    d.tri_dminv = s->upload(tdm);
+    d.tri_w = s->upload(trw);
+    d.tri_vol = s->upload(trvol);
+    d.tri_mat = s->upload(Nt ? p.tri_mat : std::vector<int32_t>(1, 0));
+  }
+  d.contrib = s->alloc<float4>(4 * (size_t)T + 3 * (size_t)Nt);
   {
     std::vector<int> cnt(n + 1, 0);
     for (int t = 0; t < T; ++t)
@@ -689,15 +715,53 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
         int iv = p.internal[p.tets[4 * (size_t)t + a]];
         if (iv < n) ++cnt[iv + 1];
       }
+    for (int t = 0; t < Nt; ++t)
+      for (int a = 0; a < 3; ++a) {
+        int iv = p.internal[p.tris[3 * (size_t)t + a]];
+        if (iv < n) ++cnt[iv + 1];
+      }
     for (int i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
-    std::vector<int> idx(cnt[n]), fill(cnt.begin(), cnt.end() - 1);
+    std::vector<int> idx(std::max(1, cnt[n])), fill(cnt.begin(), cnt.end() - 1);
     for (int t = 0; t < T; ++t)
       for (int a = 0; a < 4; ++a) {
         int iv = p.internal[p.tets[4 * (size_t)t + a]];
         if (iv < n) idx[fill[iv]++] = 4 * t + a;
       }
+    for (int t = 0; t < Nt; ++t)
+      for (int a = 0; a < 3; ++a) {
+        int iv = p.internal[p.tris[3 * (size_t)t + a]];
+        if (iv < n) idx[fill[iv]++] = 4 * T + 3 * t + a;
+      }
     d.inc_ptr = s->upload(cnt);
     d.inc_idx = s->upload(idx);
+  }
+  // bending rows of the free vertices in internal numbering
+  d.bend_ptr = nullptr;
+  d.bend_idx = nullptr;
+  d.bend_val = nullptr;
+  d.bend_f = nullptr;
+  if (!p.Kx.empty()) {
+    std::vector<int> bp(n + 1, 0), bi;
+    std::vector<double> bv;
+    std::vector<int> caller_of(n);
+    for (int v = 0; v < n_all; ++v)
+      if (p.internal[v] < n) caller_of[p.internal[v]] = v;
+    for (int i = 0; i < n; ++i) {
+      const int v = caller_of[i];
+      for (int64_t e = p.Kp[v]; e < p.Kp[v + 1]; ++e) {
+        bi.push_back(p.internal[p.Ki[e]]);
+        bv.push_back(p.Kx[e]);
+      }
+      bp[i + 1] = (int)bi.size();
+    }
+    if (bi.empty()) {
+      bi.push_back(0);
+      bv.push_back(0.0);
+    }
+    d.bend_ptr = s->upload(bp);
+    d.bend_idx = s->upload(bi);
+    d.bend_val = s->upload(bv);
+    d.bend_f = s->alloc<float>(3 * (size_t)n);
   }
   // ---- S~ profile and tile schedule ---------------------------------------------------
   {
@@ -903,6 +967,20 @@ double mean_edge(const sim_mesh& m) {
       ++cnt;
     }
   }
+  for (int t = 0; t < m.n_tris; ++t) {
+    const int32_t* v = m.tris + 3 * (size_t)t;
+    if (v[0] < 0 || v[0] >= m.n_verts) continue;
+    for (int a = 1; a < 3; ++a) {
+      if (v[a] < 0 || v[a] >= m.n_verts) continue;
+      double e2 = 0;
+      for (int r = 0; r < 3; ++r) {
+        const double dx = m.rest_pos[3 * (size_t)v[a] + r] - m.rest_pos[3 * (size_t)v[0] + r];
+        e2 += dx * dx;
+      }
+      sum += std::sqrt(e2);
+      ++cnt;
+    }
+  }
   return cnt ? sum / cnt : 0.0;
 }
 
@@ -945,16 +1023,20 @@ int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_opt
   sim_default_options(&def);
   const sim_options* o = opts ? opts : &def;
   if (check_options(o) != SIM_OK) return SIM_EINVAL;
-  long long nv_tot = 0, nt_tot = 0, np_tot = 0;
+  long long nv_tot = 0, nt_tot = 0, np_tot = 0, ntr_tot = 0;
   for (int k = 0; k < n_scenes; ++k) {
     const sim_scene& sc = scenes[k];
-    if (sc.mesh.n_verts <= 0 || sc.mesh.n_tets <= 0 || !sc.mesh.rest_pos || !sc.mesh.tets ||
+    if (sc.mesh.n_verts <= 0 || sc.mesh.n_tets < 0 || sc.mesh.n_tris < 0 ||
+        sc.mesh.n_tets + sc.mesh.n_tris <= 0 || !sc.mesh.rest_pos ||
+        (sc.mesh.n_tets > 0 && !sc.mesh.tets) || (sc.mesh.n_tris > 0 && !sc.mesh.tris) ||
+        (sc.mesh.n_tris > 0 && o->local_solver == SIM_LOCAL_ADMM) ||
         !sc.materials || sc.n_materials <= 0 || sc.n_obstacles < 0 ||
         (sc.n_obstacles > 0 && !sc.obstacles) || sc.mesh.n_pinned < 0 ||
         (sc.mesh.n_pinned > 0 && !sc.mesh.pinned))
       return SIM_EINVAL;
     nv_tot += sc.mesh.n_verts;
     nt_tot += sc.mesh.n_tets;
+    ntr_tot += sc.mesh.n_tris;
     np_tot += sc.mesh.n_pinned;
   }
   if (nv_tot >= (1LL << 31) || nt_tot >= (1LL << 29)) return SIM_EINVAL;
@@ -966,7 +1048,8 @@ int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_opt
   s->alloc_ctx = o->alloc_ctx;
   int st = guarded([&]() {
     std::vector<double> X;
-    std::vector<int32_t> tets, tmat, pinned, vscene;
+    std::vector<int32_t> tets, tmat, pinned, vscene, tris, trmat;
+    std::vector<double> trthick, vbend;
     std::vector<sim_material> mats;
     SceneData sd;
     X.reserve(3 * nv_tot);
@@ -985,6 +1068,16 @@ int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_opt
         const int mt = m.tet_material ? m.tet_material[t] : 0;
         tmat.push_back(mt >= 0 && mt < sc.n_materials ? mt + moff : -1);
       }
+      for (int t = 0; t < m.n_tris; ++t) {
+        for (int a = 0; a < 3; ++a) {
+          const int v = m.tris[3 * (size_t)t + a];
+          tris.push_back(v >= 0 && v < m.n_verts ? v + voff : -1);
+        }
+        const int mt = m.tri_material ? m.tri_material[t] : 0;
+        trmat.push_back(mt >= 0 && mt < sc.n_materials ? mt + moff : -1);
+        trthick.push_back(m.thickness);
+      }
+      vbend.insert(vbend.end(), m.n_verts, m.bending);
       for (int q = 0; q < m.n_pinned; ++q)
         pinned.push_back(m.pinned[q] >= 0 && m.pinned[q] < m.n_verts ? m.pinned[q] + voff : -1);
       mats.insert(mats.end(), sc.materials, sc.materials + sc.n_materials);
@@ -1023,9 +1116,22 @@ int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_opt
         };
         mix(&m.n_verts, sizeof(m.n_verts));
         mix(m.rest_pos, sizeof(double) * 3 * (size_t)m.n_verts);
-        mix(m.tets, sizeof(int32_t) * 4 * (size_t)m.n_tets);
+        if (m.n_tets > 0) mix(m.tets, sizeof(int32_t) * 4 * (size_t)m.n_tets);
+        if (m.n_tris > 0) mix(m.tris, sizeof(int32_t) * 3 * (size_t)m.n_tris);
+        mix(&m.thickness, sizeof(double));
+        mix(&m.bending, sizeof(double));
         for (int t = 0; t < m.n_tets; ++t) {
           const int mt = m.tet_material ? m.tet_material[t] : 0;
+          if (mt >= 0 && mt < sc.n_materials) {
+            const sim_material& ma = sc.materials[mt];
+            mix(&ma.model, sizeof(ma.model));
+            mix(&ma.E, sizeof(double));
+            mix(&ma.nu, sizeof(double));
+            mix(&ma.rho, sizeof(double));
+          }
+        }
+        for (int t = 0; t < m.n_tris; ++t) {
+          const int mt = m.tri_material ? m.tri_material[t] : 0;
           if (mt >= 0 && mt < sc.n_materials) {
             const sim_material& ma = sc.materials[mt];
             mix(&ma.model, sizeof(ma.model));
@@ -1064,12 +1170,15 @@ int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_opt
     um.rest_pos = X.data();
     um.tets = tets.data();
     um.tet_material = tmat.data();
+    um.tris = tris.empty() ? nullptr : tris.data();
+    um.tri_material = trmat.empty() ? nullptr : trmat.data();
+    um.n_tris = (int32_t)ntr_tot;
     um.pinned = pinned.empty() ? nullptr : pinned.data();
     um.n_pinned = (int32_t)np_tot;
     for (int r = 0; r < 3; ++r) um.handle_vel[r] = scenes[0].mesh.handle_vel[r];
     std::string err;
     int r = silg::build_plan(&um, mats.data(), (int)mats.size(), h, o->n_host_threads, &s->plan,
-                             &err, vscene.data(), n_scenes);
+                             &err, vscene.data(), n_scenes, trthick.data(), vbend.data());
     if (r != SIM_OK) return r;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) return SIM_ECUDA;

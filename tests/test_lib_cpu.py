@@ -157,3 +157,33 @@ def test_allocator_hooks_must_come_in_pairs():
     with pytest.raises(SimError) as e:
         Simulator(sg.cube_drop(m=3), dev_alloc=lambda n, c: None)
     assert e.value.status == -1
+
+
+@pytest.mark.parametrize("bend,model,tilt", [(1e-4, sg.MODEL_COROT, 0.0), (0.0, sg.MODEL_ARAP, 20.0),
+                                             (3e-4, sg.MODEL_ARAP, 35.0)])
+def test_host_profile_solve_of_a_sheet_equals_the_direct_solve(bend, model, tilt):
+    # the host plan's system matrix with membranes and bending, through x = S^T (S b)
+    from oracle.fem import FEM
+    sc = sg.cloth(n=9, model=model, bending=bend, tilt_deg=tilt, pin="corners")
+    p = Plan(sc)
+    f = FEM(sc)
+    b = np.random.default_rng(0).normal(size=(sc.n_verts, 3))
+    x = p.apply_inverse_host(b)
+    xr = np.zeros_like(b)
+    xr[f.free_verts] = f.solve(b[f.free_verts].reshape(-1)).reshape(-1, 3)
+    assert np.linalg.norm(x - xr) < 1e-12 * np.linalg.norm(xr)
+
+
+@pytest.mark.parametrize("bad", ["snh", "thickness", "admm"])
+def test_invalid_sheets_are_rejected(bad):
+    sc = sg.cloth(n=5)
+    kw = {}
+    if bad == "snh":
+        sc.materials = [sg.Material(sg.MODEL_SNH, 1e5, 0.3, 200.0)]
+    elif bad == "thickness":
+        sc.thickness = 0.0
+    else:
+        kw["local_solver"] = "admm"
+    with pytest.raises(SimError) as e:
+        Simulator(sc, **kw)
+    assert e.value.status == -1
