@@ -386,6 +386,29 @@ def variants_timing(scene, q0, v0, steps, flush):
                      "contacts": sim.stats()["n_contacts"],
                      "final_residual": float(f"{statistics.mean(res):.3e}")}
         sim.close()
+    # a sheet of the paper's cloth size (20.2k vertices, 40k triangles) with Laplace-Beltrami
+    # bending, lying across a cylinder (its middle rows in contact), from rest
+    cyl = sg.Obstacle(sg.OBST_CYLINDER, (0.0, 0.0, -0.018), (1.0, 0.0, 0.0), radius=0.02,
+                      mu=0.3)
+    sheet = sg.cloth(n=142, size=1.0, model=sg.MODEL_COROT, bending=1e-4, pin="none",
+                     height=0.0, obstacles=[cyl])
+    sim = Simulator(sheet, autotune=0, phase_marks=0)
+    times, res = [], []
+    for k in range(3 + steps):
+        sim.set_state(sheet.q0, sheet.v0)
+        flush.zero_()
+        torch.cuda.synchronize()
+        sim.step()
+        if k >= 3:
+            times.append(sum(sim.phase_times().values()) / sheet.n_iters)
+            res.append(sim.stats()["residuals"][-1])
+    info = sim.plan_info()
+    out["cloth_20k_bending"] = {"ms_per_iter": round(statistics.mean(times), 5),
+                                "contacts": sim.stats()["n_contacts"],
+                                "final_residual": float(f"{statistics.mean(res):.3e}"),
+                                "verts": sheet.n_verts, "tris": int(len(sheet.tris)),
+                                "nnz_S": info["nnz_S"]}
+    sim.close()
     return out
 
 
