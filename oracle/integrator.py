@@ -26,6 +26,8 @@ Readings of the paper used here (the paper leaves these open):
     compliance E_b = e entering the Schur system as E_b / h^2 and right-hand side
     -phi_b + J_b q^k like a normal row (Eqs. 19-21); they count in the residual with
     max |phi_b| / L;
+  * the Jacobi global step (Sec. 8's comparison of complete and incomplete global solves) is
+    for scenes without contact: the Schur complement needs A^-1 itself;
   * ADMM-PD (the paper's implementation follows Overby et al. 2017; Sec. 7): the scaled
     dual variables u_i start at 0 every frame; per iteration z_i = prox of V_i psi_i with
     weight w_i at G_i q + u_i, u_i += G_i q - z_i, and the global step reads z_i - u_i.
@@ -56,6 +58,8 @@ class OracleOptions:
     exact_constraint_solve: bool = False   # dense solve instead of CR (isolates CR error)
     ncp: str = "fb"                        # "fb" (App. B.2) or "minmap" (App. B.1)
     local: str = "pd"                      # "pd" (Eq. 5) or "admm" (ADMM-PD, Sec. 7)
+    global_solver: str = "direct"          # "direct" (A^-1 b) or "jacobi" (the comparison
+    jacobi_sweeps: int = 10                #  of Sec. 8's convergence figure: sweeps from q^k)
     precond: str = "delassus"              # "delassus" (Eq. 28) or "mass" (Sec. 5.4)
 
 
@@ -86,6 +90,15 @@ class Oracle:
         pt = project_membrane(f.triangle_gradients(q), f.t_model, f.t_w, f.t_V, f.t_mu,
                               f.t_lam)
         return np.concatenate([p.reshape(-1), pt.reshape(-1)])
+
+    def jacobi(self, b, x, sweeps):
+        """The incomplete global step of the comparison in Sec. 8's convergence figure:
+        Jacobi sweeps x <- D^-1 (b - (A - D) x) on A_ff x = b, from the current iterate."""
+        A = self.fem.A_ff
+        dinv = 1.0 / A.diagonal()
+        for _ in range(sweeps):
+            x = x + dinv * (b - A @ x)
+        return x
 
     def admm_local_step(self, q, u):
         """ADMM-PD's local step with scaled dual variables u (one 3x3 per element): z_i the
@@ -194,6 +207,8 @@ class Oracle:
         q_pin = self.pinned_positions(q_t)
         contacts = C.detect(self.scene, s_tilde, fv, t + h)
         c = len(contacts)
+        if c and opts.global_solver == "jacobi":
+            raise ValueError("the Jacobi global step is for scenes without contact")
         H = self.contact_jacobian(contacts)
         W = self.delassus(H)
         r_n, r_f = self.preconditioner(W, c)                 # also the residual's scale
@@ -224,6 +239,8 @@ class Oracle:
             raise ValueError("local must be 'pd' or 'admm'")
         if opts.local == "admm" and f.Nt:
             raise ValueError("ADMM-PD is for tetrahedra only")
+        if opts.global_solver not in ("direct", "jacobi"):
+            raise ValueError("global_solver must be 'direct' or 'jacobi'")
         u = np.zeros((f.T, 3, 3))          # ADMM-PD duals, zero at every frame start
         for _k in range(opts.n_iters):
             if opts.local == "admm":
@@ -254,6 +271,8 @@ class Oracle:
                 lam = lam + dlam.reshape(c, 3)                           # Eq. 23a
                 omega_last = cs["omega"]
                 q_f = f.solve(b + h ** 2 * (J.T @ lam.reshape(-1)))      # Eq. 23b
+            elif opts.global_solver == "jacobi":
+                q_f = self.jacobi(b, q[fv].reshape(-1), opts.jacobi_sweeps)
             else:
                 q_f = f.solve(b)                                         # Eq. 6
             q = q.copy()

@@ -350,6 +350,27 @@ def cloth(n: int = 12, size: float = 0.5, model: int = MODEL_ARAP, E: float = 1e
                  bending=bending)
 
 
+def twisting_bar(nxy: int = 4, nz: int = 16, spacing: float = 0.02, twist_deg: float = 90.0,
+                 model: int = MODEL_ARAP, E: float = 1e6, nu: float = 0.45, rho: float = 1000.0,
+                 h: float = 1.0 / 60.0) -> Scene:
+    """The large-rotation scene of the paper's convergence comparison (Sec. 8): a bar along z
+    whose two end layers are pinned, the top one turned by twist_deg about the bar's axis;
+    the rest of the bar starts untwisted and at rest, without gravity."""
+    X, tets = lattice_tets(nxy, nxy, nz, spacing,
+                           origin=(-0.5 * (nxy - 1) * spacing, -0.5 * (nxy - 1) * spacing, 0.0))
+    zmax = X[:, 2].max()
+    bottom = np.nonzero(X[:, 2] < 1e-9)[0]
+    top = np.nonzero(X[:, 2] > zmax - 1e-9)[0]
+    q0 = X.copy()
+    a = math.radians(twist_deg)
+    R = np.array([[math.cos(a), -math.sin(a), 0.0], [math.sin(a), math.cos(a), 0.0], [0, 0, 1.0]])
+    q0[top] = X[top] @ R.T
+    return Scene(f"bar{nxy}x{nz}", X, tets, np.zeros(len(tets), np.int32),
+                 [Material(model, E, nu, rho)], [], h, gravity=(0.0, 0.0, 0.0),
+                 pinned=np.concatenate([bottom, top]).astype(np.int32), q0=q0,
+                 spacing=spacing)
+
+
 def hanging_cube(m: int = 5, edge: float = 0.1, model: int = MODEL_ARAP, E: float = 1e5,
                  nu: float = 0.4, rho: float = 1000.0, compliance: float = 0.0,
                  target_vel=(0.0, 0.0, 0.0), h: float = 1.0 / 60.0, floor: bool = False,

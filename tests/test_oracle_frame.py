@@ -443,3 +443,39 @@ def test_admm_pd_equals_pd_for_arap():
     q_admm, _, _ = o.frame(q0, v0, OracleOptions(n_iters=1200, local="admm"))
     q_pd, _, _ = o.frame(q0, v0, OracleOptions(n_iters=1200))
     assert np.abs(q_admm - q_pd).max() < 1e-12 * sc.bbox_diagonal
+
+
+def _relative_energy_error(o, sc, q, q_star, s_tilde):
+    f = o.fem
+
+    def eps(x):
+        kin = 0.5 / sc.h ** 2 * float((f.mass[:, None] * (x - s_tilde) ** 2).sum())
+        return kin + elastic_energy(f.deformation_gradients(x), f.model, f.V, f.emu, f.elam,
+                                    f.alpha)
+    return (eps(q) - eps(q_star)) / (eps(sc.q0) - eps(q_star))
+
+
+def test_jacobi_global_step_converges_to_the_direct_solve():
+    sc = sg.twisting_bar(nxy=3, nz=8)
+    o = Oracle(sc)
+    f = o.fem
+    b = np.random.default_rng(4).normal(size=len(f.free_dofs))
+    x = o.jacobi(b, np.zeros_like(b), 3000)
+    assert np.linalg.norm(x - f.solve(b)) < 1e-10 * np.linalg.norm(f.solve(b))
+
+
+def test_complete_global_solve_converges_faster_than_jacobi():
+    # Sec. 8's convergence comparison on a twisted bar: at the same number of local-global
+    # iterations the complete (sparse-inverse) global solve is closer to the converged frame
+    # in energy than 10 Jacobi sweeps per global step
+    sc = sg.twisting_bar(E=1e7)
+    o = Oracle(sc)
+    s_tilde = o.predict(sc.q0, sc.v0)
+    q_star, _, _ = o.frame(sc.q0, sc.v0, OracleOptions(n_iters=400))
+    for k in (3, 10, 30):
+        qd, _, _ = o.frame(sc.q0, sc.v0, OracleOptions(n_iters=k))
+        qj, _, _ = o.frame(sc.q0, sc.v0, OracleOptions(n_iters=k, global_solver="jacobi",
+                                                      jacobi_sweeps=10))
+        ed = _relative_energy_error(o, sc, qd, q_star, s_tilde)
+        ej = _relative_energy_error(o, sc, qj, q_star, s_tilde)
+        assert 0 < ed < 0.6 * ej, (k, ed, ej)
