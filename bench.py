@@ -247,7 +247,7 @@ class OracleTimer:
         c = self.c
         with self.limits(1):
             q_it = self.s_tilde.copy()
-            q_it[self.scene.pinned] = o.pinned_positions(self.q)
+            q_it[o.fem.pin_verts] = o.pinned_positions(self.q)
             lam = np.zeros((c, 3))
             r_n = np.full(c, 1e-6)
             r_f = np.full(c, 1e-4)

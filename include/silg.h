@@ -62,6 +62,10 @@ enum { SIM_LOCAL_PD = 0,        /* the local step of Eq. 5 (projective dynamics)
        SIM_LOCAL_ADMM = 1 };    /* ADMM-PD: scaled dual variables per element, zero at each
                                    frame start; the local step projects G q + u, the global
                                    step reads z - u; ARAP elements use mu |F - R|^2        */
+enum { SIM_GLOBAL_SPARSE_INVERSE = 0, /* the global step x = S^T S b (Eq. 8)            */
+       SIM_GLOBAL_JACOBI = 1 }; /* jacobi_sweeps Jacobi sweeps on A x = b from the current
+                                   iterate: the incomplete solve the paper compares against
+                                   (Sec. 8); scenes without obstacles or anchors only    */
 enum { SIM_PRECOND_DELASSUS = 0,/* r_n = h^2 W_jj, r_f = h W_jj from the Delassus operator
                                    (Eq. 28)                                               */
        SIM_PRECOND_MASS = 1 };  /* r_n = h^2 [H M^-1 H^T]_jj, r_f = h [H M^-1 H^T]_jj: the
@@ -140,6 +144,9 @@ typedef struct {
                                   the option's n_iters. Negative or NaN: SIM_EINVAL.     */
   int32_t max_iters;           /* cap of those iterations, 1..63 (default 40)             */
   int32_t local_solver;        /* SIM_LOCAL_PD (default) or SIM_LOCAL_ADMM                */
+  int32_t global_solver;       /* SIM_GLOBAL_SPARSE_INVERSE (default) or SIM_GLOBAL_JACOBI  */
+  int32_t jacobi_sweeps;       /* sweeps per global step with SIM_GLOBAL_JACOBI, 1..1000
+                                  (default 1: the single sweep of Sec. 8's baseline)     */
   int32_t phase_marks;         /* 1 (default): event nodes around every phase of every
                                   iteration (sim_get_phase_times itemises them); 0: only
                                   around the frame's once-per-frame phases, the iterations

@@ -233,7 +233,8 @@ class FEM:
         self.pinned_mask = pinned
         self.free_verts = np.nonzero(~pinned)[0]
         self.free_dofs = (3 * self.free_verts[:, None] + np.arange(3)).ravel()
-        self.pin_dofs = (3 * np.nonzero(pinned)[0][:, None] + np.arange(3)).ravel()
+        self.pin_verts = np.nonzero(pinned)[0]          # increasing vertex order
+        self.pin_dofs = (3 * self.pin_verts[:, None] + np.arange(3)).ravel()
         self.A_ff = self.A[self.free_dofs][:, self.free_dofs].tocsc()
         self.A_fp = self.A[self.free_dofs][:, self.pin_dofs].tocsc()
         self._lu = None
@@ -257,9 +258,10 @@ class FEM:
 
     def assemble_rhs(self, s_tilde, p, q_pinned):
         """b = M s~ + h^2 sum_i w_i G_i^T p_i (Eq. 6), restricted to the free DoFs, with the
-        pinned vertices' prescribed positions moved to the right-hand side. p holds the
-        tetrahedra's 9 values then the triangles' 6 per element (the bending term has no
-        projection: its rest curvature is zero)."""
+        pinned vertices' prescribed positions q_pinned (rows in increasing vertex order,
+        pin_verts) moved to the right-hand side. p holds the tetrahedra's 9 values then the
+        triangles' 6 per element (the bending term has no projection: its rest curvature is
+        zero)."""
         full = (np.repeat(self.mass, 3) * s_tilde.reshape(-1)
                 + self.h ** 2 * (self.G.T @ (self.wvec * p.reshape(-1))))
         b = full[self.free_dofs]

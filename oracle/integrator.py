@@ -59,7 +59,7 @@ class OracleOptions:
     ncp: str = "fb"                        # "fb" (App. B.2) or "minmap" (App. B.1)
     local: str = "pd"                      # "pd" (Eq. 5) or "admm" (ADMM-PD, Sec. 7)
     global_solver: str = "direct"          # "direct" (A^-1 b) or "jacobi" (the comparison
-    jacobi_sweeps: int = 10                #  of Sec. 8's convergence figure: sweeps from q^k)
+    jacobi_sweeps: int = 1                 #  of Sec. 8's convergence figure: sweeps from q^k)
     precond: str = "delassus"              # "delassus" (Eq. 28) or "mass" (Sec. 5.4)
 
 
@@ -77,7 +77,9 @@ class Oracle:
         return q_t + self.h * v_t + self.h ** 2 * self.g[None, :]
 
     def pinned_positions(self, q_t):
-        return q_t[self.scene.pinned] + self.h * np.asarray(self.scene.handle_vel)[None, :]
+        """End-of-frame positions of the pinned vertices, in increasing vertex order (the
+        order of the columns of A_fp), whatever the order of the scene's pinned list."""
+        return (q_t[self.fem.pin_verts] + self.h * np.asarray(self.scene.handle_vel)[None, :])
 
     def local_step(self, q):
         """p_i = project(G_i q) for every element (Eq. 5): the tetrahedra's (T, 3, 3), then,
@@ -228,7 +230,7 @@ class Oracle:
             return self.residual(cs, lam, r_n), cs
 
         q = s_tilde.copy()
-        q[self.scene.pinned] = q_pin
+        q[f.pin_verts] = q_pin
         if dq0 is not None:
             q[fv] += dq0[fv]
         lam = np.zeros((c, 3)) if lam0 is None else np.array(lam0, dtype=np.float64)

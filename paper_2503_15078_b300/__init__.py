@@ -127,7 +127,8 @@ def _options(scene=None, **kw):
 # options that also take names: the complementarity functions (App. B.1-B.2), the
 # complementarity preconditioner (Sec. 5.4) and the local step (PD or ADMM-PD)
 _NAMED = {"ncp": {"fb": 0, "minmap": 1}, "precond": {"delassus": 0, "mass": 1},
-          "local_solver": {"pd": 0, "admm": 1}}
+          "local_solver": {"pd": 0, "admm": 1},
+          "global_solver": {"sparse_inverse": 0, "jacobi": 1}}
 
 
 class Plan:

@@ -62,7 +62,8 @@ class SimOptions(C.Structure):
                 ("n_host_threads", C.c_int32), ("autotune", C.c_int32),
                 ("ncp", C.c_int32), ("precond", C.c_int32),
                 ("residual_tol", C.c_double), ("max_iters", C.c_int32),
-                ("local_solver", C.c_int32), ("phase_marks", C.c_int32),
+                ("local_solver", C.c_int32), ("global_solver", C.c_int32),
+                ("jacobi_sweeps", C.c_int32), ("phase_marks", C.c_int32),
                 ("dev_alloc", DEV_ALLOC), ("dev_free", DEV_FREE), ("alloc_ctx", C.c_void_p)]
 
 

@@ -47,6 +47,8 @@ void sim_default_options(sim_options* o) {
   o->residual_tol = 0.0;
   o->max_iters = 40;
   o->local_solver = SIM_LOCAL_PD;
+  o->global_solver = SIM_GLOBAL_SPARSE_INVERSE;
+  o->jacobi_sweeps = 1;
   o->phase_marks = 1;
 }
 

@@ -80,6 +80,10 @@ struct DevSim {
   // zeroed at every frame start (null with the plain local step)
   int admm;
   float* tet_u;
+  // SIM_GLOBAL_JACOBI: sweeps per global step (0: the sparse-inverse solve) and the second
+  // buffer of the sweeps (3 n_all)
+  int jacobi_sweeps;
+  float* dq_alt;
   // iterating to a tolerance (sim_options.residual_tol > 0, sim_step with n_iters <= 0): the
   // device counts the finished global updates and a CUDA graph while-node repeats the
   // iteration until R_k <= res_tol or max_iters updates
@@ -310,6 +314,8 @@ void launch_iter_advance(const DevSim& d, cudaStream_t s);
 void launch_iter_decide(const DevSim& d, cudaStream_t s, cudaGraphConditionalHandle h);
 void launch_iter_clear(const DevSim& d, cudaStream_t s);
 void launch_rhs(const DevSim& d, cudaStream_t s);
+// the Jacobi global step: d.jacobi_sweeps sweeps dq <- dq + D^-1 (g - A~ dq), result in d.dq
+void launch_jacobi(const DevSim& d, cudaStream_t s);
 // z = S~ g: the product (partial sums) and the fixed-order reduction into zvec
 void launch_pass1(const DevSim& d, cudaStream_t s);
 void launch_reduce1(const DevSim& d, cudaStream_t s);

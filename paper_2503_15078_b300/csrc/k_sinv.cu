@@ -21,6 +21,8 @@
 // deterministic.
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include "device.cuh"
 
 namespace silg {
@@ -410,7 +412,37 @@ __global__ void k_residual(DevSim d) {
   d.gsave[2 * d.n_pad + i] = (float)r2;
 }
 
+// One Jacobi sweep of A~ dq = g (the incomplete global step of the comparison in Sec. 8):
+// dst_i = src_i + (g_i - (A~ src)_i) / A~_ii for the free vertices, sums in FP64.
+__global__ void k_jacobi(DevSim d, const float* src, float* dst) {
+  pdl_wait();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n) return;
+  double r0 = d.gvec[i], r1 = d.gvec[d.n_pad + i], r2 = d.gvec[2 * d.n_pad + i], dia = 1.0;
+  for (int e = d.A_ptr[i]; e < d.A_ptr[i + 1]; ++e) {
+    const int j = d.A_idx[e];
+    const double a = d.A_val[e];
+    if (j == i) dia = a;
+    r0 -= a * src[3 * j];
+    r1 -= a * src[3 * j + 1];
+    r2 -= a * src[3 * j + 2];
+  }
+  dst[3 * i] = (float)(src[3 * i] + r0 / dia);
+  dst[3 * i + 1] = (float)(src[3 * i + 1] + r1 / dia);
+  dst[3 * i + 2] = (float)(src[3 * i + 2] + r2 / dia);
+}
+
 }  // namespace
+
+void launch_jacobi(const DevSim& d, cudaStream_t s) {
+  float* a = d.dq;
+  float* b = d.dq_alt;
+  for (int k = 0; k < d.jacobi_sweeps; ++k) {
+    launch_k(d.pdl, k_jacobi, (d.n + 255) / 256, 256, 0, s, d, (const float*)a, b);
+    std::swap(a, b);
+  }
+  if (a != d.dq) cudaMemcpyAsync(d.dq, a, 3 * sizeof(float) * (size_t)d.n, cudaMemcpyDeviceToDevice, s);
+}
 
 int sinv_setup() {
   // pass 1 stages the g slices of a CTA's column tiles: up to 3 KB per tile of its range

@@ -133,7 +133,7 @@ int sync_and_check(sim_s* s) {
 
 // iterations of a K-iteration frame that end with a residual correction (BF16 profile)
 int refined_iters(const sim_s* s, int K) {
-  if (!s->d.s_bf16 || s->d.refine <= 0) return 0;
+  if (!s->d.s_bf16 || s->d.refine <= 0 || s->d.jacobi_sweeps) return 0;
   return s->d.refine >= 2 ? K : 1;
 }
 
@@ -155,12 +155,13 @@ int local_kernels(const sim_s* s) { return (s->d.n_tets > 0) + (s->d.n_tris > 0)
 // launches of a frame to a tolerance that made K updates (enqueue_frame_to_tolerance)
 int kernels_per_frame_to_tolerance(const sim_s* s, int K) {
   const bool c = s->has_obstacles;
-  const int refine_body = s->d.s_bf16 && s->d.refine >= 2 ? 5 : 0;
-  const int refine_end = s->d.s_bf16 && s->d.refine == 1 ? 6 : 0;
+  const int refine_body = s->d.s_bf16 && s->d.refine >= 2 && !s->d.jacobi_sweeps ? 5 : 0;
+  const int refine_end = s->d.s_bf16 && s->d.refine == 1 && !s->d.jacobi_sweeps ? 6 : 0;
+  const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 : 0) + 2;
   const int before = 1 + (s->d.bend_ptr != nullptr) +
                      (c ? 4 + 12 + silg::ws_kernels(s->d.ws_mode) : 0) + local_kernels(s) +
                      (c ? 1 : 0);
-  const int body = 1 + 2 + (c ? 3 : 0) + 2 + refine_body + 1 + (c ? 1 : 0) + local_kernels(s) + 1;
+  const int body = 1 + global + refine_body + 1 + (c ? 1 : 0) + local_kernels(s) + 1;
   const int after = refine_end + (c ? 1 : 0) + 1 + (c && s->d.pf_copies > 1 ? 1 : 0);
   return before + K * body + after;
 }
@@ -169,8 +170,9 @@ int kernels_per_frame(const sim_s* s, int K) {
   const bool c = s->has_obstacles;
   // per iteration: local, [contact eval], rhs, pass 1 + reduction, [Y^T z, CR, Y u],
   // pass 2 + reduction; a residual correction adds the residual and both passes
+  const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 : 0) + 2;
   return 1 + (s->d.bend_ptr != nullptr) + (c ? 4 + 12 : 0) +
-         K * (local_kernels(s) + (c ? 1 : 0) + 1 + 2 + (c ? 3 : 0) + 2) + (c ? 1 : 0) + 1 +
+         K * (local_kernels(s) + (c ? 1 : 0) + 1 + global) + (c ? 1 : 0) + 1 +
          5 * refined_iters(s, K) + (c ? silg::ws_kernels(s->d.ws_mode) : 0) +
          (c && s->d.pf_copies > 1 ? 1 : 0);
 }
@@ -239,6 +241,11 @@ void enqueue_frame(sim_s* s, int K, cudaStream_t st) {
     imark(e);
     silg::launch_rhs(d, st);
     imark(e + 1);
+    if (d.jacobi_sweeps) {
+      // the incomplete global step of the comparison (timed as the first product's phase)
+      silg::launch_jacobi(d, st);
+      for (int m = 2; m <= 5; ++m) imark(e + m);
+    } else {
     silg::launch_pass1(d, st);
     imark(e + 2);
     silg::launch_reduce1(d, st);
@@ -252,6 +259,7 @@ void enqueue_frame(sim_s* s, int K, cudaStream_t st) {
     silg::launch_pass2(d, st);
     imark(e + 5);
     silg::launch_reduce2(d, st, silg::kOutDq);
+    }
     if (k >= K - refined_iters(s, K)) {
       // BF16 profile: dq += S~^T S~ (rhs - A~ dq), the residual summed in FP64 and the
       // iteration's contact impulses held fixed
@@ -350,16 +358,20 @@ cudaError_t enqueue_frame_to_tolerance(sim_s* s, cudaStream_t st) {
     e = cudaStreamBeginCaptureToGraph(b, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     silg::launch_rhs(d, b);
-    silg::launch_pass1(d, b);
-    silg::launch_reduce1(d, b);
-    if (s->has_obstacles) {
-      silg::launch_ytz(d, b);
-      silg::launch_cr(d, b, s->cluster);
-      silg::launch_yu(d, b);
+    if (d.jacobi_sweeps) {
+      silg::launch_jacobi(d, b);
+    } else {
+      silg::launch_pass1(d, b);
+      silg::launch_reduce1(d, b);
+      if (s->has_obstacles) {
+        silg::launch_ytz(d, b);
+        silg::launch_cr(d, b, s->cluster);
+        silg::launch_yu(d, b);
+      }
+      silg::launch_pass2(d, b);
+      silg::launch_reduce2(d, b, silg::kOutDq);
     }
-    silg::launch_pass2(d, b);
-    silg::launch_reduce2(d, b, silg::kOutDq);
-    if (d.s_bf16 && d.refine >= 2) {
+    if (d.s_bf16 && d.refine >= 2 && !d.jacobi_sweeps) {
       silg::launch_residual(d, b, s->has_obstacles ? silg::kResFrameContact : silg::kResFrame);
       DevSim dr = d;
       dr.gvec = d.gsave;
@@ -380,7 +392,7 @@ cudaError_t enqueue_frame_to_tolerance(sim_s* s, cudaStream_t st) {
     if (e != cudaSuccess) return e;
   }
   mark(4);
-  if (d.s_bf16 && d.refine == 1) {
+  if (d.s_bf16 && d.refine == 1 && !d.jacobi_sweeps) {
     // the correction after the last update; its residual entries are evaluated again
     silg::launch_iter_clear(d, st);
     silg::launch_residual(d, st, s->has_obstacles ? silg::kResFrameContact : silg::kResFrame);
@@ -595,6 +607,9 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   d.max_iters = o->max_iters;
   d.admm = o->local_solver == SIM_LOCAL_ADMM;
   d.tet_u = d.admm ? s->alloc<float>(9 * (size_t)T) : nullptr;
+  d.jacobi_sweeps = o->global_solver == SIM_GLOBAL_JACOBI ? o->jacobi_sweeps : 0;
+  d.dq_alt = d.jacobi_sweeps ? s->alloc<float>(3 * (size_t)n_all) : nullptr;
+  if (d.jacobi_sweeps && (n_obs > 0 || !sd.anchors.empty())) return SIM_EINVAL;
   d.h = p.h;
   d.h2f = (float)(p.h * p.h);
   for (int r = 0; r < 3; ++r) d.grav[r] = o->gravity[r];
@@ -1004,6 +1019,10 @@ int check_options(const sim_options* o) {
   if (o->refine < 0 || o->refine > 2) return SIM_EINVAL;
   if (o->ncp != SIM_NCP_FB && o->ncp != SIM_NCP_MINMAP) return SIM_EINVAL;
   if (o->local_solver != SIM_LOCAL_PD && o->local_solver != SIM_LOCAL_ADMM) return SIM_EINVAL;
+  if (o->global_solver != SIM_GLOBAL_SPARSE_INVERSE && o->global_solver != SIM_GLOBAL_JACOBI)
+    return SIM_EINVAL;
+  if (o->global_solver == SIM_GLOBAL_JACOBI && (o->jacobi_sweeps < 1 || o->jacobi_sweeps > 1000))
+    return SIM_EINVAL;
   if (!(o->residual_tol >= 0.0) || o->max_iters < 1 || o->max_iters > silg::kMaxIters)
     return SIM_EINVAL;
   if ((o->dev_alloc == nullptr) != (o->dev_free == nullptr)) return SIM_EINVAL;
@@ -1030,6 +1049,8 @@ int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_opt
         sc.mesh.n_tets + sc.mesh.n_tris <= 0 || !sc.mesh.rest_pos ||
         (sc.mesh.n_tets > 0 && !sc.mesh.tets) || (sc.mesh.n_tris > 0 && !sc.mesh.tris) ||
         (sc.mesh.n_tris > 0 && o->local_solver == SIM_LOCAL_ADMM) ||
+        // the Jacobi comparison solves the contact-free system only
+        (o->global_solver == SIM_GLOBAL_JACOBI && (sc.n_obstacles > 0 || sc.n_anchors > 0)) ||
         !sc.materials || sc.n_materials <= 0 || sc.n_obstacles < 0 ||
         (sc.n_obstacles > 0 && !sc.obstacles) || sc.mesh.n_pinned < 0 ||
         (sc.mesh.n_pinned > 0 && !sc.mesh.pinned))

@@ -187,3 +187,12 @@ def test_invalid_sheets_are_rejected(bad):
     with pytest.raises(SimError) as e:
         Simulator(sc, **kw)
     assert e.value.status == -1
+
+
+def test_jacobi_global_step_needs_a_scene_without_contact():
+    with pytest.raises(SimError) as e:
+        Simulator(sg.cube_drop(m=3), global_solver="jacobi")
+    assert e.value.status == -1
+    with pytest.raises(SimError) as e:
+        Simulator(sg.twisting_bar(nxy=3, nz=4), global_solver="jacobi", jacobi_sweeps=0)
+    assert e.value.status == -1
