@@ -409,6 +409,49 @@ def variants_timing(scene, q0, v0, steps, flush):
                                 "verts": sheet.n_verts, "tris": int(len(sheet.tris)),
                                 "nnz_S": info["nnz_S"]}
     sim.close()
+    out["twisting_bar_20k"] = twisting_bar_timing(steps, flush)
+    return out
+
+
+def twisting_bar_timing(steps, flush):
+    """The paper's largest twisting bar (its Tab. of timings: 20.8k vertices, ARAP, E = 1e9,
+    nu = 0.45, rho = 1000) as a 12 x 12 x 145 lattice (20,880 vertices, 104.5k tets), the top
+    turned 45 degrees: device ms per local-global iteration of the production graph with the
+    complete global step (x = S^T S b) and with the single Jacobi sweep of Sec. 8's baseline,
+    the instrumented graph's split of one iteration into local and global time, and how far
+    the baseline's 60-iteration frame still is from the complete one (relative displacement)."""
+    import numpy as np
+    import torch
+    import scenegen as sg
+    from paper_2503_15078_b300 import Simulator
+    bar = sg.twisting_bar(nxy=12, nz=145, spacing=0.01, E=1e9, nu=0.45, rho=1000.0)
+    out = {"verts": bar.n_verts, "tets": int(len(bar.tets)), "iters": 10}
+    q60 = {}
+    for name, kw in (("complete", {}), ("jacobi1", dict(global_solver="jacobi",
+                                                          jacobi_sweeps=1))):
+        prod = Simulator(bar, autotune=0, phase_marks=0, **kw)
+        inst = Simulator(bar, autotune=0, phase_marks=1, **kw)
+        times, split = [], []
+        for k in range(3 + steps):
+            for sim, acc in ((prod, times), (inst, split)):
+                sim.set_state(bar.q0, bar.v0)
+                flush.zero_()
+                torch.cuda.synchronize()
+                sim.step(n_iters=10)
+                if k >= 3:
+                    acc.append(sim.phase_times())
+        glob = ("spmv1", "reduce", "solve", "spmv2")
+        out[name] = {
+            "ms_per_iter": round(statistics.mean(sum(t.values()) for t in times) / 10, 5),
+            "local_ms_per_iter": round(statistics.mean(t["local"] for t in split) / 10, 5),
+            "global_ms_per_iter": round(statistics.mean(sum(t.get(g, 0.0) for g in glob)
+                                                        for t in split) / 10, 5)}
+        prod.set_state(bar.q0, bar.v0)
+        prod.step(n_iters=60)
+        q60[name] = prod.state()[0]
+        prod.close()
+        inst.close()
+    out["jacobi1_gap_at_60_iters"] = float(f"{np.linalg.norm(q60['jacobi1'] - q60['complete']) / np.linalg.norm(q60['complete'] - bar.q0):.3e}")
     return out
 
 
