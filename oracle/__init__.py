@@ -25,7 +25,9 @@ Modules:
                   Neo-Hookean energies; ARAP and co-rotational membranes
   contact         collision detection and linearisation (App. A.1), Fischer-Burmeister
                   functions and their derivatives (App. B.2), the minimum map (App. B.1),
-                  anchors (bilateral constraints), conjugate residual
+                  anchors (bilateral constraints), contact between deformable bodies
+                  (a vertex against another body's nearest surface triangle), conjugate
+                  residual
   sparse_inverse  elimination tree, Cholesky factor and its inverse (Theorem 1, Alg. 2)
   integrator      the frame loop of Alg. 4, residual and energy diagnostics
   precision       BF16 storage of S and one residual correction (not from the paper)

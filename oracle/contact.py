@@ -75,11 +75,137 @@ def closest_point(obst, x):
     raise ValueError("unknown obstacle kind")
 
 
-def detect(scene, s_tilde, free_verts, t_end=0.0):
+# -- contact between deformable bodies (App. A.1 with a two-sided contact map) ----------
+def mesh_bodies(n_verts, tets):
+    """Body id of every vertex: the connected components of the tetrahedra, numbered in
+    order of their smallest vertex id (a vertex in no element is a body of its own)."""
+    parent = list(range(n_verts))
+
+    def root(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+    for t in np.asarray(tets):
+        r0 = root(int(t[0]))
+        for v in t[1:]:
+            r = root(int(v))
+            if r != r0:
+                parent[max(r, r0)] = min(r, r0)
+                r0 = min(r, r0)
+    roots = [root(v) for v in range(n_verts)]
+    ids = {}
+    for r in roots:               # roots are the components' smallest ids, met in order
+        ids.setdefault(r, len(ids))
+    return np.array([ids[r] for r in roots], dtype=np.int64)
+
+
+def surface_triangles(X, tets):
+    """The faces of the tetrahedra that belong to one element only, each oriented so that
+    its normal (b - a) x (c - a) points away from the element (at the rest shape X) and
+    rotated to start at its smallest vertex id; sorted by their sorted vertex triples."""
+    count, owner = {}, {}
+    for t in np.asarray(tets):
+        for k in range(4):
+            face = tuple(int(t[i]) for i in range(4) if i != k)
+            key = tuple(sorted(face))
+            count[key] = count.get(key, 0) + 1
+            owner[key] = (face, int(t[k]))
+    out = []
+    for key in sorted(k for k, c in count.items() if c == 1):
+        (a, b, c), d = owner[key]
+        if np.dot(np.cross(X[b] - X[a], X[c] - X[a]), X[d] - X[a]) > 0:
+            b, c = c, b
+        tri = [a, b, c]
+        i = int(np.argmin(tri))
+        out.append(tri[i:] + tri[:i])
+    return np.array(out, dtype=np.int64).reshape(-1, 3)
+
+
+def closest_point_triangle(x, a, b, c):
+    """(closest point of the triangle abc to x, its barycentric weights). Inside the
+    triangle's projection the point is the orthogonal projection onto the plane; otherwise
+    it lies on the boundary, the nearest of the three edges' clamped projections (edges in
+    the order ab, bc, ca; the first wins a tie)."""
+    e1, e2, r = b - a, c - a, x - a
+    G = np.array([[e1 @ e1, e1 @ e2], [e1 @ e2, e2 @ e2]])
+    u, v = np.linalg.solve(G, np.array([e1 @ r, e2 @ r]))
+    if u >= 0.0 and v >= 0.0 and u + v <= 1.0:
+        w = np.array([1.0 - u - v, u, v])
+        return w[0] * a + w[1] * b + w[2] * c, w
+    best = None
+    for i, j in ((0, 1), (1, 2), (2, 0)):
+        P, Q = (a, b, c)[i], (a, b, c)[j]
+        t = float(np.clip((x - P) @ (Q - P) / ((Q - P) @ (Q - P)), 0.0, 1.0))
+        p = P + t * (Q - P)
+        dist = float(np.linalg.norm(x - p))
+        if best is None or dist < best[0]:
+            w = np.zeros(3)
+            w[i], w[j] = 1.0 - t, t
+            best = (dist, p, w)
+    return best[1], best[2]
+
+
+def detect_bodies(scene, s_tilde, free_mask, bodies, tris, id_base):
+    """Contacts between the scene's bodies at the predicted positions, one per vertex at
+    most: every free vertex of a surface triangle is matched with the nearest surface
+    triangle (Euclidean distance to its closest point p; the lowest index on a tie) of
+    another body whose corners are all free. The gap g is signed by the triangle's unit
+    normal m at s~ where p lies inside the triangle (g = m . (x - p) = +-|x - p|); where p
+    is on its boundary (an edge or a corner) x is taken to be outside the other body,
+    g = |x - p| (a single face's plane does not tell inside from outside there). The pair
+    is a contact when -2 margin < g < margin. Its normal is n = (x - p) / g, the direction
+    of the distance (m itself when x = p): above the triangle's interior that is m, at an
+    edge or a corner it does not depend on which of the triangles sharing it was taken. The map is x_v - sum_k w_k x_k (w the closest point's barycentric weights, a
+    corner with w_k = 0 dropped), the frame (n, f1, f2), d_n = d_f = 0 (the other body's
+    motion is in the map itself). Returns {vertex: contact} with the id id_base + triangle
+    index."""
+    margin = float(scene.contact_margin)
+    surf = np.unique(tris)
+    ok_tri = np.all(free_mask[tris], axis=1)
+    out = {}
+    for v in surf:
+        if not free_mask[v]:
+            continue
+        x = s_tilde[v]
+        best = None
+        for t in np.nonzero(ok_tri & (bodies[tris[:, 0]] != bodies[v]))[0]:
+            a, b, c = (s_tilde[k] for k in tris[t])
+            p, w = closest_point_triangle(x, a, b, c)
+            d = float(np.linalg.norm(x - p))
+            if best is None or d < best[0]:
+                best = (d, t, p, w)
+        if best is None:
+            continue
+        d, t, p, w = best
+        a, b, c = (s_tilde[k] for k in tris[t])
+        m = np.cross(b - a, c - a)
+        m /= np.linalg.norm(m)
+        inside = bool(np.all(w > 0.0))
+        g = float(m @ (x - p)) if inside else d
+        if not (-2.0 * margin < g < margin):
+            continue
+        n = (x - p) / g if d > 0.0 else m
+        phi = float(n @ (x - p))
+        f1, f2 = tangent_frame(n)
+        corners = [(int(tris[t][k]), float(w[k])) for k in range(3) if w[k] != 0.0]
+        out[int(v)] = dict(vertex=int(v), obstacle=id_base + int(t), n=n, f1=f1, f2=f2,
+                           d_n=0.0, d_f=np.zeros(2), mu=float(scene.body_mu), gap=phi,
+                           corners=corners, body=True)
+    return out
+
+
+def detect(scene, s_tilde, free_verts, t_end=0.0, body_data=None):
     """All (vertex, obstacle) pairs with signed distance below the contact margin at the
     predicted positions, ordered by vertex id then obstacle index; then, at its vertex, each
     anchor (a bilateral constraint, App. A.1's b rows) with the id n_obstacles + its index,
-    its target at time t_end (the end of the frame) and the world axes as its three rows."""
+    its target at time t_end (the end of the frame) and the world axes as its three rows;
+    then, with body_data = (free mask, bodies, surface triangles), the vertex's contact with
+    another body (detect_bodies) with the id n_obstacles + n_anchors + triangle index."""
+    body_ct = {}
+    if body_data is not None:
+        n_ids = len(scene.obstacles) + len(getattr(scene, "anchors", []))
+        body_ct = detect_bodies(scene, s_tilde, *body_data, n_ids)
     out = []
     anchor_of = {int(a.vertex): i for i, a in enumerate(getattr(scene, "anchors", []))}
     n_obs = len(scene.obstacles)
@@ -101,6 +227,8 @@ def detect(scene, s_tilde, free_verts, t_end=0.0):
             out.append(dict(vertex=int(v), obstacle=n_obs + a, n=eye[0], f1=eye[1], f2=eye[2],
                             anchor=True, target=target, compliance=float(an.compliance),
                             d_n=float(target[0]), d_f=np.zeros(2), mu=0.0, gap=0.0))
+        if int(v) in body_ct:
+            out.append(body_ct[int(v)])
     return out
 
 

@@ -70,6 +70,12 @@ class Oracle:
         self.h = float(scene.h)
         self.g = np.asarray(scene.gravity, dtype=np.float64)
         self.L_ref = scene.bbox_diagonal
+        self.body_data = None
+        if getattr(scene, "body_contact", False):
+            free = np.zeros(scene.n_verts, dtype=bool)
+            free[self.fem.free_verts] = True
+            self.body_data = (free, C.mesh_bodies(scene.n_verts, scene.tets),
+                              C.surface_triangles(scene.X, scene.tets))
 
     # -- pieces of Alg. 4 ---------------------------------------------------------------
     def predict(self, q_t, v_t):
@@ -118,16 +124,19 @@ class Oracle:
         return z - u, u
 
     def contact_jacobian(self, contacts):
-        """H (3c x 3n_f): rows n_j, f1_j, f2_j at the DoFs of contact j's vertex (Eqs. 36-37)."""
+        """H (3c x 3n_f): rows n_j, f1_j, f2_j at the DoFs of contact j's vertex (Eqs. 36-37);
+        a contact with another body has them also at its triangle's corners, times -w_k."""
         f = self.fem
         pos = {int(v): i for i, v in enumerate(f.free_verts)}
         c = len(contacts)
         H = np.zeros((3 * c, 3 * len(f.free_verts)))
         for j, ct in enumerate(contacts):
+            D = np.stack([ct["n"], ct["f1"], ct["f2"]])
             k = pos[ct["vertex"]]
-            H[3 * j + 0, 3 * k:3 * k + 3] = ct["n"]
-            H[3 * j + 1, 3 * k:3 * k + 3] = ct["f1"]
-            H[3 * j + 2, 3 * k:3 * k + 3] = ct["f2"]
+            H[3 * j:3 * j + 3, 3 * k:3 * k + 3] += D
+            for vk, w in ct.get("corners", ()):
+                k = pos[vk]
+                H[3 * j:3 * j + 3, 3 * k:3 * k + 3] -= w * D
         return H
 
     def delassus(self, H):
@@ -207,7 +216,7 @@ class Oracle:
         fv = f.free_verts
         s_tilde = self.predict(q_t, v_t)
         q_pin = self.pinned_positions(q_t)
-        contacts = C.detect(self.scene, s_tilde, fv, t + h)
+        contacts = C.detect(self.scene, s_tilde, fv, t + h, self.body_data)
         c = len(contacts)
         if c and opts.global_solver == "jacobi":
             raise ValueError("the Jacobi global step is for scenes without contact")

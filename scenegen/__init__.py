@@ -94,6 +94,10 @@ class Scene:
     q0: Optional[np.ndarray] = None       # (n, 3) initial positions (default: X)
     v0: Optional[np.ndarray] = None       # (n, 3) initial velocities (default: 0)
     contact_margin: float = 0.0           # a contact exists when the gap is below this
+    # contact between the scene's separate bodies (connected components of its tetrahedra):
+    # a vertex against the nearest surface triangle of another body, friction body_mu
+    body_contact: bool = False
+    body_mu: float = 0.0
     n_iters: int = 5                      # local-global iterations per frame
     n_cr: int = 10                        # conjugate-residual iterations per solve
     n_frames: int = 1
@@ -372,6 +376,34 @@ def twisting_bar(nxy: int = 4, nz: int = 16, spacing: float = 0.02, twist_deg: f
                  [Material(model, E, nu, rho)], [], h, gravity=(0.0, 0.0, 0.0),
                  pinned=np.concatenate([bottom, top]).astype(np.int32), q0=q0,
                  spacing=spacing)
+
+
+def box_stack(n_boxes: int = 3, m: int = 4, edge: float = 0.1, model: int = MODEL_SNH,
+              E: float = 1e8, nu: float = 0.45, rho: float = 1000.0, mu: float = 0.8,
+              incline_deg: float = 20.0, gap: float = 0.25, offset: float = 0.2,
+              seed: int = 0, h: float = 1.0 / 60.0, n_iters: int = 10) -> Scene:
+    """A stack of n_boxes m^3-vertex boxes (edge ``edge``) on a plane inclined by
+    ``incline_deg`` about the y axis: each box rests on the one below across a gap of
+    ``gap`` lattice spacings (the lowest on the plane), shifted within the plane by a seeded
+    offset of up to ``offset`` edges along each axis; friction mu on the plane and between
+    the boxes (the stress case's deformable box-box contacts). Rest shape = start."""
+    rng = np.random.default_rng(seed)
+    sp = edge / (m - 1)
+    Xb, tb = lattice_tets(m, m, m, sp, origin=(-edge / 2, -edge / 2, 0.0))
+    R = _rot_y(incline_deg)
+    Xs, Ts = [], []
+    for k in range(n_boxes):
+        dx, dy = rng.uniform(-offset, offset, size=2) * edge
+        z0 = gap * sp + k * (edge + gap * sp)
+        Xs.append((Xb + np.array([dx, dy, z0])) @ R.T)
+        Ts.append(tb + k * len(Xb))
+    X = np.concatenate(Xs)
+    tets = np.concatenate(Ts)
+    n_plane = R @ np.array([0.0, 0.0, 1.0])
+    obst = [Obstacle(OBST_PLANE, (0.0, 0.0, 0.0), tuple(n_plane), mu=mu)]
+    return Scene(f"stack{n_boxes}x{m}", X, tets, np.zeros(len(tets), np.int32),
+                 [Material(model, E, nu, rho)], obst, h, contact_margin=0.5 * sp,
+                 n_iters=n_iters, spacing=sp, body_contact=True, body_mu=mu)
 
 
 def hanging_cube(m: int = 5, edge: float = 0.1, model: int = MODEL_ARAP, E: float = 1e5,
