@@ -282,7 +282,24 @@ typedef struct {
 /* One independent scene of a batch: its mesh, its materials (tet_material indexes this
  * list), its obstacles (they act on this scene's vertices only), its contact margin
  * (<= 0: half the scene's mean edge; opts->contact_margin is not used by a batch) and its
- * anchors (may be NULL with n_anchors = 0). */
+ * anchors (may be NULL with n_anchors = 0).
+ *
+ * body_contact = 1: contact between the scene's bodies, the connected components of its
+ * tetrahedra (App. A.1's contact map with both sides moving). The surface triangles are
+ * the element faces that belong to one tetrahedron, oriented outward (at rest) and
+ * numbered in the order of their sorted vertex triples. Each frame, every free vertex of a
+ * surface triangle is matched with the nearest surface triangle of another body whose
+ * corners are all free (closest point p, Euclidean distance; the lower number on a tie),
+ * at the predicted positions. The gap g is signed by the triangle's plane where p is
+ * inside the triangle; at an edge or a corner the vertex counts as outside (g = |x - p|).
+ * It is a contact when -2 margin < g < margin, with normal n = (x - p) / g (the triangle's
+ * normal when x = p), rows (n, f1, f2), the map x_v - sum_k w_k x_k (w: p's barycentric
+ * weights; a corner with w_k = 0 drops out), d = 0 and friction coefficient body_mu. One
+ * such contact per vertex at most, after its obstacles and anchor; sim_get_contacts lists
+ * it with obstacle id = n_obstacles + n_anchors (of the whole simulator) + the triangle's
+ * number (numbers run over the scenes with body contact, scene by scene). Triangle corners
+ * become contact vertices: W~ covers them (Eq. 27 with the map's weights). Not with
+ * SIM_GLOBAL_JACOBI. body_contact = 0: none (body_mu unused). */
 typedef struct {
   sim_mesh mesh;
   const sim_material* materials;
@@ -292,6 +309,8 @@ typedef struct {
   double contact_margin;
   const sim_anchor* anchors;
   int32_t n_anchors;
+  int32_t body_contact;
+  double body_mu;
 } sim_scene;
 
 /*

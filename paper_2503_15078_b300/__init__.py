@@ -251,8 +251,9 @@ class Simulator:
 
     def __init__(self, scene, use_torch_stream=True, **opts):
         batch = isinstance(scene, (list, tuple))
-        if not batch and getattr(scene, "anchors", None):
-            scene, batch = [scene], True     # anchors travel in sim_scene (sim_create_batch)
+        if not batch and (getattr(scene, "anchors", None) or getattr(scene, "body_contact", False)):
+            # anchors and body contact travel in sim_scene (sim_create_batch)
+            scene, batch = [scene], True
         first = scene[0] if batch else scene
         o = _options(first, **opts)
         if use_torch_stream and "cuda_stream" not in opts:
@@ -284,6 +285,8 @@ class Simulator:
                     self._keep.append(an)
                     scs[k].anchors = C.cast(an, C.POINTER(_abi.SimAnchor))
                     scs[k].n_anchors = len(anchors)
+                scs[k].body_contact = 1 if getattr(sc, "body_contact", False) else 0
+                scs[k].body_mu = float(getattr(sc, "body_mu", 0.0))
             self._keep.append(scs)
             _check(lib().sim_create_batch(scs, len(scene), float(first.h), C.byref(o),
                                           C.byref(handle)), "sim_create_batch")

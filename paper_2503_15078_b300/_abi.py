@@ -46,7 +46,8 @@ class SimScene(C.Structure):
     _fields_ = [("mesh", SimMesh), ("materials", C.POINTER(SimMaterial)),
                 ("n_materials", C.c_int32), ("obstacles", C.POINTER(SimObstacle)),
                 ("n_obstacles", C.c_int32), ("contact_margin", C.c_double),
-                ("anchors", C.POINTER(SimAnchor)), ("n_anchors", C.c_int32)]
+                ("anchors", C.POINTER(SimAnchor)), ("n_anchors", C.c_int32),
+                ("body_contact", C.c_int32), ("body_mu", C.c_double)]
 
 
 # device allocator hooks of sim_options

@@ -220,6 +220,27 @@ struct DevSim {
 
   // obstacles
   const ObstDev* obst;
+  // contact between bodies (connected components of a scene's tetrahedra): a vertex
+  // against the nearest surface triangle of another body, the map x_v - sum_k w_k x_k
+  int bc_on;               // some scene has it (every array below is null otherwise)
+  int n_bodies;
+  const int* vert_body;    // n: body of a free surface vertex, -1 otherwise
+  const int4* btri;        // surface triangles with free corners, grouped by body: internal
+                           // corner ids, w = the triangle's number
+  const int* body_toff;    // n_bodies + 1
+  const int* scene_bfirst; // n_scenes + 1
+  const double* scene_bmu; // n_scenes: friction coefficient between bodies
+  double* body_box;        // 6 per body: bounds of its triangles' corners at s~
+  int* bc_tri;             // n: the vertex's matched triangle (index into btri) or -1
+  double* bc_w;            // 3 n: barycentric weights of the closest point
+  double* bc_n;            // 3 n: contact normal
+  int* x_cnt;              // n: corner terms at free vertex i (contacts whose triangle has
+  int* x_fill;             //    it as a corner with a non-zero weight)
+  int* x_off;              // n + 1
+  int* x_list;             // 3 cap: corner terms 3 j + k, per vertex ascending
+  int* ct_tri;             // cap: index into btri, -1 for other contacts
+  double* ct_bw;           // 3 cap: the corners' weights w_k (0: no term)
+  int* ct_tcv;             // 3 cap: the corners' contact-vertex indices (-1: no term)
 
   // contacts (capacity cap), sorted by internal vertex then obstacle
   int* counters;    // kNumCounters

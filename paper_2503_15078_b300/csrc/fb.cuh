@@ -86,7 +86,35 @@ __device__ inline void ncp_rows(bool minmap, double dn, const double vf[2], doub
   o.phif1 = vf[1] + o.Ef * lf1;
 }
 
-// contact j at vertex position q (world) with impulses lam (n, f1, f2); L: residual scale
+// The map of contact j applied to a per-vertex field: f_v for a contact at one vertex,
+// f_v - sum_k w_k f_k (the triangle's corners) for a contact with another body.
+template <typename Field>
+__device__ inline void contact_map(const DevSim& d, int j, Field f, double o[3]) {
+  const int v = d.ct_vert[j];
+  for (int r = 0; r < 3; ++r) o[r] = f(v, r);
+  if (!d.bc_on || d.ct_tri[j] < 0) return;
+  const int4 t = d.btri[d.ct_tri[j]];
+  const int cs[3] = {t.x, t.y, t.z};
+  for (int k = 0; k < 3; ++k) {
+    const double w = d.ct_bw[3 * j + k];
+    if (w != 0.0)
+      for (int r = 0; r < 3; ++r) o[r] -= w * f(cs[k], r);
+  }
+}
+
+// the map at the iterate q = q_ref + dq, and of dq alone; a common translation `shift` of
+// the scene adds to a one-vertex contact only (the weights of a contact with another body
+// sum to one)
+__device__ inline void contact_q(const DevSim& d, int j, const double* shift, double q[3]) {
+  contact_map(d, j, [&](int v, int r) { return d.q_ref[3 * v + r] + (double)d.dq[3 * v + r]; }, q);
+  if (shift && !(d.bc_on && d.ct_tri[j] >= 0))
+    for (int r = 0; r < 3; ++r) q[r] += shift[r];
+}
+__device__ inline void contact_dq(const DevSim& d, int j, double dq[3]) {
+  contact_map(d, j, [&](int v, int r) { return (double)d.dq[3 * v + r]; }, dq);
+}
+
+// contact j at map position q (world) with impulses lam (n, f1, f2); L: residual scale
 __device__ inline FbTerms fb_terms(const DevSim& d, int j, const double q[3], const double lam[3],
                                    double L) {
   FbTerms o;
@@ -112,7 +140,7 @@ __device__ inline FbTerms fb_terms(const DevSim& d, int j, const double q[3], co
     return o;
   }
   double qt[3];
-  for (int r = 0; r < 3; ++r) qt[r] = d.q_t[3 * v + r];
+  contact_map(d, j, [&](int u, int r) { return d.q_t[3 * u + r]; }, qt);
   o.dn = D[0] * q[0] + D[1] * q[1] + D[2] * q[2] - d.ct_dn[j];
   for (int a = 0; a < 2; ++a) {
     const double* f = D + 3 + 3 * a;

@@ -96,6 +96,166 @@ __device__ __forceinline__ bool maybe_contact(const ObstDev& o, const double* x,
   return phi < (float)margin + kPrefilterSlack * scale;
 }
 
+// Closest point of the triangle abc to x by the Voronoi-region method (Ericson, Real-Time
+// Collision Detection, Sec. 5.1.5): the corner regions, then the edge regions, else the
+// interior. Writes the barycentric weights w (exact zeros away from the corner or edge
+// found); returns whether the point lies inside the triangle (all weights positive).
+__device__ bool tri_closest(const double* x, const double* a, const double* b, const double* c,
+                            double* w) {
+  double ab[3], ac[3], ap[3], bp[3], cp[3];
+  for (int r = 0; r < 3; ++r) {
+    ab[r] = b[r] - a[r];
+    ac[r] = c[r] - a[r];
+    ap[r] = x[r] - a[r];
+    bp[r] = x[r] - b[r];
+    cp[r] = x[r] - c[r];
+  }
+  auto dot = [](const double* u, const double* v) { return u[0] * v[0] + u[1] * v[1] + u[2] * v[2]; };
+  w[0] = w[1] = w[2] = 0.0;
+  const double d1 = dot(ab, ap), d2 = dot(ac, ap);
+  if (d1 <= 0.0 && d2 <= 0.0) { w[0] = 1.0; return false; }
+  const double d3 = dot(ab, bp), d4 = dot(ac, bp);
+  if (d3 >= 0.0 && d4 <= d3) { w[1] = 1.0; return false; }
+  const double vc = d1 * d4 - d3 * d2;
+  if (vc <= 0.0 && d1 >= 0.0 && d3 <= 0.0) {
+    const double t = d1 / (d1 - d3);
+    w[0] = 1.0 - t;
+    w[1] = t;
+    return false;
+  }
+  const double d5 = dot(ab, cp), d6 = dot(ac, cp);
+  if (d6 >= 0.0 && d5 <= d6) { w[2] = 1.0; return false; }
+  const double vb = d5 * d2 - d1 * d6;
+  if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) {
+    const double t = d2 / (d2 - d6);
+    w[0] = 1.0 - t;
+    w[2] = t;
+    return false;
+  }
+  const double va = d3 * d6 - d5 * d4;
+  if (va <= 0.0 && d4 - d3 >= 0.0 && d5 - d6 >= 0.0) {
+    const double t = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+    w[1] = 1.0 - t;
+    w[2] = t;
+    return false;
+  }
+  const double inv = 1.0 / (va + vb + vc);
+  w[0] = va * inv;
+  w[1] = vb * inv;
+  w[2] = vc * inv;
+  return true;
+}
+
+__device__ __forceinline__ void load3(const double* src, int v, double* o) {
+  o[0] = src[3 * v];
+  o[1] = src[3 * v + 1];
+  o[2] = src[3 * v + 2];
+}
+
+// bounds of every body's triangle corners at the predicted positions (one CTA per body)
+constexpr int kBoxThreads = 128;
+__global__ void __launch_bounds__(kBoxThreads) k_body_box(DevSim d) {
+  const int b = blockIdx.x;
+  __shared__ double red[6][kBoxThreads];
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int t = d.body_toff[b] + threadIdx.x; t < d.body_toff[b + 1]; t += blockDim.x) {
+    const int4 tv = d.btri[t];
+    const int cs[3] = {tv.x, tv.y, tv.z};
+    for (int k = 0; k < 3; ++k)
+      for (int r = 0; r < 3; ++r) {
+        const double v = d.s_tilde[3 * cs[k] + r];
+        lo[r] = fmin(lo[r], v);
+        hi[r] = fmax(hi[r], v);
+      }
+  }
+  for (int r = 0; r < 3; ++r) {
+    red[r][threadIdx.x] = lo[r];
+    red[3 + r][threadIdx.x] = hi[r];
+  }
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int r = 0; r < 3; ++r) {
+        red[r][threadIdx.x] = fmin(red[r][threadIdx.x], red[r][threadIdx.x + w]);
+        red[3 + r][threadIdx.x] = fmax(red[3 + r][threadIdx.x], red[3 + r][threadIdx.x + w]);
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x < 6) d.body_box[6 * b + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// The body contact of free vertex i, if any (bc_tri, bc_w, bc_n): the nearest surface
+// triangle of another body of its scene (distance to the closest point, then the
+// triangle's number), accepted when its gap g lies in (-2 margin, margin). Only triangles
+// within 2 margins can be accepted, so bodies and triangles farther than that (bounds
+// padded by a relative 1e-6) are skipped without changing the choice.
+__device__ bool body_match(const DevSim& d, int i, const double* x, double margin) {
+  const int vb = d.vert_body[i];
+  d.bc_tri[i] = -1;
+  if (vb < 0) return false;
+  const int sc = d.vert_scene[i];
+  const double lim = 2.0 * margin * (1.0 + 1e-6) + 1e-12 * (fabs(x[0]) + fabs(x[1]) + fabs(x[2]));
+  double best_d = 1e300, bw[3] = {0.0, 0.0, 0.0};
+  int best = -1, best_id = 0;
+  bool best_in = false;
+  for (int b = d.scene_bfirst[sc]; b < d.scene_bfirst[sc + 1]; ++b) {
+    if (b == vb) continue;
+    const double* bx = d.body_box + 6 * b;
+    if (x[0] < bx[0] - lim || x[1] < bx[1] - lim || x[2] < bx[2] - lim || x[0] > bx[3] + lim ||
+        x[1] > bx[4] + lim || x[2] > bx[5] + lim)
+      continue;
+    for (int t = d.body_toff[b]; t < d.body_toff[b + 1]; ++t) {
+      const int4 tv = d.btri[t];
+      double a[3], bb[3], c[3];
+      load3(d.s_tilde, tv.x, a);
+      load3(d.s_tilde, tv.y, bb);
+      load3(d.s_tilde, tv.z, c);
+      bool far = false;
+      for (int r = 0; r < 3; ++r)
+        far = far || x[r] < fmin(a[r], fmin(bb[r], c[r])) - lim ||
+              x[r] > fmax(a[r], fmax(bb[r], c[r])) + lim;
+      if (far) continue;
+      double w[3];
+      const bool in = tri_closest(x, a, bb, c, w);
+      double e[3];
+      for (int r = 0; r < 3; ++r) e[r] = x[r] - (w[0] * a[r] + w[1] * bb[r] + w[2] * c[r]);
+      const double dist = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+      if (dist < best_d || (dist == best_d && tv.w < best_id)) {
+        best_d = dist;
+        best = t;
+        best_id = tv.w;
+        best_in = in;
+        for (int k = 0; k < 3; ++k) bw[k] = w[k];
+      }
+    }
+  }
+  if (best < 0) return false;
+  const int4 tv = d.btri[best];
+  double a[3], bb[3], c[3];
+  load3(d.s_tilde, tv.x, a);
+  load3(d.s_tilde, tv.y, bb);
+  load3(d.s_tilde, tv.z, c);
+  double e1[3], e2[3], m[3], e[3];
+  for (int r = 0; r < 3; ++r) {
+    e1[r] = bb[r] - a[r];
+    e2[r] = c[r] - a[r];
+    e[r] = x[r] - (bw[0] * a[r] + bw[1] * bb[r] + bw[2] * c[r]);
+  }
+  m[0] = e1[1] * e2[2] - e1[2] * e2[1];
+  m[1] = e1[2] * e2[0] - e1[0] * e2[2];
+  m[2] = e1[0] * e2[1] - e1[1] * e2[0];
+  const double mn = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+  for (int r = 0; r < 3; ++r) m[r] /= mn;
+  const double g = best_in ? m[0] * e[0] + m[1] * e[1] + m[2] * e[2] : best_d;
+  if (!(g > -2.0 * margin && g < margin)) return false;
+  for (int r = 0; r < 3; ++r) {
+    d.bc_n[3 * i + r] = best_d > 0.0 ? e[r] / g : m[r];
+    d.bc_w[3 * i + r] = bw[r];
+  }
+  d.bc_tri[i] = best;
+  return true;
+}
+
 __global__ void k_collide_count(DevSim d) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n) return;
@@ -109,14 +269,52 @@ __global__ void k_collide_count(DevSim d) {
     if (obst_query(d.obst[o], x, nn, ph) < margin) ++cnt;
   }
   if (d.n_anc > 0 && d.anc_of[i] >= 0) ++cnt;   // its anchor: one more slot, after the obstacles
+  if (d.bc_on) {
+    // its contact with another body: one more slot, after the anchor
+    d.x_cnt[i] = 0;
+    d.x_fill[i] = 0;
+    if (body_match(d, i, x, margin)) ++cnt;
+  }
   d.ct_cnt[i] = cnt;
   d.cv_flag[i] = cnt > 0;
 }
 
+// a matched triangle's corners (non-zero weights) become contact vertices and count one
+// corner term each
+__global__ void k_corner_flag(DevSim d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n) return;
+  const int t = d.bc_tri[i];
+  if (t < 0) return;
+  const int4 tv = d.btri[t];
+  const int cs[3] = {tv.x, tv.y, tv.z};
+  for (int k = 0; k < 3; ++k)
+    if (d.bc_w[3 * i + k] != 0.0) {
+      d.cv_flag[cs[k]] = 1;
+      atomicAdd(d.x_cnt + cs[k], 1);
+    }
+}
+
+// each vertex's corner terms in ascending order (the fill order above is not fixed)
+__global__ void k_corner_sort(DevSim d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n) return;
+  const int b = d.x_off[i], e = min(d.x_off[i + 1], 3 * d.cap);
+  for (int p = b + 1; p < e; ++p) {
+    const int key = d.x_list[p];
+    int q = p - 1;
+    while (q >= b && d.x_list[q] > key) {
+      d.x_list[q + 1] = d.x_list[q];
+      --q;
+    }
+    d.x_list[q + 1] = key;
+  }
+}
+
 __global__ void k_collide_write(DevSim d) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0 && d.ct_off[d.n] > d.cap) atomicOr(d.err, kErrCapacity);
-  if (i >= d.n || d.ct_cnt[i] == 0) return;
+  if (i == 0 && (d.ct_off[d.n] > d.cap || d.cv_off[d.n] > d.cap)) atomicOr(d.err, kErrCapacity);
+  if (i >= d.n || (d.ct_cnt[i] == 0 && !d.cv_flag[i])) return;
   double x[3] = {d.s_tilde[3 * i], d.s_tilde[3 * i + 1], d.s_tilde[3 * i + 2]};
   int j = d.ct_off[i];
   const int cv = d.cv_off[i];
@@ -143,6 +341,7 @@ __global__ void k_collide_write(DevSim d) {
       d.ct_vert[j] = i;
       d.ct_obst[j] = o;
       d.ct_cv[j] = cv;
+      if (d.bc_on) d.ct_tri[j] = -1;
       d.ct_dn[j] = n[0] * ph[0] + n[1] * ph[1] + n[2] * ph[2];
       d.ct_df[2 * j] = f1[0] * ob.vel[0] + f1[1] * ob.vel[1] + f1[2] * ob.vel[2];
       d.ct_df[2 * j + 1] = f2[0] * ob.vel[0] + f2[1] * ob.vel[1] + f2[2] * ob.vel[2];
@@ -162,6 +361,40 @@ __global__ void k_collide_write(DevSim d) {
     d.ct_df[2 * j] = d.anc_pos[3 * a + 1];
     d.ct_df[2 * j + 1] = d.anc_pos[3 * a + 2];
     d.ct_mu[j] = d.anc_e[a];
+    if (d.bc_on) d.ct_tri[j] = -1;
+  }
+  if (a >= 0) ++j;
+  const int t = d.bc_on ? d.bc_tri[i] : -1;
+  if (t >= 0 && j < d.cap) {
+    // the contact with another body: rows (n, f1, f2), the map x_i - sum_k w_k x_k, d = 0;
+    // the id -1 - the triangle's number; each corner with a non-zero weight gets a term
+    double n[3], f1[3], f2[3];
+    for (int r = 0; r < 3; ++r) n[r] = d.bc_n[3 * i + r];
+    tangent_frame(n, f1, f2);
+    for (int r = 0; r < 3; ++r) {
+      d.ct_D[9 * j + r] = n[r];
+      d.ct_D[9 * j + 3 + r] = f1[r];
+      d.ct_D[9 * j + 6 + r] = f2[r];
+    }
+    const int4 tv = d.btri[t];
+    d.ct_vert[j] = i;
+    d.ct_obst[j] = -1 - tv.w;
+    d.ct_cv[j] = cv;
+    d.ct_dn[j] = 0.0;
+    d.ct_df[2 * j] = d.ct_df[2 * j + 1] = 0.0;
+    d.ct_mu[j] = d.scene_bmu[sc];
+    d.ct_tri[j] = t;
+    const int cs[3] = {tv.x, tv.y, tv.z};
+    for (int k = 0; k < 3; ++k) {
+      const double w = d.bc_w[3 * i + k];
+      d.ct_bw[3 * j + k] = w;
+      d.ct_tcv[3 * j + k] = -1;
+      if (w == 0.0) continue;
+      const int cc = d.cv_off[cs[k]];
+      if (cc < d.cap) d.ct_tcv[3 * j + k] = cc;
+      const int pos = d.x_off[cs[k]] + atomicAdd(d.x_fill + cs[k], 1);
+      if (pos < 3 * d.cap) d.x_list[pos] = 3 * j + k;
+    }
   }
 }
 
@@ -534,14 +767,36 @@ __global__ void k_precond(DevSim d) {
   const int ncv = min(d.counters[kCntCv], d.cap);
   const int cv = d.ct_cv[j];
   double w = 0.0;
-  if (cv < ncv) {
-    const int sc = d.vert_scene[d.ct_vert[j]], l = cv - d.sc_cvb[sc];
-    w = (double)d.wt[d.sc_wtoff[sc] + (size_t)l * d.sc_ld[sc] + l];
+  // the contact's terms: its vertex (weight 1) and, for a contact with another body, the
+  // triangle's corners (weights -w_k); W_jj = sum_pq c_p c_q W~_pq (the frame rows are
+  // orthonormal), [H M^-1 H^T]_jj = sum_p c_p^2 / m_p
+  int tc[4] = {cv, -1, -1, -1};
+  double tw[4] = {1.0, 0.0, 0.0, 0.0};
+  int tv[4] = {d.ct_vert[j], 0, 0, 0};
+  if (d.bc_on && d.ct_tri[j] >= 0) {
+    const int4 t = d.btri[d.ct_tri[j]];
+    const int cs[3] = {t.x, t.y, t.z};
+    for (int k = 0; k < 3; ++k) {
+      tc[1 + k] = d.ct_tcv[3 * j + k];
+      tw[1 + k] = -d.ct_bw[3 * j + k];
+      tv[1 + k] = cs[k];
+    }
+  }
+  double wm = 0.0;
+  const int sc = d.vert_scene[d.ct_vert[j]];
+  const float* Wb = d.wt + d.sc_wtoff[sc];
+  const int ld = d.sc_ld[sc], cvb = d.sc_cvb[sc];
+  for (int p = 0; p < 4; ++p) {
+    if (tc[p] < 0 || tc[p] >= ncv) continue;
+    wm += tw[p] * tw[p] / d.mass[tv[p]];
+    for (int q = 0; q < 4; ++q)
+      if (tc[q] >= 0 && tc[q] < ncv)
+        w += tw[p] * tw[q] * (double)Wb[(size_t)(tc[p] - cvb) * ld + (tc[q] - cvb)];
   }
   // the residual's scale is always the Delassus diagonal (Eq. 28); the iteration's is that
-  // or, with the mass-inverse preconditioner (Sec. 5.4), [H M^-1 H^T]_jj = 1 / m_v for a
-  // one-vertex contact with unit frame rows
-  const double wi = d.precond == SIM_PRECOND_MASS ? 1.0 / d.mass[d.ct_vert[j]] : w;
+  // or, with the mass-inverse preconditioner (Sec. 5.4), [H M^-1 H^T]_jj (1 / m_v for a
+  // one-vertex contact with unit frame rows)
+  const double wi = d.precond == SIM_PRECOND_MASS ? wm : w;
   d.ct_r[4 * j] = d.h * d.h * wi;
   d.ct_r[4 * j + 1] = d.h * wi;
   d.ct_r[4 * j + 2] = d.h * d.h * w;
@@ -561,10 +816,8 @@ __global__ void k_contact_eval(DevSim d, int k, int final_eval) {
   double D[9];
   for (int r = 0; r < 9; ++r) D[r] = d.ct_D[9 * j + r];
   double dqv[3], q[3];
-  for (int r = 0; r < 3; ++r) {
-    dqv[r] = (double)d.dq[3 * v + r];
-    q[r] = d.q_ref[3 * v + r] + dqv[r];
-  }
+  contact_dq(d, j, dqv);
+  contact_q(d, j, nullptr, q);
   const double lamv[3] = {d.ct_lam[3 * j], d.ct_lam[3 * j + 1], d.ct_lam[3 * j + 2]};
   const int sc = d.vert_scene[v];
   const FbTerms fb = fb_terms(d, j, q, lamv, d.scene_Lref[sc]);
@@ -650,8 +903,14 @@ __global__ void __launch_bounds__(kYtzThreads) k_ytz(DevSim d) {
         s1 += part[1][w];
         s2 += part[2][w];
       }
+      if (d.bc_on && lane == 0) {
+        d.svec[3 * c] = s0;
+        d.svec[3 * c + 1] = s1;
+        d.svec[3 * c + 2] = s2;
+      }
       const int j0 = d.cv_first[c], j1 = min(j0 + d.cv_nct[c], d.cap);
       for (int j = j0 + lane; j < j1; j += 32) {
+        if (d.bc_on && d.ct_tri[j] >= 0) continue;   // k_body_rhs
         for (int r = 0; r < 3; ++r) {
           const float* Dr = d.ct_Df + 9 * j + 3 * r;
           const float jag = d.ct_omega[3 * j + r] * (Dr[0] * s0 + Dr[1] * s1 + Dr[2] * s2);
@@ -660,6 +919,30 @@ __global__ void __launch_bounds__(kYtzThreads) k_ytz(DevSim d) {
       }
     }
     __syncthreads();   // part[] is reused by the next contact vertex
+  }
+}
+
+// the Schur right-hand side of the contacts with another body, whose J A^-1 g combines
+// (Y^T z) of the vertex and the triangle's corners with the map's weights
+__global__ void k_body_rhs(DevSim d) {
+  pdl_wait();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = min(d.counters[kCntContacts], d.cap);
+  const int ncv = min(d.counters[kCntCv], d.cap);
+  if (j >= c || d.ct_tri[j] < 0 || d.yc_ptr[ncv] > d.cap_y) return;
+  const double ih2 = 1.0 / (d.h * d.h);
+  const int cv = d.ct_cv[j];
+  float s[3] = {d.svec[3 * cv], d.svec[3 * cv + 1], d.svec[3 * cv + 2]};
+  for (int k = 0; k < 3; ++k) {
+    const int t = d.ct_tcv[3 * j + k];
+    if (t < 0) continue;
+    const float w = (float)d.ct_bw[3 * j + k];
+    for (int r = 0; r < 3; ++r) s[r] -= w * d.svec[3 * t + r];
+  }
+  for (int r = 0; r < 3; ++r) {
+    const float* Dr = d.ct_Df + 9 * j + 3 * r;
+    const float jag = d.ct_omega[3 * j + r] * (Dr[0] * s[0] + Dr[1] * s[1] + Dr[2] * s[2]);
+    d.ct_rhs[3 * j + r] = (float)((d.ct_hv[3 * j + r] - (double)jag) * ih2);
   }
 }
 
@@ -765,9 +1048,16 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
   //   uall[ldw] float4 u for all contact vertices (each rank writes its own range everywhere)
   const int ldw = d.sc_ld[scene];
   const float* wblk = d.wt + d.sc_wtoff[scene];  // the scene's W~ block, row-major
+  // With contacts between bodies (a contact's map also reaches the corners of a triangle,
+  // whose contact vertices may belong to another rank) two more exchanges per product:
+  //   tall[c] float4   D_j^T (omega_j v_j) of every contact of the scene
+  //   wall[ldw] float4 (W~ u) of every contact vertex of the scene
+  const bool gen = d.bc_on != 0;
   float4* dots = reinterpret_cast<float4*>(sm);          // 16 float4
   float4* uall = dots + 16;                              // ldw float4
-  float4* uloc = uall + ldw;                             // nv_max float4 (own slice)
+  float4* tall = uall + ldw;                             // c float4 (gen)
+  float4* wall = tall + (gen ? L.c : 0);                 // ldw float4 (gen)
+  float4* uloc = wall + (gen ? ldw : 0);                 // nv_max float4 (own slice)
   float* wloc = reinterpret_cast<float*>(uloc + nv_max); // 3 nv
   float* vx = wloc + 3 * nv_max;      // per owned contact: x, r, p, Ar, Ap (3 each)
   float* vr = vx + 3 * nj_max;
@@ -780,9 +1070,12 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
   int* cvf = reinterpret_cast<int*>(ec + 3 * nj_max);   // owned cv: first local contact
   int* cvn = cvf + nv_max;                              // owned cv: contact count
   int* ctl = cvn + nv_max;                              // owned contact: local cv index
+  int* tcl = ctl + nj_max;                              // owned contact: its corners' scene
+                                                        // cv indices, -1: none (gen, 3 nj)
+  float* twl = reinterpret_cast<float*>(tcl + (gen ? 3 * nj_max : 0));   // their weights
   // the owned rows of W~ that fit (16-byte aligned, one bulk copy); the rest are read from
   // global memory
-  float* wrows = sm + ((((reinterpret_cast<float*>(ctl + nj_max)) - sm) + 3) & ~size_t(3));
+  float* wrows = sm + ((((twl + (gen ? 3 * nj_max : 0)) - sm) + 3) & ~size_t(3));
   const size_t used = (size_t)(wrows - sm) * sizeof(float);
   __shared__ __align__(8) unsigned long long wbar;
   if (used > (size_t)smem_bytes) {   // uniform: depends only on cluster-wide maxima
@@ -824,6 +1117,12 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
   }
   for (int jl = threadIdx.x; jl < nj; jl += blockDim.x)
     ctl[jl] = min(max(d.ct_cv[L.j0 + jl] - cvb - L.cv0, 0), max(nv - 1, 0));
+  if (gen)
+    for (int e = threadIdx.x; e < 3 * nj; e += blockDim.x) {
+      const int j = L.j0 + e / 3, t = d.ct_tri[j] >= 0 ? d.ct_tcv[3 * j + e % 3] : -1;
+      tcl[e] = t >= cvb && t < cvb + L.ncv ? t - cvb : -1;
+      twl[e] = t >= 0 ? (float)d.ct_bw[3 * j + e % 3] : 0.f;
+    }
   for (int e = L.ncv + threadIdx.x; e < ldw; e += blockDim.x) uall[e] = make_float4(0, 0, 0, 0);
   __syncthreads();
   const bool w_copy = rows_sm > 0;
@@ -839,11 +1138,14 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
   cl.sync();
 
   // Kv = K v for the owned contacts; v must be complete in shared memory on entry
-  auto apply = [&](const float* v, float* Kv) {
-    for (int cvl = threadIdx.x; cvl < nv; cvl += blockDim.x) {
-      float u0 = 0.f, u1 = 0.f, u2 = 0.f;
-      const int jb = cvf[cvl], je = jb + cvn[cvl];
-      for (int jl = jb; jl < je; ++jl) {
+  // u = sum over the terms at each owned contact vertex of the terms' weights times
+  // D_j^T (omega_j v_j): its own contacts (weight 1, contiguous) and, with contacts between
+  // bodies, the corner terms (-w_k, ascending contact order) read from tall
+  auto vertex_u = [&](const float* v, int cvl) {
+    float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+    const int jb0 = cvf[cvl], je0 = jb0 + cvn[cvl];
+    if (!gen) {
+      for (int jl = jb0; jl < je0; ++jl) {
         const float* D = Df + 9 * jl;
         const float a0 = om[3 * jl] * v[3 * jl], a1 = om[3 * jl + 1] * v[3 * jl + 1],
                     a2 = om[3 * jl + 2] * v[3 * jl + 2];
@@ -851,8 +1153,43 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
         u1 += D[1] * a0 + D[4] * a1 + D[7] * a2;
         u2 += D[2] * a0 + D[5] * a1 + D[8] * a2;
       }
-      uloc[cvl] = make_float4(u0, u1, u2, 0.f);
+      return make_float4(u0, u1, u2, 0.f);
     }
+    for (int jl = jb0; jl < je0; ++jl) {
+      const float4 t = tall[L.j0 - jb + jl];
+      u0 += t.x;
+      u1 += t.y;
+      u2 += t.z;
+    }
+    const int vtx = d.cv_vert[cvb + L.cv0 + cvl];
+    const int xe = min(d.x_off[vtx + 1], 3 * d.cap);
+    for (int e = d.x_off[vtx]; e < xe; ++e) {
+      const int tk = d.x_list[e], jg = tk / 3 - jb;
+      if (jg < 0 || jg >= L.c) continue;
+      const float w = (float)d.ct_bw[tk];
+      const float4 t = tall[jg];
+      u0 -= w * t.x;
+      u1 -= w * t.y;
+      u2 -= w * t.z;
+    }
+    return make_float4(u0, u1, u2, 0.f);
+  };
+  // tall <- D_j^T (omega_j v_j) of the owned contacts, in every rank
+  auto publish_t = [&](const float* v) {
+    for (int e = threadIdx.x; e < L.R * nj; e += blockDim.x) {
+      const int r = e / nj, jl = e - r * nj;
+      const float* D = Df + 9 * jl;
+      const float a0 = om[3 * jl] * v[3 * jl], a1 = om[3 * jl + 1] * v[3 * jl + 1],
+                  a2 = om[3 * jl + 2] * v[3 * jl + 2];
+      cl.map_shared_rank(tall, r)[L.j0 - jb + jl] =
+          make_float4(D[0] * a0 + D[3] * a1 + D[6] * a2, D[1] * a0 + D[4] * a1 + D[7] * a2,
+                      D[2] * a0 + D[5] * a1 + D[8] * a2, 0.f);
+    }
+    cl.sync();
+  };
+  auto apply = [&](const float* v, float* Kv) {
+    if (gen) publish_t(v);
+    for (int cvl = threadIdx.x; cvl < nv; cvl += blockDim.x) uloc[cvl] = vertex_u(v, cvl);
     __syncthreads();
     // one 16-byte remote store per (rank, owned vertex), spread over all threads
     for (int e = threadIdx.x; e < L.R * nv; e += blockDim.x) {
@@ -953,6 +1290,32 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
     }
     }
     __syncthreads();
+    if (gen) {
+      // every rank's W~ u, then the map's combination at each owned contact
+      for (int e = threadIdx.x; e < L.R * nv; e += blockDim.x) {
+        const int r = e / nv, cvl = e - r * nv;
+        cl.map_shared_rank(wall, r)[L.cv0 + cvl] =
+            make_float4(wloc[3 * cvl], wloc[3 * cvl + 1], wloc[3 * cvl + 2], 0.f);
+      }
+      cl.sync();
+      for (int e = threadIdx.x; e < 3 * nj; e += blockDim.x) {
+        const int jl = e / 3, r = e % 3;
+        const float4 w0 = wall[L.cv0 + ctl[jl]];
+        float wx = w0.x, wy = w0.y, wz = w0.z;
+        for (int k = 0; k < 3; ++k) {
+          const int t = tcl[3 * jl + k];
+          if (t < 0) continue;
+          const float c = twl[3 * jl + k];
+          const float4 q = wall[t];
+          wx -= c * q.x;
+          wy -= c * q.y;
+          wz -= c * q.z;
+        }
+        const float* D = Df + 9 * jl + 3 * r;
+        Kv[e] = om[e] * (D[0] * wx + D[1] * wy + D[2] * wz) + ec[e] * v[e];
+      }
+      return;
+    }
     for (int e = threadIdx.x; e < 3 * nj; e += blockDim.x) {
       const int jl = e / 3, r = e % 3;
       const int cvl = ctl[jl];
@@ -1040,21 +1403,13 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
   __syncthreads();
   // lambda += dlambda; u = D^T (omega * dlambda) per owned contact vertex
   for (int e = threadIdx.x; e < 3 * nj; e += blockDim.x) d.ct_lam[3 * L.j0 + e] += (double)vx[e];
+  if (gen) publish_t(vx);
   for (int cvl = threadIdx.x; cvl < nv; cvl += blockDim.x) {
     const int cv = cvb + L.cv0 + cvl;
-    float u0 = 0.f, u1 = 0.f, u2 = 0.f;
-    const int jb = cvf[cvl], je = jb + cvn[cvl];
-    for (int jl = jb; jl < je; ++jl) {
-      const float* D = Df + 9 * jl;
-      const float a0 = om[3 * jl] * vx[3 * jl], a1 = om[3 * jl + 1] * vx[3 * jl + 1],
-                  a2 = om[3 * jl + 2] * vx[3 * jl + 2];
-      u0 += D[0] * a0 + D[3] * a1 + D[6] * a2;
-      u1 += D[1] * a0 + D[4] * a1 + D[7] * a2;
-      u2 += D[2] * a0 + D[5] * a1 + D[8] * a2;
-    }
-    d.uvec[3 * cv] = u0;
-    d.uvec[3 * cv + 1] = u1;
-    d.uvec[3 * cv + 2] = u2;
+    const float4 u = vertex_u(vx, cvl);
+    d.uvec[3 * cv] = u.x;
+    d.uvec[3 * cv + 1] = u.y;
+    d.uvec[3 * cv + 2] = u.z;
   }
   // a copy that timed out may still be in flight: give it another bounded wait before the
   // shared memory is released
@@ -1070,10 +1425,16 @@ void launch_scan(const int* in, int* out, int n, const int* n_dev, int* total, c
 
 void launch_collide(const DevSim& d, cudaStream_t s) {
   const int g = (d.n + 63) / 64;
+  if (d.bc_on) k_body_box<<<d.n_bodies, kBoxThreads, 0, s>>>(d);
   k_collide_count<<<g, 64, 0, s>>>(d);
+  if (d.bc_on) {
+    k_corner_flag<<<(d.n + 255) / 256, 256, 0, s>>>(d);
+    launch_scan(d.x_cnt, d.x_off, d.n, nullptr, nullptr, s);
+  }
   launch_scan(d.ct_cnt, d.ct_off, d.n, nullptr, d.counters + kCntContacts, s);
   launch_scan(d.cv_flag, d.cv_off, d.n, nullptr, d.counters + kCntCv, s);
   k_collide_write<<<g, 64, 0, s>>>(d);
+  if (d.bc_on) k_corner_sort<<<(d.n + 255) / 256, 256, 0, s>>>(d);
 }
 
 void launch_delassus(const DevSim& d, cudaStream_t s) {
@@ -1142,6 +1503,7 @@ void launch_iter_clear(const DevSim& d, cudaStream_t s) { k_iter_clear<<<1, 256,
 
 void launch_ytz(const DevSim& d, cudaStream_t s) {
   launch_k(d.pdl, k_ytz, std::min(d.cap, 8 * d.n_sm), kYtzThreads, 0, s, d);
+  if (d.bc_on) launch_k(d.pdl, k_body_rhs, (d.cap + 127) / 128, 128, 0, s, d);
 }
 
 void launch_yu(const DevSim& d, cudaStream_t s) {

@@ -489,6 +489,16 @@ __global__ void k_rhs(DevSim d) {
 #pragma unroll
       for (int r = 0; r < 3; ++r) b[r] += h2 * d.ct_force[3 * j + r];
   }
+  if (d.bc_on) {
+    // the vertex as a corner of other bodies' contacts: -w_k of their force
+    const int xe = min(d.x_off[i + 1], 3 * d.cap);
+    for (int e = d.x_off[i]; e < xe; ++e) {
+      const int tk = d.x_list[e];
+      const double w = d.ct_bw[tk];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) b[r] -= h2 * w * d.ct_force[3 * (tk / 3) + r];
+    }
+  }
   if (d.bend_f)
 #pragma unroll
     for (int r = 0; r < 3; ++r) e[r] += d.bend_f[3 * i + r];

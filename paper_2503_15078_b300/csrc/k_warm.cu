@@ -35,8 +35,9 @@ __global__ void k_ws_features(DevSim d) {
   const double w = fmax(wt_diag(d, j), 1e-300);
   const double scale = margin / (h * h * w);
   float* f = d.ws_feat + (size_t)j * kMlpIn;
-  if (o >= d.n_obs) {
-    // an anchor: not guessed (its impulse starts at 0); no features
+  if (o < 0 || o >= d.n_obs) {
+    // an anchor or a contact with another body: not guessed (its impulse starts at 0); no
+    // features
     for (int r = 0; r < kMlpIn; ++r) f[r] = 0.f;
     d.ws_scale[j] = scale;
     return;
@@ -65,7 +66,8 @@ __global__ void k_ws_features(DevSim d) {
 // lambda_n) and the move of its vertex along the normal
 __device__ void ws_guess(const DevSim& d, int j) {
   const int v = d.ct_vert[j], sc = d.vert_scene[v];
-  if (d.ct_obst[j] >= d.n_obs) {   // anchors start from lambda = 0
+  if (d.ct_obst[j] < 0 || d.ct_obst[j] >= d.n_obs) {   // anchors and body contacts start
+                                                        // from lambda = 0
     for (int r = 0; r < 3; ++r) d.ws_lam0[3 * j + r] = 0.0;
     d.ws_move[j] = 0.0;
     return;
@@ -159,13 +161,10 @@ __global__ void __launch_bounds__(kWsThreads) k_ws_scene(DevSim d) {
   const double L = d.scene_Lref[sc];
   const double zero[3] = {0.0, 0.0, 0.0};
   for (int j = jb + threadIdx.x; j < je; j += blockDim.x) {
-    const int v = d.ct_vert[j];
     double q[3], q0[3], lam[3];
-    for (int r = 0; r < 3; ++r) {
-      q0[r] = d.q_ref[3 * v + r] + (double)d.dq[3 * v + r];
-      q[r] = q0[r] + shift[r];
-      lam[r] = d.ws_lam0[3 * j + r];
-    }
+    contact_q(d, j, nullptr, q0);
+    contact_q(d, j, shift, q);
+    for (int r = 0; r < 3; ++r) lam[r] = d.ws_lam0[3 * j + r];
     rg = fmax(rg, fb_terms(d, j, q, lam, L).res);
     rc = fmax(rc, fb_terms(d, j, q0, zero, L).res);
   }
@@ -212,7 +211,7 @@ __global__ void k_ws_record(DevSim d) {
   double mv = 0.0;
   for (int r = 0; r < 3; ++r)
     mv += D[r] * (d.q_ref[3 * v + r] + (double)d.dq[3 * v + r] - d.s_tilde[3 * v + r]);
-  if (d.cv_first[d.ct_cv[j]] == j && d.ct_obst[j] < d.n_obs) {
+  if (d.cv_first[d.ct_cv[j]] == j && d.ct_obst[j] >= 0 && d.ct_obst[j] < d.n_obs) {
     d.prev_valid[v] = 1;
     d.prev_obst[v] = d.ct_obst[j];
     d.prev_move[v] = mv;

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -155,11 +156,13 @@ int local_kernels(const sim_s* s) { return (s->d.n_tets > 0) + (s->d.n_tris > 0)
 // launches of a frame to a tolerance that made K updates (enqueue_frame_to_tolerance)
 int kernels_per_frame_to_tolerance(const sim_s* s, int K) {
   const bool c = s->has_obstacles;
+  const int bc = s->d.bc_on ? 1 : 0;   // contacts between bodies: 4 more collision launches,
+                                       // one more per constraint solve
   const int refine_body = s->d.s_bf16 && s->d.refine >= 2 && !s->d.jacobi_sweeps ? 5 : 0;
   const int refine_end = s->d.s_bf16 && s->d.refine == 1 && !s->d.jacobi_sweeps ? 6 : 0;
-  const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 : 0) + 2;
+  const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 + bc : 0) + 2;
   const int before = 1 + (s->d.bend_ptr != nullptr) +
-                     (c ? 4 + 12 + silg::ws_kernels(s->d.ws_mode) : 0) + local_kernels(s) +
+                     (c ? 4 + 12 + 4 * bc + silg::ws_kernels(s->d.ws_mode) : 0) + local_kernels(s) +
                      (c ? 1 : 0);
   const int body = 1 + global + refine_body + 1 + (c ? 1 : 0) + local_kernels(s) + 1;
   const int after = refine_end + (c ? 1 : 0) + 1 + (c && s->d.pf_copies > 1 ? 1 : 0);
@@ -170,8 +173,9 @@ int kernels_per_frame(const sim_s* s, int K) {
   const bool c = s->has_obstacles;
   // per iteration: local, [contact eval], rhs, pass 1 + reduction, [Y^T z, CR, Y u],
   // pass 2 + reduction; a residual correction adds the residual and both passes
-  const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 : 0) + 2;
-  return 1 + (s->d.bend_ptr != nullptr) + (c ? 4 + 12 : 0) +
+  const int bc = s->d.bc_on ? 1 : 0;
+  const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 + bc : 0) + 2;
+  return 1 + (s->d.bend_ptr != nullptr) + (c ? 4 + 12 + 4 * bc : 0) +
          K * (local_kernels(s) + (c ? 1 : 0) + 1 + global) + (c ? 1 : 0) + 1 +
          5 * refined_iters(s, K) + (c ? silg::ws_kernels(s->d.ws_mode) : 0) +
          (c && s->d.pf_copies > 1 ? 1 : 0);
@@ -584,7 +588,83 @@ struct SceneData {
   std::vector<int32_t> obstacle_scene;
   std::vector<double> margin, L_ref, hvel;  // hvel: 3 per scene
   std::vector<sim_anchor> anchors;          // vertex ids in the union's numbering
+  // contact between bodies (union numbering): the first body of every scene (n_scenes + 1),
+  // every body's surface triangles whose corners are all free (body_toff, n_bodies + 1;
+  // corners and the triangle's number in btri), the body of every surface vertex (-1: none,
+  // or a pinned vertex) and each scene's friction coefficient between bodies
+  std::vector<int> scene_bfirst, body_toff, vert_body;
+  std::vector<std::array<int, 4>> btri;
+  std::vector<double> bmu;
 };
+
+// The connected components of a scene's tetrahedra (numbered in order of their smallest
+// vertex id) and its surface triangles: faces of one element only, oriented so that
+// (b - a) x (c - a) points away from the element at rest, rotated to start at the smallest
+// id, in the order of their sorted vertex triples.
+void scene_surface(const sim_mesh& m, std::vector<int>& comp,
+                   std::vector<std::array<int, 3>>& tris) {
+  const int nv = m.n_verts;
+  std::vector<int> parent(nv);
+  std::iota(parent.begin(), parent.end(), 0);
+  auto root = [&](int a) {
+    while (parent[a] != a) a = parent[a] = parent[parent[a]];
+    return a;
+  };
+  for (int t = 0; t < m.n_tets; ++t) {
+    const int32_t* v = m.tets + 4 * (size_t)t;
+    int r0 = root(v[0]);
+    for (int k = 1; k < 4; ++k) {
+      const int r = root(v[k]);
+      if (r != r0) {
+        parent[std::max(r, r0)] = std::min(r, r0);
+        r0 = std::min(r, r0);
+      }
+    }
+  }
+  comp.assign(nv, -1);
+  std::vector<int> id(nv, -1);
+  int nc = 0;
+  for (int v = 0; v < nv; ++v) {
+    const int r = root(v);
+    if (id[r] < 0) id[r] = nc++;
+    comp[v] = id[r];
+  }
+  struct Face { int cnt; std::array<int, 3> f; int opp; };
+  std::map<std::array<int, 3>, Face> faces;
+  for (int t = 0; t < m.n_tets; ++t) {
+    const int32_t* v = m.tets + 4 * (size_t)t;
+    for (int k = 0; k < 4; ++k) {
+      std::array<int, 3> f;
+      int q = 0;
+      for (int i = 0; i < 4; ++i)
+        if (i != k) f[q++] = v[i];
+      std::array<int, 3> key = f;
+      std::sort(key.begin(), key.end());
+      auto it = faces.find(key);
+      if (it == faces.end()) faces.emplace(key, Face{1, f, v[k]});
+      else ++it->second.cnt;
+    }
+  }
+  tris.clear();
+  const double* X = m.rest_pos;
+  for (const auto& kv : faces) {
+    if (kv.second.cnt != 1) continue;
+    int a = kv.second.f[0], b = kv.second.f[1], c = kv.second.f[2];
+    const int dd = kv.second.opp;
+    double e1[3], e2[3], e3[3];
+    for (int r = 0; r < 3; ++r) {
+      e1[r] = X[3 * b + r] - X[3 * a + r];
+      e2[r] = X[3 * c + r] - X[3 * a + r];
+      e3[r] = X[3 * dd + r] - X[3 * a + r];
+    }
+    const double nx = e1[1] * e2[2] - e1[2] * e2[1], ny = e1[2] * e2[0] - e1[0] * e2[2],
+                 nz = e1[0] * e2[1] - e1[1] * e2[0];
+    if (nx * e3[0] + ny * e3[1] + nz * e3[2] > 0) std::swap(b, c);
+    std::array<int, 3> tr = {a, b, c};
+    const int i0 = (int)(std::min_element(tr.begin(), tr.end()) - tr.begin());
+    tris.push_back({tr[i0], tr[(i0 + 1) % 3], tr[(i0 + 2) % 3]});
+  }
+}
 
 int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   const sim_obstacle* obstacles = sd.obstacles.data();
@@ -649,6 +729,38 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
     for (int q = n_obs - 1; q >= 0; --q) of[sd.obstacle_scene[q]] = q;
     for (int sc = p.n_scenes - 1; sc >= 0; --sc) of[sc] = std::min(of[sc], of[sc + 1]);
     d.scene_ofirst = s->upload(of);
+  }
+  {
+    // contact between bodies: per free vertex its body; per body its triangles (internal
+    // corner ids, the triangle's number in w)
+    const int nb = (int)sd.body_toff.size() - 1;
+    d.n_bodies = nb;
+    d.bc_on = nb > 0;
+    if (d.bc_on) {
+      std::vector<int> vb(std::max(1, n), -1);
+      for (int v = 0; v < n_all; ++v)
+        if (p.internal[v] < n) vb[p.internal[v]] = sd.vert_body[v];
+      d.vert_body = s->upload(vb);
+      std::vector<int4> bt(std::max<size_t>(1, sd.btri.size()));
+      for (size_t t = 0; t < sd.btri.size(); ++t)
+        bt[t] = make_int4(p.internal[sd.btri[t][0]], p.internal[sd.btri[t][1]],
+                          p.internal[sd.btri[t][2]], sd.btri[t][3]);
+      d.btri = s->upload(bt);
+      d.body_toff = s->upload(sd.body_toff);
+      d.scene_bfirst = s->upload(sd.scene_bfirst);
+      d.scene_bmu = s->upload(sd.bmu);
+      d.body_box = s->alloc<double>(6 * (size_t)nb);
+      d.bc_tri = s->alloc<int>(n);
+      d.bc_w = s->alloc<double>(3 * (size_t)n);
+      d.bc_n = s->alloc<double>(3 * (size_t)n);
+      d.x_cnt = s->alloc<int>(n);
+      d.x_fill = s->alloc<int>(n);
+      d.x_off = s->alloc<int>(n + 1);
+      d.x_list = s->alloc<int>(3 * (size_t)d.cap);
+      d.ct_tri = s->alloc<int>(d.cap);
+      d.ct_bw = s->alloc<double>(3 * (size_t)d.cap);
+      d.ct_tcv = s->alloc<int>(3 * (size_t)d.cap);
+    }
   }
   d.scene_margin = s->upload(sd.margin);
   d.scene_Lref = s->upload(sd.L_ref);
@@ -888,7 +1000,7 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   d.iter_k = s->alloc<int>(1);
   d.err = s->alloc<int>(1);
   d.p_out = s->alloc<float>(9 * (size_t)T);
-  s->has_obstacles = n_obs > 0 || !sd.anchors.empty();
+  s->has_obstacles = n_obs > 0 || !sd.anchors.empty() || d.bc_on;
   d.wt_grid = 4 * d.n_sm;
   d.spin_limit = o->spin_limit;
   d.kb_lo = s->alloc<int>(n / 32 + 1);
@@ -1050,7 +1162,11 @@ int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_opt
         (sc.mesh.n_tets > 0 && !sc.mesh.tets) || (sc.mesh.n_tris > 0 && !sc.mesh.tris) ||
         (sc.mesh.n_tris > 0 && o->local_solver == SIM_LOCAL_ADMM) ||
         // the Jacobi comparison solves the contact-free system only
-        (o->global_solver == SIM_GLOBAL_JACOBI && (sc.n_obstacles > 0 || sc.n_anchors > 0)) ||
+        (o->global_solver == SIM_GLOBAL_JACOBI &&
+         (sc.n_obstacles > 0 || sc.n_anchors > 0 || sc.body_contact)) ||
+        (sc.body_contact != 0 && sc.body_contact != 1) ||
+        (sc.body_contact && !(std::isfinite(sc.body_mu) && sc.body_mu >= 0.0)) ||
+        (sc.body_contact && sc.mesh.n_tets <= 0) ||
         !sc.materials || sc.n_materials <= 0 || sc.n_obstacles < 0 ||
         (sc.n_obstacles > 0 && !sc.obstacles) || sc.mesh.n_pinned < 0 ||
         (sc.mesh.n_pinned > 0 && !sc.mesh.pinned))
@@ -1075,7 +1191,7 @@ int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_opt
     SceneData sd;
     X.reserve(3 * nv_tot);
     tets.reserve(4 * nt_tot);
-    int voff = 0;
+    int voff = 0, btri_base = 0;
     for (int k = 0; k < n_scenes; ++k) {
       const sim_scene& sc = scenes[k];
       const sim_mesh& m = sc.mesh;
@@ -1121,6 +1237,40 @@ int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_opt
           used[a.vertex] = 2;
           a.vertex += voff;
           sd.anchors.push_back(a);
+        }
+      }
+      {
+        // contact between the scene's bodies: components, surface, per-body triangle lists
+        const int nb0 = (int)sd.body_toff.size();
+        sd.scene_bfirst.push_back(nb0);
+        sd.bmu.push_back(sc.body_contact ? sc.body_mu : 0.0);
+        sd.vert_body.insert(sd.vert_body.end(), m.n_verts, -1);
+        if (sc.body_contact) {
+          for (size_t e = 0; e < 4 * (size_t)m.n_tets; ++e)
+            if (m.tets[e] < 0 || m.tets[e] >= m.n_verts) return SIM_EINVAL;
+          std::vector<int> comp;
+          std::vector<std::array<int, 3>> st;
+          scene_surface(m, comp, st);
+          std::vector<char> pin(m.n_verts, 0);
+          for (int q = 0; q < m.n_pinned; ++q)
+            if (m.pinned[q] >= 0 && m.pinned[q] < m.n_verts) pin[m.pinned[q]] = 1;
+          const int ncomp = m.n_verts > 0 ? *std::max_element(comp.begin(), comp.end()) + 1 : 0;
+          std::vector<std::vector<std::array<int, 4>>> per(ncomp);
+          for (size_t t = 0; t < st.size(); ++t) {
+            bool free = true;
+            for (int v : st[t]) {
+              if (!pin[v]) sd.vert_body[voff + v] = nb0 + comp[v];
+              free = free && !pin[v];
+            }
+            if (free)
+              per[comp[st[t][0]]].push_back(
+                  {st[t][0] + voff, st[t][1] + voff, st[t][2] + voff, btri_base + (int)t});
+          }
+          for (int b = 0; b < ncomp; ++b) {
+            sd.body_toff.push_back((int)sd.btri.size());
+            sd.btri.insert(sd.btri.end(), per[b].begin(), per[b].end());
+          }
+          btri_base += (int)st.size();
         }
       }
       const double me = mean_edge(m);
@@ -1173,6 +1323,8 @@ int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_opt
           mix(ob.vel, sizeof(ob.vel));
         }
         mix(&sd.margin.back(), sizeof(double));
+        mix(&sc.body_contact, sizeof(sc.body_contact));
+        if (sc.body_contact) mix(&sc.body_mu, sizeof(double));
         for (int q = 0; q < sc.n_anchors; ++q) {
           const sim_anchor& a = sc.anchors[q];
           mix(&a.vertex, sizeof(a.vertex));
@@ -1185,6 +1337,8 @@ int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_opt
       voff += m.n_verts;
     }
     if (sd.obstacle_scene.empty()) sd.obstacle_scene.push_back(0);
+    sd.scene_bfirst.push_back((int)sd.body_toff.size());
+    sd.body_toff.push_back((int)sd.btri.size());
     sim_mesh um{};
     um.n_verts = (int32_t)nv_tot;
     um.n_tets = (int32_t)nt_tot;
@@ -1336,7 +1490,7 @@ int sim_get_warmstart_samples(sim_t* s, int32_t capacity, float* X, float* T, in
   std::vector<int> obst(std::max(1, c));
   if (c > 0) cudaMemcpy(obst.data(), s->d.ct_obst, sizeof(int) * c, cudaMemcpyDeviceToHost);
   int ns = 0;
-  for (int j = 0; j < c; ++j) ns += obst[j] < s->d.n_obs;
+  for (int j = 0; j < c; ++j) ns += obst[j] >= 0 && obst[j] < s->d.n_obs;
   *n_out = ns;
   if (ns == 0 || capacity < ns) return st;
   std::vector<float> f((size_t)c * silg::kMlpIn), t(4 * (size_t)c);
@@ -1345,7 +1499,7 @@ int sim_get_warmstart_samples(sim_t* s, int32_t capacity, float* X, float* T, in
   if (e != cudaSuccess) return cuda_status(e);
   int row = 0;
   for (int j = 0; j < c; ++j) {
-    if (obst[j] >= s->d.n_obs) continue;
+    if (obst[j] < 0 || obst[j] >= s->d.n_obs) continue;
     if (X)
       for (int q = 0; q < silg::kMlpNF; ++q) X[(size_t)row * silg::kMlpNF + q] = f[(size_t)j * silg::kMlpIn + q];
     if (T)
@@ -1551,6 +1705,9 @@ int sim_get_contacts(sim_t* s, int32_t capacity, int32_t* vertex, int32_t* obsta
   std::vector<double> cl(3 * (size_t)c), cD(9 * (size_t)c);
   cudaMemcpy(cv.data(), s->d.ct_vert, sizeof(int) * c, cudaMemcpyDeviceToHost);
   cudaMemcpy(co.data(), s->d.ct_obst, sizeof(int) * c, cudaMemcpyDeviceToHost);
+  // a contact with another body: its id follows the obstacles' and the anchors'
+  for (int& o : co)
+    if (o < 0) o = s->d.n_obs + s->d.n_anc + (-1 - o);
   cudaMemcpy(cl.data(), s->d.ct_lam, sizeof(double) * 3 * c, cudaMemcpyDeviceToHost);
   cudaMemcpy(cD.data(), s->d.ct_D, sizeof(double) * 9 * c, cudaMemcpyDeviceToHost);
   std::vector<int> perm(c);

@@ -196,3 +196,16 @@ def test_jacobi_global_step_needs_a_scene_without_contact():
     with pytest.raises(SimError) as e:
         Simulator(sg.twisting_bar(nxy=3, nz=4), global_solver="jacobi", jacobi_sweeps=0)
     assert e.value.status == -1
+
+
+def test_body_contact_options_are_checked():
+    sc = sg.box_stack(n_boxes=2, m=3)
+    for field, bad in (("body_mu", -0.1), ("body_mu", float("nan"))):
+        s2 = sg.box_stack(n_boxes=2, m=3)
+        setattr(s2, field, bad)
+        with pytest.raises(SimError) as e:
+            Simulator(s2)
+        assert e.value.status == -1
+    with pytest.raises(SimError) as e:
+        Simulator(sc, global_solver="jacobi")
+    assert e.value.status == -1
