@@ -59,9 +59,10 @@ def parse():
                     help="skip the timing of the paper's variants on the star frame")
     ap.add_argument("--no-warmstart", action="store_true",
                     help="skip the learned-vs-plain frame time to residual 1e-4")
-    ap.add_argument("--workload", choices=["star", "batch64"], default="star",
+    ap.add_argument("--workload", choices=["star", "batch64", "stack"], default="star",
                     help="star: the 57k-DoF pulled star (the headline); batch64: 64 uneven "
-                         "cubes on tilted planes in one simulator")
+                         "cubes on tilted planes in one simulator; stack: the stress case, "
+                         "8 x 32 stiff boxes of 12^3 vertices with box-box contacts")
     ap.add_argument("--autotune", type=int, default=1,
                     help="1: let the library time the products' launch configurations")
     ap.add_argument("--refine", type=int, default=1,
@@ -466,8 +467,14 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    batch = args.workload == "batch64"
-    if batch:
+    batch = args.workload in ("batch64", "stack")
+    stack = args.workload == "stack"
+    if stack:
+        scenes = sg.stack_stress(seed=rank)
+        scene = scenes[0]
+        q0 = np.concatenate([sc.q0 for sc in scenes])
+        v0 = np.zeros_like(q0)
+    elif batch:
         scenes = sg.batch(n_scenes=64, seed=rank)
         scene = scenes[0]
         if args.s_precision == "fp32" and "--s-precision" not in sys.argv:
@@ -479,7 +486,7 @@ def run_ours(args):
     bf16 = args.s_precision == "bf16"
     sim = Simulator(scenes if batch else scene, s_precision=1 if bf16 else 0,
                     refine=args.refine, autotune=args.autotune,
-                    contact_capacity=16384 if batch else 4096)
+                    contact_capacity=65536 if stack else (16384 if batch else 4096))
     n_iters = scene.n_iters
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -577,6 +584,13 @@ def run_ours(args):
         "data": "synthetic",
         "config": {
             "workload": (
+                "stack: the stress case, 8 copies x 32 stiff boxes of 12^3 vertices (SNH, "
+                "E=1e8, nu=0.45), 16 columns of 2 boxes per copy, each column a scene "
+                "(128 scenes), mu=0.8 on a 20 deg incline and between the boxes, boxes "
+                "pressed 1/20 lattice spacing into each other and the plane (box-box "
+                "contacts: vertex against the other box's surface triangles), FP32, "
+                "cold start, 10 L-G + 10 CR iterations per frame"
+                if stack else
                 "batch64: 64 cubes of 8^3..20^3 vertices (seeded), ARAP/co-rot vs SNH, E "
                 "log-uniform 1e4..1e7, nu 0.3..0.48, planes tilted 0..30 deg, mu 0.1..0.8, "
                 "each placed a quarter lattice spacing into its plane; one simulator, "

@@ -231,6 +231,9 @@ struct DevSim {
   const int* scene_bfirst; // n_scenes + 1
   const double* scene_bmu; // n_scenes: friction coefficient between bodies
   double* body_box;        // 6 per body: bounds of its triangles' corners at s~
+  int n_btri;
+  float* chunk_box;        // 6 per run of kTriChunk consecutive triangles: their bounds
+  float* tri_box;          // 6 per triangle: its bounds (both rounded outward to FP32)
   int* bc_tri;             // n: the vertex's matched triangle (index into btri) or -1
   double* bc_w;            // 3 n: barycentric weights of the closest point
   double* bc_n;            // 3 n: contact normal
@@ -313,6 +316,7 @@ void launch_delassus(const DevSim& d, cudaStream_t s);
 // wt_items_max(cap, grid) items
 constexpr int kWtMaxSplit = 16;
 constexpr int kCrMaxRanks = 16;
+constexpr int kTriChunk = 16;   // surface triangles per bounding box of the body search
 constexpr int kMaxStagedCols = 32;  // column tiles of g staged per pass-1 CTA (96 KB)
 inline long long wt_items_max(int cap, int grid) {
   long long best = 0;

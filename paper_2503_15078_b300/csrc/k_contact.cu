@@ -184,6 +184,42 @@ __global__ void __launch_bounds__(kBoxThreads) k_body_box(DevSim d) {
   if (threadIdx.x < 6) d.body_box[6 * b + threadIdx.x] = red[threadIdx.x][0];
 }
 
+// bounds of every triangle and of every run of kTriChunk consecutive triangles, in FP32
+// rounded outward (runs may straddle two bodies: the bounds then cover both parts, still a
+// bound for either). One warp per run, a lane per triangle.
+__global__ void k_chunk_box(DevSim d) {
+  const int lane = threadIdx.x & 31;
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int t = c * kTriChunk + lane;
+  const bool own = lane < kTriChunk && t < d.n_btri;
+  float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
+  if (own) {
+    const int4 tv = d.btri[t];
+    const int cs[3] = {tv.x, tv.y, tv.z};
+    for (int k = 0; k < 3; ++k)
+      for (int r = 0; r < 3; ++r) {
+        const double v = d.s_tilde[3 * cs[k] + r];
+        lo[r] = fminf(lo[r], __double2float_rd(v));
+        hi[r] = fmaxf(hi[r], __double2float_ru(v));
+      }
+    for (int r = 0; r < 3; ++r) {
+      d.tri_box[6 * t + r] = lo[r];
+      d.tri_box[6 * t + 3 + r] = hi[r];
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1)
+    for (int r = 0; r < 3; ++r) {
+      lo[r] = fminf(lo[r], __shfl_xor_sync(0xffffffffu, lo[r], o));
+      hi[r] = fmaxf(hi[r], __shfl_xor_sync(0xffffffffu, hi[r], o));
+    }
+  if (lane < 6 && c * kTriChunk < d.n_btri) d.chunk_box[6 * c + lane] = lane < 3 ? lo[lane] : hi[lane - 3];
+}
+
+__device__ __forceinline__ bool far_from(const float* box, const float* x, float lim) {
+  return x[0] < box[0] - lim || x[1] < box[1] - lim || x[2] < box[2] - lim ||
+         x[0] > box[3] + lim || x[1] > box[4] + lim || x[2] > box[5] + lim;
+}
+
 // The body contact of free vertex i, if any (bc_tri, bc_w, bc_n): the nearest surface
 // triangle of another body of its scene (distance to the closest point, then the
 // triangle's number), accepted when its gap g lies in (-2 margin, margin). Only triangles
@@ -194,27 +230,35 @@ __device__ bool body_match(const DevSim& d, int i, const double* x, double margi
   d.bc_tri[i] = -1;
   if (vb < 0) return false;
   const int sc = d.vert_scene[i];
-  const double lim = 2.0 * margin * (1.0 + 1e-6) + 1e-12 * (fabs(x[0]) + fabs(x[1]) + fabs(x[2]));
+  // the culling runs in FP32 on bounds rounded outward, with the limit padded by a relative
+  // 1e-5 (far above FP32 rounding of x and of the subtraction): it only ever keeps more
+  const double ax = fabs(x[0]) + fabs(x[1]) + fabs(x[2]);
+  const float lim = __double2float_ru(2.0 * margin * (1.0 + 1e-5) + 1e-5 * ax);
+  const float xf[3] = {(float)x[0], (float)x[1], (float)x[2]};
   double best_d = 1e300, bw[3] = {0.0, 0.0, 0.0};
   int best = -1, best_id = 0;
   bool best_in = false;
   for (int b = d.scene_bfirst[sc]; b < d.scene_bfirst[sc + 1]; ++b) {
     if (b == vb) continue;
     const double* bx = d.body_box + 6 * b;
-    if (x[0] < bx[0] - lim || x[1] < bx[1] - lim || x[2] < bx[2] - lim || x[0] > bx[3] + lim ||
-        x[1] > bx[4] + lim || x[2] > bx[5] + lim)
-      continue;
-    for (int t = d.body_toff[b]; t < d.body_toff[b + 1]; ++t) {
+    const float bxf[6] = {__double2float_rd(bx[0]), __double2float_rd(bx[1]),
+                          __double2float_rd(bx[2]), __double2float_ru(bx[3]),
+                          __double2float_ru(bx[4]), __double2float_ru(bx[5])};
+    if (far_from(bxf, xf, lim)) continue;
+    const int te = d.body_toff[b + 1];
+    for (int t = d.body_toff[b]; t < te; ++t) {
+      // skip the rest of a run of triangles whose bounds are farther than the limit
+      if ((t == d.body_toff[b] || t % kTriChunk == 0) &&
+          far_from(d.chunk_box + 6 * (t / kTriChunk), xf, lim)) {
+        t = min(te, (t / kTriChunk + 1) * kTriChunk) - 1;
+        continue;
+      }
+      if (far_from(d.tri_box + 6 * t, xf, lim)) continue;
       const int4 tv = d.btri[t];
       double a[3], bb[3], c[3];
       load3(d.s_tilde, tv.x, a);
       load3(d.s_tilde, tv.y, bb);
       load3(d.s_tilde, tv.z, c);
-      bool far = false;
-      for (int r = 0; r < 3; ++r)
-        far = far || x[r] < fmin(a[r], fmin(bb[r], c[r])) - lim ||
-              x[r] > fmax(a[r], fmax(bb[r], c[r])) + lim;
-      if (far) continue;
       double w[3];
       const bool in = tri_closest(x, a, bb, c, w);
       double e[3];
@@ -1425,7 +1469,10 @@ void launch_scan(const int* in, int* out, int n, const int* n_dev, int* total, c
 
 void launch_collide(const DevSim& d, cudaStream_t s) {
   const int g = (d.n + 63) / 64;
-  if (d.bc_on) k_body_box<<<d.n_bodies, kBoxThreads, 0, s>>>(d);
+  if (d.bc_on) {
+    k_body_box<<<d.n_bodies, kBoxThreads, 0, s>>>(d);
+    k_chunk_box<<<((d.n_btri / kTriChunk + 1) * 32 + 127) / 128, 128, 0, s>>>(d);
+  }
   k_collide_count<<<g, 64, 0, s>>>(d);
   if (d.bc_on) {
     k_corner_flag<<<(d.n + 255) / 256, 256, 0, s>>>(d);

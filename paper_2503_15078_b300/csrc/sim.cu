@@ -156,13 +156,13 @@ int local_kernels(const sim_s* s) { return (s->d.n_tets > 0) + (s->d.n_tris > 0)
 // launches of a frame to a tolerance that made K updates (enqueue_frame_to_tolerance)
 int kernels_per_frame_to_tolerance(const sim_s* s, int K) {
   const bool c = s->has_obstacles;
-  const int bc = s->d.bc_on ? 1 : 0;   // contacts between bodies: 4 more collision launches,
+  const int bc = s->d.bc_on ? 1 : 0;   // contacts between bodies: 5 more collision launches,
                                        // one more per constraint solve
   const int refine_body = s->d.s_bf16 && s->d.refine >= 2 && !s->d.jacobi_sweeps ? 5 : 0;
   const int refine_end = s->d.s_bf16 && s->d.refine == 1 && !s->d.jacobi_sweeps ? 6 : 0;
   const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 + bc : 0) + 2;
   const int before = 1 + (s->d.bend_ptr != nullptr) +
-                     (c ? 4 + 12 + 4 * bc + silg::ws_kernels(s->d.ws_mode) : 0) + local_kernels(s) +
+                     (c ? 4 + 12 + 5 * bc + silg::ws_kernels(s->d.ws_mode) : 0) + local_kernels(s) +
                      (c ? 1 : 0);
   const int body = 1 + global + refine_body + 1 + (c ? 1 : 0) + local_kernels(s) + 1;
   const int after = refine_end + (c ? 1 : 0) + 1 + (c && s->d.pf_copies > 1 ? 1 : 0);
@@ -175,7 +175,7 @@ int kernels_per_frame(const sim_s* s, int K) {
   // pass 2 + reduction; a residual correction adds the residual and both passes
   const int bc = s->d.bc_on ? 1 : 0;
   const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 + bc : 0) + 2;
-  return 1 + (s->d.bend_ptr != nullptr) + (c ? 4 + 12 + 4 * bc : 0) +
+  return 1 + (s->d.bend_ptr != nullptr) + (c ? 4 + 12 + 5 * bc : 0) +
          K * (local_kernels(s) + (c ? 1 : 0) + 1 + global) + (c ? 1 : 0) + 1 +
          5 * refined_iters(s, K) + (c ? silg::ws_kernels(s->d.ws_mode) : 0) +
          (c && s->d.pf_copies > 1 ? 1 : 0);
@@ -750,6 +750,9 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
       d.scene_bfirst = s->upload(sd.scene_bfirst);
       d.scene_bmu = s->upload(sd.bmu);
       d.body_box = s->alloc<double>(6 * (size_t)nb);
+      d.n_btri = (int)sd.btri.size();
+      d.chunk_box = s->alloc<float>(6 * (size_t)(d.n_btri / silg::kTriChunk + 1));
+      d.tri_box = s->alloc<float>(6 * (size_t)std::max(1, d.n_btri));
       d.bc_tri = s->alloc<int>(n);
       d.bc_w = s->alloc<double>(3 * (size_t)n);
       d.bc_n = s->alloc<double>(3 * (size_t)n);

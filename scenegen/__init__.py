@@ -406,6 +406,20 @@ def box_stack(n_boxes: int = 3, m: int = 4, edge: float = 0.1, model: int = MODE
                  n_iters=n_iters, spacing=sp, body_contact=True, body_mu=mu)
 
 
+def stack_stress(copies: int = 8, columns: int = 16, boxes: int = 2, m: int = 12,
+                 seed: int = 0) -> List[Scene]:
+    """The stress case: copies x (columns x boxes) stiff boxes (SNH, E = 1e8, nu = 0.45) of
+    m^3 vertices, mu = 0.8 on a 20 degree incline and between the boxes, 10 local-global
+    iterations per frame. Each column of ``boxes`` boxes is a scene of its own (the
+    columns stand apart, so they share no contact), with a seeded lateral offset of its
+    boxes; the boxes start a twentieth of a lattice spacing into each other and into the
+    plane, so that every frame has box-box and box-ground contacts. With the defaults:
+    8 x 32 boxes of 12^3 vertices, 128 scenes."""
+    return [box_stack(n_boxes=boxes, m=m, model=MODEL_SNH, E=1e8, nu=0.45, mu=0.8,
+                      incline_deg=20.0, gap=-0.05, seed=seed * 100003 + k, n_iters=10)
+            for k in range(copies * columns)]
+
+
 def hanging_cube(m: int = 5, edge: float = 0.1, model: int = MODEL_ARAP, E: float = 1e5,
                  nu: float = 0.4, rho: float = 1000.0, compliance: float = 0.0,
                  target_vel=(0.0, 0.0, 0.0), h: float = 1.0 / 60.0, floor: bool = False,
