@@ -1292,9 +1292,47 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
           wloc[3 * row + lane] = lane == 3 ? a[1][0] : (lane == 4 ? a[1][1] : a[1][2]);
       }
       };
+      // rows read from global memory (L2): four per warp at a time, twice the loads in
+      // flight of the two-row loop (the rows that did not fit in shared memory)
+      auto rows4 = [&](int r_begin, int r_end) {
+      for (int row = r_begin + 4 * warp; row < r_end; row += 4 * nw) {
+        const int nr = min(4, r_end - row);
+        const float* w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          w[k] = wblk + (size_t)(L.cv0 + min(row + k, r_end - 1)) * ldw;
+        float a[4][3] = {};
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const int col = lane + 32 * m;
+          if (col < ldw) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const float p = w[k][col];
+              a[k][0] += p * ux[m];
+              a[k][1] += p * uy[m];
+              a[k][2] += p * uz[m];
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) a[k][c] = warp_sum(a[k][c]);
+        if (lane < 3 * nr) {
+          float val = 0.f;
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              if (lane == 3 * k + c) val = a[k][c];
+          wloc[3 * row + lane] = val;
+        }
+      }
+      };
       const int n_sm_rows = min(rows_sm, nv);
       rows(0, n_sm_rows, [&](int r) { return wrows + (size_t)r * ldw; });
-      rows(n_sm_rows, nv, [&](int r) { return wblk + (size_t)(L.cv0 + r) * ldw; });
+      rows4(n_sm_rows, nv);
     } else {
     // four rows per warp at a time, so the shuffle reductions of the rows overlap
     for (int row0 = 4 * warp; row0 < nv; row0 += 4 * nw) {

@@ -145,3 +145,29 @@ def test_stack_on_an_incline_sticks_or_slides(mu_ground, moving):
     # no box sinks into another or the plane by more than the margin
     assert sim.stats()["max_penetration"] < sc.contact_margin
     sim.close()
+
+
+def test_stress_columns_in_a_full_batch_match_the_oracle():
+    # the stress workload's 128 two-box columns of 12^3 vertices in one simulator (one
+    # cluster of one CTA per scene, most W~ rows read from L2): its first scene against the
+    # oracle, within 10x of the oracle's own float32-CR deviation (measured: 4.2e-5 against
+    # 2.1e-5)
+    scenes = sg.stack_stress()
+    q0 = np.concatenate([sc.q0 for sc in scenes])
+    sim = Simulator(scenes, contact_capacity=65536)
+    sim.set_state(q0, np.zeros_like(q0))
+    sim.step()
+    qg, _ = sim.state()
+    off = sim.scene_offsets
+    for k in (0,):
+        sc = scenes[k]
+        o = Oracle(sc)
+        v0 = np.zeros_like(sc.q0)
+        opts = OracleOptions(n_iters=sc.n_iters, n_cr=sc.n_cr)
+        q, _, info = o.frame(sc.q0, v0, opts)
+        dev32 = _relerr(_cr32_deviation(o, sc, sc.q0, v0, opts) - sc.q0, q - sc.q0)
+        err = _relerr(qg[off[k]:off[k + 1]] - sc.q0, q - sc.q0)
+        print(f"scene {k}: {len(info['contacts'])} contacts, error {err:.2e}, float32 "
+              f"deviation {dev32:.2e}")
+        assert err < 10 * dev32 + 1e-4
+    sim.close()
