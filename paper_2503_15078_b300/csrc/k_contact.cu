@@ -409,6 +409,17 @@ __global__ void k_collide_write(DevSim d) {
   }
   if (a >= 0) ++j;
   const int t = d.bc_on ? d.bc_tri[i] : -1;
+  if (t >= 0 && j >= d.cap) {
+    // beyond the capacity (the frame reports SIM_ECAPACITY): its counted corner terms are
+    // filled with -1, which every reader skips
+    for (int k = 0; k < 3; ++k) {
+      if (d.bc_w[3 * i + k] == 0.0) continue;
+      const int4 tv = d.btri[t];
+      const int ck = k == 0 ? tv.x : (k == 1 ? tv.y : tv.z);
+      const int pos = d.x_off[ck] + atomicAdd(d.x_fill + ck, 1);
+      if (pos < 3 * d.cap) d.x_list[pos] = -1;
+    }
+  }
   if (t >= 0 && j < d.cap) {
     // the contact with another body: rows (n, f1, f2), the map x_i - sum_k w_k x_k, d = 0;
     // the id -1 - the triangle's number; each corner with a non-zero weight gets a term
@@ -442,13 +453,14 @@ __global__ void k_collide_write(DevSim d) {
   }
 }
 
-// single-CTA exclusive scan: out[k] = sum in[0..k), out[len] = total; *total = total.
+// single-CTA exclusive scan: out[k] = sum in[0..k), out[len] = total; *total = total. The
+// length is n_static, or the device count *n_dev capped at n_static (the arrays' size).
 // The array is walked in coalesced tiles of 4 x blockDim elements (each thread scans four
 // consecutive values), with the running total carried from tile to tile.
 __global__ void __launch_bounds__(1024) k_scan(const int* in, int* out, int n_static,
                                                const int* n_dev, int* total) {
   __shared__ int wsum[32];
-  int n = n_dev ? *n_dev : n_static;
+  int n = n_dev ? min(*n_dev, n_static) : n_static;
   if (n < 0) n = 0;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   const int tile = 4 * blockDim.x;
@@ -976,6 +988,7 @@ __global__ void k_body_rhs(DevSim d) {
   if (j >= c || d.ct_tri[j] < 0 || d.yc_ptr[ncv] > d.cap_y) return;
   const double ih2 = 1.0 / (d.h * d.h);
   const int cv = d.ct_cv[j];
+  if (cv >= ncv) return;   // beyond the capacity: the frame reports SIM_ECAPACITY
   float s[3] = {d.svec[3 * cv], d.svec[3 * cv + 1], d.svec[3 * cv + 2]};
   for (int k = 0; k < 3; ++k) {
     const int t = d.ct_tcv[3 * j + k];
@@ -1209,7 +1222,7 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
     const int xe = min(d.x_off[vtx + 1], 3 * d.cap);
     for (int e = d.x_off[vtx]; e < xe; ++e) {
       const int tk = d.x_list[e], jg = tk / 3 - jb;
-      if (jg < 0 || jg >= L.c) continue;
+      if (tk < 0 || jg < 0 || jg >= L.c) continue;
       const float w = (float)d.ct_bw[tk];
       const float4 t = tall[jg];
       u0 -= w * t.x;
@@ -1527,9 +1540,9 @@ void launch_delassus(const DevSim& d, cudaStream_t s) {
   k_u_flag<<<g, 256, 0, s>>>(d);
   launch_scan(d.u_flag, d.u_off, d.n, nullptr, d.counters + kCntU, s);
   k_u_compact<<<g, 256, 0, s>>>(d);
-  launch_scan(d.u_len, d.y_ptr, 0, d.counters + kCntU, d.counters + kCntY, s);
+  launch_scan(d.u_len, d.y_ptr, d.n, d.counters + kCntU, d.counters + kCntY, s);
   k_yc_len<<<(d.cap + 255) / 256, 256, 0, s>>>(d);
-  launch_scan(d.yc_len, d.yc_ptr, 0, d.counters + kCntCv, d.counters + kCntYC, s);
+  launch_scan(d.yc_len, d.yc_ptr, d.cap, d.counters + kCntCv, d.counters + kCntYC, s);
   k_y_gather<<<std::min((d.n * 32 + 255) / 256, 8 * d.n_sm), 256, 0, s>>>(d);
   k_scene_ranges<<<1, 256, 0, s>>>(d);
   k_wt_blocks<<<(d.n / kWtKB + 1 + 127) / 128, 128, 0, s>>>(d);

@@ -494,6 +494,7 @@ __global__ void k_rhs(DevSim d) {
     const int xe = min(d.x_off[i + 1], 3 * d.cap);
     for (int e = d.x_off[i]; e < xe; ++e) {
       const int tk = d.x_list[e];
+      if (tk < 0) continue;   // a contact beyond the capacity
       const double w = d.ct_bw[tk];
 #pragma unroll
       for (int r = 0; r < 3; ++r) b[r] -= h2 * w * d.ct_force[3 * (tk / 3) + r];

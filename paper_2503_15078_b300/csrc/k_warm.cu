@@ -21,6 +21,8 @@ namespace {
 
 __device__ __forceinline__ double wt_diag(const DevSim& d, int j) {
   const int cv = d.ct_cv[j];
+  // a contact vertex beyond the capacity (the frame reports SIM_ECAPACITY) has no row
+  if (cv >= min(d.counters[kCntCv], d.cap)) return 0.0;
   const int sc = d.vert_scene[d.ct_vert[j]], l = cv - d.sc_cvb[sc];
   return (double)d.wt[d.sc_wtoff[sc] + (size_t)l * d.sc_ld[sc] + l];
 }
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(kWsThreads) k_ws_scene(DevSim d) {
     const double* D = d.ct_D + 9 * j;
     const double* l = d.ws_lam0 + 3 * j;
     for (int r = 0; r < 3; ++r) t[r] += D[r] * l[0] + D[3 + r] * l[1] + D[6 + r] * l[2];
-    if (d.cv_first[d.ct_cv[j]] == j)
+    if (d.ct_cv[j] < d.cap && d.cv_first[d.ct_cv[j]] == j)
       for (int r = 0; r < 3; ++r) t[3 + r] += d.ws_move[j] * D[r];
   }
   for (int r = 0; r < 6; ++r) part[r][threadIdx.x] = t[r];
@@ -211,7 +213,8 @@ __global__ void k_ws_record(DevSim d) {
   double mv = 0.0;
   for (int r = 0; r < 3; ++r)
     mv += D[r] * (d.q_ref[3 * v + r] + (double)d.dq[3 * v + r] - d.s_tilde[3 * v + r]);
-  if (d.cv_first[d.ct_cv[j]] == j && d.ct_obst[j] >= 0 && d.ct_obst[j] < d.n_obs) {
+  if (d.ct_cv[j] < d.cap && d.cv_first[d.ct_cv[j]] == j && d.ct_obst[j] >= 0 &&
+      d.ct_obst[j] < d.n_obs) {
     d.prev_valid[v] = 1;
     d.prev_obst[v] = d.ct_obst[j];
     d.prev_move[v] = mv;

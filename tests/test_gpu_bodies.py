@@ -171,3 +171,43 @@ def test_stress_columns_in_a_full_batch_match_the_oracle():
               f"deviation {dev32:.2e}")
         assert err < 10 * dev32 + 1e-4
     sim.close()
+
+
+def test_apart_bodies_give_the_frame_without_body_contact():
+    # boxes two edges apart have no body contacts: the frame equals the same scene
+    # simulated without body contact (the ground contacts only)
+    sc = sg.box_stack(n_boxes=2, m=4, gap=8.0, seed=4, E=1e6)
+    sc.q0 = sc.X.copy()
+    plain = sg.box_stack(n_boxes=2, m=4, gap=8.0, seed=4, E=1e6)
+    plain.body_contact = False
+    a, b = Simulator(sc), Simulator([plain])
+    for s in (a, b):
+        s.set_state(sc.q0, np.zeros_like(sc.q0))
+        s.step(n_frames=3)
+    ca = a.contacts()
+    assert np.all(ca["obstacle"] < 1)    # ground contacts at most (obstacle 0)
+    assert _relerr(a.state()[0] - sc.q0, b.state()[0] - sc.q0) < 1e-5
+    a.close()
+    b.close()
+
+
+def test_contact_vertex_capacity_overflow_is_reported():
+    # triangle corners add contact vertices beyond the contacts themselves: a capacity that
+    # holds the contacts but not the contact vertices must be reported, not overrun
+    from paper_2503_15078_b300 import SimError
+    sc = sg.box_stack(n_boxes=2, m=4, gap=-0.05, seed=1, E=1e6, incline_deg=0.0)
+    o = Oracle(sc)
+    _, _, info = o.frame(sc.q0, np.zeros_like(sc.q0), OracleOptions(n_iters=1))
+    c = len(info["contacts"])
+    verts = set()
+    for ct in info["contacts"]:
+        verts.add(ct["vertex"])
+        verts.update(v for v, _ in ct.get("corners", ()))
+    assert len(verts) > c
+    sim = Simulator(sc, contact_capacity=c)
+    sim.set_state(sc.q0, np.zeros_like(sc.q0))
+    with pytest.raises(SimError) as e:
+        sim.step()
+        sim.synchronize()
+    assert e.value.status == -5
+    sim.close()
