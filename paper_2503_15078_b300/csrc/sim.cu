@@ -997,7 +997,13 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   d.yc_ptr = s->alloc<int>(cap + 1);
   d.yc_val = s->alloc<float>(cap_y);
   d.yc_row = s->alloc<int>(cap_y);
-  d.wt = s->alloc<float>((size_t)cap * ((cap + 3) & ~3));
+  // W~ holds one block per scene, nv_s x ld_s floats (ld_s = nv_s rounded up to 4), with
+  // sum_s nv_s <= cap and nv_s <= V = min(cap, the largest scene's free vertex count)
+  int vmax = 1;
+  for (int sc = 0; sc < p.n_scenes; ++sc)
+    vmax = std::max(vmax, p.scene_vfirst[sc + 1] - p.scene_vfirst[sc]);
+  const int V = std::min(cap, vmax);
+  d.wt = s->alloc<float>((size_t)cap * ((V + 3) & ~3));
   d.resid = s->alloc<double>(silg::kMaxIters + 1);
   d.max_pen = s->alloc<double>(1);
   d.iter_k = s->alloc<int>(1);
@@ -1008,9 +1014,16 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   d.spin_limit = o->spin_limit;
   d.kb_lo = s->alloc<int>(n / 32 + 1);
   d.kb_hi = s->alloc<int>(n / 32 + 1);
-  // every scene may add one partly filled block row of W~ tiles
-  d.wt_part = s->alloc<float>(
-      (size_t)silg::wt_items_max(cap + 64 * p.n_scenes, d.wt_grid) * 64 * 64);
+  // work items of the W~ product: the bound for one scene of every contact vertex (each
+  // scene may add one partly filled block row), or, smaller with many small scenes, the
+  // tiles of blocks of at most ceil(V / 64) tile rows over at most cap / 64 + n_scenes + 1
+  // tile rows in all, plus one grid of K splits
+  {
+    const long long one = silg::wt_items_max(cap + 64 * p.n_scenes, d.wt_grid);
+    const long long nbm = (V + 63) / 64;
+    const long long many = (cap / 64 + p.n_scenes + 1) * (nbm + 1) / 2 + 1 + d.wt_grid;
+    d.wt_part = s->alloc<float>((size_t)std::min(one, many) * 64 * 64);
+  }
   if (silg::sinv_setup() != SIM_OK) return SIM_ECUDA;
   s->ev.resize(5 + kMarksPerIter * silg::kMaxIters);
   for (auto& e : s->ev)
