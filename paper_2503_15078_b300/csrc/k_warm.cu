@@ -38,9 +38,14 @@ __global__ void k_ws_features(DevSim d) {
   const double scale = margin / (h * h * w);
   float* f = d.ws_feat + (size_t)j * kMlpIn;
   if (o < 0 || o >= d.n_obs) {
-    // an anchor or a contact with another body: not guessed (its impulse starts at 0); no
-    // features
+    // an anchor: not guessed (its impulse starts at 0), no features. A contact with another
+    // body: only the previous frame's impulse at the same vertex and triangle (features
+    // 7..9); the network, trained on obstacle contacts, does not see it
     for (int r = 0; r < kMlpIn; ++r) f[r] = 0.f;
+    if (o < 0 && d.prev_valid[v] && d.prev_obst[v] == o)
+      for (int r = 0; r < 3; ++r)
+        f[7 + r] = (float)((D[3 * r] * d.prev_force[3 * v] + D[3 * r + 1] * d.prev_force[3 * v + 1] +
+                            D[3 * r + 2] * d.prev_force[3 * v + 2]) / scale);
     d.ws_scale[j] = scale;
     return;
   }
@@ -68,15 +73,18 @@ __global__ void k_ws_features(DevSim d) {
 // lambda_n) and the move of its vertex along the normal
 __device__ void ws_guess(const DevSim& d, int j) {
   const int v = d.ct_vert[j], sc = d.vert_scene[v];
-  if (d.ct_obst[j] < 0 || d.ct_obst[j] >= d.n_obs) {   // anchors and body contacts start
-                                                        // from lambda = 0
+  if (d.ct_obst[j] >= d.n_obs) {   // anchors start from lambda = 0
     for (int r = 0; r < 3; ++r) d.ws_lam0[3 * j + r] = 0.0;
     d.ws_move[j] = 0.0;
     return;
   }
   const double scale = d.ws_scale[j], mu = d.ct_mu[j], margin = d.scene_margin[sc];
   double lam[3] = {0.0, 0.0, 0.0}, move = 0.0;
-  if (d.ws_mode == 1) {
+  if (d.ct_obst[j] < 0) {
+    // a contact with another body, in either mode: its previous impulse, no move
+    const float* f = d.ws_feat + (size_t)j * kMlpIn;
+    for (int r = 0; r < 3; ++r) lam[r] = (double)f[7 + r] * scale;
+  } else if (d.ws_mode == 1) {
     // the network predicts the change from the previous frame's impulse (features 7..9)
     const float* y = d.ws_out + (size_t)j * kMlpOut;
     const float* f = d.ws_feat + (size_t)j * kMlpIn;
@@ -129,6 +137,7 @@ __global__ void __launch_bounds__(kWsThreads) k_ws_scene(DevSim d) {
   __syncthreads();
   double t[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   for (int j = jb + threadIdx.x; j < je; j += blockDim.x) {
+    if (d.ct_obst[j] < 0) continue;   // contacts between bodies are internal forces
     const double* D = d.ct_D + 9 * j;
     const double* l = d.ws_lam0 + 3 * j;
     for (int r = 0; r < 3; ++r) t[r] += D[r] * l[0] + D[3 + r] * l[1] + D[6 + r] * l[2];
@@ -213,8 +222,7 @@ __global__ void k_ws_record(DevSim d) {
   double mv = 0.0;
   for (int r = 0; r < 3; ++r)
     mv += D[r] * (d.q_ref[3 * v + r] + (double)d.dq[3 * v + r] - d.s_tilde[3 * v + r]);
-  if (d.ct_cv[j] < d.cap && d.cv_first[d.ct_cv[j]] == j && d.ct_obst[j] >= 0 &&
-      d.ct_obst[j] < d.n_obs) {
+  if (d.ct_cv[j] < d.cap && d.cv_first[d.ct_cv[j]] == j && d.ct_obst[j] < d.n_obs) {
     d.prev_valid[v] = 1;
     d.prev_obst[v] = d.ct_obst[j];
     d.prev_move[v] = mv;
@@ -255,8 +263,10 @@ __global__ void k_pf_sync(DevSim d, int K) {
     d.v_t[3 * v + r] = d.v_t[3 * w + r];
     d.prev_force[3 * v + r] = d.prev_force[3 * w + r];
   }
-  d.prev_valid[v] = d.prev_valid[w];
-  // the same obstacle of this copy (copies list their obstacles in the same order)
+  // the same obstacle of this copy (copies list their obstacles in the same order); a
+  // contact with another body (negative id: the triangles are numbered over all scenes)
+  // is not carried over
+  d.prev_valid[v] = d.prev_obst[w] < 0 ? 0 : d.prev_valid[w];
   d.prev_obst[v] = d.prev_obst[w] - d.scene_ofirst[best] + d.scene_ofirst[sc];
   d.prev_move[v] = d.prev_move[w];
 }
