@@ -209,6 +209,8 @@ struct DevSim {
   int s1_grid, s2_grid, n_seg1, n_seg2;
   int s1_unroll, s2_unroll;  // tiles in flight per warp: 1 the format's, 0 half, 2 twice
   int n_sm;         // persistent-kernel grid size
+  int ytz_warp;     // Y^T z with a warp per contact vertex (short ancestor paths) instead
+                    // of a CTA per contact vertex
   const float* zero;  // kTileW zeros: the load target of lanes outside a row's range
   float* p1_part;   // [n_seg1][3][kRowGroup]
   float* p2_part;   // [n_seg2][3][kTileW]

@@ -978,6 +978,46 @@ __global__ void __launch_bounds__(kYtzThreads) k_ytz(DevSim d) {
   }
 }
 
+// The same with one warp per contact vertex (no block barriers; more vertices in flight),
+// for meshes whose ancestor paths are short (many small scenes).
+__global__ void k_ytz_warp(DevSim d) {
+  pdl_wait();
+  const int ncv = min(d.counters[kCntCv], d.cap);
+  if (d.yc_ptr[ncv] > d.cap_y) return;   // uniform over the grid
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const double ih2 = 1.0 / (d.h * d.h);
+  for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < ncv; c += nwarps) {
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    const int k1 = d.yc_ptr[c + 1];
+#pragma unroll 4
+    for (int k = d.yc_ptr[c] + lane; k < k1; k += 32) {
+      const float y = d.yc_val[k];
+      const int a = d.yc_row[k];
+      s0 += y * d.zvec[a];
+      s1 += y * d.zvec[d.n_pad + a];
+      s2 += y * d.zvec[2 * d.n_pad + a];
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if (d.bc_on && lane == 0) {
+      d.svec[3 * c] = s0;
+      d.svec[3 * c + 1] = s1;
+      d.svec[3 * c + 2] = s2;
+    }
+    const int j0 = d.cv_first[c], j1 = min(j0 + d.cv_nct[c], d.cap);
+    for (int j = j0 + lane; j < j1; j += 32) {
+      if (d.bc_on && d.ct_tri[j] >= 0) continue;   // k_body_rhs
+      for (int r = 0; r < 3; ++r) {
+        const float* Dr = d.ct_Df + 9 * j + 3 * r;
+        const float jag = d.ct_omega[3 * j + r] * (Dr[0] * s0 + Dr[1] * s1 + Dr[2] * s2);
+        d.ct_rhs[3 * j + r] = (float)((d.ct_hv[3 * j + r] - (double)jag) * ih2);
+      }
+    }
+  }
+}
+
 // the Schur right-hand side of the contacts with another body, whose J A^-1 g combines
 // (Y^T z) of the vertex and the triangle's corners with the map's weights
 __global__ void k_body_rhs(DevSim d) {
@@ -1600,7 +1640,10 @@ void launch_iter_decide(const DevSim& d, cudaStream_t s, cudaGraphConditionalHan
 void launch_iter_clear(const DevSim& d, cudaStream_t s) { k_iter_clear<<<1, 256, 0, s>>>(d); }
 
 void launch_ytz(const DevSim& d, cudaStream_t s) {
-  launch_k(d.pdl, k_ytz, std::min(d.cap, 8 * d.n_sm), kYtzThreads, 0, s, d);
+  if (d.ytz_warp)
+    launch_k(d.pdl, k_ytz_warp, std::min((d.cap + 7) / 8, 8 * d.n_sm), 256, 0, s, d);
+  else
+    launch_k(d.pdl, k_ytz, std::min(d.cap, 8 * d.n_sm), kYtzThreads, 0, s, d);
   if (d.bc_on) launch_k(d.pdl, k_body_rhs, (d.cap + 127) / 128, 128, 0, s, d);
 }
 

@@ -1011,6 +1011,8 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   d.p_out = s->alloc<float>(9 * (size_t)T);
   s->has_obstacles = n_obs > 0 || !sd.anchors.empty() || d.bc_on;
   d.wt_grid = 4 * d.n_sm;
+  // the path of a contact vertex in Y is its ancestor chain: a warp covers a short one
+  d.ytz_warp = p.mean_depth < 600.0 ? 1 : 0;
   d.spin_limit = o->spin_limit;
   d.kb_lo = s->alloc<int>(n / 32 + 1);
   d.kb_hi = s->alloc<int>(n / 32 + 1);

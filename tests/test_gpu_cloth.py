@@ -84,13 +84,17 @@ def test_free_running_drape_stays_with_the_oracle():
     sim = Simulator(sc)
     q, v = sc.q0.copy(), sc.v0.copy()
     L = sc.bbox_diagonal
+    # the energy includes the gravitational potential, which passes through small values:
+    # the gate is scaled like the other free-running tests', by the larger of the current
+    # and the initial energy
+    e0 = abs(o.energy(q, v))
     for _ in range(40):
         q, v, _ = o.frame(q, v, OracleOptions(n_iters=5, n_cr=sc.n_cr))
         sim.step(n_iters=5)
         qg, vg = sim.state()
         assert abs(o.max_penetration(qg) - o.max_penetration(q)) < 1e-3 * L
         e_o, e_g = o.energy(q, v), o.energy(qg, vg)
-        assert abs(e_g - e_o) < 1e-2 * max(abs(e_o), 1e-9)
+        assert abs(e_g - e_o) < 1e-2 * max(abs(e_o), e0, 1e-9)
     sim.close()
 
 
