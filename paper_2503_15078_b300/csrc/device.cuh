@@ -209,6 +209,7 @@ struct DevSim {
   int s1_grid, s2_grid, n_seg1, n_seg2;
   int s1_unroll, s2_unroll;  // tiles in flight per warp: 1 the format's, 0 half, 2 twice
   int n_sm;         // persistent-kernel grid size
+  int* scan_part;   // scratch of the two-pass scans (tile sums and offsets)
   int ytz_warp;     // Y^T z with a warp per contact vertex (short ancestor paths) instead
                     // of a CTA per contact vertex
   const float* zero;  // kTileW zeros: the load target of lanes outside a row's range
@@ -374,7 +375,13 @@ int ws_kernels(int mode);   // launches of launch_ws_start
 // residual after a K-iteration frame (one launch)
 // (K < 0: read from d.iter_k)
 void launch_pf_sync(const DevSim& d, cudaStream_t s, int K);
-void launch_scan(const int* in, int* out, int n, const int* n_dev, int* total, cudaStream_t s);
+// exclusive scan of n ints (or of min(*n_dev, n)): one CTA, or with `scratch`
+// (scan_scratch_ints(n) ints) and n above 65,536 one CTA per 4,096-element tile in three
+// launches (scan_launches(n))
+void launch_scan(const int* in, int* out, int n, const int* n_dev, int* total, cudaStream_t s,
+                 int* scratch = nullptr);
+int scan_launches(int n);
+int scan_scratch_ints(int n);
 int cr_setup(int n_scenes, int* cluster_out, size_t* smem_out);
 int sinv_setup();
 

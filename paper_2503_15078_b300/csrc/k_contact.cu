@@ -457,51 +457,94 @@ __global__ void k_collide_write(DevSim d) {
 // length is n_static, or the device count *n_dev capped at n_static (the arrays' size).
 // The array is walked in coalesced tiles of 4 x blockDim elements (each thread scans four
 // consecutive values), with the running total carried from tile to tile.
+// one tile of 4 x blockDim elements from `base`, exclusive, starting from `carry`; returns
+// the tile's sum
+__device__ __forceinline__ int scan_tile(const int* in, int* out, int n, int base, int carry,
+                                         int* wsum) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int idx = base + 4 * tid;
+  int v0 = idx < n ? in[idx] : 0, v1 = idx + 1 < n ? in[idx + 1] : 0;
+  int v2 = idx + 2 < n ? in[idx + 2] : 0, v3 = idx + 3 < n ? in[idx + 3] : 0;
+  const int sum4 = v0 + v1 + v2 + v3;
+  int incl = sum4;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) wsum[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int w = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    wsum[lane] = w;
+  }
+  __syncthreads();
+  int run = carry + (wid > 0 ? wsum[wid - 1] : 0) + incl - sum4;
+  if (idx < n) out[idx] = run;
+  run += v0;
+  if (idx + 1 < n) out[idx + 1] = run;
+  run += v1;
+  if (idx + 2 < n) out[idx + 2] = run;
+  run += v2;
+  if (idx + 3 < n) out[idx + 3] = run;
+  const int tile_sum = wsum[31];
+  __syncthreads();
+  return tile_sum;
+}
+
+__device__ __forceinline__ int scan_len(int n_static, const int* n_dev) {
+  const int n = n_dev ? min(*n_dev, n_static) : n_static;
+  return n < 0 ? 0 : n;
+}
+
 __global__ void __launch_bounds__(1024) k_scan(const int* in, int* out, int n_static,
                                                const int* n_dev, int* total) {
   __shared__ int wsum[32];
-  int n = n_dev ? min(*n_dev, n_static) : n_static;
-  if (n < 0) n = 0;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-  const int tile = 4 * blockDim.x;
+  const int n = scan_len(n_static, n_dev);
   int carry = 0;
-  for (int base = 0; base < n; base += tile) {
-    const int idx = base + 4 * tid;
-    int v0 = idx < n ? in[idx] : 0, v1 = idx + 1 < n ? in[idx + 1] : 0;
-    int v2 = idx + 2 < n ? in[idx + 2] : 0, v3 = idx + 3 < n ? in[idx + 3] : 0;
-    const int sum4 = v0 + v1 + v2 + v3;
-    int incl = sum4;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    if (lane == 31) wsum[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-      int w = lane < nw ? wsum[lane] : 0;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += t;
-      }
-      wsum[lane] = w;
-    }
-    __syncthreads();
-    int run = carry + (wid > 0 ? wsum[wid - 1] : 0) + incl - sum4;
-    if (idx < n) out[idx] = run;
-    run += v0;
-    if (idx + 1 < n) out[idx + 1] = run;
-    run += v1;
-    if (idx + 2 < n) out[idx + 2] = run;
-    run += v2;
-    if (idx + 3 < n) out[idx + 3] = run;
-    carry += wsum[31];
-    __syncthreads();
-  }
-  if (tid == 0) {
+  for (int base = 0; base < n; base += 4 * blockDim.x)
+    carry += scan_tile(in, out, n, base, carry, wsum);
+  if (threadIdx.x == 0) {
     out[n] = carry;
     if (total) *total = carry;
+  }
+}
+
+// Long arrays in two passes, one CTA per tile: the tiles' sums, their scan (k_scan on
+// them), then every tile scanned from its offset.
+constexpr int kScanTile = 4096;     // elements per tile: 1024 threads x 4
+constexpr int kScanSplit = 65536;   // arrays longer than this take the two-pass scan
+__global__ void __launch_bounds__(1024) k_scan_tiles(const int* in, int n_static,
+                                                     const int* n_dev, int* part) {
+  __shared__ int wsum[32];
+  const int n = scan_len(n_static, n_dev);
+  const int idx = blockIdx.x * kScanTile + 4 * threadIdx.x;
+  int v = 0;
+  for (int q = 0; q < 4; ++q) v += idx + q < n ? in[idx + q] : 0;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int w = threadIdx.x < (blockDim.x >> 5) ? wsum[threadIdx.x] : 0;
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (threadIdx.x == 0) part[blockIdx.x] = w;
+  }
+}
+__global__ void __launch_bounds__(1024) k_scan_fin(const int* in, int* out, int n_static,
+                                                   const int* n_dev, const int* part_off,
+                                                   int n_tiles, int* total) {
+  __shared__ int wsum[32];
+  const int n = scan_len(n_static, n_dev);
+  const int base = blockIdx.x * kScanTile;
+  if (base < n) scan_tile(in, out, n, base, part_off[blockIdx.x], wsum);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    out[n] = part_off[n_tiles];
+    if (total) *total = part_off[n_tiles];
   }
 }
 
@@ -1554,9 +1597,21 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
 
 }  // namespace
 
-void launch_scan(const int* in, int* out, int n, const int* n_dev, int* total, cudaStream_t s) {
-  k_scan<<<1, 1024, 0, s>>>(in, out, n, n_dev, total);
+void launch_scan(const int* in, int* out, int n, const int* n_dev, int* total, cudaStream_t s,
+                 int* scratch) {
+  if (!scratch || n <= kScanSplit) {
+    k_scan<<<1, 1024, 0, s>>>(in, out, n, n_dev, total);
+    return;
+  }
+  // scratch: n_tiles tile sums, then their n_tiles + 1 offsets
+  const int nt = (n + kScanTile - 1) / kScanTile;
+  k_scan_tiles<<<nt, 1024, 0, s>>>(in, n, n_dev, scratch);
+  k_scan<<<1, 1024, 0, s>>>(scratch, scratch + nt, nt, nullptr, nullptr);
+  k_scan_fin<<<nt, 1024, 0, s>>>(in, out, n, n_dev, scratch + nt, nt, total);
 }
+
+int scan_launches(int n) { return n > kScanSplit ? 3 : 1; }
+int scan_scratch_ints(int n) { return 2 * ((n + kScanTile - 1) / kScanTile) + 2; }
 
 void launch_collide(const DevSim& d, cudaStream_t s) {
   const int g = (d.n + 63) / 64;
@@ -1567,10 +1622,10 @@ void launch_collide(const DevSim& d, cudaStream_t s) {
   k_collide_count<<<g, 64, 0, s>>>(d);
   if (d.bc_on) {
     k_corner_flag<<<(d.n + 255) / 256, 256, 0, s>>>(d);
-    launch_scan(d.x_cnt, d.x_off, d.n, nullptr, nullptr, s);
+    launch_scan(d.x_cnt, d.x_off, d.n, nullptr, nullptr, s, d.scan_part);
   }
-  launch_scan(d.ct_cnt, d.ct_off, d.n, nullptr, d.counters + kCntContacts, s);
-  launch_scan(d.cv_flag, d.cv_off, d.n, nullptr, d.counters + kCntCv, s);
+  launch_scan(d.ct_cnt, d.ct_off, d.n, nullptr, d.counters + kCntContacts, s, d.scan_part);
+  launch_scan(d.cv_flag, d.cv_off, d.n, nullptr, d.counters + kCntCv, s, d.scan_part);
   k_collide_write<<<g, 64, 0, s>>>(d);
   if (d.bc_on) k_corner_sort<<<(d.n + 255) / 256, 256, 0, s>>>(d);
 }
@@ -1578,11 +1633,11 @@ void launch_collide(const DevSim& d, cudaStream_t s) {
 void launch_delassus(const DevSim& d, cudaStream_t s) {
   const int g = (d.n + 255) / 256;
   k_u_flag<<<g, 256, 0, s>>>(d);
-  launch_scan(d.u_flag, d.u_off, d.n, nullptr, d.counters + kCntU, s);
+  launch_scan(d.u_flag, d.u_off, d.n, nullptr, d.counters + kCntU, s, d.scan_part);
   k_u_compact<<<g, 256, 0, s>>>(d);
-  launch_scan(d.u_len, d.y_ptr, d.n, d.counters + kCntU, d.counters + kCntY, s);
+  launch_scan(d.u_len, d.y_ptr, d.n, d.counters + kCntU, d.counters + kCntY, s, d.scan_part);
   k_yc_len<<<(d.cap + 255) / 256, 256, 0, s>>>(d);
-  launch_scan(d.yc_len, d.yc_ptr, d.cap, d.counters + kCntCv, d.counters + kCntYC, s);
+  launch_scan(d.yc_len, d.yc_ptr, d.cap, d.counters + kCntCv, d.counters + kCntYC, s, d.scan_part);
   k_y_gather<<<std::min((d.n * 32 + 255) / 256, 8 * d.n_sm), 256, 0, s>>>(d);
   k_scene_ranges<<<1, 256, 0, s>>>(d);
   k_wt_blocks<<<(d.n / kWtKB + 1 + 127) / 128, 128, 0, s>>>(d);

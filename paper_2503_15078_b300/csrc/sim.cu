@@ -150,6 +150,15 @@ int frame_iters(sim_s* s) {
   return k;
 }
 
+// the extra launches of the two-pass scans of a frame with contacts: the n-length scans
+// (contacts, contact vertices, corner terms with body contact, U flags, Y row lengths) and
+// the capacity-length one (Y column lengths)
+int scan_extra(const sim_s* s) {
+  const int n = s->d.n, cap = s->d.cap;
+  return (3 + (s->d.bc_on ? 1 : 0) + 1) * (silg::scan_launches(n) - 1) +
+         (silg::scan_launches(cap) - 1);
+}
+
 // local-step launches per iteration (tetrahedra, triangles) and per-frame extras (bending)
 int local_kernels(const sim_s* s) { return (s->d.n_tets > 0) + (s->d.n_tris > 0); }
 
@@ -158,11 +167,13 @@ int kernels_per_frame_to_tolerance(const sim_s* s, int K) {
   const bool c = s->has_obstacles;
   const int bc = s->d.bc_on ? 1 : 0;   // contacts between bodies: 5 more collision launches,
                                        // one more per constraint solve
+  const int scans = scan_extra(s);
   const int refine_body = s->d.s_bf16 && s->d.refine >= 2 && !s->d.jacobi_sweeps ? 5 : 0;
   const int refine_end = s->d.s_bf16 && s->d.refine == 1 && !s->d.jacobi_sweeps ? 6 : 0;
   const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 + bc : 0) + 2;
   const int before = 1 + (s->d.bend_ptr != nullptr) +
-                     (c ? 4 + 12 + 5 * bc + silg::ws_kernels(s->d.ws_mode) : 0) + local_kernels(s) +
+                     (c ? 4 + 12 + 5 * bc + scans + silg::ws_kernels(s->d.ws_mode) : 0) +
+                     local_kernels(s) +
                      (c ? 1 : 0);
   const int body = 1 + global + refine_body + 1 + (c ? 1 : 0) + local_kernels(s) + 1;
   const int after = refine_end + (c ? 1 : 0) + 1 + (c && s->d.pf_copies > 1 ? 1 : 0);
@@ -175,7 +186,7 @@ int kernels_per_frame(const sim_s* s, int K) {
   // pass 2 + reduction; a residual correction adds the residual and both passes
   const int bc = s->d.bc_on ? 1 : 0;
   const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 + bc : 0) + 2;
-  return 1 + (s->d.bend_ptr != nullptr) + (c ? 4 + 12 + 5 * bc : 0) +
+  return 1 + (s->d.bend_ptr != nullptr) + (c ? 4 + 12 + 5 * bc + scan_extra(s) : 0) +
          K * (local_kernels(s) + (c ? 1 : 0) + 1 + global) + (c ? 1 : 0) + 1 +
          5 * refined_iters(s, K) + (c ? silg::ws_kernels(s->d.ws_mode) : 0) +
          (c && s->d.pf_copies > 1 ? 1 : 0);
@@ -1011,6 +1022,7 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   d.p_out = s->alloc<float>(9 * (size_t)T);
   s->has_obstacles = n_obs > 0 || !sd.anchors.empty() || d.bc_on;
   d.wt_grid = 4 * d.n_sm;
+  d.scan_part = s->alloc<int>(silg::scan_scratch_ints(std::max(n, cap)));
   // the path of a contact vertex in Y is its ancestor chain: a warp covers a short one
   d.ytz_warp = p.mean_depth < 600.0 ? 1 : 0;
   d.spin_limit = o->spin_limit;
