@@ -237,6 +237,7 @@ struct DevSim {
   int n_btri;
   float* chunk_box;        // 6 per run of kTriChunk consecutive triangles: their bounds
   float* tri_box;          // 6 per triangle: its bounds (both rounded outward to FP32)
+  float* super_box;        // 6 per run of kTriSuper triangles (kTriSuper / kTriChunk runs)
   int* bc_tri;             // n: the vertex's matched triangle (index into btri) or -1
   double* bc_w;            // 3 n: barycentric weights of the closest point
   double* bc_n;            // 3 n: contact normal
@@ -320,6 +321,7 @@ void launch_delassus(const DevSim& d, cudaStream_t s);
 constexpr int kWtMaxSplit = 16;
 constexpr int kCrMaxRanks = 16;
 constexpr int kTriChunk = 16;   // surface triangles per bounding box of the body search
+constexpr int kTriSuper = 256;  // ... and per bounding box of the level above
 constexpr int kMaxStagedCols = 32;  // column tiles of g staged per pass-1 CTA (96 KB)
 inline long long wt_items_max(int cap, int grid) {
   long long best = 0;

@@ -215,6 +215,21 @@ __global__ void k_chunk_box(DevSim d) {
   if (lane < 6 && c * kTriChunk < d.n_btri) d.chunk_box[6 * c + lane] = lane < 3 ? lo[lane] : hi[lane - 3];
 }
 
+// bounds of every run of kTriSuper triangles from its runs' bounds (one thread per run)
+__global__ void k_super_box(DevSim d) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c0 = u * (kTriSuper / kTriChunk);
+  const int c1 = min(c0 + kTriSuper / kTriChunk, (d.n_btri + kTriChunk - 1) / kTriChunk);
+  if (c0 >= c1) return;
+  float b[6] = {3e38f, 3e38f, 3e38f, -3e38f, -3e38f, -3e38f};
+  for (int c = c0; c < c1; ++c)
+    for (int r = 0; r < 3; ++r) {
+      b[r] = fminf(b[r], d.chunk_box[6 * c + r]);
+      b[3 + r] = fmaxf(b[3 + r], d.chunk_box[6 * c + 3 + r]);
+    }
+  for (int r = 0; r < 6; ++r) d.super_box[6 * u + r] = b[r];
+}
+
 __device__ __forceinline__ bool far_from(const float* box, const float* x, float lim) {
   return x[0] < box[0] - lim || x[1] < box[1] - lim || x[2] < box[2] - lim ||
          x[0] > box[3] + lim || x[1] > box[4] + lim || x[2] > box[5] + lim;
@@ -247,7 +262,13 @@ __device__ bool body_match(const DevSim& d, int i, const double* x, double margi
     if (far_from(bxf, xf, lim)) continue;
     const int te = d.body_toff[b + 1];
     for (int t = d.body_toff[b]; t < te; ++t) {
-      // skip the rest of a run of triangles whose bounds are farther than the limit
+      // skip the rest of a run of triangles whose bounds are farther than the limit: first
+      // the runs of kTriSuper, then those of kTriChunk
+      if ((t == d.body_toff[b] || t % kTriSuper == 0) &&
+          far_from(d.super_box + 6 * (t / kTriSuper), xf, lim)) {
+        t = min(te, (t / kTriSuper + 1) * kTriSuper) - 1;
+        continue;
+      }
       if ((t == d.body_toff[b] || t % kTriChunk == 0) &&
           far_from(d.chunk_box + 6 * (t / kTriChunk), xf, lim)) {
         t = min(te, (t / kTriChunk + 1) * kTriChunk) - 1;
@@ -1618,6 +1639,7 @@ void launch_collide(const DevSim& d, cudaStream_t s) {
   if (d.bc_on) {
     k_body_box<<<d.n_bodies, kBoxThreads, 0, s>>>(d);
     k_chunk_box<<<((d.n_btri / kTriChunk + 1) * 32 + 127) / 128, 128, 0, s>>>(d);
+    k_super_box<<<(d.n_btri / kTriSuper + 1 + 127) / 128, 128, 0, s>>>(d);
   }
   k_collide_count<<<g, 64, 0, s>>>(d);
   if (d.bc_on) {

@@ -165,14 +165,14 @@ int local_kernels(const sim_s* s) { return (s->d.n_tets > 0) + (s->d.n_tris > 0)
 // launches of a frame to a tolerance that made K updates (enqueue_frame_to_tolerance)
 int kernels_per_frame_to_tolerance(const sim_s* s, int K) {
   const bool c = s->has_obstacles;
-  const int bc = s->d.bc_on ? 1 : 0;   // contacts between bodies: 5 more collision launches,
+  const int bc = s->d.bc_on ? 1 : 0;   // contacts between bodies: 6 more collision launches,
                                        // one more per constraint solve
   const int scans = scan_extra(s);
   const int refine_body = s->d.s_bf16 && s->d.refine >= 2 && !s->d.jacobi_sweeps ? 5 : 0;
   const int refine_end = s->d.s_bf16 && s->d.refine == 1 && !s->d.jacobi_sweeps ? 6 : 0;
   const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 + bc : 0) + 2;
   const int before = 1 + (s->d.bend_ptr != nullptr) +
-                     (c ? 4 + 12 + 5 * bc + scans + silg::ws_kernels(s->d.ws_mode) : 0) +
+                     (c ? 4 + 12 + 6 * bc + scans + silg::ws_kernels(s->d.ws_mode) : 0) +
                      local_kernels(s) +
                      (c ? 1 : 0);
   const int body = 1 + global + refine_body + 1 + (c ? 1 : 0) + local_kernels(s) + 1;
@@ -186,7 +186,7 @@ int kernels_per_frame(const sim_s* s, int K) {
   // pass 2 + reduction; a residual correction adds the residual and both passes
   const int bc = s->d.bc_on ? 1 : 0;
   const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 + bc : 0) + 2;
-  return 1 + (s->d.bend_ptr != nullptr) + (c ? 4 + 12 + 5 * bc + scan_extra(s) : 0) +
+  return 1 + (s->d.bend_ptr != nullptr) + (c ? 4 + 12 + 6 * bc + scan_extra(s) : 0) +
          K * (local_kernels(s) + (c ? 1 : 0) + 1 + global) + (c ? 1 : 0) + 1 +
          5 * refined_iters(s, K) + (c ? silg::ws_kernels(s->d.ws_mode) : 0) +
          (c && s->d.pf_copies > 1 ? 1 : 0);
@@ -764,6 +764,7 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
       d.n_btri = (int)sd.btri.size();
       d.chunk_box = s->alloc<float>(6 * (size_t)(d.n_btri / silg::kTriChunk + 1));
       d.tri_box = s->alloc<float>(6 * (size_t)std::max(1, d.n_btri));
+      d.super_box = s->alloc<float>(6 * (size_t)(d.n_btri / silg::kTriSuper + 1));
       d.bc_tri = s->alloc<int>(n);
       d.bc_w = s->alloc<double>(3 * (size_t)n);
       d.bc_n = s->alloc<double>(3 * (size_t)n);
@@ -1296,9 +1297,38 @@ int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_opt
               per[comp[st[t][0]]].push_back(
                   {st[t][0] + voff, st[t][1] + voff, st[t][2] + voff, btri_base + (int)t});
           }
+          // within a body, triangles in Morton order of their rest centroids, so that the
+          // runs of kTriChunk consecutive triangles whose bounds the search tests are
+          // compact (the search breaks ties by the triangle's number, not by this order)
+          const double* X = m.rest_pos;
           for (int b = 0; b < ncomp; ++b) {
+            auto& tl = per[b];
+            double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+            std::vector<std::array<double, 3>> cen(tl.size());
+            for (size_t t = 0; t < tl.size(); ++t)
+              for (int r = 0; r < 3; ++r) {
+                cen[t][r] = (X[3 * (tl[t][0] - voff) + r] + X[3 * (tl[t][1] - voff) + r] +
+                             X[3 * (tl[t][2] - voff) + r]) / 3.0;
+                lo[r] = std::min(lo[r], cen[t][r]);
+                hi[r] = std::max(hi[r], cen[t][r]);
+              }
+            std::vector<std::pair<uint64_t, int>> key(tl.size());
+            for (size_t t = 0; t < tl.size(); ++t) {
+              uint64_t code = 0;
+              uint32_t qv[3];
+              for (int r = 0; r < 3; ++r) {
+                const double span = hi[r] - lo[r];
+                qv[r] = span > 0 ? (uint32_t)std::min(1023.0, 1023.0 * (cen[t][r] - lo[r]) / span) : 0u;
+              }
+              for (int bit = 9; bit >= 0; --bit)
+                for (int r = 0; r < 3; ++r) code = (code << 1) | ((qv[r] >> bit) & 1u);
+              key[t] = {code, tl[t][3]};
+            }
+            std::vector<int> ord(tl.size());
+            std::iota(ord.begin(), ord.end(), 0);
+            std::sort(ord.begin(), ord.end(), [&](int a, int c) { return key[a] < key[c]; });
             sd.body_toff.push_back((int)sd.btri.size());
-            sd.btri.insert(sd.btri.end(), per[b].begin(), per[b].end());
+            for (int t : ord) sd.btri.push_back(tl[t]);
           }
           btri_base += (int)st.size();
         }
