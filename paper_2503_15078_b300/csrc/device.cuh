@@ -163,7 +163,8 @@ struct DevSim {
   const float* tet_vol;
   const int* tet_mat;
   const MatDev* mats;
-  float4* contrib;         // [n_tets * 4 + n_tris * 3]: h^2 w (p - F_ref) g_a per corner
+  float4* contrib;         // h^2 w (p - F_ref) g_a per element corner, stored at the
+                           // corner's incidence slot (vertex-major)
   // triangle (membrane) elements
   int n_tris;
   const int4* tri_v;       // internal vertex ids (w unused)
@@ -179,6 +180,8 @@ struct DevSim {
   float* bend_f;           // 3 n
   const int* inc_ptr;      // n + 1: incidences of free vertex i
   const int* inc_idx;      // entries 4 t + a
+  const int* inc_slot;     // 4 n_tets + 3 n_tris: the corner's position in the incidence
+                           // lists (-1: pinned), where contrib holds its contribution
 
   // S~ profile (FP32 values, or BF16 bit patterns when s_bf16 is set)
   const float* S;

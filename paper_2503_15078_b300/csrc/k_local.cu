@@ -339,7 +339,8 @@ __global__ void __launch_bounds__(128) k_local(DevSim d) {
     for (int r = 0; r < 3; ++r)
       o[r] = s * ((p[3 * r] - Fr[3 * r]) * g[a][0] + (p[3 * r + 1] - Fr[3 * r + 1]) * g[a][1] +
                   (p[3 * r + 2] - Fr[3 * r + 2]) * g[a][2]);
-    d.contrib[4 * t + a] = make_float4(o[0], o[1], o[2], 0.f);
+    const int sl = d.inc_slot[4 * t + a];
+    if (sl >= 0) d.contrib[sl] = make_float4(o[0], o[1], o[2], 0.f);
   }
 }
 
@@ -348,7 +349,8 @@ __global__ void __launch_bounds__(128) k_local(DevSim d) {
 // with V and sigma^2 the eigenpairs of the 2 x 2 F^T F (a Jacobi rotation). ARAP:
 // sigma_hat = 1 (the closest matrix with orthonormal columns); co-rotational: the closed-form
 // minimiser of w/2 |x - sigma|^2 + V (mu |x - 1|^2 + lam/2 (sum x - 2)^2). Corner a's
-// contribution h^2 w (p - F_ref) g_a goes to contrib[4 n_tets + 3 t + a].
+// contribution h^2 w (p - F_ref) g_a goes to the incidence slot of element entry
+// 4 n_tets + 3 t + a.
 __global__ void __launch_bounds__(128) k_local_tri(DevSim d) {
   pdl_wait();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -426,7 +428,8 @@ __global__ void __launch_bounds__(128) k_local_tri(DevSim d) {
 #pragma unroll
     for (int r = 0; r < 3; ++r)
       o[r] = sc * ((p[2 * r] - Fr[2 * r]) * g[a][0] + (p[2 * r + 1] - Fr[2 * r + 1]) * g[a][1]);
-    d.contrib[base + a] = make_float4(o[0], o[1], o[2], 0.f);
+    const int sl = d.inc_slot[base + a];
+    if (sl >= 0) d.contrib[sl] = make_float4(o[0], o[1], o[2], 0.f);
   }
 }
 
@@ -462,7 +465,7 @@ __global__ void k_rhs(DevSim d) {
   float e[3] = {0.f, 0.f, 0.f};
   const int k0 = i < d.n ? d.inc_ptr[i] : 0, k1 = i < d.n ? d.inc_ptr[i + 1] : 0;
   for (int k = k0 + sub; k < k1; k += kRhsLanes) {
-    const float4 c = d.contrib[d.inc_idx[k]];
+    const float4 c = d.contrib[k];   // the vertex's run of incidence slots
     e[0] += c.x;
     e[1] += c.y;
     e[2] += c.z;

@@ -829,7 +829,7 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   std::vector<silg::MatDev> md;
   for (auto& m : p.mats) md.push_back({m.model, (float)m.mu, (float)m.lam, (float)m.alpha});
   d.mats = s->upload(md);
-  // triangles: corner contributions follow the tetrahedra's in contrib
+  // triangles: element entries 4 n_tets + 3 t + a follow the tetrahedra's
   const int Nt = p.n_tris;
   d.n_tris = Nt;
   {
@@ -876,6 +876,12 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
       }
     d.inc_ptr = s->upload(cnt);
     d.inc_idx = s->upload(idx);
+    // where each element corner's contribution is stored: its place in its vertex's
+    // incidence list (-1: a pinned vertex, not summed), so the right-hand side reads each
+    // vertex's contributions as one contiguous run
+    std::vector<int> slot(std::max<size_t>(1, 4 * (size_t)T + 3 * (size_t)Nt), -1);
+    for (int k = 0; k < cnt[n]; ++k) slot[idx[k]] = k;
+    d.inc_slot = s->upload(slot);
   }
   // bending rows of the free vertices in internal numbering
   d.bend_ptr = nullptr;
