@@ -235,3 +235,30 @@ def test_previous_impulses_start_body_contacts_closer():
     assert iters[2] < iters[0]
     # frames stopped at a tolerance differ within it: compare against the stack's size
     assert np.abs(states[2] - states[0]).max() < 1e-3 * sc.bbox_diagonal
+
+
+def test_stress_columns_hold_on_the_incline_for_200_frames():
+    # four of the stress workload's columns (two stiff boxes of 12^3 vertices, E = 1e8,
+    # mu = 0.8 > tan 20 deg) for 200 frames of 10 iterations with the previous-impulse
+    # start: the stacks stay put (Coulomb sticking), nothing sinks in by a margin, and the
+    # frames stay finite
+    scenes = sg.stack_stress(copies=1, columns=4)
+    q0 = np.concatenate([sc.q0 for sc in scenes])
+    sim = Simulator(scenes, contact_capacity=8192)
+    sim.set_warmstart(2)
+    sim.set_state(q0, np.zeros_like(q0))
+    for _ in range(200):
+        sim.step()
+    q, v = sim.state()
+    assert np.all(np.isfinite(q)) and np.all(np.isfinite(v))
+    th = np.radians(20.0)
+    down = np.array([np.cos(th), 0.0, -np.sin(th)])
+    off = sim.scene_offsets
+    for k, sc in enumerate(scenes):
+        vs = v[off[k]:off[k + 1]] @ down
+        assert np.abs(vs).max() < 1e-2, (k, np.abs(vs).max())
+        # the stack has not slid: its mean displacement along the slope stays below a
+        # lattice spacing
+        assert abs(((q[off[k]:off[k + 1]] - sc.q0) @ down).mean()) < sc.spacing
+    assert sim.stats()["max_penetration"] < scenes[0].contact_margin
+    sim.close()
