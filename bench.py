@@ -282,18 +282,10 @@ class OracleTimer:
 
 
 def contact_state(scene, placement):
-    """The rest shape translated along +x so that its leading face lies `placement` metres
-    beyond the axes of the first cylinder row, every vertex moving at the pull speed (pure
-    geometry of the scene: no simulation). At 0.1025 m the star's tips are inside the first
-    row's cylinders: 810 contacts at 810 distinct vertices on the predicted positions."""
-    import numpy as np
-    q = scene.q0.copy()
-    x_front = scene.X[:, 0].max()
-    first_col = min(o.p[0] for o in scene.obstacles)
-    q[:, 0] += (first_col - x_front) + placement
-    v = np.zeros_like(q)
-    v[:, 0] = scene.handle_vel[0]
-    return q, v
+    """The placed star: the rest shape moved `placement` metres past the first cylinder
+    row's axes, moving at the pull speed (scenegen.star_placed; pure geometry)."""
+    import scenegen as sg
+    return sg.star_placed(scene, placement)
 
 
 def batch_state(scenes):

@@ -253,10 +253,13 @@ int sim_plan_get_ordering(const sim_plan_t* plan, int32_t* order, int32_t* paren
 int sim_plan_apply_inverse_host(const sim_plan_t* plan, const double* b, double* x);
 
 /*
- * Create a simulator on one GPU: runs the host precompute, uploads everything, and
- * prepares the per-frame CUDA graph. opts may be NULL (defaults). Positions start at the
- * rest shape with zero velocity (sim_set_state to change). Errors: SIM_EINVAL,
- * SIM_ENOTSPD, SIM_ENOMEM, SIM_ECUDA.
+ * Create a simulator on one GPU for the implicit-Euler problem of Sec. 3.1 (Eq. 1: the
+ * mesh, its materials, the obstacles and the step h): runs the host precompute (the
+ * system matrix of Eq. 6, its Cholesky factor and S = L^-1 P, Sec. 4.2 and Theorem 1: the
+ * one-time first line of Alg. 4), uploads everything, and prepares the per-frame CUDA graph.
+ * opts may be NULL (defaults). Positions start at the rest shape with zero velocity
+ * (sim_set_state to change). All inputs are copied. Errors: SIM_EINVAL, SIM_ENOTSPD,
+ * SIM_ENOMEM, SIM_ECUDA.
  */
 int sim_create(const sim_mesh* mesh, const sim_material* mats, int32_t n_mat,
                const sim_obstacle* obstacles, int32_t n_obs, double h,
@@ -331,9 +334,15 @@ int sim_create_batch(const sim_scene* scenes, int32_t n_scenes, double h,
 int sim_get_scene_residuals(sim_t* sim, int32_t capacity, double* out);
 /* The products' launch configuration (tuned or fixed). */
 int sim_get_tuning(const sim_t* sim, sim_tuning* out);
+/* Release a simulator (waits for its stream; frees every device buffer through the
+ * allocator it was created with). NULL is ignored. The paper's method keeps no state beyond
+ * the precompute and the frame state (Alg. 4), all of it owned by the handle. */
 void sim_destroy(sim_t* sim);
 
-/* One frame of Alg. 4 with n_iters local-global iterations (n_iters <= 0: the option's
+/* One frame of Alg. 4 (Sec. 6): prediction s~ (Eq. 1), collision and linearisation
+ * (App. A.1), Delassus operator and preconditioner (Eqs. 27-28), then local steps (Eq. 5),
+ * Fischer-Burmeister evaluation (App. B.2), constrained global steps through S (Eqs. 19-23,
+ * Eq. 8) and integration, with n_iters local-global iterations (n_iters <= 0: the option's
  * n_iters, or, if sim_options.residual_tol > 0, iterations until R_k <= residual_tol: at
  * least 1 and at most max_iters, the stopping decision taken on the device; sim_stats
  * reports the count). Asynchronous on the handle's stream. */
@@ -341,11 +350,31 @@ int sim_step(sim_t* sim, int32_t n_iters);
 /* Wait for the handle's stream; returns the first device-side error, if any. */
 int sim_synchronize(sim_t* sim);
 
-/* Copy the state out (synchronises). q, v: n_verts x 3 (NULL to skip). */
-int sim_get_state(sim_t* sim, double* q, double* v);
-/* Replace the state (positions, velocities; pinned vertices included). Resets the frame
- * counter. */
+/* Copy the state out (synchronises): the positions q_{t+h} and velocities
+ * v_{t+h} = (q_{t+h} - q_t) / h of the last frame (the integration line of Alg. 4), its
+ * contact impulses lambda (Eq. 23a; per contact the n, f1, f2 components in N, in the order
+ * sim_get_contacts lists them, `capacity` rows; the count goes to *n_contacts, and may exceed
+ * capacity) and its statistics (as sim_get_stats). q, v: n_verts x 3. Every output pointer
+ * may be NULL; lambda needs capacity > 0. */
+int sim_get_state(sim_t* sim, double* q, double* v, int32_t capacity, double* lambda,
+                  int32_t* n_contacts, sim_stats* stats);
+/* Replace the state (positions, velocities; pinned vertices included) from which the next
+ * frame starts (q_t, v_t of Alg. 4). Resets the frame counter and the anchors' time, and
+ * forgets the previous frame's contacts: the next frame starts like a first frame in every
+ * warm-start mode. To resume exactly, contacts included, use sim_set_checkpoint. */
 int sim_set_state(sim_t* sim, const double* q, const double* v);
+/* Checkpoint and restore of everything a later frame depends on: q_t, v_t, the frame
+ * counter, the anchors' current targets and the previous frame's contact record that the
+ * warm starts read (per vertex: contact, obstacle, world impulse D^T lambda, normal move). A
+ * restored simulator continues bit for bit as the saved one would in every start mode (cold,
+ * learned, previous-frame, portfolio). The paper has no counterpart (its method holds no
+ * state across frames but q and v).
+ * sim_get_checkpoint: *bytes receives the size (buf may be NULL to ask for it only); with
+ * buf, capacity >= that size (else SIM_ECAPACITY). Synchronises.
+ * sim_set_checkpoint: bytes must be that size and the checkpoint must come from a simulator
+ * with the same scenes (a signature of every input is checked), else SIM_EINVAL. */
+int sim_get_checkpoint(sim_t* sim, void* buf, size_t capacity, size_t* bytes);
+int sim_set_checkpoint(sim_t* sim, const void* buf, size_t bytes);
 int sim_get_stats(sim_t* sim, sim_stats* stats);
 /* Contacts of the last frame, ordered by (caller vertex id, obstacle index): vertex,
  * obstacle, lambda (n, f1, f2 components, N), frame rows (n, f1, f2: 9 doubles). Arrays of
@@ -355,6 +384,11 @@ int sim_get_contacts(sim_t* sim, int32_t capacity, int32_t* vertex, int32_t* obs
 
 /* Sizes of the simulator's precomputed structure (same fields as sim_plan_get_info). */
 int sim_get_plan_info(const sim_t* sim, sim_plan_info* info);
+/* The simulator's internal row order (Sec. 4.2: the nested-dissection order in postorder of
+ * its elimination forest, Theorem 1), as sim_plan_get_ordering gives it for a plan, for one
+ * scene or a whole batch (vertex ids in the batch numbering of sim_create_batch; a batch's
+ * rows run scene by scene). n_free entries each (sim_get_plan_info); NULL skips an array. */
+int sim_get_ordering(const sim_t* sim, int32_t* order, int32_t* parent, int32_t* first_desc);
 
 /* Per-phase device time of the most recent frame (synchronises). ms: SIM_NUM_PHASES. */
 int sim_get_phase_times(sim_t* sim, double* ms);
@@ -408,6 +442,11 @@ int sim_mlp_train(sim_mlp_t* net, const float* X, const float* T, int32_t rows, 
  * if the residual of its impulses at k = 0 (at the position they predict) is below the cold
  * start's. */
 int sim_set_warmstart(sim_t* sim, const sim_mlp_t* net, int32_t mode);
+/* Load a trained warm-start network and switch the learned start on (mode 1 of
+ * sim_set_warmstart): weights is the flat FP32 parameter vector in the layout above
+ * (SIM_MLP_PARAMS values, as sim_mlp_get_params writes it), bytes = 4 * SIM_MLP_PARAMS.
+ * The simulator keeps its own copy. Errors: SIM_EINVAL (size, non-finite value). */
+int sim_load_warmstart(sim_t* sim, const void* weights, size_t bytes);
 /* Portfolio start (not from the paper): the simulator's scenes (sim_create_batch) are groups
  * of `copies` identical copies of a scene, consecutive (scenes g * copies .. g * copies +
  * copies - 1 form group g). Copy 0 of each group always runs the cold start; the other
@@ -444,8 +483,9 @@ int sim_get_warmstart_samples(sim_t* sim, int32_t capacity, float* X, float* T, 
  * profile, which the device holds in either s_precision mode, and applies no correction.
  *
  * g, x: device pointers to n_free x 3 FP32 row-major arrays in the solver's internal row
- * order (row k is caller vertex order[k] of sim_plan_get_ordering for the same mesh;
- * pinned vertices have no row). stream: a cudaStream_t, or NULL for the legacy stream.
+ * order (row k is caller vertex order[k] of sim_get_ordering; pinned vertices have no row).
+ * stream: a cudaStream_t, or NULL for the legacy stream. The work runs on the simulator's
+ * device; the calling thread's current device is the same after the call as before it.
  * The call only enqueues work and returns; it calls no allocator. Its scratch (at most
  * 16 MiB: the padded copy of g, z = S g and the partial sums of both products) is one
  * static device array that every GPU loading the library holds until the process exits;
@@ -453,7 +493,9 @@ int sim_get_warmstart_samples(sim_t* sim, int32_t capacity, float* X, float* T, 
  * looks up that array's device address, so make the first call before any stream
  * capture. Every call shares the array and overwrites all of it that it reads; calls that
  * overlap on the GPU (for example on two streams, or from two handles on one device) race.
- * Errors: SIM_EINVAL (null argument), SIM_ECAPACITY, SIM_ECUDA (launch failure).
+ * Errors: SIM_EINVAL (null argument), SIM_ECAPACITY, SIM_ECUDA (a failed launch of this
+ * call, or a sticky device error). A launch error that an earlier call of this library left
+ * pending on the thread is cleared at entry, not reported here.
  */
 int sim_apply_inverse_noalloc(const sim_t* sim, const float* g, float* x, void* stream);
 

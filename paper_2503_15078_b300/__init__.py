@@ -377,8 +377,44 @@ class Simulator:
     def state(self):
         q = np.zeros((self.n_verts, 3))
         v = np.zeros((self.n_verts, 3))
-        _check(lib().sim_get_state(self._h, _dptr(q), _dptr(v)), "sim_get_state")
+        _check(lib().sim_get_state(self._h, _dptr(q), _dptr(v), 0, None, None, None),
+               "sim_get_state")
         return q, v
+
+    def full_state(self):
+        """(q, v, lambda, stats) of the last frame in one call: lambda per contact (n, f1, f2)
+        in the order of contacts()."""
+        q = np.zeros((self.n_verts, 3))
+        v = np.zeros((self.n_verts, 3))
+        cap = int(self.options.contact_capacity)
+        lam = np.zeros((max(cap, 1), 3))
+        n = C.c_int32()
+        s = _abi.SimStats()
+        _check(lib().sim_get_state(self._h, _dptr(q), _dptr(v), max(cap, 1), _dptr(lam),
+                                   C.byref(n), C.byref(s)), "sim_get_state")
+        st = {f: getattr(s, f) for f, _ in s._fields_ if f != "residual"}
+        st["residuals"] = [s.residual[k] for k in range(min(s.n_residuals, _abi.SIM_MAX_RESIDUALS))]
+        return q, v, lam[:min(n.value, cap)], st
+
+    def checkpoint(self):
+        """Everything a later frame depends on, as bytes (sim_get_checkpoint)."""
+        size = C.c_size_t()
+        _check(lib().sim_get_checkpoint(self._h, None, 0, C.byref(size)), "sim_get_checkpoint")
+        buf = C.create_string_buffer(size.value)
+        _check(lib().sim_get_checkpoint(self._h, buf, size.value, C.byref(size)),
+               "sim_get_checkpoint")
+        return buf.raw
+
+    def restore(self, blob):
+        """Continue exactly from a checkpoint() of this simulator (sim_set_checkpoint)."""
+        buf = C.create_string_buffer(bytes(blob), len(blob))
+        _check(lib().sim_set_checkpoint(self._h, buf, len(blob)), "sim_set_checkpoint")
+
+    def load_warmstart(self, theta):
+        """Load a trained network's FP32 parameter vector and use the learned start."""
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(lib().sim_load_warmstart(self._h, t.ctypes.data_as(C.c_void_p), t.nbytes),
+               "sim_load_warmstart")
 
     def set_state(self, q, v):
         q = np.ascontiguousarray(q, dtype=np.float64)
@@ -396,6 +432,17 @@ class Simulator:
         i = _abi.SimPlanInfo()
         _check(lib().sim_get_plan_info(self._h, C.byref(i)), "sim_get_plan_info")
         return {f: getattr(i, f) for f, _ in i._fields_}
+
+    def ordering(self):
+        """(order, parent, first_desc) of the simulator's internal rows: row k is caller
+        vertex order[k] (batch numbering for a batch)."""
+        nf = self.plan_info()["n_free"]
+        order = np.zeros(nf, np.int32)
+        parent = np.zeros(nf, np.int32)
+        fd = np.zeros(nf, np.int32)
+        _check(lib().sim_get_ordering(self._h, _iptr(order), _iptr(parent), _iptr(fd)),
+               "sim_get_ordering")
+        return order, parent, fd
 
     def phase_times(self):
         """Device milliseconds per phase of the most recent frame (event nodes in its graph)."""

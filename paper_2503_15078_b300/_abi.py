@@ -125,12 +125,18 @@ PROTOTYPES = {
     "sim_destroy": (None, [C.c_void_p]),
     "sim_step": (C.c_int, [C.c_void_p, C.c_int32]),
     "sim_synchronize": (C.c_int, [C.c_void_p]),
-    "sim_get_state": (C.c_int, [C.c_void_p, _dp, _dp]),
+    "sim_get_state": (C.c_int, [C.c_void_p, _dp, _dp, C.c_int32, _dp, _ip,
+                                C.POINTER(SimStats)]),
+    "sim_get_checkpoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t,
+                                     C.POINTER(C.c_size_t)]),
+    "sim_set_checkpoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "sim_load_warmstart": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "sim_set_state": (C.c_int, [C.c_void_p, _dp, _dp]),
     "sim_get_stats": (C.c_int, [C.c_void_p, C.POINTER(SimStats)]),
     "sim_get_contacts": (C.c_int, [C.c_void_p, C.c_int32, _ip, _ip, _dp, _dp, _ip]),
     "sim_get_phase_times": (C.c_int, [C.c_void_p, _dp]),
     "sim_get_plan_info": (C.c_int, [C.c_void_p, C.POINTER(SimPlanInfo)]),
+    "sim_get_ordering": (C.c_int, [C.c_void_p, _ip, _ip, _ip]),
     "sim_apply_inverse": (C.c_int, [C.c_void_p, _dp, _dp]),
     "sim_local_project": (C.c_int, [C.c_void_p, _dp, _dp]),
     "sim_get_delassus": (C.c_int, [C.c_void_p, C.c_int32, _dp, _ip, _ip]),

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "devguard.hpp"
 #include "mlp.cuh"
 #include "plan.hpp"
 

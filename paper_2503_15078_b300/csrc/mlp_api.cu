@@ -8,6 +8,7 @@
 #include <numeric>
 #include <vector>
 
+#include "devguard.hpp"
 #include "mlp.cuh"
 #include "silg.h"
 
@@ -95,6 +96,7 @@ const silg::MlpDev* silg_mlp_dev(const sim_mlp_t* net, int* device) {
 
 int sim_mlp_create(int32_t device, int32_t max_batch, sim_mlp_t** out) {
   if (!out || max_batch <= 0) return SIM_EINVAL;
+  silg::DeviceGuard dg;   // the caller's current device is restored on return
   *out = nullptr;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) return SIM_ECUDA;
@@ -135,13 +137,13 @@ int sim_mlp_create(int32_t device, int32_t max_batch, sim_mlp_t** out) {
 
 void sim_mlp_destroy(sim_mlp_t* n) {
   if (!n) return;
-  cudaSetDevice(n->device);
+  silg::DeviceGuard dg(n->device);
   delete n;
 }
 
 int sim_mlp_set_params(sim_mlp_t* n, const float* theta) {
   if (!n || !theta) return SIM_EINVAL;
-  cudaSetDevice(n->device);
+  silg::DeviceGuard dg(n->device);
   cudaMemcpyAsync(n->m.theta, theta, sizeof(float) * silg::kMlpParams, cudaMemcpyHostToDevice, n->stream);
   cudaMemsetAsync(n->m.adam_m, 0, sizeof(float) * silg::kMlpParams, n->stream);
   cudaMemsetAsync(n->m.adam_v, 0, sizeof(float) * silg::kMlpParams, n->stream);
@@ -174,7 +176,7 @@ int sim_mlp_init(sim_mlp_t* n, uint64_t seed) {
 
 int sim_mlp_get_params(const sim_mlp_t* n, float* theta) {
   if (!n || !theta) return SIM_EINVAL;
-  cudaSetDevice(n->device);
+  silg::DeviceGuard dg(n->device);
   cudaStreamSynchronize(n->stream);
   return status_of(cudaMemcpy(theta, n->m.theta, sizeof(float) * silg::kMlpParams, cudaMemcpyDeviceToHost));
 }
@@ -182,7 +184,7 @@ int sim_mlp_get_params(const sim_mlp_t* n, float* theta) {
 int sim_mlp_forward(sim_mlp_t* n, const float* X, int32_t rows, float* Y) {
   if (!n || rows < 0 || (rows > 0 && (!X || !Y))) return SIM_EINVAL;
   if (rows == 0) return SIM_OK;
-  cudaSetDevice(n->device);
+  silg::DeviceGuard dg(n->device);
   std::vector<void*> tmp;
   float* dx = upload_features(n, X, rows, tmp);
   float* dy = upload(n, nullptr, sizeof(float) * rows * silg::kMlpOut, tmp);
@@ -205,7 +207,7 @@ int sim_mlp_gradient(sim_mlp_t* n, const float* X, const float* T, int32_t rows,
                      float* loss) {
   if (!n || !X || !T || rows <= 0) return SIM_EINVAL;
   if (rows > n->m.max_ctas * silg::kMlpRows) return SIM_ECAPACITY;
-  cudaSetDevice(n->device);
+  silg::DeviceGuard dg(n->device);
   std::vector<void*> tmp;
   float* dx = upload_features(n, X, rows, tmp);
   float* dt = upload(n, T, sizeof(float) * rows * silg::kMlpNY, tmp);
@@ -226,7 +228,7 @@ int sim_mlp_train(sim_mlp_t* n, const float* X, const float* T, int32_t rows, in
                   int32_t batch, float lr, uint64_t seed, float* epoch_loss) {
   if (!n || !X || !T || rows <= 0 || epochs < 0 || batch <= 0 || !(lr > 0)) return SIM_EINVAL;
   if (batch > n->m.max_ctas * silg::kMlpRows) return SIM_ECAPACITY;
-  cudaSetDevice(n->device);
+  silg::DeviceGuard dg(n->device);
   std::vector<void*> tmp;
   float* dx = upload_features(n, X, rows, tmp);
   float* dt = upload(n, T, sizeof(float) * rows * silg::kMlpNY, tmp);

@@ -36,6 +36,32 @@ __global__ void k_rows_to_soa(const float* g, float* gs, int n, int n_pad) {
   for (int r = 0; r < 3; ++r) gs[r * n_pad + i] = i < n ? g[3 * i + r] : 0.f;
 }
 
+// Runs the solve with `dev` current; the caller restores its own device afterwards.
+int solve_on_device(silg::DevSim d, int dev, const float* g, float* x, cudaStream_t s) {
+  if (cudaSetDevice(dev) != cudaSuccess) return SIM_ECUDA;
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SIM_ECUDA;
+    g_scratch_addr[dev] = static_cast<float*>(p);
+  }
+  const size_t n_vec = align_up(3 * (size_t)d.n_pad, 64);
+  const size_t n_p1 = align_up((size_t)d.n_seg1 * 3 * silg::kRowGroup, 64);
+  float* base = g_scratch_addr[dev];
+  d.gvec = base;
+  d.zvec = base + n_vec;
+  d.p1_part = base + 2 * n_vec;
+  d.p2_part = base + 2 * n_vec + n_p1;
+  d.xout = x;
+  // an error left pending by an earlier launch of this library on this thread is not this
+  // call's: clear it so that the checks below see only the launches made here (a sticky
+  // device error persists and fails them)
+  (void)cudaGetLastError();
+  k_rows_to_soa<<<(d.n_pad + 255) / 256, 256, 0, s>>>(g, d.gvec, d.n, d.n_pad);
+  if (cudaGetLastError() != cudaSuccess) return SIM_ECUDA;
+  silg::launch_solve(d, s, silg::kOutX);
+  return cudaGetLastError() == cudaSuccess ? SIM_OK : SIM_ECUDA;
+}
+
 }  // namespace
 
 extern "C" int sim_apply_inverse_noalloc(const sim_t* sim, const float* g, float* x, void* stream) {
@@ -49,20 +75,11 @@ extern "C" int sim_apply_inverse_noalloc(const sim_t* sim, const float* g, float
   const size_t n_p1 = align_up((size_t)d.n_seg1 * 3 * silg::kRowGroup, 64);
   const size_t n_p2 = align_up((size_t)d.n_seg2 * 3 * silg::kTileW, 64);
   if (2 * n_vec + n_p1 + n_p2 > kNoAllocFloats) return SIM_ECAPACITY;
-  if (cudaSetDevice(dev) != cudaSuccess) return SIM_ECUDA;
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SIM_ECUDA;
-    g_scratch_addr[dev] = static_cast<float*>(p);
-  }
-  float* base = g_scratch_addr[dev];
-  d.gvec = base;
-  d.zvec = base + n_vec;
-  d.p1_part = base + 2 * n_vec;
-  d.p2_part = base + 2 * n_vec + n_p1;
-  d.xout = x;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  k_rows_to_soa<<<(d.n_pad + 255) / 256, 256, 0, s>>>(g, d.gvec, d.n, d.n_pad);
-  silg::launch_solve(d, s, silg::kOutX);
-  return cudaGetLastError() == cudaSuccess ? SIM_OK : SIM_ECUDA;
+  int caller_dev = -1;
+  if (cudaGetDevice(&caller_dev) != cudaSuccess) return SIM_ECUDA;
+  const int status = solve_on_device(d, dev, g, x, static_cast<cudaStream_t>(stream));
+  // the caller's current device is left as it was
+  if (caller_dev != dev && cudaSetDevice(caller_dev) != cudaSuccess && status == SIM_OK)
+    return SIM_ECUDA;
+  return status;
 }

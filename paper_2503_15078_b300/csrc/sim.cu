@@ -1112,6 +1112,16 @@ int sim_get_plan_info(const sim_t* s, sim_plan_info* info) {
   return SIM_OK;
 }
 
+int sim_get_ordering(const sim_t* s, int32_t* order, int32_t* parent, int32_t* first_desc) {
+  if (!s) return SIM_EINVAL;
+  const silg::Plan& p = s->plan;
+  const size_t nf = (size_t)p.n_free;
+  if (order) std::memcpy(order, p.order.data(), sizeof(int32_t) * nf);
+  if (parent) std::memcpy(parent, p.parent.data(), sizeof(int32_t) * nf);
+  if (first_desc) std::memcpy(first_desc, p.first_desc.data(), sizeof(int32_t) * nf);
+  return SIM_OK;
+}
+
 namespace {
 
 double mean_edge(const sim_mesh& m) {
@@ -1184,6 +1194,7 @@ int check_options(const sim_options* o) {
 // replaces every scene's margin (sim_create's option).
 int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_options* opts,
                   double margin_override, sim_t** out) {
+  silg::DeviceGuard dg;   // creation selects the simulator's device; the caller's returns
   if (!out) return SIM_EINVAL;
   *out = nullptr;
   if (!scenes || n_scenes < 1) return SIM_EINVAL;
@@ -1479,17 +1490,21 @@ const silg::MlpDev* silg_mlp_dev(const sim_mlp_t* net, int* device);
 
 int sim_set_warmstart(sim_t* s, const sim_mlp_t* net, int32_t mode) {
   if (!s || mode < 0 || mode > 2 || (mode == 1 && !net)) return SIM_EINVAL;
-  cudaSetDevice(s->device);
+  silg::DeviceGuard dg(s->device);
   cudaError_t e = cudaStreamSynchronize(s->launch);
   if (e != cudaSuccess) return cuda_status(e);
   if (mode == 1) {
     int dev = -1;
     const silg::MlpDev* m = silg_mlp_dev(net, &dev);
     if (!m || dev != s->device) return SIM_EINVAL;
-    e = cudaMemcpy(s->d.ws_net.theta, m->theta, sizeof(float) * silg::kMlpParams, cudaMemcpyDeviceToDevice);
+    // on the frame's stream, finished before returning: the next frame reads the copy and
+    // the caller may destroy the network right away
+    e = cudaMemcpyAsync(s->d.ws_net.theta, m->theta, sizeof(float) * silg::kMlpParams,
+                        cudaMemcpyDeviceToDevice, s->launch);
     if (e == cudaSuccess)
-      e = cudaMemcpy(s->d.ws_net.w_t, m->w_t, sizeof(__nv_bfloat16) * silg::kWTElems,
-                     cudaMemcpyDeviceToDevice);
+      e = cudaMemcpyAsync(s->d.ws_net.w_t, m->w_t, sizeof(__nv_bfloat16) * silg::kWTElems,
+                          cudaMemcpyDeviceToDevice, s->launch);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->launch);
     if (e != cudaSuccess) return cuda_status(e);
   }
   s->d.ws_mode = mode;   // graphs are cached per mode; the network's weights are read at launch
@@ -1528,7 +1543,7 @@ int sim_set_portfolio(sim_t* s, int32_t copies) {
         }
       }
   }
-  cudaSetDevice(s->device);
+  silg::DeviceGuard dg(s->device);
   cudaError_t e = cudaStreamSynchronize(s->launch);
   if (e != cudaSuccess) return cuda_status(e);
   if (s->d.pf_copies != copies) {
@@ -1545,7 +1560,7 @@ int sim_set_portfolio(sim_t* s, int32_t copies) {
 
 int sim_get_warmstart_samples(sim_t* s, int32_t capacity, float* X, float* T, int32_t* n_out) {
   if (!s || !n_out || capacity < 0) return SIM_EINVAL;
-  cudaSetDevice(s->device);
+  silg::DeviceGuard dg(s->device);
   int st = sync_and_check(s);
   if (st == SIM_ECUDA) return st;
   int c = 0;
@@ -1590,7 +1605,7 @@ int sim_get_tuning(const sim_t* s, sim_tuning* out) {
 
 int sim_get_scene_residuals(sim_t* s, int32_t capacity, double* out) {
   if (!s || !out || capacity < 0) return SIM_EINVAL;
-  cudaSetDevice(s->device);
+  silg::DeviceGuard dg(s->device);
   int st = sync_and_check(s);
   if (st == SIM_ECUDA) return st;
   const int K = frame_iters(s), S = s->plan.n_scenes;
@@ -1609,7 +1624,7 @@ int sim_get_scene_residuals(sim_t* s, int32_t capacity, double* out) {
 
 void sim_destroy(sim_t* s) {
   if (!s) return;
-  cudaSetDevice(s->device);
+  silg::DeviceGuard dg(s->device);
   if (s->launch) cudaStreamSynchronize(s->launch);
   delete s;
 }
@@ -1620,7 +1635,7 @@ int sim_step(sim_t* s, int32_t n_iters) {
   const bool to_tol = n_iters <= 0 && s->d.res_tol > 0.0;
   int K = to_tol ? 0 : (n_iters > 0 ? n_iters : s->n_iters_default);
   if (K > silg::kMaxIters) return SIM_EINVAL;
-  cudaSetDevice(s->device);
+  silg::DeviceGuard dg(s->device);
   cudaGraphExec_t exec = nullptr;
   int st = get_graph(s, K, &exec);
   if (st != SIM_OK) return st;
@@ -1635,13 +1650,14 @@ int sim_step(sim_t* s, int32_t n_iters) {
 
 int sim_synchronize(sim_t* s) {
   if (!s) return SIM_EINVAL;
-  cudaSetDevice(s->device);
+  silg::DeviceGuard dg(s->device);
   return sync_and_check(s);
 }
 
-int sim_get_state(sim_t* s, double* q, double* v) {
-  if (!s) return SIM_EINVAL;
-  cudaSetDevice(s->device);
+int sim_get_state(sim_t* s, double* q, double* v, int32_t capacity, double* lambda,
+                  int32_t* n_contacts, sim_stats* stats) {
+  if (!s || capacity < 0 || (lambda && capacity == 0)) return SIM_EINVAL;
+  silg::DeviceGuard dg(s->device);
   const Plan& p = s->plan;
   const size_t m = 3 * (size_t)p.n_verts;
   // both copies on the frame's stream into page-locked staging, then one wait
@@ -1658,12 +1674,22 @@ int sim_get_state(sim_t* s, double* q, double* v) {
       for (int r = 0; r < 3; ++r) dsts[k][3 * (size_t)vv + r] = srcs[k][iv + r];
     }
   }
+  if (lambda || n_contacts) {
+    int32_t c = 0;
+    const int sc = sim_get_contacts(s, lambda ? capacity : 0, nullptr, nullptr, lambda, nullptr, &c);
+    if (sc == SIM_ECUDA) return sc;
+    if (n_contacts) *n_contacts = c;
+  }
+  if (stats) {
+    const int ss = sim_get_stats(s, stats);
+    if (ss == SIM_ECUDA) return ss;
+  }
   return st;
 }
 
 int sim_set_state(sim_t* s, const double* q, const double* v) {
   if (!s || !q || !v) return SIM_EINVAL;
-  cudaSetDevice(s->device);
+  silg::DeviceGuard dg(s->device);
   // the staging may still feed an earlier copy: wait for the frame's stream first
   cudaError_t e = cudaStreamSynchronize(s->launch);
   if (e != cudaSuccess) return cuda_status(e);
@@ -1693,9 +1719,112 @@ int sim_set_state(sim_t* s, const double* q, const double* v) {
   return cuda_status(e);
 }
 
+namespace {
+// A checkpoint: this header, then q_t and v_t (3 n_all doubles each, internal order), the
+// anchors' current targets (3 n_anc doubles), and the previous-frame contact record the warm
+// starts read (per free vertex: contact flag and obstacle as int32, the impulse D^T lambda in
+// world coordinates as 3 doubles, the move along the normal as a double).
+struct CheckpointHeader {
+  uint64_t magic;        // "SILGCKP1"
+  uint64_t signature;    // hash of every scene's inputs: a checkpoint fits its simulator only
+  int64_t frame;
+  int32_t n_all, n, n_anc, version;
+};
+constexpr uint64_t kCkptMagic = 0x31504b43474c4953ull;
+
+uint64_t checkpoint_signature(const sim_s* s) {
+  uint64_t h = 1469598103934665603ull ^ (uint64_t)s->scene_sig.size();
+  for (uint64_t x : s->scene_sig) h = (h ^ x) * 1099511628211ull;
+  return h;
+}
+
+size_t checkpoint_bytes(const sim_s* s) {
+  const size_t na = (size_t)s->d.n_all, n = (size_t)s->d.n, nanc = (size_t)s->d.n_anc;
+  return sizeof(CheckpointHeader) + sizeof(double) * (6 * na + 3 * nanc + 4 * n) +
+         sizeof(int32_t) * 2 * n;
+}
+
+// the device arrays of a checkpoint in their order: pointer and bytes
+std::vector<std::pair<void*, size_t>> checkpoint_parts(sim_s* s) {
+  const size_t na = (size_t)s->d.n_all, n = (size_t)s->d.n, nanc = (size_t)s->d.n_anc;
+  return {{s->d.q_t, sizeof(double) * 3 * na},
+          {s->d.v_t, sizeof(double) * 3 * na},
+          {s->d.anc_pos, sizeof(double) * 3 * nanc},
+          {s->d.prev_valid, sizeof(int32_t) * n},
+          {s->d.prev_obst, sizeof(int32_t) * n},
+          {s->d.prev_force, sizeof(double) * 3 * n},
+          {s->d.prev_move, sizeof(double) * n}};
+}
+}  // namespace
+
+int sim_get_checkpoint(sim_t* s, void* buf, size_t capacity, size_t* bytes) {
+  if (!s || (!buf && !bytes)) return SIM_EINVAL;
+  const size_t need = checkpoint_bytes(s);
+  if (bytes) *bytes = need;
+  if (!buf) return SIM_OK;
+  if (capacity < need) return SIM_ECAPACITY;
+  silg::DeviceGuard dg(s->device);
+  int st = sync_and_check(s);
+  if (st == SIM_ECUDA) return st;
+  CheckpointHeader hd{kCkptMagic, checkpoint_signature(s), s->frame, s->d.n_all, s->d.n,
+                      s->d.n_anc, 1};
+  char* out = static_cast<char*>(buf);
+  std::memcpy(out, &hd, sizeof(hd));
+  size_t off = sizeof(hd);
+  cudaError_t e = cudaSuccess;
+  for (auto& part : checkpoint_parts(s)) {
+    if (part.second && e == cudaSuccess)
+      e = cudaMemcpyAsync(out + off, part.first, part.second, cudaMemcpyDeviceToHost, s->launch);
+    off += part.second;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->launch);
+  return e != cudaSuccess ? cuda_status(e) : st;
+}
+
+int sim_set_checkpoint(sim_t* s, const void* buf, size_t bytes) {
+  if (!s || !buf) return SIM_EINVAL;
+  CheckpointHeader hd;
+  if (bytes != checkpoint_bytes(s)) return SIM_EINVAL;
+  std::memcpy(&hd, buf, sizeof(hd));
+  if (hd.magic != kCkptMagic || hd.version != 1 || hd.signature != checkpoint_signature(s) ||
+      hd.n_all != s->d.n_all || hd.n != s->d.n || hd.n_anc != s->d.n_anc || hd.frame < 0)
+    return SIM_EINVAL;
+  silg::DeviceGuard dg(s->device);
+  cudaError_t e = cudaStreamSynchronize(s->launch);
+  if (e != cudaSuccess) return cuda_status(e);
+  const char* in = static_cast<const char*>(buf);
+  size_t off = sizeof(hd);
+  for (auto& part : checkpoint_parts(s)) {
+    if (part.second && e == cudaSuccess)
+      e = cudaMemcpyAsync(part.first, in + off, part.second, cudaMemcpyHostToDevice, s->launch);
+    off += part.second;
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d.err, 0, sizeof(int), s->launch);
+  // the caller's buffer is read before returning
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->launch);
+  if (e != cudaSuccess) return cuda_status(e);
+  s->frame = hd.frame;
+  return SIM_OK;
+}
+
+int sim_load_warmstart(sim_t* s, const void* weights, size_t bytes) {
+  if (!s || !weights || bytes != sizeof(float) * SIM_MLP_PARAMS) return SIM_EINVAL;
+  std::vector<float> theta(SIM_MLP_PARAMS);
+  std::memcpy(theta.data(), weights, bytes);
+  for (float x : theta)
+    if (!std::isfinite(x)) return SIM_EINVAL;
+  sim_mlp_t* net = nullptr;
+  int st = sim_mlp_create(s->device, 1, &net);
+  if (st != SIM_OK) return st;
+  st = sim_mlp_set_params(net, theta.data());
+  if (st == SIM_OK) st = sim_set_warmstart(s, net, 1);
+  sim_mlp_destroy(net);
+  return st;
+}
+
 int sim_get_stats(sim_t* s, sim_stats* out) {
   if (!s || !out) return SIM_EINVAL;
-  cudaSetDevice(s->device);
+  silg::DeviceGuard dg(s->device);
   int st = sync_and_check(s);
   if (st == SIM_ECUDA) return st;
   if (frame_iters(s) < 0) return SIM_ECUDA;
@@ -1719,7 +1848,7 @@ int sim_get_stats(sim_t* s, sim_stats* out) {
 
 int sim_get_phase_times(sim_t* s, double* ms) {
   if (!s || !ms) return SIM_EINVAL;
-  cudaSetDevice(s->device);
+  silg::DeviceGuard dg(s->device);
   for (int k = 0; k < SIM_NUM_PHASES; ++k) ms[k] = 0.0;
   if (s->frame == 0 || s->last_iters == 0) return SIM_OK;
   auto el = [&](int a, int b) {
@@ -1759,7 +1888,7 @@ int sim_get_phase_times(sim_t* s, double* ms) {
 int sim_get_contacts(sim_t* s, int32_t capacity, int32_t* vertex, int32_t* obstacle,
                      double* lambda, double* frame, int32_t* n_out) {
   if (!s || !n_out || capacity < 0) return SIM_EINVAL;
-  cudaSetDevice(s->device);
+  silg::DeviceGuard dg(s->device);
   int st = sync_and_check(s);
   if (st == SIM_ECUDA) return st;
   int c = 0;
@@ -1797,7 +1926,7 @@ int sim_get_contacts(sim_t* s, int32_t capacity, int32_t* vertex, int32_t* obsta
 
 int sim_apply_inverse(sim_t* s, const double* b, double* x) {
   if (!s || !b || !x) return SIM_EINVAL;
-  cudaSetDevice(s->device);
+  silg::DeviceGuard dg(s->device);
   const Plan& p = s->plan;
   const int n = p.n_free, np = p.n_pad;
   std::vector<float> g(3 * (size_t)np, 0.f);
@@ -1827,7 +1956,7 @@ int sim_apply_inverse(sim_t* s, const double* b, double* x) {
 
 int sim_local_project(sim_t* s, const double* q, double* pout) {
   if (!s || !q || !pout) return SIM_EINVAL;
-  cudaSetDevice(s->device);
+  silg::DeviceGuard dg(s->device);
   const Plan& p = s->plan;
   const int n_all = p.n_verts, T = p.n_tets;
   std::vector<double> qi(3 * (size_t)n_all);
@@ -1848,7 +1977,7 @@ int sim_local_project(sim_t* s, const double* q, double* pout) {
 
 int sim_get_delassus(sim_t* s, int32_t capacity, double* Wt, int32_t* cv_vertex, int32_t* n_out) {
   if (!s || !n_out || capacity < 0) return SIM_EINVAL;
-  cudaSetDevice(s->device);
+  silg::DeviceGuard dg(s->device);
   int st = sync_and_check(s);
   if (st == SIM_ECUDA) return st;
   int m = 0;

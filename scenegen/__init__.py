@@ -302,6 +302,21 @@ def star_pull(n_side: int = 42, layers: int = 27, spacing: float = 0.01, seed: i
                  contact_margin=0.5 * spacing, n_frames=n_frames, spacing=spacing)
 
 
+def star_placed(scene: Scene, placement: float = 0.1025):
+    """A contact state of a star_pull scene (pure geometry, no simulation): the rest shape
+    translated along +x so that its leading face lies ``placement`` metres beyond the axes of
+    the first cylinder row, every vertex moving at the pull speed. At 0.1025 m on the 42 x 42
+    x 27 star the tips are inside the first row's cylinders: 810 contacts at 810 distinct
+    vertices on the predicted positions. Returns (q, v)."""
+    q = scene.q0.copy()
+    x_front = scene.X[:, 0].max()
+    first_col = min(o.p[0] for o in scene.obstacles)
+    q[:, 0] += (first_col - x_front) + placement
+    v = np.zeros_like(q)
+    v[:, 0] = scene.handle_vel[0]
+    return q, v
+
+
 def anchored_handle(scene: Scene, compliance: float = 0.0) -> Scene:
     """The same scene with its pinned handle replaced by anchors: every pinned vertex
     becomes a free vertex tied to a target that starts at its initial position and moves

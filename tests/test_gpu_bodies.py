@@ -149,22 +149,42 @@ def test_stack_on_an_incline_sticks_or_slides(mu_ground, moving):
 
 def test_stress_columns_in_a_full_batch_match_the_oracle():
     # the stress workload's 128 two-box columns of 12^3 vertices in one simulator (one
-    # cluster of one CTA per scene, most W~ rows read from L2): its first scene against the
-    # oracle, within 10x of the oracle's own float32-CR deviation (measured: 4.2e-5 against
-    # 2.1e-5)
+    # cluster of one CTA per scene, most W~ rows read from L2): the first, a middle and the
+    # last scene against the oracle, within 10x of the oracle's own float32-CR deviation
+    # (measured on scene 0: 4.2e-5 against 2.1e-5). Their contact lists must equal the
+    # oracle's exactly: the batch's 442k vertices are scanned in tiles of 4,096 entries, and
+    # the middle and last scenes lie in tiles far beyond the first, so a wrong tile offset
+    # or total would shift their contacts, contact vertices, Y rows or impulses.
+    from oracle.contact import surface_triangles
     scenes = sg.stack_stress()
     q0 = np.concatenate([sc.q0 for sc in scenes])
     sim = Simulator(scenes, contact_capacity=65536)
     sim.set_state(q0, np.zeros_like(q0))
     sim.step()
     qg, _ = sim.state()
+    ct = sim.contacts()
     off = sim.scene_offsets
-    for k in (0,):
+    assert off[-1] > 16 * 4096
+    n_obs = [len(sc.obstacles) for sc in scenes]
+    n_tri = [len(surface_triangles(sc.X, sc.tets)) for sc in scenes]
+    obs_total = sum(n_obs)
+    for k in (0, len(scenes) // 2, len(scenes) - 1):
         sc = scenes[k]
         o = Oracle(sc)
         v0 = np.zeros_like(sc.q0)
         opts = OracleOptions(n_iters=sc.n_iters, n_cr=sc.n_cr)
         q, _, info = o.frame(sc.q0, v0, opts)
+        # the scene's contacts in the batch, ids translated to the scene's own numbering
+        sel = (ct["vertex"] >= off[k]) & (ct["vertex"] < off[k + 1])
+        keys_g = []
+        for vtx, ob in zip(ct["vertex"][sel].tolist(), ct["obstacle"][sel].tolist()):
+            if ob < obs_total:
+                ob -= sum(n_obs[:k])
+            else:
+                ob = ob - obs_total - sum(n_tri[:k]) + n_obs[k]
+            keys_g.append((vtx - int(off[k]), ob))
+        keys_o = [(c["vertex"], c["obstacle"]) for c in info["contacts"]]
+        assert keys_g == keys_o and len(keys_o) > 100, (k, len(keys_g), len(keys_o))
         dev32 = _relerr(_cr32_deviation(o, sc, sc.q0, v0, opts) - sc.q0, q - sc.q0)
         err = _relerr(qg[off[k]:off[k + 1]] - sc.q0, q - sc.q0)
         print(f"scene {k}: {len(info['contacts'])} contacts, error {err:.2e}, float32 "

@@ -95,7 +95,13 @@ def test_frame_with_contact_matches_oracle(model):
     assert keys_g == keys_o and len(keys_o) > 3
     assert _relerr(qg, q) < REL
     lam_o, lam_g = info["lam"], ct["lam"]
-    assert _relerr(lam_g, lam_o) < 1e-3, _relerr(lam_g, lam_o)
+    # contacts whose normal impulse is rounding residue (|lambda_n| < 1e-6 max) sit on the
+    # friction indicator's flip (App. B.2) and are left out; the rest agree to 1e-5
+    keep = np.abs(lam_o[:, 0]) >= 1e-6 * np.abs(lam_o[:, 0]).max()
+    print(f"\nlambda rel. error {_relerr(lam_g[keep], lam_o[keep]):.2e}, "
+          f"{int((~keep).sum())} of {len(keep)} excluded")
+    assert keep.sum() >= len(keep) // 2
+    assert _relerr(lam_g[keep], lam_o[keep]) < REL, _relerr(lam_g[keep], lam_o[keep])
     st = sim.stats()
     assert st["n_contacts"] == len(keys_o)
     assert abs(st["residuals"][-1] - info["residuals"][-1]) < 1e-4 + 0.05 * info["residuals"][-1]
@@ -170,8 +176,9 @@ def test_trajectory_resynchronised_frames_match_oracle():
 def test_trajectory_free_running_stays_close():
     # Free-running trajectories over the 100 frames of the 6^3 drop: contact activation and
     # stick/slip switches are not smooth in the state, so rounding differences grow at
-    # impacts; bound penetration (1e-3 of the body size) and energy (1% of the initial
-    # energy), not pointwise agreement.
+    # impacts; the trajectory bounds are on penetration (1e-3 of the body size), on the
+    # per-frame residual (1e-4) and on energy (1e-3 relative to the initial energy), not on
+    # pointwise agreement.
     sc = sg.cube_drop(m=6, seed=0)
     frames = 100
     o = Oracle(sc)
@@ -180,12 +187,21 @@ def test_trajectory_free_running_stays_close():
     sim.set_state(q, v)
     L = sc.bbox_diagonal
     e0 = o.energy(q, v)
+    d_pen = d_res = d_en = 0.0
     for f in range(frames):
         q, v, info = o.frame(q, v)
         sim.step()
         qg, vg = sim.state()
-        assert abs(o.max_penetration(qg) - o.max_penetration(q)) <= 1e-3 * L
-        assert abs(o.energy(qg, vg) - o.energy(q, v)) <= 1e-2 * abs(e0)
+        d_pen = max(d_pen, abs(o.max_penetration(qg) - o.max_penetration(q)) / L)
+        d_en = max(d_en, abs(o.energy(qg, vg) - o.energy(q, v)) / abs(e0))
+        r_o = info["residuals"][-1] if info["residuals"] else 0.0
+        r_g = sim.stats()["residuals"][-1] if info["residuals"] else 0.0
+        d_res = max(d_res, abs(r_g - r_o))
+    print(f"\nfree-running 100 frames: penetration {d_pen:.2e} L, residual {d_res:.2e}, "
+          f"energy {d_en:.2e} E0, final rel. position {_relerr(qg, q):.2e}")
+    assert d_pen <= 1e-3
+    assert d_res <= 1e-4
+    assert d_en <= 1e-3
     assert _relerr(qg, q) < 1e-2
     sim.close()
 
@@ -257,7 +273,8 @@ def test_device_wait_timeout_is_reported_and_results_stay_correct():
     sim = Simulator(sc, spin_limit=1)
     sim.step()
     q = np.zeros((sc.n_verts, 3))
-    status = lib().sim_get_state(sim.handle, q.ctypes.data_as(C.POINTER(C.c_double)), None)
+    status = lib().sim_get_state(sim.handle, q.ctypes.data_as(C.POINTER(C.c_double)), None,
+                                 0, None, None, None)
     assert status in (0, -6), status
     assert _relerr(q, q_ref) < 1e-6
     sim.close()
