@@ -3,15 +3,15 @@
 
 Workload (synthetic stand-in for the paper's "crossing gingerbread man" teaser scene:
 58.5k DoFs, 800 contacts, 5 local-global iterations per frame): an extruded five-point
-star (19,008 vertices, 57,024 DoFs, 96,252 tetrahedra), stable Neo-Hookean E = 1e6 Pa,
+star (19,926 vertices, 59,778 DoFs, 101,400 tetrahedra), stable Neo-Hookean E = 1e6 Pa,
 nu = 0.45, rho = 1000, its leading cap pinned to a handle moving at 0.5 m/s through a
 seeded 4 x 4 array of fixed cylinders (mu = 0.3); h = 1/60 s, 5 iterations and 10 CR
 iterations per frame, FP32 device arithmetic (FP64 state and contact logic).
 
 A step is one frame (collision, Delassus operator, 5 local-global iterations,
 integration) from one fixed contact state: the rest-shape star translated along the pull
-direction until its leading face is 10.25 cm beyond the axes of the first cylinder row,
-moving at the pull speed (810 contacts at 810 contact vertices after the frame's
+direction until its leading face is 9.4 cm beyond the axes of the first cylinder row,
+moving at the pull speed (837 contacts at 837 contact vertices after the frame's
 prediction step; the paper's scene peaks at 800); every timed step
 replays that frame. The state is plain geometry of the scene, so both arms (and the CPU
 baseline) start from exactly the same input. Each step's device time comes from
@@ -49,16 +49,18 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--placement", type=float, default=0.1025,
+    ap.add_argument("--placement", type=float, default=0.094,
                     help="metres the star is moved past first touching the cylinders")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--n-side", type=int, default=42)
+    ap.add_argument("--n-side", type=int, default=43)
     ap.add_argument("--s-precision", choices=["fp32", "bf16"], default="fp32",
                     help="storage of the S~ values (bf16: FP32 accumulation)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the timing of the paper's variants on the star frame")
     ap.add_argument("--no-warmstart", action="store_true",
                     help="skip the learned-vs-plain frame time to residual 1e-4")
+    ap.add_argument("--no-trajectory", action="store_true",
+                    help="skip the 300-frame pulls through the cylinders (seeds 0-4)")
     ap.add_argument("--workload", choices=["star", "batch64", "stack"], default="star",
                     help="star: the 57k-DoF pulled star (the headline); batch64: 64 uneven "
                          "cubes on tilted planes in one simulator; stack: the stress case, "
@@ -353,7 +355,8 @@ def variants_timing(scene, q0, v0, steps, flush):
     import scenegen as sg
     from paper_2503_15078_b300 import Simulator
     cases = {"minmap": dict(ncp="minmap"), "mass_precond": dict(precond="mass"),
-             "admm_pd": dict(local_solver="admm"), "anchored_handle": {}}
+             "admm_pd": dict(local_solver="admm"), "anchored_handle": {},
+             "cr_two_exchanges": dict(cr_exchanges=2)}
     out = {}
     for name, kw in cases.items():
         sc, v = scene, v0.copy()
@@ -448,6 +451,74 @@ def twisting_bar_timing(steps, flush):
     return out
 
 
+def pull_trajectory(n_side, frames, seeds, steps, flush):
+    """The config-2 scene as a trajectory: the star's pinned cap pulled at 0.5 m/s through the
+    seeded 4 x 4 cylinder field for `frames` frames (5 local-global and 10 CR iterations each)
+    for every seed, from rest, in the production graph. Per seed: contact counts (max, mean
+    over frames with contact), the last iteration's residual R (max, median over contact
+    frames), the largest penetration (as a fraction of the scene's residual length),
+    finiteness, and the device time per frame. Then the frame with the most contacts of seed
+    0 is replayed `steps` times from its start state (L2 flushed before each) and timed as
+    ms per local-global iteration."""
+    import numpy as np
+    import torch
+    import scenegen as sg
+    from paper_2503_15078_b300 import SimError, Simulator
+    out = {"frames": frames, "seeds": list(seeds), "per_seed": []}
+    peak = None
+    for seed in seeds:
+        sc = sg.star_pull(n_side=n_side, seed=seed)
+        sim = Simulator(sc, autotune=0, phase_marks=0)
+        L = sc.bbox_diagonal
+        cts, res, pen, ms, finite = [], [], [], [], True
+        prev = sim.state()
+        for f in range(frames):
+            try:
+                sim.step()
+                st = sim.stats()
+            except SimError:
+                finite = False
+                break
+            ms.append(sum(sim.phase_times().values()))
+            cts.append(st["n_contacts"])
+            if st["n_contacts"]:
+                res.append(st["residuals"][-1])
+                pen.append(st["max_penetration"] / L)
+            if seed == seeds[0] and (peak is None or st["n_contacts"] > peak[0]):
+                peak = (st["n_contacts"], f, prev)
+            if seed == seeds[0]:
+                prev = sim.state()
+        q, v = sim.state()
+        finite = finite and bool(np.all(np.isfinite(q)) and np.all(np.isfinite(v)))
+        cf = [c for c in cts if c]
+        out["per_seed"].append({
+            "seed": seed, "finite": finite, "frames_run": len(cts),
+            "contact_frames": len(cf), "max_contacts": max(cts) if cts else 0,
+            "mean_contacts": round(float(np.mean(cf)), 1) if cf else 0.0,
+            "max_residual": float(f"{max(res):.3e}") if res else 0.0,
+            "median_residual": float(f"{np.median(res):.3e}") if res else 0.0,
+            "max_penetration_over_L": float(f"{max(pen):.3e}") if pen else 0.0,
+            "mean_frame_ms": round(float(np.mean(ms)), 4) if ms else None,
+            "max_frame_ms": round(float(np.max(ms)), 4) if ms else None})
+        sim.close()
+    if peak is not None and peak[0] > 0:
+        sc = sg.star_pull(n_side=n_side, seed=seeds[0])
+        sim = Simulator(sc, autotune=1, phase_marks=0)
+        times = []
+        for k in range(3 + steps):
+            sim.set_state(*peak[2])
+            flush.zero_()
+            torch.cuda.synchronize()
+            sim.step()
+            if k >= 3:
+                times.append(sum(sim.phase_times().values()) / sc.n_iters)
+        out["peak_frame"] = {"seed": seeds[0], "frame": peak[1], "contacts": peak[0],
+                             "ms_per_iter": round(statistics.mean(times), 5),
+                             "final_residual": float(f"{sim.stats()['residuals'][-1]:.3e}")}
+        sim.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -461,14 +532,20 @@ def run_ours(args):
         dist.init_process_group("nccl")
     batch = args.workload in ("batch64", "stack")
     stack = args.workload == "stack"
-    if stack:
-        scenes = sg.stack_stress(seed=rank)
+    n_batch = 0
+    if batch:
+        # one batch, split over the ranks by scene (nnz(S~)-balanced, no data-path exchange);
+        # each rank simulates its own scenes in one simulator
+        from paper_2503_15078_b300 import shard
+        scenes = sg.stack_stress(seed=0) if stack else sg.batch(n_scenes=64, seed=0)
+        n_batch = len(scenes)
+        if world > 1:
+            _, scenes = shard.shard(scenes, rank, world)
         scene = scenes[0]
+    if stack:
         q0 = np.concatenate([sc.q0 for sc in scenes])
         v0 = np.zeros_like(q0)
     elif batch:
-        scenes = sg.batch(n_scenes=64, seed=rank)
-        scene = scenes[0]
         if args.s_precision == "fp32" and "--s-precision" not in sys.argv:
             args.s_precision = "bf16"   # the batch workload stores S~ in BF16 by definition
         q0, v0 = batch_state(scenes)
@@ -570,7 +647,7 @@ def run_ours(args):
         "warmup": max(3, args.warmup),
         "ms_per_step": round(mean_frame, 5),
         "higher_is_better": False,
-        "scaling": "weak",
+        "scaling": "strong" if batch else "weak",
         "vs_baseline": None,
         "dtype": "bf16/f32" if bf16 else "f32",
         "data": "synthetic",
@@ -588,13 +665,16 @@ def run_ours(args):
                 "each placed a quarter lattice spacing into its plane; one simulator, "
                 "S~ in BF16 + FP32 correction, 5 L-G + 10 CR iterations per frame"
                 if batch else
-                "star_pull: extruded 5-point star 42x42x27 lattice, 19008 verts / "
-                "57024 DoFs / 96252 tets, SNH E=1e6 nu=0.45, pinned cap pulled at "
+                f"star_pull: extruded 5-point star {args.n_side}x{args.n_side}x27 lattice, "
+                f"{sim.n_verts} verts / {3 * sim.n_verts} DoFs / {sim.n_tets} tets, SNH E=1e6 "
+                "nu=0.45, pinned cap pulled at "
                 "0.5 m/s through 4x4 seeded cylinders mu=0.3, h=1/60, 5 L-G + 10 CR "
                 "iterations per frame; every step replays one frame from the star placed "
-                "10.25 cm into the first cylinder row (810 contacts)"),
+                f"{100 * args.placement:.2f} cm into the first cylinder row "
+                f"({round(statistics.mean(contacts))} contacts)"),
             "dofs": 3 * sim.n_verts,
-            "scenes": sim.n_scenes,
+            "scenes": n_batch if batch else 1,
+            "scenes_this_rank": sim.n_scenes,
             "free_dofs": 3 * n_free,
             "tets": sim.n_tets,
             "contacts_mean": round(statistics.mean(contacts), 1),
@@ -607,7 +687,8 @@ def run_ours(args):
                                          "pass2_unroll", "pass1_balance", "pass2_balance")},
             "refine": args.refine if bf16 else None,
             "l2": "flushed (256 MB write) before every timed step",
-            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "parallelism": (f"scene shards x{world} of one {n_batch}-scene batch" if batch
+                            else f"replicas x{world}") if world > 1 else "single GPU",
         },
         "phases_ms_per_frame": {k: round(v, 5) for k, v in phase_mean.items()},
         "instrumented_ms_per_step": round(instrumented_frame, 5),
@@ -633,6 +714,9 @@ def run_ours(args):
     }
     if rank == 0 and not batch and not args.no_variants:
         out["variants"] = variants_timing(scene, q0, v0, min(args.steps, 10), flush)
+    if rank == 0 and not batch and not args.no_trajectory:
+        out["pull_trajectory"] = pull_trajectory(args.n_side, 300, range(5),
+                                                 min(args.steps, 20), flush)
     if rank == 0 and not batch and not args.no_warmstart:
         out["warmstart"] = warmstart_ab()
     if rank == 0:
@@ -661,7 +745,8 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT,
            "n_gpus": world, "steps": len(vals), "warmup": max(1, args.warmup),
            "higher_is_better": False, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "star_pull 57024 DoFs (FP64 CPU oracle, bounded sample)"},
+           "config": {"workload": f"star_pull {3 * scene.n_verts} DoFs (FP64 CPU oracle, "
+                                  "bounded sample)"},
            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores,
                             "kind": "oracle", "sample": desc},
            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0,

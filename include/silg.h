@@ -161,6 +161,20 @@ typedef struct {
   void* (*dev_alloc)(size_t bytes, void* ctx);
   void (*dev_free)(void* ptr, void* ctx);
   void* alloc_ctx;
+  int32_t cr_exchanges;        /* cluster exchanges per conjugate-residual iteration: 1
+                                  (default) where a scene's layout fits in shared memory and
+                                  it has no contacts between bodies (the vertex images of r
+                                  and Ap are advanced by the iteration's recurrences), else
+                                  2; 2: always the two-exchange form (one for the product's
+                                  input, one for the dot products). Both give the same
+                                  iteration up to rounding. Other values: SIM_EINVAL.   */
+  int32_t delassus_reuse;      /* 1 (default): a frame whose contact vertices are the
+                                  previous frame's (the same sorted list) keeps Y and W~ =
+                                  Y^T Y instead of building them again: both depend on that
+                                  list only (S is constant; the Delassus reuse across steps
+                                  that Sec. 5.3 and Sec. 6 point to). The result is
+                                  bit-identical. sim_set_state, sim_set_checkpoint and a new
+                                  start mode or portfolio forget the list. 0: always build. */
 } sim_options;
 
 /* Launch configuration of the two profile products (z = S g, x = S^T y), chosen by the
@@ -188,6 +202,8 @@ typedef struct {
   double residual[SIM_MAX_RESIDUALS]; /* R_k = max_j max(|min(dn, r_n ln)|, h|phi_f|)/L */
   double max_penetration;      /* max over contacts of -delta_n at the end of the frame  */
   int32_t kernels_per_frame;   /* kernel launches in one frame of the last n_iters        */
+  int32_t delassus_reused;     /* 1 if the last frame kept the previous frame's Y and W~  */
+  int64_t delassus_reuse_frames; /* frames that did so since creation                    */
 } sim_stats;
 
 /* Phases of a frame timed by event nodes inside the frame's CUDA graph (milliseconds,

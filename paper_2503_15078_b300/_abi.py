@@ -65,7 +65,8 @@ class SimOptions(C.Structure):
                 ("residual_tol", C.c_double), ("max_iters", C.c_int32),
                 ("local_solver", C.c_int32), ("global_solver", C.c_int32),
                 ("jacobi_sweeps", C.c_int32), ("phase_marks", C.c_int32),
-                ("dev_alloc", DEV_ALLOC), ("dev_free", DEV_FREE), ("alloc_ctx", C.c_void_p)]
+                ("dev_alloc", DEV_ALLOC), ("dev_free", DEV_FREE), ("alloc_ctx", C.c_void_p),
+                ("cr_exchanges", C.c_int32), ("delassus_reuse", C.c_int32)]
 
 
 class SimTuning(C.Structure):
@@ -80,7 +81,8 @@ class SimStats(C.Structure):
     _fields_ = [("frame", C.c_int64), ("n_contacts", C.c_int32), ("n_contact_verts", C.c_int32),
                 ("n_iters", C.c_int32), ("n_residuals", C.c_int32),
                 ("residual", C.c_double * SIM_MAX_RESIDUALS), ("max_penetration", C.c_double),
-                ("kernels_per_frame", C.c_int32)]
+                ("kernels_per_frame", C.c_int32), ("delassus_reused", C.c_int32),
+                ("delassus_reuse_frames", C.c_int64)]
 
 
 class SimPlanInfo(C.Structure):

@@ -50,6 +50,8 @@ void sim_default_options(sim_options* o) {
   o->global_solver = SIM_GLOBAL_SPARSE_INVERSE;
   o->jacobi_sweeps = 1;
   o->phase_marks = 1;
+  o->cr_exchanges = 1;
+  o->delassus_reuse = 1;
 }
 
 int sim_plan_create(const sim_mesh* mesh, const sim_material* mats, int32_t n_mat, double h,

@@ -214,6 +214,13 @@ struct DevSim {
   int s1_unroll, s2_unroll;  // tiles in flight per warp: 1 the format's, 0 half, 2 twice
   int n_sm;         // persistent-kernel grid size
   int* scan_part;   // scratch of the two-pass scans (tile sums and offsets)
+  // Delassus reuse across frames: W~ = Y^T Y and Y depend only on the list of contact
+  // vertices (S~ is constant), so a frame whose list equals the previous frame's keeps them.
+  // dl_state[0]: 1 when the current frame reuses them; [1]: the previous frame's
+  // contact-vertex count (-1: none to compare with); [2]: frames that reused them.
+  int dl_reuse_on;
+  int* dl_state;
+  int* dl_prev_cv;  // cap: the previous frame's contact vertices
   int ytz_warp;     // Y^T z with a warp per contact vertex (short ancestor paths) instead
                     // of a CTA per contact vertex
   const float* zero;  // kTileW zeros: the load target of lanes outside a row's range
@@ -300,6 +307,7 @@ struct DevSim {
   float* wt_part;   // partial 64 x 64 tiles of W~
   int wt_grid;      // CTAs of the W~ product
   int cr_R;         // CTAs per CR cluster (one cluster per scene)
+  int cr_single;    // 1: one cluster exchange per CR iteration where it fits; 0: two always
   int* cr_split;    // per scene 2 (kCrMaxRanks + 1): first contact vertex (scene-local) and
                     // first contact (global) of each rank
   unsigned long long spin_limit;  // polls of a device-side wait before it reports a timeout
@@ -384,8 +392,9 @@ void launch_pf_sync(const DevSim& d, cudaStream_t s, int K);
 // exclusive scan of n ints (or of min(*n_dev, n)): one CTA, or with `scratch`
 // (scan_scratch_ints(n) ints) and n above 65,536 one CTA per 4,096-element tile in three
 // launches (scan_launches(n))
+// skip: when non-null and *skip != 0 on the device, the launches do nothing
 void launch_scan(const int* in, int* out, int n, const int* n_dev, int* total, cudaStream_t s,
-                 int* scratch = nullptr);
+                 int* scratch = nullptr, const int* skip = nullptr);
 int scan_launches(int n);
 int scan_scratch_ints(int n);
 int cr_setup(int n_scenes, int* cluster_out, size_t* smem_out);

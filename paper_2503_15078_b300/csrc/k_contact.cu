@@ -524,7 +524,8 @@ __device__ __forceinline__ int scan_len(int n_static, const int* n_dev) {
 }
 
 __global__ void __launch_bounds__(1024) k_scan(const int* in, int* out, int n_static,
-                                               const int* n_dev, int* total) {
+                                               const int* n_dev, int* total, const int* skip) {
+  if (skip && *skip) return;
   __shared__ int wsum[32];
   const int n = scan_len(n_static, n_dev);
   int carry = 0;
@@ -541,7 +542,9 @@ __global__ void __launch_bounds__(1024) k_scan(const int* in, int* out, int n_st
 constexpr int kScanTile = 4096;     // elements per tile: 1024 threads x 4
 constexpr int kScanSplit = 65536;   // arrays longer than this take the two-pass scan
 __global__ void __launch_bounds__(1024) k_scan_tiles(const int* in, int n_static,
-                                                     const int* n_dev, int* part) {
+                                                     const int* n_dev, int* part,
+                                                     const int* skip) {
+  if (skip && *skip) return;
   __shared__ int wsum[32];
   const int n = scan_len(n_static, n_dev);
   const int idx = blockIdx.x * kScanTile + 4 * threadIdx.x;
@@ -558,7 +561,8 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(const int* in, int n_static
 }
 __global__ void __launch_bounds__(1024) k_scan_fin(const int* in, int* out, int n_static,
                                                    const int* n_dev, const int* part_off,
-                                                   int n_tiles, int* total) {
+                                                   int n_tiles, int* total, const int* skip) {
+  if (skip && *skip) return;
   __shared__ int wsum[32];
   const int n = scan_len(n_static, n_dev);
   const int base = blockIdx.x * kScanTile;
@@ -578,8 +582,32 @@ __device__ __forceinline__ int lower_bound_i(const int* a, int n, int key) {
   return lo;
 }
 
+// Whether this frame's contact vertices are the previous frame's (same count, same sorted
+// list): then Y and W~ = Y^T Y, functions of that list alone, are kept, and the kernels that
+// build them return at once. Not after an error, nor when the previous list is unknown
+// (creation, sim_set_state, a new start mode). One CTA; records the list for the next frame.
+__global__ void __launch_bounds__(1024) k_dl_check(DevSim d) {
+  __shared__ int differs;
+  const int ncv_raw = d.counters[kCntCv], ncv = min(ncv_raw, d.cap);
+  const int prev = d.dl_state[1];
+  if (threadIdx.x == 0)
+    differs = !d.dl_reuse_on || prev < 0 || prev != ncv_raw || ncv_raw > d.cap || *d.err != 0;
+  __syncthreads();
+  if (!differs)
+    for (int i = threadIdx.x; i < ncv; i += blockDim.x)
+      if (d.cv_vert[i] != d.dl_prev_cv[i]) differs = 1;
+  __syncthreads();
+  for (int i = threadIdx.x; i < ncv; i += blockDim.x) d.dl_prev_cv[i] = d.cv_vert[i];
+  if (threadIdx.x == 0) {
+    d.dl_state[0] = !differs;
+    d.dl_state[1] = ncv_raw <= d.cap ? ncv_raw : -1;
+    d.dl_state[2] += !differs;
+  }
+}
+
 // rows of U: a is an ancestor of some contact vertex iff its subtree [fd(a), a] holds one
 __global__ void k_u_flag(DevSim d) {
+  if (*d.dl_state) return;   // Y and W~ kept from the previous frame
   int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= d.n) return;
   int ncv = min(d.counters[kCntCv], d.cap);
@@ -591,6 +619,7 @@ __global__ void k_u_flag(DevSim d) {
 }
 
 __global__ void k_u_compact(DevSim d) {
+  if (*d.dl_state) return;   // Y and W~ kept from the previous frame
   int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= d.n || !d.u_flag[a]) return;
   int idx = d.u_off[a];
@@ -600,6 +629,7 @@ __global__ void k_u_compact(DevSim d) {
 }
 
 __global__ void k_yc_len(DevSim d) {
+  if (*d.dl_state) return;   // Y and W~ kept from the previous frame
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   int ncv = min(d.counters[kCntCv], d.cap);
   if (c >= ncv) return;
@@ -609,6 +639,7 @@ __global__ void k_yc_len(DevSim d) {
 // Y rows (row-major over U) and Y columns (contact vertex major, bottom-up along the
 // ancestor path) gathered from the S~ profile.
 __global__ void k_y_gather(DevSim d) {
+  if (*d.dl_state) return;   // Y and W~ kept from the previous frame
   const int lane = threadIdx.x & 31, nwarps = (gridDim.x * blockDim.x) >> 5;
   const int nU = d.counters[kCntU];
   if (d.y_ptr[nU] > d.cap_y || d.yc_ptr[min(d.counters[kCntCv], d.cap)] > d.cap_y) {
@@ -701,6 +732,7 @@ __global__ void k_scene_ranges(DevSim d) {
 
 // union of the contact-vertex intervals of each block of kWtKB rows of U
 __global__ void k_wt_blocks(DevSim d) {
+  if (*d.dl_state) return;   // Y and W~ kept from the previous frame
   const int kb = blockIdx.x * blockDim.x + threadIdx.x;
   const int nU = d.counters[kCntU];
   if (kb * kWtKB >= nU) return;
@@ -714,6 +746,7 @@ __global__ void k_wt_blocks(DevSim d) {
 }
 
 __global__ void __launch_bounds__(kWtThreads) k_wt_items(DevSim d) {
+  if (*d.dl_state) return;   // Y and W~ kept from the previous frame
   const int ncv = min(d.counters[kCntCv], d.cap);
   const int nU = d.counters[kCntU];
   if (ncv == 0 || nU == 0 || d.y_ptr[nU] > d.cap_y) return;
@@ -827,6 +860,7 @@ __global__ void __launch_bounds__(kWtThreads) k_wt_items(DevSim d) {
 }
 
 __global__ void k_wt_reduce(DevSim d) {
+  if (*d.dl_state) return;   // Y and W~ kept from the previous frame
   const int ncv = min(d.counters[kCntCv], d.cap);
   const int nU = d.counters[kCntU];
   if (ncv == 0 || nU == 0 || d.y_ptr[nU] > d.cap_y) return;
@@ -1172,8 +1206,18 @@ struct CrLayout {
   int R, rank, c, ncv, cv0, cv1, j0, j1;
 };
 
-__global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) {
-  pdl_wait();
+// Shared arrays of the two constraint-solve bodies, declared once in the kernel.
+struct CrShared {
+  int* split_cv;               // kCrMaxRanks + 1
+  int* split_j;                // kCrMaxRanks + 1
+  unsigned long long* wbar;    // mbarrier of the bulk copy of the W~ rows
+  float (*wpart)[32];          // [3][32] per-warp partial sums
+  float* red3;                 // 3
+};
+
+// Two cluster exchanges per CR iteration (every scene; the only one with contacts between
+// bodies).
+__device__ __noinline__ void cr_two_exchanges(const DevSim& d, int smem_bytes, CrShared& sh) {
   extern __shared__ __align__(16) float sm[];
   cg::cluster_group cl = cg::this_cluster();
   CrLayout L;
@@ -1187,7 +1231,8 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
   // every CTA reads the same counters, so this exit is taken by all or by none
   if (L.c == 0 || L.ncv == 0) return;
   // split of the contact vertices over the cluster ranks, computed once per CTA
-  __shared__ int split_cv[kCrMaxRanks + 1], split_j[kCrMaxRanks + 1];
+  int* split_cv = sh.split_cv;
+  int* split_j = sh.split_j;
   if (threadIdx.x <= L.R) {
     const int* sp = d.cr_split + scene * 2 * (kCrMaxRanks + 1);
     split_cv[threadIdx.x] = sp[threadIdx.x];
@@ -1238,7 +1283,7 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
   // global memory
   float* wrows = sm + ((((twl + (gen ? 3 * nj_max : 0)) - sm) + 3) & ~size_t(3));
   const size_t used = (size_t)(wrows - sm) * sizeof(float);
-  __shared__ __align__(8) unsigned long long wbar;
+  unsigned long long& wbar = *sh.wbar;
   if (used > (size_t)smem_bytes) {   // uniform: depends only on cluster-wide maxima
     if (threadIdx.x == 0 && L.rank == 0) atomicOr(d.err, kErrCapacity);
     cl.sync();
@@ -1526,8 +1571,8 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
   // cluster-wide sums of three values. Per warp, then per CTA in warp 0, then over the
   // ranks in warp 0 of every CTA: the same shuffle tree on the same values everywhere, so
   // every CTA holds identical scalars (deterministic).
-  __shared__ float wpart[3][32];
-  __shared__ float red3[3];
+  float (*wpart)[32] = sh.wpart;
+  float* red3 = sh.red3;
   auto exchange = [&](float& a, float& b, float& c) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     a = warp_sum(a);
@@ -1616,19 +1661,446 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
   cl.sync();  // no CTA leaves while another may still write into its shared memory
 }
 
+
+// ---- conjugate residual with one cluster exchange per iteration --------------------------
+// The iteration of k_cr (unpreconditioned CR from x = 0, n_cr iterations, (Ap, Ap) expanded
+// from (Ar, Ar), (Ar, Ap) and beta), for scenes without contacts between bodies, rearranged
+// so that each iteration needs one exchange between the CTAs instead of two. K = B^T W~ B + E
+// with B v = sum over a vertex's contacts of D_j^T (omega_j v_j). Every CTA keeps the
+// vertex-space images y_r = B r and y_Ap = B Ap of the whole scene and advances them with
+// the iteration's own recurrences (r -= alpha Ap gives y_r -= alpha y_Ap; Ap = Ar + beta Ap
+// gives y_Ap = B Ar + beta y_Ap); W~ y_r is a full product every iteration. The only data
+// an iteration needs from the other CTAs are then their partial dot products and the B Ar of
+// their contact vertices, which travel together. The final x = dlambda and its B x are
+// computed directly (not from the recurrences).
+//
+// Row products: lane l of a warp owns the column pairs (2l, 2l + 1) + 64 m of y_r in
+// registers; a warp multiplies four rows of W~ at a time with 8-byte shared-memory loads and
+// packed FP32 FMAs (fma.rn.f32x2: two independent round-to-nearest FMAs) and reduces the
+// twelve row sums over the warp with a butterfly of 16 shuffles.
+constexpr int kCr1Pairs = 16;    // register-held column pairs per lane: rows up to 2048 wide
+
+__device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
+  return (unsigned long long)__float_as_uint(lo) |
+         ((unsigned long long)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ float f2lo(unsigned long long v) { return __uint_as_float((unsigned)v); }
+__device__ __forceinline__ float f2hi(unsigned long long v) {
+  return __uint_as_float((unsigned)(v >> 32));
+}
+// d = a * b + c, lane-wise on two FP32 values
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// Sum each of v[0..11] over the warp; afterwards lanes 2i and 2i + 1 hold the total of v[i]
+// in v[0]. Butterfly halving: at each step a lane keeps half of its values and adds the
+// partner's copy of that half.
+__device__ __forceinline__ float warp_sum12(float (&v)[16], int lane) {
+#pragma unroll
+  for (int i = 12; i < 16; ++i) v[i] = 0.f;
+#pragma unroll
+  for (int o = 16, n = 16; o >= 2; o >>= 1, n >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < n / 2; ++i) {
+      const float keep = up ? v[i + n / 2] : v[i];
+      const float send = up ? v[i] : v[i + n / 2];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// Shared-memory bytes (dynamic) the single-exchange body needs before the W~ rows, for a
+// scene's cluster: nj_max / nv_max the largest owned contact / contact-vertex counts.
+__device__ __forceinline__ size_t cr1_layout_bytes(int ldw, int nj_max, int nv_max) {
+  // dots (32 float4), yr / yap / yar[2] (4 ldw float4), wloc (3 nv), x r p Ar Ap (5 x 3 nj),
+  // D (9 nj), omega and E (2 x 3 nj); then cvf, cvn (nv ints) and ctl (nj ints)
+  const size_t floats = 4 * 32 + 16 * (size_t)ldw + 3 * (size_t)nv_max + 30 * (size_t)nj_max;
+  const size_t ints = 2 * (size_t)nv_max + (size_t)nj_max;
+  return ((floats + ints + 3) & ~size_t(3)) * sizeof(float);
+}
+
+// One cluster exchange per CR iteration (scenes without contacts between bodies; see k_cr for
+// when). The split arrays are loaded.
+__device__ __noinline__ void cr_one_exchange(const DevSim& d, int smem_bytes, CrShared& sh) {
+  extern __shared__ __align__(16) float sm[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int R = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int scene = blockIdx.x / R;
+  const int cvb = d.sc_cvb[scene], jb = d.sc_jb[scene];
+  const int c = d.sc_jb[scene + 1] - jb, ncv = d.sc_cvb[scene + 1] - cvb;
+  if (c == 0 || ncv == 0) return;
+  const int* split_cv = sh.split_cv;
+  const int* split_j = sh.split_j;
+  const int cv0 = split_cv[rank], cv1 = split_cv[rank + 1];
+  const int j0 = split_j[rank], j1 = max(split_j[rank + 1], j0);
+  const int nj = j1 - j0, nv = cv1 - cv0;
+  int nj_max = 0, nv_max = 0;
+  for (int r = 0; r < R; ++r) {
+    nj_max = max(nj_max, max(0, split_j[r + 1] - split_j[r]));
+    nv_max = max(nv_max, split_cv[r + 1] - split_cv[r]);
+  }
+  const int ldw = d.sc_ld[scene];
+  const float* wblk = d.wt + d.sc_wtoff[scene];
+  // shared layout (identical offsets in every CTA for the parts written remotely):
+  //   dots[2][16] float4   per-rank partial dot products (two exchange buffers)
+  //   yr[ldw], yap[ldw]     B r and B Ap of every contact vertex of the scene
+  //   yar[2][ldw]           B Ar of every contact vertex (two exchange buffers)
+  float4* dots = reinterpret_cast<float4*>(sm);
+  float4* yr = dots + 32;
+  float4* yap = yr + ldw;
+  float4* yar = yap + ldw;
+  float* wloc = reinterpret_cast<float*>(yar + 2 * ldw);   // 3 nv: (W~ y_r) of owned rows
+  float* vx = wloc + 3 * nv_max;   // per owned contact (3 each): x, r, p, Ar, Ap
+  float* vr = vx + 3 * nj_max;
+  float* vp = vr + 3 * nj_max;
+  float* vAr = vp + 3 * nj_max;
+  float* vAp = vAr + 3 * nj_max;
+  float* Df = vAp + 3 * nj_max;    // 9 nj
+  float* om = Df + 9 * nj_max;     // 3 nj
+  float* ec = om + 3 * nj_max;     // 3 nj
+  int* cvf = reinterpret_cast<int*>(ec + 3 * nj_max);   // owned cv: first local contact
+  int* cvn = cvf + nv_max;                              // owned cv: contact count
+  int* ctl = cvn + nv_max;                              // owned contact: local cv index
+  float* wrows = sm + ((((reinterpret_cast<float*>(ctl + nj_max)) - sm) + 3) & ~size_t(3));
+  const size_t used = (size_t)(wrows - sm) * sizeof(float);
+  unsigned long long& wbar = *sh.wbar;
+  int rows_sm = (int)min((size_t)nv, ((size_t)smem_bytes - used) / ((size_t)ldw * sizeof(float)));
+  if (threadIdx.x == 0 && rows_sm > 0) {
+    // owned rows are contiguous in W~ (row-major, ld a multiple of 4 floats): 16-byte
+    // aligned source and destination, sizes multiples of 16 bytes
+    const unsigned bar = smem_u32(&wbar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const unsigned long long bytes = (unsigned long long)rows_sm * ldw * sizeof(float);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"((unsigned)bytes) : "memory");
+    const char* src = reinterpret_cast<const char*>(wblk + (size_t)cv0 * ldw);
+    const unsigned dst = smem_u32(wrows);
+    for (unsigned long long off = 0; off < bytes; off += kBulkChunk) {
+      const unsigned sz = (unsigned)min((unsigned long long)kBulkChunk, bytes - off);
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+              "r"(dst + (unsigned)off), "l"(src + off), "r"(sz), "r"(bar) : "memory");
+    }
+  }
+  for (int e = threadIdx.x; e < 3 * nj; e += blockDim.x) {
+    const int j = j0 + e / 3;
+    vx[e] = 0.f;
+    vr[e] = d.ct_rhs[3 * j + e % 3];
+    om[e] = d.ct_omega[3 * j + e % 3];
+    ec[e] = d.ct_ecal[3 * j + e % 3];
+  }
+  for (int e = threadIdx.x; e < 9 * nj; e += blockDim.x) Df[e] = d.ct_Df[9 * j0 + e];
+  for (int cvl = threadIdx.x; cvl < nv; cvl += blockDim.x) {
+    const int jf = max(0, d.cv_first[cvb + cv0 + cvl] - j0);
+    cvf[cvl] = jf;
+    cvn[cvl] = max(0, min(nj, jf + d.cv_nct[cvb + cv0 + cvl]) - jf);
+  }
+  for (int jl = threadIdx.x; jl < nj; jl += blockDim.x)
+    ctl[jl] = min(max(d.ct_cv[j0 + jl] - cvb - cv0, 0), max(nv - 1, 0));
+  // the padding columns [ncv, ldw) multiply zero entries of W~: keep them zero (finite) in
+  // the four contiguous vectors yr, yap, yar[0], yar[1]
+  if (ldw > ncv)
+    for (int e = threadIdx.x; e < 4 * (ldw - ncv); e += blockDim.x)
+      yr[(e / (ldw - ncv)) * ldw + ncv + e % (ldw - ncv)] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  bool w_late = false;
+  if (rows_sm > 0 && !mbar_wait(smem_u32(&wbar), 0, d.spin_limit)) {
+    // the copy did not complete in time: report it and read every row from global memory
+    if (threadIdx.x == 0) atomicOr(d.err, kErrTimeout);
+    rows_sm = 0;
+    w_late = true;
+  }
+  __syncthreads();
+  // every CTA of the cluster must be running before shared memory is written remotely
+  cl.sync();
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // B v at owned contact vertex cvl: sum over its contacts of D_j^T (omega_j v_j)
+  auto vertex_b = [&](const float* v, int cvl) {
+    float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+    const int jb0 = cvf[cvl], je0 = jb0 + cvn[cvl];
+    for (int jl = jb0; jl < je0; ++jl) {
+      const float* D = Df + 9 * jl;
+      const float a0 = om[3 * jl] * v[3 * jl], a1 = om[3 * jl + 1] * v[3 * jl + 1],
+                  a2 = om[3 * jl + 2] * v[3 * jl + 2];
+      u0 += D[0] * a0 + D[3] * a1 + D[6] * a2;
+      u1 += D[1] * a0 + D[4] * a1 + D[7] * a2;
+      u2 += D[2] * a0 + D[5] * a1 + D[8] * a2;
+    }
+    return make_float4(u0, u1, u2, 0.f);
+  };
+  // B v of the owned vertices into `buf` of every CTA (one 16-byte remote store per
+  // (rank, vertex), spread over all threads); v must be complete in shared memory
+  auto publish = [&](const float* v, float4* buf) {
+    for (int e = threadIdx.x; e < R * nv; e += blockDim.x) {
+      const int r = e / nv, cvl = e - r * nv;
+      cl.map_shared_rank(buf, r)[cv0 + cvl] = vertex_b(v, cvl);
+    }
+  };
+  // wloc = W~ y_r over the owned rows
+  auto product = [&]() {
+    if (ldw <= 64 * kCr1Pairs) {
+      unsigned long long ux[kCr1Pairs], uy[kCr1Pairs], uz[kCr1Pairs];
+#pragma unroll
+      for (int m = 0; m < kCr1Pairs; ++m) {
+        const int col = 2 * lane + 64 * m;
+        const float4 a = col < ldw ? yr[col] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 b = col < ldw ? yr[col + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        ux[m] = f2pack(a.x, b.x);
+        uy[m] = f2pack(a.y, b.y);
+        uz[m] = f2pack(a.z, b.z);
+      }
+      auto rows4 = [&](int r_begin, int r_end, auto row_ptr) {
+        for (int row = r_begin + 4 * warp; row < r_end; row += 4 * nw) {
+          const int nr = min(4, r_end - row);
+          const float* w[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) w[k] = row_ptr(min(row + k, r_end - 1));
+          unsigned long long acc[4][3];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0ull;
+#pragma unroll
+          for (int m = 0; m < kCr1Pairs; ++m) {
+            const int col = 2 * lane + 64 * m;
+            if (col < ldw) {
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const float2 p = *reinterpret_cast<const float2*>(w[k] + col);
+                const unsigned long long pp = f2pack(p.x, p.y);
+                acc[k][0] = ffma2(pp, ux[m], acc[k][0]);
+                acc[k][1] = ffma2(pp, uy[m], acc[k][1]);
+                acc[k][2] = ffma2(pp, uz[m], acc[k][2]);
+              }
+            }
+          }
+          float v[16];
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) v[3 * k + q] = f2lo(acc[k][q]) + f2hi(acc[k][q]);
+          const float tot = warp_sum12(v, lane);
+          const int idx = lane >> 1;
+          if (!(lane & 1) && idx < 3 * nr) wloc[3 * row + idx] = tot;
+        }
+      };
+      const int n_sm = min(rows_sm, nv);
+      rows4(0, n_sm, [&](int r) { return static_cast<const float*>(wrows + (size_t)r * ldw); });
+      rows4(n_sm, nv, [&](int r) { return wblk + (size_t)(cv0 + r) * ldw; });
+    } else {
+      // wide rows: four rows per warp at a time, 16-byte loads of W~ and y_r
+      const int ng = ldw / 4;
+      for (int row0 = 4 * warp; row0 < nv; row0 += 4 * nw) {
+        float acc[4][3] = {};
+        const int nrow = min(4, nv - row0);
+        const float4* wrow[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int row = min(row0 + k, nv - 1);
+          wrow[k] = reinterpret_cast<const float4*>(row < rows_sm ? wrows + (size_t)row * ldw
+                                                                  : wblk + (size_t)(cv0 + row) * ldw);
+        }
+        for (int g4 = lane; g4 < ng; g4 += 32) {
+          const float4 a = yr[4 * g4], b = yr[4 * g4 + 1], cc = yr[4 * g4 + 2], e = yr[4 * g4 + 3];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float4 w = wrow[k][g4];
+            acc[k][0] += w.x * a.x + w.y * b.x + w.z * cc.x + w.w * e.x;
+            acc[k][1] += w.x * a.y + w.y * b.y + w.z * cc.y + w.w * e.y;
+            acc[k][2] += w.x * a.z + w.y * b.z + w.z * cc.z + w.w * e.z;
+          }
+        }
+        float v[16];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) v[3 * k + q] = acc[k][q];
+        const float tot = warp_sum12(v, lane);
+        const int idx = lane >> 1;
+        if (!(lane & 1) && idx < 3 * nrow) wloc[3 * row0 + idx] = tot;
+      }
+    }
+  };
+  // Ar = omega D (W~ y_r) + E r over the owned contacts, with the partial dot products
+  // (r, Ar), (Ar, Ar), (Ar, Ap) of this CTA
+  auto apply_dots = [&](float& s1, float& s2, float& s3) {
+    s1 = s2 = s3 = 0.f;
+    for (int e = threadIdx.x; e < 3 * nj; e += blockDim.x) {
+      const int jl = e / 3, r = e % 3;
+      const int cvl = ctl[jl];
+      const float* D = Df + 9 * jl + 3 * r;
+      const float dw = D[0] * wloc[3 * cvl] + D[1] * wloc[3 * cvl + 1] + D[2] * wloc[3 * cvl + 2];
+      const float ar = om[e] * dw + ec[e] * vr[e];
+      vAr[e] = ar;
+      s1 += vr[e] * ar;
+      s2 += ar * ar;
+      s3 += ar * vAp[e];
+    }
+  };
+  // reduce three values over the CTA (per warp, then warp 0 in warp order) and send them to
+  // slot `rank` of dots buffer `buf` in every CTA; ends with the CTA's shared writes visible
+  float (*wpart)[32] = sh.wpart;
+  auto send_dots = [&](float a, float b, float cc, int buf) {
+    a = warp_sum(a);
+    b = warp_sum(b);
+    cc = warp_sum(cc);
+    if (lane == 0) {
+      wpart[0][warp] = a;
+      wpart[1][warp] = b;
+      wpart[2][warp] = cc;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      a = warp_sum(lane < nw ? wpart[0][lane] : 0.f);
+      b = warp_sum(lane < nw ? wpart[1][lane] : 0.f);
+      cc = warp_sum(lane < nw ? wpart[2][lane] : 0.f);
+      if (lane < R) cl.map_shared_rank(dots + 16 * buf, lane)[rank] = make_float4(a, b, cc, 0.f);
+    }
+  };
+  // the cluster-wide sums: every thread adds the ranks' partials in rank order, so every CTA
+  // holds identical scalars (deterministic)
+  auto gather_dots = [&](int buf) {
+    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int r = 0; r < R; ++r) {
+      const float4 q = dots[16 * buf + r];
+      t.x += q.x;
+      t.y += q.y;
+      t.z += q.z;
+    }
+    return t;
+  };
+
+  // r = rhs, x = 0: y_r = B r everywhere, then Ar = K r, p = r, Ap = Ar, y_Ap = B Ar
+  publish(vr, yr);
+  cl.sync();
+  product();
+  __syncthreads();
+  float s1, s2, s3;
+  apply_dots(s1, s2, s3);
+  for (int e = threadIdx.x; e < 3 * nj; e += blockDim.x) {
+    vp[e] = vr[e];
+    vAp[e] = vAr[e];
+  }
+  send_dots(s1, s2, 0.f, 0);
+  publish(vAr, yar);
+  cl.sync();
+  float4 t = gather_dots(0);
+  float rAr = t.x, ApAp = t.y;
+  for (int i = threadIdx.x; i < ncv; i += blockDim.x) yap[i] = yar[i];
+  __syncthreads();
+  for (int it = 0; it < d.n_cr; ++it) {
+    if (!(ApAp > 0.f)) break;   // identical scalars everywhere: a uniform exit
+    const float alpha = rAr / ApAp;
+    for (int e = threadIdx.x; e < 3 * nj; e += blockDim.x) {
+      vx[e] += alpha * vp[e];
+      vr[e] -= alpha * vAp[e];
+    }
+    if (it == d.n_cr - 1) break;   // x is final; the last update needs no product
+    for (int i = threadIdx.x; i < ncv; i += blockDim.x) {
+      const float4 a = yr[i], b = yap[i];
+      yr[i] = make_float4(a.x - alpha * b.x, a.y - alpha * b.y, a.z - alpha * b.z, 0.f);
+    }
+    __syncthreads();
+    product();
+    __syncthreads();
+    apply_dots(s1, s2, s3);
+    const int buf = (it + 1) & 1;
+    send_dots(s1, s2, s3, buf);    // its barrier also publishes Ar within the CTA
+    publish(vAr, yar + buf * ldw);
+    cl.sync();
+    t = gather_dots(buf);
+    const float beta = rAr != 0.f ? t.x / rAr : 0.f;
+    ApAp = t.y + 2.f * beta * t.z + beta * beta * ApAp;
+    rAr = t.x;
+    for (int e = threadIdx.x; e < 3 * nj; e += blockDim.x) {
+      vp[e] = vr[e] + beta * vp[e];
+      vAp[e] = vAr[e] + beta * vAp[e];
+    }
+    const float4* yb = yar + buf * ldw;
+    for (int i = threadIdx.x; i < ncv; i += blockDim.x) {
+      const float4 a = yb[i], b = yap[i];
+      yap[i] = make_float4(a.x + beta * b.x, a.y + beta * b.y, a.z + beta * b.z, 0.f);
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  // lambda += dlambda; u = B dlambda per owned contact vertex
+  for (int e = threadIdx.x; e < 3 * nj; e += blockDim.x) d.ct_lam[3 * j0 + e] += (double)vx[e];
+  for (int cvl = threadIdx.x; cvl < nv; cvl += blockDim.x) {
+    const int cv = cvb + cv0 + cvl;
+    const float4 u = vertex_b(vx, cvl);
+    d.uvec[3 * cv] = u.x;
+    d.uvec[3 * cv + 1] = u.y;
+    d.uvec[3 * cv + 2] = u.z;
+  }
+  // a copy that timed out may still be in flight: give it another bounded wait before the
+  // shared memory is released
+  if (w_late) mbar_wait(smem_u32(&wbar), 0, d.spin_limit);
+  cl.sync();  // no CTA leaves while another may still write into its shared memory
+}
+
+// The constraint solve of one local-global iteration: one thread-block cluster per scene.
+// The single-exchange body runs where its layout fits in shared memory with all but at most
+// 32 owned W~ rows and the scene has no contacts between bodies; the two-exchange body
+// everywhere else. The
+// choice depends only on the scene's sizes, so every CTA of a cluster makes the same one.
+__global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) {
+  pdl_wait();
+  __shared__ int split_cv[kCrMaxRanks + 1], split_j[kCrMaxRanks + 1];
+  __shared__ __align__(8) unsigned long long wbar;
+  __shared__ float wpart[3][32];
+  __shared__ float red3[3];
+  CrShared sh{split_cv, split_j, &wbar, wpart, red3};
+  cg::cluster_group cl = cg::this_cluster();
+  const int R = (int)cl.num_blocks();
+  const int scene = blockIdx.x / R;
+  bool one = !d.bc_on && d.cr_single;
+  if (one) {
+    if (threadIdx.x <= R) {
+      const int* sp = d.cr_split + scene * 2 * (kCrMaxRanks + 1);
+      split_cv[threadIdx.x] = sp[threadIdx.x];
+      split_j[threadIdx.x] = sp[kCrMaxRanks + 1 + threadIdx.x];
+    }
+    __syncthreads();
+    int nj_max = 0, nv_max = 0;
+    for (int r = 0; r < R; ++r) {
+      nj_max = max(nj_max, max(0, split_j[r + 1] - split_j[r]));
+      nv_max = max(nv_max, split_cv[r + 1] - split_cv[r]);
+    }
+    // the single-exchange layout must fit, and at most one pass of 32 owned rows (four per
+    // warp) may have to come from L2 instead of shared memory
+    const int ldw = d.sc_ld[scene];
+    const size_t lay = cr1_layout_bytes(ldw, nj_max, nv_max);
+    const size_t rows_fit = lay <= (size_t)smem_bytes
+                                ? ((size_t)smem_bytes - lay) / ((size_t)ldw * sizeof(float)) : 0;
+    one = lay <= (size_t)smem_bytes && (size_t)nv_max <= rows_fit + 4 * (kCrThreads / 32);
+    __syncthreads();   // split arrays are reloaded by the body that runs
+  }
+  if (one)
+    cr_one_exchange(d, smem_bytes, sh);
+  else
+    cr_two_exchanges(d, smem_bytes, sh);
+}
+
 }  // namespace
 
 void launch_scan(const int* in, int* out, int n, const int* n_dev, int* total, cudaStream_t s,
-                 int* scratch) {
+                 int* scratch, const int* skip) {
   if (!scratch || n <= kScanSplit) {
-    k_scan<<<1, 1024, 0, s>>>(in, out, n, n_dev, total);
+    k_scan<<<1, 1024, 0, s>>>(in, out, n, n_dev, total, skip);
     return;
   }
   // scratch: n_tiles tile sums, then their n_tiles + 1 offsets
   const int nt = (n + kScanTile - 1) / kScanTile;
-  k_scan_tiles<<<nt, 1024, 0, s>>>(in, n, n_dev, scratch);
-  k_scan<<<1, 1024, 0, s>>>(scratch, scratch + nt, nt, nullptr, nullptr);
-  k_scan_fin<<<nt, 1024, 0, s>>>(in, out, n, n_dev, scratch + nt, nt, total);
+  k_scan_tiles<<<nt, 1024, 0, s>>>(in, n, n_dev, scratch, skip);
+  k_scan<<<1, 1024, 0, s>>>(scratch, scratch + nt, nt, nullptr, nullptr, skip);
+  k_scan_fin<<<nt, 1024, 0, s>>>(in, out, n, n_dev, scratch + nt, nt, total, skip);
 }
 
 int scan_launches(int n) { return n > kScanSplit ? 3 : 1; }
@@ -1654,12 +2126,15 @@ void launch_collide(const DevSim& d, cudaStream_t s) {
 
 void launch_delassus(const DevSim& d, cudaStream_t s) {
   const int g = (d.n + 255) / 256;
+  k_dl_check<<<1, 1024, 0, s>>>(d);
+  const int* skip = d.dl_state;
   k_u_flag<<<g, 256, 0, s>>>(d);
-  launch_scan(d.u_flag, d.u_off, d.n, nullptr, d.counters + kCntU, s, d.scan_part);
+  launch_scan(d.u_flag, d.u_off, d.n, nullptr, d.counters + kCntU, s, d.scan_part, skip);
   k_u_compact<<<g, 256, 0, s>>>(d);
-  launch_scan(d.u_len, d.y_ptr, d.n, d.counters + kCntU, d.counters + kCntY, s, d.scan_part);
+  launch_scan(d.u_len, d.y_ptr, d.n, d.counters + kCntU, d.counters + kCntY, s, d.scan_part, skip);
   k_yc_len<<<(d.cap + 255) / 256, 256, 0, s>>>(d);
-  launch_scan(d.yc_len, d.yc_ptr, d.cap, d.counters + kCntCv, d.counters + kCntYC, s, d.scan_part);
+  launch_scan(d.yc_len, d.yc_ptr, d.cap, d.counters + kCntCv, d.counters + kCntYC, s, d.scan_part,
+              skip);
   k_y_gather<<<std::min((d.n * 32 + 255) / 256, 8 * d.n_sm), 256, 0, s>>>(d);
   k_scene_ranges<<<1, 256, 0, s>>>(d);
   k_wt_blocks<<<(d.n / kWtKB + 1 + 127) / 128, 128, 0, s>>>(d);

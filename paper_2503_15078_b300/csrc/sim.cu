@@ -122,6 +122,11 @@ int err_status(int bits) {
   return SIM_OK;
 }
 
+// forget the previous frame's contact-vertex list: the next frame builds Y and W~ afresh
+void delassus_forget(sim_s* s, cudaStream_t st) {
+  cudaMemsetAsync(s->d.dl_state + 1, 0xff, sizeof(int), st);
+}
+
 int sync_and_check(sim_s* s) {
   cudaError_t e = cudaStreamSynchronize(s->launch);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->work);
@@ -172,7 +177,7 @@ int kernels_per_frame_to_tolerance(const sim_s* s, int K) {
   const int refine_end = s->d.s_bf16 && s->d.refine == 1 && !s->d.jacobi_sweeps ? 6 : 0;
   const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 + bc : 0) + 2;
   const int before = 1 + (s->d.bend_ptr != nullptr) +
-                     (c ? 4 + 12 + 6 * bc + scans + silg::ws_kernels(s->d.ws_mode) : 0) +
+                     (c ? 4 + 13 + 6 * bc + scans + silg::ws_kernels(s->d.ws_mode) : 0) +
                      local_kernels(s) +
                      (c ? 1 : 0);
   const int body = 1 + global + refine_body + 1 + (c ? 1 : 0) + local_kernels(s) + 1;
@@ -186,7 +191,7 @@ int kernels_per_frame(const sim_s* s, int K) {
   // pass 2 + reduction; a residual correction adds the residual and both passes
   const int bc = s->d.bc_on ? 1 : 0;
   const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 + bc : 0) + 2;
-  return 1 + (s->d.bend_ptr != nullptr) + (c ? 4 + 12 + 6 * bc + scan_extra(s) : 0) +
+  return 1 + (s->d.bend_ptr != nullptr) + (c ? 4 + 13 + 6 * bc + scan_extra(s) : 0) +
          K * (local_kernels(s) + (c ? 1 : 0) + 1 + global) + (c ? 1 : 0) + 1 +
          5 * refined_iters(s, K) + (c ? silg::ws_kernels(s->d.ws_mode) : 0) +
          (c && s->d.pf_copies > 1 ? 1 : 0);
@@ -1030,6 +1035,10 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   s->has_obstacles = n_obs > 0 || !sd.anchors.empty() || d.bc_on;
   d.wt_grid = 4 * d.n_sm;
   d.scan_part = s->alloc<int>(silg::scan_scratch_ints(std::max(n, cap)));
+  d.dl_reuse_on = o->delassus_reuse ? 1 : 0;
+  d.dl_state = s->alloc<int>(4);
+  d.dl_prev_cv = s->alloc<int>(cap);
+  cudaMemsetAsync(d.dl_state + 1, 0xff, sizeof(int), s->work);   // no previous list yet
   // the path of a contact vertex in Y is its ancestor chain: a warp covers a short one
   d.ytz_warp = p.mean_depth < 600.0 ? 1 : 0;
   d.spin_limit = o->spin_limit;
@@ -1073,6 +1082,7 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
     if (st != SIM_OK) return st;
   }
   d.cr_R = s->cluster;
+  d.cr_single = o->cr_exchanges == 1 ? 1 : 0;
   if (o->autotune) {
     int st = autotune_products(s);
     if (st != SIM_OK) return st;
@@ -1186,6 +1196,8 @@ int check_options(const sim_options* o) {
     return SIM_EINVAL;
   if ((o->dev_alloc == nullptr) != (o->dev_free == nullptr)) return SIM_EINVAL;
   if (o->precond != SIM_PRECOND_DELASSUS && o->precond != SIM_PRECOND_MASS) return SIM_EINVAL;
+  if (o->cr_exchanges != 1 && o->cr_exchanges != 2) return SIM_EINVAL;
+  if (o->delassus_reuse != 0 && o->delassus_reuse != 1) return SIM_EINVAL;
   return SIM_OK;
 }
 
@@ -1508,6 +1520,7 @@ int sim_set_warmstart(sim_t* s, const sim_mlp_t* net, int32_t mode) {
     if (e != cudaSuccess) return cuda_status(e);
   }
   s->d.ws_mode = mode;   // graphs are cached per mode; the network's weights are read at launch
+  delassus_forget(s, s->launch);
   return SIM_OK;
 }
 
@@ -1554,6 +1567,7 @@ int sim_set_portfolio(sim_t* s, int32_t copies) {
     }
     s->graphs.clear();
     s->d.pf_copies = copies;
+    delassus_forget(s, s->launch);
   }
   return SIM_OK;
 }
@@ -1708,6 +1722,7 @@ int sim_set_state(sim_t* s, const double* q, const double* v) {
   }
   // in stream order before the next frame; the copies read the staging asynchronously
   cudaMemsetAsync(s->d.prev_valid, 0, sizeof(int) * s->d.n, s->launch);
+  delassus_forget(s, s->launch);   // a replayed frame is never served from the previous one
   if (s->d.n_anc > 0)   // time restarts at 0: so do the anchors' targets
     cudaMemcpyAsync(s->d.anc_pos, s->d.anc_pos0, 3 * sizeof(double) * s->d.n_anc,
                     cudaMemcpyDeviceToDevice, s->launch);
@@ -1800,6 +1815,7 @@ int sim_set_checkpoint(sim_t* s, const void* buf, size_t bytes) {
     off += part.second;
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d.err, 0, sizeof(int), s->launch);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d.dl_state + 1, 0xff, sizeof(int), s->launch);
   // the caller's buffer is read before returning
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->launch);
   if (e != cudaSuccess) return cuda_status(e);
@@ -1840,6 +1856,12 @@ int sim_get_stats(sim_t* s, sim_stats* out) {
   out->n_iters = s->last_iters;
   out->n_residuals = s->has_obstacles && s->frame > 0 ? s->last_iters + 1 : 0;
   for (int k = 0; k < out->n_residuals; ++k) out->residual[k] = res[k];
+  if (s->has_obstacles && s->frame > 0) {
+    int dl[3] = {0, 0, 0};
+    cudaMemcpy(dl, s->d.dl_state, sizeof(dl), cudaMemcpyDeviceToHost);
+    out->delassus_reused = dl[0];
+    out->delassus_reuse_frames = dl[2];
+  }
   out->kernels_per_frame = s->last_to_tol ? kernels_per_frame_to_tolerance(s, s->last_iters)
                                           : kernels_per_frame(s, s->last_iters > 0 ? s->last_iters
                                                                                    : s->n_iters_default);

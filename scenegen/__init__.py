@@ -302,12 +302,13 @@ def star_pull(n_side: int = 42, layers: int = 27, spacing: float = 0.01, seed: i
                  contact_margin=0.5 * spacing, n_frames=n_frames, spacing=spacing)
 
 
-def star_placed(scene: Scene, placement: float = 0.1025):
+def star_placed(scene: Scene, placement: float = 0.094):
     """A contact state of a star_pull scene (pure geometry, no simulation): the rest shape
     translated along +x so that its leading face lies ``placement`` metres beyond the axes of
-    the first cylinder row, every vertex moving at the pull speed. At 0.1025 m on the 42 x 42
-    x 27 star the tips are inside the first row's cylinders: 810 contacts at 810 distinct
-    vertices on the predicted positions. Returns (q, v)."""
+    the first cylinder row, every vertex moving at the pull speed. At 0.094 m on the 43 x 43
+    x 27 star (59,778 DoFs) the tips are inside the first row's cylinders: 837 contacts at
+    837 distinct vertices on the predicted positions (0.1025 m on the 42 x 42 x 27 star:
+    810). Returns (q, v)."""
     q = scene.q0.copy()
     x_front = scene.X[:, 0].max()
     first_col = min(o.p[0] for o in scene.obstacles)

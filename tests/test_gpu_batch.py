@@ -115,3 +115,39 @@ def test_sixty_four_uneven_scenes_run_in_one_simulator():
         assert _relerr(q2[sl] - sc.q0, qo - sc.q0) < 5e-2, k
     sim.close()
     sim2.close()
+
+
+def test_sharded_batch_equals_the_whole_batch_scene_by_scene():
+    # a batch split over two ranks by nnz(S~) (paper_2503_15078_b300.shard), each part
+    # simulated on its own as one rank would (here one after the other on the one GPU): every
+    # scene's trajectory equals the whole batch's up to the rounding of its reordered sums,
+    # and its contact list is the same
+    from paper_2503_15078_b300 import shard
+    scenes = sg.batch(n_scenes=10, seed=5, m_lo=4, m_hi=10)
+    for sc in scenes:   # start 0.2 mm inside the (tilted) plane
+        sc.q0 = sc.q0 - 0.0502 * np.asarray(sc.obstacles[0].axis)
+    whole = Simulator(scenes)
+    whole.step(n_frames=3)
+    qw, _ = whole.state()
+    cw = whole.contacts()
+    off = whole.scene_offsets
+    costs = shard.scene_costs(scenes)
+    parts = shard.partition(costs, 2)
+    assert all(parts) and sorted(parts[0] + parts[1]) == list(range(len(scenes)))
+    n_contact_scenes = 0
+    for part in parts:
+        sim = Simulator([scenes[i] for i in part])
+        sim.step(n_frames=3)
+        qp, _ = sim.state()
+        cp = sim.contacts()
+        for k, i in enumerate(part):
+            a, b = sim.scene_offsets[k], sim.scene_offsets[k + 1]
+            ref = qw[off[i]:off[i + 1]]
+            assert _relerr(qp[a:b] - scenes[i].q0, ref - scenes[i].q0) < 1e-5, i
+            mine_p = (cp["vertex"] >= a) & (cp["vertex"] < b)
+            mine_w = (cw["vertex"] >= off[i]) & (cw["vertex"] < off[i + 1])
+            assert np.array_equal(cp["vertex"][mine_p] - a, cw["vertex"][mine_w] - off[i])
+            n_contact_scenes += int(mine_w.sum() > 0)
+        sim.close()
+    assert n_contact_scenes >= 5
+    whole.close()

@@ -52,8 +52,22 @@ def test_checkpoint_replay_is_bitwise(mode):
     fresh.restore(blob)
     fresh.step(n_frames=4)
     assert np.array_equal(fresh.state()[0], q10)
-    # a plain state replay forgets the contact record (and the anchors' time)
-    if mode in ("previous", "anchor"):
+    # the restored contact record is what the warm starts read: the first restored frame's
+    # features (7..9: the previous frame's impulse) equal the original continuation's; a
+    # plain state replay forgets the record (zero features) and the anchors' time
+    if mode in ("previous", "learned"):
+        sim.restore(blob)
+        sim.step()
+        X_ck, _ = sim.warmstart_samples()
+        fresh.restore(blob)
+        fresh.step()
+        assert np.array_equal(fresh.warmstart_samples()[0], X_ck)
+        assert np.abs(X_ck[:, 7:10]).max() > 0
+        sim.set_state(q6, v6)
+        sim.step()
+        X_st, _ = sim.warmstart_samples()
+        assert np.all(X_st[:, 7:10] == 0)
+    if mode == "anchor":
         sim.set_state(q6, v6)
         sim.step(n_frames=4)
         assert not np.array_equal(sim.state()[0], q10)

@@ -1,9 +1,9 @@
-"""GPU parity at the benchmarked size: the 57k-DoF star (42 x 42 x 27 lattice, 19,008
-vertices, 96,252 tetrahedra, stable Neo-Hookean E = 1e6) placed 10.25 cm into the first row
-of cylinders, 810 contacts, one 5-iteration frame with 10 CR iterations (Alg. 4), in the
+"""GPU parity at the benchmarked size: the 59.8k-DoF star (43 x 43 x 27 lattice, 19,926
+vertices, 101,400 tetrahedra, stable Neo-Hookean E = 1e6) placed 9.4 cm into the first row
+of cylinders, 837 contacts, one 5-iteration frame with 10 CR iterations (Alg. 4), in the
 launch configuration the benchmark times (autotuned products, a 16-CTA constraint-solve
 cluster, contact capacity 4096). The FP64 oracle runs the same frame on the host (its W
-from 2,430 direct solves, about a minute).
+from 2,511 direct solves, about a minute and a half).
 
 Gates (single step from an identical state, FP32 on the device):
   * the contact sets are equal (vertex, obstacle), in order;
@@ -24,12 +24,12 @@ from paper_2503_15078_b300 import Simulator
 
 pytestmark = pytest.mark.gpu
 
-PLACEMENT = 0.1025
+N_SIDE, PLACEMENT = 43, 0.094
 
 
 @pytest.fixture(scope="module")
 def star_frame():
-    sc = sg.star_pull(n_side=42, seed=0)
+    sc = sg.star_pull(n_side=N_SIDE, seed=0)
     q0, v0 = sg.star_placed(sc, PLACEMENT)
     sim = Simulator(sc, autotune=1, contact_capacity=4096)
     sim.set_state(q0, v0)
@@ -37,6 +37,13 @@ def star_frame():
     qg, vg = sim.state()
     gpu = dict(q=qg, v=vg, contacts=sim.contacts(), stats=sim.stats(), delassus=sim.delassus(),
                tuning=sim.tuning())
+    sim.close()
+    # the same frame with the two-exchange constraint solve
+    sim = Simulator(sc, autotune=1, contact_capacity=4096, cr_exchanges=2)
+    sim.set_state(q0, v0)
+    sim.step(n_iters=5)
+    gpu["q2"], _ = sim.state()
+    gpu["lam2"] = sim.contacts()["lam"]
     sim.close()
     o = Oracle(sc)
     q, v, info = o.frame(q0, v0, OracleOptions(n_iters=5, n_cr=10))
@@ -66,15 +73,19 @@ def test_fullsize_positions_match(star_frame):
     assert _relerr(vg, v) <= 1e-3, _relerr(vg, v)
 
 
-def test_fullsize_impulses_match(star_frame):
-    lam_g = star_frame["gpu"]["contacts"]["lam"]
+@pytest.mark.parametrize("form", ["one_exchange", "two_exchanges"])
+def test_fullsize_impulses_match(star_frame, form):
+    lam_g = star_frame["gpu"]["contacts"]["lam"] if form == "one_exchange" else \
+        star_frame["gpu"]["lam2"]
     lam_o = star_frame["ref"]["info"]["lam"]
     keep = np.abs(lam_o[:, 0]) >= 1e-6 * np.abs(lam_o[:, 0]).max()
     err = _relerr(lam_g[keep], lam_o[keep])
-    print(f"\nfull-size star: lambda rel. error {err:.2e} over {int(keep.sum())} contacts, "
-          f"{int((~keep).sum())} excluded (|lambda_n| < 1e-6 max)")
+    print(f"\nfull-size star ({form}): lambda rel. error {err:.2e} over {int(keep.sum())} "
+          f"contacts, {int((~keep).sum())} excluded (|lambda_n| < 1e-6 max)")
     assert keep.sum() >= 0.5 * len(keep)
     assert err <= 1e-5, err
+    if form == "two_exchanges":
+        assert _relerr(star_frame["gpu"]["q2"], star_frame["ref"]["q"]) <= 1e-5
 
 
 def test_fullsize_delassus_matches(star_frame):
