@@ -558,6 +558,17 @@ def run_ours(args):
                     contact_capacity=65536 if stack else (16384 if batch else 4096))
     n_iters = scene.n_iters
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    # the one-time precompute: host ordering, symbolic analysis and FP64 Cholesky, then
+    # S~ = L~^-1 P on the device in FP64; the host build of S~ for comparison
+    pinfo = sim.plan_info()
+    precompute = {"host_factor_seconds": round(pinfo["precompute_seconds"], 3),
+                  "s_build_seconds": round(pinfo["s_build_seconds"], 4),
+                  "s_built_on_device": pinfo["s_built_on_device"]}
+    if not batch:
+        from paper_2503_15078_b300 import Plan
+        hp = Plan(scene).info()
+        precompute["host_s_build_seconds"] = round(hp["s_build_seconds"], 3)
+        precompute["host_total_seconds"] = round(hp["precompute_seconds"], 3)
 
     def one_step():
         # every step replays the same frame from the placed contact state;
@@ -686,6 +697,7 @@ def run_ours(args):
                                 if k in ("tuned", "pass1_ctas", "pass2_ctas", "pass1_unroll",
                                          "pass2_unroll", "pass1_balance", "pass2_balance")},
             "refine": args.refine if bf16 else None,
+            "precompute_s": precompute,
             "l2": "flushed (256 MB write) before every timed step",
             "parallelism": (f"scene shards x{world} of one {n_batch}-scene batch" if batch
                             else f"replicas x{world}") if world > 1 else "single GPU",

@@ -168,6 +168,14 @@ typedef struct {
                                   2; 2: always the two-exchange form (one for the product's
                                   input, one for the dot products). Both give the same
                                   iteration up to rounding. Other values: SIM_EINVAL.   */
+  int32_t s_build;             /* where a simulator builds S~ = L~^-1 P from the host's
+                                  FP64 Cholesky factor: 1 (default) on the device in FP64
+                                  (one warp per column along its elimination-tree path; the
+                                  same FP64 values as the host loop), 0 on the host (all
+                                  cores). Meshes whose elimination tree is too deep for the
+                                  device kernel's shared memory are built on the host. The
+                                  host-only plan (sim_plan_create) always builds on the
+                                  host. Other values: SIM_EINVAL.                        */
   int32_t delassus_reuse;      /* 1 (default): a frame whose contact vertices are the
                                   previous frame's (the same sorted list) keeps Y and W~ =
                                   Y^T Y instead of building them again: both depend on that
@@ -238,7 +246,10 @@ typedef struct {
   int32_t etree_max_depth;
   double etree_mean_depth;
   int32_t n_roots;
-  double precompute_seconds;
+  double precompute_seconds;   /* host precompute, wall clock (with S~ when built there)  */
+  double s_build_seconds;      /* the build of S~ = L~^-1 P alone: host loop, or device
+                                  kernel (Sec. 4.2) with its uploads, wall clock         */
+  int32_t s_built_on_device;   /* 1 if S~ was built on the device (sim_options.s_build)   */
 } sim_plan_info;
 
 typedef struct sim_s sim_t;

@@ -66,7 +66,8 @@ class SimOptions(C.Structure):
                 ("local_solver", C.c_int32), ("global_solver", C.c_int32),
                 ("jacobi_sweeps", C.c_int32), ("phase_marks", C.c_int32),
                 ("dev_alloc", DEV_ALLOC), ("dev_free", DEV_FREE), ("alloc_ctx", C.c_void_p),
-                ("cr_exchanges", C.c_int32), ("delassus_reuse", C.c_int32)]
+                ("cr_exchanges", C.c_int32), ("s_build", C.c_int32),
+                ("delassus_reuse", C.c_int32)]
 
 
 class SimTuning(C.Structure):
@@ -90,7 +91,8 @@ class SimPlanInfo(C.Structure):
                 ("nnz_A", C.c_int64), ("nnz_L", C.c_int64), ("nnz_S", C.c_int64),
                 ("stored_S", C.c_int64), ("etree_max_depth", C.c_int32),
                 ("etree_mean_depth", C.c_double), ("n_roots", C.c_int32),
-                ("precompute_seconds", C.c_double)]
+                ("precompute_seconds", C.c_double), ("s_build_seconds", C.c_double),
+                ("s_built_on_device", C.c_int32)]
 
 
 # name -> (restype, argtypes); every entry must be exported by libsilg.so

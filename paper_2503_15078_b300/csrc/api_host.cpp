@@ -51,6 +51,7 @@ void sim_default_options(sim_options* o) {
   o->jacobi_sweeps = 1;
   o->phase_marks = 1;
   o->cr_exchanges = 1;
+  o->s_build = 1;
   o->delassus_reuse = 1;
 }
 
@@ -97,11 +98,13 @@ void silg_fill_plan_info(const silg::Plan& p, sim_plan_info* info) {
   info->nnz_A = p.nnz_A;
   info->nnz_L = p.nnz_L;
   info->nnz_S = p.nnz_S;
-  info->stored_S = (int64_t)p.S.size();
+  info->stored_S = p.rowbase.empty() ? 0 : (int64_t)p.rowbase.back();
   info->etree_max_depth = p.max_depth;
   info->etree_mean_depth = p.mean_depth;
   info->n_roots = p.n_roots;
   info->precompute_seconds = p.seconds;
+  info->s_build_seconds = p.s_seconds;
+  info->s_built_on_device = p.s_on_device;
 }
 
 int sim_plan_get_ordering(const sim_plan_t* pp, int32_t* order, int32_t* parent,

@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "devguard.hpp"
 #include "mlp.cuh"
 #include "plan.hpp"
@@ -398,6 +400,24 @@ void launch_scan(const int* in, int* out, int n, const int* n_dev, int* total, c
 int scan_launches(int n);
 int scan_scratch_ints(int n);
 int cr_setup(int n_scenes, int* cluster_out, size_t* smem_out);
+// S~ built on the device in FP64 from the host's factor L~ (k_sbuild.cu)
+struct SinvBuildArgs {
+  int nf;
+  const long long* Lp;      // nf + 1: column starts of L~ (diagonal first)
+  const int* Ldd;           // per entry: depth(column) - depth(row), 0 on the diagonal
+  const double* Lx;
+  const int* parent;
+  const int* depth;
+  const long long* rowbase; // S~ profile: offset of column lo of each row
+  const int* lo;
+  int max_depth;
+  int* next_col;            // work counter (1 int)
+  float* S;                 // stored values, zero-initialised
+  unsigned short* Sb;       // BF16 copy, or null
+};
+bool sinv_build_fits(int max_depth);
+int launch_sinv_build(const SinvBuildArgs& a, cudaStream_t s);
+void sinv_build_depth_steps(const Plan& p, std::vector<int>* ldd);
 int sinv_setup();
 
 }  // namespace silg

@@ -90,9 +90,50 @@ struct Dissector {
 
 }  // namespace
 
+// S~ = L~^-1 P on the host in FP64, column by column over elimination-tree ancestors
+// (Alg. 2, Theorem 1), multithreaded over columns.
+void build_sinv_host(Plan& p, int n_threads) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int nf = p.n_free;
+  p.S.assign(p.rowbase[nf], 0.0);
+  {
+    int nt = n_threads > 0 ? n_threads : (int)std::thread::hardware_concurrency();
+    nt = std::max(1, std::min(nt, 256));
+    std::atomic<int> next_col(0);
+    auto worker = [&]() {
+      std::vector<double> x(nf, 0.0);
+      std::vector<int32_t> path;
+      for (;;) {
+        int j0 = next_col.fetch_add(16);
+        if (j0 >= nf) break;
+        for (int j = j0; j < std::min(nf, j0 + 16); ++j) {
+          path.clear();
+          for (int a = j; a != -1; a = p.parent[a]) path.push_back(a);
+          x[j] = 1.0;
+          for (int a : path) {
+            double xa = x[a] / p.Lx[p.Lp[a]];
+            x[a] = xa;
+            for (int64_t q = p.Lp[a] + 1; q < p.Lp[a + 1]; ++q) x[p.Li[q]] -= p.Lx[q] * xa;
+          }
+          for (int a : path) {
+            p.S[p.rowbase[a] + (j - p.lo[a])] = x[a];
+            x[a] = 0.0;
+          }
+        }
+      }
+    };
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t) th.emplace_back(worker);
+    for (auto& t : th) t.join();
+  }
+  p.s_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  p.s_on_device = 0;
+}
+
 int build_plan(const sim_mesh* mesh, const sim_material* mats, int n_mat, double h,
                int n_threads, Plan* P, std::string* err, const int32_t* vertex_scene,
-               int n_scenes, const double* tri_thickness, const double* vert_bending) {
+               int n_scenes, const double* tri_thickness, const double* vert_bending,
+               bool build_S) {
   auto t0 = std::chrono::steady_clock::now();
   Plan& p = *P;
   if (!mesh || !mesh->rest_pos || mesh->n_verts <= 0 || mesh->n_tets < 0 || mesh->n_tris < 0 ||
@@ -644,37 +685,7 @@ int build_plan(const sim_mesh* mesh, const sim_material* mats, int n_mat, double
     p.rowbase[i + 1] = p.rowbase[i] + (p.hi[i] - p.lo[i]);
     p.nnz_S += i - p.first_desc[i] + 1;
   }
-  p.S.assign(p.rowbase[nf], 0.0);
-  {
-    int nt = n_threads > 0 ? n_threads : (int)std::thread::hardware_concurrency();
-    nt = std::max(1, std::min(nt, 256));
-    std::atomic<int> next_col(0);
-    auto worker = [&]() {
-      std::vector<double> x(nf, 0.0);
-      std::vector<int32_t> path;
-      for (;;) {
-        int j0 = next_col.fetch_add(16);
-        if (j0 >= nf) break;
-        for (int j = j0; j < std::min(nf, j0 + 16); ++j) {
-          path.clear();
-          for (int a = j; a != -1; a = p.parent[a]) path.push_back(a);
-          x[j] = 1.0;
-          for (int a : path) {
-            double xa = x[a] / p.Lx[p.Lp[a]];
-            x[a] = xa;
-            for (int64_t q = p.Lp[a] + 1; q < p.Lp[a + 1]; ++q) x[p.Li[q]] -= p.Lx[q] * xa;
-          }
-          for (int a : path) {
-            p.S[p.rowbase[a] + (j - p.lo[a])] = x[a];
-            x[a] = 0.0;
-          }
-        }
-      }
-    };
-    std::vector<std::thread> th;
-    for (int t = 0; t < nt; ++t) th.emplace_back(worker);
-    for (auto& t : th) t.join();
-  }
+  if (build_S) build_sinv_host(p, n_threads);
   // ---- tiles of the device products ------------------------------------------------
   const int RG = kRowGroup, TW = kTileW;
   p.n_rg = (nf + RG - 1) / RG;

@@ -102,6 +102,8 @@ struct Plan {
   int64_t nnz_A = 0, nnz_L = 0;
   int max_depth = 0, n_roots = 0;
   double mean_depth = 0, seconds = 0;
+  double s_seconds = 0;           // the build of S~ (host loop, or device kernel incl. uploads)
+  int s_on_device = 0;            // 1: S~ was built on the device
 };
 
 // Build the plan. Returns SIM_OK or an error code; *err receives a message.
@@ -109,10 +111,15 @@ struct Plan {
 // scene by scene so that every scene's free vertices are contiguous.
 // tri_thickness (per triangle) and vert_bending (per vertex) override the mesh's single
 // thickness and bending (a batch's scenes each have their own)
+// build_S = false leaves S empty (the profile's shape -- lo, hi, rowbase -- is built): a
+// simulator then builds the values on the device, or with build_sinv_host.
 int build_plan(const sim_mesh* mesh, const sim_material* mats, int n_mat, double h,
                int n_threads, Plan* plan, std::string* err,
                const int32_t* vertex_scene = nullptr, int n_scenes = 1,
-               const double* tri_thickness = nullptr, const double* vert_bending = nullptr);
+               const double* tri_thickness = nullptr, const double* vert_bending = nullptr,
+               bool build_S = true);
+// S~ = L~^-1 P on the host (FP64), into plan->S.
+void build_sinv_host(Plan& p, int n_threads);
 
 // Device work split of one product: CTA c streams tiles [cta_first[c], cta_first[c+1])
 // of the pass's tile order, split so that every CTA has about the same cost; each run of

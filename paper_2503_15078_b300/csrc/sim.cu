@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <array>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -78,6 +79,16 @@ struct sim_s {
     allocs.push_back(p);
     cudaMemsetAsync(p, 0, count * sizeof(T), work);
     return static_cast<T*>(p);
+  }
+  // return one buffer to the allocator before destruction (temporaries of the creation)
+  void release(void* p) {
+    auto it = std::find(allocs.begin(), allocs.end(), p);
+    if (it == allocs.end()) return;
+    if (dev_free)
+      dev_free(p, alloc_ctx);
+    else
+      cudaFree(p);
+    allocs.erase(it);
   }
   template <class T>
   T* upload(const std::vector<T>& v) {
@@ -918,22 +929,57 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   }
   // ---- S~ profile and tile schedule ---------------------------------------------------
   {
-    std::vector<float> Sf(p.S.size());
-    for (size_t k = 0; k < p.S.size(); ++k) Sf[k] = (float)p.S[k];
-    d.S = s->upload(Sf);
     d.s_bf16 = o->s_precision == SIM_S_BF16;
     d.refine = std::max(0, std::min(2, o->refine));
     d.Sb = nullptr;
-    if (d.s_bf16) {
-      // round to nearest even from the FP32 value (finite inputs)
-      std::vector<uint16_t> Sb(Sf.size());
-      for (size_t k = 0; k < Sf.size(); ++k) {
-        uint32_t u;
-        std::memcpy(&u, &Sf[k], 4);
-        u += 0x7fffu + ((u >> 16) & 1u);
-        Sb[k] = (uint16_t)(u >> 16);
+    std::vector<long long> rb(p.rowbase.begin(), p.rowbase.end());
+    d.rowbase = s->upload(rb);
+    d.lo = s->upload(p.lo);
+    d.hi = s->upload(p.hi);
+    // an elimination tree too deep for the device kernel's path vectors: the host builds S~
+    if (p.S.empty() && !silg::sinv_build_fits(p.max_depth)) silg::build_sinv_host(p, o->n_host_threads);
+    if (!p.S.empty()) {
+      std::vector<float> Sf(p.S.size());
+      for (size_t k = 0; k < p.S.size(); ++k) Sf[k] = (float)p.S[k];
+      d.S = s->upload(Sf);
+      if (d.s_bf16) {
+        // round to nearest even from the FP32 value (finite inputs)
+        std::vector<uint16_t> Sb(Sf.size());
+        for (size_t k = 0; k < Sf.size(); ++k) {
+          uint32_t u;
+          std::memcpy(&u, &Sf[k], 4);
+          u += 0x7fffu + ((u >> 16) & 1u);
+          Sb[k] = (uint16_t)(u >> 16);
+        }
+        d.Sb = reinterpret_cast<const unsigned short*>(s->upload(Sb));
       }
-      d.Sb = reinterpret_cast<const unsigned short*>(s->upload(Sb));
+    } else {
+      // S~ = L~^-1 P on the device in FP64 from the host's factor (k_sbuild.cu); the factor
+      // and the kernel's work counter are released once the values are in place
+      const auto t0 = std::chrono::steady_clock::now();
+      const size_t stored = (size_t)p.rowbase[p.n_free];
+      float* Sd = s->alloc<float>(stored);
+      unsigned short* Sbd = d.s_bf16 ? s->alloc<unsigned short>(stored) : nullptr;
+      std::vector<long long> lp(p.Lp.begin(), p.Lp.end());
+      std::vector<int> ldd;
+      silg::sinv_build_depth_steps(p, &ldd);
+      long long* Lp_d = s->upload(lp);
+      int* Ldd_d = s->upload(ldd);
+      double* Lx_d = s->upload(p.Lx);
+      int* ctr = s->alloc<int>(1);
+      silg::SinvBuildArgs a{p.n_free, Lp_d, Ldd_d, Lx_d, d.parent, d.depth, d.rowbase, d.lo,
+                            p.max_depth, ctr, Sd, Sbd};
+      int st = silg::launch_sinv_build(a, s->work);
+      if (st != SIM_OK) return st;
+      const cudaError_t e = cudaStreamSynchronize(s->work);
+      if (e != cudaSuccess) return cuda_status(e);
+      for (void* t : {static_cast<void*>(Lp_d), static_cast<void*>(Ldd_d),
+                      static_cast<void*>(Lx_d), static_cast<void*>(ctr)})
+        s->release(t);
+      d.S = Sd;
+      d.Sb = Sbd;
+      p.s_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      p.s_on_device = 1;
     }
     // A~ over the free vertices (FP64) for residuals of the global solve
     std::vector<int> ap(p.Ap.begin(), p.Ap.end());
@@ -941,10 +987,6 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
     d.A_idx = s->upload(p.Ai);
     d.A_val = s->upload(p.Ax);
     d.gsave = s->alloc<float>(3 * (size_t)p.n_pad);
-    std::vector<long long> rb(p.rowbase.begin(), p.rowbase.end());
-    d.rowbase = s->upload(rb);
-    d.lo = s->upload(p.lo);
-    d.hi = s->upload(p.hi);
     d.n_rg = p.n_rg;
     d.n_ct = p.n_ct;
     int dev = 0, nsm = 0;
@@ -1198,6 +1240,7 @@ int check_options(const sim_options* o) {
   if (o->precond != SIM_PRECOND_DELASSUS && o->precond != SIM_PRECOND_MASS) return SIM_EINVAL;
   if (o->cr_exchanges != 1 && o->cr_exchanges != 2) return SIM_EINVAL;
   if (o->delassus_reuse != 0 && o->delassus_reuse != 1) return SIM_EINVAL;
+  if (o->s_build != 0 && o->s_build != 1) return SIM_EINVAL;
   return SIM_OK;
 }
 
@@ -1442,7 +1485,8 @@ int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_opt
     for (int r = 0; r < 3; ++r) um.handle_vel[r] = scenes[0].mesh.handle_vel[r];
     std::string err;
     int r = silg::build_plan(&um, mats.data(), (int)mats.size(), h, o->n_host_threads, &s->plan,
-                             &err, vscene.data(), n_scenes, trthick.data(), vbend.data());
+                             &err, vscene.data(), n_scenes, trthick.data(), vbend.data(),
+                             o->s_build == 0);
     if (r != SIM_OK) return r;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) return SIM_ECUDA;

@@ -44,6 +44,27 @@ def test_apply_inverse_matches_direct_solve(maker):
     sim.close()
 
 
+@pytest.mark.parametrize("case", ["star", "star_bf16", "batch"])
+def test_device_built_sparse_inverse_equals_the_host_build(case):
+    # S~ = L~^-1 P built on the device in FP64 (one warp per column along its elimination-
+    # tree path) rounds to the same FP32 and BF16 values as the host loop: the solves through
+    # the two simulators are equal bit for bit
+    scene = ([sg.star_pull(n_side=20, layers=12), sg.cube_drop(m=9, model=sg.MODEL_SNH, E=1e6)]
+             if case == "batch" else sg.star_pull(n_side=20, layers=12))
+    prec = 1 if case == "star_bf16" else 0
+    dev = Simulator(scene, s_build=1, s_precision=prec)
+    host = Simulator(scene, s_build=0, s_precision=prec)
+    i_dev, i_host = dev.plan_info(), host.plan_info()
+    assert i_dev["s_built_on_device"] == 1 and i_host["s_built_on_device"] == 0
+    assert i_dev["stored_S"] == i_host["stored_S"] > 0
+    print(f"\nS~ build ({case}): device {i_dev['s_build_seconds']:.3f} s, host "
+          f"{i_host['s_build_seconds']:.3f} s")
+    b = np.random.default_rng(2).normal(size=(dev.n_verts, 3))
+    assert np.array_equal(dev.apply_inverse(b), host.apply_inverse(b))
+    dev.close()
+    host.close()
+
+
 @pytest.mark.parametrize("model", [sg.MODEL_ARAP, sg.MODEL_COROT, sg.MODEL_SNH])
 def test_local_projection_matches_oracle(model):
     sc = sg.cube_drop(m=7, model=model, E=3e5, nu=0.45)

@@ -1,0 +1,84 @@
+"""The pulled star as a trajectory (the benchmark scene's dynamics at a size the oracle runs
+in a minute): a 14 x 14 x 6 star of 3 cm lattice spacing (552 vertices, about as wide as the
+benchmark's) pulled at 0.5 m/s by its pinned cap into the seeded 4 x 4 cylinder field, 150
+frames of 5 local-global and 10 CR iterations, from rest, free-running on the GPU and in the
+FP64 oracle.
+
+Contact switches make the two trajectories part at the first impacts, so the comparison is on
+trajectory measures, frame by frame: the largest penetration (within 1e-3 of the scene's
+residual length L), the energy (within 1e-3 of the largest energy the oracle's trajectory
+reaches; the star starts at rest, so E0 = 0), and the last iteration's residual R (within
+twice the distance between the oracle and the same oracle with its conjugate residual in
+float32, plus 1e-4). Every GPU state stays finite."""
+import numpy as np
+import pytest
+
+import scenegen as sg
+from oracle import Oracle
+
+pytestmark = pytest.mark.gpu
+
+FRAMES = 150
+
+
+def _scene():
+    return sg.star_pull(n_side=14, layers=6, spacing=0.03, seed=0)
+
+
+def _oracle_run(sc, cr=None):
+    import oracle.contact as OC
+    cr64 = OC.conjugate_residual
+    if cr is not None:
+        OC.conjugate_residual = cr
+    try:
+        o = Oracle(sc)
+        q, v = sc.q0.copy(), sc.v0.copy()
+        out = []
+        for _ in range(FRAMES):
+            q, v, info = o.frame(q, v)
+            out.append((o.max_penetration(q), o.energy(q, v),
+                        info["residuals"][-1] if info["residuals"] else 0.0,
+                        len(info["contacts"])))
+    finally:
+        OC.conjugate_residual = cr64
+    return np.array(out)
+
+
+def test_pull_trajectory_matches_the_oracle():
+    import oracle.contact as OC
+    from paper_2503_15078_b300 import Simulator
+    cr64 = OC.conjugate_residual
+
+    def cr32(apply, b, n_iter):
+        return cr64(lambda v: apply(v.astype(np.float64)).astype(np.float32),
+                    b.astype(np.float32), n_iter).astype(np.float64)
+
+    sc = _scene()
+    ref = _oracle_run(sc)
+    ref32 = _oracle_run(sc, cr32)
+    o = Oracle(sc)
+    sim = Simulator(sc)
+    gpu = []
+    for _ in range(FRAMES):
+        sim.step()
+        q, v = sim.state()
+        assert np.all(np.isfinite(q)) and np.all(np.isfinite(v))
+        st = sim.stats()
+        gpu.append((o.max_penetration(q), o.energy(q, v),
+                    st["residuals"][-1] if st["residuals"] else 0.0, st["n_contacts"]))
+    gpu = np.array(gpu)
+    sim.close()
+    L = sc.bbox_diagonal
+    e_scale = np.abs(ref[:, 1]).max()
+    d_pen = np.abs(gpu[:, 0] - ref[:, 0]).max() / L
+    d_en = np.abs(gpu[:, 1] - ref[:, 1]).max() / e_scale
+    d_res = np.abs(gpu[:, 2] - ref[:, 2]).max()
+    d_res32 = np.abs(ref32[:, 2] - ref[:, 2]).max()
+    contact_frames = int((ref[:, 3] > 0).sum())
+    print(f"\npull trajectory: {contact_frames} contact frames (max {int(ref[:, 3].max())} "
+          f"contacts); penetration {d_pen:.2e} L, energy {d_en:.2e} of max, residual "
+          f"{d_res:.2e} (oracle float32-CR {d_res32:.2e})")
+    assert contact_frames >= 40
+    assert d_pen <= 1e-3
+    assert d_en <= 1e-3
+    assert d_res <= 2 * d_res32 + 1e-4
