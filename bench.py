@@ -46,7 +46,7 @@ UNIT = "ms/iter"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--placement", type=float, default=0.094,
@@ -59,6 +59,8 @@ def parse():
                     help="skip the timing of the paper's variants on the star frame")
     ap.add_argument("--no-warmstart", action="store_true",
                     help="skip the learned-vs-plain frame time to residual 1e-4")
+    ap.add_argument("--no-batch64", action="store_true",
+                    help="skip the 64-scene BF16 batch sub-record")
     ap.add_argument("--no-trajectory", action="store_true",
                     help="skip the 300-frame pulls through the cylinders (seeds 0-4)")
     ap.add_argument("--workload", choices=["star", "batch64", "stack"], default="star",
@@ -322,15 +324,22 @@ def warmstart_ab():
     Xv, Tv = warmstart.collect(sg.warmstart_scenes(range(200, 204), frames=80), frames=80,
                                n_iters=20)
     net, losses = warmstart.train(X, T, epochs=60, batch=512, lr=1e-3, seed=0, X_val=Xv, T_val=Tv)
+    # the blend of the network's outputs with the previous frame's start, chosen on the
+    # validation seeds by frame time to the tolerance
+    gains, table = warmstart.choose_gains(net, sg.warmstart_scenes(range(200, 204), frames=60),
+                                          60)
     modes = ["cold", "previous", "learned", "portfolio"]
     held_out = sg.warmstart_scenes(range(100, 105), frames=60)
-    traces = warmstart.evaluate_from_states(held_out, 60, modes, net=net)
-    timed = warmstart.evaluate_to_tolerance(held_out, 60, modes, net=net)
+    traces = warmstart.evaluate_from_states(held_out, 60, modes, net=net, gains=gains)
+    timed = warmstart.evaluate_to_tolerance(held_out, 60, modes, net=net, gains=gains)
     out = {"workload": "6^3 cube drops (config-1 scene, seeded height/rotation/tilt); 16 "
                        "training seeds x 80 frames, 4 validation seeds (output shrinkage), "
                        "5 held-out seeds x 60 frames",
            "training_samples": int(len(X)), "train_loss": [float(losses[0]), float(losses[-1])],
-           "tolerance": 1e-4, "max_iters": 40}
+           "tolerance": 1e-4, "max_iters": 40,
+           "gains": {"persist": gains[0], "fresh": gains[1], "move": gains[2],
+                     "validation": {f"{g[0]},{g[1]},{g[2]}": [round(v[0], 2), round(v[1], 4)]
+                                    for g, v in table.items()}}}
     for m in modes:
         R5 = traces[m]["residuals"][:, 5]
         r = timed[m]
@@ -519,6 +528,48 @@ def pull_trajectory(n_side, frames, seeds, steps, flush):
     return out
 
 
+def batch64_record(steps, flush):
+    """The batch workload as a sub-record of the default run: 64 cubes of 8^3..20^3 vertices
+    (seeded; mixed materials, tilted planes) in one simulator, S~ in BF16 with FP32
+    accumulation and one FP32 residual correction per frame, each placed a quarter lattice
+    spacing into its plane; every step replays one frame (L2 flushed before it). Reports ms
+    per local-global iteration of the whole batch and the products' roofline on their BF16
+    bytes (per launch, mean of both products, timed by the instrumented graph's event
+    nodes)."""
+    import torch
+    import scenegen as sg
+    from paper_2503_15078_b300 import Simulator
+    scenes = sg.batch(n_scenes=64, seed=0)
+    q0, v0 = batch_state(scenes)
+    sim = Simulator(scenes, s_precision=1, refine=1, autotune=1, contact_capacity=16384)
+    n_iters = scenes[0].n_iters
+    prod, inst = [], []
+    for marks, acc in ((False, prod), (True, inst)):
+        sim.set_phase_marks(marks)
+        for k in range(3 + steps):
+            sim.set_state(q0, v0)
+            flush.zero_()
+            torch.cuda.synchronize()
+            sim.step()
+            if k >= 3:
+                acc.append(sim.phase_times())
+    info = sim.plan_info()
+    ph = {k: statistics.mean(p[k] for p in inst) for k in inst[0]}
+    t_pass = (ph["spmv1"] + ph["spmv2"]) / (2 * n_iters)
+    bytes_pass = 2 * info["nnz_S"] + 2 * 12 * info["n_free"]
+    peak, kind = measured_peaks()
+    out = {"scenes": 64, "dofs": 3 * sim.n_verts, "nnz_S": info["nnz_S"],
+           "contacts": sim.stats()["n_contacts"], "s_precision": "bf16", "refine": 1,
+           "ms_per_iter": round(statistics.mean(sum(p.values()) for p in prod) / n_iters, 5),
+           "roofline": {"kernel": "S~ profile products, BF16 values (mean of both, per launch)",
+                        "bound": "hbm", "achieved": round(bytes_pass / (t_pass * 1e-3) / 1e9, 1),
+                        "peak": peak, "peak_source": kind, "unit": "GB/s",
+                        "frac": round(bytes_pass / (t_pass * 1e-3) / 1e9 / peak, 4),
+                        "algorithmic_bytes_per_pass": bytes_pass}}
+    sim.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -609,8 +660,13 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     clocks = clk.summary()
-    mean_frame = statistics.mean(sum(p.values()) for p in prod_frames)
+    frame_ms = sorted(sum(p.values()) for p in prod_frames)
+    mean_frame = statistics.mean(frame_ms)
     mean_frame = max_over_ranks(mean_frame)
+    spread = {"median_ms_per_iter": round(statistics.median(frame_ms) / n_iters, 5),
+              "p10_ms_per_iter": round(frame_ms[len(frame_ms) // 10] / n_iters, 5),
+              "p90_ms_per_iter": round(frame_ms[(9 * len(frame_ms)) // 10] / n_iters, 5),
+              "timed_frames": len(frame_ms)}
     instrumented_frame = statistics.mean(sum(p.values()) for p in frames)
     phase_mean = {k: statistics.mean(p[k] for p in frames) for k in frames[0]}
     stats = sim.stats()
@@ -702,6 +758,7 @@ def run_ours(args):
             "parallelism": (f"scene shards x{world} of one {n_batch}-scene batch" if batch
                             else f"replicas x{world}") if world > 1 else "single GPU",
         },
+        "spread": spread,
         "phases_ms_per_frame": {k: round(v, 5) for k, v in phase_mean.items()},
         "instrumented_ms_per_step": round(instrumented_frame, 5),
         "wall_ms_per_step": round(1e3 * t_wall / args.steps, 4),
@@ -726,6 +783,8 @@ def run_ours(args):
     }
     if rank == 0 and not batch and not args.no_variants:
         out["variants"] = variants_timing(scene, q0, v0, min(args.steps, 10), flush)
+    if rank == 0 and not batch and not args.no_batch64:
+        out["batch64"] = batch64_record(min(args.steps, 20), flush)
     if rank == 0 and not batch and not args.no_trajectory:
         out["pull_trajectory"] = pull_trajectory(args.n_side, 300, range(5),
                                                  min(args.steps, 20), flush)

@@ -469,6 +469,14 @@ int sim_mlp_train(sim_mlp_t* net, const float* X, const float* T, int32_t rows, 
  * if the residual of its impulses at k = 0 (at the position they predict) is below the cold
  * start's. */
 int sim_set_warmstart(sim_t* sim, const sim_mlp_t* net, int32_t mode);
+/* Gains of the network's outputs in the learned start (not from the paper): lambda^0 =
+ * (previous impulse + g x predicted change) x scale with g = persist for a contact that had
+ * an impulse at the same vertex and obstacle in the previous frame and g = fresh for a new
+ * one; the normal move is scaled by move. 0 leaves that part at the previous frame's value
+ * (persist, fresh) or at no move; 1, 1, 1 (the default) is the network as trained. Chosen,
+ * for example, on validation frames by iterations to a residual tolerance. Non-negative
+ * finite values, else SIM_EINVAL. Synchronises the handle's stream. */
+int sim_set_warmstart_gains(sim_t* sim, float persist, float fresh, float move);
 /* Load a trained warm-start network and switch the learned start on (mode 1 of
  * sim_set_warmstart): weights is the flat FP32 parameter vector in the layout above
  * (SIM_MLP_PARAMS values, as sim_mlp_get_params writes it), bytes = 4 * SIM_MLP_PARAMS.

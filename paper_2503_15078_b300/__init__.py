@@ -318,6 +318,12 @@ class Simulator:
         _check(lib().sim_set_warmstart(self._h, net.handle if net is not None else None,
                                        int(mode)), "sim_set_warmstart")
 
+    def set_warmstart_gains(self, persist=1.0, fresh=1.0, move=1.0):
+        """Gains of the network's outputs in the learned start (persisting contacts' impulse
+        change, new contacts' impulse, normal move)."""
+        _check(lib().sim_set_warmstart_gains(self._h, float(persist), float(fresh), float(move)),
+               "sim_set_warmstart_gains")
+
     def set_phase_marks(self, on):
         """Event nodes around every phase of every iteration (True) or only around the
         once-per-frame phases, the iterations timed as one phase (False)."""

@@ -133,6 +133,10 @@ struct DevSim {
   // copy continues from the copy with the lowest final residual (1: off)
   int pf_copies;
   MlpDev ws_net;              // BF16 weights (w_t) and the parameter vector (biases)
+  // gains of the network's outputs in the learned start: the impulse change of a contact
+  // that had an impulse at the same vertex and obstacle in the previous frame, the impulse
+  // of a new contact, the normal move (1, 1, 1 by default)
+  float ws_gain[3];
   float* ws_feat;             // cap x kMlpIn: features at the frame start
   float* ws_out;              // cap x kMlpOut: network outputs
   double* ws_scale;           // cap: impulse scale margin / (h^2 W~_vv)
@@ -223,6 +227,14 @@ struct DevSim {
   int dl_reuse_on;
   int* dl_state;
   int* dl_prev_cv;  // cap: the previous frame's contact vertices
+  // Y^T z and Y u in chunks of 256 path entries (k_ytz_chunk, k_yu_chunk; 0 chunks: the
+  // one-warp or one-CTA per vertex (row) kernels): chunks per contact vertex and per row of
+  // U, partial sums per (vertex or row, chunk), completion counters (zero between launches)
+  int ytz_nch, yu_nch;
+  float4* ytz_part;
+  int* ytz_done;
+  float4* yu_part;
+  int* yu_done;
   int ytz_warp;     // Y^T z with a warp per contact vertex (short ancestor paths) instead
                     // of a CTA per contact vertex
   const float* zero;  // kTileW zeros: the load target of lanes outside a row's range

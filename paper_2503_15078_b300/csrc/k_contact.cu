@@ -1116,6 +1116,137 @@ __global__ void k_ytz_warp(DevSim d) {
   }
 }
 
+// Y^T z and Y u in chunks of kYChunk path entries, one warp per (vertex or row, chunk), so
+// that every contact vertex's long ancestor path (and every long row of U) is spread over
+// many warps. A chunk's partial sums go to scratch; the warp that completes the last chunk
+// of a vertex (row) -- counted with an atomic, which that warp resets for the next launch --
+// adds the partials in chunk order (deterministic) and finishes the vertex (row).
+constexpr int kYChunk = 256;
+
+// the Schur right-hand side h^-2 (h - J A^-1 g) of the contacts at contact vertex c, from
+// s = (Y^T z)_c (their own contacts; a contact with another body in k_body_rhs)
+__device__ __forceinline__ void ytz_finish(const DevSim& d, int c, float s0, float s1, float s2,
+                                           int lane) {
+  const double ih2 = 1.0 / (d.h * d.h);
+  if (d.bc_on && lane == 0) {
+    d.svec[3 * c] = s0;
+    d.svec[3 * c + 1] = s1;
+    d.svec[3 * c + 2] = s2;
+  }
+  const int j0 = d.cv_first[c], j1 = min(j0 + d.cv_nct[c], d.cap);
+  for (int j = j0 + lane; j < j1; j += 32) {
+    if (d.bc_on && d.ct_tri[j] >= 0) continue;   // k_body_rhs
+    for (int r = 0; r < 3; ++r) {
+      const float* Dr = d.ct_Df + 9 * j + 3 * r;
+      const float jag = d.ct_omega[3 * j + r] * (Dr[0] * s0 + Dr[1] * s1 + Dr[2] * s2);
+      d.ct_rhs[3 * j + r] = (float)((d.ct_hv[3 * j + r] - (double)jag) * ih2);
+    }
+  }
+}
+
+__global__ void k_ytz_chunk(DevSim d) {
+  pdl_wait();
+  const int ncv = min(d.counters[kCntCv], d.cap);
+  if (d.yc_ptr[ncv] > d.cap_y) return;   // uniform over the grid
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5, nch = d.ytz_nch;
+  for (int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < ncv * nch; item += nwarps) {
+    const int c = item / nch, h = item - c * nch;
+    const int k0 = d.yc_ptr[c], len = d.yc_ptr[c + 1] - k0;
+    const int n_c = max(1, (len + kYChunk - 1) / kYChunk);
+    if (h >= n_c) continue;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    const int kb = k0 + h * kYChunk, ke = min(k0 + len, kb + kYChunk);
+#pragma unroll 4
+    for (int k = kb + lane; k < ke; k += 32) {
+      const float y = d.yc_val[k];
+      const int a = d.yc_row[k];
+      s0 += y * d.zvec[a];
+      s1 += y * d.zvec[d.n_pad + a];
+      s2 += y * d.zvec[2 * d.n_pad + a];
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if (n_c == 1) {            // a short path: one chunk, finished here
+      ytz_finish(d, c, s0, s1, s2, lane);
+      continue;
+    }
+    int last = 0;
+    if (lane == 0) {
+      d.ytz_part[(size_t)c * nch + h] = make_float4(s0, s1, s2, 0.f);
+      __threadfence();
+      last = atomicAdd(d.ytz_done + c, 1) == n_c - 1;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) continue;
+    __threadfence();
+    s0 = s1 = s2 = 0.f;
+    for (int q = 0; q < n_c; ++q) {    // every lane, in chunk order
+      const float4 t = __ldcg(d.ytz_part + (size_t)c * nch + q);
+      s0 += t.x;
+      s1 += t.y;
+      s2 += t.z;
+    }
+    if (lane == 0) d.ytz_done[c] = 0;
+    ytz_finish(d, c, s0, s1, s2, lane);
+  }
+}
+
+// y = z + h^2 Y u on the rows of U, in chunks of each row's contact-vertex interval
+__global__ void k_yu_chunk(DevSim d) {
+  pdl_wait();
+  const int lane = threadIdx.x & 31, nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int nU = d.counters[kCntU], nch = d.yu_nch;
+  if (d.y_ptr[nU] > d.cap_y) return;
+  const float h2 = (float)(d.h * d.h);
+  for (int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < nU * nch; item += nwarps) {
+    const int idx = item / nch, h = item - idx * nch;
+    const int len = d.u_len[idx];
+    const int n_c = max(1, (len + kYChunk - 1) / kYChunk);
+    if (h >= n_c) continue;
+    const int clo = d.u_clo[idx], base = d.y_ptr[idx];
+    const int kb = h * kYChunk, ke = min(len, kb + kYChunk);
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+#pragma unroll 4
+    for (int k = kb + lane; k < ke; k += 32) {
+      const float y = d.y_val[base + k];
+      const float* u = d.uvec + 3 * (clo + k);
+      t0 += y * u[0];
+      t1 += y * u[1];
+      t2 += y * u[2];
+    }
+    t0 = warp_sum(t0);
+    t1 = warp_sum(t1);
+    t2 = warp_sum(t2);
+    if (n_c > 1) {
+      int last = 0;
+      if (lane == 0) {
+        d.yu_part[(size_t)idx * nch + h] = make_float4(t0, t1, t2, 0.f);
+        __threadfence();
+        last = atomicAdd(d.yu_done + idx, 1) == n_c - 1;
+      }
+      last = __shfl_sync(0xffffffffu, last, 0);
+      if (!last) continue;
+      __threadfence();
+      t0 = t1 = t2 = 0.f;
+      for (int q = 0; q < n_c; ++q) {
+        const float4 t = __ldcg(d.yu_part + (size_t)idx * nch + q);
+        t0 += t.x;
+        t1 += t.y;
+        t2 += t.z;
+      }
+      if (lane == 0) d.yu_done[idx] = 0;
+    }
+    if (lane == 0) {
+      const int a = d.u_list[idx];
+      d.zvec[a] += h2 * t0;
+      d.zvec[d.n_pad + a] += h2 * t1;
+      d.zvec[2 * d.n_pad + a] += h2 * t2;
+    }
+  }
+}
+
 // the Schur right-hand side of the contacts with another body, whose J A^-1 g combines
 // (Y^T z) of the vertex and the triangle's corners with the map's weights
 __global__ void k_body_rhs(DevSim d) {
@@ -2192,7 +2323,9 @@ void launch_iter_decide(const DevSim& d, cudaStream_t s, cudaGraphConditionalHan
 void launch_iter_clear(const DevSim& d, cudaStream_t s) { k_iter_clear<<<1, 256, 0, s>>>(d); }
 
 void launch_ytz(const DevSim& d, cudaStream_t s) {
-  if (d.ytz_warp)
+  if (d.ytz_nch > 0)
+    launch_k(d.pdl, k_ytz_chunk, 8 * d.n_sm, 256, 0, s, d);
+  else if (d.ytz_warp)
     launch_k(d.pdl, k_ytz_warp, std::min((d.cap + 7) / 8, 8 * d.n_sm), 256, 0, s, d);
   else
     launch_k(d.pdl, k_ytz, std::min(d.cap, 8 * d.n_sm), kYtzThreads, 0, s, d);
@@ -2200,7 +2333,10 @@ void launch_ytz(const DevSim& d, cudaStream_t s) {
 }
 
 void launch_yu(const DevSim& d, cudaStream_t s) {
-  launch_k(d.pdl, k_yu, std::min((d.n * 32 + 255) / 256, 8 * d.n_sm), 256, 0, s, d);
+  if (d.yu_nch > 0)
+    launch_k(d.pdl, k_yu_chunk, 8 * d.n_sm, 256, 0, s, d);
+  else
+    launch_k(d.pdl, k_yu, std::min((d.n * 32 + 255) / 256, 8 * d.n_sm), 256, 0, s, d);
 }
 
 static size_t g_cr_smem = 0;

@@ -85,11 +85,14 @@ __device__ void ws_guess(const DevSim& d, int j) {
     const float* f = d.ws_feat + (size_t)j * kMlpIn;
     for (int r = 0; r < 3; ++r) lam[r] = (double)f[7 + r] * scale;
   } else if (d.ws_mode == 1) {
-    // the network predicts the change from the previous frame's impulse (features 7..9)
+    // the network predicts the change from the previous frame's impulse (features 7..9),
+    // scaled by the gain of its contact class (persisting or new)
     const float* y = d.ws_out + (size_t)j * kMlpOut;
     const float* f = d.ws_feat + (size_t)j * kMlpIn;
-    for (int r = 0; r < 3; ++r) lam[r] = ((double)f[7 + r] + (double)y[r]) * scale;
-    move = (double)y[3] * margin;
+    const bool persists = d.prev_valid[v] && d.prev_obst[v] == d.ct_obst[j];
+    const double g = persists ? d.ws_gain[0] : d.ws_gain[1];
+    for (int r = 0; r < 3; ++r) lam[r] = ((double)f[7 + r] + g * (double)y[r]) * scale;
+    move = (double)d.ws_gain[2] * (double)y[3] * margin;
   } else {
     const float* f = d.ws_feat + (size_t)j * kMlpIn;
     for (int r = 0; r < 3; ++r) lam[r] = (double)f[7 + r] * scale;

@@ -1083,6 +1083,14 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   cudaMemsetAsync(d.dl_state + 1, 0xff, sizeof(int), s->work);   // no previous list yet
   // the path of a contact vertex in Y is its ancestor chain: a warp covers a short one
   d.ytz_warp = p.mean_depth < 600.0 ? 1 : 0;
+  // chunks of 256 entries: a contact vertex's path is at most the tree depth long, a row of
+  // U's interval at most the contact capacity
+  d.ytz_nch = (p.max_depth + 255) / 256 + 1;
+  d.yu_nch = (cap + 255) / 256;
+  d.ytz_part = s->alloc<float4>((size_t)cap * d.ytz_nch);
+  d.ytz_done = s->alloc<int>(cap);
+  d.yu_part = s->alloc<float4>((size_t)n * d.yu_nch);
+  d.yu_done = s->alloc<int>(n);
   d.spin_limit = o->spin_limit;
   d.kb_lo = s->alloc<int>(n / 32 + 1);
   d.kb_hi = s->alloc<int>(n / 32 + 1);
@@ -1124,6 +1132,7 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
     if (st != SIM_OK) return st;
   }
   d.cr_R = s->cluster;
+  d.ws_gain[0] = d.ws_gain[1] = d.ws_gain[2] = 1.f;
   d.cr_single = o->cr_exchanges == 1 ? 1 : 0;
   if (o->autotune) {
     int st = autotune_products(s);
@@ -1565,6 +1574,23 @@ int sim_set_warmstart(sim_t* s, const sim_mlp_t* net, int32_t mode) {
   }
   s->d.ws_mode = mode;   // graphs are cached per mode; the network's weights are read at launch
   delassus_forget(s, s->launch);
+  return SIM_OK;
+}
+
+int sim_set_warmstart_gains(sim_t* s, float persist, float fresh, float move) {
+  if (!s || !std::isfinite(persist) || !std::isfinite(fresh) || !std::isfinite(move) ||
+      persist < 0.f || fresh < 0.f || move < 0.f)
+    return SIM_EINVAL;
+  s->d.ws_gain[0] = persist;   // read at graph capture: the cached graphs are dropped
+  s->d.ws_gain[1] = fresh;
+  s->d.ws_gain[2] = move;
+  silg::DeviceGuard dg(s->device);
+  cudaStreamSynchronize(s->launch);
+  for (auto& kv : s->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.g) cudaGraphDestroy(kv.second.g);
+  }
+  s->graphs.clear();
   return SIM_OK;
 }
 

@@ -69,7 +69,8 @@ def train(X, T, epochs=60, batch=512, lr=1e-3, seed=0, device=0, X_val=None, T_v
     return net, losses
 
 
-def evaluate_from_states(scenes, frames, modes, net=None, k_max=40, tol=1e-4, **opts):
+def evaluate_from_states(scenes, frames, modes, net=None, k_max=40, tol=1e-4, gains=None,
+                         **opts):
     """A/B from identical states: each scene's reference trajectory is run with the cold start
     and k_max iterations per frame; every frame with contacts is then replayed once per
     start in `modes` from the reference state of the frame before it (one cold frame to set
@@ -97,6 +98,10 @@ def evaluate_from_states(scenes, frames, modes, net=None, k_max=40, tol=1e-4, **
         if pf_modes:
             pf = Simulator([sc, sc], n_iters=k_max, **opts)
             pf.set_portfolio(2)
+        if gains is not None:
+            for s_g in (sim, pf):
+                if s_g is not None:
+                    s_g.set_warmstart_gains(*gains)
         for f in range(1, len(contact)):
             if not contact[f]:
                 continue
@@ -144,11 +149,13 @@ def evaluate_from_states(scenes, frames, modes, net=None, k_max=40, tol=1e-4, **
     return res
 
 
-def evaluate_to_tolerance(scenes, frames, modes, net=None, k_max=40, tol=1e-4, **opts):
+def evaluate_to_tolerance(scenes, frames, modes, net=None, k_max=40, tol=1e-4, gains=None,
+                          **opts):
     """The A/B of evaluate_from_states with frames that stop on the device when the residual
     reaches tol (sim_options.residual_tol; at least one update, at most k_max): per mode the
     updates each contact frame took and its measured device time (the whole frame: collision,
-    Delassus, start, iterations, integration). A portfolio stops when either copy is done."""
+    Delassus, start, iterations, integration). A portfolio stops when either copy is done.
+    gains: (persist, fresh, move) output gains of the learned start (sim_set_warmstart_gains)."""
     out = {m: {"iters": [], "ms": []} for m in modes}
     for sc in scenes:
         ref = Simulator(sc, n_iters=k_max, **opts)
@@ -169,6 +176,8 @@ def evaluate_to_tolerance(scenes, frames, modes, net=None, k_max=40, tol=1e-4, *
                             max_iters=k_max, **opts)
             if pf:
                 sim.set_portfolio(2)
+            if gains is not None:
+                sim.set_warmstart_gains(*gains)
             sims[m] = sim
         for f in range(1, len(contact)):
             if not contact[f]:
@@ -238,3 +247,19 @@ def evaluate(scenes, frames, mode, net=None, k_max=40, tol=1e-4, **opts):
             "unreached": int((iters > k_max).sum()),
             "mean_ms": float(np.nanmean(ms)) if len(ms) else 0.0,
             "diverged": int(np.isnan(ms).sum())}
+
+
+GAIN_GRID = [(p, f, m) for p in (0.0, 0.5, 1.0) for f in (0.0, 0.5, 1.0) for m in (0.0, 1.0)]
+
+
+def choose_gains(net, scenes, frames, grid=GAIN_GRID, k_max=40, tol=1e-4, **opts):
+    """The output gains of the learned start that give the lowest mean frame time to the
+    residual tolerance on validation scenes (device-stopped frames, the measure of the
+    held-out A/B). Returns (gains, {gains: (mean updates, mean ms)})."""
+    table = {}
+    for g in grid:
+        r = evaluate_to_tolerance(scenes, frames, ["learned"], net=net, k_max=k_max, tol=tol,
+                                  gains=g, **opts)["learned"]
+        table[g] = (r["mean_iters"], r["mean_ms"])
+    best = min(grid, key=lambda g: (table[g][1], table[g][0], g))
+    return best, table
