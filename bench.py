@@ -365,7 +365,7 @@ def variants_timing(scene, q0, v0, steps, flush):
     from paper_2503_15078_b300 import Simulator
     cases = {"minmap": dict(ncp="minmap"), "mass_precond": dict(precond="mass"),
              "admm_pd": dict(local_solver="admm"), "anchored_handle": {},
-             "cr_two_exchanges": dict(cr_exchanges=2)}
+             "cr_cluster_barriers": dict(cr_sync=1), "cr_one_exchange": dict(cr_exchanges=1)}
     out = {}
     for name, kw in cases.items():
         sc, v = scene, v0.copy()
@@ -783,6 +783,17 @@ def run_ours(args):
     }
     if rank == 0 and not batch and not args.no_variants:
         out["variants"] = variants_timing(scene, q0, v0, min(args.steps, 10), flush)
+    if rank == 0 and not batch:
+        # the cost of one phase boundary: a kernel per phase in a graph with programmatic
+        # dependent launch (the frame graph) against a grid barrier in one cooperative
+        # kernel (a persistent kernel per iteration), at one and two CTAs per SM
+        from paper_2503_15078_b300 import measure_phase_boundaries
+        lb = {}
+        for cps in (1, 2):
+            g_us, b_us = measure_phase_boundaries(n_phases=128, ctas_per_sm=cps, device=local)
+            lb[f"{cps}_cta_per_sm"] = {"graph_pdl_us": round(g_us, 3),
+                                       "grid_barrier_us": round(b_us, 3)}
+        out["phase_boundary"] = lb
     if rank == 0 and not batch and not args.no_batch64:
         out["batch64"] = batch64_record(min(args.steps, 20), flush)
     if rank == 0 and not batch and not args.no_trajectory:

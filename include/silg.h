@@ -161,13 +161,25 @@ typedef struct {
   void* (*dev_alloc)(size_t bytes, void* ctx);
   void (*dev_free)(void* ptr, void* ctx);
   void* alloc_ctx;
-  int32_t cr_exchanges;        /* cluster exchanges per conjugate-residual iteration: 1
-                                  (default) where a scene's layout fits in shared memory and
-                                  it has no contacts between bodies (the vertex images of r
-                                  and Ap are advanced by the iteration's recurrences), else
-                                  2; 2: always the two-exchange form (one for the product's
-                                  input, one for the dot products). Both give the same
-                                  iteration up to rounding. Other values: SIM_EINVAL.   */
+  int32_t cr_exchanges;        /* cluster exchanges per conjugate-residual iteration: 2
+                                  (default) one for the product's input and one for the dot
+                                  products, the iteration as written; 1 one exchange (the
+                                  vertex images of r and Ap advanced by the iteration's own
+                                  recurrences) for scenes without contacts between bodies
+                                  (with them: 2). Equal in exact arithmetic; in FP32 the
+                                  one-exchange form can end an order of magnitude further
+                                  from the FP64 iteration on ill-conditioned systems, and
+                                  its vertex vectors (64 bytes per contact vertex of a scene
+                                  in shared memory) must fit, else SIM_ECAPACITY. Other
+                                  values: SIM_EINVAL.                                    */
+  int32_t cr_sync;             /* how the CTAs of a constraint-solve cluster exchange their
+                                  data in the two-exchange form: 0 (default) point to point,
+                                  stores into the other CTAs' shared memory that count their
+                                  bytes on the receiver's barrier (st.async, mbarrier), each
+                                  CTA waiting only for its own data; 1 a cluster-wide barrier
+                                  after each exchange. Same results bit for bit. Scenes with
+                                  contacts between bodies always use 1. Other values:
+                                  SIM_EINVAL.                                            */
   int32_t s_build;             /* where a simulator builds S~ = L~^-1 P from the host's
                                   FP64 Cholesky factor: 1 (default) on the device in FP64
                                   (one warp per column along its elimination-tree path; the
@@ -533,6 +545,21 @@ int sim_get_warmstart_samples(sim_t* sim, int32_t capacity, float* X, float* T, 
  * pending on the thread is cleared at entry, not reported here.
  */
 int sim_apply_inverse_noalloc(const sim_t* sim, const float* g, float* x, void* stream);
+
+/*
+ * A diagnostic of the frame's structure (not from the paper): the device time per phase
+ * boundary of a chain of n_phases small phases on `device`, run (a) as one kernel per phase in
+ * a CUDA graph with programmatic dependent launch (how the frame graph chains the steps of an
+ * iteration) and (b) as one cooperative kernel whose phases are separated by a software grid
+ * barrier (how a persistent kernel per iteration would separate them), each with
+ * ctas_per_sm CTAs of 256 threads per SM; medians over 20 runs, microseconds per boundary.
+ * The barrier's wait is bounded: SIM_ETIMEOUT if it gave up (the numbers are then not
+ * meaningful). Allocates and frees its own small buffers. Errors: SIM_EINVAL (n_phases
+ * outside 2..4096, ctas_per_sm outside 1..8, null outputs), SIM_ENOTSUP (no cooperative
+ * launch, or that many CTAs cannot be resident), SIM_ECUDA.
+ */
+int sim_measure_phase_boundaries(int32_t device, int32_t n_phases, int32_t ctas_per_sm,
+                                 double* graph_us, double* barrier_us);
 
 #ifdef __cplusplus
 }

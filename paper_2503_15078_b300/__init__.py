@@ -172,6 +172,17 @@ class Plan:
         return x
 
 
+def measure_phase_boundaries(n_phases=64, ctas_per_sm=1, device=0):
+    """Device microseconds per phase boundary: (kernel per phase in a CUDA graph with
+    programmatic dependent launch, software grid barrier in one cooperative kernel)."""
+    a = np.zeros(1)
+    b = np.zeros(1)
+    _check(lib().sim_measure_phase_boundaries(int(device), int(n_phases), int(ctas_per_sm),
+                                              _dptr(a), _dptr(b)),
+           "sim_measure_phase_boundaries")
+    return float(a[0]), float(b[0])
+
+
 def _torch_stream():
     try:
         import torch

@@ -66,7 +66,7 @@ class SimOptions(C.Structure):
                 ("local_solver", C.c_int32), ("global_solver", C.c_int32),
                 ("jacobi_sweeps", C.c_int32), ("phase_marks", C.c_int32),
                 ("dev_alloc", DEV_ALLOC), ("dev_free", DEV_FREE), ("alloc_ctx", C.c_void_p),
-                ("cr_exchanges", C.c_int32), ("s_build", C.c_int32),
+                ("cr_exchanges", C.c_int32), ("cr_sync", C.c_int32), ("s_build", C.c_int32),
                 ("delassus_reuse", C.c_int32)]
 
 
@@ -146,6 +146,7 @@ PROTOTYPES = {
     "sim_local_project": (C.c_int, [C.c_void_p, _dp, _dp]),
     "sim_get_delassus": (C.c_int, [C.c_void_p, C.c_int32, _dp, _ip, _ip]),
     "sim_apply_inverse_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sim_measure_phase_boundaries": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _dp, _dp]),
 }
 
 

@@ -50,7 +50,7 @@ void sim_default_options(sim_options* o) {
   o->global_solver = SIM_GLOBAL_SPARSE_INVERSE;
   o->jacobi_sweeps = 1;
   o->phase_marks = 1;
-  o->cr_exchanges = 1;
+  o->cr_exchanges = 2;
   o->s_build = 1;
   o->delassus_reuse = 1;
 }

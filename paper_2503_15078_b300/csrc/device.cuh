@@ -321,7 +321,8 @@ struct DevSim {
   float* wt_part;   // partial 64 x 64 tiles of W~
   int wt_grid;      // CTAs of the W~ product
   int cr_R;         // CTAs per CR cluster (one cluster per scene)
-  int cr_single;    // 1: one cluster exchange per CR iteration where it fits; 0: two always
+  int cr_single;    // 1: one cluster exchange per CR iteration (k_cr1); 0: two (k_cr)
+  int cr_sync;      // k_cr's exchanges: 0 point-to-point (st.async + mbarrier), 1 cluster barriers
   int* cr_split;    // per scene 2 (kCrMaxRanks + 1): first contact vertex (scene-local) and
                     // first contact (global) of each rank
   unsigned long long spin_limit;  // polls of a device-side wait before it reports a timeout

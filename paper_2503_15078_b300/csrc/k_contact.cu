@@ -1311,7 +1311,6 @@ __global__ void k_yu(DevSim d) {
 // cluster in rank order, so every CTA holds the same scalars and the result is
 // deterministic.
 constexpr unsigned kBulkChunk = 32768;  // bytes per bulk-copy instruction
-constexpr int kCrG = 8;  // register-held column groups per lane: W~ rows up to 1024 wide
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -1333,22 +1332,89 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, unsigne
   return false;
 }
 
+// Point-to-point exchange between the CTAs of a cluster: 16-byte stores into another CTA's
+// shared memory (st.async) that count their bytes on that CTA's mbarrier, which its threads
+// wait on (cluster-scope acquire) instead of a cluster-wide barrier.
+__device__ __forceinline__ unsigned mapa_u32(unsigned addr, int rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_async_v4(unsigned remote_addr, float4 v, unsigned remote_bar) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::
+          "r"(remote_addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(remote_bar) : "memory");
+}
+// this CTA's arrival on its barrier for the current phase, expecting `bytes` from the stores
+__device__ __forceinline__ void mbar_expect(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cluster.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+               "r"(bytes) : "memory");
+}
+// wait for phase `parity` with cluster-scope acquire (the stores of other CTAs become
+// visible), at most `limit` polls (0: 2^22); false on timeout
+__device__ __forceinline__ bool mbar_wait_cluster(unsigned bar, unsigned parity,
+                                                  unsigned long long limit) {
+  if (limit == 0) limit = 1ull << 22;
+  for (unsigned long long i = 0; i < limit; ++i) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
 struct CrLayout {
   int R, rank, c, ncv, cv0, cv1, j0, j1;
 };
 
-// Shared arrays of the two constraint-solve bodies, declared once in the kernel.
-struct CrShared {
-  int* split_cv;               // kCrMaxRanks + 1
-  int* split_j;                // kCrMaxRanks + 1
-  unsigned long long* wbar;    // mbarrier of the bulk copy of the W~ rows
-  float (*wpart)[32];          // [3][32] per-warp partial sums
-  float* red3;                 // 3
-};
+// Row products of the constraint solves: lane l of a warp owns the column pairs
+// (2l, 2l + 1) + 64 m of the vertex vector in registers; a warp multiplies four rows of W~ at
+// a time with 8-byte loads and packed FP32 FMAs and reduces the twelve row sums over the warp
+// with a butterfly of 16 shuffles.
+constexpr int kCrPairs = 16;     // register-held column pairs per lane: rows up to 1024 wide
 
-// Two cluster exchanges per CR iteration (every scene; the only one with contacts between
-// bodies).
-__device__ __noinline__ void cr_two_exchanges(const DevSim& d, int smem_bytes, CrShared& sh) {
+__device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
+  return (unsigned long long)__float_as_uint(lo) |
+         ((unsigned long long)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ float f2lo(unsigned long long v) { return __uint_as_float((unsigned)v); }
+__device__ __forceinline__ float f2hi(unsigned long long v) {
+  return __uint_as_float((unsigned)(v >> 32));
+}
+// d = a * b + c, lane-wise on two FP32 values
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// Sum each of v[0..11] over the warp; afterwards lanes 2i and 2i + 1 hold the total of v[i]
+// in v[0]. Butterfly halving: at each step a lane keeps half of its values and adds the
+// partner's copy of that half.
+__device__ __forceinline__ float warp_sum12(float (&v)[16], int lane) {
+#pragma unroll
+  for (int i = 12; i < 16; ++i) v[i] = 0.f;
+#pragma unroll
+  for (int o = 16, n = 16; o >= 2; o >>= 1, n >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < n / 2; ++i) {
+      const float keep = up ? v[i + n / 2] : v[i];
+      const float send = up ? v[i] : v[i + n / 2];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+__global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) {
+  pdl_wait();
   extern __shared__ __align__(16) float sm[];
   cg::cluster_group cl = cg::this_cluster();
   CrLayout L;
@@ -1362,8 +1428,7 @@ __device__ __noinline__ void cr_two_exchanges(const DevSim& d, int smem_bytes, C
   // every CTA reads the same counters, so this exit is taken by all or by none
   if (L.c == 0 || L.ncv == 0) return;
   // split of the contact vertices over the cluster ranks, computed once per CTA
-  int* split_cv = sh.split_cv;
-  int* split_j = sh.split_j;
+  __shared__ int split_cv[kCrMaxRanks + 1], split_j[kCrMaxRanks + 1];
   if (threadIdx.x <= L.R) {
     const int* sp = d.cr_split + scene * 2 * (kCrMaxRanks + 1);
     split_cv[threadIdx.x] = sp[threadIdx.x];
@@ -1414,7 +1479,7 @@ __device__ __noinline__ void cr_two_exchanges(const DevSim& d, int smem_bytes, C
   // global memory
   float* wrows = sm + ((((twl + (gen ? 3 * nj_max : 0)) - sm) + 3) & ~size_t(3));
   const size_t used = (size_t)(wrows - sm) * sizeof(float);
-  unsigned long long& wbar = *sh.wbar;
+  __shared__ __align__(8) unsigned long long wbar;
   if (used > (size_t)smem_bytes) {   // uniform: depends only on cluster-wide maxima
     if (threadIdx.x == 0 && L.rank == 0) atomicOr(d.err, kErrCapacity);
     cl.sync();
@@ -1439,6 +1504,16 @@ __device__ __noinline__ void cr_two_exchanges(const DevSim& d, int smem_bytes, C
               "r"(dst + (unsigned)off), "l"(src + off), "r"(sz), "r"(bar) : "memory");
     }
   }
+  // point-to-point exchanges (sim_options.cr_sync = 0) for scenes without contacts between
+  // bodies; the byte count of one phase must stay below the mbarrier's 2^20 limit
+  const bool async_x = d.cr_sync == 0 && !gen && L.ncv < 65536;
+  __shared__ __align__(8) unsigned long long xbar[2];   // [0]: u slices, [1]: dot products
+  if (threadIdx.x == 0 && async_x) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&xbar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&xbar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  unsigned ph_u = 0, ph_d = 0;
   for (int e = threadIdx.x; e < 3 * nj; e += blockDim.x) {
     const int j = L.j0 + e / 3;
     vx[e] = 0.f;
@@ -1526,106 +1601,86 @@ __device__ __noinline__ void cr_two_exchanges(const DevSim& d, int smem_bytes, C
   };
   auto apply = [&](const float* v, float* Kv) {
     if (gen) publish_t(v);
+    // this phase brings every contact vertex's u (16 bytes each) from its owner
+    if (async_x && threadIdx.x == 0) mbar_expect(smem_u32(&xbar[0]), (unsigned)L.ncv * 16u);
     for (int cvl = threadIdx.x; cvl < nv; cvl += blockDim.x) uloc[cvl] = vertex_u(v, cvl);
     __syncthreads();
     // one 16-byte remote store per (rank, owned vertex), spread over all threads
-    for (int e = threadIdx.x; e < L.R * nv; e += blockDim.x) {
-      const int r = e / nv, cvl = e - r * nv;
-      cl.map_shared_rank(uall, r)[L.cv0 + cvl] = uloc[cvl];
+    if (async_x) {
+      const unsigned ub = smem_u32(uall + L.cv0), bb = smem_u32(&xbar[0]);
+      for (int e = threadIdx.x; e < L.R * nv; e += blockDim.x) {
+        const int r = e / nv, cvl = e - r * nv;
+        st_async_v4(mapa_u32(ub + 16u * (unsigned)cvl, r), uloc[cvl], mapa_u32(bb, r));
+      }
+      if (!mbar_wait_cluster(smem_u32(&xbar[0]), ph_u & 1u, d.spin_limit) && threadIdx.x == 0)
+        atomicOr(d.err, kErrTimeout);
+      ++ph_u;
+    } else {
+      for (int e = threadIdx.x; e < L.R * nv; e += blockDim.x) {
+        const int r = e / nv, cvl = e - r * nv;
+        cl.map_shared_rank(uall, r)[L.cv0 + cvl] = uloc[cvl];
+      }
+      cl.sync();   // every rank's slice of u is now in every CTA
     }
-    cl.sync();   // every rank's slice of u is now in every CTA
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int ng = ldw / 4;
     auto wrow_ptr = [&](int row) {
       return reinterpret_cast<const float4*>(
           row < rows_sm ? wrows + (size_t)row * ldw : wblk + (size_t)(L.cv0 + row) * ldw);
     };
-    if (ldw <= 32 * 4 * kCrG) {
-      // lane l owns the columns l + 32 m (m < 4 kCrG): its u values live in registers
-      // (loaded conflict-free: consecutive lanes read consecutive 16-byte entries), and
-      // each warp streams whole rows of W~, two at a time, with consecutive lanes on
-      // consecutive words (no bank conflicts)
-      constexpr int M = 4 * kCrG;
-      float ux[M], uy[M], uz[M];
+    if (ldw <= 64 * kCrPairs) {
+      // lane l owns the column pairs (2l, 2l + 1) + 64 m of u in registers; a warp
+      // multiplies four rows of W~ at a time with 8-byte loads and packed FP32 FMAs
+      // (fma.rn.f32x2: two independent round-to-nearest FMAs), and reduces the twelve row
+      // sums over the warp with a butterfly of 16 shuffles
+      unsigned long long ux[kCrPairs], uy[kCrPairs], uz[kCrPairs];
 #pragma unroll
-      for (int m = 0; m < M; ++m) {
-        const int col = lane + 32 * m;
-        const float4 t = col < ldw ? uall[col] : make_float4(0.f, 0.f, 0.f, 0.f);
-        ux[m] = t.x;
-        uy[m] = t.y;
-        uz[m] = t.z;
+      for (int m = 0; m < kCrPairs; ++m) {
+        const int col = 2 * lane + 64 * m;
+        const float4 a = col < ldw ? uall[col] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 b = col < ldw ? uall[col + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        ux[m] = f2pack(a.x, b.x);
+        uy[m] = f2pack(a.y, b.y);
+        uz[m] = f2pack(a.z, b.z);
       }
-      // rows held in shared memory are read through a shared-memory pointer (so the loads
-      // are shared-memory loads, not generic ones); the rest through a global one
-      auto rows = [&](int r_begin, int r_end, auto row_ptr) {
-      for (int row = r_begin + 2 * warp; row < r_end; row += 2 * nw) {
-        const bool two = row + 1 < r_end;
-        const float* w0 = row_ptr(row);
-        const float* w1 = row_ptr(two ? row + 1 : row);
-        float a[2][3] = {};
+      auto rows4 = [&](int r_begin, int r_end, auto row_ptr) {
+        for (int row = r_begin + 4 * warp; row < r_end; row += 4 * nw) {
+          const int nr = min(4, r_end - row);
+          const float* w[4];
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-          const int col = lane + 32 * m;
-          if (col < ldw) {
-            const float p = w0[col], q = w1[col];
-            a[0][0] += p * ux[m];
-            a[0][1] += p * uy[m];
-            a[0][2] += p * uz[m];
-            a[1][0] += q * ux[m];
-            a[1][1] += q * uy[m];
-            a[1][2] += q * uz[m];
-          }
-        }
+          for (int k = 0; k < 4; ++k) w[k] = row_ptr(min(row + k, r_end - 1));
+          unsigned long long acc[4][3];
 #pragma unroll
-        for (int k = 0; k < 2; ++k)
+          for (int k = 0; k < 4; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0ull;
 #pragma unroll
-          for (int c = 0; c < 3; ++c) a[k][c] = warp_sum(a[k][c]);
-        if (lane < 3) wloc[3 * row + lane] = lane == 0 ? a[0][0] : (lane == 1 ? a[0][1] : a[0][2]);
-        if (two && lane >= 3 && lane < 6)
-          wloc[3 * row + lane] = lane == 3 ? a[1][0] : (lane == 4 ? a[1][1] : a[1][2]);
-      }
-      };
-      // rows read from global memory (L2): four per warp at a time, twice the loads in
-      // flight of the two-row loop (the rows that did not fit in shared memory)
-      auto rows4 = [&](int r_begin, int r_end) {
-      for (int row = r_begin + 4 * warp; row < r_end; row += 4 * nw) {
-        const int nr = min(4, r_end - row);
-        const float* w[4];
+          for (int m = 0; m < kCrPairs; ++m) {
+            const int col = 2 * lane + 64 * m;
+            if (col < ldw) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          w[k] = wblk + (size_t)(L.cv0 + min(row + k, r_end - 1)) * ldw;
-        float a[4][3] = {};
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-          const int col = lane + 32 * m;
-          if (col < ldw) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const float p = w[k][col];
-              a[k][0] += p * ux[m];
-              a[k][1] += p * uy[m];
-              a[k][2] += p * uz[m];
+              for (int k = 0; k < 4; ++k) {
+                const float2 p = *reinterpret_cast<const float2*>(w[k] + col);
+                const unsigned long long pp = f2pack(p.x, p.y);
+                acc[k][0] = ffma2(pp, ux[m], acc[k][0]);
+                acc[k][1] = ffma2(pp, uy[m], acc[k][1]);
+                acc[k][2] = ffma2(pp, uz[m], acc[k][2]);
+              }
             }
           }
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) a[k][c] = warp_sum(a[k][c]);
-        if (lane < 3 * nr) {
-          float val = 0.f;
+          float v[16];
 #pragma unroll
           for (int k = 0; k < 4; ++k)
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-              if (lane == 3 * k + c) val = a[k][c];
-          wloc[3 * row + lane] = val;
+            for (int q = 0; q < 3; ++q) v[3 * k + q] = f2lo(acc[k][q]) + f2hi(acc[k][q]);
+          const float tot = warp_sum12(v, lane);
+          const int idx = lane >> 1;
+          if (!(lane & 1) && idx < 3 * nr) wloc[3 * row + idx] = tot;
         }
-      }
       };
+      // rows held in shared memory are read through a shared-memory pointer (shared-memory
+      // loads, not generic ones); the rest through a global one
       const int n_sm_rows = min(rows_sm, nv);
-      rows(0, n_sm_rows, [&](int r) { return wrows + (size_t)r * ldw; });
-      rows4(n_sm_rows, nv);
+      rows4(0, n_sm_rows, [&](int r) { return static_cast<const float*>(wrows + (size_t)r * ldw); });
+      rows4(n_sm_rows, nv, [&](int r) { return wblk + (size_t)(L.cv0 + r) * ldw; });
     } else {
     // four rows per warp at a time, so the shuffle reductions of the rows overlap
     for (int row0 = 4 * warp; row0 < nv; row0 += 4 * nw) {
@@ -1702,8 +1757,8 @@ __device__ __noinline__ void cr_two_exchanges(const DevSim& d, int smem_bytes, C
   // cluster-wide sums of three values. Per warp, then per CTA in warp 0, then over the
   // ranks in warp 0 of every CTA: the same shuffle tree on the same values everywhere, so
   // every CTA holds identical scalars (deterministic).
-  float (*wpart)[32] = sh.wpart;
-  float* red3 = sh.red3;
+  __shared__ float wpart[3][32];
+  __shared__ float red3[3];
   auto exchange = [&](float& a, float& b, float& c) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     a = warp_sum(a);
@@ -1719,9 +1774,23 @@ __device__ __noinline__ void cr_two_exchanges(const DevSim& d, int smem_bytes, C
       a = warp_sum(lane < nw ? wpart[0][lane] : 0.f);
       b = warp_sum(lane < nw ? wpart[1][lane] : 0.f);
       c = warp_sum(lane < nw ? wpart[2][lane] : 0.f);
-      if (lane < L.R) cl.map_shared_rank(dots, lane)[L.rank] = make_float4(a, b, c, 0.f);
+      if (async_x) {
+        // this phase brings one float4 from every rank
+        if (lane == 0) mbar_expect(smem_u32(&xbar[1]), (unsigned)L.R * 16u);
+        if (lane < L.R)
+          st_async_v4(mapa_u32(smem_u32(dots + L.rank), lane), make_float4(a, b, c, 0.f),
+                      mapa_u32(smem_u32(&xbar[1]), lane));
+      } else if (lane < L.R) {
+        cl.map_shared_rank(dots, lane)[L.rank] = make_float4(a, b, c, 0.f);
+      }
     }
-    cl.sync();
+    if (async_x) {
+      if (!mbar_wait_cluster(smem_u32(&xbar[1]), ph_d & 1u, d.spin_limit) && threadIdx.x == 0)
+        atomicOr(d.err, kErrTimeout);
+      ++ph_d;
+    } else {
+      cl.sync();
+    }
     if (wid == 0) {
       const float4 t = lane < L.R ? dots[lane] : make_float4(0, 0, 0, 0);
       a = warp_sum(t.x);
@@ -1803,71 +1872,29 @@ __device__ __noinline__ void cr_two_exchanges(const DevSim& d, int smem_bytes, C
 // gives y_Ap = B Ar + beta y_Ap); W~ y_r is a full product every iteration. The only data
 // an iteration needs from the other CTAs are then their partial dot products and the B Ar of
 // their contact vertices, which travel together. The final x = dlambda and its B x are
-// computed directly (not from the recurrences).
-//
-// Row products: lane l of a warp owns the column pairs (2l, 2l + 1) + 64 m of y_r in
-// registers; a warp multiplies four rows of W~ at a time with 8-byte shared-memory loads and
-// packed FP32 FMAs (fma.rn.f32x2: two independent round-to-nearest FMAs) and reduces the
-// twelve row sums over the warp with a butterfly of 16 shuffles.
-constexpr int kCr1Pairs = 16;    // register-held column pairs per lane: rows up to 2048 wide
-
-__device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
-  return (unsigned long long)__float_as_uint(lo) |
-         ((unsigned long long)__float_as_uint(hi) << 32);
-}
-__device__ __forceinline__ float f2lo(unsigned long long v) { return __uint_as_float((unsigned)v); }
-__device__ __forceinline__ float f2hi(unsigned long long v) {
-  return __uint_as_float((unsigned)(v >> 32));
-}
-// d = a * b + c, lane-wise on two FP32 values
-__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
-                                                    unsigned long long c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-
-// Sum each of v[0..11] over the warp; afterwards lanes 2i and 2i + 1 hold the total of v[i]
-// in v[0]. Butterfly halving: at each step a lane keeps half of its values and adds the
-// partner's copy of that half.
-__device__ __forceinline__ float warp_sum12(float (&v)[16], int lane) {
-#pragma unroll
-  for (int i = 12; i < 16; ++i) v[i] = 0.f;
-#pragma unroll
-  for (int o = 16, n = 16; o >= 2; o >>= 1, n >>= 1) {
-    const bool up = (lane & o) != 0;
-#pragma unroll
-    for (int i = 0; i < n / 2; ++i) {
-      const float keep = up ? v[i + n / 2] : v[i];
-      const float send = up ? v[i] : v[i + n / 2];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-    }
-  }
-  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
-}
-
-// Shared-memory bytes (dynamic) the single-exchange body needs before the W~ rows, for a
-// scene's cluster: nj_max / nv_max the largest owned contact / contact-vertex counts.
-__device__ __forceinline__ size_t cr1_layout_bytes(int ldw, int nj_max, int nv_max) {
-  // dots (32 float4), yr / yap / yar[2] (4 ldw float4), wloc (3 nv), x r p Ar Ap (5 x 3 nj),
-  // D (9 nj), omega and E (2 x 3 nj); then cvf, cvn (nv ints) and ctl (nj ints)
-  const size_t floats = 4 * 32 + 16 * (size_t)ldw + 3 * (size_t)nv_max + 30 * (size_t)nj_max;
-  const size_t ints = 2 * (size_t)nv_max + (size_t)nj_max;
-  return ((floats + ints + 3) & ~size_t(3)) * sizeof(float);
-}
-
-// One cluster exchange per CR iteration (scenes without contacts between bodies; see k_cr for
-// when). The split arrays are loaded.
-__device__ __noinline__ void cr_one_exchange(const DevSim& d, int smem_bytes, CrShared& sh) {
+// computed directly (not from the recurrences). In FP32 the recurrences carry rounding
+// from one iteration to the next: on ill-conditioned systems the result can be an order of
+// magnitude further from the FP64 iteration than k_cr's, so this form is an option.
+// The constraint solve with one cluster exchange per CR iteration (sim_options.cr_exchanges
+// = 1; scenes without contacts between bodies). Owned W~ rows that do not fit in shared
+// memory are read from L2; a layout that does not fit at all reports SIM_ECAPACITY.
+__global__ void __launch_bounds__(kCrThreads, 1) k_cr1(DevSim d, int smem_bytes) {
+  pdl_wait();
   extern __shared__ __align__(16) float sm[];
   cg::cluster_group cl = cg::this_cluster();
   const int R = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int scene = blockIdx.x / R;
   const int cvb = d.sc_cvb[scene], jb = d.sc_jb[scene];
   const int c = d.sc_jb[scene + 1] - jb, ncv = d.sc_cvb[scene + 1] - cvb;
+  // every CTA reads the same counters, so this exit is taken by all or by none
   if (c == 0 || ncv == 0) return;
-  const int* split_cv = sh.split_cv;
-  const int* split_j = sh.split_j;
+  __shared__ int split_cv[kCrMaxRanks + 1], split_j[kCrMaxRanks + 1];
+  if (threadIdx.x <= R) {
+    const int* sp = d.cr_split + scene * 2 * (kCrMaxRanks + 1);
+    split_cv[threadIdx.x] = sp[threadIdx.x];
+    split_j[threadIdx.x] = sp[kCrMaxRanks + 1 + threadIdx.x];
+  }
+  __syncthreads();
   const int cv0 = split_cv[rank], cv1 = split_cv[rank + 1];
   const int j0 = split_j[rank], j1 = max(split_j[rank + 1], j0);
   const int nj = j1 - j0, nv = cv1 - cv0;
@@ -1900,7 +1927,12 @@ __device__ __noinline__ void cr_one_exchange(const DevSim& d, int smem_bytes, Cr
   int* ctl = cvn + nv_max;                              // owned contact: local cv index
   float* wrows = sm + ((((reinterpret_cast<float*>(ctl + nj_max)) - sm) + 3) & ~size_t(3));
   const size_t used = (size_t)(wrows - sm) * sizeof(float);
-  unsigned long long& wbar = *sh.wbar;
+  __shared__ __align__(8) unsigned long long wbar;
+  if (used > (size_t)smem_bytes) {   // uniform: depends only on cluster-wide maxima
+    if (threadIdx.x == 0 && rank == 0) atomicOr(d.err, kErrCapacity);
+    cl.sync();
+    return;
+  }
   int rows_sm = (int)min((size_t)nv, ((size_t)smem_bytes - used) / ((size_t)ldw * sizeof(float)));
   if (threadIdx.x == 0 && rows_sm > 0) {
     // owned rows are contiguous in W~ (row-major, ld a multiple of 4 floats): 16-byte
@@ -1977,10 +2009,10 @@ __device__ __noinline__ void cr_one_exchange(const DevSim& d, int smem_bytes, Cr
   };
   // wloc = W~ y_r over the owned rows
   auto product = [&]() {
-    if (ldw <= 64 * kCr1Pairs) {
-      unsigned long long ux[kCr1Pairs], uy[kCr1Pairs], uz[kCr1Pairs];
+    if (ldw <= 64 * kCrPairs) {
+      unsigned long long ux[kCrPairs], uy[kCrPairs], uz[kCrPairs];
 #pragma unroll
-      for (int m = 0; m < kCr1Pairs; ++m) {
+      for (int m = 0; m < kCrPairs; ++m) {
         const int col = 2 * lane + 64 * m;
         const float4 a = col < ldw ? yr[col] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 b = col < ldw ? yr[col + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1998,7 +2030,7 @@ __device__ __noinline__ void cr_one_exchange(const DevSim& d, int smem_bytes, Cr
 #pragma unroll
           for (int k = 0; k < 4; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0ull;
 #pragma unroll
-          for (int m = 0; m < kCr1Pairs; ++m) {
+          for (int m = 0; m < kCrPairs; ++m) {
             const int col = 2 * lane + 64 * m;
             if (col < ldw) {
 #pragma unroll
@@ -2076,7 +2108,7 @@ __device__ __noinline__ void cr_one_exchange(const DevSim& d, int smem_bytes, Cr
   };
   // reduce three values over the CTA (per warp, then warp 0 in warp order) and send them to
   // slot `rank` of dots buffer `buf` in every CTA; ends with the CTA's shared writes visible
-  float (*wpart)[32] = sh.wpart;
+  __shared__ float wpart[3][32];
   auto send_dots = [&](float a, float b, float cc, int buf) {
     a = warp_sum(a);
     b = warp_sum(b);
@@ -2174,49 +2206,6 @@ __device__ __noinline__ void cr_one_exchange(const DevSim& d, int smem_bytes, Cr
   // shared memory is released
   if (w_late) mbar_wait(smem_u32(&wbar), 0, d.spin_limit);
   cl.sync();  // no CTA leaves while another may still write into its shared memory
-}
-
-// The constraint solve of one local-global iteration: one thread-block cluster per scene.
-// The single-exchange body runs where its layout fits in shared memory with all but at most
-// 32 owned W~ rows and the scene has no contacts between bodies; the two-exchange body
-// everywhere else. The
-// choice depends only on the scene's sizes, so every CTA of a cluster makes the same one.
-__global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) {
-  pdl_wait();
-  __shared__ int split_cv[kCrMaxRanks + 1], split_j[kCrMaxRanks + 1];
-  __shared__ __align__(8) unsigned long long wbar;
-  __shared__ float wpart[3][32];
-  __shared__ float red3[3];
-  CrShared sh{split_cv, split_j, &wbar, wpart, red3};
-  cg::cluster_group cl = cg::this_cluster();
-  const int R = (int)cl.num_blocks();
-  const int scene = blockIdx.x / R;
-  bool one = !d.bc_on && d.cr_single;
-  if (one) {
-    if (threadIdx.x <= R) {
-      const int* sp = d.cr_split + scene * 2 * (kCrMaxRanks + 1);
-      split_cv[threadIdx.x] = sp[threadIdx.x];
-      split_j[threadIdx.x] = sp[kCrMaxRanks + 1 + threadIdx.x];
-    }
-    __syncthreads();
-    int nj_max = 0, nv_max = 0;
-    for (int r = 0; r < R; ++r) {
-      nj_max = max(nj_max, max(0, split_j[r + 1] - split_j[r]));
-      nv_max = max(nv_max, split_cv[r + 1] - split_cv[r]);
-    }
-    // the single-exchange layout must fit, and at most one pass of 32 owned rows (four per
-    // warp) may have to come from L2 instead of shared memory
-    const int ldw = d.sc_ld[scene];
-    const size_t lay = cr1_layout_bytes(ldw, nj_max, nv_max);
-    const size_t rows_fit = lay <= (size_t)smem_bytes
-                                ? ((size_t)smem_bytes - lay) / ((size_t)ldw * sizeof(float)) : 0;
-    one = lay <= (size_t)smem_bytes && (size_t)nv_max <= rows_fit + 4 * (kCrThreads / 32);
-    __syncthreads();   // split arrays are reloaded by the body that runs
-  }
-  if (one)
-    cr_one_exchange(d, smem_bytes, sh);
-  else
-    cr_two_exchanges(d, smem_bytes, sh);
 }
 
 }  // namespace
@@ -2349,9 +2338,11 @@ int cr_setup(int n_scenes, int* cluster_out, size_t* smem_out) {
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   size_t smem = (size_t)optin - 1024;  // leave room for static shared memory
-  if (cudaFuncSetAttribute(k_cr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (cudaFuncSetAttribute(k_cr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_cr1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return SIM_ECUDA;
   cudaFuncSetAttribute(k_cr, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(k_cr1, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   int chosen = 0;
   for (int R : {16, 8, 4, 2, 1}) {
     cudaLaunchConfig_t cfg = {};
@@ -2395,7 +2386,11 @@ int launch_cr(const DevSim& d, cudaStream_t s, int cluster) {
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = d.pdl ? 2 : 1;
-  return cudaLaunchKernelEx(&cfg, k_cr, d, (int)g_cr_smem) == cudaSuccess ? SIM_OK : SIM_ECUDA;
+  // one exchange per CR iteration when asked for and the scene has no contacts between
+  // bodies; the two-exchange form otherwise
+  const bool one = d.cr_single && !d.bc_on;
+  return cudaLaunchKernelEx(&cfg, one ? k_cr1 : k_cr, d, (int)g_cr_smem) == cudaSuccess ? SIM_OK
+                                                                                       : SIM_ECUDA;
 }
 
 }  // namespace silg

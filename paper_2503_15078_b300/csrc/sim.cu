@@ -1134,6 +1134,7 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   d.cr_R = s->cluster;
   d.ws_gain[0] = d.ws_gain[1] = d.ws_gain[2] = 1.f;
   d.cr_single = o->cr_exchanges == 1 ? 1 : 0;
+  d.cr_sync = o->cr_sync;
   if (o->autotune) {
     int st = autotune_products(s);
     if (st != SIM_OK) return st;
@@ -1249,6 +1250,7 @@ int check_options(const sim_options* o) {
   if (o->precond != SIM_PRECOND_DELASSUS && o->precond != SIM_PRECOND_MASS) return SIM_EINVAL;
   if (o->cr_exchanges != 1 && o->cr_exchanges != 2) return SIM_EINVAL;
   if (o->delassus_reuse != 0 && o->delassus_reuse != 1) return SIM_EINVAL;
+  if (o->cr_sync != 0 && o->cr_sync != 1) return SIM_EINVAL;
   if (o->s_build != 0 && o->s_build != 1) return SIM_EINVAL;
   return SIM_OK;
 }

