@@ -461,6 +461,14 @@ typedef struct sim_mlp_s sim_mlp_t;
 /* A network on `device` with zero parameters; max_batch bounds the rows of one gradient. */
 int sim_mlp_create(int32_t device, int32_t max_batch, sim_mlp_t** out);
 void sim_mlp_destroy(sim_mlp_t* net);
+/* Which tensor-core instructions run the network's inference (sim_mlp_forward, and a
+ * simulator's learned start, which takes the choice with the network in sim_set_warmstart):
+ * SIM_MLP_MMA_SYNC (default) warp-level mma.sync, each warp carrying 16 rows; SIM_MLP_TCGEN05
+ * the 5th-generation tensor cores, one CTA of 128 rows per tcgen05.mma chain with its FP32
+ * accumulators in tensor memory. Both take BF16 weights and activations with FP32
+ * accumulation. Training always uses mma.sync. Other values: SIM_EINVAL. */
+enum { SIM_MLP_MMA_SYNC = 0, SIM_MLP_TCGEN05 = 1 };
+int sim_mlp_set_tensor_cores(sim_mlp_t* net, int32_t kind);
 /* Weights uniform in +-sqrt(6 / (fan_in + fan_out)) from a splitmix64 stream, biases 0. */
 int sim_mlp_init(sim_mlp_t* net, uint64_t seed);
 int sim_mlp_set_params(sim_mlp_t* net, const float* theta);   /* also resets Adam's moments */

@@ -221,6 +221,12 @@ class WarmStartNet:
     def handle(self):
         return self._h
 
+    def set_tensor_cores(self, kind):
+        """"mma_sync" (warp-level, the default) or "tcgen05" (5th-generation tensor cores with
+        tensor-memory accumulators) for the inference."""
+        k = {"mma_sync": 0, "tcgen05": 1}[kind]
+        _check(lib().sim_mlp_set_tensor_cores(self._h, k), "sim_mlp_set_tensor_cores")
+
     def set_params(self, theta):
         t = np.ascontiguousarray(theta, dtype=np.float32)
         assert t.size == self.PARAMS

@@ -110,6 +110,7 @@ PROTOTYPES = {
                                             C.POINTER(C.c_int32)]),
     "sim_mlp_destroy": (None, [C.c_void_p]),
     "sim_mlp_init": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "sim_mlp_set_tensor_cores": (C.c_int, [C.c_void_p, C.c_int32]),
     "sim_mlp_set_params": (C.c_int, [C.c_void_p, _fp]),
     "sim_mlp_get_params": (C.c_int, [C.c_void_p, _fp]),
     "sim_mlp_forward": (C.c_int, [C.c_void_p, _fp, C.c_int32, _fp]),

@@ -432,7 +432,8 @@ void mlp_launch_convert(const MlpDev& m, cudaStream_t s) {
 }
 
 int mlp_setup() {
-  if (cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (mlp_tc_setup() != 0 ||
+      cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kInferSmem) != cudaSuccess ||
       cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kTrainSmem) != cudaSuccess)
@@ -442,12 +443,20 @@ int mlp_setup() {
 
 void mlp_launch_infer(const MlpDev& m, const float* X, int n, float* Y, cudaStream_t s) {
   if (n <= 0) return;
+  if (m.tc) {
+    mlp_launch_infer_tc(m, X, n, nullptr, Y, s);
+    return;
+  }
   k_mlp_infer<<<(n + kMlpRows - 1) / kMlpRows, 128, kInferSmem, s>>>(m, X, n, nullptr, Y);
 }
 
 void mlp_launch_infer_dev(const MlpDev& m, const float* X, const int* n_dev, int n_max, float* Y,
                           cudaStream_t s) {
   if (n_max <= 0) return;
+  if (m.tc) {
+    mlp_launch_infer_tc(m, X, n_max, n_dev, Y, s);
+    return;
+  }
   k_mlp_infer<<<(n_max + kMlpRows - 1) / kMlpRows, 128, kInferSmem, s>>>(m, X, n_max, n_dev, Y);
 }
 

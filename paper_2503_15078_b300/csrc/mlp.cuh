@@ -38,6 +38,9 @@ constexpr int kWRowElems = kMlpIn * kLdH + 2 * kMlpH * kLdH + kMlpH * kLdOut;
 constexpr int kWTElems = kMlpH * kLdIn + 2 * kMlpH * kLdH + kMlpOut * kLdH;
 constexpr int kMlpRows = 64;        // rows (samples) per CTA
 
+// error bit set by a tensor-core inference whose wait gave up (the simulator's timeout bit)
+constexpr int kMlpErrTimeout = 4;
+
 struct MlpDev {
   float* theta;            // master parameters (kMlpParams)
   float* adam_m;
@@ -49,6 +52,9 @@ struct MlpDev {
   float* part_loss;        // max_ctas
   float* loss;             // 1
   int max_ctas;
+  int tc;                  // inference on the 5th-generation tensor cores (tcgen05, TMEM): 1;
+                           // warp-level mma.sync: 0
+  int* err;                // error word of the inference (kMlpErrTimeout), or null
 };
 
 // shared-memory limits of the kernels (per device, before the first launch); 0 on success
@@ -60,6 +66,11 @@ void mlp_launch_infer(const MlpDev& m, const float* X, int n, float* Y, cudaStre
 // the same for min(*n_dev, n_max) rows, the count read on the device (graph capture)
 void mlp_launch_infer_dev(const MlpDev& m, const float* X, const int* n_dev, int n_max, float* Y,
                           cudaStream_t s);
+// the tcgen05 inference (k_mlp_tc.cu): its shared-memory limit, and its launch (n_dev
+// optional); both inference launchers above dispatch to it when m.tc is set
+int mlp_tc_setup();
+void mlp_launch_infer_tc(const MlpDev& m, const float* X, int n, const int* n_dev, float* Y,
+                         cudaStream_t s);
 // gradient of the mean squared error over the batch rows idx[0..n) (all rows if idx is
 // null) into m.grad, loss into m.loss; n <= m.max_ctas * kMlpRows
 void mlp_launch_gradient(const MlpDev& m, const float* X, const float* T, const int* idx, int n,

@@ -122,6 +122,8 @@ int sim_mlp_create(int32_t device, int32_t max_batch, sim_mlp_t** out) {
     m.part = n->alloc<float>((size_t)m.max_ctas * silg::kMlpParams);
     m.part_loss = n->alloc<float>(m.max_ctas);
     m.loss = n->alloc<float>(1);
+    m.err = n->alloc<int>(1);
+    m.tc = 0;
   } catch (const std::bad_alloc&) {
     delete n;
     return SIM_ENOMEM;
@@ -132,6 +134,12 @@ int sim_mlp_create(int32_t device, int32_t max_batch, sim_mlp_t** out) {
     return st;
   }
   *out = n;
+  return SIM_OK;
+}
+
+int sim_mlp_set_tensor_cores(sim_mlp_t* n, int32_t kind) {
+  if (!n || (kind != SIM_MLP_MMA_SYNC && kind != SIM_MLP_TCGEN05)) return SIM_EINVAL;
+  n->m.tc = kind == SIM_MLP_TCGEN05 ? 1 : 0;
   return SIM_OK;
 }
 
@@ -194,10 +202,14 @@ int sim_mlp_forward(sim_mlp_t* n, const float* X, int32_t rows, float* Y) {
   }
   silg::mlp_launch_infer(n->m, dx, rows, dy, n->stream);
   std::vector<float> y((size_t)rows * silg::kMlpOut);
+  int err = 0;
   cudaMemcpyAsync(y.data(), dy, y.size() * sizeof(float), cudaMemcpyDeviceToHost, n->stream);
+  cudaMemcpyAsync(&err, n->m.err, sizeof(int), cudaMemcpyDeviceToHost, n->stream);
+  cudaMemsetAsync(n->m.err, 0, sizeof(int), n->stream);
   int st = finish(n);
   release(n, tmp);
   if (st != SIM_OK) return st;
+  if (err) return SIM_ETIMEOUT;
   for (int r = 0; r < rows; ++r)
     for (int c = 0; c < silg::kMlpNY; ++c) Y[(size_t)r * silg::kMlpNY + c] = y[(size_t)r * silg::kMlpOut + c];
   return SIM_OK;

@@ -1114,6 +1114,7 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   d.ws_net = silg::MlpDev{};
   d.ws_net.theta = s->alloc<float>(silg::kMlpParams);
   d.ws_net.w_t = s->alloc<__nv_bfloat16>(silg::kWTElems);
+  d.ws_net.err = d.err;   // a tensor-core wait that gives up is the frame's SIM_ETIMEOUT
   d.ws_feat = s->alloc<float>((size_t)cap * silg::kMlpIn);
   d.ws_out = s->alloc<float>((size_t)cap * silg::kMlpOut);
   d.ws_scale = s->alloc<double>(cap);
@@ -1573,6 +1574,15 @@ int sim_set_warmstart(sim_t* s, const sim_mlp_t* net, int32_t mode) {
                           cudaMemcpyDeviceToDevice, s->launch);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->launch);
     if (e != cudaSuccess) return cuda_status(e);
+    if (s->d.ws_net.tc != m->tc) {
+      // the network's choice of tensor-core instructions is part of the captured frames
+      s->d.ws_net.tc = m->tc;
+      for (auto& kv : s->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.g) cudaGraphDestroy(kv.second.g);
+      }
+      s->graphs.clear();
+    }
   }
   s->d.ws_mode = mode;   // graphs are cached per mode; the network's weights are read at launch
   delassus_forget(s, s->launch);
