@@ -492,8 +492,9 @@ int sim_set_warmstart(sim_t* sim, const sim_mlp_t* net, int32_t mode);
 /* Gains of the network's outputs in the learned start (not from the paper): lambda^0 =
  * (previous impulse + g x predicted change) x scale with g = persist for a contact that had
  * an impulse at the same vertex and obstacle in the previous frame and g = fresh for a new
- * one; the normal move is scaled by move. 0 leaves that part at the previous frame's value
- * (persist, fresh) or at no move; 1, 1, 1 (the default) is the network as trained. Chosen,
+ * one; the predicted change of the normal move from the previous frame's is scaled by move.
+ * 0 leaves that part at the previous frame's value, so 0, 0, 0 is the previous-frame start
+ * (mode 2) with the network's cost; 1, 1, 1 (the default) is the network as trained. Chosen,
  * for example, on validation frames by iterations to a residual tolerance. Non-negative
  * finite values, else SIM_EINVAL. Synchronises the handle's stream. */
 int sim_set_warmstart_gains(sim_t* sim, float persist, float fresh, float move);
@@ -521,9 +522,11 @@ int sim_set_phase_marks(sim_t* sim, int32_t on);
  * velocity h / margin (3), the previous frame's impulse at the same vertex and obstacle in
  * this frame's basis / scale (3, or 0), m_v W~_vv -- where scale = margin / (h^2 W~_vv); T
  * (n x 4) what the network should output: the frame's final impulse / scale minus features
- * 7..9, and the vertex's move along the normal over the frame / margin. The learned start
- * uses lambda^0 = (features 7..9 + output 0..2) scale and translates the scene by the mean
- * over its contact vertices of (output 3 x margin) x normal, kept within one margin of the
+ * 7..9, and the change of the vertex's move along the normal over the frame from the previous
+ * frame's move at the same vertex and obstacle (0 if none) / margin. The learned start uses
+ * lambda^0 = (features 7..9 + gain x output 0..2) scale and translates the scene by the mean
+ * over its contact vertices of (previous move + gain x output 3 x margin) x normal (see
+ * sim_set_warmstart_gains), kept within one margin of the
  * translation h^2 sum_j D_j^T lambda_j^0 / (the scene's free mass) that the impulses give
  * it. *n_out receives the count; arrays hold `capacity` rows. */
 int sim_get_warmstart_samples(sim_t* sim, int32_t capacity, float* X, float* T, int32_t* n_out);

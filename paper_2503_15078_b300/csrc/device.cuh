@@ -28,6 +28,23 @@ __device__ __forceinline__ void pdl_wait() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Two FP32 values in one 64-bit register pair, for the packed FMA (lo in bits 0-31).
+__device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
+  return (unsigned long long)__float_as_uint(lo) |
+         ((unsigned long long)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ float f2lo(unsigned long long v) { return __uint_as_float((unsigned)v); }
+__device__ __forceinline__ float f2hi(unsigned long long v) {
+  return __uint_as_float((unsigned)(v >> 32));
+}
+// d = a * b + c, lane-wise on two FP32 values (each rounded as one fmaf)
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 // kernel<<<grid, block, smem, s>>>(args...), with programmatic stream serialisation when
 // pdl is set
 template <class Kernel, class... Args>
@@ -61,7 +78,8 @@ constexpr int kErrTimeout = 4;
 constexpr int kErrYCapacity = 8;
 
 // counters[]: per-frame sizes decided on the device
-enum { kCntContacts = 0, kCntCv = 1, kCntU = 2, kCntY = 3, kCntYC = 4, kNumCounters = 8 };
+enum { kCntContacts = 0, kCntCv = 1, kCntU = 2, kCntY = 3, kCntYC = 4, kCntYtzItems = 5,
+       kCntYuItems = 6, kNumCounters = 8 };
 
 struct ObstDev {
   int kind;
@@ -142,6 +160,8 @@ struct DevSim {
   double* ws_scale;           // cap: impulse scale margin / (h^2 W~_vv)
   double* ws_lam0;            // cap x 3: the guess (contact frame)
   double* ws_move;            // cap: the guessed move of the contact's vertex along its normal
+  double* ws_pmove;           // cap: the previous frame's move along the normal at the same
+                              // vertex and obstacle, at the frame's start (0: none)
   double* ws_shift;           // 6 per scene: the impulse translation and the applied one
   double* ws_res;             // 2 per scene: residual of the guess, of the cold start
   float* ws_target;           // cap x 4: the frame's final impulse / scale, normal move / margin
@@ -227,16 +247,21 @@ struct DevSim {
   int dl_reuse_on;
   int* dl_state;
   int* dl_prev_cv;  // cap: the previous frame's contact vertices
-  // Y^T z and Y u in chunks of 256 path entries (k_ytz_chunk, k_yu_chunk; 0 chunks: the
-  // one-warp or one-CTA per vertex (row) kernels): chunks per contact vertex and per row of
-  // U, partial sums per (vertex or row, chunk), completion counters (zero between launches)
-  int ytz_nch, yu_nch;
-  float4* ytz_part;
-  int* ytz_done;
-  float4* yu_part;
-  int* yu_done;
-  int ytz_warp;     // Y^T z with a warp per contact vertex (short ancestor paths) instead
-                    // of a CTA per contact vertex
+  // Y^T z and Y u in chunks of 256 path entries (k_ytz_chunk, k_yu_chunk): chunks per
+  // contact vertex (ytz_cnt) and per row of U (yu_cnt), their exclusive prefix sums, the
+  // flattened (vertex or row, chunk) work items, one partial sum per item, and completion
+  // counters per vertex (row), zero between launches. Built with Y, kept when Y is reused.
+  int* ytz_cnt;     // cap
+  int* ytz_off;     // cap + 1
+  int2* ytz_item;   // ytz_items_cap
+  float4* ytz_part; // ytz_items_cap
+  int* ytz_done;    // cap
+  int* yu_cnt;      // n
+  int* yu_off;      // n + 1
+  int2* yu_item;    // yu_items_cap
+  float4* yu_part;  // yu_items_cap
+  int* yu_done;     // n
+  int ytz_items_cap, yu_items_cap;
   const float* zero;  // kTileW zeros: the load target of lanes outside a row's range
   float* p1_part;   // [n_seg1][3][kRowGroup]
   float* p2_part;   // [n_seg2][3][kTileW]

@@ -155,18 +155,20 @@ __global__ void __launch_bounds__(256, PassOcc<T, U>::kMinBlocks) k_pass1(DevSim
   }
   bool g_ready = false;
   int cur = __shfl_sync(0xffffffffu, mt.key, 0);
-  float acc[kRowsPerWarp][3];
+  // per row and component, two running sums (even and odd columns) in one register pair,
+  // advanced by packed FMAs
+  unsigned long long acc[kRowsPerWarp][3];
 #pragma unroll
-  for (int k = 0; k < kRowsPerWarp; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0.f;
+  for (int k = 0; k < kRowsPerWarp; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0ull;
   auto flush = [&]() {
     float* out = d.p1_part + (size_t)slot * 3 * RG;
 #pragma unroll
     for (int k = 0; k < kRowsPerWarp; ++k)
 #pragma unroll
       for (int comp = 0; comp < 3; ++comp) {
-        const float v = warp_sum(acc[k][comp]);
+        const float v = warp_sum(f2lo(acc[k][comp]) + f2hi(acc[k][comp]));
         if (lane == 0) out[comp * RG + warp * kRowsPerWarp + k] = v;
-        acc[k][comp] = 0.f;
+        acc[k][comp] = 0ull;
       }
     ++slot;
   };
@@ -208,14 +210,17 @@ __global__ void __launch_bounds__(256, PassOcc<T, U>::kMinBlocks) k_pass1(DevSim
       }
 #pragma unroll
       for (int m = 0; m < kChunks; ++m) {
-        const float4* gp = gsm + gs * 3 * (TW / 4) + lane + 32 * m;
-        const float4 g0 = gp[0], g1 = gp[TW / 4], g2 = gp[2 * (TW / 4)];
+        // g's four columns as the pairs (0, 1) and (2, 3)
+        const ulonglong2* gp =
+            reinterpret_cast<const ulonglong2*>(gsm + gs * 3 * (TW / 4) + lane + 32 * m);
+        const ulonglong2 g0 = gp[0], g1 = gp[TW / 4], g2 = gp[2 * (TW / 4)];
 #pragma unroll
         for (int k = 0; k < kRowsPerWarp; ++k) {
           const float4 sv = F::widen(v[u][k][m]);
-          acc[k][0] += dot4(sv, g0);
-          acc[k][1] += dot4(sv, g1);
-          acc[k][2] += dot4(sv, g2);
+          const unsigned long long s01 = f2pack(sv.x, sv.y), s23 = f2pack(sv.z, sv.w);
+          acc[k][0] = ffma2(s23, g0.y, ffma2(s01, g0.x, acc[k][0]));
+          acc[k][1] = ffma2(s23, g1.y, ffma2(s01, g1.x, acc[k][1]));
+          acc[k][2] = ffma2(s23, g2.y, ffma2(s01, g2.x, acc[k][2]));
         }
       }
     }
@@ -263,23 +268,21 @@ __global__ void __launch_bounds__(256, PassOcc<T, U>::kMinBlocks) k_pass2(DevSim
   int slot = d.s2_seg_base[blockIdx.x];
   LaneMeta mt = fetch_meta<true>(d, d.s2_tiles, t1, t0, lane, warp, true);
   int cur = __shfl_sync(0xffffffffu, mt.key, 0);
-  float acc[kChunks][3][4];
+  // per chunk and component, the four columns' sums as the pairs (0, 1) and (2, 3)
+  unsigned long long acc[kChunks][3][2];
 #pragma unroll
   for (int m = 0; m < kChunks; ++m)
 #pragma unroll
-    for (int comp = 0; comp < 3; ++comp)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[m][comp][e] = 0.f;
+    for (int comp = 0; comp < 3; ++comp) acc[m][comp][0] = acc[m][comp][1] = 0ull;
   // every warp reaches a flush at the same tile, so the barriers are uniform
   auto flush = [&]() {
 #pragma unroll
     for (int m = 0; m < kChunks; ++m)
 #pragma unroll
       for (int comp = 0; comp < 3; ++comp) {
-        *reinterpret_cast<float4*>(&red[(warp * 3 + comp) * TW + 4 * lane + 128 * m]) =
-            make_float4(acc[m][comp][0], acc[m][comp][1], acc[m][comp][2], acc[m][comp][3]);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) acc[m][comp][e] = 0.f;
+        *reinterpret_cast<ulonglong2*>(&red[(warp * 3 + comp) * TW + 4 * lane + 128 * m]) =
+            make_ulonglong2(acc[m][comp][0], acc[m][comp][1]);
+        acc[m][comp][0] = acc[m][comp][1] = 0ull;
       }
     __syncthreads();
     float* out = d.p2_part + (size_t)slot * 3 * TW;
@@ -328,15 +331,18 @@ __global__ void __launch_bounds__(256, PassOcc<T, U>::kMinBlocks) k_pass2(DevSim
         const float y0 = __shfl_sync(0xffffffffu, ly0, u * 4 + k);
         const float y1 = __shfl_sync(0xffffffffu, ly1, u * 4 + k);
         const float y2 = __shfl_sync(0xffffffffu, ly2, u * 4 + k);
+        const unsigned long long y00 = f2pack(y0, y0), y11 = f2pack(y1, y1),
+                                 y22 = f2pack(y2, y2);
 #pragma unroll
         for (int m = 0; m < kChunks; ++m) {
           const float4 sv = F::widen(v[u][k][m]);
-          acc[m][0][0] += sv.x * y0; acc[m][0][1] += sv.y * y0;
-          acc[m][0][2] += sv.z * y0; acc[m][0][3] += sv.w * y0;
-          acc[m][1][0] += sv.x * y1; acc[m][1][1] += sv.y * y1;
-          acc[m][1][2] += sv.z * y1; acc[m][1][3] += sv.w * y1;
-          acc[m][2][0] += sv.x * y2; acc[m][2][1] += sv.y * y2;
-          acc[m][2][2] += sv.z * y2; acc[m][2][3] += sv.w * y2;
+          const unsigned long long s01 = f2pack(sv.x, sv.y), s23 = f2pack(sv.z, sv.w);
+          acc[m][0][0] = ffma2(s01, y00, acc[m][0][0]);
+          acc[m][0][1] = ffma2(s23, y00, acc[m][0][1]);
+          acc[m][1][0] = ffma2(s01, y11, acc[m][1][0]);
+          acc[m][1][1] = ffma2(s23, y11, acc[m][1][1]);
+          acc[m][2][0] = ffma2(s01, y22, acc[m][2][0]);
+          acc[m][2][1] = ffma2(s23, y22, acc[m][2][1]);
         }
       }
     }

