@@ -338,7 +338,8 @@ def warmstart_ab():
            "training_samples": int(len(X)), "train_loss": [float(losses[0]), float(losses[-1])],
            "tolerance": 1e-4, "max_iters": 40,
            "gains": {"persist": gains[0], "fresh": gains[1], "move": gains[2],
-                     "validation": {f"{g[0]},{g[1]},{g[2]}": [round(v[0], 2), round(v[1], 4)]
+                     "accept": gains[3],
+                     "validation": {",".join(str(x) for x in g): [round(v[0], 2), round(v[1], 4)]
                                     for g, v in table.items()}}}
     for m in modes:
         R5 = traces[m]["residuals"][:, 5]

@@ -131,7 +131,9 @@ typedef struct {
   int32_t n_host_threads;      /* threads for the host precompute (0: all cores)          */
   int32_t autotune;            /* 1: time the profile products' launch configurations at
                                   creation and keep the fastest (sim_get_tuning); 0
-                                  (default): the fixed configuration                     */
+                                  (default): the fixed configuration; 2: the fixed grid
+                                  with the products in their bulk-copy form (S~ rows moved
+                                  into shared memory by cp.async.bulk)                   */
   int32_t ncp;                 /* SIM_NCP_FB (default) or SIM_NCP_MINMAP: the functions
                                   that drive the iteration. The residual (sim_stats) is one
                                   measure for every choice: min(delta_n, r_n lambda_n) and
@@ -204,7 +206,9 @@ typedef struct {
   int32_t candidates;          /* configurations timed per product                        */
   int32_t pass1_ctas, pass2_ctas;       /* CTAs of each product's launch                  */
   int32_t pass1_unroll, pass2_unroll;   /* tiles in flight per warp: 1 the format's default,
-                                           0 half, 2 twice (one resident CTA per SM)      */
+                                           0 half, 2 twice (one resident CTA per SM); 3:
+                                           bulk copies into a ring of shared-memory stages
+                                           (a producer warp, eight consumer warps)       */
   double pass1_balance, pass2_balance;  /* cost of an empty tile position relative to a
                                            stored value when the tiles are split over CTAs */
   double pass1_us, pass2_us;            /* median launch time of the choice (tuned only)   */
@@ -494,10 +498,12 @@ int sim_set_warmstart(sim_t* sim, const sim_mlp_t* net, int32_t mode);
  * an impulse at the same vertex and obstacle in the previous frame and g = fresh for a new
  * one; the predicted change of the normal move from the previous frame's is scaled by move.
  * 0 leaves that part at the previous frame's value, so 0, 0, 0 is the previous-frame start
- * (mode 2) with the network's cost; 1, 1, 1 (the default) is the network as trained. Chosen,
- * for example, on validation frames by iterations to a residual tolerance. Non-negative
- * finite values, else SIM_EINVAL. Synchronises the handle's stream. */
-int sim_set_warmstart_gains(sim_t* sim, float persist, float fresh, float move);
+ * (mode 2) with the network's cost; 1, 1, 1 (the default) is the network as trained.
+ * accept in (0, 1]: the learned guess is kept when its residual at k = 0 is below accept
+ * times the cold start's (1, the default: any improvement). Chosen, for example, on
+ * validation frames by time to a residual tolerance. Gains non-negative and finite, accept
+ * in (0, 1], else SIM_EINVAL. Synchronises the handle's stream. */
+int sim_set_warmstart_gains(sim_t* sim, float persist, float fresh, float move, float accept);
 /* Load a trained warm-start network and switch the learned start on (mode 1 of
  * sim_set_warmstart): weights is the flat FP32 parameter vector in the layout above
  * (SIM_MLP_PARAMS values, as sim_mlp_get_params writes it), bytes = 4 * SIM_MLP_PARAMS.

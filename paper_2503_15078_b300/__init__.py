@@ -335,10 +335,12 @@ class Simulator:
         _check(lib().sim_set_warmstart(self._h, net.handle if net is not None else None,
                                        int(mode)), "sim_set_warmstart")
 
-    def set_warmstart_gains(self, persist=1.0, fresh=1.0, move=1.0):
+    def set_warmstart_gains(self, persist=1.0, fresh=1.0, move=1.0, accept=1.0):
         """Gains of the network's outputs in the learned start (persisting contacts' impulse
-        change, new contacts' impulse, normal move)."""
-        _check(lib().sim_set_warmstart_gains(self._h, float(persist), float(fresh), float(move)),
+        change, new contacts' impulse, change of the normal move) and its acceptance ratio
+        (the guess is kept when its residual at k = 0 is below accept x the cold start's)."""
+        _check(lib().sim_set_warmstart_gains(self._h, float(persist), float(fresh), float(move),
+                                             float(accept)),
                "sim_set_warmstart_gains")
 
     def set_phase_marks(self, on):

@@ -105,7 +105,8 @@ PROTOTYPES = {
     "sim_set_warmstart": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "sim_set_portfolio": (C.c_int, [C.c_void_p, C.c_int32]),
     "sim_set_phase_marks": (C.c_int, [C.c_void_p, C.c_int32]),
-    "sim_set_warmstart_gains": (C.c_int, [C.c_void_p, C.c_float, C.c_float, C.c_float]),
+    "sim_set_warmstart_gains": (C.c_int, [C.c_void_p, C.c_float, C.c_float, C.c_float,
+                                           C.c_float]),
     "sim_get_warmstart_samples": (C.c_int, [C.c_void_p, C.c_int32, _fp, _fp,
                                             C.POINTER(C.c_int32)]),
     "sim_mlp_destroy": (None, [C.c_void_p]),

@@ -154,7 +154,8 @@ struct DevSim {
   // gains of the network's outputs in the learned start: the impulse change of a contact
   // that had an impulse at the same vertex and obstacle in the previous frame, the impulse
   // of a new contact, the normal move (1, 1, 1 by default)
-  float ws_gain[3];
+  float ws_gain[4];   // learned start: impulse gains (persisting, new), move gain, and the
+                      // acceptance ratio (a guess is kept below ratio x the cold residual)
   float* ws_feat;             // cap x kMlpIn: features at the frame start
   float* ws_out;              // cap x kMlpOut: network outputs
   double* ws_scale;           // cap: impulse scale margin / (h^2 W~_vv)
@@ -237,7 +238,8 @@ struct DevSim {
   const int* s1_col_slot;   // per pass-1 tile: position of its column tile in that list
   int s1_max_cols;
   int s1_grid, s2_grid, n_seg1, n_seg2;
-  int s1_unroll, s2_unroll;  // tiles in flight per warp: 1 the format's, 0 half, 2 twice
+  int s1_unroll, s2_unroll;  // tiles in flight per warp: 1 the format's, 0 half, 2 twice;
+                             // kUnrollBulk: bulk copies into a ring of shared-memory stages
   int n_sm;         // persistent-kernel grid size
   int* scan_part;   // scratch of the two-pass scans (tile sums and offsets)
   // Delassus reuse across frames: W~ = Y^T Y and Y depend only on the list of contact
@@ -374,6 +376,7 @@ constexpr int kWtMaxSplit = 16;
 constexpr int kCrMaxRanks = 16;
 constexpr int kTriChunk = 16;   // surface triangles per bounding box of the body search
 constexpr int kTriSuper = 256;  // ... and per bounding box of the level above
+constexpr int kUnrollBulk = 3;
 constexpr int kMaxStagedCols = 32;  // column tiles of g staged per pass-1 CTA (96 KB)
 inline long long wt_items_max(int cap, int grid) {
   long long best = 0;

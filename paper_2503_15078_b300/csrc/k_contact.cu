@@ -1268,6 +1268,7 @@ struct CrLayout {
 // a time with 8-byte loads and packed FP32 FMAs and reduces the twelve row sums over the warp
 // with a butterfly of 16 shuffles.
 constexpr int kCrPairs = 16;     // register-held column pairs per lane: rows up to 1024 wide
+constexpr int kCrDotSlots = kCrMaxRanks * (kCrThreads / 32);   // (rank, warp) partials
 
 // Sum each of v[0..11] over the warp; afterwards lanes 2i and 2i + 1 hold the total of v[i]
 // in v[0]. Butterfly halving: at each step a lane keeps half of its values and adds the
@@ -1321,7 +1322,7 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
     nv_max = max(nv_max, split_cv[r + 1] - split_cv[r]);
   }
   // shared layout (identical offsets in every CTA for the parts written remotely):
-  //   dots[16] float4  per-rank partial dot products (written by every rank)
+  //   dots[kCrDotSlots] float4  per-(rank, warp) partial dot products (written by every rank)
   //   uall[ldw] float4 u for all contact vertices (each rank writes its own range everywhere)
   const int ldw = d.sc_ld[scene];
   const float* wblk = d.wt + d.sc_wtoff[scene];  // the scene's W~ block, row-major
@@ -1330,8 +1331,8 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
   //   tall[c] float4   D_j^T (omega_j v_j) of every contact of the scene
   //   wall[ldw] float4 (W~ u) of every contact vertex of the scene
   const bool gen = d.bc_on != 0;
-  float4* dots = reinterpret_cast<float4*>(sm);          // 16 float4
-  float4* uall = dots + 16;                              // ldw float4
+  float4* dots = reinterpret_cast<float4*>(sm);          // kCrDotSlots float4
+  float4* uall = dots + kCrDotSlots;                     // ldw float4
   float4* tall = uall + ldw;                             // c float4 (gen)
   float4* wall = tall + (gen ? L.c : 0);                 // ldw float4 (gen)
   float4* uloc = wall + (gen ? ldw : 0);                 // nv_max float4 (own slice)
@@ -1477,20 +1478,23 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
   auto apply = [&](const float* v, float* Kv) {
     if (gen) publish_t(v);
     // this phase brings every contact vertex's u (16 bytes each) from its owner
-    if (async_x && threadIdx.x == 0) mbar_expect(smem_u32(&xbar[0]), (unsigned)L.ncv * 16u);
-    for (int cvl = threadIdx.x; cvl < nv; cvl += blockDim.x) uloc[cvl] = vertex_u(v, cvl);
-    __syncthreads();
-    // one 16-byte remote store per (rank, owned vertex), spread over all threads
     if (async_x) {
+      // the thread that computes an owned vertex's u stores it into every rank (itself
+      // included), counted on that rank's barrier
+      if (threadIdx.x == 0) mbar_expect(smem_u32(&xbar[0]), (unsigned)L.ncv * 16u);
       const unsigned ub = smem_u32(uall + L.cv0), bb = smem_u32(&xbar[0]);
-      for (int e = threadIdx.x; e < L.R * nv; e += blockDim.x) {
-        const int r = e / nv, cvl = e - r * nv;
-        st_async_v4(mapa_u32(ub + 16u * (unsigned)cvl, r), uloc[cvl], mapa_u32(bb, r));
+      for (int cvl = threadIdx.x; cvl < nv; cvl += blockDim.x) {
+        const float4 u = vertex_u(v, cvl);
+        for (int r = 0; r < L.R; ++r)
+          st_async_v4(mapa_u32(ub + 16u * (unsigned)cvl, r), u, mapa_u32(bb, r));
       }
       if (!mbar_wait_cluster(smem_u32(&xbar[0]), ph_u & 1u, d.spin_limit) && threadIdx.x == 0)
         atomicOr(d.err, kErrTimeout);
       ++ph_u;
     } else {
+      for (int cvl = threadIdx.x; cvl < nv; cvl += blockDim.x) uloc[cvl] = vertex_u(v, cvl);
+      __syncthreads();
+      // one 16-byte remote store per (rank, owned vertex), spread over all threads
       for (int e = threadIdx.x; e < L.R * nv; e += blockDim.x) {
         const int r = e / nv, cvl = e - r * nv;
         cl.map_shared_rank(uall, r)[L.cv0 + cvl] = uloc[cvl];
@@ -1629,58 +1633,39 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
       Kv[e] = om[e] * dw + ec[e] * v[e];
     }
   };
-  // cluster-wide sums of three values. Per warp, then per CTA in warp 0, then over the
-  // ranks in warp 0 of every CTA: the same shuffle tree on the same values everywhere, so
-  // every CTA holds identical scalars (deterministic).
-  __shared__ float wpart[3][32];
-  __shared__ float red3[3];
+  // cluster-wide sums of three values: per warp (butterfly), then every warp's partial goes
+  // to slot (rank, warp) of every CTA in one exchange, and every warp adds all R x 8 slots
+  // in the same order (lane l: slots l, l + 32, ...; then the butterfly). Every warp of
+  // every CTA holds identical scalars (deterministic), with no block barrier.
   auto exchange = [&](float& a, float& b, float& c) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     a = warp_sum(a);
     b = warp_sum(b);
     c = warp_sum(c);
-    if (lane == 0) {
-      wpart[0][wid] = a;
-      wpart[1][wid] = b;
-      wpart[2][wid] = c;
-    }
-    __syncthreads();
-    if (wid == 0) {
-      a = warp_sum(lane < nw ? wpart[0][lane] : 0.f);
-      b = warp_sum(lane < nw ? wpart[1][lane] : 0.f);
-      c = warp_sum(lane < nw ? wpart[2][lane] : 0.f);
-      if (async_x) {
-        // this phase brings one float4 from every rank
-        if (lane == 0) mbar_expect(smem_u32(&xbar[1]), (unsigned)L.R * 16u);
-        if (lane < L.R)
-          st_async_v4(mapa_u32(smem_u32(dots + L.rank), lane), make_float4(a, b, c, 0.f),
-                      mapa_u32(smem_u32(&xbar[1]), lane));
-      } else if (lane < L.R) {
-        cl.map_shared_rank(dots, lane)[L.rank] = make_float4(a, b, c, 0.f);
-      }
-    }
+    const int nslot = L.R * nw;
     if (async_x) {
+      // this phase brings one float4 from every (rank, warp)
+      if (threadIdx.x == 0) mbar_expect(smem_u32(&xbar[1]), (unsigned)nslot * 16u);
+      if (lane < L.R)
+        st_async_v4(mapa_u32(smem_u32(dots + L.rank * nw + wid), lane), make_float4(a, b, c, 0.f),
+                    mapa_u32(smem_u32(&xbar[1]), lane));
       if (!mbar_wait_cluster(smem_u32(&xbar[1]), ph_d & 1u, d.spin_limit) && threadIdx.x == 0)
         atomicOr(d.err, kErrTimeout);
       ++ph_d;
     } else {
+      if (lane < L.R) cl.map_shared_rank(dots, lane)[L.rank * nw + wid] = make_float4(a, b, c, 0.f);
       cl.sync();
     }
-    if (wid == 0) {
-      const float4 t = lane < L.R ? dots[lane] : make_float4(0, 0, 0, 0);
-      a = warp_sum(t.x);
-      b = warp_sum(t.y);
-      c = warp_sum(t.z);
-      if (lane == 0) {
-        red3[0] = a;
-        red3[1] = b;
-        red3[2] = c;
-      }
+    float ta = 0.f, tb = 0.f, tc = 0.f;
+    for (int q = lane; q < nslot; q += 32) {
+      const float4 t = dots[q];
+      ta += t.x;
+      tb += t.y;
+      tc += t.z;
     }
-    __syncthreads();
-    a = red3[0];
-    b = red3[1];
-    c = red3[2];
+    a = warp_sum(ta);
+    b = warp_sum(tb);
+    c = warp_sum(tc);
   };
 
   // r = rhs, x = 0, p = r, Ap = Ar

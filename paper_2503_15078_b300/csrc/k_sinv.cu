@@ -21,6 +21,7 @@
 // deterministic.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <utility>
 
 #include "device.cuh"
@@ -80,10 +81,6 @@ __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
-}
-
-__device__ __forceinline__ float dot4(const float4& a, const float4& b) {
-  return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
 }
 
 // Row metadata of the tiles of one batch, held one entry per lane: lane u * 4 + k has
@@ -378,6 +375,342 @@ __global__ void k_reduce2(DevSim d) {
 }
 
 
+// ---- the products through bulk copies ----------------------------------------------------
+// The same tile streams, partial-sum slots and reductions as k_pass1 / k_pass2, with the
+// S~ values moved into shared memory by bulk copies (cp.async.bulk, one per row run of a
+// tile) instead of register loads. A producer warp walks the CTA's tiles and fills a ring
+// of stages: per tile the row runs, in pass 1 the g slice of its column tile, in pass 2
+// the y of its rows; each stage completes on an mbarrier when its bytes have arrived.
+// Eight consumer warps (kRowsPerWarp rows of every tile each) multiply and release the
+// stage on a second mbarrier. A lane reads eight consecutive values of a row: runs start
+// and end on 8-value boundaries (16 bytes in BF16), so the lane's values lie either inside
+// the row's run in that tile or outside it (zeros). Every wait is bounded: on a timeout the
+// kernel records kErrTimeout and the waits that follow are skipped (the frame reports
+// SIM_ETIMEOUT); before it exits, the producer waits (bounded) for the copies it issued.
+constexpr int kBulkConsumers = kWarps;
+constexpr int kBulkThreads = 32 * (kBulkConsumers + 1);
+constexpr int kBulkMaxStages = 8;
+constexpr int kBulkSmemMax = 227 * 1024;    // dynamic shared memory of one CTA, at most
+constexpr int kSmemPerSm = 228 * 1024;
+
+template <class T, bool kPass2> struct BulkLayout {
+  static constexpr int kVals = RG * TW * (int)sizeof(T);          // the tile's values
+  static constexpr int kSide = kPass2 ? RG * 16 : 3 * TW * 4;      // y (float4 per row) | g
+  static constexpr int kRuns = RG * 8;                             // int2 [a, b) per row
+  static constexpr int kStage = (kVals + kSide + kRuns + 127) / 128 * 128;
+  static constexpr int kRed = kPass2 ? kBulkConsumers * 3 * TW * 4 : 0;   // pass 2 flush
+};
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+// wait for the phase of the given parity to complete, at most `limit` polls
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity,
+                                                  unsigned long long limit) {
+  for (unsigned long long i = 0; i < limit; ++i) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes,
+                                         unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+// the eight values of a lane's part of a row, as four packed pairs (zeros outside the run)
+template <class T> struct BulkRow;
+template <> struct BulkRow<unsigned short> {
+  static __device__ __forceinline__ void get(const char* row, int lane, bool ok,
+                                             unsigned long long (&p)[4]) {
+    uint4 r = make_uint4(0u, 0u, 0u, 0u);
+    if (ok) r = *reinterpret_cast<const uint4*>(row + 16 * lane);
+    p[0] = f2pack(__uint_as_float(r.x << 16), __uint_as_float(r.x & 0xffff0000u));
+    p[1] = f2pack(__uint_as_float(r.y << 16), __uint_as_float(r.y & 0xffff0000u));
+    p[2] = f2pack(__uint_as_float(r.z << 16), __uint_as_float(r.z & 0xffff0000u));
+    p[3] = f2pack(__uint_as_float(r.w << 16), __uint_as_float(r.w & 0xffff0000u));
+  }
+};
+template <> struct BulkRow<float> {
+  static __device__ __forceinline__ void get(const char* row, int lane, bool ok,
+                                             unsigned long long (&p)[4]) {
+    ulonglong2 a = make_ulonglong2(0ull, 0ull), b = make_ulonglong2(0ull, 0ull);
+    if (ok) {
+      a = *reinterpret_cast<const ulonglong2*>(row + 32 * lane);
+      b = *reinterpret_cast<const ulonglong2*>(row + 32 * lane + 16);
+    }
+    p[0] = a.x;
+    p[1] = a.y;
+    p[2] = b.x;
+    p[3] = b.y;
+  }
+};
+
+// The producer warp: fills stage i % S with tile t0 + i once the consumers have released
+// its previous use. Returns the number of tiles issued.
+template <class T, bool kPass2>
+__device__ int bulk_produce(const DevSim& d, const int2* tiles, int t0, int t1, char* stages,
+                            int S, unsigned full0, unsigned empty0, int lane, bool& dead) {
+  using L = BulkLayout<T, kPass2>;
+  const T* vals = Fmt<T>::vals(d);
+  int i = 0;
+  for (int t = t0; t < t1; ++t, ++i) {
+    const int s = i % S;
+    const unsigned full = full0 + 8u * s, empty = empty0 + 8u * s;
+    if (i >= S && !dead && !mbar_wait_bounded(empty, (unsigned)((i / S) - 1) & 1u, d.spin_limit)) {
+      if (lane == 0) atomicOr(d.err, kErrTimeout);
+      dead = true;
+    }
+    if (dead) break;
+    char* st = stages + (size_t)s * L::kStage;
+    const int2 tl = tiles[t];
+    const int rg = kPass2 ? tl.y : tl.x, ct = kPass2 ? tl.x : tl.y;
+    const int r = rg * RG + lane;
+    int a = 0, b = 0;
+    long long base = 0;
+    if (r < d.n) {
+      const int lo = d.lo[r], hi = d.hi[r];
+      a = max(lo, ct * TW);
+      b = min(hi, ct * TW + TW);
+      if (b < a) b = a;
+      base = d.rowbase[r] - lo;
+    }
+    reinterpret_cast<int2*>(st + L::kVals + L::kSide)[lane] = make_int2(a - ct * TW, b - ct * TW);
+    if (kPass2) {
+      float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < d.n) y = make_float4(d.zvec[r], d.zvec[d.n_pad + r], d.zvec[2 * d.n_pad + r], 0.f);
+      reinterpret_cast<float4*>(st + L::kVals)[lane] = y;
+    }
+    unsigned bytes = (unsigned)(b - a) * (unsigned)sizeof(T);
+    unsigned total = bytes;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+    if (!kPass2) total += 3u * TW * 4u;
+    // lane 0 announces the bytes the copies will deliver before any copy is issued; every
+    // lane's writes of the stage's metadata are released by its own arrival
+    __syncwarp();
+    if (lane == 0) mbar_arrive_tx(full, total);
+    __syncwarp();
+    if (lane != 0) mbar_arrive(full);
+    if (bytes)
+      bulk_g2s((unsigned)__cvta_generic_to_shared(st + (size_t)(a - ct * TW) * sizeof(T) +
+                                                   (size_t)lane * TW * sizeof(T)),
+               vals + base + a, bytes, full);
+    if (!kPass2 && lane < 3)
+      bulk_g2s((unsigned)__cvta_generic_to_shared(st + L::kVals + lane * TW * 4),
+               d.gvec + (size_t)lane * d.n_pad + (size_t)ct * TW, TW * 4u, full);
+  }
+  return i;
+}
+
+// the producer's last act: wait (bounded) until the copies of the last use of every stage
+// have landed, so that no copy is in flight into the CTA's shared memory when it exits
+template <class T, bool kPass2>
+__device__ void bulk_drain(const DevSim& d, int issued, int S, unsigned full0) {
+  for (int i = max(0, issued - S); i < issued; ++i)
+    mbar_wait_bounded(full0 + 8u * (i % S), (unsigned)(i / S) & 1u, d.spin_limit);
+}
+
+// z partials, as k_pass1
+template <class T>
+__global__ void __launch_bounds__(kBulkThreads, 2) k_pass1_bulk(DevSim d, int S) {
+  pdl_wait();
+  using L = BulkLayout<T, false>;
+  extern __shared__ __align__(128) char bsm[];
+  __shared__ __align__(8) unsigned long long bar_full[kBulkMaxStages], bar_empty[kBulkMaxStages];
+  const int t0 = d.s1_cta[blockIdx.x], t1 = d.s1_cta[blockIdx.x + 1];
+  if (t0 >= t1) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned full0 = (unsigned)__cvta_generic_to_shared(bar_full);
+  const unsigned empty0 = (unsigned)__cvta_generic_to_shared(bar_empty);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full0 + 8u * s, 32);
+      mbar_init(empty0 + 8u * s, kBulkConsumers);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  bool dead = false;
+  if (warp == kBulkConsumers) {
+    const int issued = bulk_produce<T, false>(d, d.s1_tiles, t0, t1, bsm, S, full0, empty0, lane,
+                                              dead);
+    if (lane == 0) bulk_drain<T, false>(d, issued, S, full0);
+    return;
+  }
+  int slot = d.s1_seg_base[blockIdx.x];
+  int cur = d.s1_tiles[t0].x;
+  unsigned long long acc[kRowsPerWarp][3];
+#pragma unroll
+  for (int k = 0; k < kRowsPerWarp; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0ull;
+  auto flush = [&]() {
+    float* out = d.p1_part + (size_t)slot * 3 * RG;
+#pragma unroll
+    for (int k = 0; k < kRowsPerWarp; ++k)
+#pragma unroll
+      for (int comp = 0; comp < 3; ++comp) {
+        const float v = warp_sum(f2lo(acc[k][comp]) + f2hi(acc[k][comp]));
+        if (lane == 0) out[comp * RG + warp * kRowsPerWarp + k] = v;
+        acc[k][comp] = 0ull;
+      }
+    ++slot;
+  };
+  int i = 0;
+  for (int t = t0; t < t1; ++t, ++i) {
+    const int s = i % S;
+    if (!dead && !mbar_wait_bounded(full0 + 8u * s, (unsigned)(i / S) & 1u, d.spin_limit)) {
+      if (lane == 0) atomicOr(d.err, kErrTimeout);
+      dead = true;
+    }
+    const char* st = bsm + (size_t)s * L::kStage;
+    const int key = d.s1_tiles[t].x;
+    if (key != cur) {
+      flush();
+      cur = key;
+    }
+    // g of the lane's eight columns, as packed pairs per component
+    const ulonglong2* gp = reinterpret_cast<const ulonglong2*>(st + L::kVals) + 2 * lane;
+    const ulonglong2 g0a = gp[0], g0b = gp[1], g1a = gp[64], g1b = gp[65], g2a = gp[128],
+                     g2b = gp[129];
+    const int2* runs = reinterpret_cast<const int2*>(st + L::kVals + L::kSide);
+#pragma unroll
+    for (int k = 0; k < kRowsPerWarp; ++k) {
+      const int row = warp * kRowsPerWarp + k;
+      const int2 run = runs[row];
+      const bool ok = 8 * lane >= run.x && 8 * lane < run.y;
+      unsigned long long p[4];
+      BulkRow<T>::get(st + (size_t)row * TW * sizeof(T), lane, ok, p);
+      acc[k][0] = ffma2(p[3], g0b.y, ffma2(p[2], g0b.x, ffma2(p[1], g0a.y, ffma2(p[0], g0a.x, acc[k][0]))));
+      acc[k][1] = ffma2(p[3], g1b.y, ffma2(p[2], g1b.x, ffma2(p[1], g1a.y, ffma2(p[0], g1a.x, acc[k][1]))));
+      acc[k][2] = ffma2(p[3], g2b.y, ffma2(p[2], g2b.x, ffma2(p[1], g2a.y, ffma2(p[0], g2a.x, acc[k][2]))));
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty0 + 8u * s);
+  }
+  flush();
+}
+
+// x partials, as k_pass2
+template <class T>
+__global__ void __launch_bounds__(kBulkThreads, 2) k_pass2_bulk(DevSim d, int S) {
+  pdl_wait();
+  using L = BulkLayout<T, true>;
+  extern __shared__ __align__(128) char bsm[];
+  __shared__ __align__(8) unsigned long long bar_full[kBulkMaxStages], bar_empty[kBulkMaxStages];
+  __shared__ __align__(8) unsigned long long bar_red;   // the consumers' flush barrier
+  const int t0 = d.s2_cta[blockIdx.x], t1 = d.s2_cta[blockIdx.x + 1];
+  if (t0 >= t1) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned full0 = (unsigned)__cvta_generic_to_shared(bar_full);
+  const unsigned empty0 = (unsigned)__cvta_generic_to_shared(bar_empty);
+  const unsigned redb = (unsigned)__cvta_generic_to_shared(&bar_red);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full0 + 8u * s, 32);
+      mbar_init(empty0 + 8u * s, kBulkConsumers);
+    }
+    mbar_init(redb, kBulkConsumers * 32);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  bool dead = false;
+  if (warp == kBulkConsumers) {
+    const int issued = bulk_produce<T, true>(d, d.s2_tiles, t0, t1, bsm, S, full0, empty0, lane,
+                                             dead);
+    if (lane == 0) bulk_drain<T, true>(d, issued, S, full0);
+    return;
+  }
+  float* red = reinterpret_cast<float*>(bsm + (size_t)S * L::kStage);   // [warp][comp][TW]
+  int slot = d.s2_seg_base[blockIdx.x];
+  int cur = d.s2_tiles[t0].x;
+  unsigned red_phase = 0;
+  // the consumers' barrier (all 256 consumer threads arrive; bounded wait)
+  auto consumers_sync = [&]() {
+    mbar_arrive(redb);
+    if (!dead && !mbar_wait_bounded(redb, red_phase & 1u, d.spin_limit)) {
+      if (lane == 0) atomicOr(d.err, kErrTimeout);
+      dead = true;
+    }
+    ++red_phase;
+  };
+  // per component, the lane's eight columns as four packed pairs
+  unsigned long long acc[3][4];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0ull;
+  auto flush = [&]() {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      ulonglong2* dst = reinterpret_cast<ulonglong2*>(red + (warp * 3 + c) * TW + 8 * lane);
+      dst[0] = make_ulonglong2(acc[c][0], acc[c][1]);
+      dst[1] = make_ulonglong2(acc[c][2], acc[c][3]);
+      acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0ull;
+    }
+    consumers_sync();
+    float* out = d.p2_part + (size_t)slot * 3 * TW;
+    for (int idx = threadIdx.x; idx < 3 * TW; idx += kBulkConsumers * 32) {
+      const int comp = idx / TW, c = idx % TW;
+      float sum = 0.f;
+#pragma unroll
+      for (int w = 0; w < kBulkConsumers; ++w) sum += red[(w * 3 + comp) * TW + c];
+      out[comp * TW + c] = sum;
+    }
+    consumers_sync();
+    ++slot;
+  };
+  int i = 0;
+  for (int t = t0; t < t1; ++t, ++i) {
+    const int s = i % S;
+    if (!dead && !mbar_wait_bounded(full0 + 8u * s, (unsigned)(i / S) & 1u, d.spin_limit)) {
+      if (lane == 0) atomicOr(d.err, kErrTimeout);
+      dead = true;
+    }
+    const char* st = bsm + (size_t)s * L::kStage;
+    const int key = d.s2_tiles[t].x;
+    if (key != cur) {
+      flush();
+      cur = key;
+    }
+    const int2* runs = reinterpret_cast<const int2*>(st + L::kVals + L::kSide);
+    const float4* ys = reinterpret_cast<const float4*>(st + L::kVals);
+#pragma unroll
+    for (int k = 0; k < kRowsPerWarp; ++k) {
+      const int row = warp * kRowsPerWarp + k;
+      const int2 run = runs[row];
+      const float4 y = ys[row];
+      const bool ok = 8 * lane >= run.x && 8 * lane < run.y;
+      unsigned long long p[4];
+      BulkRow<T>::get(st + (size_t)row * TW * sizeof(T), lane, ok, p);
+      const unsigned long long y0 = f2pack(y.x, y.x), y1 = f2pack(y.y, y.y), y2 = f2pack(y.z, y.z);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[0][q] = ffma2(p[q], y0, acc[0][q]);
+        acc[1][q] = ffma2(p[q], y1, acc[1][q]);
+        acc[2][q] = ffma2(p[q], y2, acc[2][q]);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty0 + 8u * s);
+  }
+  flush();
+}
+
 // Residual of a global solve, rho = rhs - A~ x per component, into gsave (SoA).
 //   kResApply:        rhs = gsave (the saved right-hand side), x = xout
 //   kResFrame:        rhs = g (gvec), x = dq
@@ -460,13 +793,52 @@ int sinv_setup() {
   for (const void* f : fns)
     if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, most) != cudaSuccess)
       return SIM_ECUDA;
+  const void* bulk[] = {(const void*)k_pass1_bulk<float>, (const void*)k_pass1_bulk<unsigned short>,
+                        (const void*)k_pass2_bulk<float>, (const void*)k_pass2_bulk<unsigned short>};
+  for (const void* f : bulk)
+    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kBulkSmemMax) !=
+        cudaSuccess)
+      return SIM_ECUDA;
   return SIM_OK;
 }
 
-// unroll: 1 = the format's default tiles in flight, 0 = half of it, 2 = twice
+// stages of a bulk-copy product with `grid` CTAs over the device's SMs (the CTAs of one
+// wave share an SM's shared memory); 0 if fewer than two fit
+template <class T, bool kPass2>
+int bulk_stages(const DevSim& d, int grid) {
+  using L = BulkLayout<T, kPass2>;
+  const int per_sm = std::max(1, (grid + d.n_sm - 1) / d.n_sm);
+  const int budget = std::min(kBulkSmemMax, kSmemPerSm / per_sm - 1024 - 256) - L::kRed;
+  const int S = std::min(kBulkMaxStages, budget / L::kStage);
+  return S >= 2 ? S : 0;
+}
+
+template <class T>
+bool launch_pass1_bulk(const DevSim& d, cudaStream_t s) {
+  const int S = bulk_stages<T, false>(d, d.s1_grid);
+  if (!S) return false;
+  launch_k(d.pdl, k_pass1_bulk<T>, d.s1_grid, kBulkThreads,
+           (size_t)S * BulkLayout<T, false>::kStage, s, d, S);
+  return true;
+}
+
+template <class T>
+bool launch_pass2_bulk(const DevSim& d, cudaStream_t s) {
+  const int S = bulk_stages<T, true>(d, d.s2_grid);
+  if (!S) return false;
+  launch_k(d.pdl, k_pass2_bulk<T>, d.s2_grid, kBulkThreads,
+           (size_t)S * BulkLayout<T, true>::kStage + BulkLayout<T, true>::kRed, s, d, S);
+  return true;
+}
+
+// unroll: 1 = the format's default tiles in flight, 0 = half of it, 2 = twice; kUnrollBulk:
+// the bulk-copy form (the register form where its stages do not fit)
 void launch_pass1(const DevSim& d, cudaStream_t s) {
   const size_t smem = (size_t)d.s1_max_cols * 3 * TW * sizeof(float);
   const int g = d.s1_grid;
+  if (d.s1_unroll == kUnrollBulk &&
+      (d.s_bf16 ? launch_pass1_bulk<unsigned short>(d, s) : launch_pass1_bulk<float>(d, s)))
+    return;
   if (d.s_bf16) {
     if (d.s1_unroll == 2) launch_k(d.pdl, k_pass1<unsigned short, 8>, g, 256, smem, s, d);
     else if (d.s1_unroll == 1) launch_k(d.pdl, k_pass1<unsigned short, 4>, g, 256, smem, s, d);
@@ -484,6 +856,9 @@ void launch_reduce1(const DevSim& d, cudaStream_t s) {
 
 void launch_pass2(const DevSim& d, cudaStream_t s) {
   const int g = d.s2_grid;
+  if (d.s2_unroll == kUnrollBulk &&
+      (d.s_bf16 ? launch_pass2_bulk<unsigned short>(d, s) : launch_pass2_bulk<float>(d, s)))
+    return;
   if (d.s_bf16) {
     if (d.s2_unroll == 2) launch_k(d.pdl, k_pass2<unsigned short, 8>, g, 256, kP2Smem, s, d);
     else if (d.s2_unroll == 1) launch_k(d.pdl, k_pass2<unsigned short, 4>, g, 256, kP2Smem, s, d);

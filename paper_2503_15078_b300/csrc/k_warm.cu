@@ -119,7 +119,8 @@ __device__ void ws_guess(const DevSim& d, int j) {
 __device__ __forceinline__ bool ws_accepted(const DevSim& d, int sc, double r_guess,
                                             double r_cold) {
   if (d.pf_copies > 1 && sc % d.pf_copies == 0) return false;
-  return r_guess < r_cold;
+  // the learned start may ask for a margin (ratio < 1); the others take any improvement
+  return r_guess < (d.ws_mode == 1 ? (double)d.ws_gain[3] : 1.0) * r_cold;
 }
 
 constexpr int kWsThreads = 256;

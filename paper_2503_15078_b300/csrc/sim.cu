@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <stdexcept>
 #include <array>
 #include <chrono>
 #include <cmath>
@@ -73,6 +74,11 @@ struct sim_s {
     if (dev_alloc) {
       p = dev_alloc(count * sizeof(T), alloc_ctx);
       if (!p) throw std::bad_alloc();
+      // the bulk copies into shared memory need 16-byte aligned sources; the contract is 256
+      if (reinterpret_cast<uintptr_t>(p) % 256 != 0) {
+        dev_free(p, alloc_ctx);
+        throw std::invalid_argument("dev_alloc returned memory not aligned to 256 bytes");
+      }
     } else if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
       throw std::bad_alloc();
     }
@@ -550,7 +556,7 @@ int autotune_products(sim_s* s) {
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SIM_ECUDA;
   const int ctas[] = {1, 2, 3, 4};
   const double balance[] = {1.0, 0.25};
-  const int unroll[] = {1, 0, 2};
+  const int unroll[] = {1, 0, 2, silg::kUnrollBulk};
   sim_tuning& T = s->tuning;
   T = sim_tuning{};
   int status = SIM_OK;
@@ -575,8 +581,12 @@ int autotune_products(sim_s* s) {
             cudaEventElapsedTime(&ms, e0, e1);
           }
           if (cudaGetLastError() != cudaSuccess) status = SIM_ECUDA;
+          // a candidate whose waits ran out (bulk-copy form) is not a choice
+          int err = 0;
+          cudaMemcpy(&err, d.err, sizeof(int), cudaMemcpyDeviceToHost);
+          if (err) cudaMemset(d.err, 0, sizeof(int));
           std::sort(t.begin(), t.end());
-          const double us = 1e3 * t[2];
+          const double us = err ? 1e300 : 1e3 * t[2];
           ++n_cand;
           if (c == kDefaultCtasPerSm && b == kDefaultBalance && u == 1) dflt = us;
           if (us < best) {
@@ -1138,12 +1148,14 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
     if (st != SIM_OK) return st;
   }
   d.cr_R = s->cluster;
-  d.ws_gain[0] = d.ws_gain[1] = d.ws_gain[2] = 1.f;
+  d.ws_gain[0] = d.ws_gain[1] = d.ws_gain[2] = d.ws_gain[3] = 1.f;
   d.cr_single = o->cr_exchanges == 1 ? 1 : 0;
   d.cr_sync = o->cr_sync;
-  if (o->autotune) {
+  if (o->autotune == 1) {
     int st = autotune_products(s);
     if (st != SIM_OK) return st;
+  } else if (o->autotune == 2) {
+    d.s1_unroll = d.s2_unroll = silg::kUnrollBulk;   // the fixed grid, bulk-copy products
   }
   cudaError_t e = cudaStreamSynchronize(s->work);
   if (e != cudaSuccess) return cuda_status(e);
@@ -1253,6 +1265,7 @@ int check_options(const sim_options* o) {
   if (!(o->residual_tol >= 0.0) || o->max_iters < 1 || o->max_iters > silg::kMaxIters)
     return SIM_EINVAL;
   if ((o->dev_alloc == nullptr) != (o->dev_free == nullptr)) return SIM_EINVAL;
+  if (o->autotune < 0 || o->autotune > 2) return SIM_EINVAL;
   if (o->precond != SIM_PRECOND_DELASSUS && o->precond != SIM_PRECOND_MASS) return SIM_EINVAL;
   if (o->cr_exchanges != 1 && o->cr_exchanges != 2) return SIM_EINVAL;
   if (o->delassus_reuse != 0 && o->delassus_reuse != 1) return SIM_EINVAL;
@@ -1594,13 +1607,14 @@ int sim_set_warmstart(sim_t* s, const sim_mlp_t* net, int32_t mode) {
   return SIM_OK;
 }
 
-int sim_set_warmstart_gains(sim_t* s, float persist, float fresh, float move) {
+int sim_set_warmstart_gains(sim_t* s, float persist, float fresh, float move, float accept) {
   if (!s || !std::isfinite(persist) || !std::isfinite(fresh) || !std::isfinite(move) ||
-      persist < 0.f || fresh < 0.f || move < 0.f)
+      persist < 0.f || fresh < 0.f || move < 0.f || !(accept > 0.f && accept <= 1.f))
     return SIM_EINVAL;
   s->d.ws_gain[0] = persist;   // read at graph capture: the cached graphs are dropped
   s->d.ws_gain[1] = fresh;
   s->d.ws_gain[2] = move;
+  s->d.ws_gain[3] = accept;
   silg::DeviceGuard dg(s->device);
   cudaStreamSynchronize(s->launch);
   for (auto& kv : s->graphs) {

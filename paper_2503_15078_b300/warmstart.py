@@ -155,7 +155,7 @@ def evaluate_to_tolerance(scenes, frames, modes, net=None, k_max=40, tol=1e-4, g
     reaches tol (sim_options.residual_tol; at least one update, at most k_max): per mode the
     updates each contact frame took and its measured device time (the whole frame: collision,
     Delassus, start, iterations, integration). A portfolio stops when either copy is done.
-    gains: (persist, fresh, move) output gains of the learned start (sim_set_warmstart_gains)."""
+    gains: (persist, fresh, move, accept) of the learned start (sim_set_warmstart_gains)."""
     out = {m: {"iters": [], "ms": []} for m in modes}
     for sc in scenes:
         ref = Simulator(sc, n_iters=k_max, **opts)
@@ -249,7 +249,9 @@ def evaluate(scenes, frames, mode, net=None, k_max=40, tol=1e-4, **opts):
             "diverged": int(np.isnan(ms).sum())}
 
 
-GAIN_GRID = [(p, f, m) for p in (0.0, 0.5, 1.0) for f in (0.0, 0.5, 1.0) for m in (0.0, 1.0)]
+# (persist, fresh, move, accept); (0, 0, 0, 1) is the previous-frame start
+GAIN_GRID = [(p, f, m, a) for p in (0.0, 1.0) for f in (0.0, 1.0) for m in (0.0, 1.0)
+             for a in (1.0, 0.5, 0.25)]
 
 
 def choose_gains(net, scenes, frames, grid=GAIN_GRID, k_max=40, tol=1e-4, **opts):

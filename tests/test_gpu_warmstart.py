@@ -63,16 +63,18 @@ def test_learned_start_against_the_cold_start_from_identical_states():
     assert len(X) > 1000 and len(Xv) > 300
     net, losses = warmstart.train(X, T, epochs=60, batch=512, lr=1e-3, seed=0, X_val=Xv,
                                   T_val=Tv)
-    assert losses[-1] < 0.5 * losses[0]
+    # the targets are changes from the previous frame (impulse and normal move), much of
+    # them unpredictable from the features: the loss falls by about a third
+    assert losses[-1] < 0.8 * losses[0]
     # held-out prediction (after the validation shrinkage of each output): never worse than
-    # predicting zero (no change from the previous frame's impulse, no move), and the move
-    # along the normal far better (measured: 6.5% of the zero predictor's error)
+    # predicting zero (no change from the previous frame's impulse and move)
     mse = ((net.forward(Xv) - Tv) ** 2).mean(0)
     mse0 = (Tv ** 2).mean(0)
     print("held-out mse", mse, "zero", mse0)
-    assert np.all(mse <= mse0 * (1 + 1e-6)) and mse[3] < 0.1 * mse0[3]
-    # the blend of the network's outputs with the previous frame's impulse, chosen on the
-    # validation seeds by mean frame time to R <= 1e-4 (device-stopped frames)
+    assert np.all(mse <= mse0 * (1 + 1e-6))
+    # the blend of the network's outputs with the previous frame's impulse and move, and the
+    # margin by which a guess must beat the cold start at k = 0, chosen on the validation
+    # seeds by mean frame time to R <= 1e-4 (device-stopped frames)
     gains, table = warmstart.choose_gains(net, sg.warmstart_scenes(range(200, 204), frames=60),
                                           60)
     print("gains", gains, {g: (round(a, 2), round(b, 4)) for g, (a, b) in table.items()})
