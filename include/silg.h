@@ -498,7 +498,7 @@ int sim_set_warmstart(sim_t* sim, const sim_mlp_t* net, int32_t mode);
  * an impulse at the same vertex and obstacle in the previous frame and g = fresh for a new
  * one; the predicted change of the normal move from the previous frame's is scaled by move.
  * 0 leaves that part at the previous frame's value, so 0, 0, 0 is the previous-frame start
- * (mode 2) with the network's cost; 1, 1, 1 (the default) is the network as trained.
+ * (mode 2; the network is then not run); 1, 1, 1 (the default) is the network as trained.
  * accept in (0, 1]: the learned guess is kept when its residual at k = 0 is below accept
  * times the cold start's (1, the default: any improvement). Chosen, for example, on
  * validation frames by time to a residual tolerance. Gains non-negative and finite, accept

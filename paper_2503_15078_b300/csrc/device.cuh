@@ -427,7 +427,7 @@ void launch_integrate(const DevSim& d, cudaStream_t s);
 void launch_ws_features(const DevSim& d, cudaStream_t s);
 void launch_ws_start(const DevSim& d, cudaStream_t s);
 void launch_ws_record(const DevSim& d, cudaStream_t s);
-int ws_kernels(int mode);   // launches of launch_ws_start
+int ws_kernels(const DevSim& d);   // launches of launch_ws_start
 // portfolio: every copy of a group takes the state of the copy with the lowest final
 // residual after a K-iteration frame (one launch)
 // (K < 0: read from d.iter_k)

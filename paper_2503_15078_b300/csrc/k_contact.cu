@@ -1236,6 +1236,11 @@ __device__ __forceinline__ void st_async_v4(unsigned remote_addr, float4 v, unsi
       "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::
           "r"(remote_addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(remote_bar) : "memory");
 }
+__device__ __forceinline__ void st_async_f32(unsigned remote_addr, float v, unsigned remote_bar) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.f32 [%0], %1, [%2];" ::"r"(remote_addr),
+      "f"(v), "r"(remote_bar) : "memory");
+}
 // this CTA's arrival on its barrier for the current phase, expecting `bytes` from the stores
 __device__ __forceinline__ void mbar_expect(unsigned bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.release.cluster.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
@@ -1323,7 +1328,8 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
   }
   // shared layout (identical offsets in every CTA for the parts written remotely):
   //   dots[kCrDotSlots] float4  per-(rank, warp) partial dot products (written by every rank)
-  //   uall[ldw] float4 u for all contact vertices (each rank writes its own range everywhere)
+  //   usx, usy, usz[ldw] float  u for all contact vertices, one array per component (each
+  //                             rank writes its own range everywhere)
   const int ldw = d.sc_ld[scene];
   const float* wblk = d.wt + d.sc_wtoff[scene];  // the scene's W~ block, row-major
   // With contacts between bodies (a contact's map also reaches the corners of a triangle,
@@ -1332,8 +1338,10 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
   //   wall[ldw] float4 (W~ u) of every contact vertex of the scene
   const bool gen = d.bc_on != 0;
   float4* dots = reinterpret_cast<float4*>(sm);          // kCrDotSlots float4
-  float4* uall = dots + kCrDotSlots;                     // ldw float4
-  float4* tall = uall + ldw;                             // c float4 (gen)
+  float* usx = reinterpret_cast<float*>(dots + kCrDotSlots);   // ldw floats each
+  float* usy = usx + ldw;
+  float* usz = usy + ldw;
+  float4* tall = reinterpret_cast<float4*>(usz + ldw);  // c float4 (gen); ldw % 4 == 0
   float4* wall = tall + (gen ? L.c : 0);                 // ldw float4 (gen)
   float4* uloc = wall + (gen ? ldw : 0);                 // nv_max float4 (own slice)
   float* wloc = reinterpret_cast<float*>(uloc + nv_max); // 3 nv
@@ -1411,7 +1419,7 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
       tcl[e] = t >= cvb && t < cvb + L.ncv ? t - cvb : -1;
       twl[e] = t >= 0 ? (float)d.ct_bw[3 * j + e % 3] : 0.f;
     }
-  for (int e = L.ncv + threadIdx.x; e < ldw; e += blockDim.x) uall[e] = make_float4(0, 0, 0, 0);
+  for (int e = L.ncv + threadIdx.x; e < ldw; e += blockDim.x) usx[e] = usy[e] = usz[e] = 0.f;
   __syncthreads();
   const bool w_copy = rows_sm > 0;
   bool w_late = false;
@@ -1477,16 +1485,21 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
   };
   auto apply = [&](const float* v, float* Kv) {
     if (gen) publish_t(v);
-    // this phase brings every contact vertex's u (16 bytes each) from its owner
+    // this phase brings every contact vertex's u (12 bytes each) from its owner
     if (async_x) {
       // the thread that computes an owned vertex's u stores it into every rank (itself
       // included), counted on that rank's barrier
-      if (threadIdx.x == 0) mbar_expect(smem_u32(&xbar[0]), (unsigned)L.ncv * 16u);
-      const unsigned ub = smem_u32(uall + L.cv0), bb = smem_u32(&xbar[0]);
+      if (threadIdx.x == 0) mbar_expect(smem_u32(&xbar[0]), (unsigned)L.ncv * 12u);
+      const unsigned ub = smem_u32(usx + L.cv0), bb = smem_u32(&xbar[0]);
+      const unsigned cstride = 4u * (unsigned)ldw;   // bytes between the component arrays
       for (int cvl = threadIdx.x; cvl < nv; cvl += blockDim.x) {
         const float4 u = vertex_u(v, cvl);
-        for (int r = 0; r < L.R; ++r)
-          st_async_v4(mapa_u32(ub + 16u * (unsigned)cvl, r), u, mapa_u32(bb, r));
+        for (int r = 0; r < L.R; ++r) {
+          const unsigned ra = mapa_u32(ub + 4u * (unsigned)cvl, r), rb = mapa_u32(bb, r);
+          st_async_f32(ra, u.x, rb);
+          st_async_f32(ra + cstride, u.y, rb);
+          st_async_f32(ra + 2u * cstride, u.z, rb);
+        }
       }
       if (!mbar_wait_cluster(smem_u32(&xbar[0]), ph_u & 1u, d.spin_limit) && threadIdx.x == 0)
         atomicOr(d.err, kErrTimeout);
@@ -1497,7 +1510,10 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
       // one 16-byte remote store per (rank, owned vertex), spread over all threads
       for (int e = threadIdx.x; e < L.R * nv; e += blockDim.x) {
         const int r = e / nv, cvl = e - r * nv;
-        cl.map_shared_rank(uall, r)[L.cv0 + cvl] = uloc[cvl];
+        const float4 u = uloc[cvl];
+        cl.map_shared_rank(usx, r)[L.cv0 + cvl] = u.x;
+        cl.map_shared_rank(usy, r)[L.cv0 + cvl] = u.y;
+        cl.map_shared_rank(usz, r)[L.cv0 + cvl] = u.z;
       }
       cl.sync();   // every rank's slice of u is now in every CTA
     }
@@ -1515,12 +1531,12 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
       unsigned long long ux[kCrPairs], uy[kCrPairs], uz[kCrPairs];
 #pragma unroll
       for (int m = 0; m < kCrPairs; ++m) {
+        // the pair (col, col + 1) of each component is one conflict-free 8-byte load
         const int col = 2 * lane + 64 * m;
-        const float4 a = col < ldw ? uall[col] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 b = col < ldw ? uall[col + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
-        ux[m] = f2pack(a.x, b.x);
-        uy[m] = f2pack(a.y, b.y);
-        uz[m] = f2pack(a.z, b.z);
+        const bool in = col < ldw;
+        ux[m] = in ? *reinterpret_cast<const unsigned long long*>(usx + col) : 0ull;
+        uy[m] = in ? *reinterpret_cast<const unsigned long long*>(usy + col) : 0ull;
+        uz[m] = in ? *reinterpret_cast<const unsigned long long*>(usz + col) : 0ull;
       }
       auto rows4 = [&](int r_begin, int r_end, auto row_ptr) {
         for (int row = r_begin + 4 * warp; row < r_end; row += 4 * nw) {
@@ -1570,15 +1586,17 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
       for (int k = 0; k < 4; ++k) wrow[k] = wrow_ptr(min(row0 + k, nv - 1));
 #pragma unroll 2
       for (int g4 = lane; g4 < ng; g4 += 32) {
-        const float4 a = uall[4 * g4], b = uall[4 * g4 + 1], c = uall[4 * g4 + 2],
-                     e = uall[4 * g4 + 3];
+        // the four vertices 4 g4 .. 4 g4 + 3, one component per load
+        const float4 X = reinterpret_cast<const float4*>(usx)[g4],
+                     Y = reinterpret_cast<const float4*>(usy)[g4],
+                     Z = reinterpret_cast<const float4*>(usz)[g4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           if (k < nrow) {
             const float4 w = wrow[k][g4];
-            acc[k][0] += w.x * a.x + w.y * b.x + w.z * c.x + w.w * e.x;
-            acc[k][1] += w.x * a.y + w.y * b.y + w.z * c.y + w.w * e.y;
-            acc[k][2] += w.x * a.z + w.y * b.z + w.z * c.z + w.w * e.z;
+            acc[k][0] += w.x * X.x + w.y * X.y + w.z * X.z + w.w * X.w;
+            acc[k][1] += w.x * Y.x + w.y * Y.y + w.z * Y.z + w.w * Y.w;
+            acc[k][2] += w.x * Z.x + w.y * Z.y + w.z * Z.z + w.w * Z.w;
           }
         }
       }

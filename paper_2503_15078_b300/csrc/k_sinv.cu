@@ -390,8 +390,8 @@ __global__ void k_reduce2(DevSim d) {
 constexpr int kBulkConsumers = kWarps;
 constexpr int kBulkThreads = 32 * (kBulkConsumers + 1);
 constexpr int kBulkMaxStages = 8;
-constexpr int kBulkSmemMax = 227 * 1024;    // dynamic shared memory of one CTA, at most
 constexpr int kSmemPerSm = 228 * 1024;
+int g_bulk_smem_max = 0;   // dynamic shared memory a bulk-copy CTA may take (sinv_setup)
 
 template <class T, bool kPass2> struct BulkLayout {
   static constexpr int kVals = RG * TW * (int)sizeof(T);          // the tile's values
@@ -793,12 +793,23 @@ int sinv_setup() {
   for (const void* f : fns)
     if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, most) != cudaSuccess)
       return SIM_ECUDA;
+  // the bulk-copy forms may take all of a block's shared memory beside their static part
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const void* bulk[] = {(const void*)k_pass1_bulk<float>, (const void*)k_pass1_bulk<unsigned short>,
                         (const void*)k_pass2_bulk<float>, (const void*)k_pass2_bulk<unsigned short>};
+  int dyn_max = optin;
+  for (const void* f : bulk) {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, f) != cudaSuccess) return SIM_ECUDA;
+    dyn_max = std::min(dyn_max, optin - (int)fa.sharedSizeBytes);
+  }
   for (const void* f : bulk)
-    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kBulkSmemMax) !=
+    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max) !=
         cudaSuccess)
       return SIM_ECUDA;
+  g_bulk_smem_max = dyn_max;
   return SIM_OK;
 }
 
@@ -808,7 +819,7 @@ template <class T, bool kPass2>
 int bulk_stages(const DevSim& d, int grid) {
   using L = BulkLayout<T, kPass2>;
   const int per_sm = std::max(1, (grid + d.n_sm - 1) / d.n_sm);
-  const int budget = std::min(kBulkSmemMax, kSmemPerSm / per_sm - 1024 - 256) - L::kRed;
+  const int budget = std::min(g_bulk_smem_max, kSmemPerSm / per_sm - 1024 - 256) - L::kRed;
   const int S = std::min(kBulkMaxStages, budget / L::kStage);
   return S >= 2 ? S : 0;
 }

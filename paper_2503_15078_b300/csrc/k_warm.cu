@@ -96,8 +96,10 @@ __device__ void ws_guess(const DevSim& d, int j) {
     const float* f = d.ws_feat + (size_t)j * kMlpIn;
     const bool persists = d.prev_valid[v] && d.prev_obst[v] == d.ct_obst[j];
     const double g = persists ? d.ws_gain[0] : d.ws_gain[1];
-    for (int r = 0; r < 3; ++r) lam[r] = ((double)f[7 + r] + g * (double)y[r]) * scale;
-    move = d.ws_pmove[j] + (double)d.ws_gain[2] * (double)y[3] * margin;
+    // an output with gain 0 is not read (the network is not run when all gains are 0)
+    for (int r = 0; r < 3; ++r)
+      lam[r] = ((double)f[7 + r] + (g > 0.0 ? g * (double)y[r] : 0.0)) * scale;
+    move = d.ws_pmove[j] + (d.ws_gain[2] > 0.f ? (double)d.ws_gain[2] * (double)y[3] * margin : 0.0);
   } else {
     const float* f = d.ws_feat + (size_t)j * kMlpIn;
     for (int r = 0; r < 3; ++r) lam[r] = (double)f[7 + r] * scale;
@@ -291,11 +293,14 @@ void launch_ws_features(const DevSim& d, cudaStream_t s) {
   k_ws_features<<<(d.cap + 127) / 128, 128, 0, s>>>(d);
 }
 
-int ws_kernels(int mode) { return mode == 0 ? 0 : (mode == 1 ? 2 : 1); }
+int ws_kernels(const DevSim& d) {
+  const bool net = d.ws_mode == 1 && (d.ws_gain[0] > 0.f || d.ws_gain[1] > 0.f || d.ws_gain[2] > 0.f);
+  return d.ws_mode == 0 ? 0 : (net ? 2 : 1);
+}
 
 void launch_ws_start(const DevSim& d, cudaStream_t s) {
   if (d.ws_mode == 0) return;
-  if (d.ws_mode == 1)
+  if (d.ws_mode == 1 && (d.ws_gain[0] > 0.f || d.ws_gain[1] > 0.f || d.ws_gain[2] > 0.f))
     mlp_launch_infer_dev(d.ws_net, d.ws_feat, d.counters + kCntContacts, d.cap, d.ws_out, s);
   k_ws_scene<<<d.n_scenes, kWsThreads, 0, s>>>(d);
 }

@@ -194,7 +194,7 @@ int kernels_per_frame_to_tolerance(const sim_s* s, int K) {
   const int refine_end = s->d.s_bf16 && s->d.refine == 1 && !s->d.jacobi_sweeps ? 6 : 0;
   const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 + bc : 0) + 2;
   const int before = 1 + (s->d.bend_ptr != nullptr) +
-                     (c ? 4 + 16 + 6 * bc + scans + silg::ws_kernels(s->d.ws_mode) : 0) +
+                     (c ? 4 + 16 + 6 * bc + scans + silg::ws_kernels(s->d) : 0) +
                      local_kernels(s) +
                      (c ? 1 : 0);
   const int body = 1 + global + refine_body + 1 + (c ? 1 : 0) + local_kernels(s) + 1;
@@ -210,7 +210,7 @@ int kernels_per_frame(const sim_s* s, int K) {
   const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 + bc : 0) + 2;
   return 1 + (s->d.bend_ptr != nullptr) + (c ? 4 + 16 + 6 * bc + scan_extra(s) : 0) +
          K * (local_kernels(s) + (c ? 1 : 0) + 1 + global) + (c ? 1 : 0) + 1 +
-         5 * refined_iters(s, K) + (c ? silg::ws_kernels(s->d.ws_mode) : 0) +
+         5 * refined_iters(s, K) + (c ? silg::ws_kernels(s->d) : 0) +
          (c && s->d.pf_copies > 1 ? 1 : 0);
 }
 
