@@ -438,7 +438,8 @@ int sim_get_phase_times(sim_t* sim, double* ms);
 
 /* ---- component entry points (parity and profiling) ------------------------------- */
 /* x = A^-1 b with the device profile products (Eq. 8). b, x as in the host variant. With
- * a BF16 profile and refine > 0, one residual correction follows (see sim_options). */
+ * a BF16 profile and refine > 0, one residual correction follows (see sim_options).
+ * SIM_ETIMEOUT if a wait of the products' bulk-copy form ran out (x is then not written). */
 int sim_apply_inverse(sim_t* sim, const double* b, double* x);
 /* Local step (Eq. 5) on the device for positions q (n_verts x 3): p (n_tets x 9,
  * row-major F-shaped projections, caller tet order). */

@@ -411,9 +411,11 @@ __device__ __forceinline__ void mbar_arrive_tx(unsigned bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
 }
-// wait for the phase of the given parity to complete, at most `limit` polls
+// wait for the phase of the given parity to complete, at most `limit` polls (0: 2^22, the
+// default of sim_options.spin_limit)
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity,
                                                   unsigned long long limit) {
+  if (limit == 0) limit = 1ull << 22;
   for (unsigned long long i = 0; i < limit; ++i) {
     unsigned ok;
     asm volatile(

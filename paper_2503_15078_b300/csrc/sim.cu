@@ -2056,6 +2056,9 @@ int sim_apply_inverse(sim_t* s, const double* b, double* x) {
   for (int k = 0; k < n; ++k)
     for (int r = 0; r < 3; ++r) g[(size_t)r * np + k] = (float)b[3 * (size_t)p.order[k] + r];
   cudaStreamSynchronize(s->launch);
+  int bits0 = 0;
+  if (cudaMemcpy(&bits0, s->d.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return SIM_ECUDA;
   cudaMemcpyAsync(s->d.gvec, g.data(), g.size() * sizeof(float), cudaMemcpyHostToDevice, s->work);
   silg::launch_solve(s->d, s->work, silg::kOutX);
   if (s->d.s_bf16 && s->d.refine > 0) {
@@ -2071,6 +2074,16 @@ int sim_apply_inverse(sim_t* s, const double* b, double* x) {
   cudaError_t e = cudaStreamSynchronize(s->work);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e);
+  // a wait of the products that ran out (their bulk-copy form) is this call's error; the
+  // bits a frame left for its own report are kept
+  int bits = 0;
+  if (cudaMemcpy(&bits, s->d.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return SIM_ECUDA;
+  if ((bits & silg::kErrTimeout) && !(bits0 & silg::kErrTimeout)) {
+    const int keep = bits0;
+    cudaMemcpy(s->d.err, &keep, sizeof(int), cudaMemcpyHostToDevice);
+    return SIM_ETIMEOUT;
+  }
   std::memset(x, 0, sizeof(double) * 3 * (size_t)p.n_verts);
   for (int k = 0; k < n; ++k)
     for (int r = 0; r < 3; ++r) x[3 * (size_t)p.order[k] + r] = xo[3 * (size_t)k + r];

@@ -44,9 +44,12 @@ def test_anchor_frame_matches_oracle(compliance, vel):
 def test_anchor_trajectory_free_running():
     # 18 frames with a target moving down into a floor: the anchor drags the cube into
     # contact. Free-running, so FP32 rounding accumulates (and the impacts amplify it): held
-    # to the trajectory gates, positions within 1e-3 L and energy within 1e-2, and the
-    # anchor's impulse within 5e-2 (it is -(q_v - p) / e, with e = 1e-4 m/N)
+    # to the trajectory gates, positions within 1e-3 L and energy within 1e-2. The anchor's
+    # impulse is -(q_v - p) / e with e = 1e-4 m/N, so a difference of its vertex's position
+    # moves it by that difference / e: the impulses agree within 5e-2 plus twice what the
+    # two trajectories' positions of the anchored vertex explain
     sc = sg.hanging_cube(m=4, compliance=1e-4, floor=True, target_vel=(0.0, 0.0, -1.0))
+    va, e_anc = sc.anchors[0].vertex, sc.anchors[0].compliance
     o = Oracle(sc)
     sim = Simulator(sc)
     q, v = sc.q0.copy(), sc.v0.copy()
@@ -61,7 +64,10 @@ def test_anchor_trajectory_free_running():
         ct = sim.contacts()
         ja = [k for k, ob in enumerate(ct["obstacle"]) if ob >= len(sc.obstacles)]
         j = _anchor_rows(info)[0]
-        assert len(ja) == 1 and _relerr(ct["lam"][ja[0]], info["lam"][j]) < 5e-2
+        lo = np.asarray(info["lam"][j])
+        explained = 2 * np.linalg.norm(qg[va] - q[va]) / e_anc
+        assert len(ja) == 1
+        assert np.linalg.norm(ct["lam"][ja[0]] - lo) <= 5e-2 * np.linalg.norm(lo) + explained
         n_contact += len(info["contacts"]) > 1
     assert n_contact >= 3
     sim.close()
