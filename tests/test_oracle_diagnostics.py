@@ -152,3 +152,71 @@ def test_full_factor_is_the_kronecker_product_of_the_per_vertex_factor():
     S3 = sparse_inverse_columns(L3, etree(P3 @ A @ P3.T)) @ P3
     assert np.abs(S3 - np.kron(S, np.eye(3))).max() < 1e-12 * np.abs(S3).max()
     assert np.abs(S3.T @ S3 - np.linalg.inv(A)).max() < 1e-10 * np.abs(np.linalg.inv(A)).max()
+
+
+def test_fb_terms_evaluated_in_fp32_move_on_the_drop_frames():
+    # Why the device evaluates the contact terms (Eqs. 52-57) in FP64: the inputs the oracle
+    # meets on a 6^3 drop (impact, bounce, rest; 40 frames of 5 iterations), evaluated once
+    # more with every operation in float32, move the compliances by far more than the 1e-5
+    # parity gate on a sizeable share of the rows: the difference delta + r lambda - rho
+    # cancels near the complementarity point, and the sticking / outside-cone branches of
+    # E_f flip. (The kernel is latency-bound, so FP32 would not make it faster either.)
+    import oracle.contact as C
+    from oracle import OracleOptions
+    rec_n, rec_f = [], []
+    fb_n, fb_f = C.NCP_TERMS["fb"]
+
+    def nt(dn, ln, rn):
+        rec_n.append((dn, ln, rn))
+        return fb_n(dn, ln, rn)
+
+    def ft(vf, lf, ln, mu, rf, active=None):
+        rec_f.append((np.array(vf, float), np.array(lf, float), ln, mu, rf, active))
+        return fb_f(vf, lf, ln, mu, rf, active)
+
+    C.NCP_TERMS["fb"] = (nt, ft)
+    try:
+        sc = sg.cube_drop(m=6, seed=0)
+        o = Oracle(sc)
+        q, v = sc.q0.copy(), sc.v0.copy()
+        for _ in range(40):
+            q, v, _ = o.frame(q, v, OracleOptions(n_iters=5, n_cr=sc.n_cr))
+    finally:
+        C.NCP_TERMS["fb"] = (fb_n, fb_f)
+    f32 = np.float32
+
+    def rel(a, b):
+        return abs(float(a) - b) / abs(b) if b != 0 else float(a != 0)
+
+    err_n = []
+    for dn, ln, rn in rec_n:
+        _, _, E64 = fb_n(dn, ln, rn)
+        d, l, r = f32(dn), f32(ln), f32(rn)
+        rho = np.sqrt(d * d + r * r * l * l)
+        E32 = (f32(1) - r * l / rho) * r if rho != 0 else f32(0)
+        err_n.append(rel(E32, E64))
+    err_f = []
+    for vf, lf, ln, mu, rf, act in rec_f:
+        if not (act if act is not None else ln > 0) or mu <= 0:
+            continue
+        E64 = fb_f(vf, lf, ln, mu, rf, act)[1]
+        a = np.sqrt((vf.astype(f32) ** 2).sum())
+        lmag = np.sqrt((lf.astype(f32) ** 2).sum())
+        l32, m32, r32 = f32(ln), f32(mu), f32(rf)
+        s = m32 * l32 - lmag
+        root = np.sqrt(a * a + r32 * r32 * s * s)
+        num, den = root - r32 * s, a + m32 * r32 * l32 - root
+        scale = a + m32 * r32 * l32 + r32 * abs(s)
+        if num <= f32(C.TINY_REL) * scale:
+            E32 = f32(0)
+        elif den <= f32(C.TINY_REL) * scale:
+            E32 = (a + r32 * (lmag - m32 * l32)) / (m32 * l32)
+        else:
+            E32 = num / den * r32
+        err_f.append(rel(E32, E64))
+    err_n, err_f = np.array(err_n), np.array(err_f)
+    share_n, share_f = (err_n > 1e-5).mean(), (err_f > 1e-2).mean()
+    print(f"\nFP32 contact terms: E_n {len(err_n)} rows, {share_n:.1%} off by > 1e-5; E_f "
+          f"{len(err_f)} rows, {share_f:.1%} off by > 1e-2")
+    assert len(err_n) > 1000 and len(err_f) > 200
+    assert share_n > 0.05 and share_f > 0.02
