@@ -1268,11 +1268,12 @@ struct CrLayout {
   int R, rank, c, ncv, cv0, cv1, j0, j1;
 };
 
-// Row products of the constraint solves: lane l of a warp owns the column pairs
-// (2l, 2l + 1) + 64 m of the vertex vector in registers; a warp multiplies four rows of W~ at
-// a time with 8-byte loads and packed FP32 FMAs and reduces the twelve row sums over the warp
-// with a butterfly of 16 shuffles.
-constexpr int kCrPairs = 16;     // register-held column pairs per lane: rows up to 1024 wide
+// Row products of the constraint solves: lane l of a warp takes the column pairs
+// (2l, 2l + 1) + 64 m of the vertex vector; a warp multiplies four rows of W~ at a time with
+// 8-byte loads and packed FP32 FMAs and reduces the twelve row sums over the warp with a
+// butterfly of 16 shuffles.
+constexpr int kCrPairs = 16;     // column pairs per lane of the packed row product: rows up to
+                                 // 1024 wide (wider ones take the float4 path)
 constexpr int kCrDotSlots = kCrMaxRanks * (kCrThreads / 32);   // (rank, warp) partials
 
 // Sum each of v[0..11] over the warp; afterwards lanes 2i and 2i + 1 hold the total of v[i]
@@ -1524,20 +1525,12 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
           row < rows_sm ? wrows + (size_t)row * ldw : wblk + (size_t)(L.cv0 + row) * ldw);
     };
     if (ldw <= 64 * kCrPairs) {
-      // lane l owns the column pairs (2l, 2l + 1) + 64 m of u in registers; a warp
-      // multiplies four rows of W~ at a time with 8-byte loads and packed FP32 FMAs
-      // (fma.rn.f32x2: two independent round-to-nearest FMAs), and reduces the twelve row
-      // sums over the warp with a butterfly of 16 shuffles
-      unsigned long long ux[kCrPairs], uy[kCrPairs], uz[kCrPairs];
-#pragma unroll
-      for (int m = 0; m < kCrPairs; ++m) {
-        // the pair (col, col + 1) of each component is one conflict-free 8-byte load
-        const int col = 2 * lane + 64 * m;
-        const bool in = col < ldw;
-        ux[m] = in ? *reinterpret_cast<const unsigned long long*>(usx + col) : 0ull;
-        uy[m] = in ? *reinterpret_cast<const unsigned long long*>(usy + col) : 0ull;
-        uz[m] = in ? *reinterpret_cast<const unsigned long long*>(usz + col) : 0ull;
-      }
+      // lane l takes the column pairs (2l, 2l + 1) + 64 m; a warp multiplies four rows of W~
+      // at a time with 8-byte loads of W~ and of each component of u (one conflict-free load
+      // each) and packed FP32 FMAs (fma.rn.f32x2: two independent round-to-nearest FMAs),
+      // and reduces the twelve row sums over the warp with a butterfly of 16 shuffles. The
+      // loop over the pairs stays rolled (measured faster than the fully unrolled form with
+      // u held in registers: less code per iteration of the solve)
       auto rows4 = [&](int r_begin, int r_end, auto row_ptr) {
         for (int row = r_begin + 4 * warp; row < r_end; row += 4 * nw) {
           const int nr = min(4, r_end - row);
@@ -1547,18 +1540,18 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
           unsigned long long acc[4][3];
 #pragma unroll
           for (int k = 0; k < 4; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0ull;
+#pragma unroll 2
+          for (int col = 2 * lane; col < ldw; col += 64) {
+            const unsigned long long ux = *reinterpret_cast<const unsigned long long*>(usx + col);
+            const unsigned long long uy = *reinterpret_cast<const unsigned long long*>(usy + col);
+            const unsigned long long uz = *reinterpret_cast<const unsigned long long*>(usz + col);
 #pragma unroll
-          for (int m = 0; m < kCrPairs; ++m) {
-            const int col = 2 * lane + 64 * m;
-            if (col < ldw) {
-#pragma unroll
-              for (int k = 0; k < 4; ++k) {
-                const float2 p = *reinterpret_cast<const float2*>(w[k] + col);
-                const unsigned long long pp = f2pack(p.x, p.y);
-                acc[k][0] = ffma2(pp, ux[m], acc[k][0]);
-                acc[k][1] = ffma2(pp, uy[m], acc[k][1]);
-                acc[k][2] = ffma2(pp, uz[m], acc[k][2]);
-              }
+            for (int k = 0; k < 4; ++k) {
+              const float2 p = *reinterpret_cast<const float2*>(w[k] + col);
+              const unsigned long long pp = f2pack(p.x, p.y);
+              acc[k][0] = ffma2(pp, ux, acc[k][0]);
+              acc[k][1] = ffma2(pp, uy, acc[k][1]);
+              acc[k][2] = ffma2(pp, uz, acc[k][2]);
             }
           }
           float v[16];

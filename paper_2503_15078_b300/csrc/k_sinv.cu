@@ -463,15 +463,49 @@ template <> struct BulkRow<float> {
   }
 };
 
+// The producer lane's row of one tile: its run [a, b) in the tile's columns, the offset of
+// the row's column 0, and (pass 2) its y.
+struct BulkRowMeta {
+  int a, b, ct;
+  long long base;
+  float4 y;
+};
+
+template <bool kPass2>
+__device__ __forceinline__ BulkRowMeta bulk_row_meta(const DevSim& d, int2 tl, int lane) {
+  BulkRowMeta m;
+  const int rg = kPass2 ? tl.y : tl.x;
+  m.ct = kPass2 ? tl.x : tl.y;
+  const int r = rg * RG + lane;
+  m.a = m.b = 0;
+  m.base = 0;
+  m.y = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (r < d.n) {
+    const int lo = d.lo[r], hi = d.hi[r];
+    m.a = max(lo, m.ct * TW);
+    m.b = max(m.a, min(hi, m.ct * TW + TW));
+    m.base = d.rowbase[r] - lo;
+    if (kPass2) m.y = make_float4(d.zvec[r], d.zvec[d.n_pad + r], d.zvec[2 * d.n_pad + r], 0.f);
+  }
+  return m;
+}
+
 // The producer warp: fills stage i % S with tile t0 + i once the consumers have released
-// its previous use. Returns the number of tiles issued.
+// its previous use. The loads are software-pipelined: while tile t is issued, the rows of
+// tile t + 1 and the entry of tile t + 2 are already on their way. Returns the number of
+// tiles issued.
 template <class T, bool kPass2>
 __device__ int bulk_produce(const DevSim& d, const int2* tiles, int t0, int t1, char* stages,
                             int S, unsigned full0, unsigned empty0, int lane, bool& dead) {
   using L = BulkLayout<T, kPass2>;
   const T* vals = Fmt<T>::vals(d);
+  const int2 none = make_int2(0, 0);
+  BulkRowMeta cur = bulk_row_meta<kPass2>(d, tiles[t0], lane);
+  int2 tl_next = t0 + 1 < t1 ? tiles[t0 + 1] : none;
   int i = 0;
   for (int t = t0; t < t1; ++t, ++i) {
+    const BulkRowMeta nxt = t + 1 < t1 ? bulk_row_meta<kPass2>(d, tl_next, lane) : cur;
+    const int2 tl_next2 = t + 2 < t1 ? tiles[t + 2] : none;
     const int s = i % S;
     const unsigned full = full0 + 8u * s, empty = empty0 + 8u * s;
     if (i >= S && !dead && !mbar_wait_bounded(empty, (unsigned)((i / S) - 1) & 1u, d.spin_limit)) {
@@ -480,25 +514,10 @@ __device__ int bulk_produce(const DevSim& d, const int2* tiles, int t0, int t1, 
     }
     if (dead) break;
     char* st = stages + (size_t)s * L::kStage;
-    const int2 tl = tiles[t];
-    const int rg = kPass2 ? tl.y : tl.x, ct = kPass2 ? tl.x : tl.y;
-    const int r = rg * RG + lane;
-    int a = 0, b = 0;
-    long long base = 0;
-    if (r < d.n) {
-      const int lo = d.lo[r], hi = d.hi[r];
-      a = max(lo, ct * TW);
-      b = min(hi, ct * TW + TW);
-      if (b < a) b = a;
-      base = d.rowbase[r] - lo;
-    }
-    reinterpret_cast<int2*>(st + L::kVals + L::kSide)[lane] = make_int2(a - ct * TW, b - ct * TW);
-    if (kPass2) {
-      float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (r < d.n) y = make_float4(d.zvec[r], d.zvec[d.n_pad + r], d.zvec[2 * d.n_pad + r], 0.f);
-      reinterpret_cast<float4*>(st + L::kVals)[lane] = y;
-    }
-    unsigned bytes = (unsigned)(b - a) * (unsigned)sizeof(T);
+    const int c0 = cur.ct * TW;
+    reinterpret_cast<int2*>(st + L::kVals + L::kSide)[lane] = make_int2(cur.a - c0, cur.b - c0);
+    if (kPass2) reinterpret_cast<float4*>(st + L::kVals)[lane] = cur.y;
+    const unsigned bytes = (unsigned)(cur.b - cur.a) * (unsigned)sizeof(T);
     unsigned total = bytes;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
@@ -510,12 +529,14 @@ __device__ int bulk_produce(const DevSim& d, const int2* tiles, int t0, int t1, 
     __syncwarp();
     if (lane != 0) mbar_arrive(full);
     if (bytes)
-      bulk_g2s((unsigned)__cvta_generic_to_shared(st + (size_t)(a - ct * TW) * sizeof(T) +
+      bulk_g2s((unsigned)__cvta_generic_to_shared(st + (size_t)(cur.a - c0) * sizeof(T) +
                                                    (size_t)lane * TW * sizeof(T)),
-               vals + base + a, bytes, full);
+               vals + cur.base + cur.a, bytes, full);
     if (!kPass2 && lane < 3)
       bulk_g2s((unsigned)__cvta_generic_to_shared(st + L::kVals + lane * TW * 4),
-               d.gvec + (size_t)lane * d.n_pad + (size_t)ct * TW, TW * 4u, full);
+               d.gvec + (size_t)lane * d.n_pad + (size_t)c0, TW * 4u, full);
+    cur = nxt;
+    tl_next = tl_next2;
   }
   return i;
 }
@@ -574,14 +595,17 @@ __global__ void __launch_bounds__(kBulkThreads, 2) k_pass1_bulk(DevSim d, int S)
     ++slot;
   };
   int i = 0;
+  int key_next = cur;
   for (int t = t0; t < t1; ++t, ++i) {
+    // the next tile's key is loaded one tile ahead
+    const int key = key_next;
+    if (t + 1 < t1) key_next = d.s1_tiles[t + 1].x;
     const int s = i % S;
     if (!dead && !mbar_wait_bounded(full0 + 8u * s, (unsigned)(i / S) & 1u, d.spin_limit)) {
       if (lane == 0) atomicOr(d.err, kErrTimeout);
       dead = true;
     }
     const char* st = bsm + (size_t)s * L::kStage;
-    const int key = d.s1_tiles[t].x;
     if (key != cur) {
       flush();
       cur = key;
@@ -677,14 +701,17 @@ __global__ void __launch_bounds__(kBulkThreads, 2) k_pass2_bulk(DevSim d, int S)
     ++slot;
   };
   int i = 0;
+  int key_next = cur;
   for (int t = t0; t < t1; ++t, ++i) {
+    // the next tile's key is loaded one tile ahead
+    const int key = key_next;
+    if (t + 1 < t1) key_next = d.s2_tiles[t + 1].x;
     const int s = i % S;
     if (!dead && !mbar_wait_bounded(full0 + 8u * s, (unsigned)(i / S) & 1u, d.spin_limit)) {
       if (lane == 0) atomicOr(d.err, kErrTimeout);
       dead = true;
     }
     const char* st = bsm + (size_t)s * L::kStage;
-    const int key = d.s2_tiles[t].x;
     if (key != cur) {
       flush();
       cur = key;
