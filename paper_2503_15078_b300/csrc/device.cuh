@@ -165,6 +165,8 @@ struct DevSim {
                               // vertex and obstacle, at the frame's start (0: none)
   double* ws_shift;           // 6 per scene: the impulse translation and the applied one
   double* ws_res;             // 2 per scene: residual of the guess, of the cold start
+  double* ws_rg;              // cap: the guess's residual at each contact (k = 0)
+  double* ws_rc;              // cap: the cold start's residual at each contact (k = 0)
   float* ws_target;           // cap x 4: the frame's final impulse / scale, normal move / margin
   int* prev_valid;            // n: the vertex had a contact in the previous frame
   int* prev_obst;             // n: its obstacle
@@ -440,7 +442,7 @@ void launch_scan(const int* in, int* out, int n, const int* n_dev, int* total, c
                  int* scratch = nullptr, const int* skip = nullptr);
 int scan_launches(int n);
 int scan_scratch_ints(int n);
-int cr_setup(int n_scenes, int* cluster_out, size_t* smem_out);
+int cr_setup(int n_scenes, int max_cv, int max_ct, int* cluster_out, size_t* smem_out);
 // S~ built on the device in FP64 from the host's factor L~ (k_sbuild.cu)
 struct SinvBuildArgs {
   int nf;

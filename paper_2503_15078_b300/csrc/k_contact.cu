@@ -2199,8 +2199,11 @@ void launch_yu(const DevSim& d, cudaStream_t s) {
 static size_t g_cr_smem = 0;
 
 // Cluster size of the CR kernel: the largest R (16, 8, 4, 2, 1) such that one cluster per
-// scene can be resident at once; R = 1 when not even that fits in one wave.
-int cr_setup(int n_scenes, int* cluster_out, size_t* smem_out) {
+// scene can be resident at once, then halved while a rank's share of the largest scene
+// still fits in three quarters of a CTA's shared memory (its W~ rows for max_cv contact
+// vertices and its contacts' vectors for max_ct contacts): a small scene's solve is then
+// not spread over CTAs that mostly exchange. R = 1 when not even one cluster fits a wave.
+int cr_setup(int n_scenes, int max_cv, int max_ct, int* cluster_out, size_t* smem_out) {
   int dev = 0;
   cudaGetDevice(&dev);
   int optin = 0;
@@ -2233,6 +2236,14 @@ int cr_setup(int n_scenes, int* cluster_out, size_t* smem_out) {
     cudaGetLastError();
   }
   if (!chosen) return SIM_ECUDA;
+  auto fits = [&](int R) {
+    const size_t rows = (size_t)(max_cv + R - 1) / R, ld = (size_t)((max_cv + 3) & ~3);
+    const size_t cts = (size_t)(max_ct + R - 1) / R;
+    // W~ rows, u per component, per-vertex and per-contact vectors, dot slots and slack
+    const size_t bytes = rows * ld * 4 + ld * 12 + rows * 48 + cts * 160 + 8192;
+    return bytes <= smem * 3 / 4;
+  };
+  while (chosen > 1 && fits(chosen / 2)) chosen /= 2;
   g_cr_smem = smem;
   *cluster_out = chosen;
   *smem_out = smem;

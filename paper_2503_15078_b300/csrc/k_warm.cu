@@ -2,7 +2,7 @@
 // q = s~): per contact, the impulse lambda^0 and a move of its vertex along the normal,
 // predicted by the network from per-contact features (impulse and move as changes of the
 // previous frame's) or taken from the previous frame's contact at the same vertex and
-// obstacle; per scene, a translation from the moves (see k_ws_scene). The guess is kept
+// obstacle; per scene, a translation from the moves (see k_ws_shift). The guess is kept
 // only if the residual of its impulses (the frame's residual measure at k = 0, at the
 // position those impulses predict) is below the cold start's; the decision is per scene.
 //
@@ -126,26 +126,39 @@ __device__ __forceinline__ bool ws_accepted(const DevSim& d, int sc, double r_gu
 }
 
 constexpr int kWsThreads = 256;
+constexpr int kWsContactThreads = 32;   // per-contact kernels: their FP64 work spreads over SMs
 
-// The warm start of one scene per CTA, in the order of its steps:
-//  1. the guess of every contact of the scene (ws_guess);
-//  2. two translations, summed in a fixed order. The impulse translation
-//     h^2 sum_j D_j^T lambda_j^0 / M is what the guessed impulses give the scene's free mass
-//     over one step (an impulse guess that holds a resting body up also lifts its predicted
-//     position by the sag of gravity); it judges the impulse guess. The move translation is
-//     the mean over the scene's contact vertices of their guessed move along the normal; the
-//     scene is moved by it, kept within one contact margin of the impulse translation;
-//  3. the residuals at k = 0 of the guess (translated scene, guessed impulses) and of the
-//     cold start (s~, lambda = 0), max over the scene's contacts;
-//  4. if the guess is kept: its impulses, and the translation of the scene's free vertices.
-__global__ void __launch_bounds__(kWsThreads) k_ws_scene(DevSim d) {
+// The warm start of every scene, in the order of its steps:
+//  1. per contact (k_ws_contact): the guess (ws_guess) and the residual of the cold start
+//     (s~, lambda = 0) at that contact;
+//  2. per scene (k_ws_shift): two translations, summed in a fixed order. The impulse
+//     translation h^2 sum_j D_j^T lambda_j^0 / M is what the guessed impulses give the
+//     scene's free mass over one step (an impulse guess that holds a resting body up also
+//     lifts its predicted position by the sag of gravity); it judges the impulse guess. The
+//     move translation is the mean over the scene's contact vertices of their guessed move
+//     along the normal; the scene is moved by it, kept within one contact margin of the
+//     impulse translation;
+//  3. per contact (k_ws_resid): the residual of the guess (translated scene, guessed
+//     impulses) at that contact;
+//  4. per scene (k_ws_apply): the residuals at k = 0 of the guess and of the cold start, max
+//     over the scene's contacts; if the guess is kept, its impulses and the translation of
+//     the scene's free vertices.
+__global__ void k_ws_contact(DevSim d) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = min(d.counters[kCntContacts], d.cap);
+  if (j >= c) return;
+  ws_guess(d, j);
+  const int sc = d.vert_scene[d.ct_vert[j]];
+  const double zero[3] = {0.0, 0.0, 0.0};
+  double q0[3];
+  contact_q(d, j, nullptr, q0);
+  d.ws_rc[j] = fb_terms(d, j, q0, zero, d.scene_Lref[sc]).res;
+}
+
+__global__ void __launch_bounds__(kWsThreads) k_ws_shift(DevSim d) {
   const int sc = blockIdx.x;
   const int jb = d.sc_jb[sc], je = d.sc_jb[sc + 1];
   __shared__ double part[6][kWsThreads];
-  __shared__ double shift[6];
-  __shared__ int keep;
-  for (int j = jb + threadIdx.x; j < je; j += blockDim.x) ws_guess(d, j);
-  __syncthreads();
   double t[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   for (int j = jb + threadIdx.x; j < je; j += blockDim.x) {
     if (d.ct_obst[j] < 0) continue;   // contacts between bodies are internal forces
@@ -173,22 +186,32 @@ __global__ void __launch_bounds__(kWsThreads) k_ws_scene(DevSim d) {
     dn = sqrt(dn);
     const double lim = d.scene_margin[sc], f = dn > lim ? lim / dn : 1.0;
     for (int r = 0; r < 3; ++r) {
-      shift[r] = imp[r];                 // judges the impulses
-      shift[3 + r] = imp[r] + f * dev[r];  // applied
+      d.ws_shift[6 * sc + r] = imp[r];                  // judges the impulses
+      d.ws_shift[6 * sc + 3 + r] = imp[r] + f * dev[r];  // applied
     }
-    for (int r = 0; r < 6; ++r) d.ws_shift[6 * sc + r] = shift[r];
   }
-  __syncthreads();
+}
+
+__global__ void k_ws_resid(DevSim d) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = min(d.counters[kCntContacts], d.cap);
+  if (j >= c) return;
+  const int sc = d.vert_scene[d.ct_vert[j]];
+  double q[3], lam[3];
+  contact_q(d, j, d.ws_shift + 6 * sc, q);
+  for (int r = 0; r < 3; ++r) lam[r] = d.ws_lam0[3 * j + r];
+  d.ws_rg[j] = fb_terms(d, j, q, lam, d.scene_Lref[sc]).res;
+}
+
+__global__ void __launch_bounds__(kWsThreads) k_ws_apply(DevSim d) {
+  const int sc = blockIdx.x;
+  const int jb = d.sc_jb[sc], je = d.sc_jb[sc + 1];
+  __shared__ double part[2][kWsThreads];
+  __shared__ int keep;
   double rg = 0.0, rc = 0.0;
-  const double L = d.scene_Lref[sc];
-  const double zero[3] = {0.0, 0.0, 0.0};
   for (int j = jb + threadIdx.x; j < je; j += blockDim.x) {
-    double q[3], q0[3], lam[3];
-    contact_q(d, j, nullptr, q0);
-    contact_q(d, j, shift, q);
-    for (int r = 0; r < 3; ++r) lam[r] = d.ws_lam0[3 * j + r];
-    rg = fmax(rg, fb_terms(d, j, q, lam, L).res);
-    rc = fmax(rc, fb_terms(d, j, q0, zero, L).res);
+    rg = fmax(rg, d.ws_rg[j]);
+    rc = fmax(rc, d.ws_rc[j]);
   }
   part[0][threadIdx.x] = rg;
   part[1][threadIdx.x] = rc;
@@ -209,6 +232,7 @@ __global__ void __launch_bounds__(kWsThreads) k_ws_scene(DevSim d) {
   if (!keep) return;
   for (int j = jb + threadIdx.x; j < je; j += blockDim.x)
     for (int r = 0; r < 3; ++r) d.ct_lam[3 * j + r] = d.ws_lam0[3 * j + r];
+  const double* shift = d.ws_shift + 6 * sc;
   const float s0 = (float)shift[3], s1 = (float)shift[4], s2 = (float)shift[5];
   for (int v = d.scene_vfirst[sc] + threadIdx.x; v < d.scene_vfirst[sc + 1]; v += blockDim.x) {
     d.dq[3 * v] += s0;
@@ -290,19 +314,24 @@ void launch_pf_sync(const DevSim& d, cudaStream_t s, int K) {
 }
 
 void launch_ws_features(const DevSim& d, cudaStream_t s) {
-  k_ws_features<<<(d.cap + 127) / 128, 128, 0, s>>>(d);
+  // FP64 per contact: small CTAs spread it over the SMs
+  k_ws_features<<<(d.cap + kWsContactThreads - 1) / kWsContactThreads, kWsContactThreads, 0, s>>>(d);
 }
 
 int ws_kernels(const DevSim& d) {
   const bool net = d.ws_mode == 1 && (d.ws_gain[0] > 0.f || d.ws_gain[1] > 0.f || d.ws_gain[2] > 0.f);
-  return d.ws_mode == 0 ? 0 : (net ? 2 : 1);
+  return d.ws_mode == 0 ? 0 : (net ? 5 : 4);
 }
 
 void launch_ws_start(const DevSim& d, cudaStream_t s) {
   if (d.ws_mode == 0) return;
   if (d.ws_mode == 1 && (d.ws_gain[0] > 0.f || d.ws_gain[1] > 0.f || d.ws_gain[2] > 0.f))
     mlp_launch_infer_dev(d.ws_net, d.ws_feat, d.counters + kCntContacts, d.cap, d.ws_out, s);
-  k_ws_scene<<<d.n_scenes, kWsThreads, 0, s>>>(d);
+  const int gc = (d.cap + kWsContactThreads - 1) / kWsContactThreads;
+  k_ws_contact<<<gc, kWsContactThreads, 0, s>>>(d);
+  k_ws_shift<<<d.n_scenes, kWsThreads, 0, s>>>(d);
+  k_ws_resid<<<gc, kWsContactThreads, 0, s>>>(d);
+  k_ws_apply<<<d.n_scenes, kWsThreads, 0, s>>>(d);
 }
 
 void launch_ws_record(const DevSim& d, cudaStream_t s) {

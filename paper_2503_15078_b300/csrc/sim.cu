@@ -47,6 +47,7 @@ struct sim_s {
   cudaStream_t launch = nullptr;  // where frames run (caller stream or work)
   int cluster = 1;
   size_t cr_smem = 0;
+  int cr_vmax = 1, cr_cmax = 1;   // bounds of one scene's contact vertices and contacts
   int n_iters_default = 5;
   bool has_obstacles = false;
   std::map<int, Graph> graphs;
@@ -1079,6 +1080,14 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
     vmax = std::max(vmax, p.scene_vfirst[sc + 1] - p.scene_vfirst[sc]);
   const int V = std::min(cap, vmax);
   d.wt = s->alloc<float>((size_t)cap * ((V + 3) & ~3));
+  // contacts of one scene: at most one per vertex and obstacle, anchor and other body
+  std::vector<int> obs_per_scene(p.n_scenes, 0);
+  for (int o : sd.obstacle_scene)
+    if (o >= 0 && o < p.n_scenes) ++obs_per_scene[o];
+  const int omax = obs_per_scene.empty() ? 0
+                                         : *std::max_element(obs_per_scene.begin(), obs_per_scene.end());
+  s->cr_vmax = V;
+  s->cr_cmax = (int)std::min<long long>(cap, (long long)V * (omax + 2));
   d.resid = s->alloc<double>(silg::kMaxIters + 1);
   d.max_pen = s->alloc<double>(1);
   d.iter_k = s->alloc<int>(1);
@@ -1137,6 +1146,8 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   d.ws_move = s->alloc<double>(cap);
   d.ws_shift = s->alloc<double>(6 * (size_t)p.n_scenes);
   d.ws_res = s->alloc<double>(2 * (size_t)p.n_scenes);
+  d.ws_rg = s->alloc<double>(cap);
+  d.ws_rc = s->alloc<double>(cap);
   d.ws_target = s->alloc<float>(4 * (size_t)cap);
   d.prev_valid = s->alloc<int>(n);
   d.prev_obst = s->alloc<int>(n);
@@ -1144,7 +1155,7 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   d.prev_move = s->alloc<double>(n);
   if (silg::mlp_setup() != 0) return SIM_ECUDA;
   if (s->has_obstacles) {
-    int st = silg::cr_setup(p.n_scenes, &s->cluster, &s->cr_smem);
+    int st = silg::cr_setup(p.n_scenes, s->cr_vmax, s->cr_cmax, &s->cluster, &s->cr_smem);
     if (st != SIM_OK) return st;
   }
   d.cr_R = s->cluster;
