@@ -78,8 +78,7 @@ constexpr int kErrTimeout = 4;
 constexpr int kErrYCapacity = 8;
 
 // counters[]: per-frame sizes decided on the device
-enum { kCntContacts = 0, kCntCv = 1, kCntU = 2, kCntY = 3, kCntYC = 4, kCntYtzItems = 5,
-       kCntYuItems = 6, kNumCounters = 8 };
+enum { kCntContacts = 0, kCntCv = 1, kCntU = 2, kCntY = 3, kCntYC = 4, kNumCounters = 8 };
 
 struct ObstDev {
   int kind;
@@ -251,21 +250,8 @@ struct DevSim {
   int dl_reuse_on;
   int* dl_state;
   int* dl_prev_cv;  // cap: the previous frame's contact vertices
-  // Y^T z and Y u in chunks of 256 path entries (k_ytz_chunk, k_yu_chunk): chunks per
-  // contact vertex (ytz_cnt) and per row of U (yu_cnt), their exclusive prefix sums, the
-  // flattened (vertex or row, chunk) work items, one partial sum per item, and completion
-  // counters per vertex (row), zero between launches. Built with Y, kept when Y is reused.
-  int* ytz_cnt;     // cap
-  int* ytz_off;     // cap + 1
-  int2* ytz_item;   // ytz_items_cap
-  float4* ytz_part; // ytz_items_cap
-  int* ytz_done;    // cap
-  int* yu_cnt;      // n
-  int* yu_off;      // n + 1
-  int2* yu_item;    // yu_items_cap
-  float4* yu_part;  // yu_items_cap
-  int* yu_done;     // n
-  int ytz_items_cap, yu_items_cap;
+  int ytz_warp;     // Y^T z with a warp per contact vertex (short ancestor paths) instead
+                    // of a CTA per contact vertex
   const float* zero;  // kTileW zeros: the load target of lanes outside a row's range
   float* p1_part;   // [n_seg1][3][kRowGroup]
   float* p2_part;   // [n_seg2][3][kTileW]

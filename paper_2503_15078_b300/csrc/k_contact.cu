@@ -605,8 +605,6 @@ __global__ void __launch_bounds__(1024) k_dl_check(DevSim d) {
   }
 }
 
-constexpr int kYChunk = 256;   // path entries per chunk of Y^T z and Y u
-
 // rows of U: a is an ancestor of some contact vertex iff its subtree [fd(a), a] holds one
 __global__ void k_u_flag(DevSim d) {
   if (*d.dl_state) return;   // Y and W~ kept from the previous frame
@@ -628,7 +626,6 @@ __global__ void k_u_compact(DevSim d) {
   d.u_list[idx] = a;
   d.u_clo[idx] = d.row_clo[a];
   d.u_len[idx] = d.row_len[a];
-  d.yu_cnt[idx] = max(1, (d.row_len[a] + kYChunk - 1) / kYChunk);
 }
 
 __global__ void k_yc_len(DevSim d) {
@@ -636,22 +633,7 @@ __global__ void k_yc_len(DevSim d) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   int ncv = min(d.counters[kCntCv], d.cap);
   if (c >= ncv) return;
-  const int len = d.depth[d.cv_vert[c]];
-  d.yc_len[c] = len;
-  d.ytz_cnt[c] = max(1, (len + kYChunk - 1) / kYChunk);
-}
-
-// the flattened chunk items of Y^T z (contact vertex, chunk) and of Y u (row of U, chunk)
-__global__ void k_y_items(DevSim d) {
-  if (*d.dl_state) return;   // Y and W~ kept from the previous frame
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int ncv = min(d.counters[kCntCv], d.cap), nU = d.counters[kCntU];
-  if (i < ncv)
-    for (int h = 0, o = d.ytz_off[i]; h < d.ytz_cnt[i] && o + h < d.ytz_items_cap; ++h)
-      d.ytz_item[o + h] = make_int2(i, h);
-  if (i < nU)
-    for (int h = 0, o = d.yu_off[i]; h < d.yu_cnt[i] && o + h < d.yu_items_cap; ++h)
-      d.yu_item[o + h] = make_int2(i, h);
+  d.yc_len[c] = d.depth[d.cv_vert[c]];
 }
 
 // Y rows (row-major over U) and Y columns (contact vertex major, bottom-up along the
@@ -1035,51 +1017,24 @@ __global__ void k_contact_eval(DevSim d, int k, int final_eval) {
   }
 }
 
-// Y^T z and Y u in chunks of kYChunk path entries, one warp per (vertex or row, chunk) item
-// of the flattened lists built with Y (k_y_items), so that every contact vertex's long
-// ancestor path (and every long row of U) is spread over many warps and no warp visits an
-// empty item. A chunk's partial sums go to the item's scratch slot; the warp that completes
-// the last chunk of a vertex (row) -- counted with an atomic, which that warp resets for the
-// next launch -- adds the partials in chunk order (deterministic) and finishes the vertex
-// (row).
-
-// the Schur right-hand side h^-2 (h - J A^-1 g) of the contacts at contact vertex c, from
-// s = (Y^T z)_c (their own contacts; a contact with another body in k_body_rhs)
-__device__ __forceinline__ void ytz_finish(const DevSim& d, int c, float s0, float s1, float s2,
-                                           int lane) {
-  const double ih2 = 1.0 / (d.h * d.h);
-  if (d.bc_on && lane == 0) {
-    d.svec[3 * c] = s0;
-    d.svec[3 * c + 1] = s1;
-    d.svec[3 * c + 2] = s2;
-  }
-  const int j0 = d.cv_first[c], j1 = min(j0 + d.cv_nct[c], d.cap);
-  for (int j = j0 + lane; j < j1; j += 32) {
-    if (d.bc_on && d.ct_tri[j] >= 0) continue;   // k_body_rhs
-    for (int r = 0; r < 3; ++r) {
-      const float* Dr = d.ct_Df + 9 * j + 3 * r;
-      const float jag = d.ct_omega[3 * j + r] * (Dr[0] * s0 + Dr[1] * s1 + Dr[2] * s2);
-      d.ct_rhs[3 * j + r] = (float)((d.ct_hv[3 * j + r] - (double)jag) * ih2);
-    }
-  }
-}
-
-__global__ void k_ytz_chunk(DevSim d) {
+// (Y^T z) per contact vertex, then the Schur right-hand side h^-2 (h - J A^-1 g) per
+// contact. One 128-thread CTA per contact vertex strides along its ancestor path and the
+// partial sums are combined in a fixed order.
+constexpr int kYtzThreads = 128;
+__global__ void __launch_bounds__(kYtzThreads) k_ytz(DevSim d) {
   pdl_wait();
   const int ncv = min(d.counters[kCntCv], d.cap);
   if (d.yc_ptr[ncv] > d.cap_y) return;   // uniform over the grid
-  const int lane = threadIdx.x & 31;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int n_items = min(d.counters[kCntYtzItems], d.ytz_items_cap);
-  for (int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < n_items; item += nwarps) {
-    const int2 ch = d.ytz_item[item];
-    const int c = ch.x, h = ch.y;
-    const int k0 = d.yc_ptr[c], len = d.yc_ptr[c + 1] - k0;
-    const int n_c = max(1, (len + kYChunk - 1) / kYChunk);
+  __shared__ float part[3][kYtzThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const double ih2 = 1.0 / (d.h * d.h);
+  // CTAs walk the contact vertices with a grid stride (the grid is sized for the SMs, not
+  // for the capacity); every thread of a CTA runs the same iterations
+  for (int c = blockIdx.x; c < ncv; c += gridDim.x) {
     float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-    const int kb = k0 + h * kYChunk, ke = min(k0 + len, kb + kYChunk);
+    const int k1 = d.yc_ptr[c + 1];
 #pragma unroll 4
-    for (int k = kb + lane; k < ke; k += 32) {
+    for (int k = d.yc_ptr[c] + threadIdx.x; k < k1; k += kYtzThreads) {
       const float y = d.yc_val[k];
       const int a = d.yc_row[k];
       s0 += y * d.zvec[a];
@@ -1089,82 +1044,74 @@ __global__ void k_ytz_chunk(DevSim d) {
     s0 = warp_sum(s0);
     s1 = warp_sum(s1);
     s2 = warp_sum(s2);
-    if (n_c == 1) {            // a short path: one chunk, finished here
-      ytz_finish(d, c, s0, s1, s2, lane);
-      continue;
-    }
-    int last = 0;
     if (lane == 0) {
-      d.ytz_part[item] = make_float4(s0, s1, s2, 0.f);
-      __threadfence();
-      last = atomicAdd(d.ytz_done + c, 1) == n_c - 1;
+      part[0][wid] = s0;
+      part[1][wid] = s1;
+      part[2][wid] = s2;
     }
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (!last) continue;
-    __threadfence();
-    s0 = s1 = s2 = 0.f;
-    for (int q = 0; q < n_c; ++q) {    // every lane, in chunk order
-      const float4 t = __ldcg(d.ytz_part + (item - h) + q);
-      s0 += t.x;
-      s1 += t.y;
-      s2 += t.z;
+    __syncthreads();
+    if (wid == 0) {
+      s0 = s1 = s2 = 0.f;
+      for (int w = 0; w < kYtzThreads / 32; ++w) {
+        s0 += part[0][w];
+        s1 += part[1][w];
+        s2 += part[2][w];
+      }
+      if (d.bc_on && lane == 0) {
+        d.svec[3 * c] = s0;
+        d.svec[3 * c + 1] = s1;
+        d.svec[3 * c + 2] = s2;
+      }
+      const int j0 = d.cv_first[c], j1 = min(j0 + d.cv_nct[c], d.cap);
+      for (int j = j0 + lane; j < j1; j += 32) {
+        if (d.bc_on && d.ct_tri[j] >= 0) continue;   // k_body_rhs
+        for (int r = 0; r < 3; ++r) {
+          const float* Dr = d.ct_Df + 9 * j + 3 * r;
+          const float jag = d.ct_omega[3 * j + r] * (Dr[0] * s0 + Dr[1] * s1 + Dr[2] * s2);
+          d.ct_rhs[3 * j + r] = (float)((d.ct_hv[3 * j + r] - (double)jag) * ih2);
+        }
+      }
     }
-    if (lane == 0) d.ytz_done[c] = 0;
-    ytz_finish(d, c, s0, s1, s2, lane);
+    __syncthreads();   // part[] is reused by the next contact vertex
   }
 }
 
-// y = z + h^2 Y u on the rows of U, in chunks of each row's contact-vertex interval
-__global__ void k_yu_chunk(DevSim d) {
+// The same with one warp per contact vertex (no block barriers; more vertices in flight),
+// for meshes whose ancestor paths are short (many small scenes).
+__global__ void k_ytz_warp(DevSim d) {
   pdl_wait();
-  const int lane = threadIdx.x & 31, nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int nU = d.counters[kCntU];
-  if (d.y_ptr[nU] > d.cap_y) return;
-  const float h2 = (float)(d.h * d.h);
-  const int n_items = min(d.counters[kCntYuItems], d.yu_items_cap);
-  for (int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < n_items; item += nwarps) {
-    const int2 ch = d.yu_item[item];
-    const int idx = ch.x, h = ch.y;
-    const int len = d.u_len[idx];
-    const int n_c = max(1, (len + kYChunk - 1) / kYChunk);
-    const int clo = d.u_clo[idx], base = d.y_ptr[idx];
-    const int kb = h * kYChunk, ke = min(len, kb + kYChunk);
-    float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+  const int ncv = min(d.counters[kCntCv], d.cap);
+  if (d.yc_ptr[ncv] > d.cap_y) return;   // uniform over the grid
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const double ih2 = 1.0 / (d.h * d.h);
+  for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < ncv; c += nwarps) {
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    const int k1 = d.yc_ptr[c + 1];
 #pragma unroll 4
-    for (int k = kb + lane; k < ke; k += 32) {
-      const float y = d.y_val[base + k];
-      const float* u = d.uvec + 3 * (clo + k);
-      t0 += y * u[0];
-      t1 += y * u[1];
-      t2 += y * u[2];
+    for (int k = d.yc_ptr[c] + lane; k < k1; k += 32) {
+      const float y = d.yc_val[k];
+      const int a = d.yc_row[k];
+      s0 += y * d.zvec[a];
+      s1 += y * d.zvec[d.n_pad + a];
+      s2 += y * d.zvec[2 * d.n_pad + a];
     }
-    t0 = warp_sum(t0);
-    t1 = warp_sum(t1);
-    t2 = warp_sum(t2);
-    if (n_c > 1) {
-      int last = 0;
-      if (lane == 0) {
-        d.yu_part[item] = make_float4(t0, t1, t2, 0.f);
-        __threadfence();
-        last = atomicAdd(d.yu_done + idx, 1) == n_c - 1;
-      }
-      last = __shfl_sync(0xffffffffu, last, 0);
-      if (!last) continue;
-      __threadfence();
-      t0 = t1 = t2 = 0.f;
-      for (int q = 0; q < n_c; ++q) {
-        const float4 t = __ldcg(d.yu_part + (item - h) + q);
-        t0 += t.x;
-        t1 += t.y;
-        t2 += t.z;
-      }
-      if (lane == 0) d.yu_done[idx] = 0;
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if (d.bc_on && lane == 0) {
+      d.svec[3 * c] = s0;
+      d.svec[3 * c + 1] = s1;
+      d.svec[3 * c + 2] = s2;
     }
-    if (lane == 0) {
-      const int a = d.u_list[idx];
-      d.zvec[a] += h2 * t0;
-      d.zvec[d.n_pad + a] += h2 * t1;
-      d.zvec[2 * d.n_pad + a] += h2 * t2;
+    const int j0 = d.cv_first[c], j1 = min(j0 + d.cv_nct[c], d.cap);
+    for (int j = j0 + lane; j < j1; j += 32) {
+      if (d.bc_on && d.ct_tri[j] >= 0) continue;   // k_body_rhs
+      for (int r = 0; r < 3; ++r) {
+        const float* Dr = d.ct_Df + 9 * j + 3 * r;
+        const float jag = d.ct_omega[3 * j + r] * (Dr[0] * s0 + Dr[1] * s1 + Dr[2] * s2);
+        d.ct_rhs[3 * j + r] = (float)((d.ct_hv[3 * j + r] - (double)jag) * ih2);
+      }
     }
   }
 }
@@ -1191,6 +1138,37 @@ __global__ void k_body_rhs(DevSim d) {
     const float* Dr = d.ct_Df + 9 * j + 3 * r;
     const float jag = d.ct_omega[3 * j + r] * (Dr[0] * s[0] + Dr[1] * s[1] + Dr[2] * s[2]);
     d.ct_rhs[3 * j + r] = (float)((d.ct_hv[3 * j + r] - (double)jag) * ih2);
+  }
+}
+
+// y = z + h^2 Y u, in place on z (rows of U only)
+__global__ void k_yu(DevSim d) {
+  pdl_wait();
+  const int lane = threadIdx.x & 31, nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int nU = d.counters[kCntU];
+  if (d.y_ptr[nU] > d.cap_y) return;
+  const float h2 = (float)(d.h * d.h);
+  // warps walk the rows of U with a grid stride (the grid is sized for the SMs)
+  for (int idx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; idx < nU; idx += nwarps) {
+    const int clo = d.u_clo[idx], len = d.u_len[idx], base = d.y_ptr[idx];
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+#pragma unroll 4
+    for (int k = lane; k < len; k += 32) {
+      const float y = d.y_val[base + k];
+      const float* u = d.uvec + 3 * (clo + k);
+      t0 += y * u[0];
+      t1 += y * u[1];
+      t2 += y * u[2];
+    }
+    t0 = warp_sum(t0);
+    t1 = warp_sum(t1);
+    t2 = warp_sum(t2);
+    if (lane == 0) {
+      const int a = d.u_list[idx];
+      d.zvec[a] += h2 * t0;
+      d.zvec[d.n_pad + a] += h2 * t1;
+      d.zvec[2 * d.n_pad + a] += h2 * t2;
+    }
   }
 }
 
@@ -1488,19 +1466,26 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
     if (gen) publish_t(v);
     // this phase brings every contact vertex's u (12 bytes each) from its owner
     if (async_x) {
-      // the thread that computes an owned vertex's u stores it into every rank (itself
-      // included), counted on that rank's barrier
+      // the owned vertices' u per component in uloc, then one 4-byte store per (rank,
+      // component, owned vertex) into every rank (itself included), spread over all threads
+      // and counted on that rank's barrier
       if (threadIdx.x == 0) mbar_expect(smem_u32(&xbar[0]), (unsigned)L.ncv * 12u);
-      const unsigned ub = smem_u32(usx + L.cv0), bb = smem_u32(&xbar[0]);
-      const unsigned cstride = 4u * (unsigned)ldw;   // bytes between the component arrays
+      float* ul = reinterpret_cast<float*>(uloc);   // [3][nv_max]
       for (int cvl = threadIdx.x; cvl < nv; cvl += blockDim.x) {
         const float4 u = vertex_u(v, cvl);
-        for (int r = 0; r < L.R; ++r) {
-          const unsigned ra = mapa_u32(ub + 4u * (unsigned)cvl, r), rb = mapa_u32(bb, r);
-          st_async_f32(ra, u.x, rb);
-          st_async_f32(ra + cstride, u.y, rb);
-          st_async_f32(ra + 2u * cstride, u.z, rb);
-        }
+        ul[cvl] = u.x;
+        ul[nv_max + cvl] = u.y;
+        ul[2 * nv_max + cvl] = u.z;
+      }
+      __syncthreads();
+      const unsigned ub = smem_u32(usx + L.cv0), bb = smem_u32(&xbar[0]);
+      const unsigned cstride = 4u * (unsigned)ldw;   // bytes between the component arrays
+      const int per_rank = 3 * nv;
+      for (int e = threadIdx.x; e < L.R * per_rank; e += blockDim.x) {
+        const int r = e / per_rank, rem = e - r * per_rank, comp = rem / max(nv, 1),
+                  cvl = rem - comp * nv;
+        st_async_f32(mapa_u32(ub + (unsigned)comp * cstride + 4u * (unsigned)cvl, r),
+                     ul[comp * nv_max + cvl], mapa_u32(bb, r));
       }
       if (!mbar_wait_cluster(smem_u32(&xbar[0]), ph_u & 1u, d.spin_limit) && threadIdx.x == 0)
         atomicOr(d.err, kErrTimeout);
@@ -2126,11 +2111,6 @@ void launch_delassus(const DevSim& d, cudaStream_t s) {
   k_yc_len<<<(d.cap + 255) / 256, 256, 0, s>>>(d);
   launch_scan(d.yc_len, d.yc_ptr, d.cap, d.counters + kCntCv, d.counters + kCntYC, s, d.scan_part,
               skip);
-  launch_scan(d.ytz_cnt, d.ytz_off, d.cap, d.counters + kCntCv, d.counters + kCntYtzItems, s,
-              d.scan_part, skip);
-  launch_scan(d.yu_cnt, d.yu_off, d.n, d.counters + kCntU, d.counters + kCntYuItems, s,
-              d.scan_part, skip);
-  k_y_items<<<(std::max(d.n, d.cap) + 255) / 256, 256, 0, s>>>(d);
   k_y_gather<<<std::min((d.n * 32 + 255) / 256, 8 * d.n_sm), 256, 0, s>>>(d);
   k_scene_ranges<<<1, 256, 0, s>>>(d);
   k_wt_blocks<<<(d.n / kWtKB + 1 + 127) / 128, 128, 0, s>>>(d);
@@ -2188,12 +2168,15 @@ void launch_iter_decide(const DevSim& d, cudaStream_t s, cudaGraphConditionalHan
 void launch_iter_clear(const DevSim& d, cudaStream_t s) { k_iter_clear<<<1, 256, 0, s>>>(d); }
 
 void launch_ytz(const DevSim& d, cudaStream_t s) {
-  launch_k(d.pdl, k_ytz_chunk, std::min((d.ytz_items_cap + 7) / 8, 8 * d.n_sm), 256, 0, s, d);
+  if (d.ytz_warp)
+    launch_k(d.pdl, k_ytz_warp, std::min((d.cap + 7) / 8, 8 * d.n_sm), 256, 0, s, d);
+  else
+    launch_k(d.pdl, k_ytz, std::min(d.cap, 8 * d.n_sm), kYtzThreads, 0, s, d);
   if (d.bc_on) launch_k(d.pdl, k_body_rhs, (d.cap + 127) / 128, 128, 0, s, d);
 }
 
 void launch_yu(const DevSim& d, cudaStream_t s) {
-  launch_k(d.pdl, k_yu_chunk, std::min((d.yu_items_cap + 7) / 8, 8 * d.n_sm), 256, 0, s, d);
+  launch_k(d.pdl, k_yu, std::min((d.n * 32 + 255) / 256, 8 * d.n_sm), 256, 0, s, d);
 }
 
 static size_t g_cr_smem = 0;

@@ -174,12 +174,12 @@ int frame_iters(sim_s* s) {
 }
 
 // the extra launches of the two-pass scans of a frame with contacts: the n-length scans
-// (contacts, contact vertices, corner terms with body contact, U flags, Y row lengths, Y u
-// chunk counts) and the capacity-length ones (Y column lengths, Y^T z chunk counts)
+// (contacts, contact vertices, corner terms with body contact, U flags, Y row lengths) and
+// the capacity-length one (Y column lengths)
 int scan_extra(const sim_s* s) {
   const int n = s->d.n, cap = s->d.cap;
-  return (3 + (s->d.bc_on ? 1 : 0) + 2) * (silg::scan_launches(n) - 1) +
-         2 * (silg::scan_launches(cap) - 1);
+  return (3 + (s->d.bc_on ? 1 : 0) + 1) * (silg::scan_launches(n) - 1) +
+         (silg::scan_launches(cap) - 1);
 }
 
 // local-step launches per iteration (tetrahedra, triangles) and per-frame extras (bending)
@@ -195,7 +195,7 @@ int kernels_per_frame_to_tolerance(const sim_s* s, int K) {
   const int refine_end = s->d.s_bf16 && s->d.refine == 1 && !s->d.jacobi_sweeps ? 6 : 0;
   const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 + bc : 0) + 2;
   const int before = 1 + (s->d.bend_ptr != nullptr) +
-                     (c ? 4 + 16 + 6 * bc + scans + silg::ws_kernels(s->d) : 0) +
+                     (c ? 4 + 13 + 6 * bc + scans + silg::ws_kernels(s->d) : 0) +
                      local_kernels(s) +
                      (c ? 1 : 0);
   const int body = 1 + global + refine_body + 1 + (c ? 1 : 0) + local_kernels(s) + 1;
@@ -209,7 +209,7 @@ int kernels_per_frame(const sim_s* s, int K) {
   // pass 2 + reduction; a residual correction adds the residual and both passes
   const int bc = s->d.bc_on ? 1 : 0;
   const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 + bc : 0) + 2;
-  return 1 + (s->d.bend_ptr != nullptr) + (c ? 4 + 16 + 6 * bc + scan_extra(s) : 0) +
+  return 1 + (s->d.bend_ptr != nullptr) + (c ? 4 + 13 + 6 * bc + scan_extra(s) : 0) +
          K * (local_kernels(s) + (c ? 1 : 0) + 1 + global) + (c ? 1 : 0) + 1 +
          5 * refined_iters(s, K) + (c ? silg::ws_kernels(s->d) : 0) +
          (c && s->d.pf_copies > 1 ? 1 : 0);
@@ -1100,20 +1100,8 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
   d.dl_state = s->alloc<int>(4);
   d.dl_prev_cv = s->alloc<int>(cap);
   cudaMemsetAsync(d.dl_state + 1, 0xff, sizeof(int), s->work);   // no previous list yet
-  // chunk items of 256 path entries: with at most cap_y entries in either layout of Y, a
-  // contact vertex (row of U) has at most len / 256 + 1 of them
-  d.ytz_items_cap = (int)std::min<long long>(cap_y / 256 + cap + 1, 1LL << 30);
-  d.yu_items_cap = (int)std::min<long long>(cap_y / 256 + n + 1, 1LL << 30);
-  d.ytz_cnt = s->alloc<int>(cap);
-  d.ytz_off = s->alloc<int>(cap + 1);
-  d.ytz_item = s->alloc<int2>(d.ytz_items_cap);
-  d.ytz_part = s->alloc<float4>(d.ytz_items_cap);
-  d.ytz_done = s->alloc<int>(cap);
-  d.yu_cnt = s->alloc<int>(n);
-  d.yu_off = s->alloc<int>(n + 1);
-  d.yu_item = s->alloc<int2>(d.yu_items_cap);
-  d.yu_part = s->alloc<float4>(d.yu_items_cap);
-  d.yu_done = s->alloc<int>(n);
+  // the path of a contact vertex in Y is its ancestor chain: a warp covers a short one
+  d.ytz_warp = p.mean_depth < 600.0 ? 1 : 0;
   d.spin_limit = o->spin_limit;
   d.kb_lo = s->alloc<int>(n / 32 + 1);
   d.kb_hi = s->alloc<int>(n / 32 + 1);
