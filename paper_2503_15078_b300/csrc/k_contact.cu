@@ -1466,26 +1466,20 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
     if (gen) publish_t(v);
     // this phase brings every contact vertex's u (12 bytes each) from its owner
     if (async_x) {
-      // the owned vertices' u per component in uloc, then one 4-byte store per (rank,
-      // component, owned vertex) into every rank (itself included), spread over all threads
-      // and counted on that rank's barrier
+      // the thread that computes an owned vertex's u stores it into every rank (itself
+      // included), counted on that rank's barrier (measured faster than staging u and
+      // spreading the stores over all threads after a block barrier)
       if (threadIdx.x == 0) mbar_expect(smem_u32(&xbar[0]), (unsigned)L.ncv * 12u);
-      float* ul = reinterpret_cast<float*>(uloc);   // [3][nv_max]
-      for (int cvl = threadIdx.x; cvl < nv; cvl += blockDim.x) {
-        const float4 u = vertex_u(v, cvl);
-        ul[cvl] = u.x;
-        ul[nv_max + cvl] = u.y;
-        ul[2 * nv_max + cvl] = u.z;
-      }
-      __syncthreads();
       const unsigned ub = smem_u32(usx + L.cv0), bb = smem_u32(&xbar[0]);
       const unsigned cstride = 4u * (unsigned)ldw;   // bytes between the component arrays
-      const int per_rank = 3 * nv;
-      for (int e = threadIdx.x; e < L.R * per_rank; e += blockDim.x) {
-        const int r = e / per_rank, rem = e - r * per_rank, comp = rem / max(nv, 1),
-                  cvl = rem - comp * nv;
-        st_async_f32(mapa_u32(ub + (unsigned)comp * cstride + 4u * (unsigned)cvl, r),
-                     ul[comp * nv_max + cvl], mapa_u32(bb, r));
+      for (int cvl = threadIdx.x; cvl < nv; cvl += blockDim.x) {
+        const float4 u = vertex_u(v, cvl);
+        for (int r = 0; r < L.R; ++r) {
+          const unsigned ra = mapa_u32(ub + 4u * (unsigned)cvl, r), rb = mapa_u32(bb, r);
+          st_async_f32(ra, u.x, rb);
+          st_async_f32(ra + cstride, u.y, rb);
+          st_async_f32(ra + 2u * cstride, u.z, rb);
+        }
       }
       if (!mbar_wait_cluster(smem_u32(&xbar[0]), ph_u & 1u, d.spin_limit) && threadIdx.x == 0)
         atomicOr(d.err, kErrTimeout);
