@@ -317,12 +317,21 @@ int sim_create(const sim_mesh* mesh, const sim_material* mats, int32_t n_mat,
  * max |phi_b| / L, appear among the contacts (sim_get_contacts) with obstacle id = the
  * simulator's obstacle count + the anchor's index over all scenes, and in n_contacts.
  * vertex: a free (not pinned) vertex of its scene, at most one anchor per vertex;
- * compliance >= 0 (m/N; 0: a hard constraint). Anything else: SIM_EINVAL at creation. */
+ * compliance >= 0 (m/N; 0: a hard constraint).
+ * paired = 1 ties the vertex to another vertex instead (App. A.1's two-vertex bilateral
+ * rows, e.g. a cable): the rows of
+ *   phi_b = (q_v - q_partner) - p(t) + compliance * lambda_b = 0,
+ * p(t) the target offset; the impulse acts on the vertex and, opposite, on the partner (a
+ * free vertex of the same scene other than the vertex; it may be the partner of several
+ * anchors). paired = 0 (zero-initialised): the target form above, partner ignored.
+ * Anything else: SIM_EINVAL at creation. */
 typedef struct {
   int32_t vertex;
   double target[3];
   double vel[3];
   double compliance;
+  int32_t paired;
+  int32_t partner;
 } sim_anchor;
 
 /* One independent scene of a batch: its mesh, its materials (tet_material indexes this

@@ -199,7 +199,9 @@ def detect(scene, s_tilde, free_verts, t_end=0.0, body_data=None):
     """All (vertex, obstacle) pairs with signed distance below the contact margin at the
     predicted positions, ordered by vertex id then obstacle index; then, at its vertex, each
     anchor (a bilateral constraint, App. A.1's b rows) with the id n_obstacles + its index,
-    its target at time t_end (the end of the frame) and the world axes as its three rows;
+    its target at time t_end (the end of the frame) and the world axes as its three rows (an
+    anchor with a partner vertex is a two-vertex row: its map is q_v - q_partner, the
+    partner a corner of weight 1, and its target an offset);
     then, with body_data = (free mask, bodies, surface triangles), the vertex's contact with
     another body (detect_bodies) with the id n_obstacles + n_anchors + triangle index."""
     body_ct = {}
@@ -224,9 +226,13 @@ def detect(scene, s_tilde, free_verts, t_end=0.0, body_data=None):
             an = scene.anchors[a]
             target = np.asarray(an.target, float) + t_end * np.asarray(an.vel, float)
             eye = np.eye(3)
-            out.append(dict(vertex=int(v), obstacle=n_obs + a, n=eye[0], f1=eye[1], f2=eye[2],
-                            anchor=True, target=target, compliance=float(an.compliance),
-                            d_n=float(target[0]), d_f=np.zeros(2), mu=0.0, gap=0.0))
+            row = dict(vertex=int(v), obstacle=n_obs + a, n=eye[0], f1=eye[1], f2=eye[2],
+                       anchor=True, target=target, compliance=float(an.compliance),
+                       d_n=float(target[0]), d_f=np.zeros(2), mu=0.0, gap=0.0)
+            partner = int(getattr(an, "partner", -1))
+            if partner >= 0:
+                row["corners"] = [(partner, 1.0)]
+            out.append(row)
         if int(v) in body_ct:
             out.append(body_ct[int(v)])
     return out

@@ -299,6 +299,9 @@ class Simulator:
                             an[i].target[r] = float(a.target[r])
                             an[i].vel[r] = float(a.vel[r])
                         an[i].compliance = float(a.compliance)
+                        partner = int(getattr(a, "partner", -1))
+                        an[i].paired = 1 if partner >= 0 else 0
+                        an[i].partner = max(partner, 0)
                     self._keep.append(an)
                     scs[k].anchors = C.cast(an, C.POINTER(_abi.SimAnchor))
                     scs[k].n_anchors = len(anchors)

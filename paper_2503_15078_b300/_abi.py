@@ -39,7 +39,7 @@ class SimObstacle(C.Structure):
 
 class SimAnchor(C.Structure):
     _fields_ = [("vertex", C.c_int32), ("target", C.c_double * 3), ("vel", C.c_double * 3),
-                ("compliance", C.c_double)]
+                ("compliance", C.c_double), ("paired", C.c_int32), ("partner", C.c_int32)]
 
 
 class SimScene(C.Structure):

@@ -129,6 +129,10 @@ struct DevSim {
   const double* anc_pos0;     // 3 n_anc: the target at time 0
   const double* anc_vel;      // 3 n_anc
   const double* anc_e;        // n_anc: compliance
+  const int* anc_partner;     // n_anc: the partner of a two-vertex row (internal id), or -1
+  const int* anc_ptri;        // n_anc: its one-corner map entry in btri, or -1
+  int n_pairs;                // anchors with a partner
+  int map_on;                 // contact maps beyond one vertex (bodies or pairs)
   const double* scene_margin; // contact margin
   const double* scene_Lref;   // rest bounding-box diagonal (residual scale)
   const double* scene_hvel;   // 3 per scene: velocity of the scene's pinned vertices

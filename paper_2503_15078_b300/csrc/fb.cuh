@@ -87,12 +87,13 @@ __device__ inline void ncp_rows(bool minmap, double dn, const double vf[2], doub
 }
 
 // The map of contact j applied to a per-vertex field: f_v for a contact at one vertex,
-// f_v - sum_k w_k f_k (the triangle's corners) for a contact with another body.
+// f_v - sum_k w_k f_k (the triangle's corners) for a contact with another body, and
+// f_v - f_partner for a two-vertex anchor row (a one-corner map entry of weight 1).
 template <typename Field>
 __device__ inline void contact_map(const DevSim& d, int j, Field f, double o[3]) {
   const int v = d.ct_vert[j];
   for (int r = 0; r < 3; ++r) o[r] = f(v, r);
-  if (!d.bc_on || d.ct_tri[j] < 0) return;
+  if (!d.map_on || d.ct_tri[j] < 0) return;
   const int4 t = d.btri[d.ct_tri[j]];
   const int cs[3] = {t.x, t.y, t.z};
   for (int k = 0; k < 3; ++k) {
@@ -104,10 +105,10 @@ __device__ inline void contact_map(const DevSim& d, int j, Field f, double o[3])
 
 // the map at the iterate q = q_ref + dq, and of dq alone; a common translation `shift` of
 // the scene adds to a one-vertex contact only (the weights of a contact with another body
-// sum to one)
+// sum to one, and a two-vertex row's map is a difference)
 __device__ inline void contact_q(const DevSim& d, int j, const double* shift, double q[3]) {
   contact_map(d, j, [&](int v, int r) { return d.q_ref[3 * v + r] + (double)d.dq[3 * v + r]; }, q);
-  if (shift && !(d.bc_on && d.ct_tri[j] >= 0))
+  if (shift && !(d.map_on && d.ct_tri[j] >= 0))
     for (int r = 0; r < 3; ++r) q[r] += shift[r];
 }
 __device__ inline void contact_dq(const DevSim& d, int j, double dq[3]) {

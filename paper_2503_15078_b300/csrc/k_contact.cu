@@ -334,12 +334,12 @@ __global__ void k_collide_count(DevSim d) {
     if (obst_query(d.obst[o], x, nn, ph) < margin) ++cnt;
   }
   if (d.n_anc > 0 && d.anc_of[i] >= 0) ++cnt;   // its anchor: one more slot, after the obstacles
-  if (d.bc_on) {
-    // its contact with another body: one more slot, after the anchor
+  if (d.map_on) {
     d.x_cnt[i] = 0;
     d.x_fill[i] = 0;
-    if (body_match(d, i, x, margin)) ++cnt;
   }
+  // its contact with another body: one more slot, after the anchor
+  if (d.bc_on && body_match(d, i, x, margin)) ++cnt;
   d.ct_cnt[i] = cnt;
   d.cv_flag[i] = cnt > 0;
 }
@@ -349,6 +349,13 @@ __global__ void k_collide_count(DevSim d) {
 __global__ void k_corner_flag(DevSim d) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n) return;
+  // the partner of a two-vertex anchor row at i: a contact vertex with one corner term
+  const int a = d.n_anc > 0 ? d.anc_of[i] : -1;
+  if (a >= 0 && d.anc_partner[a] >= 0) {
+    d.cv_flag[d.anc_partner[a]] = 1;
+    atomicAdd(d.x_cnt + d.anc_partner[a], 1);
+  }
+  if (!d.bc_on) return;
   const int t = d.bc_tri[i];
   if (t < 0) return;
   const int4 tv = d.btri[t];
@@ -406,7 +413,7 @@ __global__ void k_collide_write(DevSim d) {
       d.ct_vert[j] = i;
       d.ct_obst[j] = o;
       d.ct_cv[j] = cv;
-      if (d.bc_on) d.ct_tri[j] = -1;
+      if (d.map_on) d.ct_tri[j] = -1;
       d.ct_dn[j] = n[0] * ph[0] + n[1] * ph[1] + n[2] * ph[2];
       d.ct_df[2 * j] = f1[0] * ob.vel[0] + f1[1] * ob.vel[1] + f1[2] * ob.vel[2];
       d.ct_df[2 * j + 1] = f2[0] * ob.vel[0] + f2[1] * ob.vel[1] + f2[2] * ob.vel[2];
@@ -415,9 +422,10 @@ __global__ void k_collide_write(DevSim d) {
     ++j;
   }
   const int a = d.n_anc > 0 ? d.anc_of[i] : -1;
+  const int pb = a >= 0 ? d.anc_partner[a] : -1;   // the partner of a two-vertex row
   if (a >= 0 && j < d.cap) {
-    // the anchor's slot: rows e_x, e_y, e_z; the target (at the frame's end) in ct_dn and
-    // ct_df; the compliance in ct_mu
+    // the anchor's slot: rows e_x, e_y, e_z; the target (or target offset, at the frame's
+    // end) in ct_dn and ct_df; the compliance in ct_mu
     for (int r = 0; r < 9; ++r) d.ct_D[9 * j + r] = (r % 4 == 0) ? 1.0 : 0.0;
     d.ct_vert[j] = i;
     d.ct_obst[j] = d.n_obs + a;
@@ -426,7 +434,23 @@ __global__ void k_collide_write(DevSim d) {
     d.ct_df[2 * j] = d.anc_pos[3 * a + 1];
     d.ct_df[2 * j + 1] = d.anc_pos[3 * a + 2];
     d.ct_mu[j] = d.anc_e[a];
-    if (d.bc_on) d.ct_tri[j] = -1;
+    if (d.map_on) d.ct_tri[j] = -1;
+    if (pb >= 0) {
+      // a two-vertex row: the map x_i - 1 x_partner (a one-corner map entry, weight 1)
+      d.ct_tri[j] = d.anc_ptri[a];
+      d.ct_bw[3 * j] = 1.0;
+      d.ct_bw[3 * j + 1] = d.ct_bw[3 * j + 2] = 0.0;
+      const int cc = d.cv_off[pb];
+      d.ct_tcv[3 * j] = cc < d.cap ? cc : -1;
+      d.ct_tcv[3 * j + 1] = d.ct_tcv[3 * j + 2] = -1;
+      const int pos = d.x_off[pb] + atomicAdd(d.x_fill + pb, 1);
+      if (pos < 3 * d.cap) d.x_list[pos] = 3 * j;
+    }
+  } else if (a >= 0 && pb >= 0) {
+    // beyond the capacity (the frame reports SIM_ECAPACITY): the counted corner term is
+    // filled with -1, which every reader skips
+    const int pos = d.x_off[pb] + atomicAdd(d.x_fill + pb, 1);
+    if (pos < 3 * d.cap) d.x_list[pos] = -1;
   }
   if (a >= 0) ++j;
   const int t = d.bc_on ? d.bc_tri[i] : -1;
@@ -927,7 +951,7 @@ __global__ void k_precond(DevSim d) {
   int tc[4] = {cv, -1, -1, -1};
   double tw[4] = {1.0, 0.0, 0.0, 0.0};
   int tv[4] = {d.ct_vert[j], 0, 0, 0};
-  if (d.bc_on && d.ct_tri[j] >= 0) {
+  if (d.map_on && d.ct_tri[j] >= 0) {
     const int4 t = d.btri[d.ct_tri[j]];
     const int cs[3] = {t.x, t.y, t.z};
     for (int k = 0; k < 3; ++k) {
@@ -1057,14 +1081,14 @@ __global__ void __launch_bounds__(kYtzThreads) k_ytz(DevSim d) {
         s1 += part[1][w];
         s2 += part[2][w];
       }
-      if (d.bc_on && lane == 0) {
+      if (d.map_on && lane == 0) {
         d.svec[3 * c] = s0;
         d.svec[3 * c + 1] = s1;
         d.svec[3 * c + 2] = s2;
       }
       const int j0 = d.cv_first[c], j1 = min(j0 + d.cv_nct[c], d.cap);
       for (int j = j0 + lane; j < j1; j += 32) {
-        if (d.bc_on && d.ct_tri[j] >= 0) continue;   // k_body_rhs
+        if (d.map_on && d.ct_tri[j] >= 0) continue;   // k_body_rhs
         for (int r = 0; r < 3; ++r) {
           const float* Dr = d.ct_Df + 9 * j + 3 * r;
           const float jag = d.ct_omega[3 * j + r] * (Dr[0] * s0 + Dr[1] * s1 + Dr[2] * s2);
@@ -1099,14 +1123,14 @@ __global__ void k_ytz_warp(DevSim d) {
     s0 = warp_sum(s0);
     s1 = warp_sum(s1);
     s2 = warp_sum(s2);
-    if (d.bc_on && lane == 0) {
+    if (d.map_on && lane == 0) {
       d.svec[3 * c] = s0;
       d.svec[3 * c + 1] = s1;
       d.svec[3 * c + 2] = s2;
     }
     const int j0 = d.cv_first[c], j1 = min(j0 + d.cv_nct[c], d.cap);
     for (int j = j0 + lane; j < j1; j += 32) {
-      if (d.bc_on && d.ct_tri[j] >= 0) continue;   // k_body_rhs
+      if (d.map_on && d.ct_tri[j] >= 0) continue;   // k_body_rhs
       for (int r = 0; r < 3; ++r) {
         const float* Dr = d.ct_Df + 9 * j + 3 * r;
         const float jag = d.ct_omega[3 * j + r] * (Dr[0] * s0 + Dr[1] * s1 + Dr[2] * s2);
@@ -1315,7 +1339,7 @@ __global__ void __launch_bounds__(kCrThreads, 1) k_cr(DevSim d, int smem_bytes) 
   // whose contact vertices may belong to another rank) two more exchanges per product:
   //   tall[c] float4   D_j^T (omega_j v_j) of every contact of the scene
   //   wall[ldw] float4 (W~ u) of every contact vertex of the scene
-  const bool gen = d.bc_on != 0;
+  const bool gen = d.map_on != 0;
   float4* dots = reinterpret_cast<float4*>(sm);          // kCrDotSlots float4
   float* usx = reinterpret_cast<float*>(dots + kCrDotSlots);   // ldw floats each
   float* usy = usx + ldw;
@@ -2084,14 +2108,14 @@ void launch_collide(const DevSim& d, cudaStream_t s) {
     k_super_box<<<(d.n_btri / kTriSuper + 1 + 127) / 128, 128, 0, s>>>(d);
   }
   k_collide_count<<<g, 64, 0, s>>>(d);
-  if (d.bc_on) {
+  if (d.map_on) {
     k_corner_flag<<<(d.n + 255) / 256, 256, 0, s>>>(d);
     launch_scan(d.x_cnt, d.x_off, d.n, nullptr, nullptr, s, d.scan_part);
   }
   launch_scan(d.ct_cnt, d.ct_off, d.n, nullptr, d.counters + kCntContacts, s, d.scan_part);
   launch_scan(d.cv_flag, d.cv_off, d.n, nullptr, d.counters + kCntCv, s, d.scan_part);
   k_collide_write<<<g, 64, 0, s>>>(d);
-  if (d.bc_on) k_corner_sort<<<(d.n + 255) / 256, 256, 0, s>>>(d);
+  if (d.map_on) k_corner_sort<<<(d.n + 255) / 256, 256, 0, s>>>(d);
 }
 
 void launch_delassus(const DevSim& d, cudaStream_t s) {
@@ -2166,7 +2190,7 @@ void launch_ytz(const DevSim& d, cudaStream_t s) {
     launch_k(d.pdl, k_ytz_warp, std::min((d.cap + 7) / 8, 8 * d.n_sm), 256, 0, s, d);
   else
     launch_k(d.pdl, k_ytz, std::min(d.cap, 8 * d.n_sm), kYtzThreads, 0, s, d);
-  if (d.bc_on) launch_k(d.pdl, k_body_rhs, (d.cap + 127) / 128, 128, 0, s, d);
+  if (d.map_on) launch_k(d.pdl, k_body_rhs, (d.cap + 127) / 128, 128, 0, s, d);
 }
 
 void launch_yu(const DevSim& d, cudaStream_t s) {
@@ -2244,7 +2268,7 @@ int launch_cr(const DevSim& d, cudaStream_t s, int cluster) {
   cfg.numAttrs = d.pdl ? 2 : 1;
   // one exchange per CR iteration when asked for and the scene has no contacts between
   // bodies; the two-exchange form otherwise
-  const bool one = d.cr_single && !d.bc_on;
+  const bool one = d.cr_single && !d.map_on;
   return cudaLaunchKernelEx(&cfg, one ? k_cr1 : k_cr, d, (int)g_cr_smem) == cudaSuccess ? SIM_OK
                                                                                        : SIM_ECUDA;
 }

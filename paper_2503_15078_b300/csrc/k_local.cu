@@ -492,8 +492,9 @@ __global__ void k_rhs(DevSim d) {
 #pragma unroll
       for (int r = 0; r < 3; ++r) b[r] += h2 * d.ct_force[3 * j + r];
   }
-  if (d.bc_on) {
-    // the vertex as a corner of other bodies' contacts: -w_k of their force
+  if (d.map_on) {
+    // the vertex as a corner of other bodies' contacts (or the partner of a two-vertex
+    // anchor row): -w_k of their force
     const int xe = min(d.x_off[i + 1], 3 * d.cap);
     for (int e = d.x_off[i]; e < xe; ++e) {
       const int tk = d.x_list[e];

@@ -178,7 +178,7 @@ int frame_iters(sim_s* s) {
 // the capacity-length one (Y column lengths)
 int scan_extra(const sim_s* s) {
   const int n = s->d.n, cap = s->d.cap;
-  return (3 + (s->d.bc_on ? 1 : 0) + 1) * (silg::scan_launches(n) - 1) +
+  return (3 + (s->d.map_on ? 1 : 0) + 1) * (silg::scan_launches(n) - 1) +
          (silg::scan_launches(cap) - 1);
 }
 
@@ -188,14 +188,16 @@ int local_kernels(const sim_s* s) { return (s->d.n_tets > 0) + (s->d.n_tris > 0)
 // launches of a frame to a tolerance that made K updates (enqueue_frame_to_tolerance)
 int kernels_per_frame_to_tolerance(const sim_s* s, int K) {
   const bool c = s->has_obstacles;
-  const int bc = s->d.bc_on ? 1 : 0;   // contacts between bodies: 6 more collision launches,
-                                       // one more per constraint solve
+  // contacts between bodies: 3 more collision launches (the body search); maps beyond one
+  // vertex (bodies or two-vertex anchor rows): 3 more (corner terms) and one more per
+  // constraint solve
+  const int bc = s->d.bc_on ? 1 : 0, mp = s->d.map_on ? 1 : 0;
   const int scans = scan_extra(s);
   const int refine_body = s->d.s_bf16 && s->d.refine >= 2 && !s->d.jacobi_sweeps ? 5 : 0;
   const int refine_end = s->d.s_bf16 && s->d.refine == 1 && !s->d.jacobi_sweeps ? 6 : 0;
-  const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 + bc : 0) + 2;
+  const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 + mp : 0) + 2;
   const int before = 1 + (s->d.bend_ptr != nullptr) +
-                     (c ? 4 + 13 + 6 * bc + scans + silg::ws_kernels(s->d) : 0) +
+                     (c ? 4 + 13 + 3 * bc + 3 * mp + scans + silg::ws_kernels(s->d) : 0) +
                      local_kernels(s) +
                      (c ? 1 : 0);
   const int body = 1 + global + refine_body + 1 + (c ? 1 : 0) + local_kernels(s) + 1;
@@ -207,9 +209,9 @@ int kernels_per_frame(const sim_s* s, int K) {
   const bool c = s->has_obstacles;
   // per iteration: local, [contact eval], rhs, pass 1 + reduction, [Y^T z, CR, Y u],
   // pass 2 + reduction; a residual correction adds the residual and both passes
-  const int bc = s->d.bc_on ? 1 : 0;
-  const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 + bc : 0) + 2;
-  return 1 + (s->d.bend_ptr != nullptr) + (c ? 4 + 13 + 6 * bc + scan_extra(s) : 0) +
+  const int bc = s->d.bc_on ? 1 : 0, mp = s->d.map_on ? 1 : 0;
+  const int global = s->d.jacobi_sweeps ? s->d.jacobi_sweeps : 2 + (c ? 3 + mp : 0) + 2;
+  return 1 + (s->d.bend_ptr != nullptr) + (c ? 4 + 13 + 3 * bc + 3 * mp + scan_extra(s) : 0) +
          K * (local_kernels(s) + (c ? 1 : 0) + 1 + global) + (c ? 1 : 0) + 1 +
          5 * refined_iters(s, K) + (c ? silg::ws_kernels(s->d) : 0) +
          (c && s->d.pf_copies > 1 ? 1 : 0);
@@ -755,6 +757,14 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
       }
       e[a] = an.compliance;
     }
+    // two-vertex rows: the partner's internal id per anchor (-1: a target anchor), and a
+    // one-corner map entry per pair, appended after the bodies' surface triangles
+    std::vector<int> partner(std::max(1, na), -1);
+    for (int a = 0; a < na; ++a)
+      if (sd.anchors[a].partner >= 0) partner[a] = p.internal[sd.anchors[a].partner];
+    d.anc_partner = s->upload(partner);
+    d.n_pairs = 0;
+    for (int a = 0; a < na; ++a) d.n_pairs += partner[a] >= 0;
     d.anc_of = s->upload(of);
     d.anc_pos0 = s->upload(pos);
     d.anc_pos = s->upload(pos);
@@ -774,16 +784,50 @@ int create_device(sim_s* s, const SceneData& sd, const sim_options* o) {
     const int nb = (int)sd.body_toff.size() - 1;
     d.n_bodies = nb;
     d.bc_on = nb > 0;
+    // contact maps beyond one vertex: contacts between bodies and two-vertex anchor rows
+    d.map_on = d.bc_on || d.n_pairs > 0;
+    if (d.map_on && !d.bc_on) {
+      // pairs only: their map entries, no bodies to search
+      std::vector<int4> bt(std::max(1, d.n_pairs));
+      std::vector<int> ptri(std::max(1, (int)sd.anchors.size()), -1);
+      int k = 0;
+      for (int a = 0; a < (int)sd.anchors.size(); ++a)
+        if (sd.anchors[a].partner >= 0) {
+          const int b = p.internal[sd.anchors[a].partner];
+          bt[k] = make_int4(b, b, b, -1);
+          ptri[a] = k++;
+        }
+      d.btri = s->upload(bt);
+      d.anc_ptri = s->upload(ptri);
+      d.n_btri = 0;
+      d.x_cnt = s->alloc<int>(n);
+      d.x_fill = s->alloc<int>(n);
+      d.x_off = s->alloc<int>(n + 1);
+      d.x_list = s->alloc<int>(3 * (size_t)d.cap);
+      d.ct_tri = s->alloc<int>(d.cap);
+      d.ct_bw = s->alloc<double>(3 * (size_t)d.cap);
+      d.ct_tcv = s->alloc<int>(3 * (size_t)d.cap);
+    }
     if (d.bc_on) {
       std::vector<int> vb(std::max(1, n), -1);
       for (int v = 0; v < n_all; ++v)
         if (p.internal[v] < n) vb[p.internal[v]] = sd.vert_body[v];
       d.vert_body = s->upload(vb);
-      std::vector<int4> bt(std::max<size_t>(1, sd.btri.size()));
+      // the bodies' surface triangles, then one one-corner map entry per pair anchor
+      std::vector<int4> bt(std::max<size_t>(1, sd.btri.size() + d.n_pairs));
       for (size_t t = 0; t < sd.btri.size(); ++t)
         bt[t] = make_int4(p.internal[sd.btri[t][0]], p.internal[sd.btri[t][1]],
                           p.internal[sd.btri[t][2]], sd.btri[t][3]);
+      std::vector<int> ptri(std::max(1, (int)sd.anchors.size()), -1);
+      int k = (int)sd.btri.size();
+      for (int a = 0; a < (int)sd.anchors.size(); ++a)
+        if (sd.anchors[a].partner >= 0) {
+          const int b = p.internal[sd.anchors[a].partner];
+          bt[k] = make_int4(b, b, b, -1);
+          ptri[a] = k++;
+        }
       d.btri = s->upload(bt);
+      d.anc_ptri = s->upload(ptri);
       d.body_toff = s->upload(sd.body_toff);
       d.scene_bfirst = s->upload(sd.scene_bfirst);
       d.scene_bmu = s->upload(sd.bmu);
@@ -1362,12 +1406,19 @@ int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_opt
           if (m.pinned[q] >= 0 && m.pinned[q] < m.n_verts) used[m.pinned[q]] = 1;
         for (int q = 0; q < sc.n_anchors; ++q) {
           sim_anchor a = sc.anchors[q];
-          bool ok = a.vertex >= 0 && a.vertex < m.n_verts && used[a.vertex] == 0 &&
-                    std::isfinite(a.compliance) && a.compliance >= 0.0;
+          bool ok = a.vertex >= 0 && a.vertex < m.n_verts && used[a.vertex] != 1 &&
+                    used[a.vertex] != 2 && std::isfinite(a.compliance) &&
+                    a.compliance >= 0.0 && (a.paired == 0 || a.paired == 1);
           for (int r = 0; r < 3; ++r) ok = ok && std::isfinite(a.target[r]) && std::isfinite(a.vel[r]);
+          // the partner of a pair: another free vertex of the same scene
+          if (a.paired)
+            ok = ok && a.partner >= 0 && a.partner < m.n_verts && a.partner != a.vertex &&
+                 used[a.partner] != 1;
           if (!ok) return SIM_EINVAL;
           used[a.vertex] = 2;
           a.vertex += voff;
+          if (a.paired) a.partner += voff;
+          else a.partner = -1;
           sd.anchors.push_back(a);
         }
       }
@@ -1492,6 +1543,8 @@ int create_common(const sim_scene* scenes, int n_scenes, double h, const sim_opt
           mix(a.target, sizeof(a.target));
           mix(a.vel, sizeof(a.vel));
           mix(&a.compliance, sizeof(double));
+          mix(&a.paired, sizeof(a.paired));
+          if (a.paired) mix(&a.partner, sizeof(a.partner));
         }
         s->scene_sig.push_back(hsh);
       }

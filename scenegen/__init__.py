@@ -16,6 +16,7 @@ Scene workloads (the paper's meshes are not available, so these stand in for the
   Fig. 8): the analytic threshold is mu* = tan(theta).
 * ``single_tet``  - one regular tetrahedron, for closed-form checks.
 * ``batch``       - dozens of cubes of uneven size with mixed materials on tilted planes.
+* ``tied_cubes``  - two cubes tied across a gap by two-vertex bilateral rows (App. A.1).
 """
 from __future__ import annotations
 
@@ -47,11 +48,15 @@ class Material:
 class Anchor:
     """A bilateral constraint tying a free vertex to a target point: the three rows
     e_x, e_y, e_z of (q_v - target) + compliance * lambda = 0. The target starts at
-    ``target`` and moves at ``vel``; compliance (m/N) 0 makes the constraint hard."""
+    ``target`` and moves at ``vel``; compliance (m/N) 0 makes the constraint hard. With
+    ``partner`` >= 0 the rows tie the vertex to that vertex instead (App. A.1's two-vertex
+    bilateral rows): (q_v - q_partner) - target + compliance * lambda = 0, the target then
+    an offset."""
     vertex: int
     target: tuple
     vel: tuple = (0.0, 0.0, 0.0)
     compliance: float = 0.0
+    partner: int = -1
 
 
 @dataclass
@@ -453,6 +458,41 @@ def hanging_cube(m: int = 5, edge: float = 0.1, model: int = MODEL_ARAP, E: floa
     sc = Scene(f"hang{m}", X, tets, np.zeros(len(tets), np.int32), [Material(model, E, nu, rho)],
                obst, h, contact_margin=0.5 * edge / (m - 1), spacing=edge / (m - 1))
     sc.anchors = [Anchor(top, tuple(float(x) for x in X[top]), tuple(target_vel), compliance)]
+    return sc
+
+
+def tied_cubes(m: int = 4, edge: float = 0.1, gap: float = 0.05, model: int = MODEL_ARAP,
+               E: float = 1e5, nu: float = 0.4, rho: float = 1000.0, compliance: float = 0.0,
+               pull: float = 0.0, h: float = 1.0 / 60.0, floor: bool = True,
+               height: float = 0.01, mu: float = 0.5, gravity=GRAVITY_EARTH) -> Scene:
+    """Two m^3-vertex cubes side by side along x, ``gap`` apart, tied across the gap by
+    two-vertex bilateral rows (App. A.1) between the four corners of the facing faces (each
+    row a vertex of cube A against the facing vertex of cube B, target offset their rest
+    offset, shrinking at ``pull`` m/s along x: a cable drawing them together); optionally
+    ``height`` above a floor plane."""
+    Xa, ta = lattice_tets(m, m, m, edge / (m - 1))
+    Xb = Xa + np.array([edge + gap, 0.0, 0.0])
+    X = np.vstack([Xa, Xb])
+    tets = np.vstack([ta, ta + len(Xa)])
+    X[:, 2] += height
+    lo, hi = Xa[:, 0].min(), Xa[:, 0].max()
+    ya, za = Xa[:, 1], Xa[:, 2]
+    corners = [i for i in range(len(Xa)) if abs(Xa[i, 0] - hi) < 1e-12 and
+               min(abs(ya[i] - ya.min()), abs(ya[i] - ya.max())) < 1e-12 and
+               min(abs(za[i] - za.min()), abs(za[i] - za.max())) < 1e-12]
+    obst = []
+    if floor:
+        obst.append(Obstacle(OBST_PLANE, (0.0, 0.0, 0.0), (0.0, 0.0, 1.0), mu=mu))
+    sc = Scene(f"tied{m}", X, tets, np.zeros(len(tets), np.int32), [Material(model, E, nu, rho)],
+               obst, h, gravity=gravity, contact_margin=0.5 * edge / (m - 1),
+               spacing=edge / (m - 1))
+    for a in corners:
+        # the facing vertex of cube B: same y, z on its -x face
+        b = len(Xa) + int(np.argmin(np.abs(Xa[:, 0] - lo) * 1e3 + np.abs(ya - ya[a]) +
+                                     np.abs(za - za[a])))
+        off = X[a] - X[b]
+        sc.anchors.append(Anchor(int(a), tuple(float(x) for x in off), (pull, 0.0, 0.0),
+                                 compliance, partner=b))
     return sc
 
 
