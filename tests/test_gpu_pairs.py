@@ -38,7 +38,7 @@ def test_tied_cubes_frame_matches_oracle(compliance):
     OC, cr64, cr32 = _cr32()
     OC.conjugate_residual = cr32
     try:
-        q32, _, _ = o.frame(sc.q0, sc.v0, opts)
+        q32, _, info32 = o.frame(sc.q0, sc.v0, opts)
     finally:
         OC.conjugate_residual = cr64
     dev32 = _relerr(q32 - sc.q0, q - sc.q0)
@@ -55,10 +55,14 @@ def test_tied_cubes_frame_matches_oracle(compliance):
     print(f"\ntied cubes (e = {compliance}): {len(ref)} rows, displacement error {err:.2e}, "
           f"oracle float32 deviation {dev32:.2e}")
     assert err < max(1e-5, 10 * dev32)
-    # the pair rows' impulses
+    # the pair rows' impulses: how the load of cube B splits over four rows and the floor
+    # contacts is what FP32 moves (the oracle's own float32 run: 5.4e-2 for hard rows,
+    # 6e-3 for compliant ones), so they are held to 10x the oracle's float32 deviation
     rows = [j for j, c in enumerate(info["contacts"]) if c.get("anchor")]
     lo, lg = np.asarray(info["lam"])[rows], ct["lam"][rows]
-    assert _relerr(lg, lo) < max(1e-4, 100 * dev32)
+    lam_dev32 = _relerr(np.asarray(info32["lam"])[rows], lo)
+    print(f"pair impulses error {_relerr(lg, lo):.2e}, oracle float32 deviation {lam_dev32:.2e}")
+    assert _relerr(lg, lo) < max(1e-4, 10 * lam_dev32)
     sim.close()
 
 
@@ -85,21 +89,31 @@ def test_free_tied_cubes_conserve_momentum():
 
 
 def test_pulled_pair_rows_frame_by_frame():
-    # hard rows whose offset shrinks at 0.3 m/s, the cubes on the floor: each GPU frame
-    # starts from the oracle's state at the same time (the offset's target is time-dependent)
+    # hard rows whose offset shrinks at 0.3 m/s, the cubes on the floor, 6 frames from rest
+    # (the simulator's clock, which moves the offset, runs from its last set_state, so each
+    # comparison replays from the start). Hard rows beside floor contacts make the frames
+    # FP32-sensitive (the oracle's own float32 run moves them by 4e-3 to 9e-3), so each
+    # frame is held to 10x the oracle's float32 deviation on the same frames
     sc = sg.tied_cubes(m=4, compliance=0.0, pull=0.3, height=-0.0002)
     o = Oracle(sc)
+    OC, cr64, cr32 = _cr32()
     sim = Simulator(sc)
-    q, v = sc.q0.copy(), sc.v0.copy()
     for f in range(6):
-        # the simulator's own clock runs from its last set_state, so replay from the start
         sim.set_state(sc.q0, sc.v0)
         qo, vo = sc.q0.copy(), sc.v0.copy()
+        q3, v3 = qo.copy(), vo.copy()
         for g in range(f + 1):
-            qo, vo, info = o.frame(qo, vo, OracleOptions(n_iters=5, n_cr=sc.n_cr), t=g * sc.h)
+            opts = OracleOptions(n_iters=5, n_cr=sc.n_cr)
+            qo, vo, _ = o.frame(qo, vo, opts, t=g * sc.h)
+            OC.conjugate_residual = cr32
+            try:
+                q3, v3, _ = o.frame(q3, v3, opts, t=g * sc.h)
+            finally:
+                OC.conjugate_residual = cr64
             sim.step(n_iters=5)
         qg, _ = sim.state()
-        assert _relerr(qg - sc.q0, qo - sc.q0) < 1e-3, f
+        dev32 = _relerr(q3 - sc.q0, qo - sc.q0)
+        assert _relerr(qg - sc.q0, qo - sc.q0) < max(1e-4, 10 * dev32), f
     # the rows drew the facing corners together
     for an in sc.anchors:
         assert (qg[an.vertex, 0] - qg[an.partner, 0]) - (sc.X[an.vertex, 0] - sc.X[an.partner, 0]) > 0.01
