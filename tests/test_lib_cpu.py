@@ -153,6 +153,22 @@ def test_invalid_anchors_are_rejected(bad):
     assert e.value.status == -1
 
 
+@pytest.mark.parametrize("bad", ["self", "range", "pinned"])
+def test_invalid_pair_rows_are_rejected(bad):
+    # a two-vertex row's partner: another free vertex of the same scene
+    sc = sg.tied_cubes(m=3)
+    a = sc.anchors[0]
+    if bad == "self":
+        a.partner = a.vertex
+    elif bad == "range":
+        a.partner = sc.n_verts
+    else:
+        sc.pinned = np.array([a.partner], np.int32)
+    with pytest.raises(SimError) as e:
+        Simulator(sc)
+    assert e.value.status == -1
+
+
 def test_allocator_hooks_must_come_in_pairs():
     with pytest.raises(SimError) as e:
         Simulator(sg.cube_drop(m=3), dev_alloc=lambda n, c: None)
