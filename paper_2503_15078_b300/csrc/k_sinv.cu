@@ -18,7 +18,12 @@
 // by the lanes while those loads are in flight. A run of tiles with the same row group
 // (pass 1) or column tile (pass 2) accumulates in registers and ends in one partial-sum
 // slot; a second kernel adds each row's (column's) slots in a fixed order, so results are
-// deterministic.
+// deterministic. The accumulations use packed FP32 FMAs (fma.rn.f32x2, two columns per
+// instruction).
+//
+// A second form of both products (k_pass1_bulk, k_pass2_bulk, below) moves each tile's row
+// runs into shared memory with bulk copies instead of register loads; the autotuner times
+// it beside the register form.
 #include <cuda_runtime.h>
 
 #include <algorithm>
