@@ -36,15 +36,15 @@ namespace {
 
 constexpr int RG = kRowGroup;
 constexpr int TW = kTileW;
-constexpr int kChunks = TW / 128;  // 4-column chunks per lane per row
-
-// Value formats of the profile. A lane's 4-column chunk is one 16-byte load in FP32 and
-// one 8-byte load in BF16; the raw registers are widened to FP32 at the arithmetic.
-// BF16 keeps twice as many tiles in flight, so the bytes in flight per warp (and the
-// registers holding them) match the FP32 loop.
+// Value formats of the profile. A lane's chunk of a row is one 16-byte load: 4 values in
+// FP32, 8 in BF16 (kVec); a row of a tile is kChunks = kTileW / (32 kVec) chunks per lane.
+// The raw registers are widened to packed FP32 pairs at the arithmetic. BF16 keeps twice
+// as many tiles in flight, so the bytes in flight per warp (and the registers holding them)
+// match the FP32 loop.
 template <class T> struct Fmt;
 template <> struct Fmt<float> {
   using Raw = float4;
+  static constexpr int kVec = 4;
   static constexpr int kUnroll = 2;  // tiles in flight per warp
   static __device__ __forceinline__ const float* vals(const DevSim& d) { return d.S; }
   // streamed once: first in line for eviction from L1, so the vector slices read by
@@ -56,24 +56,36 @@ template <> struct Fmt<float> {
                  : "l"(p));
     return r;
   }
-  static __device__ __forceinline__ float4 widen(const Raw& r) { return r; }
+  // the chunk's values as the packed pairs (0, 1), (2, 3)
+  static __device__ __forceinline__ void pairs(const Raw& r, unsigned long long (&p)[2]) {
+    p[0] = f2pack(r.x, r.y);
+    p[1] = f2pack(r.z, r.w);
+  }
 };
 template <> struct Fmt<unsigned short> {
-  using Raw = uint2;
+  using Raw = uint4;
+  static constexpr int kVec = 8;
   static constexpr int kUnroll = 4;
   static __device__ __forceinline__ const unsigned short* vals(const DevSim& d) { return d.Sb; }
   static __device__ __forceinline__ Raw load(const unsigned short* p) {
     Raw r;
-    asm volatile("ld.global.nc.L1::evict_first.v2.u32 {%0, %1}, [%2];"
-                 : "=r"(r.x), "=r"(r.y)
+    asm volatile("ld.global.nc.L1::evict_first.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
                  : "l"(p));
     return r;
   }
-  // a BF16 value is the upper half of the FP32 with the same bits
-  static __device__ __forceinline__ float4 widen(const Raw& r) {
-    return make_float4(__uint_as_float(r.x << 16), __uint_as_float(r.x & 0xffff0000u),
-                       __uint_as_float(r.y << 16), __uint_as_float(r.y & 0xffff0000u));
+  // a BF16 value is the upper half of the FP32 with the same bits; the pairs (0, 1) .. (6, 7)
+  static __device__ __forceinline__ void pairs(const Raw& r, unsigned long long (&p)[4]) {
+    p[0] = f2pack(__uint_as_float(r.x << 16), __uint_as_float(r.x & 0xffff0000u));
+    p[1] = f2pack(__uint_as_float(r.y << 16), __uint_as_float(r.y & 0xffff0000u));
+    p[2] = f2pack(__uint_as_float(r.z << 16), __uint_as_float(r.z & 0xffff0000u));
+    p[3] = f2pack(__uint_as_float(r.w << 16), __uint_as_float(r.w & 0xffff0000u));
   }
+};
+template <class T> struct FmtShape {
+  static constexpr int kVec = Fmt<T>::kVec;
+  static constexpr int kPairs = kVec / 2;
+  static constexpr int kChunks = TW / (32 * kVec);
 };
 
 // CTAs per SM the products are built for: two with the format's tiles in flight (or half),
@@ -174,8 +186,10 @@ __global__ void __launch_bounds__(256, PassOcc<T, U>::kMinBlocks) k_pass1(DevSim
       }
     ++slot;
   };
+  using SH = FmtShape<T>;
+  constexpr int V = SH::kVec, NC = SH::kChunks;
   for (int t = t0; t < t1; t += U) {
-    typename F::Raw v[U][kRowsPerWarp][kChunks];
+    typename F::Raw v[U][kRowsPerWarp][NC];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int ct = __shfl_sync(0xffffffffu, mt.other, u * 4);
@@ -186,10 +200,11 @@ __global__ void __launch_bounds__(256, PassOcc<T, U>::kMinBlocks) k_pass1(DevSim
         const int hi = __shfl_sync(0xffffffffu, mt.hi, src);
         const long long base = __shfl_sync(0xffffffffu, mt.base, src);
 #pragma unroll
-        for (int m = 0; m < kChunks; ++m) {
-          const int c = ct * TW + 4 * lane + 128 * m;
+        for (int m = 0; m < NC; ++m) {
+          // runs start and end on multiples of 8 values: a chunk is inside or outside
+          const int c = ct * TW + V * lane + 32 * V * m;
           const bool ok = c >= lo && c < hi;   // empty for tiles past the range (lo = hi)
-          v[u][k][m] = F::load(ok ? S + base + c : zero + 4 * lane);
+          v[u][k][m] = F::load(ok ? S + base + c : zero + V * lane);
         }
       }
     }
@@ -211,18 +226,25 @@ __global__ void __launch_bounds__(256, PassOcc<T, U>::kMinBlocks) k_pass1(DevSim
         cur = rg;
       }
 #pragma unroll
-      for (int m = 0; m < kChunks; ++m) {
-        // g's four columns as the pairs (0, 1) and (2, 3)
-        const ulonglong2* gp =
-            reinterpret_cast<const ulonglong2*>(gsm + gs * 3 * (TW / 4) + lane + 32 * m);
-        const ulonglong2 g0 = gp[0], g1 = gp[TW / 4], g2 = gp[2 * (TW / 4)];
+      for (int m = 0; m < NC; ++m) {
+        // g's columns of the chunk as packed pairs, per component
+        const unsigned long long* gp = reinterpret_cast<const unsigned long long*>(
+            gsm + gs * 3 * (TW / 4) + (V * lane + 32 * V * m) / 4);
+        unsigned long long g[3][SH::kPairs];
+#pragma unroll
+        for (int comp = 0; comp < 3; ++comp)
+#pragma unroll
+          for (int i = 0; i < SH::kPairs; ++i) g[comp][i] = gp[comp * (TW / 2) + i];
 #pragma unroll
         for (int k = 0; k < kRowsPerWarp; ++k) {
-          const float4 sv = F::widen(v[u][k][m]);
-          const unsigned long long s01 = f2pack(sv.x, sv.y), s23 = f2pack(sv.z, sv.w);
-          acc[k][0] = ffma2(s23, g0.y, ffma2(s01, g0.x, acc[k][0]));
-          acc[k][1] = ffma2(s23, g1.y, ffma2(s01, g1.x, acc[k][1]));
-          acc[k][2] = ffma2(s23, g2.y, ffma2(s01, g2.x, acc[k][2]));
+          unsigned long long sp[SH::kPairs];
+          F::pairs(v[u][k][m], sp);
+#pragma unroll
+          for (int i = 0; i < SH::kPairs; ++i) {
+            acc[k][0] = ffma2(sp[i], g[0][i], acc[k][0]);
+            acc[k][1] = ffma2(sp[i], g[1][i], acc[k][1]);
+            acc[k][2] = ffma2(sp[i], g[2][i], acc[k][2]);
+          }
         }
       }
     }
@@ -270,21 +292,29 @@ __global__ void __launch_bounds__(256, PassOcc<T, U>::kMinBlocks) k_pass2(DevSim
   int slot = d.s2_seg_base[blockIdx.x];
   LaneMeta mt = fetch_meta<true>(d, d.s2_tiles, t1, t0, lane, warp, true);
   int cur = __shfl_sync(0xffffffffu, mt.key, 0);
-  // per chunk and component, the four columns' sums as the pairs (0, 1) and (2, 3)
-  unsigned long long acc[kChunks][3][2];
+  // per chunk and component, the chunk's columns' sums as packed pairs
+  using SH = FmtShape<T>;
+  constexpr int V = SH::kVec, NC = SH::kChunks, NP = SH::kPairs;
+  unsigned long long acc[NC][3][NP];
 #pragma unroll
-  for (int m = 0; m < kChunks; ++m)
+  for (int m = 0; m < NC; ++m)
 #pragma unroll
-    for (int comp = 0; comp < 3; ++comp) acc[m][comp][0] = acc[m][comp][1] = 0ull;
+    for (int comp = 0; comp < 3; ++comp)
+#pragma unroll
+      for (int i = 0; i < NP; ++i) acc[m][comp][i] = 0ull;
   // every warp reaches a flush at the same tile, so the barriers are uniform
   auto flush = [&]() {
 #pragma unroll
-    for (int m = 0; m < kChunks; ++m)
+    for (int m = 0; m < NC; ++m)
 #pragma unroll
       for (int comp = 0; comp < 3; ++comp) {
-        *reinterpret_cast<ulonglong2*>(&red[(warp * 3 + comp) * TW + 4 * lane + 128 * m]) =
-            make_ulonglong2(acc[m][comp][0], acc[m][comp][1]);
-        acc[m][comp][0] = acc[m][comp][1] = 0ull;
+        ulonglong2* dst =
+            reinterpret_cast<ulonglong2*>(&red[(warp * 3 + comp) * TW + V * lane + 32 * V * m]);
+#pragma unroll
+        for (int i = 0; i < NP / 2; ++i) {
+          dst[i] = make_ulonglong2(acc[m][comp][2 * i], acc[m][comp][2 * i + 1]);
+          acc[m][comp][2 * i] = acc[m][comp][2 * i + 1] = 0ull;
+        }
       }
     __syncthreads();
     float* out = d.p2_part + (size_t)slot * 3 * TW;
@@ -299,7 +329,7 @@ __global__ void __launch_bounds__(256, PassOcc<T, U>::kMinBlocks) k_pass2(DevSim
     ++slot;
   };
   for (int t = t0; t < t1; t += U) {
-    typename F::Raw v[U][kRowsPerWarp][kChunks];
+    typename F::Raw v[U][kRowsPerWarp][NC];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int ctu = __shfl_sync(0xffffffffu, mt.key, u * 4);
@@ -310,10 +340,10 @@ __global__ void __launch_bounds__(256, PassOcc<T, U>::kMinBlocks) k_pass2(DevSim
         const int hi = __shfl_sync(0xffffffffu, mt.hi, src);
         const long long base = __shfl_sync(0xffffffffu, mt.base, src);
 #pragma unroll
-        for (int m = 0; m < kChunks; ++m) {
-          const int c = ctu * TW + 4 * lane + 128 * m;
+        for (int m = 0; m < NC; ++m) {
+          const int c = ctu * TW + V * lane + 32 * V * m;
           const bool ok = c >= lo && c < hi;
-          v[u][k][m] = F::load(ok ? S + base + c : zero + 4 * lane);
+          v[u][k][m] = F::load(ok ? S + base + c : zero + V * lane);
         }
       }
     }
@@ -336,15 +366,15 @@ __global__ void __launch_bounds__(256, PassOcc<T, U>::kMinBlocks) k_pass2(DevSim
         const unsigned long long y00 = f2pack(y0, y0), y11 = f2pack(y1, y1),
                                  y22 = f2pack(y2, y2);
 #pragma unroll
-        for (int m = 0; m < kChunks; ++m) {
-          const float4 sv = F::widen(v[u][k][m]);
-          const unsigned long long s01 = f2pack(sv.x, sv.y), s23 = f2pack(sv.z, sv.w);
-          acc[m][0][0] = ffma2(s01, y00, acc[m][0][0]);
-          acc[m][0][1] = ffma2(s23, y00, acc[m][0][1]);
-          acc[m][1][0] = ffma2(s01, y11, acc[m][1][0]);
-          acc[m][1][1] = ffma2(s23, y11, acc[m][1][1]);
-          acc[m][2][0] = ffma2(s01, y22, acc[m][2][0]);
-          acc[m][2][1] = ffma2(s23, y22, acc[m][2][1]);
+        for (int m = 0; m < NC; ++m) {
+          unsigned long long sp[NP];
+          F::pairs(v[u][k][m], sp);
+#pragma unroll
+          for (int i = 0; i < NP; ++i) {
+            acc[m][0][i] = ffma2(sp[i], y00, acc[m][0][i]);
+            acc[m][1][i] = ffma2(sp[i], y11, acc[m][1][i]);
+            acc[m][2][i] = ffma2(sp[i], y22, acc[m][2][i]);
+          }
         }
       }
     }
